@@ -1,0 +1,75 @@
+"""The oracle's pins are sharp: each plausible slip, planted in a temporary
+copy of the oracle source (CPU only), makes at least one pin fail."""
+import ctypes
+import importlib.util
+import os
+import subprocess
+
+import pytest
+
+import tests.test_oracle_pins as pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# name -> (exact text in the oracle, planted replacement)
+MUTATIONS = {
+    "background term dropped from dalpha": (
+        "da += b.T * S * (gA - bgdot);", "da += b.T * S * (gA);"),
+    "camera rotation transposed in J W": (
+        "p.J[3 * i + 0] * k.R[0 + j] + p.J[3 * i + 1] * k.R[3 + j] + p.J[3 * i + 2] * k.R[6 + j]",
+        "p.J[3 * i + 0] * k.R[3 * j] + p.J[3 * i + 1] * k.R[3 * j + 1] + p.J[3 * i + 2] * k.R[3 * j + 2]"),
+    "clamped x' treated as constant in z": (
+        "else dmc[2] += p.clx * p.limx * dxcl;", "else dmc[2] += 0;"),
+    "conic off-diagonal sign": (
+        "p.conic[1] = -p.cov[1] / det;", "p.conic[1] = p.cov[1] / det;"),
+    "one quaternion partial sign": (
+        "{2 * qy, 2 * qz, 2 * w, 2 * qx},     // 2(xz + wy)",
+        "{2 * qy, 2 * qz, 2 * w, -2 * qx},     // 2(xz + wy)"),
+    "pose rotation term sign": (
+        "pose[3] += Wc[1] * dWc[2] - Wc[2] * dWc[1];", "pose[3] -= Wc[1] * dWc[2] - Wc[2] * dWc[1];"),
+    "tile rectangle end": (
+        "p.rect[2] = (int)i1 / kTile + 1;", "p.rect[2] = (int)(i1 + 1) / kTile + 1;"),
+    "suffix sum without (1 - alpha)": (
+        "Bd = b.alpha * depth[g] + (1 - b.alpha) * Bd;", "Bd = b.alpha * depth[g] + Bd;"),
+    "stop test after blending": (
+        "if (Tn < kTStop) break;\n    out.push_back({g, alpha, G, clamped, T, dx, dy});",
+        "out.push_back({g, alpha, G, clamped, T, dx, dy});\n    if (Tn < kTStop) break;"),
+    "depth order reversed": (
+        "std::sort(items.begin(), items.end());",
+        "std::sort(items.begin(), items.end(), [](const auto& a, const auto& b) {"
+        " return std::make_tuple(std::get<0>(a), -std::get<1>(a), std::get<2>(a)) <"
+        " std::make_tuple(std::get<0>(b), -std::get<1>(b), std::get<2>(b)); });"),
+    "low-pass filter dropped": (
+        "p.cov[0] = c2[0] + kLowPass;", "p.cov[0] = c2[0];"),
+}
+
+
+def _load_mutant(tmp_path, name, old, new):
+    src = open(os.path.join(ROOT, "oracle", "gsff_oracle.cpp")).read()
+    assert src.count(old) == 1, name
+    cpp = tmp_path / "mut.cpp"
+    so = tmp_path / "mut.so"
+    cpp.write_text(src.replace(old, new))
+    subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", str(cpp), "-o",
+                    str(so)], check=True, capture_output=True)
+    spec = importlib.util.spec_from_file_location("oracle_mutant", os.path.join(ROOT, "oracle", "__init__.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    lib = ctypes.CDLL(str(so))
+    lib.ora_bin.restype = ctypes.c_int64
+    lib.ora_num_threads.restype = ctypes.c_int
+    mod._lib = lib
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(tmp_path, sg, name):
+    old, new = MUTATIONS[name]
+    mut = _load_mutant(tmp_path, name, old, new)
+    failed = []
+    for tname in sorted(n for n in dir(pins) if n.startswith("test_")):
+        try:
+            getattr(pins, tname)(mut, sg)
+        except AssertionError:
+            failed.append(tname)
+    assert failed, f"no pin caught: {name}"
