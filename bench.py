@@ -1,0 +1,452 @@
+"""Benchmark: fwd+bwd of the feature-field Gaussian rasterizer at SLAM-frame scale.
+
+Workload (one step = one frame): 300,000 Gaussians on the walls and floor of
+a 6 x 5 x 3 m box room, 1200 x 680 pinhole camera (fx = fy = 600) on a
+100-frame smooth trajectory, RGB + depth + 16 feature channels. A step is
+project -> bin sort -> forward compositing -> L1 loss gradient of RGB, depth
+and features against a target rendered at the pose perturbed by Exp(1 cm,
+1 deg) -> backward (Gaussian gradients, decoupled feature gradient, SE(3) pose
+tangent). Inputs are synthetic (seeded), resident in HBM when the timed
+region starts; L2 is flushed (a 512 MB write) between timed steps.
+
+Output: one JSON line (rank 0). `value` is Gaussian-pixel blends per second
+over all ranks (blended pairs summed over the frames processed / max-over-
+ranks time); `ms_per_step` is fwd+bwd ms per frame. `--impl reference` times
+the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/frame and Gaussian-pixel blends/s at N=16..512 vs plain form"
+UNIT = "Gaussian-pixel blends/s"
+P_ROOM, WIDTH, HEIGHT, FOCAL, N_FEAT, N_FRAMES = 300_000, 1200, 680, 600.0, 16, 100
+SCENE_SEED, TRAJ_SEED = 3, 4
+WORKLOAD = "slam_frame_room300k_1200x680_N16_fwd_bwd_pose"
+
+
+def config(n_gpus, extra=None):
+    c = {"workload": WORKLOAD, "gaussians": P_ROOM, "image": [WIDTH, HEIGHT], "feature_channels": N_FEAT,
+         "frames": N_FRAMES, "pose_gradient": True, "l2": "flushed between timed steps (512 MB write)",
+         "parallelism": f"frames sharded over {n_gpus} rank(s), no collective on the data path"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def target_pose_delta(k):
+    """Seeded perturbation of frame k: |rho| = 1 cm, |theta| = 1 deg."""
+    from paper_2504_19409_gb300.scenegen import Rng
+    r = Rng(TRAJ_SEED * 1000 + k)
+    a, b = r.normal(3), r.normal(3)
+    return 0.01 * a / np.linalg.norm(a), math.radians(1.0) * b / np.linalg.norm(b)
+
+
+def frame_camera(k):
+    from paper_2504_19409_gb300 import scenegen as sg
+    return sg.room_trajectory(k % N_FRAMES, N_FRAMES, WIDTH, HEIGHT, FOCAL).as_f32()
+
+
+def target_camera(k):
+    from paper_2504_19409_gb300 import scenegen as sg
+    cam = sg.room_trajectory(k % N_FRAMES, N_FRAMES, WIDTH, HEIGHT, FOCAL)
+    rho, theta = target_pose_delta(k % N_FRAMES)
+    return sg.perturb_pose(cam, rho, theta).as_f32()
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes(stats):
+    """HBM bytes each kernel must move at minimum (see the design notes):
+    projection 44 B in + 48 B out per Gaussian; compositing fwd reads the
+    sorted id list (4 B/instance) and each visible Gaussian's record once
+    (uv 8 + conic/opacity 16 + colour 12 + depth 4 + features 4N) and writes
+    (5+N)*4 + 12 B per pixel; the adjoint reads the same plus the per-pixel
+    state (8 B) and cotangents ((5+N)*4 B) and writes 24 + (4+N)*4 B of
+    gradients per visible Gaussian."""
+    P, Pv, I, HW, N = stats["P"], stats["P_vis"], stats["I"], WIDTH * HEIGHT, N_FEAT
+    rec = 8 + 16 + 12 + 4 + 4 * N
+    return {
+        "k_project": P * (44 + 48),
+        "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12),
+        "k_render_bwd": I * 4 + Pv * rec + HW * (8 + (5 + N) * 4) + Pv * (24 + (4 + N) * 4),
+        "k_project_bwd": P * (40 + 24) + Pv * 40,
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2504_19409_gb300 as g
+    from paper_2504_19409_gb300 import scenegen as sg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sc = sg.room_scene(SCENE_SEED, P_ROOM, N_FEAT)
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    params = [tt(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors, sc.feats)]
+    means, scales, quats, opac, cols, feats = params
+    frames = [k for k in range(args.warmup + args.steps) for k in [(k * world + rank) % N_FRAMES]]
+    my_frames = sorted(set(frames))
+
+    ras = g.Rasterizer(P_ROOM, WIDTH, HEIGHT, N=N_FEAT, device=dev)
+    need = 0
+    for k in my_frames:
+        need = max(need, ras.ensure_capacity(frame_camera(k), means, scales, quats, opac))
+        need = max(need, ras.ensure_capacity(target_camera(k), means, scales, quats, opac))
+    # targets: renders at the perturbed poses (synthetic inputs of the loss)
+    targets, blends, stats = {}, {}, {}
+    for k in my_frames:
+        fw = ras.forward(target_camera(k), means, scales, quats, opac, cols, feats)
+        targets[k] = {n: fw[n].clone() for n in ("rgb", "depth", "feat")}
+    for k in my_frames:
+        fw = ras.forward(frame_camera(k), means, scales, quats, opac, cols, feats)
+        blends[k] = int(fw["n_contrib"].sum().item())
+        stats[k] = dict(I=int(ras.sort["n_instances"].item()),
+                        P_vis=int((ras.proj["tiles_touched"] > 0).sum().item()),
+                        evaluated=int(fw["last_idx"].sum().item()))
+    ras.check_status()
+    HW = WIDTH * HEIGHT
+    scales_l1 = {"rgb": 1.0 / (3 * HW), "depth": 1.0 / HW, "feat": 1.0 / (N_FEAT * HW)}
+    grads_in = {n: torch.empty_like(targets[my_frames[0]][n]) for n in ("rgb", "depth", "feat")}
+    loss = torch.zeros(1, device=dev)
+
+    def step(k):
+        cam = frame_camera(k)
+        fw = ras.forward(cam, means, scales, quats, opac, cols, feats)
+        for n in ("rgb", "depth", "feat"):
+            g.l1_loss_grad(fw[n], targets[k][n], scales_l1[n], grad=grads_in[n], loss=loss)
+        return ras.backward(cam, means, scales, quats, cols, feats, grads_in["rgb"], grads_in["depth"], None,
+                            grads_in["feat"])
+
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        step(frames[i])
+    torch.cuda.synchronize()
+    ras.check_status()
+
+    if args.profile:
+        # plain frames only (for profiler captures of the same launch shape)
+        for i in range(args.steps):
+            step(frames[args.warmup + i])
+        torch.cuda.synchronize()
+        ras.check_status()
+        return None
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed_pass(trace=False):
+        evs = []
+        if trace:
+            g.trace_enable(64 * args.steps + 64)
+        _barrier(world)
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(frames[args.warmup + i])
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        _barrier(world)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        tr = g.trace_read() if trace else None
+        if trace:
+            g.trace_enable(0)
+        return ms, tr
+
+    clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    clocks.start()
+    t_wall = time.perf_counter()
+    ms, _ = timed_pass(False)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ras.check_status()
+    ms_trace, trace = timed_pass(True)
+
+    # end-to-end through the public API with host buffers: H2D of the
+    # Gaussian parameters and the frame's target images from pinned memory,
+    # D2H of the pose gradient and the loss value, inside the timed region.
+    host_params = [p.cpu().pin_memory() for p in params]
+    e2e_frames = frames[args.warmup:args.warmup + min(args.steps, 8)]
+    host_tgt = {k: {n: targets[k][n].cpu().pin_memory() for n in ("rgb", "depth", "feat")} for k in set(e2e_frames)}
+    d_params = [torch.empty_like(p) for p in params]
+    d_tgt = {n: torch.empty_like(targets[my_frames[0]][n]) for n in ("rgb", "depth", "feat")}
+    out_pose = torch.empty(6, pin_memory=True)
+    out_loss = torch.empty(1, pin_memory=True)
+    h2d = sum(p.numel() * p.element_size() for p in host_params) + sum(
+        t.numel() * t.element_size() for t in host_tgt[e2e_frames[0]].values())
+    d2h = 6 * 4 + 4
+
+    def e2e_step(k):
+        for d, h in zip(d_params, host_params):
+            d.copy_(h, non_blocking=True)
+        for n in ("rgb", "depth", "feat"):
+            d_tgt[n].copy_(host_tgt[k][n], non_blocking=True)
+        cam = frame_camera(k)
+        m, s_, q, o, c, f = d_params
+        loss.zero_()
+        fw = ras.forward(cam, m, s_, q, o, c, f)
+        for n in ("rgb", "depth", "feat"):
+            g.l1_loss_grad(fw[n], d_tgt[n], scales_l1[n], grad=grads_in[n], loss=loss)
+        gr = ras.backward(cam, m, s_, q, c, f, grads_in["rgb"], grads_in["depth"], None, grads_in["feat"])
+        out_pose.copy_(gr["pose"], non_blocking=True)
+        out_loss.copy_(loss, non_blocking=True)
+
+    e2e_ms = []
+    for i in range(args.steps):
+        k = e2e_frames[i % len(e2e_frames)]
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step(k)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    ras.check_status()
+
+    timed = frames[args.warmup:]
+    tot_ms = sum(ms)
+    tot_blends = sum(blends[k] for k in timed)
+    e2e_blends = sum(blends[e2e_frames[i % len(e2e_frames)]] for i in range(args.steps))
+    # per-kernel durations from the traced pass
+    per = {}
+    for name, t in trace:
+        per.setdefault(name, []).append(t)
+    kernel_ms = {k: sum(v) / args.steps for k, v in per.items()}
+    launches = {k: len(v) / args.steps for k, v in per.items()}
+    mean_stats = {key: float(np.mean([stats[k][key] for k in timed])) for key in ("I", "P_vis", "evaluated")}
+    mean_stats["P"] = P_ROOM
+    return dict(ms=ms, tot_ms=tot_ms, tot_blends=tot_blends, e2e_ms=e2e_ms, e2e_blends=e2e_blends, h2d=h2d, d2h=d2h,
+                kernel_ms=kernel_ms, launches=launches, per=per, clocks=clk, stats=mean_stats,
+                blends_per_frame=float(np.mean([blends[k] for k in timed])), wall_s=t_wall,
+                traced_ms=float(np.mean(ms_trace)))
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_frame_sample(sc, k, tile_rows=None):
+    """One fwd+bwd of frame k in the FP64 oracle (optionally restricted to a
+    band of tile rows); returns (seconds, blended pairs)."""
+    import oracle
+    from paper_2504_19409_gb300 import scenegen as sg
+    cam = frame_camera(k)
+    t0 = time.perf_counter()
+    pr = oracle.project_b32(cam, sc.means, sc.scales, sc.quats, sc.opacity)
+    ranges, gids = oracle.bin_lists(cam, pr["rect"], pr["depth"])
+    if tile_rows is not None:
+        r0, r1 = tile_rows
+        tx = cam.tiles_x
+        keep = np.zeros(len(ranges), bool)
+        keep[r0 * tx:r1 * tx] = True
+        ranges = np.where(keep[:, None], ranges, 0).astype(np.int32)
+    fw = oracle.render_fwd(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity, sc.colors, pr["depth"], sc.feats)
+    cot = sg.random_linear_functional(k, cam.height, cam.width, N_FEAT)
+    rb = oracle.render_bwd(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity, sc.colors, pr["depth"], sc.feats,
+                           *cot)
+    oracle.project_bwd_f64(cam, sc.means, sc.scales, sc.quats, sc.opacity, rb["d_uv"], rb["d_conic"], rb["d_depth"])
+    return time.perf_counter() - t0, int(fw["n_contrib"].sum())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="setup, warm-up and --steps plain frames only (no timing, no JSON); for profiler captures")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_ours(args, rank, world, local_rank)
+    if r is None:
+        print("profile run done")
+        return 0
+    tot_ms = _max_over_ranks(r["tot_ms"], world)
+    tot_blends = _sum_over_ranks(r["tot_blends"], world)
+    e2e_ms = _max_over_ranks(sum(r["e2e_ms"]), world)
+    e2e_blends = _sum_over_ranks(r["e2e_blends"], world)
+    value = tot_blends / (tot_ms / 1e3)
+    if rank == 0:
+        import oracle
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        alg = algorithmic_bytes(r["stats"])
+        km = r["kernel_ms"]
+        top = max(km, key=km.get)
+        dom = top if top in alg else max((k for k in alg if k in km), key=lambda k: km[k])
+        achieved = alg[dom] / (km[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+                "kernel_ms": round(km[dom], 4), "algorithmic_bytes": alg[dom]}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            sc = None
+            from paper_2504_19409_gb300 import scenegen as sg
+            sc = sg.room_scene(SCENE_SEED, P_ROOM, N_FEAT)
+            secs, bl = oracle_frame_sample(sc, 0)
+            cpu = {"value": bl / secs, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": "one full frame (frame 0) of the workload: binary32 projection replay, tile lists, "
+                             "FP64 compositing and FP64 adjoint incl. pose; " f"{secs:.2f} s, {bl} blends"}
+        share = {k: round(v / sum(km.values()), 4) for k, v in sorted(km.items(), key=lambda kv: -kv[1])}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene and trajectory)",
+            "config": config(world, {"blends_per_frame": r["blends_per_frame"], "instances_per_frame": r["stats"]["I"],
+                                     "visible_gaussians": r["stats"]["P_vis"],
+                                     "evaluated_pairs_per_frame": r["stats"]["evaluated"]}),
+            "e2e": {"value": e2e_blends / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                    "d2h_bytes_per_step": r["d2h"], "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": int(round(sum(r["launches"].values()) * args.steps)),
+            "roofline": roof, "cpu_baseline": cpu, "clocks": r["clocks"],
+            "kernel_ms_per_step": {k: round(v, 4) for k, v in km.items()}, "kernel_share": share,
+            "traced_ms_per_step": r["traced_ms"], "ms_per_step_median": statistics.median(r["ms"]),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: each step is one bounded
+    sample of the workload (8 of the 43 tile rows of frame k, fwd + bwd)."""
+    import oracle
+    from paper_2504_19409_gb300 import scenegen as sg
+    sc = sg.room_scene(SCENE_SEED, P_ROOM, N_FEAT)
+    tiles_y = (HEIGHT + 15) // 16
+
+    def band(k):
+        r0 = (8 * k) % tiles_y
+        return (r0, min(tiles_y, r0 + 8))
+
+    for i in range(args.warmup):
+        oracle_frame_sample(sc, i, band(i))
+    secs, bl = 0.0, 0
+    for i in range(args.steps):
+        s, b = oracle_frame_sample(sc, args.warmup + i, band(args.warmup + i))
+        secs += s
+        bl += b
+    value = bl / secs
+    cpu = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "per step: 8 of 43 tile rows of one frame, fwd + bwd in FP64 (binary32 projection replay)"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded room scene)",
+            "config": config(1), "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * gsff.h -- C ABI of the GB300 feature-field Gaussian rasterizer.
+ *
+ * The library renders a set of 3D Gaussians (paper Sec. 3.1: mean mu,
+ * quaternion q, scale s, opacity alpha, colour c, feature embedding f in R^N)
+ * at a camera pose T_CW into RGB, depth, accumulated opacity and an N-channel
+ * feature map by front-to-back alpha compositing (Eq. 2-3), and back-propagates
+ * a loss through it, including the Lie-algebra pose gradient (Eq. 4) and a
+ * feature gradient that reaches only f (Sec. 3.1, "decoupled").
+ *
+ * Conventions shared by every call:
+ *  - Every array pointer is DEVICE memory owned by the caller; the library
+ *    never allocates. Scratch space comes from the caller through the
+ *    *_workspace_bytes queries (256-byte aligned base required).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream). Host pointers (the camera, bg) are
+ *    read before the call returns.
+ *  - Invalid arguments are reported synchronously by the return value and
+ *    nothing is launched. Errors found on the device are OR-ed as bit flags
+ *    (1 << gs_status) into *status (a device int32 the caller zeroes); kernels
+ *    never trap and never spin without a bound.
+ *  - Gradient outputs are ACCUMULATED (+=): the caller zeroes them.
+ *  - Array shapes below are row-major; [P,3] means 3 consecutive floats per
+ *    Gaussian.
+ */
+#ifndef GSFF_H
+#define GSFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1,  /* synchronous: a null/misaligned pointer or a size out of range */
+  GS_ERR_CAPACITY = 2,     /* device: more tile instances than the caller's capacity */
+  GS_ERR_TIMEOUT = 3,      /* device: a bounded wait gave up */
+  GS_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
+  GS_ERR_UNSUPPORTED = 5   /* a valid but unimplemented combination of options */
+} gs_status;
+
+/* Pinhole camera and world->camera transform T_CW: mu_c = R mu + t.
+ * OpenCV axes (x right, y down, z forward); pixel (i, j) has its centre at
+ * (i + 0.5, j + 0.5). R is row-major. Gaussians with z_c <= near_z are culled. */
+typedef struct gs_camera {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float R[9];
+  float t[3];
+  float near_z;
+} gs_camera;
+
+/* flags of gs_render_fwd / gs_render_bwd */
+enum {
+  GS_FEAT_OFF = 0,          /* Eq. 3 "otherwise": no feature work at all */
+  GS_FEAT_ON = 1,           /* render (and back-propagate) the N feature channels */
+  GS_FEAT_TENSOR_CORE = 2   /* with GS_FEAT_ON and BF16 features: tcgen05 contraction */
+};
+enum { GS_FEAT_GRAD_DECOUPLED = 0, GS_FEAT_GRAD_COUPLED = 1 };
+enum { GS_F32 = 0, GS_BF16 = 1 };
+enum { GS_LAYOUT_CHW = 0, GS_LAYOUT_HWC = 1 };
+
+enum { GS_TILE = 16 };      /* tiles are 16 x 16 pixels, numbered row-major */
+
+/* ---------------------------------------------------------------------------
+ * gs_project -- per-Gaussian EWA projection (Eq. 1 and the 3DGS projection
+ * the paper builds on, Sec. 3.1).
+ *
+ * In:  means [P,3], scales [P,3] (linear, > 0), quats [P,4] (w,x,y,z, not
+ *      necessarily unit), opacity [P] (already in (0,1)).
+ * Out: uv [P,2] pixel coordinates of the projected mean; conic_opacity [P,4]
+ *      = (A, B, C, opacity) with [[A,B],[B,C]] the inverse of the 2D
+ *      covariance J W Sigma W^T J^T + 0.3 I; depth [P] = z_c; rect [P,4] =
+ *      tile rectangle (x0, y0, x1, y1), ends exclusive; tiles_touched [P] =
+ *      (x1-x0)(y1-y0), 0 for a culled Gaussian.
+ *      n_instances (optional, device int64): set to sum(tiles_touched).
+ * Every output is computed in binary32 in one fixed order of operations (no
+ * fused multiply-add), so tile rectangles and depth keys are reproducible
+ * bit for bit by an independent binary32 evaluation.
+ * Culling: non-finite input, z_c <= near_z, zero quaternion, non-positive or
+ * non-finite determinant, or a 3-sigma box outside the image.
+ */
+gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const float* scales,
+                     const float* quats, const float* opacity, float* uv, float* conic_opacity,
+                     float* depth, int32_t* rect, int32_t* tiles_touched, int64_t* n_instances,
+                     void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_bin_sort -- tile x depth keys and a stable device radix sort (Sec. 3.1:
+ * "sorted by depth in a front-to-back order", per 16x16 tile).
+ *
+ * For every Gaussian g and every tile k of its rectangle one instance with
+ * key = (k << 32) | bits(depth_g) and value g is emitted in ascending g; the
+ * instances are sorted stably by key (so equal depths keep ascending g).
+ * In:  depth [P], rect [P,4], tiles_touched [P] from gs_project.
+ * Out: keys [capacity] (u64) and gids [capacity] (u32), first I entries valid;
+ *      tile_ranges [num_tiles,2] = [start, end) into gids, (0,0) if empty;
+ *      n_instances (device int64) = I.
+ * If I > capacity, GS_ERR_CAPACITY is flagged in *status and the lists are
+ * truncated (contents unspecified). workspace must hold
+ * gs_bin_sort_workspace_bytes(P, capacity, num_tiles) bytes.
+ */
+size_t gs_bin_sort_workspace_bytes(int32_t P, int64_t capacity, int32_t num_tiles);
+gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
+                      const int32_t* tiles_touched, int64_t capacity, void* workspace,
+                      size_t workspace_bytes, uint64_t* keys, uint32_t* gids, int32_t* tile_ranges,
+                      int64_t* n_instances, int32_t* status, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_render_fwd -- front-to-back alpha compositing per pixel (Eq. 2-3).
+ *
+ * For pixel p in tile k, walking k's list in order with T = 1:
+ *   power = -(A dx^2 + C dy^2)/2 - B dx dy, (dx, dy) = (u, v) - p;
+ *   skip if power > 0; alpha = min(0.99, o exp(power)); skip if alpha < 1/255;
+ *   stop (without blending) if T (1 - alpha) < 1e-4; else w = alpha T,
+ *   C += w c, D += w d, F += w f, T *= 1 - alpha.
+ * Out: out_rgb [3,H,W] = C + T bg; out_depth [H,W] = D; out_alpha [H,W] = 1 - T;
+ *      out_feat [N,H,W] (layout CHW) or [H,W,N] (HWC), only with GS_FEAT_ON;
+ *      T_final [H,W]; last_idx [H,W] = list position (from the tile's start)
+ *      of the last blended Gaussian + 1; n_contrib [H,W] = blended count.
+ * feats [P,N] is float32 (GS_F32) or bfloat16 (GS_BF16); may be NULL with
+ * GS_FEAT_OFF. bg: 3 host floats, NULL = black.
+ * GS_FEAT_TENSOR_CORE (N % 64 == 0, N <= 512, GS_BF16, layout HWC): the
+ * feature channels are computed per tile as the product of a 256 x K weight
+ * matrix (w = alpha T, rounded to bf16) and the K x N bf16 feature rows on
+ * tcgen05 tensor cores with fp32 accumulation.
+ */
+gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges,
+                        const uint32_t* gids, const float* uv, const float* conic_opacity,
+                        const float* depth, const float* colors, const void* feats, int32_t N,
+                        int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
+                        float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
+                        float* T_final, int32_t* last_idx, int32_t* n_contrib, int32_t* status,
+                        void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_render_bwd -- adjoint of gs_render_fwd and gs_project, plus the pose
+ * gradient of Eq. 4.
+ *
+ * Walks each pixel's list backwards from last_idx, recovering the
+ * transmittance in front of each blended Gaussian as T_i = T_{i+1}/(1-alpha_i)
+ * from the saved T_final (no per-pair storage). Cotangents dL_drgb [3,H,W],
+ * dL_ddepth [H,W], dL_dalpha [H,W], dL_dfeat (layout as out_feat) may be NULL
+ * (zero). feat_grad_mode GS_FEAT_GRAD_DECOUPLED is the paper's rule (Sec. 3.1):
+ * dL_dfeat reaches d_feats only; GS_FEAT_GRAD_COUPLED also sends it through
+ * alpha into the geometry (the full derivative).
+ * Out (accumulated): d_means [P,3], d_scales [P,3], d_quats [P,4],
+ *      d_opacity [P], d_colors [P,3], d_feats [P,N] (fp32 even for bf16
+ *      features), d_pose [6] = (rho, theta) of the left perturbation
+ *      T_CW <- Exp(tau) T_CW at tau = 0.
+ * workspace must hold gs_render_bwd_workspace_bytes(P) bytes.
+ */
+size_t gs_render_bwd_workspace_bytes(int32_t P);
+gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales,
+                        const float* quats, const float* colors, const void* feats, int32_t N,
+                        int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
+                        const int32_t* tile_ranges, const uint32_t* gids, const float* uv,
+                        const float* conic_opacity, const float* depth, const float* T_final,
+                        const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
+                        const float* dL_dalpha, const float* dL_dfeat, int32_t feat_grad_mode,
+                        void* workspace, size_t workspace_bytes, float* d_means, float* d_scales,
+                        float* d_quats, float* d_opacity, float* d_colors, float* d_feats,
+                        float* d_pose, int32_t* status, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_l1_loss_grad -- the L1 photometric term of the tracking and mapping
+ * losses (Eq. 5, Eq. 7): grad[i] = scale * sign(pred[i] - target[i]) (sign(0)
+ * = 0) and *loss_sum += scale * sum |pred - target| (device float, atomic).
+ */
+gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, float scale,
+                          float* grad, float* loss_sum, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Tracing: when enabled, every kernel the library launches is bracketed by
+ * CUDA events on its stream (up to `capacity` launches, then recording stops).
+ * gs_trace_get synchronizes on the i-th end event and returns the kernel's
+ * name (static storage) and its duration in milliseconds.
+ */
+gs_status gs_trace_enable(int32_t capacity); /* 0 disables and frees the events */
+void gs_trace_reset(void);
+int32_t gs_trace_count(void);
+gs_status gs_trace_get(int32_t i, const char** name, float* ms);
+
+const char* gs_status_string(gs_status s);
+int32_t gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSFF_H */

@@ -1,1 +1,410 @@
-"""GB300-native feature-field Gaussian rasterizer (package placeholder)."""
+"""GB300-native feature-field Gaussian rasterizer (GSFF-SLAM hot path).
+
+Thin Python binding over the C ABI of ``libgsff.so`` (include/gsff.h). Every
+step of the path runs in the library's CUDA kernels; this module only
+marshals torch tensors (device memory, streams) into the C calls. There is no
+CPU fallback: if the library cannot be loaded every entry point raises.
+
+Entry points with the ABI's names: :func:`project`, :func:`bin_sort`,
+:func:`render_fwd`, :func:`render_bwd`, :func:`l1_loss_grad`; a frame-level
+:class:`Rasterizer` that owns the per-frame buffers; and :func:`render`, a
+``torch.autograd.Function`` returning RGB, depth, alpha and the feature map
+with gradients for the Gaussians, the features (decoupled, Sec. 3.1) and the
+SE(3) pose tangent (Eq. 4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsff.so")
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_UNSUPPORTED = range(6)
+GS_FEAT_OFF, GS_FEAT_ON, GS_FEAT_TENSOR_CORE = 0, 1, 2
+GS_FEAT_GRAD_DECOUPLED, GS_FEAT_GRAD_COUPLED = 0, 1
+GS_F32, GS_BF16 = 0, 1
+GS_LAYOUT_CHW, GS_LAYOUT_HWC = 0, 1
+TILE = 16
+
+# Every symbol include/gsff.h declares.
+EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_render_fwd",
+           "gs_render_bwd_workspace_bytes", "gs_render_bwd", "gs_l1_loss_grad", "gs_trace_enable",
+           "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version")
+
+
+class GsffError(RuntimeError):
+    pass
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("near_z", ctypes.c_float)]
+
+
+def camera_struct(cam) -> GsCamera:
+    c = GsCamera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = np.asarray(cam.R, dtype=np.float64).reshape(9)
+    t = np.asarray(cam.t, dtype=np.float64).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.near_z = float(getattr(cam, "near", 0.2))
+    return c
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_sz = ctypes.c_size_t
+_f32 = ctypes.c_float
+
+
+def lib():
+    """Load libgsff.so (built in-tree by ``build.py``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise GsffError(f"CUDA library not built: {LIB_PATH} is missing (run paper_2504_19409_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    cam_p = ctypes.POINTER(GsCamera)
+    L.gs_project.argtypes = [cam_p, _i32] + [_vp] * 10 + [_vp]
+    L.gs_project.restype = ctypes.c_int
+    L.gs_bin_sort_workspace_bytes.argtypes = [_i32, _i64, _i32]
+    L.gs_bin_sort_workspace_bytes.restype = _sz
+    L.gs_bin_sort.argtypes = [cam_p, _i32, _vp, _vp, _vp, _i64, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.gs_bin_sort.restype = ctypes.c_int
+    L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 7 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 9)
+    L.gs_render_fwd.restype = ctypes.c_int
+    L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
+    L.gs_render_bwd_workspace_bytes.restype = _sz
+    L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +
+                                [_i32, _vp, _sz] + [_vp] * 9)
+    L.gs_render_bwd.restype = ctypes.c_int
+    L.gs_l1_loss_grad.argtypes = [_i64, _vp, _vp, _f32, _vp, _vp, _vp]
+    L.gs_l1_loss_grad.restype = ctypes.c_int
+    L.gs_trace_enable.argtypes = [_i32]
+    L.gs_trace_enable.restype = ctypes.c_int
+    L.gs_trace_count.restype = _i32
+    L.gs_trace_get.argtypes = [_i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_f32)]
+    L.gs_trace_get.restype = ctypes.c_int
+    L.gs_status_string.argtypes = [ctypes.c_int]
+    L.gs_status_string.restype = ctypes.c_char_p
+    L.gs_version.restype = _i32
+    _lib = L
+    return L
+
+
+def _check(code: int, what: str):
+    if code != GS_OK:
+        raise GsffError(f"{what}: {lib().gs_status_string(code).decode()} ({code})")
+
+
+def _ptr(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _need(t, dtype, name, shape=None):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise GsffError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise GsffError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+# ---- the four ABI calls -------------------------------------------------------
+
+def project(cam, means, scales, quats, opacity, out=None, stream=None):
+    """gs_project: returns dict(uv [P,2], conic_opacity [P,4], depth [P], rect [P,4], tiles_touched [P],
+    n_instances [1] int64)."""
+    P = means.shape[0]
+    dev = means.device
+    for t, n, s in ((means, "means", (P, 3)), (scales, "scales", (P, 3)), (quats, "quats", (P, 4)),
+                    (opacity, "opacity", (P,))):
+        _need(t, torch.float32, n, s)
+    o = out if out is not None else dict(
+        uv=torch.empty(P, 2, device=dev), conic_opacity=torch.empty(P, 4, device=dev),
+        depth=torch.empty(P, device=dev), rect=torch.empty(P, 4, dtype=torch.int32, device=dev),
+        tiles_touched=torch.empty(P, dtype=torch.int32, device=dev),
+        n_instances=torch.zeros(1, dtype=torch.int64, device=dev))
+    c = camera_struct(cam)
+    _check(lib().gs_project(ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opacity), _ptr(o["uv"]),
+                            _ptr(o["conic_opacity"]), _ptr(o["depth"]), _ptr(o["rect"]), _ptr(o["tiles_touched"]),
+                            _ptr(o["n_instances"]), _stream(stream)), "gs_project")
+    return o
+
+
+def bin_sort_workspace_bytes(P: int, capacity: int, num_tiles: int) -> int:
+    return int(lib().gs_bin_sort_workspace_bytes(P, capacity, num_tiles))
+
+
+def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=None):
+    """gs_bin_sort: returns dict(keys [cap] int64, gids [cap] int32, tile_ranges [T,2], n_instances [1])."""
+    P = proj["depth"].shape[0]
+    dev = proj["depth"].device
+    T = ((cam.width + TILE - 1) // TILE) * ((cam.height + TILE - 1) // TILE)
+    wsb = bin_sort_workspace_bytes(P, capacity, T)
+    ws = workspace if workspace is not None else torch.empty(wsb, dtype=torch.uint8, device=dev)
+    o = out if out is not None else dict(
+        keys=torch.empty(capacity, dtype=torch.int64, device=dev),
+        gids=torch.empty(capacity, dtype=torch.int32, device=dev),
+        tile_ranges=torch.empty(T, 2, dtype=torch.int32, device=dev),
+        n_instances=torch.zeros(1, dtype=torch.int64, device=dev))
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    _check(lib().gs_bin_sort(ctypes.byref(c), P, _ptr(proj["depth"]), _ptr(proj["rect"]),
+                             _ptr(proj["tiles_touched"]), int(capacity), _ptr(ws), ws.numel(), _ptr(o["keys"]),
+                             _ptr(o["gids"]), _ptr(o["tile_ranges"]), _ptr(o["n_instances"]), _ptr(st),
+                             _stream(stream)), "gs_bin_sort")
+    o["status"] = st
+    return o
+
+
+def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT_CHW, bg=None, out=None,
+               status=None, stream=None):
+    """gs_render_fwd: returns dict(rgb [3,H,W], depth [H,W], alpha [H,W], feat, T_final, last_idx, n_contrib)."""
+    H, W = cam.height, cam.width
+    dev = colors.device
+    P = colors.shape[0]
+    N = 0 if feats is None else feats.shape[1]
+    if flags is None:
+        flags = GS_FEAT_ON if N > 0 else GS_FEAT_OFF
+    feat_on = bool(flags & GS_FEAT_ON)
+    dtype = GS_BF16 if (feats is not None and feats.dtype == torch.bfloat16) else GS_F32
+    _need(colors, torch.float32, "colors", (P, 3))
+    o = out
+    if o is None:
+        o = dict(rgb=torch.empty(3, H, W, device=dev), depth=torch.empty(H, W, device=dev),
+                 alpha=torch.empty(H, W, device=dev), T_final=torch.empty(H, W, device=dev),
+                 last_idx=torch.empty(H, W, dtype=torch.int32, device=dev),
+                 n_contrib=torch.empty(H, W, dtype=torch.int32, device=dev))
+        if feat_on:
+            o["feat"] = torch.empty((N, H, W) if layout == GS_LAYOUT_CHW else (H, W, N), device=dev)
+    bgc = (ctypes.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    _check(lib().gs_render_fwd(ctypes.byref(c), P, _ptr(sort["tile_ranges"]), _ptr(sort["gids"]), _ptr(proj["uv"]),
+                               _ptr(proj["conic_opacity"]), _ptr(proj["depth"]), _ptr(colors),
+                               _ptr(feats) if feat_on else None, N if feat_on else 0, dtype, layout, flags,
+                               ctypes.cast(bgc, _vp), _ptr(o["rgb"]), _ptr(o["depth"]), _ptr(o["alpha"]),
+                               _ptr(o.get("feat")) if feat_on else None, _ptr(o["T_final"]), _ptr(o["last_idx"]),
+                               _ptr(o["n_contrib"]), _ptr(st), _stream(stream)), "gs_render_fwd")
+    return o
+
+
+def render_bwd_workspace_bytes(P: int) -> int:
+    return int(lib().gs_render_bwd_workspace_bytes(P))
+
+
+def render_bwd(cam, means, scales, quats, colors, feats, proj, sort, fwd, g_rgb=None, g_depth=None, g_alpha=None,
+               g_feat=None, flags=None, layout=GS_LAYOUT_CHW, bg=None, coupled=False, grads=None, workspace=None,
+               status=None, stream=None):
+    """gs_render_bwd: accumulates into grads (zeroed if created here) and returns it."""
+    P = means.shape[0]
+    dev = means.device
+    N = 0 if feats is None else feats.shape[1]
+    if flags is None:
+        flags = GS_FEAT_ON if N > 0 else GS_FEAT_OFF
+    feat_on = bool(flags & GS_FEAT_ON)
+    dtype = GS_BF16 if (feats is not None and feats.dtype == torch.bfloat16) else GS_F32
+    g = grads if grads is not None else dict(
+        means=torch.zeros(P, 3, device=dev), scales=torch.zeros(P, 3, device=dev),
+        quats=torch.zeros(P, 4, device=dev), opacity=torch.zeros(P, device=dev),
+        colors=torch.zeros(P, 3, device=dev), feats=torch.zeros(P, max(N, 1), device=dev)[:, :N],
+        pose=torch.zeros(6, device=dev))
+    ws = workspace if workspace is not None else torch.empty(max(render_bwd_workspace_bytes(P), 256),
+                                                             dtype=torch.uint8, device=dev)
+    bgc = (ctypes.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    cont = lambda t: None if t is None else t.contiguous()
+    g_rgb, g_depth, g_alpha, g_feat = cont(g_rgb), cont(g_depth), cont(g_alpha), cont(g_feat)
+    _check(lib().gs_render_bwd(
+        ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(colors), _ptr(feats) if feat_on else None,
+        N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(sort["tile_ranges"]),
+        _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
+        _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), _ptr(g_rgb), _ptr(g_depth), _ptr(g_alpha),
+        _ptr(g_feat) if feat_on else None, GS_FEAT_GRAD_COUPLED if coupled else GS_FEAT_GRAD_DECOUPLED,
+        _ptr(ws), ws.numel(), _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opacity"]),
+        _ptr(g["colors"]), _ptr(g["feats"]) if feat_on else None, _ptr(g["pose"]), _ptr(st), _stream(stream)),
+        "gs_render_bwd")
+    return g
+
+
+def l1_loss_grad(pred, target, scale, grad=None, loss=None, stream=None):
+    """gs_l1_loss_grad: grad = scale sign(pred - target); loss += scale sum |pred - target|."""
+    _need(pred, torch.float32, "pred")
+    _need(target, torch.float32, "target", pred.shape)
+    g = grad if grad is not None else torch.empty_like(pred)
+    _check(lib().gs_l1_loss_grad(pred.numel(), _ptr(pred), _ptr(target), float(scale), _ptr(g), _ptr(loss),
+                                 _stream(stream)), "gs_l1_loss_grad")
+    return g
+
+
+# ---- tracing ------------------------------------------------------------------
+
+def trace_enable(capacity: int) -> None:
+    _check(lib().gs_trace_enable(int(capacity)), "gs_trace_enable")
+
+
+def trace_reset() -> None:
+    lib().gs_trace_reset()
+
+
+def trace_read():
+    """[(kernel name, ms)] for every traced launch since the last reset."""
+    out = []
+    for i in range(lib().gs_trace_count()):
+        name = ctypes.c_char_p()
+        ms = ctypes.c_float()
+        _check(lib().gs_trace_get(i, ctypes.byref(name), ctypes.byref(ms)), "gs_trace_get")
+        out.append((name.value.decode(), ms.value))
+    return out
+
+
+# ---- frame-level driver -----------------------------------------------------------
+
+class Rasterizer:
+    """Owns the per-frame device buffers for one (P, image, N) shape and runs
+    project -> bin_sort -> render_fwd -> render_bwd with no host round trip
+    (instance capacity fixed up front; overflow is flagged in ``status``)."""
+
+    def __init__(self, P, width, height, N=0, capacity=None, layout=GS_LAYOUT_CHW, feat_dtype=torch.float32,
+                 device="cuda", flags=None):
+        self.P, self.W, self.H, self.N = P, width, height, N
+        self.layout = layout
+        self.flags = flags if flags is not None else (GS_FEAT_ON if N > 0 else GS_FEAT_OFF)
+        self.device = torch.device(device)
+        self.T = ((width + TILE - 1) // TILE) * ((height + TILE - 1) // TILE)
+        self.capacity = int(capacity) if capacity else max(1024, 8 * P)
+        dev = self.device
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.proj = dict(uv=torch.empty(P, 2, device=dev), conic_opacity=torch.empty(P, 4, device=dev),
+                         depth=torch.empty(P, device=dev), rect=torch.empty(P, 4, dtype=torch.int32, device=dev),
+                         tiles_touched=torch.empty(P, dtype=torch.int32, device=dev),
+                         n_instances=torch.zeros(1, dtype=torch.int64, device=dev))
+        self._alloc_sort()
+        self.fwd = dict(rgb=torch.empty(3, height, width, device=dev), depth=torch.empty(height, width, device=dev),
+                        alpha=torch.empty(height, width, device=dev), T_final=torch.empty(height, width, device=dev),
+                        last_idx=torch.empty(height, width, dtype=torch.int32, device=dev),
+                        n_contrib=torch.empty(height, width, dtype=torch.int32, device=dev))
+        if self.flags & GS_FEAT_ON:
+            shape = (N, height, width) if layout == GS_LAYOUT_CHW else (height, width, N)
+            self.fwd["feat"] = torch.empty(shape, device=dev)
+        self.bwd_ws = torch.empty(max(render_bwd_workspace_bytes(P), 256), dtype=torch.uint8, device=dev)
+        self.grads = dict(means=torch.zeros(P, 3, device=dev), scales=torch.zeros(P, 3, device=dev),
+                          quats=torch.zeros(P, 4, device=dev), opacity=torch.zeros(P, device=dev),
+                          colors=torch.zeros(P, 3, device=dev), feats=torch.zeros(P, max(N, 1), device=dev)[:, :N],
+                          pose=torch.zeros(6, device=dev))
+
+    def _alloc_sort(self):
+        dev = self.device
+        self.sort_ws = torch.empty(bin_sort_workspace_bytes(self.P, self.capacity, self.T), dtype=torch.uint8,
+                                   device=dev)
+        self.sort = dict(keys=torch.empty(self.capacity, dtype=torch.int64, device=dev),
+                         gids=torch.empty(self.capacity, dtype=torch.int32, device=dev),
+                         tile_ranges=torch.empty(self.T, 2, dtype=torch.int32, device=dev),
+                         n_instances=torch.zeros(1, dtype=torch.int64, device=dev))
+
+    def ensure_capacity(self, cam, means, scales, quats, opacity, slack=1.25):
+        """Project once, read the instance count (one sync) and grow the sort buffers if needed."""
+        project(cam, means, scales, quats, opacity, out=self.proj)
+        need = int(self.proj["n_instances"].item())
+        if need > self.capacity:
+            self.capacity = int(need * slack) + 1024
+            self._alloc_sort()
+        return need
+
+    def forward(self, cam, means, scales, quats, opacity, colors, feats=None, bg=None, stream=None):
+        project(cam, means, scales, quats, opacity, out=self.proj, stream=stream)
+        bin_sort(cam, self.proj, self.capacity, workspace=self.sort_ws, out=self.sort, status=self.status,
+                 stream=stream)
+        render_fwd(cam, self.proj, self.sort, colors, feats, flags=self.flags, layout=self.layout, bg=bg,
+                   out=self.fwd, status=self.status, stream=stream)
+        return self.fwd
+
+    def backward(self, cam, means, scales, quats, colors, feats=None, g_rgb=None, g_depth=None, g_alpha=None,
+                 g_feat=None, bg=None, coupled=False, zero=True, stream=None):
+        if zero:
+            for t in self.grads.values():
+                t.zero_()
+        render_bwd(cam, means, scales, quats, colors, feats, self.proj, self.sort, self.fwd, g_rgb, g_depth, g_alpha,
+                   g_feat, flags=self.flags, layout=self.layout, bg=bg, coupled=coupled, grads=self.grads,
+                   workspace=self.bwd_ws, status=self.status, stream=stream)
+        return self.grads
+
+    def check_status(self):
+        s = int(self.status.item())
+        if s:
+            names = [lib().gs_status_string(i).decode() for i in range(1, 6) if s & (1 << i)]
+            raise GsffError("device status: " + ", ".join(names))
+
+
+# ---- autograd -----------------------------------------------------------------
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacity, colors, feats, pose, cam, opts):
+        P = means.shape[0]
+        N = 0 if feats is None else feats.shape[1]
+        flags = GS_FEAT_ON if (N > 0 and opts.get("render_features", True)) else GS_FEAT_OFF
+        layout = opts.get("layout", GS_LAYOUT_CHW)
+        bg = opts.get("bg")
+        cont = [t.detach().contiguous() for t in (means, scales, quats, opacity, colors)]
+        fe = None if feats is None else feats.detach().contiguous()
+        proj = project(cam, *cont[:4])
+        cap = max(int(proj["n_instances"].item()), 1)
+        srt = bin_sort(cam, proj, cap)
+        fw = render_fwd(cam, proj, srt, cont[4], fe, flags=flags, layout=layout, bg=bg, status=srt["status"])
+        if int(srt["status"].item()):
+            raise GsffError("device status flagged during the forward pass")
+        ctx.cam, ctx.opts, ctx.flags, ctx.N = cam, opts, flags, N
+        ctx.proj, ctx.sort, ctx.fwd = proj, srt, fw
+        ctx.save_for_backward(*cont, fe if fe is not None else torch.empty(0, device=means.device))
+        ctx.has_feats = fe is not None
+        feat = fw.get("feat")
+        if feat is None:
+            H, W = cam.height, cam.width
+            feat = torch.zeros((N, H, W) if layout == GS_LAYOUT_CHW else (H, W, N), device=means.device)
+        ctx.mark_non_differentiable(fw["T_final"], fw["n_contrib"])
+        return fw["rgb"], fw["depth"], fw["alpha"], feat, fw["T_final"], fw["n_contrib"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_alpha, g_feat, _gT, _gn):
+        means, scales, quats, opacity, colors, fe = ctx.saved_tensors
+        fe = fe if ctx.has_feats else None
+        grads = render_bwd(ctx.cam, means, scales, quats, colors, fe, ctx.proj, ctx.sort, ctx.fwd, g_rgb, g_depth,
+                           g_alpha, g_feat, flags=ctx.flags, layout=ctx.opts.get("layout", GS_LAYOUT_CHW),
+                           bg=ctx.opts.get("bg"), coupled=ctx.opts.get("coupled", False))
+        d_feats = grads["feats"] if ctx.has_feats else None
+        if ctx.has_feats and d_feats.shape[1] == 0:
+            d_feats = torch.zeros_like(fe, dtype=torch.float32)
+        return (grads["means"], grads["scales"], grads["quats"], grads["opacity"], grads["colors"], d_feats,
+                grads["pose"], None, None)
+
+
+def render(means, scales, quats, opacity, colors, feats, pose, cam, render_features=True, layout=GS_LAYOUT_CHW,
+           bg=None, coupled=False):
+    """Differentiable render at camera ``cam``.
+
+    ``pose`` is a 6-vector tangent (rho, theta) of the left perturbation
+    T <- Exp(pose) T evaluated at 0: its value is not read, its gradient is
+    dL/dtau (Eq. 4). Returns (rgb [3,H,W], depth [H,W], alpha [H,W], feat,
+    T_final [H,W], n_contrib [H,W]).
+    """
+    opts = dict(render_features=render_features, layout=layout, bg=bg, coupled=coupled)
+    return _RenderFn.apply(means, scales, quats, opacity, colors, feats, pose, cam, opts)

@@ -1,0 +1,288 @@
+// C ABI entry points of libgsff (declared in include/gsff.h): synchronous
+// argument checks, workspace carving, and kernel launch sequencing. The
+// kernels themselves live in project.cu, binsort.cu and render.cu.
+
+#include <mutex>
+#include <vector>
+
+#include "gsff_internal.cuh"
+
+namespace gsff {
+
+void launch_project(const CamF& cam, int P, const float* means, const float* scales, const float* quats,
+                    const float* opacity, float* uv, float* co, float* depth, int32_t* rect, int32_t* touched,
+                    int64_t* n_inst, cudaStream_t st);
+void launch_project_bwd(const CamF& cam, int P, const float* means, const float* scales, const float* quats,
+                        const float* d_uv, const float* d_conic, const float* d_depth, float* d_means,
+                        float* d_scales, float* d_quats, float* d_pose, cudaStream_t st);
+size_t bin_sort_workspace_bytes(int P, long long capacity);
+gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int32_t* rect, const int32_t* touched,
+                          long long capacity, void* workspace, unsigned long long* keys, uint32_t* gids,
+                          int32_t* ranges, int64_t* n_out, int32_t* status, cudaStream_t st);
+gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+                            const float* co, const float* depth, const float* colors, const void* feats, int N,
+                            int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
+                            float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
+                            int32_t* n_contrib, cudaStream_t st);
+gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+                            const float* co, const float* depth, const float* colors, const void* feats, int N,
+                            int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
+                            const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
+                            int coupled, float* d_uv, float* d_conic, float* d_depth, float* d_opacity,
+                            float* d_colors, float* d_feats, cudaStream_t st);
+
+// ---- tracing -----------------------------------------------------------------
+namespace {
+struct TraceState {
+  std::mutex mu;
+  bool on = false;
+  int cap = 0;
+  int count = 0;
+  int open = -1;
+  std::vector<cudaEvent_t> ev;  // 2 per launch
+  std::vector<const char*> names;
+} g_trace;
+}  // namespace
+
+void trace_begin(const char* name, cudaStream_t s) {
+  if (!g_trace.on) return;
+  std::lock_guard<std::mutex> lk(g_trace.mu);
+  if (g_trace.count >= g_trace.cap) return;
+  const int i = g_trace.count;
+  cudaEventRecord(g_trace.ev[2 * i], s);
+  g_trace.names[i] = name;
+  g_trace.open = i;
+}
+
+void trace_end(cudaStream_t s) {
+  if (!g_trace.on) return;
+  std::lock_guard<std::mutex> lk(g_trace.mu);
+  if (g_trace.open < 0) return;
+  cudaEventRecord(g_trace.ev[2 * g_trace.open + 1], s);
+  g_trace.open = -1;
+  ++g_trace.count;
+}
+
+namespace {
+
+__global__ void k_l1_grad(long long n, const float* __restrict__ pred, const float* __restrict__ target, float scale,
+                          float* __restrict__ grad, float* __restrict__ loss) {
+  float acc = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = pred[i] - target[i];
+    grad[i] = d > 0.f ? scale : (d < 0.f ? -scale : 0.f);
+    acc += fabsf(d);
+  }
+  if (loss) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0 && acc != 0.f) atomicAdd(loss, acc * scale);
+  }
+}
+
+bool cam_ok(const gs_camera* cam) {
+  return cam && cam->width > 0 && cam->height > 0 && cam->width <= (1 << 15) && cam->height <= (1 << 15) &&
+         cam->fx > 0.f && cam->fy > 0.f;
+}
+
+int num_tiles(const gs_camera* cam) {
+  return ((cam->width + kTile - 1) / kTile) * ((cam->height + kTile - 1) / kTile);
+}
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+constexpr float kBlack[3] = {0.f, 0.f, 0.f};
+
+}  // namespace
+}  // namespace gsff
+
+using namespace gsff;
+
+extern "C" {
+
+int32_t gs_version(void) { return 1; }
+
+const char* gs_status_string(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_CAPACITY: return "instance capacity exceeded";
+    case GS_ERR_TIMEOUT: return "bounded wait timed out";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_UNSUPPORTED: return "unsupported option combination";
+  }
+  return "unknown status";
+}
+
+gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const float* scales, const float* quats,
+                     const float* opacity, float* uv, float* conic_opacity, float* depth, int32_t* rect,
+                     int32_t* tiles_touched, int64_t* n_instances, void* stream) {
+  if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
+  if (P > 0 && (!means || !scales || !quats || !opacity || !uv || !conic_opacity || !depth || !rect ||
+                !tiles_touched))
+    return GS_ERR_INVALID_ARG;
+  if (!aligned(quats, 16) || !aligned(conic_opacity, 16) || !aligned(rect, 16) || !aligned(uv, 8) ||
+      !aligned(n_instances, 8))
+    return GS_ERR_INVALID_ARG;
+  if (n_instances && cudaMemsetAsync(n_instances, 0, sizeof(int64_t), S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+  launch_project(make_cam(*cam), P, means, scales, quats, opacity, uv, conic_opacity, depth, rect, tiles_touched,
+                 n_instances, S(stream));
+  return last_launch_status();
+}
+
+size_t gs_bin_sort_workspace_bytes(int32_t P, int64_t capacity, int32_t) {
+  if (P < 0 || capacity < 0) return 0;
+  return bin_sort_workspace_bytes(P, capacity);
+}
+
+gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
+                      const int32_t* tiles_touched, int64_t capacity, void* workspace, size_t workspace_bytes,
+                      uint64_t* keys, uint32_t* gids, int32_t* tile_ranges, int64_t* n_instances, int32_t* status,
+                      void* stream) {
+  if (!cam_ok(cam) || P < 0 || capacity < 1 || capacity >= (1ll << 31)) return GS_ERR_INVALID_ARG;
+  if (num_tiles(cam) > (1 << 24)) return GS_ERR_INVALID_ARG;
+  if (!keys || !gids || !tile_ranges || !workspace || (P > 0 && (!depth || !rect || !tiles_touched)))
+    return GS_ERR_INVALID_ARG;
+  if (!aligned(workspace, 256) || !aligned(keys, 8) || !aligned(rect, 16) || !aligned(tile_ranges, 8) ||
+      !aligned(n_instances, 8))
+    return GS_ERR_INVALID_ARG;
+  if (workspace_bytes < bin_sort_workspace_bytes(P, capacity)) return GS_ERR_INVALID_ARG;
+  return launch_bin_sort(make_cam(*cam), P, depth, rect, tiles_touched, capacity, workspace,
+                         reinterpret_cast<unsigned long long*>(keys), gids, tile_ranges, n_instances, status,
+                         S(stream));
+}
+
+gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const uint32_t* gids,
+                        const float* uv, const float* conic_opacity, const float* depth, const float* colors,
+                        const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
+                        const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
+                        float* T_final, int32_t* last_idx, int32_t* n_contrib, int32_t* status, void* stream) {
+  (void)status;
+  if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
+  if (!tile_ranges || !gids || !out_rgb || !out_depth || !out_alpha || !T_final || !last_idx || !n_contrib)
+    return GS_ERR_INVALID_ARG;
+  if (P > 0 && (!uv || !conic_opacity || !depth || !colors)) return GS_ERR_INVALID_ARG;
+  if (!aligned(conic_opacity, 16) || !aligned(uv, 8) || !aligned(tile_ranges, 8)) return GS_ERR_INVALID_ARG;
+  if (feat_dtype != GS_F32 && feat_dtype != GS_BF16) return GS_ERR_INVALID_ARG;
+  if (layout != GS_LAYOUT_CHW && layout != GS_LAYOUT_HWC) return GS_ERR_INVALID_ARG;
+  const bool feat_on = (flags & GS_FEAT_ON) != 0;
+  int n = 0;
+  if (feat_on) {
+    if (N <= 0 || N > 4096 || !out_feat || (P > 0 && !feats)) return GS_ERR_INVALID_ARG;
+    if (!aligned(feats, 16) || !aligned(out_feat, 16)) return GS_ERR_INVALID_ARG;
+    n = N;
+  }
+  const float* b = bg ? bg : kBlack;
+  const CamF k = make_cam(*cam);
+  if (feat_on && (flags & GS_FEAT_TENSOR_CORE)) {
+    if (feat_dtype != GS_BF16 || layout != GS_LAYOUT_HWC || N % 64 != 0 || N > 512) return GS_ERR_UNSUPPORTED;
+    // geometry channels and the saved state on the SIMT kernel, features on tcgen05
+    gs_status st = launch_render_fwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, nullptr, 0, 0, 1, b,
+                                     out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, S(stream));
+    if (st != GS_OK) return st;
+    return launch_render_fwd_tc(k, tile_ranges, gids, uv, conic_opacity,
+                                static_cast<const __nv_bfloat16*>(feats), N, out_feat, status, S(stream));
+  }
+  return launch_render_fwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, n,
+                           feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, out_rgb, out_depth, out_alpha, out_feat,
+                           T_final, last_idx, n_contrib, S(stream));
+}
+
+size_t gs_render_bwd_workspace_bytes(int32_t P) {
+  if (P < 0) return 0;
+  // d_uv [P,2], d_conic [P,3], d_depth [P]
+  return align_up((size_t)P * 2 * 4, 256) + align_up((size_t)P * 3 * 4, 256) + align_up((size_t)P * 4, 256);
+}
+
+gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales, const float* quats,
+                        const float* colors, const void* feats, int32_t N, int32_t feat_dtype, int32_t layout,
+                        int32_t flags, const float* bg, const int32_t* tile_ranges, const uint32_t* gids,
+                        const float* uv, const float* conic_opacity, const float* depth, const float* T_final,
+                        const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth, const float* dL_dalpha,
+                        const float* dL_dfeat, int32_t feat_grad_mode, void* workspace, size_t workspace_bytes,
+                        float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_colors,
+                        float* d_feats, float* d_pose, int32_t* status, void* stream) {
+  (void)status;
+  if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
+  if (!tile_ranges || !gids || !T_final || !last_idx || !workspace) return GS_ERR_INVALID_ARG;
+  if (P > 0 && (!means || !scales || !quats || !colors || !uv || !conic_opacity || !depth || !d_means || !d_scales ||
+                !d_quats || !d_opacity || !d_colors))
+    return GS_ERR_INVALID_ARG;
+  if (!d_pose) return GS_ERR_INVALID_ARG;
+  if (!aligned(workspace, 256) || !aligned(quats, 16) || !aligned(conic_opacity, 16) || !aligned(uv, 8))
+    return GS_ERR_INVALID_ARG;
+  if (workspace_bytes < gs_render_bwd_workspace_bytes(P)) return GS_ERR_INVALID_ARG;
+  if (feat_dtype != GS_F32 && feat_dtype != GS_BF16) return GS_ERR_INVALID_ARG;
+  if (layout != GS_LAYOUT_CHW && layout != GS_LAYOUT_HWC) return GS_ERR_INVALID_ARG;
+  if (feat_grad_mode != GS_FEAT_GRAD_DECOUPLED && feat_grad_mode != GS_FEAT_GRAD_COUPLED) return GS_ERR_INVALID_ARG;
+  const bool feat_on = (flags & GS_FEAT_ON) != 0;
+  int n = 0;
+  if (feat_on) {
+    if (N <= 0 || N > 4096 || (P > 0 && (!d_feats || !feats))) return GS_ERR_INVALID_ARG;
+    if (!aligned(feats, 16)) return GS_ERR_INVALID_ARG;
+    n = N;
+  }
+  const bool coupled = feat_on && feat_grad_mode == GS_FEAT_GRAD_COUPLED && dL_dfeat;
+  const float* b = bg ? bg : kBlack;
+  const CamF k = make_cam(*cam);
+  char* ws = static_cast<char*>(workspace);
+  float* w_uv = reinterpret_cast<float*>(ws);
+  float* w_conic = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256));
+  float* w_depth = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256) + align_up((size_t)P * 3 * 4, 256));
+  if (cudaMemsetAsync(workspace, 0, gs_render_bwd_workspace_bytes(P), S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+  gs_status st = launch_render_bwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, n,
+                                   feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, T_final, last_idx, dL_drgb,
+                                   dL_ddepth, dL_dalpha, feat_on ? dL_dfeat : nullptr, coupled ? 1 : 0, w_uv, w_conic,
+                                   w_depth, d_opacity, d_colors, d_feats, S(stream));
+  if (st != GS_OK) return st;
+  launch_project_bwd(k, P, means, scales, quats, w_uv, w_conic, w_depth, d_means, d_scales, d_quats, d_pose, S(stream));
+  return last_launch_status();
+}
+
+gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, float scale, float* grad,
+                          float* loss_sum, void* stream) {
+  if (n < 0 || (n > 0 && (!pred || !target || !grad))) return GS_ERR_INVALID_ARG;
+  if (n == 0) return GS_OK;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  GS_TRACE("k_l1_grad", S(stream));
+  k_l1_grad<<<(unsigned)blocks, 256, 0, S(stream)>>>(n, pred, target, scale, grad, loss_sum);
+  return last_launch_status();
+}
+
+gs_status gs_trace_enable(int32_t capacity) {
+  std::lock_guard<std::mutex> lk(g_trace.mu);
+  for (cudaEvent_t e : g_trace.ev) cudaEventDestroy(e);
+  g_trace.ev.clear();
+  g_trace.names.clear();
+  g_trace.count = 0;
+  g_trace.open = -1;
+  g_trace.on = false;
+  g_trace.cap = 0;
+  if (capacity <= 0) return GS_OK;
+  g_trace.ev.resize(2 * (size_t)capacity);
+  for (auto& e : g_trace.ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return GS_ERR_CUDA;
+  g_trace.names.assign(capacity, nullptr);
+  g_trace.cap = capacity;
+  g_trace.on = true;
+  return GS_OK;
+}
+
+void gs_trace_reset(void) {
+  std::lock_guard<std::mutex> lk(g_trace.mu);
+  g_trace.count = 0;
+  g_trace.open = -1;
+}
+
+int32_t gs_trace_count(void) { return g_trace.count; }
+
+gs_status gs_trace_get(int32_t i, const char** name, float* ms) {
+  if (i < 0 || i >= g_trace.count || !name || !ms) return GS_ERR_INVALID_ARG;
+  if (cudaEventSynchronize(g_trace.ev[2 * i + 1]) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaEventElapsedTime(ms, g_trace.ev[2 * i], g_trace.ev[2 * i + 1]) != cudaSuccess) return GS_ERR_CUDA;
+  *name = g_trace.names[i];
+  return GS_OK;
+}
+
+}  // extern "C"

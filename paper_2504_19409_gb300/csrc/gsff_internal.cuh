@@ -1,0 +1,98 @@
+// Internal declarations shared by the CUDA translation units of libgsff.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gsff.h"
+
+namespace gsff {
+
+// 3DGS rules the paper's renderer builds on (Sec. 3.1); the paper does not
+// print their values.
+constexpr float kLowPass = 0.3f;          // added to the 2D covariance diagonal
+constexpr float kGuardBand = 1.3f;        // Jacobian clamp, in half-fields of view
+constexpr float kSigmas = 3.f;            // footprint radius in standard deviations
+constexpr float kEigFloor = 0.1f;         // floor under the eigenvalue discriminant
+constexpr float kAlphaMax = 0.99f;        // alpha clamp
+constexpr float kAlphaMin = 1.f / 255.f;  // alphas below this are skipped
+constexpr float kTStop = 1e-4f;           // walk stops before T falls below this
+constexpr int kTile = GS_TILE;
+constexpr int kTilePix = kTile * kTile;   // 256 pixels = 256 threads per tile block
+
+struct CamF {
+  int W, H, tiles_x, tiles_y;
+  float fx, fy, cx, cy;
+  float R[9];
+  float t[3];
+  float near_z;
+};
+
+inline CamF make_cam(const gs_camera& c) {
+  CamF k;
+  k.W = c.width;
+  k.H = c.height;
+  k.tiles_x = (c.width + kTile - 1) / kTile;
+  k.tiles_y = (c.height + kTile - 1) / kTile;
+  k.fx = c.fx;
+  k.fy = c.fy;
+  k.cx = c.cx;
+  k.cy = c.cy;
+  for (int i = 0; i < 9; ++i) k.R[i] = c.R[i];
+  for (int i = 0; i < 3; ++i) k.t[i] = c.t[i];
+  k.near_z = c.near_z;
+  return k;
+}
+
+// Device status word: error kinds OR-ed as bits.
+__device__ __forceinline__ void flag_status(int32_t* status, gs_status s) {
+  if (status) atomicOr(status, 1 << (int)s);
+}
+
+// alpha of one (pixel, Gaussian) pair. The sequence is fixed (explicit
+// roundings, explicit fused multiply-adds) so the forward and the backward
+// kernels take identical skip decisions.
+struct PairAlpha {
+  float power, G, alpha;
+  bool clamped;
+};
+
+__device__ __forceinline__ bool pair_alpha(float4 co, float dx, float dy, PairAlpha& r) {
+  const float hx = __fmul_rn(dx, dx), hy = __fmul_rn(dy, dy), hxy = __fmul_rn(dx, dy);
+  const float s = __fmaf_rn(co.x, hx, __fmul_rn(co.z, hy));
+  r.power = __fmaf_rn(-0.5f, s, -__fmul_rn(co.y, hxy));
+  if (r.power > 0.f) return false;
+  r.G = __expf(r.power);
+  const float a = __fmul_rn(co.w, r.G);
+  r.clamped = a > kAlphaMax;
+  r.alpha = r.clamped ? kAlphaMax : a;
+  return r.alpha >= kAlphaMin;
+}
+
+// ---- tracing (api.cu) -----------------------------------------------------
+void trace_begin(const char* name, cudaStream_t s);
+void trace_end(cudaStream_t s);
+
+struct TraceScope {
+  cudaStream_t s;
+  TraceScope(const char* name, cudaStream_t st) : s(st) { trace_begin(name, s); }
+  ~TraceScope() { trace_end(s); }
+};
+
+#define GS_TRACE(name, stream) ::gsff::TraceScope _gs_trace_scope_(name, stream)
+
+inline gs_status last_launch_status() {
+  return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---- launchers implemented in the .cu files ---------------------------------
+gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uint32_t* gids,
+                               const float* uv, const float* co, const __nv_bfloat16* feats,
+                               int N, float* out_feat, int32_t* status, cudaStream_t st);
+
+}  // namespace gsff

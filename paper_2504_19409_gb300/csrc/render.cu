@@ -1,0 +1,479 @@
+// Tile compositing (Sec. 3.1, Eq. 2-3) and its reverse-order adjoint.
+//
+// Both kernels run one 256-thread block per 16x16 tile (one thread per
+// pixel) and blockIdx.y over chunks of NC feature channels (chunk 0 also does
+// RGB, depth and alpha). Gaussian records of the tile's depth-sorted list
+// are staged in shared memory in batches; per-pixel work is SIMT fp32.
+//
+// Forward: early termination is tracked per pixel; a block leaves its list
+// as soon as __syncthreads_count sees every pixel done.
+//
+// Backward: each pixel walks its list from last_idx down, recovers T_i =
+// T_{i+1} / (1 - alpha_i) from the saved T_final, and forms the per-pair
+// partials of (u, v, A, B, C, opacity, colour, depth, features). The 256
+// per-pixel partials of each Gaussian are summed in two stages before one
+// global atomic per (Gaussian, channel, tile):
+//   (1) within a warp by a transpose-reduction -- 32 channel values per lane
+//       are halved five times with xor-shuffles (16+8+4+2+1 = 31 shuffles)
+//       so that lane l ends up owning the warp sum of channel l;
+//   (2) across the 8 warps through shared memory after each batch.
+
+#include "gsff_internal.cuh"
+
+namespace gsff {
+namespace {
+
+struct FwdParams {
+  CamF cam;
+  const int2* ranges;
+  const uint32_t* gids;
+  const float2* uv;
+  const float4* co;
+  const float* depth;
+  const float* colors;
+  const void* feats;
+  int N, bf16, hwc;
+  float bg[3];
+  float* out_rgb;
+  float* out_depth;
+  float* out_alpha;
+  float* out_feat;
+  float* T_final;
+  int* last_idx;
+  int* n_contrib;
+};
+
+template <int NC>
+__device__ __forceinline__ void load_feat_row(const void* feats, int bf16, int N, uint32_t g, int c0,
+                                              float* __restrict__ dst) {
+  const int nch = min(NC, N - c0);
+  if (!bf16) {
+    const float* src = static_cast<const float*>(feats) + (size_t)g * N + c0;
+    if ((N & 3) == 0 && nch == NC) {
+#pragma unroll
+      for (int c = 0; c < NC; c += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(src + c);
+        dst[c] = v.x; dst[c + 1] = v.y; dst[c + 2] = v.z; dst[c + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) dst[c] = c < nch ? src[c] : 0.f;
+    }
+  } else {
+    const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(feats) + (size_t)g * N + c0;
+    if ((N & 7) == 0 && nch == NC) {
+#pragma unroll
+      for (int c = 0; c < NC; c += 8) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(src + c);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(h[e]);
+          dst[c + 2 * e] = f.x;
+          dst[c + 2 * e + 1] = f.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) dst[c] = c < nch ? __bfloat162float(src[c]) : 0.f;
+    }
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
+  constexpr int NCs = NC > 0 ? NC : 1;
+  __shared__ float2 s_uv[kTilePix];
+  __shared__ float4 s_co[kTilePix];
+  __shared__ float4 s_cd[kTilePix];
+  __shared__ float s_f[kTilePix][NCs];
+
+  const int tile = blockIdx.x;
+  const int chunk = blockIdx.y;
+  const bool geom = chunk == 0;
+  const int c0 = chunk * NC;
+  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
+  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py = ty * kTile + (threadIdx.x / kTile);
+  const bool inside = px < p.cam.W && py < p.cam.H;
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const int2 rg = p.ranges[tile];
+
+  float T = 1.f;
+  float ac0 = 0.f, ac1 = 0.f, ac2 = 0.f, ad = 0.f;
+  float af[NCs];
+#pragma unroll
+  for (int c = 0; c < NCs; ++c) af[c] = 0.f;
+  int last = 0, cnt = 0;
+  bool done = !inside;
+
+  for (int start = rg.x; start < rg.y; start += kTilePix) {
+    if (__syncthreads_count(done) == kTilePix) break;
+    const int idx = start + threadIdx.x;
+    if (idx < rg.y) {
+      const uint32_t g = p.gids[idx];
+      s_uv[threadIdx.x] = p.uv[g];
+      s_co[threadIdx.x] = p.co[g];
+      if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
+      if (NC > 0) load_feat_row<NCs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
+    }
+    __syncthreads();
+    const int n = min(kTilePix, rg.y - start);
+    if (!done) {
+      for (int j = 0; j < n; ++j) {
+        PairAlpha pa;
+        const float2 uj = s_uv[j];
+        if (!pair_alpha(s_co[j], uj.x - pxc, uj.y - pyc, pa)) continue;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.f, pa.alpha));
+        if (Tn < kTStop) {
+          done = true;
+          break;
+        }
+        const float w = __fmul_rn(pa.alpha, T);
+        if (geom) {
+          const float4 cd = s_cd[j];
+          ac0 = __fmaf_rn(w, cd.x, ac0);
+          ac1 = __fmaf_rn(w, cd.y, ac1);
+          ac2 = __fmaf_rn(w, cd.z, ac2);
+          ad = __fmaf_rn(w, cd.w, ad);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) af[c] = __fmaf_rn(w, s_f[j][c], af[c]);
+        T = Tn;
+        last = start + j + 1 - rg.x;
+        ++cnt;
+      }
+    }
+  }
+  if (!inside) return;
+  const size_t HW = (size_t)p.cam.W * p.cam.H;
+  const size_t pix = (size_t)py * p.cam.W + px;
+  if (geom) {
+    p.out_rgb[pix] = ac0 + T * p.bg[0];
+    p.out_rgb[HW + pix] = ac1 + T * p.bg[1];
+    p.out_rgb[2 * HW + pix] = ac2 + T * p.bg[2];
+    p.out_depth[pix] = ad;
+    p.out_alpha[pix] = 1.f - T;
+    p.T_final[pix] = T;
+    p.last_idx[pix] = last;
+    p.n_contrib[pix] = cnt;
+  }
+  if (NC > 0) {
+    const int nch = min(NC, p.N - c0);
+    if (p.hwc) {
+      float* dst = p.out_feat + pix * p.N + c0;
+      if ((p.N & 3) == 0 && nch == NC) {
+#pragma unroll
+        for (int c = 0; c < NCs; c += 4) *reinterpret_cast<float4*>(dst + c) = make_float4(af[c], af[c + 1], af[c + 2], af[c + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NCs; ++c)
+          if (c < nch) dst[c] = af[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NCs; ++c)
+        if (c < nch) p.out_feat[(size_t)(c0 + c) * HW + pix] = af[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct BwdParams {
+  CamF cam;
+  const int2* ranges;
+  const uint32_t* gids;
+  const float2* uv;
+  const float4* co;
+  const float* depth;
+  const float* colors;
+  const void* feats;
+  int N, bf16, hwc;
+  float bg[3];
+  const float* T_final;
+  const int* last_idx;
+  const float* g_rgb;
+  const float* g_depth;
+  const float* g_alpha;
+  const float* g_feat;
+  float* d_uv;
+  float* d_conic;
+  float* d_depth;
+  float* d_opacity;
+  float* d_colors;
+  float* d_feats;
+};
+
+// Lane l ends up with the warp-wide sum of v[l] (see the file comment).
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      const float send = upper ? v[k] : v[k + s];
+      const float keep = upper ? v[k + s] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+constexpr int kGeomCh = 10;  // u, v, A, B, C, opacity, r, g, b, depth
+
+template <int NC>
+struct BwdShape {
+  static constexpr int CH = kGeomCh + NC;
+  static constexpr int CHP = (CH + 31) / 32 * 32;
+  static constexpr int BB = 1024 / CHP;  // Gaussians per batch: 32 KB of partials
+};
+
+template <int NC, bool COUPLED>
+__global__ void __launch_bounds__(kTilePix) k_render_bwd(const BwdParams p) {
+  using S = BwdShape<NC>;
+  constexpr int CH = S::CH, CHP = S::CHP, BB = S::BB;
+  constexpr int NCs = NC > 0 ? NC : 1;
+  constexpr int NFs = (COUPLED && NC > 0) ? NC : 1;
+  __shared__ float s_red[8][BB][CHP];
+  __shared__ float2 s_uv[BB];
+  __shared__ float4 s_co[BB];
+  __shared__ float4 s_cd[BB];
+  __shared__ float s_f[BB][NFs];
+  __shared__ uint32_t s_gid[BB];
+  __shared__ int s_maxlast;
+
+  const int tile = blockIdx.x;
+  const int chunk = blockIdx.y;
+  const bool geom = chunk == 0;
+  const int c0 = chunk * NC;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
+  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py = ty * kTile + (threadIdx.x / kTile);
+  const bool inside = px < p.cam.W && py < p.cam.H;
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const int2 rg = p.ranges[tile];
+  const size_t HW = (size_t)p.cam.W * p.cam.H;
+  const size_t pix = inside ? (size_t)py * p.cam.W + px : 0;
+
+  if (threadIdx.x == 0) s_maxlast = 0;
+  __syncthreads();
+  float T = 1.f;
+  int last = 0;
+  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
+  float gF[NCs];
+#pragma unroll
+  for (int c = 0; c < NCs; ++c) gF[c] = 0.f;
+  if (inside) {
+    T = p.T_final[pix];
+    last = p.last_idx[pix];
+    if (p.g_rgb) {
+      gC0 = p.g_rgb[pix];
+      gC1 = p.g_rgb[HW + pix];
+      gC2 = p.g_rgb[2 * HW + pix];
+    }
+    if (p.g_depth) gD = p.g_depth[pix];
+    if (p.g_alpha) gA = p.g_alpha[pix];
+    if (NC > 0 && p.g_feat) {
+      const int nch = min(NC, p.N - c0);
+#pragma unroll
+      for (int c = 0; c < NCs; ++c)
+        if (c < nch) gF[c] = p.hwc ? p.g_feat[pix * p.N + c0 + c] : p.g_feat[(size_t)(c0 + c) * HW + pix];
+    }
+    if (last > 0) atomicMax(&s_maxlast, last);
+  }
+  __syncthreads();
+  const int maxlast = s_maxlast;
+  const float bgdot = p.bg[0] * gC0 + p.bg[1] * gC1 + p.bg[2] * gC2;
+  float Bc0 = 0.f, Bc1 = 0.f, Bc2 = 0.f, Bd = 0.f, Sx = 1.f;
+  float Bf[NFs];
+#pragma unroll
+  for (int c = 0; c < NFs; ++c) Bf[c] = 0.f;
+
+  for (int hi = rg.x + maxlast; hi > rg.x; hi -= BB) {
+    const int lo = max(rg.x, hi - BB);
+    const int n = hi - lo;
+    if ((int)threadIdx.x < n) {
+      const uint32_t g = p.gids[lo + threadIdx.x];
+      s_gid[threadIdx.x] = g;
+      s_uv[threadIdx.x] = p.uv[g];
+      s_co[threadIdx.x] = p.co[g];
+      if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
+      if (COUPLED && NC > 0) load_feat_row<NFs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
+    }
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+      const int pos = lo + j - rg.x;
+      float v[CHP];
+#pragma unroll
+      for (int c = 0; c < CHP; ++c) v[c] = 0.f;
+      PairAlpha pa;
+      const float2 uj = s_uv[j];
+      const float4 cj = s_co[j];
+      const float dx = uj.x - pxc, dy = uj.y - pyc;
+      const bool contrib = pos < last && pair_alpha(cj, dx, dy, pa);
+      if (contrib) {
+        const float om = 1.f - pa.alpha;
+        T = T / om;
+        const float w = pa.alpha * T;
+        float da = 0.f;
+        if (geom) {
+          const float4 cd = s_cd[j];
+          da = T * ((cd.x - Bc0) * gC0 + (cd.y - Bc1) * gC1 + (cd.z - Bc2) * gC2 + (cd.w - Bd) * gD) +
+               T * Sx * (gA - bgdot);
+          Bc0 = pa.alpha * cd.x + om * Bc0;
+          Bc1 = pa.alpha * cd.y + om * Bc1;
+          Bc2 = pa.alpha * cd.z + om * Bc2;
+          Bd = pa.alpha * cd.w + om * Bd;
+          Sx *= om;
+          v[6] = w * gC0;
+          v[7] = w * gC1;
+          v[8] = w * gC2;
+          v[9] = w * gD;
+        }
+        if (COUPLED && NC > 0) {
+          float daf = 0.f;
+#pragma unroll
+          for (int c = 0; c < NFs; ++c) {
+            daf += (s_f[j][c] - Bf[c]) * gF[c];
+            Bf[c] = pa.alpha * s_f[j][c] + om * Bf[c];
+          }
+          da += T * daf;
+        }
+        if ((geom || COUPLED) && !pa.clamped) {
+          v[5] = da * pa.G;
+          const float dp = da * pa.alpha;
+          v[2] = -0.5f * dx * dx * dp;
+          v[3] = -dx * dy * dp;
+          v[4] = -0.5f * dy * dy * dp;
+          v[0] = -(cj.x * dx + cj.y * dy) * dp;
+          v[1] = -(cj.y * dx + cj.z * dy) * dp;
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[kGeomCh + c] = w * gF[c];
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+        for (int r = 0; r < CHP / 32; ++r) {
+          float part[32];
+#pragma unroll
+          for (int c = 0; c < 32; ++c) part[c] = v[32 * r + c];
+          s_red[wid][j][32 * r + lane] = transpose_reduce32(part);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < CHP / 32; ++r) s_red[wid][j][32 * r + lane] = 0.f;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * CH; e += kTilePix) {
+      const int j = e / CH, ch = e - j * CH;
+      float sum = 0.f;
+#pragma unroll
+      for (int w8 = 0; w8 < 8; ++w8) sum += s_red[w8][j][ch];
+      if (sum == 0.f) continue;
+      const uint32_t g = s_gid[j];
+      float* dst;
+      if (ch < 2) dst = p.d_uv + 2 * (size_t)g + ch;
+      else if (ch < 5) dst = p.d_conic + 3 * (size_t)g + (ch - 2);
+      else if (ch == 5) dst = p.d_opacity + g;
+      else if (ch < 9) dst = p.d_colors + 3 * (size_t)g + (ch - 6);
+      else if (ch == 9) dst = p.d_depth + g;
+      else {
+        const int c = c0 + ch - kGeomCh;
+        if (c >= p.N) continue;
+        dst = p.d_feats + (size_t)g * p.N + c;
+      }
+      atomicAdd(dst, sum);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+                            const float* co, const float* depth, const float* colors, const void* feats, int N,
+                            int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
+                            float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
+                            int32_t* n_contrib, cudaStream_t st) {
+  FwdParams p;
+  p.cam = cam;
+  p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.gids = gids;
+  p.uv = reinterpret_cast<const float2*>(uv);
+  p.co = reinterpret_cast<const float4*>(co);
+  p.depth = depth;
+  p.colors = colors;
+  p.feats = feats;
+  p.N = N;
+  p.bf16 = bf16;
+  p.hwc = hwc;
+  for (int i = 0; i < 3; ++i) p.bg[i] = bg[i];
+  p.out_rgb = out_rgb;
+  p.out_depth = out_depth;
+  p.out_alpha = out_alpha;
+  p.out_feat = out_feat;
+  p.T_final = T_final;
+  p.last_idx = last_idx;
+  p.n_contrib = n_contrib;
+  const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
+  GS_TRACE("k_render_fwd", st);
+  if (N <= 0) {
+    k_render_fwd<0><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+  } else if (N <= 16) {
+    k_render_fwd<16><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+  } else {
+    k_render_fwd<32><<<dim3(tiles, (N + 31) / 32), kTilePix, 0, st>>>(p);
+  }
+  return last_launch_status();
+}
+
+gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+                            const float* co, const float* depth, const float* colors, const void* feats, int N,
+                            int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
+                            const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
+                            int coupled, float* d_uv, float* d_conic, float* d_depth, float* d_opacity,
+                            float* d_colors, float* d_feats, cudaStream_t st) {
+  BwdParams p;
+  p.cam = cam;
+  p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.gids = gids;
+  p.uv = reinterpret_cast<const float2*>(uv);
+  p.co = reinterpret_cast<const float4*>(co);
+  p.depth = depth;
+  p.colors = colors;
+  p.feats = feats;
+  p.N = N;
+  p.bf16 = bf16;
+  p.hwc = hwc;
+  for (int i = 0; i < 3; ++i) p.bg[i] = bg[i];
+  p.T_final = T_final;
+  p.last_idx = last_idx;
+  p.g_rgb = g_rgb;
+  p.g_depth = g_depth;
+  p.g_alpha = g_alpha;
+  p.g_feat = g_feat;
+  p.d_uv = d_uv;
+  p.d_conic = d_conic;
+  p.d_depth = d_depth;
+  p.d_opacity = d_opacity;
+  p.d_colors = d_colors;
+  p.d_feats = d_feats;
+  const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
+  GS_TRACE("k_render_bwd", st);
+  if (N <= 0) {
+    k_render_bwd<0, false><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+  } else if (N <= 16) {
+    if (coupled) k_render_bwd<16, true><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+    else k_render_bwd<16, false><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+  } else {
+    const dim3 grid(tiles, (N + 31) / 32);
+    if (coupled) k_render_bwd<32, true><<<grid, kTilePix, 0, st>>>(p);
+    else k_render_bwd<32, false><<<grid, kTilePix, 0, st>>>(p);
+  }
+  return last_launch_status();
+}
+
+}  // namespace gsff
