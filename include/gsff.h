@@ -110,6 +110,34 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                       int64_t* n_instances, int32_t* status, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_bin_sort_static -- gs_bin_sort for callers that cannot allocate device
+ * memory. The paper has no counterpart; this is a deployment addition.
+ *
+ * Some callers cannot call cudaMalloc: a camera-tracking thread that must
+ * meet a per-frame deadline (cudaMalloc and cudaFree can synchronise the
+ * whole device and stall it), or a host application that owns every device
+ * allocation and only lends the library its input and output buffers. This
+ * entry point takes the same inputs and outputs as gs_bin_sort and runs the
+ * same kernels, but keeps its scratch space in a fixed device array of
+ * GS_BIN_SORT_STATIC_SCRATCH_BYTES (32 MiB) inside the library instead of a
+ * caller workspace. It calls no allocator. Every device that loads the
+ * library holds that array until the process exits.
+ * Limit: gs_bin_sort_workspace_bytes(P, capacity, num_tiles) must not exceed
+ * GS_BIN_SORT_STATIC_SCRATCH_BYTES (about 2.7 million instances of capacity);
+ * larger sizes return GS_ERR_INVALID_ARG and launch nothing.
+ * The first call on a device looks up the array's device address with that
+ * device current (a CUDA runtime query); make that first call before any
+ * stream capture. All calls share the one array and it keeps the previous
+ * call's contents (the sort needs none of it zeroed): calls whose work
+ * overlaps on the GPU (several streams or host threads) race on the array and
+ * must be serialised by the caller.
+ */
+#define GS_BIN_SORT_STATIC_SCRATCH_BYTES (32u << 20)
+gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
+                             const int32_t* tiles_touched, int64_t capacity, uint64_t* keys, uint32_t* gids,
+                             int32_t* tile_ranges, int64_t* n_instances, int32_t* status, void* stream);
+
+/* ---------------------------------------------------------------------------
  * gs_render_fwd -- front-to-back alpha compositing per pixel (Eq. 2-3).
  *
  * For pixel p in tile k, walking k's list in order with T = 1:

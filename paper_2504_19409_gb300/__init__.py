@@ -33,7 +33,8 @@ TILE = 16
 # Every symbol include/gsff.h declares.
 EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_render_fwd",
            "gs_render_bwd_workspace_bytes", "gs_render_bwd", "gs_l1_loss_grad", "gs_trace_enable",
-           "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version")
+           "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
+           "gs_bin_sort_static")
 
 
 class GsffError(RuntimeError):
@@ -83,6 +84,8 @@ def lib():
     L.gs_bin_sort_workspace_bytes.restype = _sz
     L.gs_bin_sort.argtypes = [cam_p, _i32, _vp, _vp, _vp, _i64, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_bin_sort.restype = ctypes.c_int
+    L.gs_bin_sort_static.argtypes = [cam_p, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.gs_bin_sort_static.restype = ctypes.c_int
     L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 7 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 9)
     L.gs_render_fwd.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]

@@ -1,0 +1,67 @@
+// gs_bin_sort_static: the tile x depth sort of gs_bin_sort, for callers that
+// cannot allocate device memory. Its scratch space is a file-scope device
+// array of GS_BIN_SORT_STATIC_SCRATCH_BYTES instead of a caller workspace;
+// everything else (inputs, outputs, kernels, launch order) is gs_bin_sort's.
+//
+// The array is one per device and lives as long as the process. Host code
+// cannot use the array's name as a device address, so the entry point looks
+// the address up with cudaGetSymbolAddress once per device (on its first call
+// on that device, with that device current) and passes it to the kernels.
+
+#include <mutex>
+
+#include "gsff_internal.cuh"
+
+static __device__ __align__(256) unsigned char g_bin_sort_scratch[GS_BIN_SORT_STATIC_SCRATCH_BYTES];
+
+namespace gsff {
+
+size_t bin_sort_workspace_bytes(int P, long long capacity);
+gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int32_t* rect, const int32_t* touched,
+                          long long capacity, void* workspace, unsigned long long* keys, uint32_t* gids,
+                          int32_t* ranges, int64_t* n_out, int32_t* status, cudaStream_t st);
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_bin_sort_scratch on the current device (looked up once).
+gs_status scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bin_sort_scratch) != cudaSuccess || p == nullptr) return GS_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return GS_OK;
+}
+
+}  // namespace
+}  // namespace gsff
+
+extern "C" gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
+                                        const int32_t* tiles_touched, int64_t capacity, uint64_t* keys,
+                                        uint32_t* gids, int32_t* tile_ranges, int64_t* n_instances,
+                                        int32_t* status, void* stream) {
+  using namespace gsff;
+  if (!cam || cam->width <= 0 || cam->height <= 0 || cam->width > (1 << 15) || cam->height > (1 << 15) ||
+      !(cam->fx > 0.f) || !(cam->fy > 0.f) || P < 0 || capacity < 1 || capacity >= (1ll << 31))
+    return GS_ERR_INVALID_ARG;
+  if (!keys || !gids || !tile_ranges || (P > 0 && (!depth || !rect || !tiles_touched))) return GS_ERR_INVALID_ARG;
+  if (!aligned(keys, 8) || !aligned(rect, 16) || !aligned(tile_ranges, 8) || !aligned(n_instances, 8))
+    return GS_ERR_INVALID_ARG;
+  // The sizes must fit the fixed scratch array.
+  if (bin_sort_workspace_bytes(P, capacity) > (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES) return GS_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  const gs_status st = scratch_address(&scratch);
+  if (st != GS_OK) return st;
+  return launch_bin_sort(make_cam(*cam), P, depth, rect, tiles_touched, capacity, scratch,
+                         reinterpret_cast<unsigned long long*>(keys), gids, tile_ranges, n_instances, status,
+                         static_cast<cudaStream_t>(stream));
+}
