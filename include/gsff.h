@@ -92,13 +92,15 @@ gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const 
  * gs_bin_sort -- tile x depth keys and a stable device radix sort (Sec. 3.1:
  * "sorted by depth in a front-to-back order", per 16x16 tile).
  *
- * For every Gaussian g and every tile k of its rectangle one instance with
- * key = (k << 32) | bits(depth_g) and value g is emitted in ascending g; the
- * instances are sorted stably by key (so equal depths keep ascending g).
+ * For every Gaussian g and every tile k of its rectangle there is one
+ * instance; the instances are ordered by the key (k << 32) | bits(depth_g)
+ * with equal keys in ascending g (bits(depth) orders like depth, as depth > 0).
+ * Computed as a stable depth sort of the Gaussians, emission of the
+ * instances in that order, and a stable sort on the tile id alone.
  * In:  depth [P], rect [P,4], tiles_touched [P] from gs_project.
- * Out: keys [capacity] (u64) and gids [capacity] (u32), first I entries valid;
- *      tile_ranges [num_tiles,2] = [start, end) into gids, (0,0) if empty;
- *      n_instances (device int64) = I.
+ * Out: gids [capacity] (u32), first I entries valid; keys [capacity] (u64,
+ *      may be NULL) = the sorted keys; tile_ranges [num_tiles,2] = [start,
+ *      end) into gids, (0,0) if empty; n_instances (device int64) = I.
  * If I > capacity, GS_ERR_CAPACITY is flagged in *status and the lists are
  * truncated (contents unspecified). workspace must hold
  * gs_bin_sort_workspace_bytes(P, capacity, num_tiles) bytes.
@@ -123,7 +125,8 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
  * caller workspace. It calls no allocator. Every device that loads the
  * library holds that array until the process exits.
  * Limit: gs_bin_sort_workspace_bytes(P, capacity, num_tiles) must not exceed
- * GS_BIN_SORT_STATIC_SCRATCH_BYTES (about 2.7 million instances of capacity);
+ * GS_BIN_SORT_STATIC_SCRATCH_BYTES (about 2.4 million instances of capacity
+ * with 300,000 Gaussians: 12 bytes per instance plus 16 per Gaussian);
  * larger sizes return GS_ERR_INVALID_ARG and launch nothing.
  * The first call on a device looks up the array's device address with that
  * device current (a CUDA runtime query); make that first call before any

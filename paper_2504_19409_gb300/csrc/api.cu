@@ -74,9 +74,16 @@ __global__ void k_l1_grad(long long n, const float* __restrict__ pred, const flo
     acc += fabsf(d);
   }
   if (loss) {
+    __shared__ float s_part[32];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0 && acc != 0.f) atomicAdd(loss, acc * scale);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_part[w];
+      if (b != 0.f) atomicAdd(loss, b * scale);
+    }
   }
 }
 
@@ -141,7 +148,7 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                       void* stream) {
   if (!cam_ok(cam) || P < 0 || capacity < 1 || capacity >= (1ll << 31)) return GS_ERR_INVALID_ARG;
   if (num_tiles(cam) > (1 << 24)) return GS_ERR_INVALID_ARG;
-  if (!keys || !gids || !tile_ranges || !workspace || (P > 0 && (!depth || !rect || !tiles_touched)))
+  if (!gids || !tile_ranges || !workspace || (P > 0 && (!depth || !rect || !tiles_touched)))
     return GS_ERR_INVALID_ARG;
   if (!aligned(workspace, 256) || !aligned(keys, 8) || !aligned(rect, 16) || !aligned(tile_ranges, 8) ||
       !aligned(n_instances, 8))
@@ -243,8 +250,8 @@ gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, flo
                           float* loss_sum, void* stream) {
   if (n < 0 || (n > 0 && (!pred || !target || !grad))) return GS_ERR_INVALID_ARG;
   if (n == 0) return GS_OK;
-  long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  long long blocks = (n + 1023) / 1024;
+  if (blocks > 152 * 8) blocks = 152 * 8;
   GS_TRACE("k_l1_grad", S(stream));
   k_l1_grad<<<(unsigned)blocks, 256, 0, S(stream)>>>(n, pred, target, scale, grad, loss_sum);
   return last_launch_status();

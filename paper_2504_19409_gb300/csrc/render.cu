@@ -5,18 +5,27 @@
 // RGB, depth and alpha). Gaussian records of the tile's depth-sorted list
 // are staged in shared memory in batches; per-pixel work is SIMT fp32.
 //
+// Each warp owns an 8x4 (forward) or 8x8 (backward, two pixels per thread)
+// block of the tile. Before evaluating a
+// Gaussian, a warp tests its block against a conservative box around the
+// region where that Gaussian's alpha can reach 1/255 (warp_skip_extent) and
+// skips it as a whole when they are disjoint: the per-pixel decisions are
+// unchanged, only work that would be discarded is avoided.
+//
 // Forward: early termination is tracked per pixel; a block leaves its list
 // as soon as __syncthreads_count sees every pixel done.
 //
 // Backward: each pixel walks its list from last_idx down, recovers T_i =
 // T_{i+1} / (1 - alpha_i) from the saved T_final, and forms the per-pair
-// partials of (u, v, A, B, C, opacity, colour, depth, features). The 256
-// per-pixel partials of each Gaussian are summed in two stages before one
-// global atomic per (Gaussian, channel, tile):
+// partials of (u, v, A, B, C, opacity, colour, depth, features). With at most
+// 16 feature channels each thread owns two pixels (rows r and r+4 of its
+// warp's 8x8 block) and sums their partials first, which halves the warp
+// reductions per pixel. The per-pixel partials of each Gaussian are then
+// summed in two stages before one global atomic per (Gaussian, channel, tile):
 //   (1) within a warp by a transpose-reduction -- 32 channel values per lane
 //       are halved five times with xor-shuffles (16+8+4+2+1 = 31 shuffles)
 //       so that lane l ends up owning the warp sum of channel l;
-//   (2) across the 8 warps through shared memory after each batch.
+//   (2) across the warps through shared memory after each batch.
 
 #include "gsff_internal.cuh"
 
@@ -42,6 +51,51 @@ struct FwdParams {
   int* last_idx;
   int* n_contrib;
 };
+
+
+// Pixel layout: each warp owns an 8-wide block of the 16x16 tile, 4*PPT
+// rows tall (PPT = pixels per thread, stacked 4 rows apart); warps tile the
+// tile 2 across. Compact blocks make the per-warp skip test effective.
+template <int PPT>
+__device__ __forceinline__ void thread_pixels(int tx, int ty, int (&px)[PPT], int (&py)[PPT]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    px[q] = tx * kTile + (w & 1) * 8 + (lane & 7);
+    py[q] = ty * kTile + (w >> 1) * (4 * PPT) + (lane >> 3) + 4 * q;
+  }
+}
+
+// Centre of this warp's block; its pixel centres lie within +-3.5 (x) and
+// +-(2 PPT - 0.5) (y) of it.
+template <int PPT>
+__device__ __forceinline__ float2 warp_centre(int tx, int ty) {
+  const int w = threadIdx.x >> 5;
+  return make_float2((float)(tx * kTile + (w & 1) * 8) + 4.f, (float)(ty * kTile + (w >> 1) * (4 * PPT)) + 2.f * PPT);
+}
+
+// Half-extents, around (u, v), of a box that holds every pixel centre of a
+// warp block that can reach alpha >= 1/255 for this Gaussian. alpha = o G
+// with G = exp(power) needs power >= -ln(255 o); at vertical offset dy the
+// largest power over dx is -dy^2 det / (2 A) (det = A C - B^2), so the
+// region is |dy| <= sqrt(2 ln(255 o) A / det), and |dx| alike with C. The
+// extents are widened by 2% + 0.05 px (far beyond fp32 error, so no skip
+// decision the exact test would keep is dropped) and by the warp block's
+// half-size (hx, hy); nearly singular conics (det < 1e-3 A C) are never
+// skipped.
+__device__ __forceinline__ float2 warp_skip_extent(float4 co, float hx, float hy) {
+  const float t = logf(255.f * co.w);
+  if (t < 0.f) return make_float2(-1.f, -1.f);  // o < 1/255: never blended
+  const float ac = co.x * co.z;
+  const float det = ac - co.y * co.y;
+  if (!(det > 1e-3f * ac)) return make_float2(3.0e38f, 3.0e38f);
+  const float ex = sqrtf(2.f * t * co.z / det), ey = sqrtf(2.f * t * co.x / det);
+  return make_float2(ex * 1.02f + 0.05f + hx, ey * 1.02f + 0.05f + hy);
+}
+
+__device__ __forceinline__ bool warp_skips(float2 uv, float2 ext, float2 wc) {
+  return fabsf(uv.x - wc.x) > ext.x || fabsf(uv.y - wc.y) > ext.y;
+}
 
 template <int NC>
 __device__ __forceinline__ void load_feat_row(const void* feats, int bf16, int N, uint32_t g, int c0,
@@ -84,6 +138,7 @@ template <int NC>
 __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   constexpr int NCs = NC > 0 ? NC : 1;
   __shared__ float2 s_uv[kTilePix];
+  __shared__ float2 s_ext[kTilePix];
   __shared__ float4 s_co[kTilePix];
   __shared__ float4 s_cd[kTilePix];
   __shared__ float s_f[kTilePix][NCs];
@@ -93,8 +148,10 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   const bool geom = chunk == 0;
   const int c0 = chunk * NC;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x / kTile);
+  int pxa[1], pya[1];
+  thread_pixels<1>(tx, ty, pxa, pya);
+  const int px = pxa[0], py = pya[0];
+  const float2 wc = warp_centre<1>(tx, ty);
   const bool inside = px < p.cam.W && py < p.cam.H;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const int2 rg = p.ranges[tile];
@@ -112,8 +169,10 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
     const int idx = start + threadIdx.x;
     if (idx < rg.y) {
       const uint32_t g = p.gids[idx];
+      const float4 co = p.co[g];
       s_uv[threadIdx.x] = p.uv[g];
-      s_co[threadIdx.x] = p.co[g];
+      s_co[threadIdx.x] = co;
+      s_ext[threadIdx.x] = warp_skip_extent(co, 3.5f, 1.5f);
       if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
       if (NC > 0) load_feat_row<NCs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
     }
@@ -121,8 +180,9 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
     const int n = min(kTilePix, rg.y - start);
     if (!done) {
       for (int j = 0; j < n; ++j) {
-        PairAlpha pa;
         const float2 uj = s_uv[j];
+        if (warp_skips(uj, s_ext[j], wc)) continue;
+        PairAlpha pa;
         if (!pair_alpha(s_co[j], uj.x - pxc, uj.y - pyc, pa)) continue;
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, pa.alpha));
         if (Tn < kTStop) {
@@ -226,17 +286,21 @@ template <int NC>
 struct BwdShape {
   static constexpr int CH = kGeomCh + NC;
   static constexpr int CHP = (CH + 31) / 32 * 32;
-  static constexpr int BB = 1024 / CHP;  // Gaussians per batch: 32 KB of partials
 };
 
-template <int NC, bool COUPLED>
-__global__ void __launch_bounds__(kTilePix) k_render_bwd(const BwdParams p) {
+// PPT pixels per thread (1 or 2); kTilePix / PPT threads per tile block.
+template <int NC, bool COUPLED, int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || COUPLED) ? 2 : 3))
+    k_render_bwd(const BwdParams p) {
   using S = BwdShape<NC>;
-  constexpr int CH = S::CH, CHP = S::CHP, BB = S::BB;
+  constexpr int CH = S::CH, CHP = S::CHP;
+  constexpr int NT = kTilePix / PPT, NW = NT / 32;
+  constexpr int BB = (8192 / (NW * CHP)) < 64 ? (8192 / (NW * CHP)) : 64;  // batch: 32 KB of partials
   constexpr int NCs = NC > 0 ? NC : 1;
   constexpr int NFs = (COUPLED && NC > 0) ? NC : 1;
-  __shared__ float s_red[8][BB][CHP];
+  __shared__ float s_red[NW][BB][CHP];
   __shared__ float2 s_uv[BB];
+  __shared__ float2 s_ext[BB];
   __shared__ float4 s_co[BB];
   __shared__ float4 s_cd[BB];
   __shared__ float s_f[BB][NFs];
@@ -249,111 +313,130 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(const BwdParams p) {
   const int c0 = chunk * NC;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x / kTile);
-  const bool inside = px < p.cam.W && py < p.cam.H;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  int px[PPT], py[PPT];
+  thread_pixels<PPT>(tx, ty, px, py);
+  const float2 wc = warp_centre<PPT>(tx, ty);
   const int2 rg = p.ranges[tile];
   const size_t HW = (size_t)p.cam.W * p.cam.H;
-  const size_t pix = inside ? (size_t)py * p.cam.W + px : 0;
 
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
-  float T = 1.f;
-  int last = 0;
-  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
-  float gF[NCs];
+  float T[PPT], pxc[PPT], pyc[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gA[PPT], bgdot[PPT];
+  float Bc0[PPT], Bc1[PPT], Bc2[PPT], Bd[PPT], Sx[PPT];
+  float gF[PPT][NCs], Bf[PPT][NFs];
+  int last[PPT];
 #pragma unroll
-  for (int c = 0; c < NCs; ++c) gF[c] = 0.f;
-  if (inside) {
-    T = p.T_final[pix];
-    last = p.last_idx[pix];
-    if (p.g_rgb) {
-      gC0 = p.g_rgb[pix];
-      gC1 = p.g_rgb[HW + pix];
-      gC2 = p.g_rgb[2 * HW + pix];
-    }
-    if (p.g_depth) gD = p.g_depth[pix];
-    if (p.g_alpha) gA = p.g_alpha[pix];
-    if (NC > 0 && p.g_feat) {
-      const int nch = min(NC, p.N - c0);
+  for (int q = 0; q < PPT; ++q) {
+    const bool inside = px[q] < p.cam.W && py[q] < p.cam.H;
+    const size_t pix = inside ? (size_t)py[q] * p.cam.W + px[q] : 0;
+    pxc[q] = (float)px[q] + 0.5f;
+    pyc[q] = (float)py[q] + 0.5f;
+    T[q] = 1.f;
+    last[q] = 0;
+    gC0[q] = gC1[q] = gC2[q] = gD[q] = gA[q] = 0.f;
+    Bc0[q] = Bc1[q] = Bc2[q] = Bd[q] = 0.f;
+    Sx[q] = 1.f;
 #pragma unroll
-      for (int c = 0; c < NCs; ++c)
-        if (c < nch) gF[c] = p.hwc ? p.g_feat[pix * p.N + c0 + c] : p.g_feat[(size_t)(c0 + c) * HW + pix];
+    for (int c = 0; c < NCs; ++c) gF[q][c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NFs; ++c) Bf[q][c] = 0.f;
+    if (inside) {
+      T[q] = p.T_final[pix];
+      last[q] = p.last_idx[pix];
+      if (p.g_rgb) {
+        gC0[q] = p.g_rgb[pix];
+        gC1[q] = p.g_rgb[HW + pix];
+        gC2[q] = p.g_rgb[2 * HW + pix];
+      }
+      if (p.g_depth) gD[q] = p.g_depth[pix];
+      if (p.g_alpha) gA[q] = p.g_alpha[pix];
+      if (NC > 0 && p.g_feat) {
+        const int nch = min(NC, p.N - c0);
+#pragma unroll
+        for (int c = 0; c < NCs; ++c)
+          if (c < nch) gF[q][c] = p.hwc ? p.g_feat[pix * p.N + c0 + c] : p.g_feat[(size_t)(c0 + c) * HW + pix];
+      }
+      if (last[q] > 0) atomicMax(&s_maxlast, last[q]);
     }
-    if (last > 0) atomicMax(&s_maxlast, last);
+    bgdot[q] = p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q];
   }
   __syncthreads();
   const int maxlast = s_maxlast;
-  const float bgdot = p.bg[0] * gC0 + p.bg[1] * gC1 + p.bg[2] * gC2;
-  float Bc0 = 0.f, Bc1 = 0.f, Bc2 = 0.f, Bd = 0.f, Sx = 1.f;
-  float Bf[NFs];
-#pragma unroll
-  for (int c = 0; c < NFs; ++c) Bf[c] = 0.f;
 
   for (int hi = rg.x + maxlast; hi > rg.x; hi -= BB) {
     const int lo = max(rg.x, hi - BB);
     const int n = hi - lo;
     if ((int)threadIdx.x < n) {
       const uint32_t g = p.gids[lo + threadIdx.x];
+      const float4 co = p.co[g];
       s_gid[threadIdx.x] = g;
       s_uv[threadIdx.x] = p.uv[g];
-      s_co[threadIdx.x] = p.co[g];
+      s_co[threadIdx.x] = co;
+      s_ext[threadIdx.x] = warp_skip_extent(co, 3.5f, 2.f * PPT - 0.5f);
       if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
       if (COUPLED && NC > 0) load_feat_row<NFs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
     }
     __syncthreads();
     for (int j = n - 1; j >= 0; --j) {
       const int pos = lo + j - rg.x;
+      const float2 uj = s_uv[j];
+      if (warp_skips(uj, s_ext[j], wc)) {
+#pragma unroll
+        for (int r = 0; r < CHP / 32; ++r) s_red[wid][j][32 * r + lane] = 0.f;
+        continue;
+      }
+      const float4 cj = s_co[j];
       float v[CHP];
 #pragma unroll
       for (int c = 0; c < CHP; ++c) v[c] = 0.f;
-      PairAlpha pa;
-      const float2 uj = s_uv[j];
-      const float4 cj = s_co[j];
-      const float dx = uj.x - pxc, dy = uj.y - pyc;
-      const bool contrib = pos < last && pair_alpha(cj, dx, dy, pa);
-      if (contrib) {
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        PairAlpha pa;
+        const float dx = uj.x - pxc[q], dy = uj.y - pyc[q];
+        if (!(pos < last[q] && pair_alpha(cj, dx, dy, pa))) continue;
+        any = true;
         const float om = 1.f - pa.alpha;
-        T = T / om;
-        const float w = pa.alpha * T;
+        T[q] = __fdividef(T[q], om);
+        const float w = pa.alpha * T[q];
         float da = 0.f;
         if (geom) {
           const float4 cd = s_cd[j];
-          da = T * ((cd.x - Bc0) * gC0 + (cd.y - Bc1) * gC1 + (cd.z - Bc2) * gC2 + (cd.w - Bd) * gD) +
-               T * Sx * (gA - bgdot);
-          Bc0 = pa.alpha * cd.x + om * Bc0;
-          Bc1 = pa.alpha * cd.y + om * Bc1;
-          Bc2 = pa.alpha * cd.z + om * Bc2;
-          Bd = pa.alpha * cd.w + om * Bd;
-          Sx *= om;
-          v[6] = w * gC0;
-          v[7] = w * gC1;
-          v[8] = w * gC2;
-          v[9] = w * gD;
+          da = T[q] * ((cd.x - Bc0[q]) * gC0[q] + (cd.y - Bc1[q]) * gC1[q] + (cd.z - Bc2[q]) * gC2[q] +
+                       (cd.w - Bd[q]) * gD[q]) +
+               T[q] * Sx[q] * (gA[q] - bgdot[q]);
+          Bc0[q] = pa.alpha * cd.x + om * Bc0[q];
+          Bc1[q] = pa.alpha * cd.y + om * Bc1[q];
+          Bc2[q] = pa.alpha * cd.z + om * Bc2[q];
+          Bd[q] = pa.alpha * cd.w + om * Bd[q];
+          Sx[q] *= om;
+          v[6] += w * gC0[q];
+          v[7] += w * gC1[q];
+          v[8] += w * gC2[q];
+          v[9] += w * gD[q];
         }
         if (COUPLED && NC > 0) {
           float daf = 0.f;
 #pragma unroll
           for (int c = 0; c < NFs; ++c) {
-            daf += (s_f[j][c] - Bf[c]) * gF[c];
-            Bf[c] = pa.alpha * s_f[j][c] + om * Bf[c];
+            daf += (s_f[j][c] - Bf[q][c]) * gF[q][c];
+            Bf[q][c] = pa.alpha * s_f[j][c] + om * Bf[q][c];
           }
-          da += T * daf;
+          da += T[q] * daf;
         }
         if ((geom || COUPLED) && !pa.clamped) {
-          v[5] = da * pa.G;
+          v[5] += da * pa.G;
           const float dp = da * pa.alpha;
-          v[2] = -0.5f * dx * dx * dp;
-          v[3] = -dx * dy * dp;
-          v[4] = -0.5f * dy * dy * dp;
-          v[0] = -(cj.x * dx + cj.y * dy) * dp;
-          v[1] = -(cj.y * dx + cj.z * dy) * dp;
+          v[2] += -0.5f * dx * dx * dp;
+          v[3] += -dx * dy * dp;
+          v[4] += -0.5f * dy * dy * dp;
+          v[0] += -(cj.x * dx + cj.y * dy) * dp;
+          v[1] += -(cj.y * dx + cj.z * dy) * dp;
         }
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[kGeomCh + c] = w * gF[c];
+        for (int c = 0; c < NC; ++c) v[kGeomCh + c] += w * gF[q][c];
       }
-      if (__any_sync(0xffffffffu, contrib)) {
+      if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
         for (int r = 0; r < CHP / 32; ++r) {
           float part[32];
@@ -367,11 +450,11 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(const BwdParams p) {
       }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n * CH; e += kTilePix) {
+    for (int e = threadIdx.x; e < n * CH; e += NT) {
       const int j = e / CH, ch = e - j * CH;
       float sum = 0.f;
 #pragma unroll
-      for (int w8 = 0; w8 < 8; ++w8) sum += s_red[w8][j][ch];
+      for (int w8 = 0; w8 < NW; ++w8) sum += s_red[w8][j][ch];
       if (sum == 0.f) continue;
       const uint32_t g = s_gid[j];
       float* dst;
@@ -464,14 +547,14 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32
   const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
   GS_TRACE("k_render_bwd", st);
   if (N <= 0) {
-    k_render_bwd<0, false><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+    k_render_bwd<0, false, 2><<<dim3(tiles, 1), kTilePix / 2, 0, st>>>(p);
   } else if (N <= 16) {
-    if (coupled) k_render_bwd<16, true><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
-    else k_render_bwd<16, false><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+    if (coupled) k_render_bwd<16, true, 1><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+    else k_render_bwd<16, false, 2><<<dim3(tiles, 1), kTilePix / 2, 0, st>>>(p);
   } else {
     const dim3 grid(tiles, (N + 31) / 32);
-    if (coupled) k_render_bwd<32, true><<<grid, kTilePix, 0, st>>>(p);
-    else k_render_bwd<32, false><<<grid, kTilePix, 0, st>>>(p);
+    if (coupled) k_render_bwd<32, true, 1><<<grid, kTilePix, 0, st>>>(p);
+    else k_render_bwd<32, false, 1><<<grid, kTilePix, 0, st>>>(p);
   }
   return last_launch_status();
 }
