@@ -188,7 +188,8 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
                                      out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, S(stream));
     if (st != GS_OK) return st;
     return launch_render_fwd_tc(k, tile_ranges, gids, uv, conic_opacity,
-                                static_cast<const __nv_bfloat16*>(feats), N, out_feat, status, S(stream));
+                                static_cast<const __nv_bfloat16*>(feats), last_idx, N, out_feat, status,
+                                S(stream));
   }
   return launch_render_fwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, n,
                            feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, out_rgb, out_depth, out_alpha, out_feat,

@@ -1,11 +1,349 @@
-// Tensor-core (tcgen05) form of the feature contraction: not yet built.
+// Tensor-core (tcgen05) form of the feature channels of Eq. 3.
+//
+// Per tile the N feature channels are a dense contraction: with the tile's
+// depth-sorted list as the contraction index k,
+//     F[p, :] = sum_k w[p, k] f[g_k, :],   w[p, k] = alpha_k(p) T_k(p)
+// (w = 0 where pixel p skips or has stopped). One CTA owns half a tile
+// (16 x 8 = 128 pixels = the 128 rows of a tcgen05 M=128 tile) and walks the
+// list in K-steps of 32 Gaussians:
+//   - 4 threads per pixel (512 threads) each evaluate alpha for 8 of the 32
+//     Gaussians with the SIMT kernel's exact skip test; below last_idx no
+//     pixel has stopped, so T_k is the product of (1 - alpha_j) over the
+//     blended j < k, combined across the 4 threads by a width-4 shuffle
+//     scan; each thread stores its 8 weights (bf16) as one 16-byte row of a
+//     core matrix of the A operand [128 x 32] (K-major);
+//   - the 32 feature rows (bf16) are copied with cp.async into the B operand
+//     [32 x N] (MN-major: channels contiguous);
+//   - one thread issues tcgen05.mma kind::f16 (M=128, N<=256 per
+//     instruction, K=16) accumulating F in fp32 in tensor memory (N columns);
+//   - a 3-stage shared-memory ring lets the next step's loads and weights
+//     proceed while the tensor core consumes the current step
+//     (tcgen05.commit -> mbarrier per stage).
+// The epilogue reads F from tensor memory (tcgen05.ld 32x32b) and writes it
+// in HWC layout. RGB, depth, alpha, T_final and last_idx come from the SIMT
+// forward kernel launched before this one (its last_idx bounds each pixel).
+//
+// Shared-memory operand layouts (no swizzle; 16-byte core-matrix rows):
+//   A: element (m, k) at (m/8)*512 + (k/8)*128 + (m%8)*16 + (k%8)*2
+//      descriptor LBO = 128 (K direction), SBO = 512 (M direction)
+//   B: element (k, n) at (n/8)*128 + (k/8)*SK + (k%8)*16 + (n%8)*2, SK = N*16
+//      descriptor LBO = SK (K direction), SBO = 128 (N direction)
+// Every wait is bounded (1 s of %globaltimer); a timeout flags
+// GS_ERR_TIMEOUT, waits (bounded) for the tensor core, frees tensor memory
+// and returns.
+
 #include "gsff_internal.cuh"
 
 namespace gsff {
+namespace {
 
-gs_status launch_render_fwd_tc(const CamF&, const int32_t*, const uint32_t*, const float*, const float*,
-                               const __nv_bfloat16*, int, float*, int32_t*, cudaStream_t) {
-  return GS_ERR_UNSUPPORTED;
+constexpr int kTcPix = 128;    // pixels per CTA = MMA M
+constexpr int kTcThreads = 512;  // 4 threads per pixel
+constexpr int kTcK = 32;       // Gaussians per K-step
+constexpr int kTcStages = 3;
+constexpr int kTcMaxN = 512;
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+struct TcStage {
+  uint8_t A[kTcPix * kTcK * 2];       // 8 KB
+  uint8_t B[kTcK * kTcMaxN * 2];      // 32 KB (for N = 512)
+  float2 uv[kTcK];
+  float4 co[kTcK];
+};
+
+struct TcSmem {
+  TcStage st[kTcStages];
+  unsigned long long mbar[kTcStages];
+  uint32_t tmem;
+  int maxlast;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: f32 accumulate, bf16 A and B, A K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N, int b_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)b_mn_major << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the given phase parity of an mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const unsigned long long t0 = gtime();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtime() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  const int n = valid ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcFwdParams {
+  CamF cam;
+  const int2* ranges;
+  const uint32_t* gids;
+  const float2* uv;
+  const float4* co;
+  const __nv_bfloat16* feats;
+  const int* last_idx;
+  int N;
+  int tmem_cols;
+  float* out_feat;
+  int32_t* status;
+};
+
+// Loads of K-step t into stage s: Gaussian records (threads 0..31) and the
+// feature rows (every thread, 16-byte cp.async chunks, zero-filled past the
+// list).
+__device__ __forceinline__ void tc_issue_loads(const TcFwdParams& p, TcStage& st, int t, int2 rg, int maxlast) {
+  const int tid = threadIdx.x;
+  const int base = rg.x + t * kTcK;
+  const int lim = rg.x + maxlast;
+  if (tid < kTcK) {
+    const int pos = base + tid;
+    if (pos < lim) {
+      const uint32_t g = p.gids[pos];
+      st.uv[tid] = p.uv[g];
+      st.co[tid] = p.co[g];
+    } else {
+      st.uv[tid] = make_float2(0.f, 0.f);
+      st.co[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  const int cpr = p.N / 8;           // 16-byte chunks per feature row
+  const uint32_t SK = (uint32_t)p.N * 16;
+  const uint32_t b0 = smem_u32(st.B);
+  for (int e = tid; e < kTcK * cpr; e += kTcThreads) {
+    const int k = e / cpr, c = e - k * cpr;
+    const int pos = base + k;
+    const bool valid = pos < lim;
+    const uint32_t g = valid ? p.gids[pos] : 0u;
+    const __nv_bfloat16* src = p.feats + (size_t)g * p.N + 8 * c;
+    const uint32_t dst = b0 + (uint32_t)c * 128u + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
+    cp_async16(dst, src, valid);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m = tid >> 2, q = tid & 3;  // pixel row of the MMA tile, quarter of the K-step
+  const int tile = blockIdx.x >> 1, half = blockIdx.x & 1;
+  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
+  const int px = tx * kTile + (m & 15);
+  const int py = ty * kTile + half * 8 + (m >> 4);
+  const bool inside = px < p.cam.W && py < p.cam.H;
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const int2 rg = p.ranges[tile];
+  const int last = inside ? p.last_idx[(size_t)py * p.cam.W + px] : 0;
+
+  if (tid == 0) S.maxlast = 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(p.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (q == 0 && last > 0) atomicMax(&S.maxlast, last);
+  __syncthreads();
+  const int maxlast = S.maxlast;
+  const uint32_t tmem = S.tmem;
+  const int nsteps = (maxlast + kTcK - 1) / kTcK;
+  const uint32_t SK = (uint32_t)p.N * 16;
+  bool ok = true;
+
+  if (nsteps > 0) tc_issue_loads(p, S.st[0], 0, rg, maxlast);
+  if (nsteps > 1) tc_issue_loads(p, S.st[1], 1, rg, maxlast);
+  float T = 1.f;  // transmittance in front of this K-step (same in the 4 threads of a pixel)
+  int last_issued = -1;  // last K-step whose MMAs were issued (block-uniform)
+  for (int t = 0; t < nsteps && ok; ++t) {
+    const int s = t % kTcStages;
+    TcStage& st = S.st[s];
+    if (t + 1 < nsteps) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // alphas of my 8 Gaussians (0 where skipped or past last_idx)
+    float a[8];
+    float prod = 1.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a[j] = 0.f;
+      const int k = 8 * q + j;
+      PairAlpha pa;
+      if (t * kTcK + k < last && pair_alpha(st.co[k], st.uv[k].x - pxc, st.uv[k].y - pyc, pa)) {
+        a[j] = pa.alpha;
+        prod = __fmul_rn(prod, __fsub_rn(1.f, pa.alpha));
+      }
+    }
+    // exclusive product over the quarters before mine (lanes 4m..4m+3)
+    float incl = prod;
+    float y = __shfl_up_sync(0xffffffffu, incl, 1, 4);
+    if (q >= 1) incl = __fmul_rn(incl, y);
+    y = __shfl_up_sync(0xffffffffu, incl, 2, 4);
+    if (q >= 2) incl = __fmul_rn(incl, y);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1, 4);
+    if (q == 0) excl = 1.f;
+    const float total = __shfl_sync(0xffffffffu, incl, 3, 4);
+    float Tj = __fmul_rn(T, excl);
+    uint32_t packed[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const float w0 = __fmul_rn(a[j], Tj);
+      if (a[j] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j]));
+      const float w1 = __fmul_rn(a[j + 1], Tj);
+      if (a[j + 1] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j + 1]));
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(w0, w1);
+      packed[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    T = __fmul_rn(T, total);
+    *reinterpret_cast<uint4*>(st.A + (m >> 3) * 512 + q * 128 + (m & 7) * 16) =
+        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_u32(st.A), b0 = smem_u32(st.B);
+      for (int n0 = 0; n0 < p.N; n0 += 256) {
+        const int nn = min(256, p.N - n0);
+        const uint32_t idesc = idesc_bf16(kTcPix, nn, 1);
+#pragma unroll
+        for (int k16 = 0; k16 < kTcK / 16; ++k16) {
+          const uint64_t ad = smem_desc(a0 + k16 * 256, 128, 512);
+          const uint64_t bd = smem_desc(b0 + (uint32_t)(n0 / 8) * 128u + (uint32_t)k16 * 2u * SK, SK, 128);
+          const uint32_t acc = (t > 0 || k16 > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)n0),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.mbar[s])));
+    }
+    last_issued = t;
+    if (t + 2 < nsteps) {
+      // stage (t+2)%3 was last read by the MMAs of step t-1
+      bool w_ok = true;
+      if (t >= 1) w_ok = mbar_wait(smem_u32(&S.mbar[(t - 1) % kTcStages]), (uint32_t)(((t - 1) / kTcStages) & 1));
+      ok = __syncthreads_and(w_ok) != 0;
+      if (ok) tc_issue_loads(p, S.st[(t + 2) % kTcStages], t + 2, rg, maxlast);
+    }
+  }
+  if (nsteps > 0 && ok) {
+    const int tl = nsteps - 1;
+    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar[tl % kTcStages]), (uint32_t)((tl / kTcStages) & 1))) != 0;
+  }
+  if (!ok) {
+    if (tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
+    // bounded drain of the last issued commit before freeing tensor memory
+    if (last_issued >= 0)
+      mbar_wait(smem_u32(&S.mbar[last_issued % kTcStages]), (uint32_t)((last_issued / kTcStages) & 1));
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // epilogue: warp w reads tensor-memory lanes 32*(w%4).. (pixel rows);
+    // the 32-column chunks go round-robin to the 4 warps sharing those lanes
+    const int row = 32 * (warp & 3) + (tid & 31);
+    const int ex = tx * kTile + (row & 15), ey = ty * kTile + half * 8 + (row >> 4);
+    const bool e_inside = ex < p.cam.W && ey < p.cam.H;
+    float* dst = p.out_feat + ((size_t)ey * p.cam.W + ex) * p.N;
+    for (int c = 32 * (warp >> 2); c < p.N; c += 128) {
+      float v[32];
+      if (nsteps > 0) {
+        tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      if (e_inside) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 4)
+          *reinterpret_cast<float4*>(dst + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+}
+
+}  // namespace
+
+gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+                               const float* co, const __nv_bfloat16* feats, const int32_t* last_idx, int N,
+                               float* out_feat, int32_t* status, cudaStream_t st) {
+  if (N <= 0 || N % 64 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
+  TcFwdParams p;
+  p.cam = cam;
+  p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.gids = gids;
+  p.uv = reinterpret_cast<const float2*>(uv);
+  p.co = reinterpret_cast<const float4*>(co);
+  p.feats = feats;
+  p.last_idx = last_idx;
+  p.N = N;
+  int cols = 32;
+  while (cols < N) cols *= 2;
+  p.tmem_cols = cols;
+  p.out_feat = out_feat;
+  p.status = status;
+  const size_t smem = sizeof(TcSmem) + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_render_feat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GS_ERR_CUDA;
+    attr_set = true;
+  }
+  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2);
+  GS_TRACE("k_render_feat_tc", st);
+  k_render_feat_tc<<<blocks, kTcThreads, smem, st>>>(p);
+  return last_launch_status();
 }
 
 }  // namespace gsff

@@ -93,6 +93,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // ---- launchers implemented in the .cu files ---------------------------------
 gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uint32_t* gids,
                                const float* uv, const float* co, const __nv_bfloat16* feats,
-                               int N, float* out_feat, int32_t* status, cudaStream_t st);
+                               const int32_t* last_idx, int N, float* out_feat, int32_t* status,
+                               cudaStream_t st);
 
 }  // namespace gsff

@@ -1,0 +1,92 @@
+"""Tensor-core (tcgen05) form of the feature channels vs the FP64 oracle.
+
+The weights w = alpha T are rounded to bf16 (the features are bf16 by
+construction and the oracle uses their exact values), products are exact and
+accumulate in fp32, so per pixel and channel
+    |F_tc - F| <= (2^-8 + 1e-5) * sum_i w_i |f_i| + 1e-7,
+with 2^-8 bounding the bf16 rounding of w (unit roundoff 2^-9, doubled) and
+1e-5 covering fp32 accumulation over a few hundred terms. sum_i w_i |f_i| is
+the oracle's render of |f|. RGB, depth, alpha and the saved state come from
+the SIMT kernel and must equal the plain path's bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_19409_gb300 import build
+    build.build()
+    import paper_2504_19409_gb300 as g
+    g.lib()
+    return g
+
+
+def _t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def _bf16_exact(f):
+    return torch.from_numpy(np.ascontiguousarray(f)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def _render(gs, cam, sc, flags):
+    means, scales, quats, opac, cols = (_t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
+    feats = _t(sc.feats, torch.bfloat16)
+    proj = gs.project(cam, means, scales, quats, opac)
+    srt = gs.bin_sort(cam, proj, max(int(proj["n_instances"].item()), 1))
+    fw = gs.render_fwd(cam, proj, srt, cols, feats, flags=flags, layout=gs.GS_LAYOUT_HWC, status=srt["status"])
+    torch.cuda.synchronize()
+    assert int(srt["status"].item()) == 0
+    return {k: v.cpu().numpy() for k, v in fw.items()}
+
+
+@pytest.mark.parametrize("N,shape,P,seed", [(512, (96, 64), 1500, 21), (128, (100, 37), 900, 22),
+                                             (256, (64, 48), 700, 23)])
+def test_tc_features_within_bound(gs, ora, sg, N, shape, P, seed):
+    cam = sg.identity_camera(shape[0], shape[1], 0.8 * shape[0]).as_f32()
+    sc = sg.frustum_scene(seed, P, cam, N)
+    g = sc.feats
+    sc.feats = (g / np.linalg.norm(g, axis=1, keepdims=True)).astype(np.float32)
+    f_exact = _bf16_exact(sc.feats)
+    tc = _render(gs, cam, sc, gs.GS_FEAT_ON | gs.GS_FEAT_TENSOR_CORE)
+    plain = _render(gs, cam, sc, gs.GS_FEAT_ON)
+    for k in ("rgb", "depth", "alpha", "T_final", "last_idx", "n_contrib"):
+        assert np.array_equal(tc[k], plain[k]), k
+    pr = ora.project_b32(cam, sc.means, sc.scales, sc.quats, sc.opacity)
+    ranges, gids = ora.bin_lists(cam, pr["rect"], pr["depth"])
+    fo = ora.render_fwd(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity, sc.colors, pr["depth"], f_exact)
+    fa = ora.render_fwd(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity, sc.colors, pr["depth"],
+                        np.abs(f_exact))
+    ok = fo["margin"] > 1e-5
+    F_tc = np.transpose(tc["feat"], (2, 0, 1))
+    bound = (2.0 ** -8 + 1e-5) * fa["feat"] + 1e-7
+    err = np.abs(F_tc - fo["feat"])
+    assert (err[:, ok] <= bound[:, ok]).all(), float((err[:, ok] / bound[:, ok]).max())
+    # the bound is not vacuous: the error is a visible fraction of it
+    assert (err[:, ok] / bound[:, ok]).max() > 0.05
+    # the plain fp32 path is far tighter
+    F_pl = np.transpose(plain["feat"], (2, 0, 1))
+    assert np.abs(F_pl - fo["feat"])[:, ok].max() <= 1e-5 * max(1.0, np.abs(fo["feat"]).max())
+
+
+def test_tc_empty_tiles_write_zeros(gs, sg):
+    cam = sg.identity_camera(64, 48, 50.0).as_f32()
+    sc = sg.frustum_scene(5, 3, cam, 64)
+    tc = _render(gs, cam, sc, gs.GS_FEAT_ON | gs.GS_FEAT_TENSOR_CORE)
+    plain = _render(gs, cam, sc, gs.GS_FEAT_ON)
+    empty = plain["n_contrib"] == 0
+    assert empty.sum() > 100
+    assert (tc["feat"][empty] == 0).all()
+
+
+def test_tc_rejects_unsupported_shapes(gs, sg):
+    cam = sg.identity_camera(64, 48, 50.0).as_f32()
+    sc = sg.frustum_scene(5, 50, cam, 48)
+    with pytest.raises(gs.GsffError):
+        _render(gs, cam, sc, gs.GS_FEAT_ON | gs.GS_FEAT_TENSOR_CORE)
