@@ -182,6 +182,12 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
  *      d_opacity [P], d_colors [P,3], d_feats [P,N] (fp32 even for bf16
  *      features), d_pose [6] = (rho, theta) of the left perturbation
  *      T_CW <- Exp(tau) T_CW at tau = 0.
+ * GS_FEAT_TENSOR_CORE (decoupled mode, bf16 features, layout HWC, N % 128
+ * == 0, N <= 512): the feature gradient is computed per half tile as the
+ * tcgen05 product dL/dF^T [N x 128 px] (rounded to bf16) times the weights
+ * W [128 px x 32 Gaussians] (bf16), fp32 accumulation; the geometry
+ * gradients stay on the fp32 SIMT kernel. Coupled mode is GS_ERR_UNSUPPORTED
+ * there.
  * workspace must hold gs_render_bwd_workspace_bytes(P) bytes.
  */
 size_t gs_render_bwd_workspace_bytes(int32_t P);

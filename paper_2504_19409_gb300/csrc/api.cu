@@ -231,6 +231,10 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
     n = N;
   }
   const bool coupled = feat_on && feat_grad_mode == GS_FEAT_GRAD_COUPLED && dL_dfeat;
+  const bool tc = feat_on && (flags & GS_FEAT_TENSOR_CORE);
+  if (tc && (coupled || feat_dtype != GS_BF16 || layout != GS_LAYOUT_HWC || N % 128 != 0 || N > 512))
+    return GS_ERR_UNSUPPORTED;
+  if (tc && dL_dfeat && !aligned(dL_dfeat, 16)) return GS_ERR_INVALID_ARG;
   const float* b = bg ? bg : kBlack;
   const CamF k = make_cam(*cam);
   char* ws = static_cast<char*>(workspace);
@@ -238,11 +242,18 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
   float* w_conic = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256));
   float* w_depth = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256) + align_up((size_t)P * 3 * 4, 256));
   if (cudaMemsetAsync(workspace, 0, gs_render_bwd_workspace_bytes(P), S(stream)) != cudaSuccess) return GS_ERR_CUDA;
-  gs_status st = launch_render_bwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, n,
+  // with the tensor-core form the SIMT adjoint does the geometry only and the
+  // feature gradient is a tcgen05 contraction
+  gs_status st = launch_render_bwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, tc ? 0 : n,
                                    feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, T_final, last_idx, dL_drgb,
-                                   dL_ddepth, dL_dalpha, feat_on ? dL_dfeat : nullptr, coupled ? 1 : 0, w_uv, w_conic,
-                                   w_depth, d_opacity, d_colors, d_feats, S(stream));
+                                   dL_ddepth, dL_dalpha, (feat_on && !tc) ? dL_dfeat : nullptr, coupled ? 1 : 0, w_uv,
+                                   w_conic, w_depth, d_opacity, d_colors, d_feats, S(stream));
   if (st != GS_OK) return st;
+  if (tc && dL_dfeat) {
+    st = launch_render_bwd_feat_tc(k, tile_ranges, gids, uv, conic_opacity, last_idx, dL_dfeat, N, d_feats, status,
+                                   S(stream));
+    if (st != GS_OK) return st;
+  }
   launch_project_bwd(k, P, means, scales, quats, w_uv, w_conic, w_depth, d_means, d_scales, d_quats, d_pose, S(stream));
   return last_launch_status();
 }

@@ -346,4 +346,273 @@ gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uin
   return last_launch_status();
 }
 
+
+// ===========================================================================
+// Adjoint of the feature channels in the paper's decoupled mode (Sec. 3.1:
+// the feature cotangent reaches only f): dL/df_g = sum_p w_g(p) dL/dF(p, :).
+// Per half tile, transposed so that every operand keeps a validated layout:
+//     D [N channels x 32 Gaussians] = dF^T [N x 128 px] * W [128 px x 32]
+//   A = dF^T, K-major, converted to bf16 once per CTA (N/128 M-blocks):
+//       element (c, p) at (c/8)*2048 + (p/8)*128 + (c%8)*16 + (p%8)*2
+//       descriptor LBO = 128 (K = pixels), SBO = 2048 (M = channels)
+//   B = W, MN-major (Gaussians contiguous for a pixel), one 16-byte row per
+//       thread exactly as in the forward:
+//       element (p, g) at (g/8)*128 + (p/8)*512 + (p%8)*16 + (g%8)*2
+//       descriptor LBO = 512 (K = pixels), SBO = 128 (N = Gaussians)
+// D is double-buffered in tensor memory (2 x N/4 columns), so the MMAs of a
+// Gaussian block overlap the epilogue of the previous one. The epilogue adds
+// each Gaussian's N-vector to dL/df with coalesced fp32 atomics (32 lanes =
+// 32 consecutive channels), skipping Gaussians that weigh nothing in this
+// half tile.
+namespace {
+
+constexpr int kTbG = 32;  // Gaussians per block (MMA N)
+
+struct TbSmem {
+  uint8_t A[kTcMaxN * kTcPix * 2];  // dF^T, 128 KB for N = 512
+  uint8_t B[2][kTcPix * kTbG * 2];  // W, 8 KB per buffer
+  float2 uv[3][kTbG];  // record ring: block b uses slot b % 3
+  float4 co[3][kTbG];
+  uint32_t gid[3][kTbG];
+  int nz[3][kTbG];
+  unsigned long long mbar[2];
+  uint32_t tmem;
+  int maxlast;
+};
+
+struct TcBwdParams {
+  CamF cam;
+  const int2* ranges;
+  const uint32_t* gids;
+  const float2* uv;
+  const float4* co;
+  const int* last_idx;
+  const float* g_feat;  // [H, W, N]
+  int N;
+  int tmem_cols;
+  float* d_feats;  // [P, N]
+  int32_t* status;
+};
+
+// Records of Gaussian block b (threads 0..31): fetched into registers, stored
+// into ring slot b % 3 later, so the global latency overlaps other work.
+struct TbRecord {
+  float2 uv;
+  float4 co;
+  uint32_t gid;
+};
+
+__device__ __forceinline__ TbRecord tb_fetch(const TcBwdParams& p, int b, int2 rg, int maxlast) {
+  TbRecord r{make_float2(0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), 0xFFFFFFFFu};
+  const int pos = rg.x + b * kTbG + (int)threadIdx.x;
+  if (pos < rg.x + maxlast) {
+    r.gid = p.gids[pos];
+    r.uv = p.uv[r.gid];
+    r.co = p.co[r.gid];
+  }
+  return r;
+}
+
+__device__ __forceinline__ void tb_store(TbSmem& S, int slot, const TbRecord& r) {
+  const int tid = threadIdx.x;
+  S.uv[slot][tid] = r.uv;
+  S.co[slot][tid] = r.co;
+  S.gid[slot][tid] = r.gid;
+  S.nz[slot][tid] = 0;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBwdParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  TbSmem& S = *reinterpret_cast<TbSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = tid >> 2, q = tid & 3;
+  const int tile = blockIdx.x >> 1, half = blockIdx.x & 1;
+  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
+  const int px = tx * kTile + (m & 15);
+  const int py = ty * kTile + half * 8 + (m >> 4);
+  const bool inside = px < p.cam.W && py < p.cam.H;
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const int2 rg = p.ranges[tile];
+  const int last = inside ? p.last_idx[(size_t)py * p.cam.W + px] : 0;
+  const int nmb = p.N / 128;         // M-blocks of 128 channels
+  const uint32_t dcols = (uint32_t)(nmb * kTbG);  // tensor-memory columns per D buffer
+
+  if (tid == 0) S.maxlast = 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(p.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // dF^T for this half tile: thread (m, q) converts channels [qN/4, (q+1)N/4) of pixel m
+  {
+    const int cq = p.N / 4;
+    const float* src = p.g_feat + ((size_t)py * p.cam.W + px) * p.N + q * cq;
+    for (int c4 = 0; c4 < cq; c4 += 4) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (inside) v = *reinterpret_cast<const float4*>(src + c4);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = q * cq + c4 + e;
+        *reinterpret_cast<__nv_bfloat16*>(S.A + (c >> 3) * 2048 + (m >> 3) * 128 + (c & 7) * 16 + (m & 7) * 2) =
+            __float2bfloat16_rn(vv[e]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (q == 0 && last > 0) atomicMax(&S.maxlast, last);
+  __syncthreads();
+  const int maxlast = S.maxlast;
+  const uint32_t tmem = S.tmem;
+  const int nb = (maxlast + kTbG - 1) / kTbG;
+  bool ok = true;
+  if (nb > 0 && tid < kTbG) tb_store(S, 0, tb_fetch(p, 0, rg, maxlast));
+  __syncthreads();
+
+  float T = 1.f;
+  int last_issued = -1;
+  auto epilogue = [&](int b) -> bool {
+    const int buf = b & 1, slot = b % 3;
+    const bool w_ok =
+        __syncthreads_and(mbar_wait(smem_u32(&S.mbar[buf]), (uint32_t)((b >> 1) & 1))) != 0;
+    if (!w_ok) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // warp w: M-block w/4 (if any), tensor-memory lanes 32*(w%4)..: channel c
+    const int mb = warp >> 2;
+    if (mb < nmb) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)buf * dcols + (uint32_t)(mb * kTbG), v);
+      const int c = mb * 128 + 32 * (warp & 3) + lane;
+#pragma unroll 4
+      for (int j = 0; j < kTbG; ++j) {
+        if (!S.nz[slot][j]) continue;
+        const uint32_t g = S.gid[slot][j];
+        atomicAdd(p.d_feats + (size_t)g * p.N + c, v[j]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    return true;
+  };
+
+  for (int b = 0; b < nb && ok; ++b) {
+    const int buf = b & 1, slot = b % 3;
+    // next block's records (slot (b+1)%3 was last read by the epilogue of
+    // block b-2, which finished in the previous iteration)
+    TbRecord nxt;
+    const bool fetch = b + 1 < nb && tid < kTbG;
+    if (fetch) nxt = tb_fetch(p, b + 1, rg, maxlast);
+    // weights of my 8 Gaussians (one 16-byte row of B)
+    float a[8];
+    float prod = 1.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a[j] = 0.f;
+      const int k = 8 * q + j;
+      PairAlpha pa;
+      if (b * kTbG + k < last && pair_alpha(S.co[slot][k], S.uv[slot][k].x - pxc, S.uv[slot][k].y - pyc, pa)) {
+        a[j] = pa.alpha;
+        prod = __fmul_rn(prod, __fsub_rn(1.f, pa.alpha));
+      }
+    }
+    float incl = prod;
+    float y = __shfl_up_sync(0xffffffffu, incl, 1, 4);
+    if (q >= 1) incl = __fmul_rn(incl, y);
+    y = __shfl_up_sync(0xffffffffu, incl, 2, 4);
+    if (q >= 2) incl = __fmul_rn(incl, y);
+    float excl = __shfl_up_sync(0xffffffffu, incl, 1, 4);
+    if (q == 0) excl = 1.f;
+    const float total = __shfl_sync(0xffffffffu, incl, 3, 4);
+    float Tj = __fmul_rn(T, excl);
+    uint32_t packed[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const float w0 = __fmul_rn(a[j], Tj);
+      if (a[j] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j]));
+      const float w1 = __fmul_rn(a[j + 1], Tj);
+      if (a[j + 1] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j + 1]));
+      if (w0 != 0.f) S.nz[slot][8 * q + j] = 1;
+      if (w1 != 0.f) S.nz[slot][8 * q + j + 1] = 1;
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(w0, w1);
+      packed[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    T = __fmul_rn(T, total);
+    *reinterpret_cast<uint4*>(S.B[buf] + q * 128 + (m >> 3) * 512 + (m & 7) * 16) =
+        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_u32(S.A), b0 = smem_u32(S.B[buf]);
+      const uint32_t idesc = idesc_bf16(kTcPix, kTbG, 1);
+      for (int mb = 0; mb < nmb; ++mb) {
+#pragma unroll
+        for (int k16 = 0; k16 < kTcPix / 16; ++k16) {
+          const uint64_t ad = smem_desc(a0 + (uint32_t)mb * 16u * 2048u + (uint32_t)k16 * 256u, 128, 2048);
+          const uint64_t bd = smem_desc(b0 + (uint32_t)k16 * 1024u, 512, 128);
+          const uint32_t acc = k16 > 0 ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                  tmem + (uint32_t)buf * dcols + (uint32_t)(mb * kTbG)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.mbar[buf])));
+    }
+    last_issued = b;
+    if (fetch) tb_store(S, (b + 1) % 3, nxt);
+    if (b >= 1) ok = epilogue(b - 1);
+    __syncthreads();
+  }
+  if (ok && nb > 0) ok = epilogue(nb - 1);
+  if (!ok) {
+    if (tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
+    if (last_issued >= 0) mbar_wait(smem_u32(&S.mbar[last_issued & 1]), (uint32_t)((last_issued >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+}
+
+}  // namespace
+
+gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+                                    const float* co, const int32_t* last_idx, const float* g_feat, int N,
+                                    float* d_feats, int32_t* status, cudaStream_t st) {
+  if (N <= 0 || N % 128 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
+  TcBwdParams p;
+  p.cam = cam;
+  p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.gids = gids;
+  p.uv = reinterpret_cast<const float2*>(uv);
+  p.co = reinterpret_cast<const float4*>(co);
+  p.last_idx = last_idx;
+  p.g_feat = g_feat;
+  p.N = N;
+  int cols = 32;
+  while (cols < 2 * (N / 128) * kTbG) cols *= 2;
+  p.tmem_cols = cols;
+  p.d_feats = d_feats;
+  p.status = status;
+  const size_t smem = sizeof(TbSmem) + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_render_feat_tc_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return GS_ERR_CUDA;
+    attr_set = true;
+  }
+  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2);
+  GS_TRACE("k_render_feat_tc_bwd", st);
+  k_render_feat_tc_bwd<<<blocks, kTcThreads, smem, st>>>(p);
+  return last_launch_status();
+}
+
 }  // namespace gsff

@@ -90,3 +90,43 @@ def test_tc_rejects_unsupported_shapes(gs, sg):
     sc = sg.frustum_scene(5, 50, cam, 48)
     with pytest.raises(gs.GsffError):
         _render(gs, cam, sc, gs.GS_FEAT_ON | gs.GS_FEAT_TENSOR_CORE)
+
+
+def test_tc_feature_gradient_within_bound(gs, ora, sg):
+    """Decoupled feature gradient on tcgen05: w and dL/dF are rounded to bf16
+    (unit roundoff 2^-9 each), so per Gaussian and channel
+        |df_tc - df| <= (2^-7 + 1e-5) sum_p w(p) |dL/dF(p)| + 1e-7;
+    the geometry gradients equal the fp32 path's (tolerance 1e-5)."""
+    N = 256
+    cam = sg.identity_camera(96, 64, 70.0).as_f32()
+    sc = sg.frustum_scene(31, 1200, cam, N)
+    sc.feats = (sc.feats / np.linalg.norm(sc.feats, axis=1, keepdims=True)).astype(np.float32)
+    f_exact = _bf16_exact(sc.feats)
+    cot = sg.random_linear_functional(32, cam.height, cam.width, N)
+    g_rgb, g_d, g_a, g_f = (_t(x) for x in cot)
+    g_f_hwc = g_f.permute(1, 2, 0).contiguous()
+    means, scales, quats, opac, cols = (_t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
+    feats = _t(sc.feats, torch.bfloat16)
+    out = {}
+    for name, flags in (("tc", gs.GS_FEAT_ON | gs.GS_FEAT_TENSOR_CORE), ("plain", gs.GS_FEAT_ON)):
+        proj = gs.project(cam, means, scales, quats, opac)
+        srt = gs.bin_sort(cam, proj, max(int(proj["n_instances"].item()), 1))
+        fw = gs.render_fwd(cam, proj, srt, cols, feats, flags=flags, layout=gs.GS_LAYOUT_HWC, status=srt["status"])
+        gr = gs.render_bwd(cam, means, scales, quats, cols, feats, proj, srt, fw, g_rgb, g_d, g_a, g_f_hwc,
+                           flags=flags, layout=gs.GS_LAYOUT_HWC, status=srt["status"])
+        torch.cuda.synchronize()
+        assert int(srt["status"].item()) == 0
+        out[name] = {k: v.cpu().numpy() for k, v in gr.items()}
+    pr = ora.project_b32(cam, sc.means, sc.scales, sc.quats, sc.opacity)
+    ranges, gids = ora.bin_lists(cam, pr["rect"], pr["depth"])
+    c64 = tuple(x.astype(np.float64) for x in cot)
+    rb = ora.render_bwd(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity, sc.colors, pr["depth"], f_exact, *c64)
+    ra = ora.render_bwd(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity, sc.colors, pr["depth"], f_exact,
+                        None, None, None, np.abs(c64[3]))
+    err = np.abs(out["tc"]["feats"] - rb["d_feats"])
+    bound = (2.0 ** -7 + 1e-5) * ra["d_feats"] + 1e-7
+    assert (err <= bound).all(), float((err / bound).max())
+    assert (err / bound).max() > 0.02
+    for k in ("means", "scales", "quats", "opacity", "colors", "pose"):
+        a, b = out["tc"][k].ravel(), out["plain"][k].ravel()
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), k
