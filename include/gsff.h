@@ -211,6 +211,48 @@ gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, flo
                           float* grad, float* loss_sum, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Per-pixel feature decoder o(.) of Eq. 9, read as a 1x1 lift of a rendered
+ * latent map (a din-channel render of per-Gaussian latents):
+ *     y = W2^T gelu(W1^T z + b1) + b2,   gelu(x) = x (1 + erf(x / sqrt 2)) / 2.
+ * W1 [din, dh] and W2 [dh, dout] are row-major fp32 arrays whose values are
+ * bf16-representable (the bf16 weights; gs_adam_step can write that
+ * rounding), b1 [dh], b2 [dout] fp32; accumulation is fp32.
+ * Limits: din <= 64, dh <= 1024, dout <= 4096; fewer than 2^31 pixels.
+ */
+typedef struct gs_decoder {
+  int32_t din, dh, dout;
+  const float* W1;
+  const float* b1;
+  const float* W2;
+  const float* b2;
+} gs_decoder;
+
+/* Workspace for gs_decoder_fwd over n pixels (training = 0) or for
+ * gs_decoder_train with n samples (training = 1). */
+size_t gs_decoder_workspace_bytes(const gs_decoder* dec, int64_t n, int32_t training);
+
+/* z [npix, din] -> y [npix, dout]. */
+gs_status gs_decoder_fwd(const gs_decoder* dec, int64_t npix, const float* z, float* y, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/* One training evaluation on nsample pixels drawn with replacement from the
+ * npix pixels of z_map [npix, din] / target [npix, dout]: sample s is pixel
+ * splitmix64(seed + (s + 1) * 0x9E3779B97F4A7C15) mod npix. Loss
+ * L = loss_scale * sum_s sum_c (y - target)^2 is added to *loss_sum (device,
+ * may be NULL); its gradients are ACCUMULATED into dW1, db1, dW2, db2 and,
+ * at the sampled pixels, into dz_map [npix, din] (may be NULL). */
+gs_status gs_decoder_train(const gs_decoder* dec, int64_t nsample, int64_t npix, uint64_t seed,
+                           const float* z_map, const float* target, float loss_scale, void* workspace,
+                           size_t workspace_bytes, float* dW1, float* db1, float* dW2, float* db2,
+                           float* dz_map, float* loss_sum, void* stream);
+
+/* Adam (Kingma and Ba 2015) with bias correction on n parameters at step
+ * `step` (>= 1); param_bf16 (may be NULL) receives the updated parameters
+ * rounded to bf16 (stored as fp32), the copy the decoder multiplies with. */
+gs_status gs_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr,
+                       float beta1, float beta2, float eps, int32_t step, float* param_bf16, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Tracing: when enabled, every kernel the library launches is bracketed by
  * CUDA events on its stream (up to `capacity` launches, then recording stops).
  * gs_trace_get synchronizes on the i-th end event and returns the kernel's

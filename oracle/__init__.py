@@ -198,3 +198,28 @@ def linear_loss(fw, g_rgb, g_depth, g_alpha, g_feat):
     if g_feat is not None and fw["feat"].shape[0] > 0:
         L += float((g_feat * fw["feat"]).sum())
     return L
+
+
+# ---- per-pixel decoder o(.) (Eq. 9) ------------------------------------------
+
+def decoder_fwd(z, W1, b1, W2, b2):
+    z = _f64(z)
+    n, din = z.shape
+    dh, dout = W2.shape
+    y = np.zeros((n, dout))
+    lib().ora_decoder_fwd(ctypes.c_int(n), ctypes.c_int(din), ctypes.c_int(dh), ctypes.c_int(dout), _p(z),
+                          _p(_f64(W1)), _p(_f64(b1)), _p(_f64(W2)), _p(_f64(b2)), _p(y))
+    return y
+
+
+def decoder_bwd(z, W1, b1, W2, g):
+    """Gradients of sum(g * y) w.r.t. (W1, b1, W2, b2, z)."""
+    z = _f64(z)
+    n, din = z.shape
+    dh, dout = W2.shape
+    out = dict(W1=np.zeros((din, dh)), b1=np.zeros(dh), W2=np.zeros((dh, dout)), b2=np.zeros(dout),
+               z=np.zeros((n, din)))
+    lib().ora_decoder_bwd(ctypes.c_int(n), ctypes.c_int(din), ctypes.c_int(dh), ctypes.c_int(dout), _p(z),
+                          _p(_f64(W1)), _p(_f64(b1)), _p(_f64(W2)), _p(_f64(g)), _p(out["W1"]), _p(out["b1"]),
+                          _p(out["W2"]), _p(out["b2"]), _p(out["z"]))
+    return out

@@ -743,3 +743,65 @@ void ora_project_bwd_f64(const double* cam, int P, const double* means, const do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Per-pixel feature decoder o(.) of Eq. 9, read as a 1x1 lift of the latent
+// feature map: y = W2^T gelu(W1^T z + b1) + b2 with the exact (erf) GELU,
+// gelu(x) = x (1 + erf(x / sqrt 2)) / 2. Shapes: z [n, din], W1 [din, dh],
+// b1 [dh], W2 [dh, dout], b2 [dout], y [n, dout]; all double.
+extern "C" {
+
+void ora_decoder_fwd(int n, int din, int dh, int dout, const double* z, const double* W1, const double* b1,
+                     const double* W2, const double* b2, double* y) {
+#pragma omp parallel for schedule(static)
+  for (int p = 0; p < n; ++p) {
+    std::vector<double> h(dh);
+    for (int j = 0; j < dh; ++j) {
+      double a = b1[j];
+      for (int i = 0; i < din; ++i) a += z[(size_t)p * din + i] * W1[(size_t)i * dh + j];
+      h[j] = 0.5 * a * (1.0 + std::erf(a / std::sqrt(2.0)));
+    }
+    for (int c = 0; c < dout; ++c) {
+      double a = b2[c];
+      for (int j = 0; j < dh; ++j) a += h[j] * W2[(size_t)j * dout + c];
+      y[(size_t)p * dout + c] = a;
+    }
+  }
+}
+
+// Gradients of L = sum_p sum_c g[p, c] y[p, c] (g given) with respect to
+// W1, b1, W2, b2 (accumulated) and z (written). gelu'(x) = Phi(x) + x phi(x).
+void ora_decoder_bwd(int n, int din, int dh, int dout, const double* z, const double* W1, const double* b1,
+                     const double* W2, const double* g, double* dW1, double* db1, double* dW2, double* db2,
+                     double* dz) {
+  const double inv_sqrt2 = 1.0 / std::sqrt(2.0), inv_sqrt2pi = 1.0 / std::sqrt(2.0 * M_PI);
+  for (int p = 0; p < n; ++p) {
+    std::vector<double> a(dh), h(dh), dhv(dh, 0.0);
+    for (int j = 0; j < dh; ++j) {
+      double s = b1[j];
+      for (int i = 0; i < din; ++i) s += z[(size_t)p * din + i] * W1[(size_t)i * dh + j];
+      a[j] = s;
+      h[j] = 0.5 * s * (1.0 + std::erf(s * inv_sqrt2));
+    }
+    for (int c = 0; c < dout; ++c) {
+      const double gc = g[(size_t)p * dout + c];
+      db2[c] += gc;
+      for (int j = 0; j < dh; ++j) {
+        dW2[(size_t)j * dout + c] += h[j] * gc;
+        dhv[j] += W2[(size_t)j * dout + c] * gc;
+      }
+    }
+    for (int i = 0; i < din; ++i) dz[(size_t)p * din + i] = 0.0;
+    for (int j = 0; j < dh; ++j) {
+      const double d = 0.5 * (1.0 + std::erf(a[j] * inv_sqrt2)) + a[j] * inv_sqrt2pi * std::exp(-0.5 * a[j] * a[j]);
+      const double da = dhv[j] * d;
+      db1[j] += da;
+      for (int i = 0; i < din; ++i) {
+        dW1[(size_t)i * dh + j] += z[(size_t)p * din + i] * da;
+        dz[(size_t)p * din + i] += W1[(size_t)i * dh + j] * da;
+      }
+    }
+  }
+}
+
+}  // extern "C"

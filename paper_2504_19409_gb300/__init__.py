@@ -34,11 +34,17 @@ TILE = 16
 EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_render_fwd",
            "gs_render_bwd_workspace_bytes", "gs_render_bwd", "gs_l1_loss_grad", "gs_trace_enable",
            "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
-           "gs_bin_sort_static")
+           "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
+           "gs_adam_step")
 
 
 class GsffError(RuntimeError):
     pass
+
+
+class GsDecoder(ctypes.Structure):
+    _fields_ = [("din", ctypes.c_int32), ("dh", ctypes.c_int32), ("dout", ctypes.c_int32),
+                ("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("W2", ctypes.c_void_p), ("b2", ctypes.c_void_p)]
 
 
 class GsCamera(ctypes.Structure):
@@ -100,6 +106,15 @@ def lib():
     L.gs_trace_count.restype = _i32
     L.gs_trace_get.argtypes = [_i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_f32)]
     L.gs_trace_get.restype = ctypes.c_int
+    dec_p = ctypes.POINTER(GsDecoder)
+    L.gs_decoder_workspace_bytes.argtypes = [dec_p, _i64, _i32]
+    L.gs_decoder_workspace_bytes.restype = _sz
+    L.gs_decoder_fwd.argtypes = [dec_p, _i64, _vp, _vp, _vp, _sz, _vp]
+    L.gs_decoder_fwd.restype = ctypes.c_int
+    L.gs_decoder_train.argtypes = [dec_p, _i64, _i64, ctypes.c_uint64, _vp, _vp, _f32, _vp, _sz] + [_vp] * 7
+    L.gs_decoder_train.restype = ctypes.c_int
+    L.gs_adam_step.argtypes = [_i64, _vp, _vp, _vp, _vp, _f32, _f32, _f32, _f32, _i32, _vp, _vp]
+    L.gs_adam_step.restype = ctypes.c_int
     L.gs_status_string.argtypes = [ctypes.c_int]
     L.gs_status_string.restype = ctypes.c_char_p
     L.gs_version.restype = _i32

@@ -195,12 +195,43 @@ def room_scene(seed: int, P: int, N: int, jitter: float = 0.02, log_scale_mu: fl
     colors = rng.uniform(3 * P).reshape(P, 3)
     if N == 0 or feat_kind == "none":
         feats = np.zeros((P, N))
+    elif feat_kind == "prototypes":
+        feats = prototype_features(seed + 7919, means, N)
     else:
         feats = rng.normal(N * P).reshape(P, N)
         if feat_kind == "unit":
             feats = feats / np.linalg.norm(feats, axis=1, keepdims=True)
     return Scene(means.astype(np.float32), scales.astype(np.float32), quats.astype(np.float32),
                  opacity.astype(np.float32), colors.astype(np.float32), feats.astype(np.float32))
+
+
+def prototype_features(seed: int, means: np.ndarray, N: int, n_proto: int = 32, patch: float = 0.75,
+                       noise: float = 0.05) -> np.ndarray:
+    """Label-structured features: the room surfaces are cut into `patch`-metre
+    cells, each cell draws one of `n_proto` unit prototype vectors, and every
+    Gaussian carries its cell's prototype plus isotropic noise of expected
+    norm `noise` (N(0, noise^2 / N) per channel), renormalised: features that
+    come from a small label set, as the paper's GT-label and text-query
+    supervision does (Sec. 3.3)."""
+    rng = Rng(seed)
+    protos = rng.normal(n_proto * N).reshape(n_proto, N)
+    protos /= np.linalg.norm(protos, axis=1, keepdims=True)
+    cell = np.floor(np.asarray(means, np.float64) / patch).astype(np.int64)
+    h = (cell[:, 0] * 73856093) ^ (cell[:, 1] * 19349663) ^ (cell[:, 2] * 83492791)
+    labels = np.mod(h, n_proto)
+    f = protos[labels] + (noise / math.sqrt(N)) * rng.normal(means.shape[0] * N).reshape(-1, N)
+    return f / np.linalg.norm(f, axis=1, keepdims=True)
+
+
+def pca_basis(feats: np.ndarray, k: int):
+    """Mean and top-k principal directions of per-Gaussian features (the
+    linear rank-k encode/decode the learned decoder is compared with)."""
+    f = np.asarray(feats, np.float64)
+    mu = f.mean(0)
+    c = np.cov((f - mu).T)
+    w, v = np.linalg.eigh(c)
+    U = v[:, np.argsort(w)[::-1][:k]]
+    return mu, U
 
 
 def look_camera(width: int, height: int, f: float, centre, yaw: float, pitch: float) -> Camera:
