@@ -342,6 +342,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="slam", choices=["slam", "wide", "decoder"],
+                    help="slam: the headline SLAM-frame workload (N=16); wide: 500k Gaussians with 512 bf16 feature "
+                         "channels, tensor-core vs plain fp32; decoder: latent render + learned decoder vs both")
+    ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--profile", action="store_true",
                     help="setup, warm-up and --steps plain frames only (no timing, no JSON); for profiler captures")
     args = ap.parse_args()
@@ -354,6 +358,11 @@ def main():
         if rank != 0:
             return 0
         return run_reference(args)
+
+    if args.workload != "slam":
+        if rank != 0:
+            return 0
+        return run_forms(args)
 
     import torch
     if world > 1:
@@ -445,6 +454,220 @@ def run_reference(args):
             "config": config(1), "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+    return 0
+
+
+# ---- wide-feature and learned-decoder forms ---------------------------------------------
+
+P_WIDE, N_WIDE = 500_000, 512
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _time_frames(fn, frames, flush, stream, trace=False):
+    import torch
+    import paper_2504_19409_gb300 as g
+    if trace:
+        g.trace_enable(256 * len(frames) + 64)
+    ms = []
+    torch.cuda.synchronize()
+    for i, k in enumerate(frames):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(k)
+        b.record(stream)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    out = [a.elapsed_time(b) for a, b in ms]
+    per = {}
+    if trace:
+        for name, t in g.trace_read():
+            per[name] = per.get(name, 0.0) + t / len(frames)
+        g.trace_enable(0)
+    return out, per
+
+
+def _tc_exec_flops(last_idx, W, H, N):
+    """Tensor-core flops one forward executes: per half tile 2 * 128 * N per
+    Gaussian of its K-steps (ceil(max last_idx / 32) steps of 32)."""
+    import numpy as np
+    li = last_idx.cpu().numpy()
+    ty, tx = (H + 15) // 16, (W + 15) // 16
+    pad = np.zeros((ty * 16, tx * 16), np.int64)
+    pad[:H, :W] = li
+    halves = pad.reshape(ty, 2, 8, tx, 16).max(axis=(2, 4))
+    ksteps = (halves + 31) // 32
+    return float(2 * 128 * N * 32 * ksteps.sum())
+
+
+def run_forms(args):
+    import numpy as np
+    import torch
+    import paper_2504_19409_gb300 as g
+    import paper_2504_19409_gb300.decoder as dm
+    from paper_2504_19409_gb300 import scenegen as sg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peaks = _peaks()
+    kind = "unit" if args.workload == "wide" else "prototypes"
+    sc = sg.room_scene(6, P_WIDE, N_WIDE, feat_kind=kind)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    scene = tuple(t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
+    feats_bf = t(sc.feats).to(torch.bfloat16)
+    frames = [k % N_FRAMES for k in range(args.warmup + args.steps)]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    HW = WIDTH * HEIGHT
+    tc = g.Rasterizer(P_WIDE, WIDTH, HEIGHT, N=N_WIDE, layout=g.GS_LAYOUT_HWC,
+                      flags=g.GS_FEAT_ON | g.GS_FEAT_TENSOR_CORE, device=dev)
+    plain = g.Rasterizer(P_WIDE, WIDTH, HEIGHT, N=N_WIDE, layout=g.GS_LAYOUT_HWC, device=dev)
+    for k in sorted(set(frames)):
+        for r in (tc, plain):
+            r.ensure_capacity(frame_camera(k), *scene[:4])
+    blends, instances = {}, {}
+    for k in sorted(set(frames)):
+        fw = plain.forward(frame_camera(k), *scene, feats_bf)
+        blends[k] = int(fw["n_contrib"].sum().item())
+        instances[k] = int(plain.sort["n_instances"].item())
+    timed = frames[args.warmup:]
+    tot_blends = sum(blends[k] for k in timed)
+    result = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+              "config": {"workload": f"{args.workload}_room500k_1200x680_N512", "gaussians": P_WIDE,
+                         "image": [WIDTH, HEIGHT], "feature_channels": N_WIDE, "features": kind + " (bf16)",
+                         "blends_per_frame": float(np.mean([blends[k] for k in timed])),
+                         "instances_per_frame": float(np.mean([instances[k] for k in timed])),
+                         "l2": "flushed between timed steps (512 MB write)"}}
+
+    if args.workload == "wide":
+        gen = torch.Generator(device=dev).manual_seed(4)
+        g_rgb = torch.randn(3, HEIGHT, WIDTH, device=dev, generator=gen)
+        g_d = torch.randn(HEIGHT, WIDTH, device=dev, generator=gen)
+        g_f = torch.randn(HEIGHT, WIDTH, N_WIDE, device=dev, generator=gen) * (1.0 / N_WIDE)
+
+        def fwd_bwd(r):
+            def f(k):
+                cam = frame_camera(k)
+                r.forward(cam, *scene, feats_bf)
+                r.backward(cam, scene[0], scene[1], scene[2], scene[4], feats_bf, g_rgb, g_d, None, g_f)
+            return f
+
+        for r in (tc, plain):
+            for k in frames[:args.warmup]:
+                fwd_bwd(r)(k)
+        forms = {}
+        for name, r in (("tensor_core", tc), ("plain_fp32", plain)):
+            ms, _ = _time_frames(fwd_bwd(r), timed, flush, stream)
+            _, per = _time_frames(fwd_bwd(r), timed[:3], flush, stream, trace=True)
+            r.check_status()
+            forms[name] = {"ms_per_frame": float(np.mean(ms)), "blends_per_s": tot_blends / (sum(ms) / 1e3),
+                           "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
+        # feature error of the tensor-core form vs the plain fp32 form, and the bound's usage
+        cam = frame_camera(timed[0])
+        F_tc = tc.forward(cam, *scene, feats_bf)["feat"].clone()
+        F_pl = plain.forward(cam, *scene, feats_bf)["feat"].clone()
+        li = plain.fwd["last_idx"].clone()
+        F_abs = plain.forward(cam, *scene, feats_bf.float().abs().contiguous())["feat"]
+        err = (F_tc - F_pl).abs()
+        bound = (2.0 ** -8 + 1e-5) * F_abs + 1e-7
+        rel = float(torch.linalg.norm(F_tc - F_pl) / torch.linalg.norm(F_pl))
+        flops = _tc_exec_flops(li, WIDTH, HEIGHT, N_WIDE)
+        k_ms = forms["tensor_core"]["kernel_ms_per_frame"].get("k_render_feat_tc", float("nan"))
+        bf16_peak = peaks.get("bf16_tflops", 1900.0)
+        result.update({
+            "value": forms["tensor_core"]["blends_per_s"], "ms_per_step": forms["tensor_core"]["ms_per_frame"],
+            "dtype": "bf16 features, fp32 accumulation",
+            "forms": forms, "speedup_vs_plain": forms["plain_fp32"]["ms_per_frame"] / forms["tensor_core"]["ms_per_frame"],
+            "feature_error": {"rel_l2_vs_plain_fp32": rel, "max_err_over_bound": float((err / bound).max()),
+                              "bound": "(2^-8 + 1e-5) sum_i w_i |f_i| + 1e-7 per pixel and channel"},
+            "roofline": {"bound": "tensor", "kernel": "k_render_feat_tc", "achieved": flops / (k_ms * 1e-3) / 1e12,
+                         "peak": bf16_peak, "unit": "TFLOP/s", "frac": flops / (k_ms * 1e-3) / 1e12 / bf16_peak,
+                         "flops": "executed tcgen05 flops (dense W including zero weights)", "traffic": None,
+                         "feature_map_write_GBps": HW * N_WIDE * 4 / (k_ms * 1e-3) / 1e9,
+                         "hbm_peak_GBps": peaks.get("hbm_gbs", 6800.0)},
+        })
+        print(json.dumps(result))
+        return 0
+
+    # ---- learned decoder -------------------------------------------------------------------
+    mu, U = sg.pca_basis(sc.feats, 16)
+    lat0 = ((sc.feats - mu) @ U).astype(np.float32)
+    n_train, n_held = 200, 50
+    train_cams = [sg.room_trajectory(k * N_FRAMES / n_train, N_FRAMES, WIDTH, HEIGHT, FOCAL).as_f32()
+                  for k in range(n_train)]
+    held_cams = [sg.room_trajectory((k + 0.5) * N_FRAMES / n_held, N_FRAMES, WIDTH, HEIGHT, FOCAL).as_f32()
+                 for k in range(n_held)]
+    dec = dm.Decoder(seed=11, device=dev)
+    trn = dm.LatentFieldTrainer(scene, lat0, train_cams[0], dec, device=dev)
+    trn.ensure_capacity(train_cams + held_cams)
+    for c in train_cams + held_cams:
+        tc.ensure_capacity(c, *scene[:4])
+        plain.ensure_capacity(c, *scene[:4])
+    t0 = time.perf_counter()
+    for step in range(args.train_steps):
+        c = train_cams[step % n_train]
+        target = tc.forward(c, *scene, feats_bf)["feat"].reshape(HW, N_WIDE)
+        trn.step(c, target, 65536, 1000 + step, lr_dec=3e-3, lr_lat=5e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # held-out evaluation against the plain fp32 512-channel render
+    mu_t, U_t = t(mu.astype(np.float32)), t(U.astype(np.float32))
+    res = {"decoder": [], "pca16": []}
+    for c in held_cams:
+        fw = plain.forward(c, *scene, feats_bf)
+        ref = fw["feat"].reshape(HW, N_WIDE)
+        mask = fw["alpha"].reshape(HW) > 0.5
+        z = trn.render_latents(c).contiguous()
+        res["decoder"].append(dm.feature_error(dec.forward_tc(z), ref, mask))
+        alpha = fw["alpha"].reshape(HW, 1)
+        res["pca16"].append(dm.feature_error(alpha * mu_t[None, :] + z @ U_t.T, ref, mask))
+    quality = {k: {"rel_l2": float(np.mean([r[0] for r in v])), "cosine": float(np.mean([r[1] for r in v]))}
+               for k, v in res.items()}
+    # inference frame timing: plain 512, tensor-core 512, latent + decoder
+    lat_ras = trn.ras
+    z_out = torch.empty(HW, 16, device=dev)
+    y_out = torch.empty(HW, N_WIDE, device=dev)
+
+    def inf_plain(k):
+        plain.forward(frame_camera(k), *scene, feats_bf)
+
+    def inf_tc(k):
+        tc.forward(frame_camera(k), *scene, feats_bf)
+
+    def inf_dec(k):
+        fw = lat_ras.forward(frame_camera(k), *scene, trn.lat)
+        dec.forward_tc(fw["feat"].reshape(HW, 16), out=y_out)
+
+    forms = {}
+    for name, fn in (("plain_fp32", inf_plain), ("tensor_core", inf_tc), ("latent16_decoder", inf_dec)):
+        for k in frames[:args.warmup]:
+            fn(k)
+        ms, _ = _time_frames(fn, timed, flush, stream)
+        _, per = _time_frames(fn, timed[:3], flush, stream, trace=True)
+        forms[name] = {"ms_per_frame": float(np.mean(ms)), "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
+    dk = forms["latent16_decoder"]["kernel_ms_per_frame"].get("k_decoder_fwd_tc", float("nan"))
+    flops = 2.0 * HW * (16 * 128 + 128 * 512)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    result.update({
+        "value": tot_blends / (sum([forms["latent16_decoder"]["ms_per_frame"]] * len(timed)) / 1e3),
+        "ms_per_step": forms["latent16_decoder"]["ms_per_frame"], "dtype": "latent fp32, decoder bf16 x bf16 -> fp32",
+        "forms_inference": forms,
+        "speedup_vs_plain": forms["plain_fp32"]["ms_per_frame"] / forms["latent16_decoder"]["ms_per_frame"],
+        "speedup_vs_tensor_core": forms["tensor_core"]["ms_per_frame"] / forms["latent16_decoder"]["ms_per_frame"],
+        "held_out_quality_vs_plain_512": quality, "held_out_poses": n_held, "train_poses": n_train,
+        "train_steps": args.train_steps, "train_seconds": train_s, "train_samples_per_step": 65536,
+        "roofline": {"bound": "tensor", "kernel": "k_decoder_fwd_tc", "achieved": flops / (dk * 1e-3) / 1e12,
+                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": flops / (dk * 1e-3) / 1e12 / bf16_peak,
+                     "output_write_GBps": HW * N_WIDE * 4 / (dk * 1e-3) / 1e9, "traffic": None},
+    })
+    print(json.dumps(result))
     return 0
 
 

@@ -246,6 +246,14 @@ gs_status gs_decoder_train(const gs_decoder* dec, int64_t nsample, int64_t npix,
                            size_t workspace_bytes, float* dW1, float* db1, float* dW2, float* db2,
                            float* dz_map, float* loss_sum, void* stream);
 
+/* The decoder forward on tcgen05 tensor cores for din = 16, dh = 128,
+ * dout = 512: z and W rounded to bf16, fp32 accumulation, the hidden layer
+ * rounded to bf16 after the exact GELU; y = D + b2 in fp32. No workspace.
+ * Device errors (a bounded wait that gave up) are OR-ed into *status
+ * (may be NULL). */
+gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, const float* z, float* y, int32_t* status,
+                            void* stream);
+
 /* Adam (Kingma and Ba 2015) with bias correction on n parameters at step
  * `step` (>= 1); param_bf16 (may be NULL) receives the updated parameters
  * rounded to bf16 (stored as fp32), the copy the decoder multiplies with. */

@@ -35,7 +35,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_render_bwd_workspace_bytes", "gs_render_bwd", "gs_l1_loss_grad", "gs_trace_enable",
            "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
-           "gs_adam_step")
+           "gs_adam_step", "gs_decoder_fwd_tc")
 
 
 class GsffError(RuntimeError):
@@ -113,6 +113,8 @@ def lib():
     L.gs_decoder_fwd.restype = ctypes.c_int
     L.gs_decoder_train.argtypes = [dec_p, _i64, _i64, ctypes.c_uint64, _vp, _vp, _f32, _vp, _sz] + [_vp] * 7
     L.gs_decoder_train.restype = ctypes.c_int
+    L.gs_decoder_fwd_tc.argtypes = [dec_p, _i64, _vp, _vp, _vp, _vp]
+    L.gs_decoder_fwd_tc.restype = ctypes.c_int
     L.gs_adam_step.argtypes = [_i64, _vp, _vp, _vp, _vp, _f32, _f32, _f32, _f32, _i32, _vp, _vp]
     L.gs_adam_step.restype = ctypes.c_int
     L.gs_status_string.argtypes = [ctypes.c_int]

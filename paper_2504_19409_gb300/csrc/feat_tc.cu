@@ -615,4 +615,220 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, cons
   return last_launch_status();
 }
 
+
+// ===========================================================================
+// Decoder inference on tcgen05 (the learned-decoder form): per 128-pixel tile
+//   D1 [128 x 128] = z [128 x 16] * W1 [16 x 128]        (one K=16 MMA)
+//   h = gelu(D1 + b1) -> bf16 -> shared memory (A operand of the next product)
+//   D2 [128 x 512] = h [128 x 128] * W2 [128 x 512]      (2 x 8 MMAs, N = 256)
+//   y = D2 + b2 -> fp32 rows [128 x 512]
+// Persistent CTAs (one per SM, 512 threads) keep W1 and W2 in shared memory
+// as bf16. Layouts (validated rule: LBO along K, SBO along M/N):
+//   A1 z  : (m/8)*256  + (k/8)*128 + (m%8)*16 + (k%8)*2   LBO 128, SBO 256
+//   B1 W1 : (n/8)*128  + (k/8)*2048 + (k%8)*16 + (n%8)*2  LBO 2048, SBO 128
+//   A2 h  : (m/8)*2048 + (k/8)*128 + (m%8)*16 + (k%8)*2   LBO 128, SBO 2048
+//   B2 W2 : (n/8)*128  + (k/8)*8192 + (k%8)*16 + (n%8)*2  LBO 8192, SBO 128
+// D1 occupies tensor-memory columns [0, 128) and is overwritten by D2
+// (columns [0, 512)) once read.
+namespace {
+
+struct DecSmem {
+  uint8_t W2[128 * 512 * 2];   // 128 KB
+  uint8_t H[128 * 128 * 2];    // 32 KB
+  uint8_t W1[16 * 128 * 2];    // 4 KB
+  uint8_t Z[128 * 16 * 2];     // 4 KB
+  float b1[128];
+  float b2[512];
+  unsigned long long mbar;
+  uint32_t tmem;
+};
+
+struct DecTcParams {
+  long long npix;
+  const float* z;
+  const float* W1;
+  const float* b1;
+  const float* W2;
+  const float* b2;
+  float* y;
+  int32_t* status;
+};
+
+__device__ __forceinline__ float gelu_exact(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  DecSmem& S = *reinterpret_cast<DecSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lg = warp & 3, cq = warp >> 2;  // tensor-memory lane group, column quarter
+  const int row = 32 * lg + lane;           // pixel row of the tile this thread reads back
+
+  // weights -> bf16 operands (once per CTA)
+  for (int e = tid; e < 128 * 512; e += 512) {
+    const int k = e / 512, n = e % 512;
+    *reinterpret_cast<__nv_bfloat16*>(S.W2 + (n >> 3) * 128 + (k >> 3) * 8192 + (k & 7) * 16 + (n & 7) * 2) =
+        __float2bfloat16_rn(p.W2[e]);
+  }
+  for (int e = tid; e < 16 * 128; e += 512) {
+    const int k = e / 128, n = e % 128;
+    *reinterpret_cast<__nv_bfloat16*>(S.W1 + (n >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 + (n & 7) * 2) =
+        __float2bfloat16_rn(p.W1[e]);
+  }
+  for (int e = tid; e < 128; e += 512) S.b1[e] = p.b1[e];
+  for (int e = tid; e < 512; e += 512) S.b2[e] = p.b2[e];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = S.tmem;
+  const uint32_t idesc1 = idesc_bf16(128, 128, 1), idesc2 = idesc_bf16(128, 256, 1);
+  const long long ntiles = (p.npix + 127) / 128;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const long long base = t * 128;
+    // z rows -> A1 (threads with cq < 2 write chunk cq of row `row`)
+    if (cq < 2) {
+      const long long pix = base + row;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      if (pix < p.npix) {
+        const float4 a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * cq);
+        const float4 b = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * cq + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      }
+      uint32_t pk[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      *reinterpret_cast<uint4*>(S.Z + (row >> 3) * 256 + cq * 128 + (row & 7) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      mma_bf16(tmem, smem_desc(smem_u32(S.Z), 128, 256), smem_desc(smem_u32(S.W1), 2048, 128), idesc1, 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.mbar)));
+    }
+    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar), phase)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    {
+      // hidden layer: columns [32 cq, 32 cq + 32) of D1 for pixel row `row`
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cq), v);
+      uint32_t pk[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float h0 = gelu_exact(v[2 * i] + S.b1[32 * cq + 2 * i]);
+        const float h1 = gelu_exact(v[2 * i + 1] + S.b1[32 * cq + 2 * i + 1]);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(h0, h1);
+        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(S.H + (row >> 3) * 2048 + (4 * cq + c) * 128 + (row & 7) * 16) =
+            make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_u32(S.H), b0 = smem_u32(S.W2);
+      for (int nh = 0; nh < 2; ++nh)
+#pragma unroll
+        for (int k16 = 0; k16 < 8; ++k16)
+          mma_bf16(tmem + (uint32_t)(256 * nh), smem_desc(a0 + k16 * 256, 128, 2048),
+                   smem_desc(b0 + (uint32_t)nh * 4096u + (uint32_t)k16 * 16384u, 8192, 128), idesc2,
+                   k16 > 0 ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.mbar)));
+    }
+    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar), phase)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    {
+      const long long pix = base + row;
+      float* dst = p.y + pix * 512;
+      for (int c = 128 * cq; c < 128 * cq + 128; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c, v);
+        if (pix < p.npix) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4*>(dst + c + i) =
+                make_float4(v[i] + S.b2[c + i], v[i + 1] + S.b2[c + i + 1], v[i + 2] + S.b2[c + i + 2],
+                            v[i + 3] + S.b2[c + i + 3]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (!ok && tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
+  if (!ok) mbar_wait(smem_u32(&S.mbar), phase ^ 1u);  // bounded drain of the outstanding commit
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+}  // namespace
 }  // namespace gsff
+
+extern "C" gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, const float* z, float* y, int32_t* status,
+                                       void* stream) {
+  using namespace gsff;
+  if (!dec || dec->din != 16 || dec->dh != 128 || dec->dout != 512 || !dec->W1 || !dec->b1 || !dec->W2 || !dec->b2)
+    return GS_ERR_UNSUPPORTED;
+  if (npix < 0 || (npix > 0 && (!z || !y)) || !aligned(z, 16) || !aligned(y, 16)) return GS_ERR_INVALID_ARG;
+  if (npix == 0) return GS_OK;
+  DecTcParams p;
+  p.npix = npix;
+  p.z = z;
+  p.W1 = dec->W1;
+  p.b1 = dec->b1;
+  p.W2 = dec->W2;
+  p.b2 = dec->b2;
+  p.y = y;
+  p.status = status;
+  const size_t smem = sizeof(DecSmem) + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_decoder_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GS_ERR_CUDA;
+    attr_set = true;
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (npix + 127) / 128;
+  const unsigned blocks = (unsigned)(ntiles < sms ? ntiles : sms);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GS_TRACE("k_decoder_fwd_tc", st);
+  k_decoder_fwd_tc<<<blocks, 512, smem, st>>>(p);
+  return last_launch_status();
+}

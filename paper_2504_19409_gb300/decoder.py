@@ -68,6 +68,15 @@ class Decoder:
                "gs_decoder_fwd")
         return y
 
+    def forward_tc(self, z: torch.Tensor, out: torch.Tensor | None = None, status=None, stream=None) -> torch.Tensor:
+        """The same map on tcgen05 (bf16 operands, fp32 accumulation)."""
+        n = z.shape[0]
+        y = out if out is not None else torch.empty(n, self.dout, device=self.device)
+        d = self.struct()
+        _check(lib().gs_decoder_fwd_tc(ctypes.byref(d), n, _ptr(z), _ptr(y), _ptr(status), _stream(stream)),
+               "gs_decoder_fwd_tc")
+        return y
+
     def zero_grad(self):
         for g in self.grads.values():
             g.zero_()

@@ -159,3 +159,30 @@ def test_trained_decoder_beats_linear_and_untrained(dec_mod):
     print(f"held-out rel-L2 / cosine: PCA-16 {pca}, untrained {untrained}, trained {trained}")
     assert trained[0] < 0.5 * pca[0], (trained, pca)
     assert trained[1] > 0.95 and trained[0] < untrained[0] and trained[1] > pca[1]
+
+
+def test_decoder_tensor_core_forward_within_bound(dec_mod, ora):
+    """gs_decoder_fwd_tc rounds z and the GELU output h to bf16 (weights are
+    bf16 already); against the oracle on the bf16-rounded z the remaining
+    difference is the rounding of h: |y_tc - y| <= 2^-8 |h| |W2| + 1e-6 per
+    output (2^-8 = twice bf16's unit roundoff)."""
+    from math import erf, sqrt
+    dec = dec_mod.Decoder(seed=13)
+    dec.params["b1"].normal_(0, 0.2)
+    dec.params["b2"].normal_(0, 0.2)
+    rng = np.random.default_rng(14)
+    n = 1000 + 37  # a ragged last tile
+    z = torch.tensor(rng.normal(size=(n, 16)).astype(np.float32), device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = dec.forward_tc(z, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    zb = z.to(torch.bfloat16).double().cpu().numpy()
+    W1, b1, W2, b2 = _np(dec.work["W1"]), _np(dec.params["b1"]), _np(dec.work["W2"]), _np(dec.params["b2"])
+    ref = ora.decoder_fwd(zb, W1, b1, W2, b2)
+    pre = zb @ W1 + b1
+    h = 0.5 * pre * (1 + np.vectorize(erf)(pre / sqrt(2)))
+    bound = 2.0 ** -8 * (np.abs(h) @ np.abs(W2)) + 1e-6
+    err = np.abs(_np(y) - ref)
+    assert (err <= bound).all(), float((err / bound).max())
+    assert (err / bound).max() > 0.01
