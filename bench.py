@@ -120,13 +120,12 @@ class Clocks:
 
 
 def algorithmic_bytes(stats):
-    """HBM bytes each kernel must move at minimum (see the design notes):
-    projection 44 B in + 48 B out per Gaussian; compositing fwd reads the
-    sorted id list (4 B/instance) and each visible Gaussian's record once
-    (uv 8 + conic/opacity 16 + colour 12 + depth 4 + features 4N) and writes
-    (5+N)*4 + 12 B per pixel; the adjoint reads the same plus the per-pixel
-    state (8 B) and cotangents ((5+N)*4 B) and writes 24 + (4+N)*4 B of
-    gradients per visible Gaussian."""
+    """HBM bytes each kernel must move at minimum: projection 44 B in + 48 B
+    out per Gaussian; compositing fwd reads the sorted id list (4 B/instance)
+    and each visible Gaussian's record once (uv 8 + conic/opacity 16 + colour
+    12 + depth 4 + features 4N) and writes (5+N)*4 + 12 B per pixel; the
+    adjoint reads the same plus the per-pixel state (8 B) and cotangents
+    ((5+N)*4 B) and writes 24 + (4+N)*4 B of gradients per visible Gaussian."""
     P, Pv, I, HW, N = stats["P"], stats["P_vis"], stats["I"], WIDTH * HEIGHT, N_FEAT
     rec = 8 + 16 + 12 + 4 + 4 * N
     return {
@@ -135,6 +134,36 @@ def algorithmic_bytes(stats):
         "k_render_bwd": I * 4 + Pv * rec + HW * (8 + (5 + N) * 4) + Pv * (24 + (4 + N) * 4),
         "k_project_bwd": P * (40 + 24) + Pv * 40,
     }
+
+
+# FP32 operations of the compositing kernels (an FMA counts 2), from the
+# formulas they evaluate:
+#   every evaluated (pixel, Gaussian) pair: offsets 2, quadratic form 9 (3
+#     products, two multiply-adds, two products), exp 1, alpha 2 -> 14;
+#   forward, per blended pair: T update 2, weight 1, colour + depth 4 FMAs,
+#     N feature FMAs -> 3 + 8 + 2N;
+#   backward, per blended pair: T recovery 2, weight 1, dalpha 17, suffix
+#     sums 13, opacity/power 2, conic 8, uv 8, colour + depth 4, N features,
+#     plus the (10 + N) additions that reduce the per-pair partials over the
+#     pixels -> 55 + 10 + 2N.
+def algorithmic_flops(stats):
+    E, B, N = stats["evaluated"], stats["blends"], N_FEAT
+    return {"k_render_fwd": 14 * E + (11 + 2 * N) * B, "k_render_bwd": 14 * E + (65 + 2 * N) * B}
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
+# capture summarised in profiles/render_fwd_bwd_room300k_N16_full.md, keyed to
+# the source it was taken on (null once render.cu changes).
+NCU_TRAFFIC = {"k_render_bwd": (None, None), "k_render_fwd": (None, None)}
+
+
+def ncu_traffic(kernel):
+    import hashlib
+    nbytes, digest = NCU_TRAFFIC.get(kernel, (None, None))
+    if nbytes is None:
+        return None
+    src = open(os.path.join(ROOT, "paper_2504_19409_gb300", "csrc", "render.cu"), "rb").read()
+    return nbytes if hashlib.sha256(src).hexdigest()[:16] == digest else None
 
 
 def run_ours(args, rank, world, local_rank):
@@ -148,7 +177,7 @@ def run_ours(args, rank, world, local_rank):
     tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     params = [tt(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors, sc.feats)]
     means, scales, quats, opac, cols, feats = params
-    frames = [k for k in range(args.warmup + args.steps) for k in [(k * world + rank) % N_FRAMES]]
+    frames = shard_frames(rank, world, args.warmup + args.steps)
     my_frames = sorted(set(frames))
 
     ras = g.Rasterizer(P_ROOM, WIDTH, HEIGHT, N=N_FEAT, device=dev)
@@ -166,7 +195,7 @@ def run_ours(args, rank, world, local_rank):
         blends[k] = int(fw["n_contrib"].sum().item())
         stats[k] = dict(I=int(ras.sort["n_instances"].item()),
                         P_vis=int((ras.proj["tiles_touched"] > 0).sum().item()),
-                        evaluated=int(fw["last_idx"].sum().item()))
+                        evaluated=int(fw["last_idx"].sum().item()), blends=blends[k])
     ras.check_status()
     HW = WIDTH * HEIGHT
     scales_l1 = {"rgb": 1.0 / (3 * HW), "depth": 1.0 / HW, "feat": 1.0 / (N_FEAT * HW)}
@@ -278,12 +307,18 @@ def run_ours(args, rank, world, local_rank):
         per.setdefault(name, []).append(t)
     kernel_ms = {k: sum(v) / args.steps for k, v in per.items()}
     launches = {k: len(v) / args.steps for k, v in per.items()}
-    mean_stats = {key: float(np.mean([stats[k][key] for k in timed])) for key in ("I", "P_vis", "evaluated")}
+    mean_stats = {key: float(np.mean([stats[k][key] for k in timed])) for key in ("I", "P_vis", "evaluated", "blends")}
     mean_stats["P"] = P_ROOM
     return dict(ms=ms, tot_ms=tot_ms, tot_blends=tot_blends, e2e_ms=e2e_ms, e2e_blends=e2e_blends, h2d=h2d, d2h=d2h,
                 kernel_ms=kernel_ms, launches=launches, per=per, clocks=clk, stats=mean_stats,
                 blends_per_frame=float(np.mean([blends[k] for k in timed])), wall_s=t_wall,
                 traced_ms=float(np.mean(ms_trace)))
+
+
+def shard_frames(rank, world, count):
+    """Frames of this rank: step i processes trajectory frame (i * world + rank)
+    mod 100, so the ranks cover disjoint frames with no data exchange."""
+    return [(i * world + rank) % N_FRAMES for i in range(count)]
 
 
 def _barrier(world):
@@ -292,24 +327,29 @@ def _barrier(world):
         dist.barrier()
 
 
-def _max_over_ranks(x, world):
+def _reduce(x, world, op, device):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
     return float(t.item())
 
 
-def _sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
+def _max_over_ranks(x, world, device="cuda"):
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.MAX, device)
+
+
+def _sum_over_ranks(x, world, device="cuda"):
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.SUM, device)
+
+
+def whole_job_throughput(units, seconds, world, device="cuda"):
+    """Units all ranks processed / the slowest rank's time (weak scaling)."""
+    return _sum_over_ranks(units, world, device) / _max_over_ranks(seconds, world, device)
 
 
 def oracle_frame_sample(sc, k, tile_rows=None):
@@ -346,6 +386,7 @@ def main():
                     help="slam: the headline SLAM-frame workload (N=16); wide: 500k Gaussians with 512 bf16 feature "
                          "channels, tensor-core vs plain fp32; decoder: latent render + learned decoder vs both")
     ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--gaussians", type=int, default=0, help="override the Gaussian count of --workload wide/decoder")
     ap.add_argument("--profile", action="store_true",
                     help="setup, warm-up and --steps plain frames only (no timing, no JSON); for profiler captures")
     args = ap.parse_args()
@@ -387,14 +428,26 @@ def main():
             pass
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
         alg = algorithmic_bytes(r["stats"])
+        flops = algorithmic_flops(r["stats"])
         km = r["kernel_ms"]
-        top = max(km, key=km.get)
-        dom = top if top in alg else max((k for k in alg if k in km), key=lambda k: km[k])
-        achieved = alg[dom] / (km[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
-                "kernel_ms": round(km[dom], 4), "algorithmic_bytes": alg[dom]}
+        dom = max(km, key=km.get)
+        sm_mhz = (r["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+        if dom in flops:
+            achieved = flops[dom] / (km[dom] * 1e-3) / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+                    "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": ncu_traffic(dom),
+                    "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz (SM clock sampled "
+                                   "during the timed region)",
+                    "algorithmic_flops": flops[dom], "kernel_ms": round(km[dom], 4),
+                    "algorithmic_bytes": alg.get(dom),
+                    "hbm_frac": round(alg.get(dom, 0) / (km[dom] * 1e-3) / 1e9 / hbm_peak, 4),
+                    "hbm_peak_gbs": hbm_peak}
+        else:
+            achieved = alg.get(dom, 0) / (km[dom] * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel_ms": round(km[dom], 4)}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             sc = None
@@ -507,6 +560,9 @@ def _tc_exec_flops(last_idx, W, H, N):
 
 
 def run_forms(args):
+    global P_WIDE
+    if args.gaussians:
+        P_WIDE = args.gaussians
     import numpy as np
     import torch
     import paper_2504_19409_gb300 as g
@@ -527,15 +583,17 @@ def run_forms(args):
     HW = WIDTH * HEIGHT
     tc = g.Rasterizer(P_WIDE, WIDTH, HEIGHT, N=N_WIDE, layout=g.GS_LAYOUT_HWC,
                       flags=g.GS_FEAT_ON | g.GS_FEAT_TENSOR_CORE, device=dev)
-    plain = g.Rasterizer(P_WIDE, WIDTH, HEIGHT, N=N_WIDE, layout=g.GS_LAYOUT_HWC, device=dev)
+    plain = None if args.profile else g.Rasterizer(P_WIDE, WIDTH, HEIGHT, N=N_WIDE, layout=g.GS_LAYOUT_HWC, device=dev)
     for k in sorted(set(frames)):
         for r in (tc, plain):
-            r.ensure_capacity(frame_camera(k), *scene[:4])
+            if r is not None:
+                r.ensure_capacity(frame_camera(k), *scene[:4])
     blends, instances = {}, {}
+    ref = plain if plain is not None else tc
     for k in sorted(set(frames)):
-        fw = plain.forward(frame_camera(k), *scene, feats_bf)
+        fw = ref.forward(frame_camera(k), *scene, feats_bf)
         blends[k] = int(fw["n_contrib"].sum().item())
-        instances[k] = int(plain.sort["n_instances"].item())
+        instances[k] = int(ref.sort["n_instances"].item())
     timed = frames[args.warmup:]
     tot_blends = sum(blends[k] for k in timed)
     result = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -559,6 +617,14 @@ def run_forms(args):
                 r.backward(cam, scene[0], scene[1], scene[2], scene[4], feats_bf, g_rgb, g_d, None, g_f)
             return f
 
+        if args.profile:
+            # plain frames of the tensor-core form only (for profiler captures)
+            for k in frames:
+                fwd_bwd(tc)(k)
+            torch.cuda.synchronize()
+            tc.check_status()
+            print("profile run done")
+            return 0
         for r in (tc, plain):
             for k in frames[:args.warmup]:
                 fwd_bwd(r)(k)

@@ -4,8 +4,10 @@
 // depth-sorted list as the contraction index k,
 //     F[p, :] = sum_k w[p, k] f[g_k, :],   w[p, k] = alpha_k(p) T_k(p)
 // (w = 0 where pixel p skips or has stopped). One CTA owns half a tile
-// (16 x 8 = 128 pixels = the 128 rows of a tcgen05 M=128 tile) and walks the
-// list in K-steps of 32 Gaussians:
+// (16 x 8 = 128 pixels = the 128 rows of a tcgen05 M=128 tile) and up to 256
+// of the channels (a 256-column accumulator, so two CTAs share an SM's tensor
+// memory and overlap one's epilogue with the other's main loop), and walks
+// the list in K-steps of 32 Gaussians:
 //   - 4 threads per pixel (512 threads) each evaluate alpha for 8 of the 32
 //     Gaussians with the SIMT kernel's exact skip test; below last_idx no
 //     pixel has stopped, so T_k is the product of (1 - alpha_j) over the
@@ -26,7 +28,8 @@
 // Shared-memory operand layouts (no swizzle; 16-byte core-matrix rows):
 //   A: element (m, k) at (m/8)*512 + (k/8)*128 + (m%8)*16 + (k%8)*2
 //      descriptor LBO = 128 (K direction), SBO = 512 (M direction)
-//   B: element (k, n) at (n/8)*128 + (k/8)*SK + (k%8)*16 + (n%8)*2, SK = N*16
+//   B: element (k, n) at (n/8)*128 + (k/8)*SK + (k%8)*16 + (n%8)*2, SK = Nc*16
+//      (Nc <= 256 channels of this CTA)
 //      descriptor LBO = SK (K direction), SBO = 128 (N direction)
 // Every wait is bounded (1 s of %globaltimer); a timeout flags
 // GS_ERR_TIMEOUT, waits (bounded) for the tensor core, frees tensor memory
@@ -42,11 +45,12 @@ constexpr int kTcThreads = 512;  // 4 threads per pixel
 constexpr int kTcK = 32;       // Gaussians per K-step
 constexpr int kTcStages = 3;
 constexpr int kTcMaxN = 512;
+constexpr int kTcNC = 256;     // channels per CTA (tensor-memory columns of one accumulator)
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 struct TcStage {
   uint8_t A[kTcPix * kTcK * 2];       // 8 KB
-  uint8_t B[kTcK * kTcMaxN * 2];      // 32 KB (for N = 512)
+  uint8_t B[kTcK * kTcNC * 2];        // 16 KB (256 channels)
   float2 uv[kTcK];
   float4 co[kTcK];
 };
@@ -123,8 +127,8 @@ struct TcFwdParams {
   const float4* co;
   const __nv_bfloat16* feats;
   const int* last_idx;
-  int N;
-  int tmem_cols;
+  int N;          // feature channels in total
+  int nsplit;     // CTAs per half tile, each owning kTcNC channels (the last may own fewer)
   float* out_feat;
   int32_t* status;
 };
@@ -132,7 +136,8 @@ struct TcFwdParams {
 // Loads of K-step t into stage s: Gaussian records (threads 0..31) and the
 // feature rows (every thread, 16-byte cp.async chunks, zero-filled past the
 // list).
-__device__ __forceinline__ void tc_issue_loads(const TcFwdParams& p, TcStage& st, int t, int2 rg, int maxlast) {
+__device__ __forceinline__ void tc_issue_loads(const TcFwdParams& p, TcStage& st, int t, int2 rg, int maxlast, int c0,
+                                               int Nc) {
   const int tid = threadIdx.x;
   const int base = rg.x + t * kTcK;
   const int lim = rg.x + maxlast;
@@ -147,27 +152,31 @@ __device__ __forceinline__ void tc_issue_loads(const TcFwdParams& p, TcStage& st
       st.co[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  const int cpr = p.N / 8;           // 16-byte chunks per feature row
-  const uint32_t SK = (uint32_t)p.N * 16;
+  const int cpr = Nc / 8;  // 16-byte chunks of this CTA's channels per feature row
+  const uint32_t SK = (uint32_t)Nc * 16;
   const uint32_t b0 = smem_u32(st.B);
   for (int e = tid; e < kTcK * cpr; e += kTcThreads) {
     const int k = e / cpr, c = e - k * cpr;
     const int pos = base + k;
     const bool valid = pos < lim;
     const uint32_t g = valid ? p.gids[pos] : 0u;
-    const __nv_bfloat16* src = p.feats + (size_t)g * p.N + 8 * c;
+    const __nv_bfloat16* src = p.feats + (size_t)g * p.N + c0 + 8 * c;
     const uint32_t dst = b0 + (uint32_t)c * 128u + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
     cp_async16(dst, src, valid);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdParams p) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int m = tid >> 2, q = tid & 3;  // pixel row of the MMA tile, quarter of the K-step
-  const int tile = blockIdx.x >> 1, half = blockIdx.x & 1;
+  const int split = blockIdx.x % p.nsplit;
+  const int tile = (blockIdx.x / p.nsplit) >> 1, half = (blockIdx.x / p.nsplit) & 1;
+  const int c0 = split * kTcNC, Nc = min(kTcNC, p.N - c0);
+  int tmem_cols = 32;
+  while (tmem_cols < Nc) tmem_cols *= 2;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
   const int px = tx * kTile + (m & 15);
   const int py = ty * kTile + half * 8 + (m >> 4);
@@ -179,7 +188,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdPar
   if (tid == 0) S.maxlast = 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
-                 "r"(p.tmem_cols));
+                 "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -194,11 +203,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdPar
   const int maxlast = S.maxlast;
   const uint32_t tmem = S.tmem;
   const int nsteps = (maxlast + kTcK - 1) / kTcK;
-  const uint32_t SK = (uint32_t)p.N * 16;
+  const uint32_t SK = (uint32_t)Nc * 16;
   bool ok = true;
 
-  if (nsteps > 0) tc_issue_loads(p, S.st[0], 0, rg, maxlast);
-  if (nsteps > 1) tc_issue_loads(p, S.st[1], 1, rg, maxlast);
+  if (nsteps > 0) tc_issue_loads(p, S.st[0], 0, rg, maxlast, c0, Nc);
+  if (nsteps > 1) tc_issue_loads(p, S.st[1], 1, rg, maxlast, c0, Nc);
   float T = 1.f;  // transmittance in front of this K-step (same in the 4 threads of a pixel)
   int last_issued = -1;  // last K-step whose MMAs were issued (block-uniform)
   for (int t = 0; t < nsteps && ok; ++t) {
@@ -248,8 +257,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdPar
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a0 = smem_u32(st.A), b0 = smem_u32(st.B);
-      for (int n0 = 0; n0 < p.N; n0 += 256) {
-        const int nn = min(256, p.N - n0);
+      for (int n0 = 0; n0 < Nc; n0 += 256) {
+        const int nn = min(256, Nc - n0);
         const uint32_t idesc = idesc_bf16(kTcPix, nn, 1);
 #pragma unroll
         for (int k16 = 0; k16 < kTcK / 16; ++k16) {
@@ -271,7 +280,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdPar
       bool w_ok = true;
       if (t >= 1) w_ok = mbar_wait(smem_u32(&S.mbar[(t - 1) % kTcStages]), (uint32_t)(((t - 1) / kTcStages) & 1));
       ok = __syncthreads_and(w_ok) != 0;
-      if (ok) tc_issue_loads(p, S.st[(t + 2) % kTcStages], t + 2, rg, maxlast);
+      if (ok) tc_issue_loads(p, S.st[(t + 2) % kTcStages], t + 2, rg, maxlast, c0, Nc);
     }
   }
   if (nsteps > 0 && ok) {
@@ -292,8 +301,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdPar
     const int row = 32 * (warp & 3) + (tid & 31);
     const int ex = tx * kTile + (row & 15), ey = ty * kTile + half * 8 + (row >> 4);
     const bool e_inside = ex < p.cam.W && ey < p.cam.H;
-    float* dst = p.out_feat + ((size_t)ey * p.cam.W + ex) * p.N;
-    for (int c = 32 * (warp >> 2); c < p.N; c += 128) {
+    float* dst = p.out_feat + ((size_t)ey * p.cam.W + ex) * p.N + c0;
+    for (int c = 32 * (warp >> 2); c < Nc; c += 128) {
       float v[32];
       if (nsteps > 0) {
         tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c, v);
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc(const TcFwdPar
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
 }  // namespace
@@ -328,9 +337,7 @@ gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uin
   p.feats = feats;
   p.last_idx = last_idx;
   p.N = N;
-  int cols = 32;
-  while (cols < N) cols *= 2;
-  p.tmem_cols = cols;
+  p.nsplit = (N + kTcNC - 1) / kTcNC;
   p.out_feat = out_feat;
   p.status = status;
   const size_t smem = sizeof(TcSmem) + 1024;
@@ -340,7 +347,7 @@ gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uin
       return GS_ERR_CUDA;
     attr_set = true;
   }
-  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2);
+  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2 * p.nsplit);
   GS_TRACE("k_render_feat_tc", st);
   k_render_feat_tc<<<blocks, kTcThreads, smem, st>>>(p);
   return last_launch_status();
