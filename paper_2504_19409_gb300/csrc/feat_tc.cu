@@ -21,8 +21,8 @@
 //   - a 3-stage shared-memory ring lets the next step's loads and weights
 //     proceed while the tensor core consumes the current step
 //     (tcgen05.commit -> mbarrier per stage).
-// The epilogue reads F from tensor memory (tcgen05.ld 32x32b) and writes it
-// in HWC layout. RGB, depth, alpha, T_final and last_idx come from the SIMT
+// The epilogue reads F from tensor memory (tcgen05.ld 32x32b), stages it in
+// shared memory and writes it in HWC layout with bulk asynchronous copies. RGB, depth, alpha, T_final and last_idx come from the SIMT
 // forward kernel launched before this one (its last_idx bounds each pixel).
 //
 // Shared-memory operand layouts (no swizzle; 16-byte core-matrix rows):
@@ -56,11 +56,13 @@ struct TcStage {
 };
 
 struct TcSmem {
-  TcStage st[kTcStages];
+  TcStage st[kTcStages];  // also the epilogue's staging area (128 rows x 528 B)
   unsigned long long mbar[kTcStages];
   uint32_t tmem;
   int maxlast;
 };
+
+static_assert(sizeof(TcStage) * kTcStages >= (kTcPix - 1) * 528 + 512, "epilogue staging does not fit the ring");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -296,26 +298,47 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    // epilogue: warp w reads tensor-memory lanes 32*(w%4).. (pixel rows);
-    // the 32-column chunks go round-robin to the 4 warps sharing those lanes
+    // Epilogue through shared memory and the bulk-copy engine: for each slab
+    // of PW <= 128 columns, warp w (tensor-memory lanes 32*(w%4).., column
+    // quarter w/4) stages its 32 x 32 block into the idle operand ring with
+    // rows padded to 528 B (conflict-free 16-byte stores), then one thread per
+    // pixel row issues a bulk copy of its PW * 4 contiguous bytes into the
+    // HWC output.
+    uint8_t* stage = S.st[0].A;  // >= 128 * 528 bytes of the idle ring
+    const uint32_t stage_u32 = smem_u32(stage);
     const int row = 32 * (warp & 3) + (tid & 31);
-    const int ex = tx * kTile + (row & 15), ey = ty * kTile + half * 8 + (row >> 4);
-    const bool e_inside = ex < p.cam.W && ey < p.cam.H;
-    float* dst = p.out_feat + ((size_t)ey * p.cam.W + ex) * p.N + c0;
-    for (int c = 32 * (warp >> 2); c < Nc; c += 128) {
-      float v[32];
-      if (nsteps > 0) {
-        tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c, v);
-      } else {
+    const int PW = Nc < 128 ? Nc : 128;
+    for (int p0 = 0; p0 < Nc; p0 += PW) {
+      const int cbase = 32 * (warp >> 2);
+      if (cbase < PW) {
+        float v[32];
+        if (nsteps > 0) {
+          tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(p0 + cbase), v);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = 0.f;
-      }
-      if (e_inside) {
+          for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        }
+        uint8_t* dst = stage + row * 528 + cbase * 4;
 #pragma unroll
         for (int i = 0; i < 32; i += 4)
-          *reinterpret_cast<float4*>(dst + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          *reinterpret_cast<float4*>(dst + i * 4) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid < kTcPix) {
+        const int ex = tx * kTile + (tid & 15), ey = ty * kTile + half * 8 + (tid >> 4);
+        if (ex < p.cam.W && ey < p.cam.H) {
+          float* g = p.out_feat + ((size_t)ey * p.cam.W + ex) * p.N + c0 + p0;
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g),
+                       "r"(stage_u32 + (uint32_t)tid * 528u), "r"(PW * 4)
+                       : "memory");
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      }
+      __syncthreads();
     }
+    if (tid < kTcPix) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -343,7 +366,8 @@ gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uin
   const size_t smem = sizeof(TcSmem) + 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_render_feat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_render_feat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_render_feat_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
       return GS_ERR_CUDA;
     attr_set = true;
   }
