@@ -187,7 +187,8 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
  * tcgen05 product dL/dF^T [N x 128 px] (rounded to bf16) times the weights
  * W [128 px x 32 Gaussians] (bf16), fp32 accumulation; the geometry
  * gradients stay on the fp32 SIMT kernel. Coupled mode is GS_ERR_UNSUPPORTED
- * there.
+ * there; dL_dfeat and d_feats must be 16-byte aligned (GS_ERR_INVALID_ARG
+ * otherwise), since d_feats rows are accumulated with vector atomics.
  * workspace must hold gs_render_bwd_workspace_bytes(P) bytes.
  */
 size_t gs_render_bwd_workspace_bytes(int32_t P);

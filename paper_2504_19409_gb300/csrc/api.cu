@@ -234,7 +234,7 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
   const bool tc = feat_on && (flags & GS_FEAT_TENSOR_CORE);
   if (tc && (coupled || feat_dtype != GS_BF16 || layout != GS_LAYOUT_HWC || N % 128 != 0 || N > 512))
     return GS_ERR_UNSUPPORTED;
-  if (tc && dL_dfeat && !aligned(dL_dfeat, 16)) return GS_ERR_INVALID_ARG;
+  if (tc && ((dL_dfeat && !aligned(dL_dfeat, 16)) || !aligned(d_feats, 16))) return GS_ERR_INVALID_ARG;
   const float* b = bg ? bg : kBlack;
   const CamF k = make_cam(*cam);
   char* ws = static_cast<char*>(workspace);

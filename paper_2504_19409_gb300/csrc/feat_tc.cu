@@ -121,6 +121,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Record slot of the k-th Gaussian of a 32-Gaussian step: thread quarter q
+// reads Gaussians 8q..8q+7, so slot 4 (k % 8) + k / 8 puts the four quarters'
+// j-th records side by side (one bank group, no conflicts).
+__device__ __forceinline__ int rec_slot(int k) { return ((k & 7) << 2) | (k >> 3); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Waits for this thread's outstanding tensor-memory loads; the values pass
+// through the barrier so that no use of them is scheduled before it.
+template <int G>
+__device__ __forceinline__ void tmem_wait_ld(float (&v)[G][8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    asm volatile("" : "+f"(v[g][0]), "+f"(v[g][1]), "+f"(v[g][2]), "+f"(v[g][3]), "+f"(v[g][4]), "+f"(v[g][5]),
+                 "+f"(v[g][6]), "+f"(v[g][7]));
+}
+
 struct TcFwdParams {
   CamF cam;
   const int2* ranges;
@@ -135,36 +160,63 @@ struct TcFwdParams {
   int32_t* status;
 };
 
-// Loads of K-step t into stage s: Gaussian records (threads 0..31) and the
-// feature rows (every thread, 16-byte cp.async chunks, zero-filled past the
-// list).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
+  const int n = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+
+// Gaussian ids a thread needs to issue the copies of one K-step: the record
+// id (threads 0..31) and the ids of its feature rows (16-byte chunks tid and
+// tid + 512). They are fetched one step before use, so no id load stalls the
+// step that issues the copies.
+struct TcIds {
+  uint32_t rec;
+  uint32_t row[2];
+};
+static_assert(kTcK * kTcNC / 8 <= 2 * kTcThreads, "two feature chunks per thread per K-step");
+
+__device__ __forceinline__ TcIds tc_fetch_ids(const TcFwdParams& p, int t, int2 rg, int maxlast, int cpr) {
+  const int tid = threadIdx.x;
+  const int base = rg.x + t * kTcK, lim = rg.x + maxlast;
+  TcIds ids{0u, {0u, 0u}};
+  if (tid < kTcK && base + tid < lim) ids.rec = p.gids[base + tid];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int e = tid + i * kTcThreads;
+    if (e < kTcK * cpr) {
+      const int k = e / cpr;
+      if (base + k < lim) ids.row[i] = p.gids[base + k];
+    }
+  }
+  return ids;
+}
+
+// Asynchronous copies of K-step t into stage `st`: the Gaussian records
+// (threads 0..31) and the feature rows (16-byte chunks), zero-filled past the
+// list; one commit group per step.
 __device__ __forceinline__ void tc_issue_loads(const TcFwdParams& p, TcStage& st, int t, int2 rg, int maxlast, int c0,
-                                               int Nc) {
+                                               int Nc, const TcIds& ids) {
   const int tid = threadIdx.x;
   const int base = rg.x + t * kTcK;
   const int lim = rg.x + maxlast;
   if (tid < kTcK) {
-    const int pos = base + tid;
-    if (pos < lim) {
-      const uint32_t g = p.gids[pos];
-      st.uv[tid] = p.uv[g];
-      st.co[tid] = p.co[g];
-    } else {
-      st.uv[tid] = make_float2(0.f, 0.f);
-      st.co[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    const bool valid = base + tid < lim;
+    cp_async8(smem_u32(&st.uv[rec_slot(tid)]), p.uv + ids.rec, valid);
+    cp_async16(smem_u32(&st.co[rec_slot(tid)]), p.co + ids.rec, valid);
   }
   const int cpr = Nc / 8;  // 16-byte chunks of this CTA's channels per feature row
   const uint32_t SK = (uint32_t)Nc * 16;
   const uint32_t b0 = smem_u32(st.B);
-  for (int e = tid; e < kTcK * cpr; e += kTcThreads) {
-    const int k = e / cpr, c = e - k * cpr;
-    const int pos = base + k;
-    const bool valid = pos < lim;
-    const uint32_t g = valid ? p.gids[pos] : 0u;
-    const __nv_bfloat16* src = p.feats + (size_t)g * p.N + c0 + 8 * c;
-    const uint32_t dst = b0 + (uint32_t)c * 128u + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
-    cp_async16(dst, src, valid);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int e = tid + i * kTcThreads;
+    if (e < kTcK * cpr) {
+      const int k = e / cpr, c = e - k * cpr;
+      const bool valid = base + k < lim;
+      const __nv_bfloat16* src = p.feats + (size_t)ids.row[i] * p.N + c0 + 8 * c;
+      const uint32_t dst = b0 + (uint32_t)c * 128u + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
+      cp_async16(dst, src, valid);
+    }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -208,8 +260,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
   const uint32_t SK = (uint32_t)Nc * 16;
   bool ok = true;
 
-  if (nsteps > 0) tc_issue_loads(p, S.st[0], 0, rg, maxlast, c0, Nc);
-  if (nsteps > 1) tc_issue_loads(p, S.st[1], 1, rg, maxlast, c0, Nc);
+  const int cpr = Nc / 8;
+  if (nsteps > 0) tc_issue_loads(p, S.st[0], 0, rg, maxlast, c0, Nc, tc_fetch_ids(p, 0, rg, maxlast, cpr));
+  if (nsteps > 1) tc_issue_loads(p, S.st[1], 1, rg, maxlast, c0, Nc, tc_fetch_ids(p, 1, rg, maxlast, cpr));
+  TcIds next_ids = tc_fetch_ids(p, 2, rg, maxlast, cpr);  // ids of the next K-step to issue
   float T = 1.f;  // transmittance in front of this K-step (same in the 4 threads of a pixel)
   int last_issued = -1;  // last K-step whose MMAs were issued (block-uniform)
   for (int t = 0; t < nsteps && ok; ++t) {
@@ -224,9 +278,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       a[j] = 0.f;
-      const int k = 8 * q + j;
+      const int k = 8 * q + j, ks = rec_slot(k);
       PairAlpha pa;
-      if (t * kTcK + k < last && pair_alpha(st.co[k], st.uv[k].x - pxc, st.uv[k].y - pyc, pa)) {
+      if (t * kTcK + k < last && pair_alpha(st.co[ks], st.uv[ks].x - pxc, st.uv[ks].y - pyc, pa)) {
         a[j] = pa.alpha;
         prod = __fmul_rn(prod, __fsub_rn(1.f, pa.alpha));
       }
@@ -282,7 +336,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
       bool w_ok = true;
       if (t >= 1) w_ok = mbar_wait(smem_u32(&S.mbar[(t - 1) % kTcStages]), (uint32_t)(((t - 1) / kTcStages) & 1));
       ok = __syncthreads_and(w_ok) != 0;
-      if (ok) tc_issue_loads(p, S.st[(t + 2) % kTcStages], t + 2, rg, maxlast, c0, Nc);
+      if (ok) {
+        tc_issue_loads(p, S.st[(t + 2) % kTcStages], t + 2, rg, maxlast, c0, Nc, next_ids);
+        next_ids = tc_fetch_ids(p, t + 3, rg, maxlast, cpr);
+      }
     }
   }
   if (nsteps > 0 && ok) {
@@ -299,18 +356,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // Epilogue through shared memory and the bulk-copy engine: for each slab
-    // of PW <= 128 columns, warp w (tensor-memory lanes 32*(w%4).., column
-    // quarter w/4) stages its 32 x 32 block into the idle operand ring with
-    // rows padded to 528 B (conflict-free 16-byte stores), then one thread per
-    // pixel row issues a bulk copy of its PW * 4 contiguous bytes into the
-    // HWC output.
+    // of pw <= 128 columns (the last slab of a 192-channel share is 64 wide),
+    // warp w (tensor-memory lanes 32*(w%4).., column quarter w/4) stages its
+    // 32 x 32 block into the idle operand ring with rows padded to 528 B
+    // (conflict-free 16-byte stores), then one thread per pixel row issues a
+    // bulk copy of its pw * 4 contiguous bytes into the HWC output.
     uint8_t* stage = S.st[0].A;  // >= 128 * 528 bytes of the idle ring
     const uint32_t stage_u32 = smem_u32(stage);
     const int row = 32 * (warp & 3) + (tid & 31);
     const int PW = Nc < 128 ? Nc : 128;
     for (int p0 = 0; p0 < Nc; p0 += PW) {
+      const int pw = min(PW, Nc - p0);  // columns in this slab: a multiple of 32 (Nc % 64 == 0)
       const int cbase = 32 * (warp >> 2);
-      if (cbase < PW) {
+      if (cbase < pw) {
         float v[32];
         if (nsteps > 0) {
           tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(p0 + cbase), v);
@@ -330,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
         if (ex < p.cam.W && ey < p.cam.H) {
           float* g = p.out_feat + ((size_t)ey * p.cam.W + ex) * p.N + c0 + p0;
           asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g),
-                       "r"(stage_u32 + (uint32_t)tid * 528u), "r"(PW * 4)
+                       "r"(stage_u32 + (uint32_t)tid * 528u), "r"(pw * 4)
                        : "memory");
         }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -383,18 +441,21 @@ gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uin
 // the feature cotangent reaches only f): dL/df_g = sum_p w_g(p) dL/dF(p, :).
 // Per half tile, transposed so that every operand keeps a validated layout:
 //     D [N channels x 32 Gaussians] = dF^T [N x 128 px] * W [128 px x 32]
-//   A = dF^T, K-major, converted to bf16 once per CTA (N/128 M-blocks):
-//       element (c, p) at (c/8)*2048 + (p/8)*128 + (c%8)*16 + (p%8)*2
-//       descriptor LBO = 128 (K = pixels), SBO = 2048 (M = channels)
+//   A = dF^T, K-major, converted to bf16 once per CTA, NMB = N/128 M-blocks.
+//       Channel c sits in M-block c % NMB, row r = c / NMB, so that a
+//       tensor-memory lane r holds the NMB contiguous channels NMB r .. and
+//       the epilogue adds them with one vector atomic:
+//       element (mb, r, p) at mb*32768 + (r/8)*2048 + (p/8)*128 + (r%8)*16 + (p%8)*2
+//       descriptor LBO = 128 (K = pixels), SBO = 2048 (M = channel rows)
 //   B = W, MN-major (Gaussians contiguous for a pixel), one 16-byte row per
 //       thread exactly as in the forward:
 //       element (p, g) at (g/8)*128 + (p/8)*512 + (p%8)*16 + (g%8)*2
 //       descriptor LBO = 512 (K = pixels), SBO = 128 (N = Gaussians)
-// D is double-buffered in tensor memory (2 x N/4 columns), so the MMAs of a
-// Gaussian block overlap the epilogue of the previous one. The epilogue adds
-// each Gaussian's N-vector to dL/df with coalesced fp32 atomics (32 lanes =
-// 32 consecutive channels), skipping Gaussians that weigh nothing in this
-// half tile.
+// D is double-buffered in tensor memory (2 x NMB x 32 columns), so the MMAs
+// of a Gaussian block overlap the epilogue of the previous one. In the
+// epilogue warp w takes lanes 32 (w % 4).. and Gaussians 8 (w / 4)..+7 of the
+// block and skips Gaussians that weigh nothing in this half tile (a bit mask
+// built with one warp reduction per warp).
 namespace {
 
 constexpr int kTbG = 32;  // Gaussians per block (MMA N)
@@ -402,10 +463,10 @@ constexpr int kTbG = 32;  // Gaussians per block (MMA N)
 struct TbSmem {
   uint8_t A[kTcMaxN * kTcPix * 2];  // dF^T, 128 KB for N = 512
   uint8_t B[2][kTcPix * kTbG * 2];  // W, 8 KB per buffer
-  float2 uv[3][kTbG];  // record ring: block b uses slot b % 3
+  float2 uv[3][kTbG];  // record ring: block b uses slot b % 3, Gaussian k at rec_slot(k)
   float4 co[3][kTbG];
-  uint32_t gid[3][kTbG];
-  int nz[3][kTbG];
+  uint32_t gid[3][kTbG];  // by position k in the block
+  uint32_t nz[3];         // bit k: Gaussian k has a nonzero weight in this half tile
   unsigned long long mbar[2];
   uint32_t tmem;
   int maxlast;
@@ -425,33 +486,26 @@ struct TcBwdParams {
   int32_t* status;
 };
 
-// Records of Gaussian block b (threads 0..31): fetched into registers, stored
-// into ring slot b % 3 later, so the global latency overlaps other work.
-struct TbRecord {
-  float2 uv;
-  float4 co;
-  uint32_t gid;
-};
-
-__device__ __forceinline__ TbRecord tb_fetch(const TcBwdParams& p, int b, int2 rg, int maxlast) {
-  TbRecord r{make_float2(0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), 0xFFFFFFFFu};
+__device__ __forceinline__ uint32_t tb_fetch_id(const TcBwdParams& p, int b, int2 rg, int maxlast) {
   const int pos = rg.x + b * kTbG + (int)threadIdx.x;
-  if (pos < rg.x + maxlast) {
-    r.gid = p.gids[pos];
-    r.uv = p.uv[r.gid];
-    r.co = p.co[r.gid];
-  }
-  return r;
+  return pos < rg.x + maxlast ? p.gids[pos] : 0u;
 }
 
-__device__ __forceinline__ void tb_store(TbSmem& S, int slot, const TbRecord& r) {
+// Records of Gaussian block b into ring slot `slot` (threads 0..31): id from
+// registers, uv and conic/opacity by asynchronous copy (zero past the list).
+__device__ __forceinline__ void tb_issue(const TcBwdParams& p, TbSmem& S, int slot, int b, int2 rg, int maxlast,
+                                         uint32_t g) {
   const int tid = threadIdx.x;
-  S.uv[slot][tid] = r.uv;
-  S.co[slot][tid] = r.co;
-  S.gid[slot][tid] = r.gid;
-  S.nz[slot][tid] = 0;
+  const bool valid = rg.x + b * kTbG + tid < rg.x + maxlast;
+  const int k = rec_slot(tid);
+  cp_async8(smem_u32(&S.uv[slot][k]), p.uv + g, valid);
+  cp_async16(smem_u32(&S.co[slot][k]), p.co + g, valid);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  S.gid[slot][tid] = g;
+  if (tid == 0) S.nz[slot] = 0u;
 }
 
+template <int NMB>
 __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBwdParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   TbSmem& S = *reinterpret_cast<TbSmem*>(smem_raw);
@@ -465,8 +519,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const int2 rg = p.ranges[tile];
   const int last = inside ? p.last_idx[(size_t)py * p.cam.W + px] : 0;
-  const int nmb = p.N / 128;         // M-blocks of 128 channels
-  const uint32_t dcols = (uint32_t)(nmb * kTbG);  // tensor-memory columns per D buffer
+  constexpr uint32_t dcols = (uint32_t)(NMB * kTbG);  // tensor-memory columns per D buffer
+  const int N = NMB * 128;
 
   if (tid == 0) S.maxlast = 0;
   if (warp == 0) {
@@ -478,19 +532,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
     for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[s])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // dF^T for this half tile: thread (m, q) converts channels [qN/4, (q+1)N/4) of pixel m
+  // dF^T for this half tile. Item (i, pg): channel quad i (4 i .. 4 i + 3) of
+  // the 8 pixels m = 8 pg .. 8 pg + 7 (one row segment of the image); the 32
+  // lanes of a warp read 32 consecutive quads of a pixel (coalesced) and write
+  // 16-byte rows of 8 pixels (distinct bank groups for NMB = 4).
   {
-    const int cq = p.N / 4;
-    const float* src = p.g_feat + ((size_t)py * p.cam.W + px) * p.N + q * cq;
-    for (int c4 = 0; c4 < cq; c4 += 4) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (inside) v = *reinterpret_cast<const float4*>(src + c4);
-      const float vv[4] = {v.x, v.y, v.z, v.w};
+    const int nq = N / 4;
+    const int ry0 = ty * kTile + half * 8;
+    const int rx0 = tx * kTile;
+    for (int it = tid; it < nq * 16; it += kTcThreads) {
+      const int i = it % nq, pg = it / nq;
+      const int ry = ry0 + (pg >> 1), rx = rx0 + (pg & 1) * 8;
+      float4 v[8];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int c = q * cq + c4 + e;
-        *reinterpret_cast<__nv_bfloat16*>(S.A + (c >> 3) * 2048 + (m >> 3) * 128 + (c & 7) * 16 + (m & 7) * 2) =
-            __float2bfloat16_rn(vv[e]);
+      for (int e = 0; e < 8; ++e) {
+        v[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ry < p.cam.H && rx + e < p.cam.W)
+          v[e] = __ldg(reinterpret_cast<const float4*>(p.g_feat + ((size_t)ry * p.cam.W + rx + e) * N) + i);
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int c = 4 * i + s, mb = c % NMB, r = c / NMB;
+        float f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = s == 0 ? v[e].x : s == 1 ? v[e].y : s == 2 ? v[e].z : v[e].w;
+        uint32_t w4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+          w4[e] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(S.A + mb * 32768 + (r >> 3) * 2048 + pg * 128 + (r & 7) * 16) =
+            make_uint4(w4[0], w4[1], w4[2], w4[3]);
       }
     }
   }
@@ -503,7 +576,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
   const uint32_t tmem = S.tmem;
   const int nb = (maxlast + kTbG - 1) / kTbG;
   bool ok = true;
-  if (nb > 0 && tid < kTbG) tb_store(S, 0, tb_fetch(p, 0, rg, maxlast));
+  uint32_t next_id = 0;  // id of this thread's Gaussian in the next block to stage (threads 0..31)
+  if (nb > 0 && tid < kTbG) {
+    tb_issue(p, S, 0, 0, rg, maxlast, tb_fetch_id(p, 0, rg, maxlast));
+    if (nb > 1) next_id = tb_fetch_id(p, 1, rg, maxlast);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
   __syncthreads();
 
   float T = 1.f;
@@ -514,17 +592,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
         __syncthreads_and(mbar_wait(smem_u32(&S.mbar[buf]), (uint32_t)((b >> 1) & 1))) != 0;
     if (!w_ok) return false;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // warp w: M-block w/4 (if any), tensor-memory lanes 32*(w%4)..: channel c
-    const int mb = warp >> 2;
-    if (mb < nmb) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)buf * dcols + (uint32_t)(mb * kTbG), v);
-      const int c = mb * 128 + 32 * (warp & 3) + lane;
-#pragma unroll 4
-      for (int j = 0; j < kTbG; ++j) {
-        if (!S.nz[slot][j]) continue;
-        const uint32_t g = S.gid[slot][j];
-        atomicAdd(p.d_feats + (size_t)g * p.N + c, v[j]);
+    const int r = 32 * (warp & 3) + lane;  // channel row: channels NMB r .. NMB r + NMB - 1
+    const int g0 = 8 * (warp >> 2);
+    float v[NMB][8];
+    const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)buf * dcols + (uint32_t)g0;
+#pragma unroll
+    for (int mb = 0; mb < NMB; ++mb) tmem_ld8(ta + (uint32_t)(mb * kTbG), v[mb]);
+    tmem_wait_ld<NMB>(v);
+    const uint32_t msk = S.nz[slot] >> g0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (!((msk >> j) & 1u)) continue;
+      float* dst = p.d_feats + (size_t)S.gid[slot][g0 + j] * N + NMB * r;
+      if constexpr (NMB == 4) {
+        atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[0][j], v[1][j], v[2][j], v[3][j]));
+      } else if constexpr (NMB == 2) {
+        atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0][j], v[1][j]));
+      } else {
+#pragma unroll
+        for (int mb = 0; mb < NMB; ++mb) atomicAdd(dst + mb, v[mb][j]);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -533,20 +619,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
 
   for (int b = 0; b < nb && ok; ++b) {
     const int buf = b & 1, slot = b % 3;
-    // next block's records (slot (b+1)%3 was last read by the epilogue of
-    // block b-2, which finished in the previous iteration)
-    TbRecord nxt;
-    const bool fetch = b + 1 < nb && tid < kTbG;
-    if (fetch) nxt = tb_fetch(p, b + 1, rg, maxlast);
+    // stage block b+1's records (slot (b+1)%3 was last read by the epilogue of
+    // block b-2, which finished in the previous iteration); fetch the ids of b+2
+    if (b + 1 < nb && tid < kTbG) {
+      tb_issue(p, S, (b + 1) % 3, b + 1, rg, maxlast, next_id);
+      if (b + 2 < nb) next_id = tb_fetch_id(p, b + 2, rg, maxlast);
+    }
     // weights of my 8 Gaussians (one 16-byte row of B)
     float a[8];
     float prod = 1.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       a[j] = 0.f;
-      const int k = 8 * q + j;
+      const int k = 8 * q + j, ks = rec_slot(k);
       PairAlpha pa;
-      if (b * kTbG + k < last && pair_alpha(S.co[slot][k], S.uv[slot][k].x - pxc, S.uv[slot][k].y - pyc, pa)) {
+      if (b * kTbG + k < last && pair_alpha(S.co[slot][ks], S.uv[slot][ks].x - pxc, S.uv[slot][ks].y - pyc, pa)) {
         a[j] = pa.alpha;
         prod = __fmul_rn(prod, __fsub_rn(1.f, pa.alpha));
       }
@@ -561,18 +648,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
     const float total = __shfl_sync(0xffffffffu, incl, 3, 4);
     float Tj = __fmul_rn(T, excl);
     uint32_t packed[4];
+    uint32_t mine = 0u;
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
       const float w0 = __fmul_rn(a[j], Tj);
       if (a[j] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j]));
       const float w1 = __fmul_rn(a[j + 1], Tj);
       if (a[j + 1] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j + 1]));
-      if (w0 != 0.f) S.nz[slot][8 * q + j] = 1;
-      if (w1 != 0.f) S.nz[slot][8 * q + j + 1] = 1;
+      if (w0 != 0.f) mine |= 1u << (8 * q + j);
+      if (w1 != 0.f) mine |= 1u << (8 * q + j + 1);
       const __nv_bfloat162 b2 = __floats2bfloat162_rn(w0, w1);
       packed[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
     }
     T = __fmul_rn(T, total);
+    const uint32_t wmask = __reduce_or_sync(0xffffffffu, mine);
+    if (lane == 0 && wmask) atomicOr(&S.nz[slot], wmask);
     *reinterpret_cast<uint4*>(S.B[buf] + q * 128 + (m >> 3) * 512 + (m & 7) * 16) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -581,7 +671,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a0 = smem_u32(S.A), b0 = smem_u32(S.B[buf]);
       const uint32_t idesc = idesc_bf16(kTcPix, kTbG, 1);
-      for (int mb = 0; mb < nmb; ++mb) {
+#pragma unroll
+      for (int mb = 0; mb < NMB; ++mb) {
 #pragma unroll
         for (int k16 = 0; k16 < kTcPix / 16; ++k16) {
           const uint64_t ad = smem_desc(a0 + (uint32_t)mb * 16u * 2048u + (uint32_t)k16 * 256u, 128, 2048);
@@ -598,18 +689,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
           smem_u32(&S.mbar[buf])));
     }
     last_issued = b;
-    if (fetch) tb_store(S, (b + 1) % 3, nxt);
     if (b >= 1) ok = epilogue(b - 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
   }
   if (ok && nb > 0) ok = epilogue(nb - 1);
   if (!ok) {
     if (tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
     if (last_issued >= 0) mbar_wait(smem_u32(&S.mbar[last_issued & 1]), (uint32_t)((last_issued >> 1) & 1));
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+}
+
+template <int NMB>
+gs_status launch_bwd_nmb(const TcBwdParams& p, const CamF& cam, cudaStream_t st) {
+  const size_t smem = sizeof(TbSmem) + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_render_feat_tc_bwd<NMB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return GS_ERR_CUDA;
+    attr_set = true;
+  }
+  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2);
+  GS_TRACE("k_render_feat_tc_bwd", st);
+  k_render_feat_tc_bwd<NMB><<<blocks, kTcThreads, smem, st>>>(p);
+  return last_launch_status();
 }
 
 }  // namespace
@@ -618,6 +726,8 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, cons
                                     const float* co, const int32_t* last_idx, const float* g_feat, int N,
                                     float* d_feats, int32_t* status, cudaStream_t st) {
   if (N <= 0 || N % 128 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
+  // the vector atomics of the epilogue need NMB * 4-byte alignment of every row
+  if ((reinterpret_cast<uintptr_t>(d_feats) & 15u) != 0) return GS_ERR_INVALID_ARG;
   TcBwdParams p;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
@@ -632,18 +742,12 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, cons
   p.tmem_cols = cols;
   p.d_feats = d_feats;
   p.status = status;
-  const size_t smem = sizeof(TbSmem) + 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(k_render_feat_tc_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return GS_ERR_CUDA;
-    attr_set = true;
+  switch (N / 128) {
+    case 1: return launch_bwd_nmb<1>(p, cam, st);
+    case 2: return launch_bwd_nmb<2>(p, cam, st);
+    case 3: return launch_bwd_nmb<3>(p, cam, st);
+    default: return launch_bwd_nmb<4>(p, cam, st);
   }
-  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2);
-  GS_TRACE("k_render_feat_tc_bwd", st);
-  k_render_feat_tc_bwd<<<blocks, kTcThreads, smem, st>>>(p);
-  return last_launch_status();
 }
 
 
