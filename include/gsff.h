@@ -103,7 +103,10 @@ gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const 
  *      end) into gids, (0,0) if empty; n_instances (device int64) = I.
  * If I > capacity, GS_ERR_CAPACITY is flagged in *status and the lists are
  * truncated (contents unspecified). workspace must hold
- * gs_bin_sort_workspace_bytes(P, capacity, num_tiles) bytes.
+ * gs_bin_sort_workspace_bytes(P, capacity, num_tiles) bytes (0 is returned
+ * for sizes out of range); the caller need not clear it. Each radix pass
+ * waits for earlier chunks' digit counts with a bounded wait: a wait longer
+ * than 1 s flags GS_ERR_TIMEOUT (the lists are then unspecified).
  */
 size_t gs_bin_sort_workspace_bytes(int32_t P, int64_t capacity, int32_t num_tiles);
 gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
@@ -125,13 +128,15 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
  * caller workspace. It calls no allocator. Every device that loads the
  * library holds that array until the process exits.
  * Limit: gs_bin_sort_workspace_bytes(P, capacity, num_tiles) must not exceed
- * GS_BIN_SORT_STATIC_SCRATCH_BYTES (about 2.4 million instances of capacity
- * with 300,000 Gaussians: 12 bytes per instance plus 16 per Gaussian);
+ * GS_BIN_SORT_STATIC_SCRATCH_BYTES (about 1.96 million instances of capacity
+ * with 300,000 Gaussians and up to 65,536 tiles: 14 bytes per instance plus
+ * 20 per Gaussian);
  * larger sizes return GS_ERR_INVALID_ARG and launch nothing.
  * The first call on a device looks up the array's device address with that
  * device current (a CUDA runtime query); make that first call before any
  * stream capture. All calls share the one array and it keeps the previous
- * call's contents (the sort needs none of it zeroed): calls whose work
+ * call's contents (the caller zeroes nothing: the sort clears the counters
+ * it needs with a memset node on its stream): calls whose work
  * overlaps on the GPU (several streams or host threads) race on the array and
  * must be serialised by the caller.
  */

@@ -15,7 +15,7 @@ void launch_project(const CamF& cam, int P, const float* means, const float* sca
 void launch_project_bwd(const CamF& cam, int P, const float* means, const float* scales, const float* quats,
                         const float* d_uv, const float* d_conic, const float* d_depth, float* d_means,
                         float* d_scales, float* d_quats, float* d_pose, cudaStream_t st);
-size_t bin_sort_workspace_bytes(int P, long long capacity);
+size_t bin_sort_workspace_bytes(int P, long long capacity, int num_tiles);
 gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int32_t* rect, const int32_t* touched,
                           long long capacity, void* workspace, unsigned long long* keys, uint32_t* gids,
                           int32_t* ranges, int64_t* n_out, int32_t* status, cudaStream_t st);
@@ -137,9 +137,9 @@ gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const 
   return last_launch_status();
 }
 
-size_t gs_bin_sort_workspace_bytes(int32_t P, int64_t capacity, int32_t) {
-  if (P < 0 || capacity < 0) return 0;
-  return bin_sort_workspace_bytes(P, capacity);
+size_t gs_bin_sort_workspace_bytes(int32_t P, int64_t capacity, int32_t num_tiles) {
+  if (P < 0 || capacity < 0 || num_tiles < 1 || num_tiles > (1 << 24)) return 0;
+  return bin_sort_workspace_bytes(P, capacity, num_tiles);
 }
 
 gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
@@ -153,7 +153,7 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
   if (!aligned(workspace, 256) || !aligned(keys, 8) || !aligned(rect, 16) || !aligned(tile_ranges, 8) ||
       !aligned(n_instances, 8))
     return GS_ERR_INVALID_ARG;
-  if (workspace_bytes < bin_sort_workspace_bytes(P, capacity)) return GS_ERR_INVALID_ARG;
+  if (workspace_bytes < bin_sort_workspace_bytes(P, capacity, num_tiles(cam))) return GS_ERR_INVALID_ARG;
   return launch_bin_sort(make_cam(*cam), P, depth, rect, tiles_touched, capacity, workspace,
                          reinterpret_cast<unsigned long long*>(keys), gids, tile_ranges, n_instances, status,
                          S(stream));

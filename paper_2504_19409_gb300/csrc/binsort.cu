@@ -15,12 +15,20 @@
 // enqueued without a host round trip (grids are sized from P and the
 // caller's capacity; idle blocks exit).
 //
-// One LSD pass over (u32 key, u32 value) pairs = three kernels:
-//   k_rs_count   per 2048-key chunk, digit counts (per warp, then per chunk)
-//   k_rs_scan    exclusive offsets for (chunk, digit), coalesced, one block
-//   k_rs_scatter stable scatter: each warp owns 256 consecutive keys, ranks
-//                equal digits with __match_any_sync in index order; warps and
-//                chunks are offset by the exclusive prefix sums.
+// One LSD pass over (u32 key, u32 value) pairs is a single kernel in the
+// one-sweep style (a decoupled look-back across chunks):
+//   - the digit counts of every pass are accumulated up front by the kernel
+//     that writes the keys (k_depth_keys for the depth passes, k_emit for the
+//     tile passes), so a pass knows where each digit starts globally;
+//   - k_os_scatter: a block takes the next chunk of 2048 items by an atomic
+//     ticket (chunks start in order), counts its digits, publishes the counts,
+//     and sums its predecessors' counts per digit by walking back until a
+//     chunk that has published its inclusive prefix; then scatters stably
+//     (each warp owns 256 consecutive items and ranks equal digits with
+//     __match_any_sync in index order). A block only waits on chunks with
+//     earlier tickets, which are already running; every wait is bounded and
+//     a timeout flags GS_ERR_TIMEOUT instead of hanging.
+// The look-back words and the counters are cleared by one memset per frame.
 
 #include "gsff_internal.cuh"
 
@@ -39,6 +47,39 @@ struct SortCtrl {
   long long n_eff;      // min(I, capacity)
   long long n_gauss;    // P
 };
+
+constexpr int kDepthPasses = 4;
+constexpr int kMaxTilePasses = 3;  // tile ids < 2^24
+constexpr int kMaxPasses = kDepthPasses + kMaxTilePasses;
+
+// Per-frame one-sweep state (zeroed by a memset before the first kernel).
+struct OsCtrl {
+  uint32_t hist[kMaxPasses][kRadix];  // digit counts of each pass over all items
+  uint32_t ticket[kMaxPasses];        // next chunk of each pass
+};
+
+// Look-back word of (chunk, digit): state in the top two bits, count below.
+constexpr unsigned long long kLbAggregate = 1ull << 62;  // this chunk's own count
+constexpr unsigned long long kLbPrefix = 2ull << 62;     // count of this and all earlier chunks
+constexpr unsigned long long kLbCount = (1ull << 62) - 1;
+constexpr unsigned long long kLbWaitNs = 1000000000ull;  // 1 s
+constexpr int kLbWindow = 8;  // look-back words loaded per round trip
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& total) {
   // blockDim.x threads (a multiple of 32, <= 1024); returns the exclusive prefix of v.
@@ -68,14 +109,45 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& tot
 }
 
 // ---- step 1: depth keys ------------------------------------------------------
-__global__ void __launch_bounds__(256) k_depth_keys(int P, const float* __restrict__ depth,
-                                                    const int* __restrict__ touched, uint32_t* __restrict__ dk,
-                                                    uint32_t* __restrict__ dv, SortCtrl* __restrict__ ctrl) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g == 0) ctrl->n_gauss = P;
-  if (g < P) {
-    dk[g] = touched[g] > 0 ? __float_as_uint(depth[g]) : 0xFFFFFFFFu;
-    dv[g] = (uint32_t)g;
+// One block per kRsChunk Gaussians. Culled Gaussians get the largest key. The
+// block also adds its digit counts for the four depth passes to the frame's
+// histograms (culled keys are 0xFFFFFFFF: digit 255 in every pass).
+__global__ void __launch_bounds__(kRsThreads) k_depth_keys(int P, const float* __restrict__ depth,
+                                                           const int* __restrict__ touched, uint32_t* __restrict__ dk,
+                                                           uint32_t* __restrict__ dv, SortCtrl* __restrict__ ctrl,
+                                                           OsCtrl* __restrict__ os) {
+  __shared__ uint32_t s_h[kDepthPasses][kRadix];
+  __shared__ uint32_t s_cull;
+  for (int i = threadIdx.x; i < kDepthPasses * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  if (threadIdx.x == 0) s_cull = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->n_gauss = P;
+  __syncthreads();
+  const int base = blockIdx.x * kRsChunk;
+  uint32_t ncull = 0;
+#pragma unroll
+  for (int r = 0; r < kRsItems; ++r) {
+    const int g = base + r * kRsThreads + threadIdx.x;
+    bool culled = false;
+    if (g < P) {
+      const bool vis = touched[g] > 0;
+      const uint32_t key = vis ? __float_as_uint(depth[g]) : 0xFFFFFFFFu;
+      dk[g] = key;
+      dv[g] = (uint32_t)g;
+      if (vis) {
+#pragma unroll
+        for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & (kRadix - 1)], 1u);
+      }
+      culled = !vis;
+    }
+    ncull += __popc(__ballot_sync(0xffffffffu, culled));
+  }
+  if ((threadIdx.x & 31) == 0 && ncull) atomicAdd(&s_cull, ncull);
+  __syncthreads();
+  const int d = threadIdx.x;
+#pragma unroll
+  for (int p = 0; p < kDepthPasses; ++p) {
+    const uint32_t v = s_h[p][d] + (d == kRadix - 1 ? s_cull : 0u);
+    if (v) atomicAdd(&os->hist[p][d], v);
   }
 }
 
@@ -144,7 +216,9 @@ __global__ void __launch_bounds__(1024) k_scan_top(int nchunks, long long* __res
 __global__ void __launch_bounds__(256) k_emit(int P, const uint32_t* __restrict__ order,
                                               const int* __restrict__ touched, const int4* __restrict__ rect,
                                               const long long* __restrict__ partial, int tiles_x, long long capacity,
-                                              uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals) {
+                                              int npass, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals,
+                                              OsCtrl* __restrict__ os) {
+  __shared__ uint32_t s_th[kMaxTilePasses][kRadix];  // digit counts of the written tile keys
   __shared__ int s_off[kScanChunk + 1];
   __shared__ uint32_t s_g[kScanChunk];
   __shared__ int4 s_rc[kScanChunk];
@@ -156,6 +230,7 @@ __global__ void __launch_bounds__(256) k_emit(int P, const uint32_t* __restrict_
     g = order[r];
     n = touched[g];
   }
+  for (int i = threadIdx.x; i < kMaxTilePasses * kRadix; i += blockDim.x) (&s_th[0][0])[i] = 0;
   s_g[threadIdx.x] = g;
   if (n > 0) s_rc[threadIdx.x] = rect[g];
   int total;
@@ -176,9 +251,16 @@ __global__ void __launch_bounds__(256) k_emit(int P, const uint32_t* __restrict_
     const int ty = rc.y + li / rw, tx = rc.x + li % rw;
     const long long o = base + i;
     if (o < capacity) {
-      tkeys[o] = (uint32_t)(ty * tiles_x + tx);
+      const uint32_t t = (uint32_t)(ty * tiles_x + tx);
+      tkeys[o] = t;
       vals[o] = s_g[lo];
+      for (int p = 0; p < npass; ++p) atomicAdd(&s_th[p][(t >> (8 * p)) & (kRadix - 1)], 1u);
     }
+  }
+  __syncthreads();
+  for (int p = 0; p < npass; ++p) {
+    const uint32_t v = s_th[p][threadIdx.x];
+    if (v) atomicAdd(&os->hist[kDepthPasses + p][threadIdx.x], v);
   }
 }
 
@@ -208,120 +290,95 @@ __device__ __forceinline__ void rs_load_and_count(const uint32_t* __restrict__ k
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kRsThreads) k_rs_count(const uint32_t* __restrict__ keys_in,
-                                                         const long long* __restrict__ n_ptr, int shift,
-                                                         uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_hist[kRsWarps][kRadix];
-  const long long n = *n_ptr;
-  const long long base = (long long)blockIdx.x * kRsChunk;
-  if (base >= n) return;
-  uint32_t k[kRsItems];
-  int d[kRsItems];
-  rs_load_and_count(keys_in, n, shift, base, k, d, s_hist);
-  uint32_t tot = 0;
-#pragma unroll
-  for (int w = 0; w < kRsWarps; ++w) tot += s_hist[w][threadIdx.x];
-  hist[(size_t)blockIdx.x * kRadix + threadIdx.x] = tot;  // block-major [chunk][digit]
-}
-
-// Exclusive offsets over (digit, chunk) in digit-major order, written back in
-// place into the block-major table. 1024 threads = 4 groups x 256 digits; a
-// group walks a contiguous quarter of the chunks (loads coalesced over digits).
-__global__ void __launch_bounds__(1024) k_rs_scan(const long long* __restrict__ n_ptr, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_part[4][kRadix];
-  __shared__ uint32_t s_warp[32];
-  const long long n = *n_ptr;
-  const int nact = (int)((n + kRsChunk - 1) / kRsChunk);
-  if (nact == 0) return;
-  const int d = threadIdx.x & (kRadix - 1), q = threadIdx.x >> 8;
-  const int per = (nact + 3) / 4;
-  const int b0 = min(nact, q * per), b1 = min(nact, b0 + per);
-  uint32_t sum = 0;
-#pragma unroll 8
-  for (int b = b0; b < b1; ++b) sum += hist[(size_t)b * kRadix + d];
-  s_part[q][d] = sum;
-  __syncthreads();
-  // digit totals and their exclusive scan (threads 0..255)
-  uint32_t total = 0;
-  if (threadIdx.x < kRadix) total = s_part[0][d] + s_part[1][d] + s_part[2][d] + s_part[3][d];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t x = total;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31 && wid < 8) s_warp[wid] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint32_t w = lane < 8 ? s_warp[lane] : 0;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
-      if (lane >= off) w += y;
-    }
-    if (lane < 8) s_warp[lane] = w;
-  }
-  __syncthreads();
-  __shared__ uint32_t s_base[kRadix];
-  if (threadIdx.x < kRadix) s_base[d] = (wid > 0 ? s_warp[wid - 1] : 0) + x - total;
-  __syncthreads();
-  uint32_t run = s_base[d];
-  for (int qq = 0; qq < q; ++qq) run += s_part[qq][d];
-  int b = b0;
-  for (; b + 8 <= b1; b += 8) {
-    uint32_t c[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) c[e] = hist[(size_t)(b + e) * kRadix + d];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      hist[(size_t)(b + e) * kRadix + d] = run;
-      run += c[e];
-    }
-  }
-  for (; b < b1; ++b) {
-    uint32_t* h = hist + (size_t)b * kRadix + d;
-    const uint32_t c = *h;
-    *h = run;
-    run += c;
-  }
-}
-
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint32_t* __restrict__ keys_in,
+// One pass: see the file comment. `hist` = this pass's digit counts over all
+// items, `ticket` its chunk counter, `lb` its look-back words [chunks][256].
+__global__ void __launch_bounds__(kRsThreads) k_os_scatter(const uint32_t* __restrict__ keys_in,
                                                            const uint32_t* __restrict__ vals_in,
                                                            uint32_t* __restrict__ keys_out,
                                                            uint32_t* __restrict__ vals_out,
                                                            const long long* __restrict__ n_ptr, int shift,
-                                                           const uint32_t* __restrict__ hist) {
+                                                           const uint32_t* __restrict__ hist, uint32_t* ticket,
+                                                           unsigned long long* lb, int32_t* __restrict__ status) {
   __shared__ uint32_t s_hist[kRsWarps][kRadix];
+  __shared__ int s_warp[32];
+  __shared__ uint32_t s_chunk;
+  if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const long long c = s_chunk;
   const long long n = *n_ptr;
-  const long long base = (long long)blockIdx.x * kRsChunk;
+  const long long base = c * kRsChunk;
   if (base >= n) return;
   uint32_t k[kRsItems];
   int d[kRsItems];
   rs_load_and_count(keys_in, n, shift, base, k, d, s_hist);
-  {
-    const int dg = threadIdx.x;
-    uint32_t run = hist[(size_t)blockIdx.x * kRadix + dg];
-#pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) {
-      const uint32_t c = s_hist[w][dg];
-      s_hist[w][dg] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
+  uint32_t v[kRsItems];  // values loaded before the look-back, so their latency overlaps it
 #pragma unroll
   for (int r = 0; r < kRsItems; ++r) {
     const long long idx = base + wid * (kRsItems * 32) + r * 32 + lane;
+    v[r] = idx < n ? vals_in[idx] : 0u;
+  }
+  const int dg = threadIdx.x;
+  uint32_t tot = 0;
+#pragma unroll
+  for (int w = 0; w < kRsWarps; ++w) tot += s_hist[w][dg];
+  unsigned long long* mine = lb + c * kRadix + dg;
+  lb_store(mine, (c == 0 ? kLbPrefix : kLbAggregate) | tot);
+  // where digit dg starts in the output: exclusive scan of the digit counts
+  int all;
+  const uint32_t start = (uint32_t)block_exclusive_scan((int)hist[dg], s_warp, all);
+  unsigned long long before = 0;  // items of digit dg in chunks 0..c-1
+  if (c > 0) {
+    // Walk back kLbWindow chunks per round trip: the words of chunks
+    // j, j-1, .. are loaded together and consumed newest first until a
+    // prefix; a chunk that has published nothing yet restarts the window
+    // at that chunk.
+    const unsigned long long t0 = globaltimer_ns();
+    long long j = c - 1;
+    while (true) {
+      unsigned long long w[kLbWindow];
+#pragma unroll
+      for (int e = 0; e < kLbWindow; ++e) w[e] = j - e >= 0 ? lb_load(lb + (j - e) * kRadix + dg) : kLbPrefix;
+      int e = 0;
+      bool done = false;
+#pragma unroll
+      for (; e < kLbWindow; ++e) {
+        const unsigned long long state = w[e] & ~kLbCount;
+        if (state == 0) break;
+        before += w[e] & kLbCount;
+        if (state == kLbPrefix) {
+          done = true;
+          break;
+        }
+      }
+      if (done) break;
+      j -= e;
+      if (e < kLbWindow && globaltimer_ns() - t0 > kLbWaitNs) {
+        flag_status(status, GS_ERR_TIMEOUT);
+        break;
+      }
+    }
+    lb_store(mine, kLbPrefix | (before + tot));
+  }
+  {
+    uint32_t run = start + (uint32_t)before;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) {
+      const uint32_t cnt = s_hist[w][dg];
+      s_hist[w][dg] = run;
+      run += cnt;
+    }
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kRsItems; ++r) {
     const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
     if (d[r] < kRadix) {
       const uint32_t pos = s_hist[wid][d[r]] + __popc(peers & lt);
       if ((long long)pos < n) {
         keys_out[pos] = k[r];
-        vals_out[pos] = vals_in[idx];
+        vals_out[pos] = v[r];
       }
     }
     __syncwarp();
@@ -346,11 +403,18 @@ __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict_
 }
 
 struct SortLayout {
-  size_t dk, dv, dk2, dv2, partial, hist, ctrl, tk_alt, tv_alt, tk, total;
-  int nscan, nblk_p, nblk_i;
+  size_t dk, dv, dk2, dv2, partial, os, lb, ctrl, tk_alt, tv_alt, tk, total;
+  size_t lb_bytes;   // look-back words of all passes (zeroed each frame with os)
+  int nscan, nblk_p, nblk_i, npass_t;
 };
 
-SortLayout sort_layout(int P, long long capacity) {
+int tile_bits(int num_tiles) {
+  int b = 1;
+  while ((1 << b) < num_tiles) ++b;
+  return b;
+}
+
+SortLayout sort_layout(int P, long long capacity, int num_tiles) {
   SortLayout L;
   L.nscan = (P + kScanChunk - 1) / kScanChunk;
   if (L.nscan < 1) L.nscan = 1;
@@ -358,7 +422,7 @@ SortLayout sort_layout(int P, long long capacity) {
   if (L.nblk_p < 1) L.nblk_p = 1;
   L.nblk_i = (int)((capacity + kRsChunk - 1) / kRsChunk);
   if (L.nblk_i < 1) L.nblk_i = 1;
-  const int nblk = L.nblk_p > L.nblk_i ? L.nblk_p : L.nblk_i;
+  L.npass_t = (tile_bits(num_tiles) + 7) / 8;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -370,8 +434,11 @@ SortLayout sort_layout(int P, long long capacity) {
   L.dk2 = take((size_t)P * 4);
   L.dv2 = take((size_t)P * 4);
   L.partial = take((size_t)L.nscan * 8);
-  L.hist = take((size_t)kRadix * nblk * 4);
   L.ctrl = take(sizeof(SortCtrl));
+  // os and lb are adjacent: one memset clears both
+  L.lb_bytes = ((size_t)kDepthPasses * L.nblk_p + (size_t)L.npass_t * L.nblk_i) * kRadix * 8;
+  L.os = take(sizeof(OsCtrl));
+  L.lb = take(L.lb_bytes);
   L.tk = take((size_t)capacity * 4);
   L.tk_alt = take((size_t)capacity * 4);
   L.tv_alt = take((size_t)capacity * 4);
@@ -379,63 +446,54 @@ SortLayout sort_layout(int P, long long capacity) {
   return L;
 }
 
-int tile_bits(int num_tiles) {
-  int b = 1;
-  while ((1 << b) < num_tiles) ++b;
-  return b;
-}
-
-void radix_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, const long long* n_ptr,
-                int shift, int nblk, uint32_t* hist, cudaStream_t st) {
-  {
-    GS_TRACE("k_rs_count", st);
-    k_rs_count<<<nblk, kRsThreads, 0, st>>>(kin, n_ptr, shift, hist);
-  }
-  {
-    GS_TRACE("k_rs_scan", st);
-    k_rs_scan<<<1, 1024, 0, st>>>(n_ptr, hist);
-  }
-  {
-    GS_TRACE("k_rs_scatter", st);
-    k_rs_scatter<<<nblk, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_ptr, shift, hist);
-  }
+void os_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, const long long* n_ptr,
+             int shift, int pass, int nblk, OsCtrl* os, unsigned long long* lb, int32_t* status, cudaStream_t st) {
+  GS_TRACE("k_os_scatter", st);
+  k_os_scatter<<<nblk, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_ptr, shift, os->hist[pass], &os->ticket[pass],
+                                            lb, status);
 }
 
 }  // namespace
 
-size_t bin_sort_workspace_bytes(int P, long long capacity) { return sort_layout(P, capacity).total; }
+size_t bin_sort_workspace_bytes(int P, long long capacity, int num_tiles) {
+  return sort_layout(P, capacity, num_tiles).total;
+}
 
 // Enqueues the whole binning on `st`. The workspace base must be 256-aligned.
 // keys64 may be null (the 64-bit keys are then not written).
 gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int32_t* rect, const int32_t* touched,
                           long long capacity, void* workspace, unsigned long long* keys64, uint32_t* gids,
                           int32_t* ranges, int64_t* n_out, int32_t* status, cudaStream_t st) {
-  const SortLayout L = sort_layout(P, capacity);
+  const int num_tiles = cam.tiles_x * cam.tiles_y;
+  const SortLayout L = sort_layout(P, capacity, num_tiles);
+  if (L.npass_t > kMaxTilePasses) return GS_ERR_INVALID_ARG;
   char* ws = static_cast<char*>(workspace);
   auto* dk = reinterpret_cast<uint32_t*>(ws + L.dk);
   auto* dv = reinterpret_cast<uint32_t*>(ws + L.dv);
   auto* dk2 = reinterpret_cast<uint32_t*>(ws + L.dk2);
   auto* dv2 = reinterpret_cast<uint32_t*>(ws + L.dv2);
   auto* partial = reinterpret_cast<long long*>(ws + L.partial);
-  auto* hist = reinterpret_cast<uint32_t*>(ws + L.hist);
   auto* ctrl = reinterpret_cast<SortCtrl*>(ws + L.ctrl);
+  auto* os = reinterpret_cast<OsCtrl*>(ws + L.os);
+  auto* lb = reinterpret_cast<unsigned long long*>(ws + L.lb);
   auto* tk = reinterpret_cast<uint32_t*>(ws + L.tk);
   auto* tk_alt = reinterpret_cast<uint32_t*>(ws + L.tk_alt);
   auto* tv_alt = reinterpret_cast<uint32_t*>(ws + L.tv_alt);
-  const int num_tiles = cam.tiles_x * cam.tiles_y;
   const long long* n_gauss = &ctrl->n_gauss;
   const long long* n_inst = &ctrl->n_eff;
+  const size_t lb_pass_p = (size_t)L.nblk_p * kRadix, lb_pass_i = (size_t)L.nblk_i * kRadix;
 
   if (cudaMemsetAsync(ranges, 0, (size_t)num_tiles * 2 * sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaMemsetAsync(os, 0, (L.lb - L.os) + L.lb_bytes, st) != cudaSuccess) return GS_ERR_CUDA;
   {
     GS_TRACE("k_depth_keys", st);
-    k_depth_keys<<<(P + 255) / 256 > 0 ? (P + 255) / 256 : 1, 256, 0, st>>>(P, depth, touched, dk, dv, ctrl);
+    k_depth_keys<<<L.nblk_p, kRsThreads, 0, st>>>(P, depth, touched, dk, dv, ctrl, os);
   }
   // 1. depth sort: 4 passes, ending in (dk, dv)
-  radix_pass(dk, dv, dk2, dv2, n_gauss, 0, L.nblk_p, hist, st);
-  radix_pass(dk2, dv2, dk, dv, n_gauss, 8, L.nblk_p, hist, st);
-  radix_pass(dk, dv, dk2, dv2, n_gauss, 16, L.nblk_p, hist, st);
-  radix_pass(dk2, dv2, dk, dv, n_gauss, 24, L.nblk_p, hist, st);
+  os_pass(dk, dv, dk2, dv2, n_gauss, 0, 0, L.nblk_p, os, lb, status, st);
+  os_pass(dk2, dv2, dk, dv, n_gauss, 8, 1, L.nblk_p, os, lb + lb_pass_p, status, st);
+  os_pass(dk, dv, dk2, dv2, n_gauss, 16, 2, L.nblk_p, os, lb + 2 * lb_pass_p, status, st);
+  os_pass(dk2, dv2, dk, dv, n_gauss, 24, 3, L.nblk_p, os, lb + 3 * lb_pass_p, status, st);
   // 2. scan + emission in depth order
   {
     GS_TRACE("k_scan_partials", st);
@@ -446,7 +504,7 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
     k_scan_top<<<1, 1024, 0, st>>>(L.nscan, partial, capacity, ctrl, reinterpret_cast<long long*>(n_out), status);
   }
   // 3. tile sort: passes ping-pong so that the last one lands in (tk, gids)
-  const int npass = (tile_bits(num_tiles) + 7) / 8;
+  const int npass = L.npass_t;
   uint32_t* kb[2];
   uint32_t* vb[2];
   if (npass % 2 == 0) {
@@ -457,10 +515,12 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   {
     GS_TRACE("k_emit", st);
     k_emit<<<L.nscan, 256, 0, st>>>(P, dv, touched, reinterpret_cast<const int4*>(rect), partial, cam.tiles_x,
-                                    capacity, kb[0], vb[0]);
+                                    capacity, npass, kb[0], vb[0], os);
   }
+  unsigned long long* lb_t = lb + kDepthPasses * lb_pass_p;
   for (int p = 0; p < npass; ++p)
-    radix_pass(kb[p & 1], vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], n_inst, 8 * p, L.nblk_i, hist, st);
+    os_pass(kb[p & 1], vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], n_inst, 8 * p, kDepthPasses + p, L.nblk_i, os,
+            lb_t + p * lb_pass_i, status, st);
   {
     GS_TRACE("k_tile_ranges", st);
     int nb = (int)((capacity + 255) / 256);

@@ -16,7 +16,7 @@ static __device__ __align__(256) unsigned char g_bin_sort_scratch[GS_BIN_SORT_ST
 
 namespace gsff {
 
-size_t bin_sort_workspace_bytes(int P, long long capacity);
+size_t bin_sort_workspace_bytes(int P, long long capacity, int num_tiles);
 gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int32_t* rect, const int32_t* touched,
                           long long capacity, void* workspace, unsigned long long* keys, uint32_t* gids,
                           int32_t* ranges, int64_t* n_out, int32_t* status, cudaStream_t st);
@@ -57,11 +57,14 @@ extern "C" gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const f
   if (!aligned(keys, 8) || !aligned(rect, 16) || !aligned(tile_ranges, 8) || !aligned(n_instances, 8))
     return GS_ERR_INVALID_ARG;
   // The sizes must fit the fixed scratch array.
-  if (bin_sort_workspace_bytes(P, capacity) > (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES) return GS_ERR_INVALID_ARG;
+  const CamF k = make_cam(*cam);
+  if ((long long)k.tiles_x * k.tiles_y > (1 << 24)) return GS_ERR_INVALID_ARG;
+  if (bin_sort_workspace_bytes(P, capacity, k.tiles_x * k.tiles_y) > (size_t)GS_BIN_SORT_STATIC_SCRATCH_BYTES)
+    return GS_ERR_INVALID_ARG;
   void* scratch = nullptr;
   const gs_status st = scratch_address(&scratch);
   if (st != GS_OK) return st;
-  return launch_bin_sort(make_cam(*cam), P, depth, rect, tiles_touched, capacity, scratch,
+  return launch_bin_sort(k, P, depth, rect, tiles_touched, capacity, scratch,
                          reinterpret_cast<unsigned long long*>(keys), gids, tile_ranges, n_instances, status,
                          static_cast<cudaStream_t>(stream));
 }
