@@ -217,10 +217,13 @@ def run_ours(args, rank, world, local_rank):
     ras.check_status()
 
     if args.profile:
-        # plain frames only (for profiler captures of the same launch shape)
+        # plain frames only (for profiler captures of the same launch shape),
+        # bracketed by cudaProfilerStart/Stop for `ncu --profile-from-start off`
+        torch.cuda.profiler.start()
         for i in range(args.steps):
             step(frames[args.warmup + i])
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         ras.check_status()
         return None
 
@@ -619,9 +622,11 @@ def run_forms(args):
 
         if args.profile:
             # plain frames of the tensor-core form only (for profiler captures)
+            torch.cuda.profiler.start()
             for k in frames:
                 fwd_bwd(tc)(k)
             torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
             tc.check_status()
             print("profile run done")
             return 0

@@ -186,6 +186,29 @@ def test_l1_loss_against_second_render(gs, ora, sg):
     check_grads(g["grads"], o["grads"], ("means", "scales", "quats", "opacity", "colors", "feats", "pose"))
 
 
+@pytest.mark.parametrize("offset,n", [(0, 1003), (1, 1003), (0, 4096), (3, 5)])
+def test_l1_loss_vector_and_scalar_paths(gs, offset, n):
+    """gs_l1_loss_grad on 16-byte-aligned arrays (float4 body + scalar tail)
+    and on arrays shifted by `offset` floats (scalar path): the same signs,
+    exactly, and the same loss."""
+    rng = np.random.default_rng(7 + offset + n)
+    p_ = rng.normal(size=n + offset).astype(np.float32)
+    t_ = rng.normal(size=n + offset).astype(np.float32)
+    t_[offset::7] = p_[offset::7]  # exact ties give a zero gradient
+    P, T = _t(p_), _t(t_)
+    G = torch.full((n + offset,), 5.0, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    scale = 0.25
+    gs.l1_loss_grad(P[offset:], T[offset:], scale, grad=G[offset:], loss=loss)
+    torch.cuda.synchronize()
+    want = (np.sign(p_[offset:] - t_[offset:]) * np.float32(scale)).astype(np.float32)
+    got = G.cpu().numpy()
+    assert np.array_equal(got[offset:], want)
+    assert (got[:offset] == 5.0).all()
+    ref = float(np.abs(p_[offset:].astype(np.float64) - t_[offset:]).sum()) * scale
+    assert abs(loss.item() - ref) <= 1e-5 * max(ref, 1e-6)
+
+
 # ---- differentiation case: 500 Gaussians at 64x48, N=64 (two 32-channel chunks) --
 
 @pytest.mark.parametrize("coupled", [False, True])
