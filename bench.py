@@ -391,6 +391,9 @@ def main():
                          "channels, tensor-core vs plain fp32; decoder: latent render + learned decoder vs both")
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--gaussians", type=int, default=0, help="override the Gaussian count of --workload wide/decoder")
+    ap.add_argument("--features", default="", choices=["", "unit", "prototypes"],
+                    help="feature set of --workload wide/decoder: i.i.d. unit-norm vectors or class prototypes "
+                         "(defaults: unit for wide, prototypes for decoder)")
     ap.add_argument("--profile", action="store_true",
                     help="setup, warm-up and --steps plain frames only (no timing, no JSON); for profiler captures")
     args = ap.parse_args()
@@ -577,7 +580,7 @@ def run_forms(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     peaks = _peaks()
-    kind = "unit" if args.workload == "wide" else "prototypes"
+    kind = args.features or ("unit" if args.workload == "wide" else "prototypes")
     sc = sg.room_scene(6, P_WIDE, N_WIDE, feat_kind=kind)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     scene = tuple(t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
