@@ -157,20 +157,35 @@ gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const float* depth
  *      out_feat [N,H,W] (layout CHW) or [H,W,N] (HWC), only with GS_FEAT_ON;
  *      T_final [H,W]; last_idx [H,W] = list position (from the tile's start)
  *      of the last blended Gaussian + 1; n_contrib [H,W] = blended count.
+ * visible [P] (u8, may be NULL): set to 1 for every Gaussian blended at some
+ *      pixel with T > 0.5 in front of it (the visibility V_id of the keyframe
+ *      selection, Sec. 3.2, Eq. 6); other entries are left unchanged, so the
+ *      caller zeroes the array (or keeps OR-ing frames into it).
  * feats [P,N] is float32 (GS_F32) or bfloat16 (GS_BF16); may be NULL with
  * GS_FEAT_OFF. bg: 3 host floats, NULL = black.
  * GS_FEAT_TENSOR_CORE (N % 64 == 0, N <= 512, GS_BF16, layout HWC): the
- * feature channels are computed per tile as the product of a 256 x K weight
- * matrix (w = alpha T, rounded to bf16) and the K x N bf16 feature rows on
- * tcgen05 tensor cores with fp32 accumulation.
+ * feature channels are computed per half tile as the product of a 128 x 32
+ * weight matrix per step of 32 Gaussians (w = alpha T, rounded to bf16) and
+ * the 32 x N bf16 feature rows on tcgen05 tensor cores, fp32 accumulation.
  */
 gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges,
                         const uint32_t* gids, const float* uv, const float* conic_opacity,
                         const float* depth, const float* colors, const void* feats, int32_t N,
                         int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
                         float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
-                        float* T_final, int32_t* last_idx, int32_t* n_contrib, int32_t* status,
-                        void* stream);
+                        float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
+                        int32_t* status, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * gs_visibility_iou -- co-visibility of two frames for keyframe selection
+ * (Sec. 3.2): counts[0] = |{g : a_g and b_g}|, counts[1] = |{g : a_g or b_g}|
+ * over two visibility vectors of gs_render_fwd (u8 [P], nonzero = visible).
+ * counts: 2 device int64, overwritten (cleared by a memset on the stream);
+ * IoU = counts[0] / counts[1]; a frame becomes a keyframe when its IoU with
+ * the last keyframe is below the caller's threshold.
+ */
+gs_status gs_visibility_iou(int32_t P, const uint8_t* vis_a, const uint8_t* vis_b, int64_t* counts,
+                            void* stream);
 
 /* ---------------------------------------------------------------------------
  * gs_render_bwd -- adjoint of gs_render_fwd and gs_project, plus the pose

@@ -124,6 +124,17 @@ def render_fwd(cam, ranges, gids, uv, conic, opacity, colors, depth, feats, bg=(
     return out
 
 
+def visibility(cam, ranges, gids, uv, conic, opacity):
+    """Per Gaussian, the largest transmittance in front of it over the pixels where it is blended
+    (0 where blended nowhere); visible in the keyframe sense (Sec. 3.2) when it exceeds 0.5."""
+    P = uv.shape[0]
+    out = np.zeros(P)
+    lib().ora_visibility(_p(cam_array(cam)), ctypes.c_int(cam.tiles_x), _p(np.ascontiguousarray(ranges, np.int32)),
+                         _p(np.ascontiguousarray(gids, np.int32)), _p(_f64(uv)), _p(_f64(conic)),
+                         _p(_f64(opacity)), ctypes.c_int(P), _p(out))
+    return out
+
+
 def render_bwd(cam, ranges, gids, uv, conic, opacity, colors, depth, feats, g_rgb=None, g_depth=None,
                g_alpha=None, g_feat=None, coupled=False, bg=(0.0, 0.0, 0.0)):
     P = uv.shape[0]

@@ -16,6 +16,9 @@
 //                        can be compared bit for bit.
 //   ora_bin              per-tile lists sorted by (tile, depth, id).
 //   ora_render_fwd       Eq. 2-3 front-to-back compositing in double.
+//   ora_visibility       per Gaussian, the largest transmittance in front of
+//                        it over the pixels where it is blended (Sec. 3.2:
+//                        visible when that transmittance exceeds 0.5).
 //   ora_render_bwd       adjoint of Eq. 2-3 per pixel from the stored list of
 //                        blended Gaussians (no division by 1-alpha).
 //   ora_project_bwd_f64  adjoint of the projection and the Lie-algebra pose
@@ -499,6 +502,37 @@ void ora_render_fwd(const double* cam, int tiles_x, const int32_t* ranges, const
           margin[pix] = mg;
         }
     }
+  }
+}
+
+// Keyframe visibility (Sec. 3.2): Gaussian g is visible in the frame when it
+// is blended at some pixel with transmittance T > 0.5 in front of it. maxT[g]
+// receives the largest such T over all pixels (0 if g is blended nowhere), so
+// visible = maxT > 0.5 and a caller can see how close each decision is.
+void ora_visibility(const double* cam, int tiles_x, const int32_t* ranges, const int32_t* gids,
+                    const double* uv, const double* conic, const double* opac, int P, double* maxT) {
+  const int W = (int)cam[0], H = (int)cam[1];
+  const int tiles_y = (H + kTile - 1) / kTile;
+  const int T = tiles_x * tiles_y;
+  for (int g = 0; g < P; ++g) maxT[g] = 0.0;
+#pragma omp parallel
+  {
+    std::vector<Blend> bl;
+    std::vector<double> mine((size_t)P, 0.0);
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < T; ++t) {
+      const int tx = t % tiles_x, ty = t / tiles_x;
+      const int s = ranges[2 * t], e = ranges[2 * t + 1];
+      for (int j = ty * kTile; j < std::min(H, (ty + 1) * kTile); ++j)
+        for (int i = tx * kTile; i < std::min(W, (tx + 1) * kTile); ++i) {
+          double Tf, mg;
+          int last;
+          walk_pixel(gids + s, e - s, i + 0.5, j + 0.5, uv, conic, opac, bl, Tf, last, mg);
+          for (const Blend& b : bl) mine[b.g] = std::max(mine[b.g], b.T);
+        }
+    }
+#pragma omp critical
+    for (int g = 0; g < P; ++g) maxT[g] = std::max(maxT[g], mine[g]);
   }
 }
 

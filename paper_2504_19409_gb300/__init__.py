@@ -35,7 +35,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_render_bwd_workspace_bytes", "gs_render_bwd", "gs_l1_loss_grad", "gs_trace_enable",
            "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
-           "gs_adam_step", "gs_decoder_fwd_tc")
+           "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou")
 
 
 class GsffError(RuntimeError):
@@ -92,8 +92,10 @@ def lib():
     L.gs_bin_sort.restype = ctypes.c_int
     L.gs_bin_sort_static.argtypes = [cam_p, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_bin_sort_static.restype = ctypes.c_int
-    L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 7 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 9)
+    L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 7 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)
     L.gs_render_fwd.restype = ctypes.c_int
+    L.gs_visibility_iou.argtypes = [_i32, _vp, _vp, _vp, _vp]
+    L.gs_visibility_iou.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
     L.gs_render_bwd_workspace_bytes.restype = _sz
     L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +
@@ -195,8 +197,10 @@ def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=
 
 
 def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT_CHW, bg=None, out=None,
-               status=None, stream=None):
-    """gs_render_fwd: returns dict(rgb [3,H,W], depth [H,W], alpha [H,W], feat, T_final, last_idx, n_contrib)."""
+               status=None, stream=None, visible=None):
+    """gs_render_fwd: returns dict(rgb [3,H,W], depth [H,W], alpha [H,W], feat, T_final, last_idx, n_contrib).
+    `visible` (uint8 [P], optional) receives 1 for every Gaussian blended with T > 0.5 in front of it;
+    the caller zeroes it."""
     H, W = cam.height, cam.width
     dev = colors.device
     P = colors.shape[0]
@@ -222,8 +226,18 @@ def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT
                                _ptr(feats) if feat_on else None, N if feat_on else 0, dtype, layout, flags,
                                ctypes.cast(bgc, _vp), _ptr(o["rgb"]), _ptr(o["depth"]), _ptr(o["alpha"]),
                                _ptr(o.get("feat")) if feat_on else None, _ptr(o["T_final"]), _ptr(o["last_idx"]),
-                               _ptr(o["n_contrib"]), _ptr(st), _stream(stream)), "gs_render_fwd")
+                               _ptr(o["n_contrib"]), _ptr(visible), _ptr(st), _stream(stream)), "gs_render_fwd")
     return o
+
+
+def visibility_iou(vis_a, vis_b, counts=None, stream=None):
+    """gs_visibility_iou: device int64 [2] = (|a and b|, |a or b|) of two uint8 visibility vectors."""
+    _need(vis_a, torch.uint8, "vis_a")
+    _need(vis_b, torch.uint8, "vis_b", vis_a.shape)
+    c = counts if counts is not None else torch.empty(2, dtype=torch.int64, device=vis_a.device)
+    _check(lib().gs_visibility_iou(vis_a.numel(), _ptr(vis_a), _ptr(vis_b), _ptr(c), _stream(stream)),
+           "gs_visibility_iou")
+    return c
 
 
 def render_bwd_workspace_bytes(P: int) -> int:
@@ -349,12 +363,12 @@ class Rasterizer:
             self._alloc_sort()
         return need
 
-    def forward(self, cam, means, scales, quats, opacity, colors, feats=None, bg=None, stream=None):
+    def forward(self, cam, means, scales, quats, opacity, colors, feats=None, bg=None, stream=None, visible=None):
         project(cam, means, scales, quats, opacity, out=self.proj, stream=stream)
         bin_sort(cam, self.proj, self.capacity, workspace=self.sort_ws, out=self.sort, status=self.status,
                  stream=stream)
         render_fwd(cam, self.proj, self.sort, colors, feats, flags=self.flags, layout=self.layout, bg=bg,
-                   out=self.fwd, status=self.status, stream=stream)
+                   out=self.fwd, status=self.status, stream=stream, visible=visible)
         return self.fwd
 
     def backward(self, cam, means, scales, quats, colors, feats=None, g_rgb=None, g_depth=None, g_alpha=None,

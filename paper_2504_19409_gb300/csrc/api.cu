@@ -23,7 +23,7 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
-                            int32_t* n_contrib, cudaStream_t st);
+                            int32_t* n_contrib, uint8_t* visible, cudaStream_t st);
 gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
@@ -109,6 +109,34 @@ __global__ void __launch_bounds__(256) k_l1_grad(long long n, const float* __res
   }
 }
 
+// counts[0] += |{g : a_g != 0 and b_g != 0}|, counts[1] += |{g : a_g != 0 or b_g != 0}|.
+__global__ void __launch_bounds__(256) k_vis_iou(int P, const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
+                                                 unsigned long long* __restrict__ counts) {
+  unsigned both = 0, either = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const bool x = a[i] != 0, y = b[i] != 0;
+    both += (x && y) ? 1u : 0u;
+    either += (x || y) ? 1u : 0u;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    both += __shfl_xor_sync(0xffffffffu, both, off);
+    either += __shfl_xor_sync(0xffffffffu, either, off);
+  }
+  __shared__ unsigned s_c[2][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_c[0][wid] = both;
+    s_c[1][wid] = either;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_c[threadIdx.x][w];
+    if (t) atomicAdd(counts + threadIdx.x, t);
+  }
+}
+
 bool cam_ok(const gs_camera* cam) {
   return cam && cam->width > 0 && cam->height > 0 && cam->width <= (1 << 15) && cam->height <= (1 << 15) &&
          cam->fx > 0.f && cam->fy > 0.f;
@@ -185,8 +213,8 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
                         const float* uv, const float* conic_opacity, const float* depth, const float* colors,
                         const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
                         const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
-                        float* T_final, int32_t* last_idx, int32_t* n_contrib, int32_t* status, void* stream) {
-  (void)status;
+                        float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
+                        int32_t* status, void* stream) {
   if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
   if (!tile_ranges || !gids || !out_rgb || !out_depth || !out_alpha || !T_final || !last_idx || !n_contrib)
     return GS_ERR_INVALID_ARG;
@@ -207,7 +235,8 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
     if (feat_dtype != GS_BF16 || layout != GS_LAYOUT_HWC || N % 64 != 0 || N > 512) return GS_ERR_UNSUPPORTED;
     // geometry channels and the saved state on the SIMT kernel, features on tcgen05
     gs_status st = launch_render_fwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, nullptr, 0, 0, 1, b,
-                                     out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, S(stream));
+                                     out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, visible,
+                                     S(stream));
     if (st != GS_OK) return st;
     return launch_render_fwd_tc(k, tile_ranges, gids, uv, conic_opacity,
                                 static_cast<const __nv_bfloat16*>(feats), last_idx, N, out_feat, status,
@@ -215,7 +244,7 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
   }
   return launch_render_fwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, n,
                            feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, out_rgb, out_depth, out_alpha, out_feat,
-                           T_final, last_idx, n_contrib, S(stream));
+                           T_final, last_idx, n_contrib, visible, S(stream));
 }
 
 size_t gs_render_bwd_workspace_bytes(int32_t P) {
@@ -289,6 +318,17 @@ gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, flo
   if (blocks > 152 * 16) blocks = 152 * 16;
   GS_TRACE("k_l1_grad", S(stream));
   k_l1_grad<<<(unsigned)blocks, 256, 0, S(stream)>>>(n, pred, target, scale, grad, loss_sum, vec);
+  return last_launch_status();
+}
+
+gs_status gs_visibility_iou(int32_t P, const uint8_t* vis_a, const uint8_t* vis_b, int64_t* counts, void* stream) {
+  if (P < 0 || !counts || !aligned(counts, 8) || (P > 0 && (!vis_a || !vis_b))) return GS_ERR_INVALID_ARG;
+  if (cudaMemsetAsync(counts, 0, 2 * sizeof(int64_t), S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+  if (P == 0) return GS_OK;
+  int blocks = (P + 1023) / 1024;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  GS_TRACE("k_vis_iou", S(stream));
+  k_vis_iou<<<blocks, 256, 0, S(stream)>>>(P, vis_a, vis_b, reinterpret_cast<unsigned long long*>(counts));
   return last_launch_status();
 }
 

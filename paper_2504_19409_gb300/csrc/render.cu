@@ -50,6 +50,7 @@ struct FwdParams {
   float* T_final;
   int* last_idx;
   int* n_contrib;
+  uint8_t* visible;  // [P] or null: set to 1 when blended with T > 0.5 in front (Sec. 3.2)
 };
 
 
@@ -134,7 +135,7 @@ __device__ __forceinline__ void load_feat_row(const void* feats, int bf16, int N
   }
 }
 
-template <int NC>
+template <int NC, bool VIS>
 __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   constexpr int NCs = NC > 0 ? NC : 1;
   __shared__ float2 s_uv[kTilePix];
@@ -142,10 +143,13 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   __shared__ float4 s_co[kTilePix];
   __shared__ float4 s_cd[kTilePix];
   __shared__ float s_f[kTilePix][NCs];
+  __shared__ uint32_t s_gid[VIS ? kTilePix : 1];
 
   const int tile = blockIdx.x;
   const int chunk = blockIdx.y;
   const bool geom = chunk == 0;
+  const bool mark = VIS && geom;
+  const unsigned lanes_below = (1u << (threadIdx.x & 31)) - 1u;
   const int c0 = chunk * NC;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
   int pxa[1], pya[1];
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
       s_uv[threadIdx.x] = p.uv[g];
       s_co[threadIdx.x] = co;
       s_ext[threadIdx.x] = warp_skip_extent(co, 3.5f, 1.5f);
+      if (VIS) s_gid[threadIdx.x] = g;
       if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
       if (NC > 0) load_feat_row<NCs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
     }
@@ -190,6 +195,10 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
           break;
         }
         const float w = __fmul_rn(pa.alpha, T);
+        if (mark && T > 0.5f) {
+          // visible (T in front > 0.5): the lowest lane of those here writes
+          if ((__activemask() & lanes_below) == 0) p.visible[s_gid[j]] = 1;
+        }
         if (geom) {
           const float4 cd = s_cd[j];
           ac0 = __fmaf_rn(w, cd.x, ac0);
@@ -480,7 +489,7 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
-                            int32_t* n_contrib, cudaStream_t st) {
+                            int32_t* n_contrib, uint8_t* visible, cudaStream_t st) {
   FwdParams p;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
@@ -501,14 +510,18 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
   p.T_final = T_final;
   p.last_idx = last_idx;
   p.n_contrib = n_contrib;
+  p.visible = visible;
   const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
   GS_TRACE("k_render_fwd", st);
-  if (N <= 0) {
-    k_render_fwd<0><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
-  } else if (N <= 16) {
-    k_render_fwd<16><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
+  const dim3 grid(tiles, N <= 16 ? 1 : (N + 31) / 32);
+  if (visible) {
+    if (N <= 0) k_render_fwd<0, true><<<grid, kTilePix, 0, st>>>(p);
+    else if (N <= 16) k_render_fwd<16, true><<<grid, kTilePix, 0, st>>>(p);
+    else k_render_fwd<32, true><<<grid, kTilePix, 0, st>>>(p);
   } else {
-    k_render_fwd<32><<<dim3(tiles, (N + 31) / 32), kTilePix, 0, st>>>(p);
+    if (N <= 0) k_render_fwd<0, false><<<grid, kTilePix, 0, st>>>(p);
+    else if (N <= 16) k_render_fwd<16, false><<<grid, kTilePix, 0, st>>>(p);
+    else k_render_fwd<32, false><<<grid, kTilePix, 0, st>>>(p);
   }
   return last_launch_status();
 }

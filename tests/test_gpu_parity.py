@@ -43,7 +43,8 @@ def _t(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
 
 
-def gpu_frame(gs, cam, sc, N=None, layout=0, bg=None, feat_bf16=False, grads=None, coupled=False, capacity=None):
+def gpu_frame(gs, cam, sc, N=None, layout=0, bg=None, feat_bf16=False, grads=None, coupled=False, capacity=None,
+              visible=False):
     """Run project -> bin_sort -> fwd (-> bwd) on the GPU; returns numpy dicts."""
     means, scales, quats, opac, cols = (_t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
     feats = None
@@ -52,9 +53,12 @@ def gpu_frame(gs, cam, sc, N=None, layout=0, bg=None, feat_bf16=False, grads=Non
     proj = gs.project(cam, means, scales, quats, opac)
     I = int(proj["n_instances"].item())
     srt = gs.bin_sort(cam, proj, capacity or max(I, 1))
-    fw = gs.render_fwd(cam, proj, srt, cols, feats, layout=layout, bg=bg, status=srt["status"])
+    vis = torch.zeros(sc.P, dtype=torch.uint8, device="cuda") if visible else None
+    fw = gs.render_fwd(cam, proj, srt, cols, feats, layout=layout, bg=bg, status=srt["status"], visible=vis)
     out = dict(I=I, proj={k: v.cpu().numpy() for k, v in proj.items()},
                sort={k: v.cpu().numpy() for k, v in srt.items()}, fwd={k: v.cpu().numpy() for k, v in fw.items()})
+    if visible:
+        out["visible"] = vis.cpu().numpy()
     if grads is not None:
         g_rgb, g_d, g_a, g_f = (None if x is None else _t(x) for x in grads)
         if g_f is not None and layout == 1:
@@ -320,7 +324,7 @@ def room_frame(gs, ora, sg):
     sc, _ = sg.room_case()
     cam = sg.room_trajectory(7).as_f32()
     cot = tuple(x.astype(np.float32) for x in sg.random_linear_functional(70, cam.height, cam.width, sc.N))
-    g = gpu_frame(gs, cam, sc, grads=cot)
+    g = gpu_frame(gs, cam, sc, grads=cot, visible=True)
     o = oracle_frame(ora, cam, sc, grads=tuple(x.astype(np.float64) for x in cot))
     return sc, cam, g, o
 
@@ -341,3 +345,62 @@ def test_room_scale_images(room_frame):
 def test_room_scale_gradients(room_frame):
     sc, cam, g, o = room_frame
     check_grads(g["grads"], o["grads"], ("means", "scales", "quats", "opacity", "colors", "feats", "pose"))
+
+
+# ---- keyframe visibility (Sec. 3.2, Eq. 6) and co-visibility IoU ----------------
+
+VIS_BAND = 1e-5  # relative distance of the oracle's max T from 0.5 below which a decision is not compared
+
+
+def check_visibility(ora, cam, sc, g, o, min_each=100):
+    maxT = ora.visibility(cam, o["ranges"], o["gids"], o["proj"]["uv"], o["proj"]["conic"], sc.opacity)
+    want = maxT > 0.5
+    sure = np.abs(maxT - 0.5) > VIS_BAND * 0.5
+    assert (~sure).sum() <= max(2, int(1e-4 * sc.P))
+    assert np.array_equal(g["visible"][sure] != 0, want[sure]), int(((g["visible"] != 0) != want)[sure].sum())
+    assert set(np.unique(g["visible"])) <= {0, 1}
+    assert want.sum() >= min_each and ((maxT > 0) & ~want).sum() >= min_each
+
+
+def test_small_case_visibility(gs, ora, sg):
+    """gs_render_fwd's visibility output (blended with T > 0.5 in front)
+    against the oracle's per-Gaussian max T: equal wherever the oracle's
+    decision is more than 1e-5 (relative) from the threshold."""
+    sc, cam = sg.small_case(seed=21)
+    cam = cam.as_f32()
+    g = gpu_frame(gs, cam, sc, visible=True)
+    o = oracle_frame(ora, cam, sc)
+    check_visibility(ora, cam, sc, g, o)
+
+
+def test_room_scale_visibility(ora, room_frame):
+    sc, cam, g, o = room_frame
+    check_visibility(ora, cam, sc, g, o, min_each=1000)
+
+
+def test_visibility_iou_counts(gs, sg):
+    """gs_visibility_iou against the definition (|a and b|, |a or b|) on the
+    visibility of two neighbouring SLAM-trajectory frames, plus the edge
+    cases: identical vectors, an empty vector, and P = 0."""
+    sc, _ = sg.room_case()
+    means, scales, quats, opac, cols = (_t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
+    ras = gs.Rasterizer(sc.P, 1200, 680, N=0)
+    vis = []
+    for k in (7, 12):
+        cam = sg.room_trajectory(k).as_f32()
+        ras.ensure_capacity(cam, means, scales, quats, opac)
+        v = torch.zeros(sc.P, dtype=torch.uint8, device="cuda")
+        ras.forward(cam, means, scales, quats, opac, cols, visible=v)
+        vis.append(v)
+    a, b = (v.cpu().numpy() != 0 for v in vis)
+    c = gs.visibility_iou(vis[0], vis[1]).cpu().numpy()
+    assert c[0] == int((a & b).sum()) and c[1] == int((a | b).sum())
+    assert 0.2 < c[0] / c[1] < 1.0
+    c = gs.visibility_iou(vis[0], vis[0]).cpu().numpy()
+    assert c[0] == c[1] == int(a.sum())
+    z = torch.zeros_like(vis[0])
+    c = gs.visibility_iou(z, vis[1]).cpu().numpy()
+    assert c[0] == 0 and c[1] == int(b.sum())
+    e = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    c = gs.visibility_iou(e, e).cpu().numpy()
+    assert c[0] == 0 and c[1] == 0

@@ -40,10 +40,14 @@ def _render(gs, cam, sc, flags):
     feats = _t(sc.feats, torch.bfloat16)
     proj = gs.project(cam, means, scales, quats, opac)
     srt = gs.bin_sort(cam, proj, max(int(proj["n_instances"].item()), 1))
-    fw = gs.render_fwd(cam, proj, srt, cols, feats, flags=flags, layout=gs.GS_LAYOUT_HWC, status=srt["status"])
+    vis = torch.zeros(sc.P, dtype=torch.uint8, device="cuda")
+    fw = gs.render_fwd(cam, proj, srt, cols, feats, flags=flags, layout=gs.GS_LAYOUT_HWC, status=srt["status"],
+                       visible=vis)
     torch.cuda.synchronize()
     assert int(srt["status"].item()) == 0
-    return {k: v.cpu().numpy() for k, v in fw.items()}
+    out = {k: v.cpu().numpy() for k, v in fw.items()}
+    out["visible"] = vis.cpu().numpy()
+    return out
 
 
 @pytest.mark.parametrize("N,shape,P,seed", [(512, (96, 64), 1500, 21), (128, (100, 37), 900, 22),
@@ -56,7 +60,7 @@ def test_tc_features_within_bound(gs, ora, sg, N, shape, P, seed):
     f_exact = _bf16_exact(sc.feats)
     tc = _render(gs, cam, sc, gs.GS_FEAT_ON | gs.GS_FEAT_TENSOR_CORE)
     plain = _render(gs, cam, sc, gs.GS_FEAT_ON)
-    for k in ("rgb", "depth", "alpha", "T_final", "last_idx", "n_contrib"):
+    for k in ("rgb", "depth", "alpha", "T_final", "last_idx", "n_contrib", "visible"):
         assert np.array_equal(tc[k], plain[k]), k
     pr = ora.project_b32(cam, sc.means, sc.scales, sc.quats, sc.opacity)
     ranges, gids = ora.bin_lists(cam, pr["rect"], pr["depth"])

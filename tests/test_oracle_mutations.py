@@ -41,6 +41,9 @@ MUTATIONS = {
         " std::make_tuple(std::get<0>(b), -std::get<1>(b), std::get<2>(b)); });"),
     "low-pass filter dropped": (
         "p.cov[0] = c2[0] + kLowPass;", "p.cov[0] = c2[0];"),
+    "visibility from T behind instead of in front": (
+        "for (const Blend& b : bl) mine[b.g] = std::max(mine[b.g], b.T);",
+        "for (const Blend& b : bl) mine[b.g] = std::max(mine[b.g], b.T * (1 - b.alpha));"),
 }
 
 

@@ -390,3 +390,78 @@ def test_stop_rule_closed_form(ora, sg):
     assert np.allclose(fw["T_final"][stop3], T2[stop3], rtol=1e-12)
     assert np.allclose(fw["rgb"][1][stop3], (al[1] * (1 - al[0]))[stop3], rtol=1e-12)
     assert np.allclose(fw["rgb"][2][stop3], 0.0)
+
+
+# ---- keyframe visibility (Sec. 3.2): blended somewhere with T > 0.5 in front --
+
+def test_visibility_behind_opaque_and_translucent_layer(ora, sg):
+    """A wide front Gaussian covers the whole 32x32 image with alpha_f(p),
+    a small one sits behind it on the axis. The largest transmittance in
+    front of the back one is max over its blended pixels of 1 - alpha_f(p):
+    exactly 1 - 0.99 when the front one is clamped (o = 0.995, invisible
+    behind it), about 0.7 when o = 0.3 (visible). The front one is first at
+    every pixel: T = 1 in front."""
+    cam = sg.identity_camera(32, 32, 40.0)
+    px, py = _pix_centres(cam)
+    for o_front, visible_back in ((0.995, False), (0.3, True)):
+        sc = _scene([[0, 0, 1.5], [0, 0, 3.0]], [[50.0, 50.0, 50.0], [0.1, 0.1, 0.1]],
+                    [[1, 0, 0, 0], [1, 0, 0, 0]], [o_front, 0.7], [[1, 0, 0], [0, 1, 0]], [[0.0], [0.0]])
+        pr = ora.project_f64(cam, sc.means, sc.scales, sc.quats, sc.opacity)
+        ranges, gids = ora.bin_lists(cam, pr["rect"], pr["depth"])
+        maxT = ora.visibility(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity)
+        assert maxT[0] == 1.0
+        cf, cb = pr["cov"][0], pr["cov"][1]
+        a_f = np.minimum(0.99, float(sc.opacity[0]) * np.exp(-0.5 * ((cam.cx - px) ** 2 / cf[0] +
+                                                                      (cam.cy - py) ** 2 / cf[2])))
+        a_b = float(sc.opacity[1]) * np.exp(-0.5 * ((cam.cx - px) ** 2 / cb[0] + (cam.cy - py) ** 2 / cb[2]))
+        tx0, ty0, tx1, ty1 = pr["rect"][1]
+        in_rect = (px >= 16 * tx0) & (px < 16 * tx1) & (py >= 16 * ty0) & (py < 16 * ty1)
+        blended = in_rect & (a_b >= 1 / 255)
+        assert blended.sum() > 10
+        want = float((1 - a_f)[blended].max())
+        assert abs(maxT[1] - want) < 1e-14, (maxT[1], want)
+        assert (maxT[1] > 0.5) == visible_back
+    assert abs((1 - 0.99) - 0.01) < 1e-15
+
+
+def _walk_max_T(cam, pr, ranges, gids, opac):
+    """Eq. 2's front-to-back walk written out again in numpy, one tile at a
+    time over its pixels: the largest T in front of each blended Gaussian."""
+    P = pr["uv"].shape[0]
+    out = np.zeros(P)
+    px_all, py_all = _pix_centres(cam)
+    for t in range(cam.tiles_x * cam.tiles_y):
+        s, e = ranges[t]
+        tx, ty = t % cam.tiles_x, t // cam.tiles_x
+        px = px_all[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16].ravel()
+        py = py_all[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16].ravel()
+        T = np.ones(px.shape)
+        done = np.zeros(px.shape, bool)
+        for g in gids[s:e]:
+            A, B, C = pr["conic"][g]
+            dx, dy = pr["uv"][g, 0] - px, pr["uv"][g, 1] - py
+            power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
+            alpha = np.minimum(0.99, opac[g] * np.exp(power))
+            ok = (power <= 0) & (alpha >= 1 / 255) & ~done
+            Tn = T * (1 - alpha)
+            stop = ok & (Tn < 1e-4)
+            bl = ok & ~stop
+            if bl.any():
+                out[g] = max(out[g], T[bl].max())
+            done |= stop
+            T = np.where(bl, Tn, T)
+    return out
+
+
+def test_visibility_brute_force(ora, sg):
+    """The oracle's per-Gaussian max T against the walk written out in numpy
+    on a random frustum scene; visibility (> 0.5) agrees exactly."""
+    sc, cam = sg.small_case(seed=21, P=2000, N=0)
+    pr = ora.project_f64(cam, sc.means, sc.scales, sc.quats, sc.opacity)
+    ranges, gids = ora.bin_lists(cam, pr["rect"], pr["depth"])
+    maxT = ora.visibility(cam, ranges, gids, pr["uv"], pr["conic"], sc.opacity)
+    want = _walk_max_T(cam, pr, ranges, gids, sc.opacity.astype(np.float64))
+    assert np.abs(maxT - want).max() < 1e-12
+    vis = maxT > 0.5
+    assert 20 < vis.sum() < sc.P and (maxT[~vis] > 0).any()
+    assert np.array_equal(vis, want > 0.5)
