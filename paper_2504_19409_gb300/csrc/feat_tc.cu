@@ -35,6 +35,11 @@
 // GS_ERR_TIMEOUT, waits (bounded) for the tensor core, frees tensor memory
 // and returns.
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "gsff_internal.cuh"
 
 namespace gsff {
@@ -765,11 +770,19 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, cons
 //   B2 W2 : (n/8)*128  + (k/8)*8192 + (k%8)*16 + (n%8)*2  LBO 8192, SBO 128
 // D1 occupies tensor-memory columns [0, 128) and is overwritten by D2
 // (columns [0, 512)) once read.
+// Epilogue: warp w (tensor-memory lanes 32 (w % 4).., columns 128 (w / 4)..)
+// adds b2 to 32 x 32 blocks of D2 and writes each into its own 4 KB box in
+// shared memory in the 128-byte swizzled order (16-byte chunk q of box row r
+// at chunk q ^ (r % 8): conflict-free stores), then stores the box with one
+// TMA tensor store. The tensor map clips rows past npix. The 16 boxes reuse
+// H (free once D2 is complete) and the 32 KB after it, from a 1024-byte
+// boundary.
 namespace {
 
 struct DecSmem {
   uint8_t W2[128 * 512 * 2];   // 128 KB
-  uint8_t H[128 * 128 * 2];    // 32 KB
+  uint8_t H[128 * 128 * 2];    // 32 KB; also the first half of the output boxes
+  uint8_t Ybox[128 * 128 * 2 + 1024];  // second half of the boxes (+ room to align them)
   uint8_t W1[16 * 128 * 2];    // 4 KB
   uint8_t Z[128 * 16 * 2];     // 4 KB
   float b1[128];
@@ -798,7 +811,8 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p) {
+__global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p,
+                                                           const __grid_constant__ CUtensorMap ymap) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   DecSmem& S = *reinterpret_cast<DecSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -907,28 +921,63 @@ __global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p) 
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
     {
-      const long long pix = base + row;
-      float* dst = p.y + pix * 512;
-      for (int c = 128 * cq; c < 128 * cq + 128; c += 32) {
+      const uint32_t box = ((smem_u32(S.H) + 1023u) & ~1023u) + (uint32_t)warp * 4096u;
+      const uint32_t rowa = box + (uint32_t)lane * 128u;
+      const int row0 = (int)(base + 32 * lg);
+      for (int s4 = 0; s4 < 4; ++s4) {
+        const int c = 128 * cq + 32 * s4;
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c, v);
-        if (pix < p.npix) {
+        if (s4 > 0) {
+          // the previous box must have been read out before it is overwritten
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          __syncwarp();
+        }
 #pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<float4*>(dst + c + i) =
-                make_float4(v[i] + S.b2[c + i], v[i + 1] + S.b2[c + i + 1], v[i + 2] + S.b2[c + i + 2],
-                            v[i + 3] + S.b2[c + i + 3]);
+        for (int q = 0; q < 8; ++q) {
+          const float4 b = *reinterpret_cast<const float4*>(&S.b2[c + 4 * q]);
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + (uint32_t)((q ^ (lane & 7)) << 4)),
+                       "f"(v[4 * q] + b.x), "f"(v[4 * q + 1] + b.y), "f"(v[4 * q + 2] + b.z),
+                       "f"(v[4 * q + 3] + b.w)
+                       : "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(&ymap),
+                       "r"(c), "r"(row0), "r"(box)
+                       : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
       }
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
   }
   if (!ok && tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
   if (!ok) mbar_wait(smem_u32(&S.mbar), phase ^ 1u);  // bounded drain of the outstanding commit
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this warp's stores complete
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
 }
 
 }  // namespace
@@ -941,6 +990,19 @@ extern "C" gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, cons
     return GS_ERR_UNSUPPORTED;
   if (npix < 0 || (npix > 0 && (!z || !y)) || !aligned(z, 16) || !aligned(y, 16)) return GS_ERR_INVALID_ARG;
   if (npix == 0) return GS_OK;
+  if (npix >= (1ll << 31)) return GS_ERR_UNSUPPORTED;  // row coordinates of the output tensor map are int32
+  // output y [npix, 512] fp32 as a 2D tensor for TMA stores of 32 x 32 boxes, 128-byte swizzle
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return GS_ERR_CUDA;
+  CUtensorMap ymap;
+  const cuuint64_t dims[2] = {512, (cuuint64_t)npix};
+  const cuuint64_t strides[1] = {512 * sizeof(float)};
+  const cuuint32_t boxdim[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  if (encode(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, y, dims, strides, boxdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return GS_ERR_CUDA;
   DecTcParams p;
   p.npix = npix;
   p.z = z;
@@ -964,6 +1026,6 @@ extern "C" gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, cons
   const unsigned blocks = (unsigned)(ntiles < sms ? ntiles : sms);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GS_TRACE("k_decoder_fwd_tc", st);
-  k_decoder_fwd_tc<<<blocks, 512, smem, st>>>(p);
+  k_decoder_fwd_tc<<<blocks, 512, smem, st>>>(p, ymap);
   return last_launch_status();
 }

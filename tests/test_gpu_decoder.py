@@ -174,9 +174,11 @@ def test_decoder_tensor_core_forward_within_bound(dec_mod, ora):
     n = 1000 + 37  # a ragged last tile
     z = torch.tensor(rng.normal(size=(n, 16)).astype(np.float32), device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    y = dec.forward_tc(z, status=st)
+    buf = torch.full((n + 40, 512), 7.0, device="cuda")  # rows past n must stay untouched
+    y = dec.forward_tc(z, out=buf[:n], status=st)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
+    assert (buf[n:] == 7.0).all()
     zb = z.to(torch.bfloat16).double().cpu().numpy()
     W1, b1, W2, b2 = _np(dec.work["W1"]), _np(dec.params["b1"]), _np(dec.work["W2"]), _np(dec.params["b2"])
     ref = ora.decoder_fwd(zb, W1, b1, W2, b2)
