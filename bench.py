@@ -386,9 +386,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="slam", choices=["slam", "wide", "decoder"],
+    ap.add_argument("--workload", default="slam", choices=["slam", "wide", "decoder", "tracking"],
                     help="slam: the headline SLAM-frame workload (N=16); wide: 500k Gaussians with 512 bf16 feature "
-                         "channels, tensor-core vs plain fp32; decoder: latent render + learned decoder vs both")
+                         "channels, tensor-core vs plain fp32; decoder: latent render + learned decoder vs both; "
+                         "tracking: the pose-tracking loop of Sec. 3.2 from 1 cm / 1 deg perturbations")
+    ap.add_argument("--track-iters", type=int, default=100, help="iteration cap per frame of --workload tracking")
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--gaussians", type=int, default=0, help="override the Gaussian count of --workload wide/decoder")
     ap.add_argument("--features", default="", choices=["", "unit", "prototypes"],
@@ -410,7 +412,7 @@ def main():
     if args.workload != "slam":
         if rank != 0:
             return 0
-        return run_forms(args)
+        return run_tracking(args) if args.workload == "tracking" else run_forms(args)
 
     import torch
     if world > 1:
@@ -527,6 +529,89 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+def run_tracking(args):
+    """Pose tracking (Sec. 3.2) on the SLAM scene: each timed frame starts at
+    the true pose perturbed by Exp(1 cm, 1 deg) (a seeded direction) and runs
+    the library's loop (render, Eq. 5 cotangents, pose-only adjoint, Adam +
+    Exp update on the device) until the update converges or --track-iters;
+    the convergence flag is read every 10 iterations. Observations are the
+    renders (RGB + depth) at the true poses."""
+    import torch
+    import paper_2504_19409_gb300 as g
+    from paper_2504_19409_gb300 import scenegen as sg
+    from paper_2504_19409_gb300.tracking import Tracker
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sc = sg.room_scene(SCENE_SEED, P_ROOM, 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    scene = tuple(t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
+    frames = [k % N_FRAMES for k in range(args.warmup + args.steps)]
+    ras = g.Rasterizer(P_ROOM, WIDTH, HEIGHT, N=0, device=dev)
+    obs = {}
+    for k in sorted(set(frames)):
+        ras.ensure_capacity(frame_camera(k), *scene[:4])
+        fw = ras.forward(frame_camera(k), *scene)
+        obs[k] = (fw["rgb"].clone(), fw["depth"].clone())
+    tr = Tracker(P_ROOM, WIDTH, HEIGHT, capacity=ras.capacity, device=dev)
+
+    def init_camera(k):
+        true = sg.room_trajectory(k % N_FRAMES, N_FRAMES, WIDTH, HEIGHT, FOCAL)
+        return sg.perturb_pose(true, *target_pose_delta(k)).as_f32()
+
+    def track(k):
+        tr.track(init_camera(k), scene, obs[k][0], obs[k][1], max_iters=args.track_iters, check_every=10)
+
+    def pose_error(k):
+        P = tr.pose.cpu().numpy().astype(np.float64)
+        R, tt = P[:9].reshape(3, 3), P[9:]
+        true = frame_camera(k)
+        dR = R @ np.asarray(true.R, np.float64).T
+        ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(dR) - 1) / 2))))
+        dc = np.linalg.norm(-R.T @ tt + np.asarray(true.R, np.float64).T @ np.asarray(true.t, np.float64))
+        return dc * 1e3, ang
+
+    for k in frames[:args.warmup]:
+        track(k)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ms, iters, err = [], [], []
+    for i, k in enumerate(frames[args.warmup:]):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        track(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        iters.append(tr.iterations)
+        err.append(pose_error(k))
+    tr.ras.check_status()
+    g.trace_enable(4096)
+    track(frames[args.warmup])
+    torch.cuda.synchronize()
+    per = {}
+    for name, tt in g.trace_read():
+        per[name] = per.get(name, 0.0) + tt / tr.iterations
+    g.trace_enable(0)
+    total_it = sum(iters)
+    result = {"metric": "tracking iterations/s (render + Eq. 5 cotangents + pose adjoint + pose update)",
+              "value": total_it / (sum(ms) / 1e3), "unit": "iterations/s", "n_gpus": 1, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene and trajectory)",
+              "config": {"workload": "tracking_room300k_1200x680", "gaussians": P_ROOM, "image": [WIDTH, HEIGHT],
+                         "features": "off", "start": "Exp(1 cm, 1 deg) from the true pose, seeded direction",
+                         "iteration_cap": args.track_iters, "l2": "flushed between timed frames (512 MB write)"},
+              "ms_per_frame": float(np.mean(ms)), "ms_per_iteration": sum(ms) / total_it,
+              "iterations_per_frame": float(np.mean(iters)),
+              "final_error_mm": {"mean": float(np.mean([e[0] for e in err])), "max": float(max(e[0] for e in err))},
+              "final_error_deg": {"mean": float(np.mean([e[1] for e in err])), "max": float(max(e[1] for e in err))},
+              "kernel_ms_per_iteration": {k: round(v, 4) for k, v in per.items()}}
+    print(json.dumps(result))
+    return 0
 
 
 def _time_frames(fn, frames, flush, stream, trace=False):

@@ -51,6 +51,11 @@ typedef struct gs_camera {
   float R[9];
   float t[3];
   float near_z;
+  /* Optional device copy of the pose: 12 floats (R row-major, then t). When
+   * not NULL the kernels read the world -> camera transform from it instead
+   * of R and t, so a pose updated on the device (gs_pose_update) is used by
+   * the next frame's calls without a host round trip. */
+  const float* pose_dev;
 } gs_camera;
 
 /* flags of gs_render_fwd / gs_render_bwd */
@@ -201,7 +206,9 @@ gs_status gs_visibility_iou(int32_t P, const uint8_t* vis_a, const uint8_t* vis_
  * Out (accumulated): d_means [P,3], d_scales [P,3], d_quats [P,4],
  *      d_opacity [P], d_colors [P,3], d_feats [P,N] (fp32 even for bf16
  *      features), d_pose [6] = (rho, theta) of the left perturbation
- *      T_CW <- Exp(tau) T_CW at tau = 0.
+ *      T_CW <- Exp(tau) T_CW at tau = 0. d_pose is required; d_means,
+ *      d_scales, d_quats, d_opacity and d_colors may each be NULL (not
+ *      written), as in tracking, where the Gaussians are frozen (Sec. 3.2).
  * GS_FEAT_TENSOR_CORE (decoupled mode, bf16 features, layout HWC, N % 128
  * == 0, N <= 512): the feature gradient is computed per half tile as the
  * tcgen05 product dL/dF^T [N x 128 px] (rounded to bf16) times the weights
@@ -230,6 +237,54 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
  */
 gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, float scale,
                           float* grad, float* loss_sum, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Camera tracking (Sec. 3.2, Eq. 5): with the Gaussians frozen, the pose is
+ * refined on its tangent until the update converges.
+ *
+ * gs_edge_mask -- m_e, the pixels of the observed image with a significant
+ * gradient: L = (r + g + b)/3 per pixel (rgb [3,H,W]); Sobel gx, gy of L with
+ * replicated borders, divided by 8 (a unit step gives 0.5); m_e [H,W] (u8) =
+ * gx^2 + gy^2 > tau^2. Every step is one binary32 operation in a fixed
+ * order: (r + g) + b, then * (1/3); a = (L(x+1,y-1) + 2 L(x+1,y)) +
+ * L(x+1,y+1), b likewise at x-1, gx = (a - b) * 0.125; gy alike with rows
+ * y+1 and y-1 (summed from x-1 to x+1); (gx gx) + (gy gy) > tau tau.
+ */
+gs_status gs_edge_mask(int32_t width, int32_t height, const float* rgb, float tau, uint8_t* m_e,
+                       void* stream);
+
+/* gs_tracking_loss_grad -- cotangents of Eq. 5 for one render:
+ *   m_v = alpha_ref > alpha_min (alpha_ref: the opacity of the frame's first
+ *   render, the 2D visibility map); colour term on m_v m_e, depth term on
+ *   m_v and gt_depth > 0;
+ *   g_rgb [3,H,W] = lambda_t / (3 H W) sign(rgb - gt_rgb) on the colour mask,
+ *   g_depth [H,W] = (1 - lambda_t) / (H W) sign(depth - gt_depth) on the depth
+ *   mask, 0 elsewhere (sign(0) = 0); *loss_sum (device float, may be NULL)
+ *   += the loss, accumulated atomically. Feed g_rgb and g_depth to
+ *   gs_render_bwd for the pose gradient.
+ */
+gs_status gs_tracking_loss_grad(int32_t width, int32_t height, const float* rgb, const float* depth,
+                                const float* gt_rgb, const float* gt_depth, const float* alpha_ref,
+                                float alpha_min, const uint8_t* m_e, float lambda_t, float* g_rgb,
+                                float* g_depth, float* loss_sum, void* stream);
+
+/* gs_pose_update -- one optimiser step of the pose (device arrays):
+ *   Adam on d_pose [6] (tangent (rho, theta) of the left perturbation, from
+ *   gs_render_bwd) with moments adam_m [6], adam_v [6] (zero at the frame's
+ *   first step), bias-corrected at `step` (1-based), step sizes lr_trans for
+ *   rho and lr_rot for theta: delta = -lr m_hat / (sqrt(v_hat) + eps);
+ *   pose_dev [12] (R row-major, t) <- Exp(delta) pose, with
+ *   Exp(rho, theta) = [R(theta), V(theta) rho], R(theta) = I + A K + B K^2,
+ *   V(theta) = I + B K + C K^2, K = [theta]x, phi = |theta|,
+ *   A = sin(phi)/phi, B = (1 - cos phi)/phi^2, C = (phi - sin phi)/phi^3
+ *   (series below phi = 1e-4);
+ *   *converged (device int32, may be NULL) = |V rho| < tol_trans and
+ *   phi < tol_rot.
+ * Use pose_dev as gs_camera.pose_dev so the next render reads it.
+ */
+gs_status gs_pose_update(float* pose_dev, const float* d_pose, float* adam_m, float* adam_v, int32_t step,
+                         float lr_trans, float lr_rot, float beta1, float beta2, float eps,
+                         float tol_trans, float tol_rot, int32_t* converged, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Per-pixel feature decoder o(.) of Eq. 9, read as a 1x1 lift of a rendered

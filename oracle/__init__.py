@@ -124,6 +124,38 @@ def render_fwd(cam, ranges, gids, uv, conic, opacity, colors, depth, feats, bg=(
     return out
 
 
+def edge_mask(rgb, tau):
+    """Tracking edge mask m_e (Sec. 3.2) of rgb [3,H,W] (float32), decided in binary32."""
+    rgb = np.ascontiguousarray(rgb, np.float32)
+    H, W = rgb.shape[1], rgb.shape[2]
+    out = np.zeros((H, W), np.uint8)
+    lib().ora_edge_mask(ctypes.c_int(W), ctypes.c_int(H), rgb.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(tau),
+                        out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def tracking_grad(rgb, depth, gt_rgb, gt_depth, alpha_ref, alpha_min, m_e, lam):
+    """(loss, g_rgb, g_depth) of Eq. 5 in double."""
+    H, W = depth.shape
+    g_rgb, g_depth = np.zeros((3, H, W)), np.zeros((H, W))
+    me = np.ascontiguousarray(m_e, np.uint8)
+    lib().ora_tracking_grad.restype = ctypes.c_double
+    loss = lib().ora_tracking_grad(ctypes.c_int(W), ctypes.c_int(H), _p(_f64(rgb)), _p(_f64(depth)), _p(_f64(gt_rgb)),
+                                   _p(_f64(gt_depth)), _p(_f64(alpha_ref)), ctypes.c_double(alpha_min),
+                                   me.ctypes.data_as(ctypes.c_void_p), ctypes.c_double(lam), _p(g_rgb), _p(g_depth))
+    return float(loss), g_rgb, g_depth
+
+
+def pose_update(pose, g, m, v, step, lr_t, lr_r, b1=0.9, b2=0.999, eps=1e-8, tol_t=1e-4, tol_r=1e-4):
+    """Adam on the pose tangent then T <- Exp(delta) T; updates pose (12), m, v (6) in place (float64
+    arrays); returns the convergence flag."""
+    for a in (pose, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return int(lib().ora_pose_update(_p(pose), _p(_f64(g)), _p(m), _p(v), ctypes.c_int(step), ctypes.c_double(lr_t),
+                                     ctypes.c_double(lr_r), ctypes.c_double(b1), ctypes.c_double(b2),
+                                     ctypes.c_double(eps), ctypes.c_double(tol_t), ctypes.c_double(tol_r)))
+
+
 def visibility(cam, ranges, gids, uv, conic, opacity):
     """Per Gaussian, the largest transmittance in front of it over the pixels where it is blended
     (0 where blended nowhere); visible in the keyframe sense (Sec. 3.2) when it exceeds 0.5."""

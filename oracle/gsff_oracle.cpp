@@ -19,6 +19,10 @@
 //   ora_visibility       per Gaussian, the largest transmittance in front of
 //                        it over the pixels where it is blended (Sec. 3.2:
 //                        visible when that transmittance exceeds 0.5).
+//   ora_edge_mask        tracking edge mask m_e (Sec. 3.2): binary32 replay
+//                        of the Sobel test, so the decision matches bit for bit.
+//   ora_tracking_grad    cotangents and value of the tracking loss (Eq. 5).
+//   ora_pose_update      Adam on the pose tangent and T <- Exp(delta) T.
 //   ora_render_bwd       adjoint of Eq. 2-3 per pixel from the stored list of
 //                        blended Gaussians (no division by 1-alpha).
 //   ora_project_bwd_f64  adjoint of the projection and the Lie-algebra pose
@@ -836,6 +840,116 @@ void ora_decoder_bwd(int n, int din, int dh, int dout, const double* z, const do
       }
     }
   }
+}
+
+
+// ---- tracking (Sec. 3.2, Eq. 5) ------------------------------------------------
+
+// Edge mask: luminance L = ((r + g) + b) * (1/3), Sobel differences with the
+// image border replicated, each divided by 8; edge where gx^2 + gy^2 > tau^2.
+// Written with float variables so that every operation rounds to binary32
+// in the order the GPU promises (compiled without contraction).
+void ora_edge_mask(int W, int H, const float* rgb, float tau, uint8_t* m_e) {
+  const size_t HW = (size_t)W * H;
+  auto L = [&](int x, int y) {
+    const size_t p = (size_t)y * W + x;
+    const float s = rgb[p] + rgb[HW + p];
+    const float s3 = s + rgb[2 * HW + p];
+    return s3 * (1.f / 3.f);
+  };
+  const float tt = tau * tau;
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      const int xm = std::max(x - 1, 0), xp = std::min(x + 1, W - 1);
+      const int ym = std::max(y - 1, 0), yp = std::min(y + 1, H - 1);
+      const float a1 = L(xp, ym) + 2.f * L(xp, y), a = a1 + L(xp, yp);
+      const float b1 = L(xm, ym) + 2.f * L(xm, y), b = b1 + L(xm, yp);
+      const float c1 = L(xm, yp) + 2.f * L(x, yp), c = c1 + L(xp, yp);
+      const float d1 = L(xm, ym) + 2.f * L(x, ym), d = d1 + L(xp, ym);
+      const float gx = (a - b) * 0.125f, gy = (c - d) * 0.125f;
+      const float gx2 = gx * gx, gy2 = gy * gy;
+      const float mag2 = gx2 + gy2;
+      m_e[(size_t)y * W + x] = mag2 > tt ? 1 : 0;
+    }
+}
+
+// Eq. 5: L = lambda/(3HW) sum_{m_v m_e} |C - C_obs| + (1 - lambda)/(HW) sum_{m_v, D_obs > 0} |D - D_obs|,
+// m_v = alpha_ref > alpha_min. Returns L; writes dL/dC and dL/dD (sign(0) = 0).
+double ora_tracking_grad(int W, int H, const double* rgb, const double* depth, const double* gt_rgb,
+                         const double* gt_depth, const double* alpha_ref, double alpha_min, const uint8_t* m_e,
+                         double lambda, double* g_rgb, double* g_depth) {
+  const size_t HW = (size_t)W * H;
+  const double sc = lambda / (3.0 * (double)HW), sd = (1.0 - lambda) / (double)HW;
+  auto sign = [](double d) { return d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0); };
+  double loss = 0.0;
+  for (size_t p = 0; p < HW; ++p) {
+    const bool mv = alpha_ref[p] > alpha_min;
+    const bool col = mv && m_e[p] != 0;
+    for (int c = 0; c < 3; ++c) {
+      const double d = rgb[c * HW + p] - gt_rgb[c * HW + p];
+      g_rgb[c * HW + p] = col ? sc * sign(d) : 0.0;
+      if (col) loss += sc * std::fabs(d);
+    }
+    const bool dep = mv && gt_depth[p] > 0;
+    const double d = depth[p] - gt_depth[p];
+    g_depth[p] = dep ? sd * sign(d) : 0.0;
+    if (dep) loss += sd * std::fabs(d);
+  }
+  return loss;
+}
+
+// Adam on the 6-vector (rho, theta) and the left update T <- Exp(delta) T,
+// Exp(rho, theta) = [R(theta), V(theta) rho] (the closed forms of the SE(3)
+// exponential). pose: R row-major then t. converged: |V rho| < tol_t and
+// |theta| < tol_r.
+int ora_pose_update(double* pose, const double* g, double* m, double* v, int step, double lr_t, double lr_r,
+                    double b1, double b2, double eps, double tol_t, double tol_r) {
+  double dl[6];
+  for (int i = 0; i < 6; ++i) {
+    m[i] = b1 * m[i] + (1 - b1) * g[i];
+    v[i] = b2 * v[i] + (1 - b2) * g[i] * g[i];
+    const double mh = m[i] / (1 - std::pow(b1, step)), vh = v[i] / (1 - std::pow(b2, step));
+    dl[i] = -(i < 3 ? lr_t : lr_r) * mh / (std::sqrt(vh) + eps);
+  }
+  const double w[3] = {dl[3], dl[4], dl[5]};
+  const double phi = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double A, B, C;
+  if (phi < 1e-6) {
+    A = 1 - phi * phi / 6;
+    B = 0.5 - phi * phi / 24;
+    C = 1.0 / 6 - phi * phi / 120;
+  } else {
+    A = std::sin(phi) / phi;
+    B = (1 - std::cos(phi)) / (phi * phi);
+    C = (phi - std::sin(phi)) / (phi * phi * phi);
+  }
+  const double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+  double K2[9], Rd[9], V[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double sum = 0;
+      for (int k = 0; k < 3; ++k) sum += K[3 * i + k] * K[3 * k + j];
+      K2[3 * i + j] = sum;
+    }
+  for (int i = 0; i < 9; ++i) {
+    const double I = (i % 4 == 0) ? 1.0 : 0.0;
+    Rd[i] = I + A * K[i] + B * K2[i];
+    V[i] = I + B * K[i] + C * K2[i];
+  }
+  double td[3], R[9], t[3];
+  for (int i = 0; i < 3; ++i) td[i] = V[3 * i] * dl[0] + V[3 * i + 1] * dl[1] + V[3 * i + 2] * dl[2];
+  for (int i = 0; i < 9; ++i) R[i] = pose[i];
+  for (int i = 0; i < 3; ++i) t[i] = pose[9 + i];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      double sum = 0;
+      for (int k = 0; k < 3; ++k) sum += Rd[3 * i + k] * R[3 * k + j];
+      pose[3 * i + j] = sum;
+    }
+    pose[9 + i] = Rd[3 * i] * t[0] + Rd[3 * i + 1] * t[1] + Rd[3 * i + 2] * t[2] + td[i];
+  }
+  const double tn = std::sqrt(td[0] * td[0] + td[1] * td[1] + td[2] * td[2]);
+  return (tn < tol_t && phi < tol_r) ? 1 : 0;
 }
 
 }  // extern "C"

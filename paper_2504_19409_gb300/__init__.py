@@ -14,6 +14,7 @@ SE(3) pose tangent (Eq. 4).
 """
 from __future__ import annotations
 
+import copy
 import ctypes
 import os
 
@@ -35,7 +36,8 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_render_bwd_workspace_bytes", "gs_render_bwd", "gs_l1_loss_grad", "gs_trace_enable",
            "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
-           "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou")
+           "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
+           "gs_pose_update")
 
 
 class GsffError(RuntimeError):
@@ -50,7 +52,8 @@ class GsDecoder(ctypes.Structure):
 class GsCamera(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
-                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("near_z", ctypes.c_float)]
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("near_z", ctypes.c_float),
+                ("pose_dev", ctypes.c_void_p)]
 
 
 def camera_struct(cam) -> GsCamera:
@@ -64,6 +67,17 @@ def camera_struct(cam) -> GsCamera:
     for i in range(3):
         c.t[i] = float(t[i])
     c.near_z = float(getattr(cam, "near", 0.2))
+    pose = getattr(cam, "pose_dev", None)
+    if pose is not None:
+        _need(pose, torch.float32, "pose_dev", (12,))
+        c.pose_dev = pose.data_ptr()
+    return c
+
+
+def with_device_pose(cam, pose):
+    """A copy of `cam` whose kernels take R, t from `pose` (CUDA float32 [12]: R row-major, then t)."""
+    c = copy.copy(cam)
+    c.pose_dev = pose
     return c
 
 
@@ -96,6 +110,13 @@ def lib():
     L.gs_render_fwd.restype = ctypes.c_int
     L.gs_visibility_iou.argtypes = [_i32, _vp, _vp, _vp, _vp]
     L.gs_visibility_iou.restype = ctypes.c_int
+    _f = ctypes.c_float
+    L.gs_edge_mask.argtypes = [_i32, _i32, _vp, _f, _vp, _vp]
+    L.gs_edge_mask.restype = ctypes.c_int
+    L.gs_tracking_loss_grad.argtypes = [_i32, _i32] + [_vp] * 5 + [_f, _vp, _f, _vp, _vp, _vp, _vp]
+    L.gs_tracking_loss_grad.restype = ctypes.c_int
+    L.gs_pose_update.argtypes = [_vp] * 4 + [_i32] + [_f] * 7 + [_vp, _vp]
+    L.gs_pose_update.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
     L.gs_render_bwd_workspace_bytes.restype = _sz
     L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +
@@ -230,6 +251,41 @@ def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT
     return o
 
 
+def edge_mask(rgb, tau, out=None, stream=None):
+    """gs_edge_mask: uint8 [H,W], 1 where the Sobel gradient of (r+g+b)/3 exceeds tau (Sec. 3.2's m_e)."""
+    _need(rgb, torch.float32, "rgb")
+    H, W = rgb.shape[1], rgb.shape[2]
+    m = out if out is not None else torch.empty(H, W, dtype=torch.uint8, device=rgb.device)
+    _check(lib().gs_edge_mask(W, H, _ptr(rgb), float(tau), _ptr(m), _stream(stream)), "gs_edge_mask")
+    return m
+
+
+def tracking_loss_grad(rgb, depth, gt_rgb, gt_depth, alpha_ref, m_e, lambda_t=0.9, alpha_min=0.5, g_rgb=None,
+                       g_depth=None, loss=None, stream=None):
+    """gs_tracking_loss_grad: the cotangents (g_rgb [3,H,W], g_depth [H,W]) of Eq. 5."""
+    H, W = depth.shape
+    for t_, n_, sh in ((rgb, "rgb", (3, H, W)), (gt_rgb, "gt_rgb", (3, H, W)), (gt_depth, "gt_depth", (H, W)),
+                       (alpha_ref, "alpha_ref", (H, W))):
+        _need(t_, torch.float32, n_, sh)
+    _need(m_e, torch.uint8, "m_e", (H, W))
+    gr = g_rgb if g_rgb is not None else torch.empty_like(rgb)
+    gd = g_depth if g_depth is not None else torch.empty_like(depth)
+    _check(lib().gs_tracking_loss_grad(W, H, _ptr(rgb), _ptr(depth), _ptr(gt_rgb), _ptr(gt_depth), _ptr(alpha_ref),
+                                       float(alpha_min), _ptr(m_e), float(lambda_t), _ptr(gr), _ptr(gd), _ptr(loss),
+                                       _stream(stream)), "gs_tracking_loss_grad")
+    return gr, gd
+
+
+def pose_update(pose, d_pose, m, v, step, lr_trans=1e-3, lr_rot=3e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                tol_trans=1e-4, tol_rot=1e-4, converged=None, stream=None):
+    """gs_pose_update: Adam on the pose tangent, then pose <- Exp(delta) pose (all on the device)."""
+    for t_, n_, sh in ((pose, "pose", (12,)), (d_pose, "d_pose", (6,)), (m, "m", (6,)), (v, "v", (6,))):
+        _need(t_, torch.float32, n_, sh)
+    _check(lib().gs_pose_update(_ptr(pose), _ptr(d_pose), _ptr(m), _ptr(v), int(step), float(lr_trans),
+                                float(lr_rot), float(beta1), float(beta2), float(eps), float(tol_trans),
+                                float(tol_rot), _ptr(converged), _stream(stream)), "gs_pose_update")
+
+
 def visibility_iou(vis_a, vis_b, counts=None, stream=None):
     """gs_visibility_iou: device int64 [2] = (|a and b|, |a or b|) of two uint8 visibility vectors."""
     _need(vis_a, torch.uint8, "vis_a")
@@ -247,7 +303,8 @@ def render_bwd_workspace_bytes(P: int) -> int:
 def render_bwd(cam, means, scales, quats, colors, feats, proj, sort, fwd, g_rgb=None, g_depth=None, g_alpha=None,
                g_feat=None, flags=None, layout=GS_LAYOUT_CHW, bg=None, coupled=False, grads=None, workspace=None,
                status=None, stream=None):
-    """gs_render_bwd: accumulates into grads (zeroed if created here) and returns it."""
+    """gs_render_bwd: accumulates into grads (zeroed if created here) and returns it. A caller-given grads
+    dict needs only "pose" (and "feats" with features on); classes it leaves out are not computed."""
     P = means.shape[0]
     dev = means.device
     N = 0 if feats is None else feats.shape[1]
@@ -273,8 +330,9 @@ def render_bwd(cam, means, scales, quats, colors, feats, proj, sort, fwd, g_rgb=
         _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
         _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), _ptr(g_rgb), _ptr(g_depth), _ptr(g_alpha),
         _ptr(g_feat) if feat_on else None, GS_FEAT_GRAD_COUPLED if coupled else GS_FEAT_GRAD_DECOUPLED,
-        _ptr(ws), ws.numel(), _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opacity"]),
-        _ptr(g["colors"]), _ptr(g["feats"]) if feat_on else None, _ptr(g["pose"]), _ptr(st), _stream(stream)),
+        _ptr(ws), ws.numel(), _ptr(g.get("means")), _ptr(g.get("scales")), _ptr(g.get("quats")),
+        _ptr(g.get("opacity")), _ptr(g.get("colors")), _ptr(g["feats"]) if feat_on else None, _ptr(g["pose"]),
+        _ptr(st), _stream(stream)),
         "gs_render_bwd")
     return g
 
@@ -380,6 +438,12 @@ class Rasterizer:
                    g_feat, flags=self.flags, layout=self.layout, bg=bg, coupled=coupled, grads=self.grads,
                    workspace=self.bwd_ws, status=self.status, stream=stream)
         return self.grads
+
+    def render_pose_grad(self, cam, means, scales, quats, colors, g_rgb, g_depth, grads, stream=None):
+        """The adjoint of the last forward into grads["pose"] only (frozen Gaussians, as in tracking)."""
+        render_bwd(cam, means, scales, quats, colors, None, self.proj, self.sort, self.fwd, g_rgb, g_depth,
+                   flags=GS_FEAT_OFF, grads=grads, workspace=self.bwd_ws, status=self.status, stream=stream)
+        return grads
 
     def check_status(self):
         s = int(self.status.item())

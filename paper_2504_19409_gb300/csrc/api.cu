@@ -264,9 +264,7 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
   (void)status;
   if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
   if (!tile_ranges || !gids || !T_final || !last_idx || !workspace) return GS_ERR_INVALID_ARG;
-  if (P > 0 && (!means || !scales || !quats || !colors || !uv || !conic_opacity || !depth || !d_means || !d_scales ||
-                !d_quats || !d_opacity || !d_colors))
-    return GS_ERR_INVALID_ARG;
+  if (P > 0 && (!means || !scales || !quats || !colors || !uv || !conic_opacity || !depth)) return GS_ERR_INVALID_ARG;
   if (!d_pose) return GS_ERR_INVALID_ARG;
   if (!aligned(workspace, 256) || !aligned(quats, 16) || !aligned(conic_opacity, 16) || !aligned(uv, 8))
     return GS_ERR_INVALID_ARG;

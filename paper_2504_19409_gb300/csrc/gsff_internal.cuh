@@ -27,7 +27,24 @@ struct CamF {
   float R[9];
   float t[3];
   float near_z;
+  const float* pose;  // device (R row-major, t) overriding R, t when not null
 };
+
+// The world -> camera rotation and translation a kernel works with: the
+// device pose when the caller gave one, else the camera struct's.
+__device__ __forceinline__ void cam_pose(const CamF& cam, float (&R)[9], float (&t)[3]) {
+  if (cam.pose) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = __ldg(cam.pose + i);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = __ldg(cam.pose + 9 + i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = cam.R[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = cam.t[i];
+  }
+}
 
 inline CamF make_cam(const gs_camera& c) {
   CamF k;
@@ -42,6 +59,7 @@ inline CamF make_cam(const gs_camera& c) {
   for (int i = 0; i < 9; ++i) k.R[i] = c.R[i];
   for (int i = 0; i < 3; ++i) k.t[i] = c.t[i];
   k.near_z = c.near_z;
+  k.pose = c.pose_dev;
   return k;
 }
 

@@ -42,10 +42,11 @@ __global__ void __launch_bounds__(256) k_project(const CamF cam, int P, const fl
             isfinite(s2) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) &&
             isfinite(o)))
         break;
-      const float* R = cam.R;
-      const float xc = fa(fa(fa(fm(R[0], m0), fm(R[1], m1)), fm(R[2], m2)), cam.t[0]);
-      const float yc = fa(fa(fa(fm(R[3], m0), fm(R[4], m1)), fm(R[5], m2)), cam.t[1]);
-      zc = fa(fa(fa(fm(R[6], m0), fm(R[7], m1)), fm(R[8], m2)), cam.t[2]);
+      float R[9], tc[3];
+      cam_pose(cam, R, tc);
+      const float xc = fa(fa(fa(fm(R[0], m0), fm(R[1], m1)), fm(R[2], m2)), tc[0]);
+      const float yc = fa(fa(fa(fm(R[3], m0), fm(R[4], m1)), fm(R[5], m2)), tc[1]);
+      zc = fa(fa(fa(fm(R[6], m0), fm(R[7], m1)), fm(R[8], m2)), tc[2]);
       if (!(zc > cam.near_z)) break;
       float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
       const float qq = fa(fa(fa(fm(qw, qw), fm(qx, qx)), fm(qy, qy)), fm(qz, qz));
@@ -168,10 +169,11 @@ __global__ void __launch_bounds__(256) k_project_bwd(
     const float dA = d_conic[3 * g], dB = d_conic[3 * g + 1], dC = d_conic[3 * g + 2];
     const float dd = d_depth[g];
     const float m0 = means[3 * g], m1 = means[3 * g + 1], m2 = means[3 * g + 2];
-    const float* R = cam.R;
-    const float x = R[0] * m0 + R[1] * m1 + R[2] * m2 + cam.t[0];
-    const float y = R[3] * m0 + R[4] * m1 + R[5] * m2 + cam.t[1];
-    const float z = R[6] * m0 + R[7] * m1 + R[8] * m2 + cam.t[2];
+    float R[9], tc[3];
+    cam_pose(cam, R, tc);
+    const float x = R[0] * m0 + R[1] * m1 + R[2] * m2 + tc[0];
+    const float y = R[3] * m0 + R[4] * m1 + R[5] * m2 + tc[1];
+    const float z = R[6] * m0 + R[7] * m1 + R[8] * m2 + tc[2];
     const bool any = (duv.x != 0.f) | (duv.y != 0.f) | (dA != 0.f) | (dB != 0.f) | (dC != 0.f) | (dd != 0.f);
     if (any && z > cam.near_z) {
       const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
@@ -265,13 +267,17 @@ __global__ void __launch_bounds__(256) k_project_bwd(
                   2.f * qy * dr[5] + 2.f * qx * dr[6] + 2.f * qy * dr[7];
       const float dot = w * dqw + qx * dqx + qy * dqy + qz * dqz;
       const float iq = 1.f / qnorm;
-      d_quats[4 * g + 0] += (dqw - w * dot) * iq;
-      d_quats[4 * g + 1] += (dqx - qx * dot) * iq;
-      d_quats[4 * g + 2] += (dqy - qy * dot) * iq;
-      d_quats[4 * g + 3] += (dqz - qz * dot) * iq;
-      d_scales[3 * g + 0] += ds[0];
-      d_scales[3 * g + 1] += ds[1];
-      d_scales[3 * g + 2] += ds[2];
+      if (d_quats) {
+        d_quats[4 * g + 0] += (dqw - w * dot) * iq;
+        d_quats[4 * g + 1] += (dqx - qx * dot) * iq;
+        d_quats[4 * g + 2] += (dqy - qy * dot) * iq;
+        d_quats[4 * g + 3] += (dqz - qz * dot) * iq;
+      }
+      if (d_scales) {
+        d_scales[3 * g + 0] += ds[0];
+        d_scales[3 * g + 1] += ds[1];
+        d_scales[3 * g + 2] += ds[2];
+      }
       // T = J W: dJ = dT W^T (entries 00, 02, 11, 12), dW = J^T dT
       const float dJ00 = dT[0] * R[0] + dT[1] * R[1] + dT[2] * R[2];
       const float dJ02 = dT[0] * R[6] + dT[1] * R[7] + dT[2] * R[8];
@@ -293,9 +299,11 @@ __global__ void __launch_bounds__(256) k_project_bwd(
       dx += cam.fx * iz * duv.x;
       dy += cam.fy * iz * duv.y;
       dz += -cam.fx * x * iz2 * duv.x - cam.fy * y * iz2 * duv.y + dd;
-      d_means[3 * g + 0] += R[0] * dx + R[3] * dy + R[6] * dz;
-      d_means[3 * g + 1] += R[1] * dx + R[4] * dy + R[7] * dz;
-      d_means[3 * g + 2] += R[2] * dx + R[5] * dy + R[8] * dz;
+      if (d_means) {
+        d_means[3 * g + 0] += R[0] * dx + R[3] * dy + R[6] * dz;
+        d_means[3 * g + 1] += R[1] * dx + R[4] * dy + R[7] * dz;
+        d_means[3 * g + 2] += R[2] * dx + R[5] * dy + R[8] * dz;
+      }
       pose[0] = dx;
       pose[1] = dy;
       pose[2] = dz;

@@ -469,9 +469,13 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
       float* dst;
       if (ch < 2) dst = p.d_uv + 2 * (size_t)g + ch;
       else if (ch < 5) dst = p.d_conic + 3 * (size_t)g + (ch - 2);
-      else if (ch == 5) dst = p.d_opacity + g;
-      else if (ch < 9) dst = p.d_colors + 3 * (size_t)g + (ch - 6);
-      else if (ch == 9) dst = p.d_depth + g;
+      else if (ch == 5) {
+        if (!p.d_opacity) continue;
+        dst = p.d_opacity + g;
+      } else if (ch < 9) {
+        if (!p.d_colors) continue;
+        dst = p.d_colors + 3 * (size_t)g + (ch - 6);
+      } else if (ch == 9) dst = p.d_depth + g;
       else {
         const int c = c0 + ch - kGeomCh;
         if (c >= p.N) continue;

@@ -24,3 +24,16 @@ def ora():
 def sg():
     from paper_2504_19409_gb300 import scenegen
     return scenegen
+
+
+@pytest.fixture(scope="session")
+def gs():
+    """The package with its CUDA library built and loaded (skips without a GPU)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_19409_gb300 import build
+    build.build()
+    import paper_2504_19409_gb300 as g
+    g.lib()
+    return g

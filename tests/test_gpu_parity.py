@@ -28,17 +28,6 @@ GRAD_TOL = 1e-4
 GRAD_COS = 0.99999
 
 
-@pytest.fixture(scope="module")
-def gs():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2504_19409_gb300 import build
-    build.build()
-    import paper_2504_19409_gb300 as g
-    g.lib()
-    return g
-
-
 def _t(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
 

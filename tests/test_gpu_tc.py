@@ -16,17 +16,6 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def gs():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2504_19409_gb300 import build
-    build.build()
-    import paper_2504_19409_gb300 as g
-    g.lib()
-    return g
-
-
 def _t(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
 

@@ -76,3 +76,38 @@ def test_pins_catch_planted_mistake(tmp_path, sg, name):
         except AssertionError:
             failed.append(tname)
     assert failed, f"no pin caught: {name}"
+
+
+# planted slips in the tracking pieces, caught by tests/test_oracle_tracking.py
+TRACKING_MUTATIONS = {
+    "pose update applied on the right": (
+        "for (int k = 0; k < 3; ++k) sum += Rd[3 * i + k] * R[3 * k + j];",
+        "for (int k = 0; k < 3; ++k) sum += R[3 * i + k] * Rd[3 * k + j];"),
+    "V matrix dropped from the translation": (
+        "for (int i = 0; i < 3; ++i) td[i] = V[3 * i] * dl[0] + V[3 * i + 1] * dl[1] + V[3 * i + 2] * dl[2];",
+        "for (int i = 0; i < 3; ++i) td[i] = dl[i];"),
+    "Sobel without the 1/8 normalisation": (
+        "const float gx = (a - b) * 0.125f, gy = (c - d) * 0.125f;",
+        "const float gx = (a - b), gy = (c - d);"),
+    "Adam step sign": (
+        "dl[i] = -(i < 3 ? lr_t : lr_r) * mh / (std::sqrt(vh) + eps);",
+        "dl[i] = (i < 3 ? lr_t : lr_r) * mh / (std::sqrt(vh) + eps);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TRACKING_MUTATIONS))
+def test_tracking_pins_catch_planted_mistake(tmp_path, name):
+    import inspect
+
+    import tests.test_oracle_tracking as tpins
+    old, new = TRACKING_MUTATIONS[name]
+    mut = _load_mutant(tmp_path, name, old, new)
+    failed = []
+    for tname in sorted(n for n in dir(tpins) if n.startswith("test_")):
+        fn = getattr(tpins, tname)
+        kw = {"scale": 1.0} if "scale" in inspect.signature(fn).parameters else {}
+        try:
+            fn(mut, **kw)
+        except AssertionError:
+            failed.append(tname)
+    assert failed, f"no pin caught: {name}"
