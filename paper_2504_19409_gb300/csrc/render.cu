@@ -6,11 +6,13 @@
 // are staged in shared memory in batches; per-pixel work is SIMT fp32.
 //
 // Each warp owns an 8x4 (forward) or 8x8 (backward, two pixels per thread)
-// block of the tile. Before evaluating a
-// Gaussian, a warp tests its block against a conservative box around the
-// region where that Gaussian's alpha can reach 1/255 (warp_skip_extent) and
-// skips it as a whole when they are disjoint: the per-pixel decisions are
-// unchanged, only work that would be discarded is avoided.
+// block of the tile. A warp skips a Gaussian as a whole when its block lies
+// outside a conservative box around the region where that Gaussian's alpha
+// can reach 1/255 (warp_skip_extent): the per-pixel decisions are unchanged,
+// only work that would be discarded is avoided. The test is taken for all
+// warp blocks by the thread that loads the Gaussian into shared memory; a
+// warp then walks only the Gaussians whose bit it holds, 32 at a time
+// through one ballot.
 //
 // Forward: early termination is tracked per pixel; a block leaves its list
 // as soon as __syncthreads_count sees every pixel done.
@@ -67,14 +69,6 @@ __device__ __forceinline__ void thread_pixels(int tx, int ty, int (&px)[PPT], in
   }
 }
 
-// Centre of this warp's block; its pixel centres lie within +-3.5 (x) and
-// +-(2 PPT - 0.5) (y) of it.
-template <int PPT>
-__device__ __forceinline__ float2 warp_centre(int tx, int ty) {
-  const int w = threadIdx.x >> 5;
-  return make_float2((float)(tx * kTile + (w & 1) * 8) + 4.f, (float)(ty * kTile + (w >> 1) * (4 * PPT)) + 2.f * PPT);
-}
-
 // Half-extents, around (u, v), of a box that holds every pixel centre of a
 // warp block that can reach alpha >= 1/255 for this Gaussian. alpha = o G
 // with G = exp(power) needs power >= -ln(255 o); at vertical offset dy the
@@ -83,7 +77,10 @@ __device__ __forceinline__ float2 warp_centre(int tx, int ty) {
 // extents are widened by 2% + 0.05 px (far beyond fp32 error, so no skip
 // decision the exact test would keep is dropped) and by the warp block's
 // half-size (hx, hy); nearly singular conics (det < 1e-3 A C) are never
-// skipped.
+// skipped. A warp block of 8 x 4 PPT pixels has its centre at (4, 2 PPT)
+// from its corner, its pixel centres within +-3.5 and +-(2 PPT - 0.5) of it;
+// the test of all warp blocks of a tile is taken once per Gaussian when a
+// batch is loaded and kept as a bit mask (bit w = warp w's block passes).
 __device__ __forceinline__ float2 warp_skip_extent(float4 co, float hx, float hy) {
   const float t = logf(255.f * co.w);
   if (t < 0.f) return make_float2(-1.f, -1.f);  // o < 1/255: never blended
@@ -94,9 +91,6 @@ __device__ __forceinline__ float2 warp_skip_extent(float4 co, float hx, float hy
   return make_float2(ex * 1.02f + 0.05f + hx, ey * 1.02f + 0.05f + hy);
 }
 
-__device__ __forceinline__ bool warp_skips(float2 uv, float2 ext, float2 wc) {
-  return fabsf(uv.x - wc.x) > ext.x || fabsf(uv.y - wc.y) > ext.y;
-}
 
 template <int NC>
 __device__ __forceinline__ void load_feat_row(const void* feats, int bf16, int N, uint32_t g, int c0,
@@ -139,7 +133,7 @@ template <int NC, bool VIS>
 __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   constexpr int NCs = NC > 0 ? NC : 1;
   __shared__ float2 s_uv[kTilePix];
-  __shared__ float2 s_ext[kTilePix];
+  __shared__ uint8_t s_wmask[kTilePix];  // bit w: warp w's pixel block passes the skip test
   __shared__ float4 s_co[kTilePix];
   __shared__ float4 s_cd[kTilePix];
   __shared__ float s_f[kTilePix][NCs];
@@ -155,7 +149,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   int pxa[1], pya[1];
   thread_pixels<1>(tx, ty, pxa, pya);
   const int px = pxa[0], py = pya[0];
-  const float2 wc = warp_centre<1>(tx, ty);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool inside = px < p.cam.W && py < p.cam.H;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const int2 rg = p.ranges[tile];
@@ -174,25 +168,43 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
     if (idx < rg.y) {
       const uint32_t g = p.gids[idx];
       const float4 co = p.co[g];
-      s_uv[threadIdx.x] = p.uv[g];
+      const float2 u = p.uv[g];
+      s_uv[threadIdx.x] = u;
       s_co[threadIdx.x] = co;
-      s_ext[threadIdx.x] = warp_skip_extent(co, 3.5f, 1.5f);
+      // the skip test of all 8 warp blocks (2 columns x 4 rows of 8x4 pixels)
+      const float2 ext = warp_skip_extent(co, 3.5f, 1.5f);
+      const float x0 = (float)(tx * kTile) + 4.f, y0 = (float)(ty * kTile) + 2.f;
+      uint32_t xok = 0, yok = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) xok |= (fabsf(u.x - (x0 + 8.f * c)) > ext.x ? 0u : 1u) << c;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) yok |= (fabsf(u.y - (y0 + 4.f * r)) > ext.y ? 0u : 1u) << r;
+      uint32_t m8 = 0;
+#pragma unroll
+      for (int w8 = 0; w8 < 8; ++w8) m8 |= ((xok >> (w8 & 1)) & (yok >> (w8 >> 1)) & 1u) << w8;
+      s_wmask[threadIdx.x] = (uint8_t)m8;
       if (VIS) s_gid[threadIdx.x] = g;
       if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
       if (NC > 0) load_feat_row<NCs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
     }
     __syncthreads();
     const int n = min(kTilePix, rg.y - start);
-    if (!done) {
-      for (int j = 0; j < n; ++j) {
+    // this warp's Gaussians of the batch, 32 at a time, in list order
+    for (int base = 0; base < n; base += 32) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const int jj = base + lane;
+      uint32_t bits = __ballot_sync(0xffffffffu, jj < n && ((s_wmask[jj] >> wid) & 1u));
+      while (bits) {
+        const int j = base + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        if (done) continue;
         const float2 uj = s_uv[j];
-        if (warp_skips(uj, s_ext[j], wc)) continue;
         PairAlpha pa;
         if (!pair_alpha(s_co[j], uj.x - pxc, uj.y - pyc, pa)) continue;
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, pa.alpha));
         if (Tn < kTStop) {
           done = true;
-          break;
+          continue;
         }
         const float w = __fmul_rn(pa.alpha, T);
         if (mark && T > 0.5f) {
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
   constexpr int NFs = (COUPLED && NC > 0) ? NC : 1;
   __shared__ float s_red[NW][BB][CHP];
   __shared__ float2 s_uv[BB];
-  __shared__ float2 s_ext[BB];
+  __shared__ uint8_t s_wmask[BB];  // bit w: warp w's pixel block passes the skip test
   __shared__ float4 s_co[BB];
   __shared__ float4 s_cd[BB];
   __shared__ float s_f[BB][NFs];
@@ -324,7 +336,6 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
   int px[PPT], py[PPT];
   thread_pixels<PPT>(tx, ty, px, py);
-  const float2 wc = warp_centre<PPT>(tx, ty);
   const int2 rg = p.ranges[tile];
   const size_t HW = (size_t)p.cam.W * p.cam.H;
 
@@ -378,22 +389,36 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
     if ((int)threadIdx.x < n) {
       const uint32_t g = p.gids[lo + threadIdx.x];
       const float4 co = p.co[g];
+      const float2 u = p.uv[g];
       s_gid[threadIdx.x] = g;
-      s_uv[threadIdx.x] = p.uv[g];
+      s_uv[threadIdx.x] = u;
       s_co[threadIdx.x] = co;
-      s_ext[threadIdx.x] = warp_skip_extent(co, 3.5f, 2.f * PPT - 0.5f);
+      // the skip test of all NW warp blocks (2 columns x NW/2 rows of 8 x 4 PPT pixels)
+      const float2 ext = warp_skip_extent(co, 3.5f, 2.f * PPT - 0.5f);
+      const float x0 = (float)(tx * kTile) + 4.f, y0 = (float)(ty * kTile) + 2.f * PPT;
+      uint32_t xok = 0, yok = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) xok |= (fabsf(u.x - (x0 + 8.f * c)) > ext.x ? 0u : 1u) << c;
+#pragma unroll
+      for (int r = 0; r < NW / 2; ++r) yok |= (fabsf(u.y - (y0 + 4.f * PPT * r)) > ext.y ? 0u : 1u) << r;
+      uint32_t m = 0;
+#pragma unroll
+      for (int w8 = 0; w8 < NW; ++w8) m |= ((xok >> (w8 & 1)) & (yok >> (w8 >> 1)) & 1u) << w8;
+      s_wmask[threadIdx.x] = (uint8_t)m;
       if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
       if (COUPLED && NC > 0) load_feat_row<NFs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
     }
     __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
+    // this warp's Gaussians of the batch, 32 at a time, in reverse list order
+    for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
+    const int jj = base + lane;
+    uint32_t bits = __ballot_sync(0xffffffffu, jj < n && ((s_wmask[jj] >> wid) & 1u));
+    while (bits) {
+      const int jb = 31 - __clz(bits);
+      bits &= ~(1u << jb);
+      const int j = base + jb;
       const int pos = lo + j - rg.x;
       const float2 uj = s_uv[j];
-      if (warp_skips(uj, s_ext[j], wc)) {
-#pragma unroll
-        for (int r = 0; r < CHP / 32; ++r) s_red[wid][j][32 * r + lane] = 0.f;
-        continue;
-      }
       const float4 cj = s_co[j];
       float v[CHP];
 #pragma unroll
@@ -458,12 +483,15 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
         for (int r = 0; r < CHP / 32; ++r) s_red[wid][j][32 * r + lane] = 0.f;
       }
     }
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < n * CH; e += NT) {
       const int j = e / CH, ch = e - j * CH;
+      const uint32_t wm = s_wmask[j];  // rows of warps that skipped j were not written
       float sum = 0.f;
 #pragma unroll
-      for (int w8 = 0; w8 < NW; ++w8) sum += s_red[w8][j][ch];
+      for (int w8 = 0; w8 < NW; ++w8)
+        if ((wm >> w8) & 1u) sum += s_red[w8][j][ch];
       if (sum == 0.f) continue;
       const uint32_t g = s_gid[j];
       float* dst;
