@@ -812,6 +812,23 @@ def run_forms(args):
         ms, _ = _time_frames(fn, timed, flush, stream)
         _, per = _time_frames(fn, timed[:3], flush, stream, trace=True)
         forms[name] = {"ms_per_frame": float(np.mean(ms)), "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
+    # open-vocabulary read-out (Eq. 11): L = 32 query vectors against the decoded 512-d pixel features
+    gq = torch.Generator(device=dev).manual_seed(12)
+    queries = torch.randn(32, N_WIDE, device=dev, generator=gq) / math.sqrt(N_WIDE)
+    inf_dec(frames[0])
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.label_probs(y_out, queries)
+    lq_ms = []
+    for i in range(5):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.label_probs(y_out, queries)
+        b.record(stream)
+        torch.cuda.synchronize()
+        lq_ms.append(a.elapsed_time(b))
+    lq = float(np.median(lq_ms))
     dk = forms["latent16_decoder"]["kernel_ms_per_frame"].get("k_decoder_fwd_tc", float("nan"))
     flops = 2.0 * HW * (16 * 128 + 128 * 512)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
@@ -823,6 +840,8 @@ def run_forms(args):
         "speedup_vs_tensor_core": forms["tensor_core"]["ms_per_frame"] / forms["latent16_decoder"]["ms_per_frame"],
         "held_out_quality_vs_plain_512": quality, "held_out_poses": n_held, "train_poses": n_train,
         "train_steps": args.train_steps, "train_seconds": train_s, "train_samples_per_step": 65536,
+        "label_query": {"labels": 32, "ms": lq, "feature_read_GBps": HW * N_WIDE * 4 / (lq * 1e-3) / 1e9,
+                        "fp32_TFLOPs": 2.0 * HW * N_WIDE * 32 / (lq * 1e-3) / 1e12},
         "roofline": {"bound": "tensor", "kernel": "k_decoder_fwd_tc", "achieved": flops / (dk * 1e-3) / 1e12,
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": flops / (dk * 1e-3) / 1e12 / bf16_peak,
                      "output_write_GBps": HW * N_WIDE * 4 / (dk * 1e-3) / 1e9, "traffic": None},

@@ -287,6 +287,36 @@ gs_status gs_pose_update(float* pose_dev, const float* d_pose, float* adam_m, fl
                          float tol_trans, float tol_rot, int32_t* converged, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Semantic supervision and read-out of the feature field (Sec. 3.3).
+ *
+ * gs_semantic_ce_grad -- the ground-truth loss of Eq. 8 on the rendered map
+ * feat (N channels, layout CHW [N,H,W] or HWC [H,W,N]) read as per-pixel
+ * logits normalised by a softmax over the channels:
+ *   loss_sum += (1/HW) sum_p [logsumexp_c F_p(c) - F_p(l_p)],
+ *   grad (same layout, may be NULL) = (softmax(F_p) - onehot(l_p)) / HW,
+ * labels [H,W] int32; a label outside [0, N) marks an ignored pixel (no loss,
+ * zero gradient). grad is the feature cotangent for gs_render_bwd.
+ */
+gs_status gs_semantic_ce_grad(int32_t width, int32_t height, int32_t N, int32_t layout, const float* feat,
+                              const int32_t* labels, float* grad, float* loss_sum, void* stream);
+
+/* gs_argmax_labels -- predicted labels argmax_c F_p(c) (Eq. 9; ties take the
+ * lowest channel) of feat (layout as above) into labels [H,W] int32.
+ */
+gs_status gs_argmax_labels(int32_t width, int32_t height, int32_t N, int32_t layout, const float* feat,
+                           int32_t* labels, void* stream);
+
+/* gs_label_probs -- label probabilities of Eq. 11 for npix pixel features
+ * feat [npix, M] (fp32 rows, 16-byte aligned; M % 4 == 0) against L query
+ * vectors queries [L, M] (1 <= L <= 64, L M <= 51200):
+ *   probs [npix, L] (may be NULL) = softmax_l(f . q(l)),
+ *   labels [npix] int32 (may be NULL) = argmax_l f . q(l) (ties: lowest l).
+ * At least one output must be given.
+ */
+gs_status gs_label_probs(int64_t npix, int32_t M, int32_t L, const float* feat, const float* queries,
+                         float* probs, int32_t* labels, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Per-pixel feature decoder o(.) of Eq. 9, read as a 1x1 lift of a rendered
  * latent map (a din-channel render of per-Gaussian latents):
  *     y = W2^T gelu(W1^T z + b1) + b2,   gelu(x) = x (1 + erf(x / sqrt 2)) / 2.

@@ -156,6 +156,46 @@ def pose_update(pose, g, m, v, step, lr_t, lr_r, b1=0.9, b2=0.999, eps=1e-8, tol
                                      ctypes.c_double(eps), ctypes.c_double(tol_t), ctypes.c_double(tol_r)))
 
 
+def semantic_ce(feat, labels, hwc=False):
+    """(loss, grad) of Eq. 8 on logits feat ([N,H,W], or [H,W,N] with hwc) in double."""
+    feat = _f64(feat)
+    if hwc:
+        H, W, N = feat.shape
+    else:
+        N, H, W = feat.shape
+    lab = np.ascontiguousarray(labels, np.int32)
+    grad = np.zeros_like(feat)
+    lib().ora_semantic_ce.restype = ctypes.c_double
+    loss = lib().ora_semantic_ce(ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(N), ctypes.c_int(int(hwc)), _p(feat),
+                                 lab.ctypes.data_as(ctypes.c_void_p), _p(grad))
+    return float(loss), grad
+
+
+def argmax_labels(feat, hwc=False):
+    """Eq. 9: argmax over the channels (first maximum) of the given binary32 values."""
+    return np.argmax(np.asarray(feat), axis=-1 if hwc else 0).astype(np.int32)
+
+
+def label_logits_b32(f, q):
+    """Eq. 11 logits replayed in binary32 (the GPU's fused multiply-add order); f [npix, M], q [L, M]."""
+    f = np.ascontiguousarray(f, np.float32)
+    q = np.ascontiguousarray(q, np.float32)
+    z = np.zeros((f.shape[0], q.shape[0]), np.float32)
+    lib().ora_label_logits_b32(ctypes.c_longlong(f.shape[0]), ctypes.c_int(f.shape[1]), ctypes.c_int(q.shape[0]),
+                               f.ctypes.data_as(ctypes.c_void_p), q.ctypes.data_as(ctypes.c_void_p),
+                               z.ctypes.data_as(ctypes.c_void_p))
+    return z
+
+
+def label_probs(f, q):
+    """Eq. 11 probabilities in double; f [npix, M], q [L, M]."""
+    f, q = _f64(f), _f64(q)
+    out = np.zeros((f.shape[0], q.shape[0]))
+    lib().ora_label_probs(ctypes.c_longlong(f.shape[0]), ctypes.c_int(f.shape[1]), ctypes.c_int(q.shape[0]), _p(f),
+                          _p(q), _p(out))
+    return out
+
+
 def visibility(cam, ranges, gids, uv, conic, opacity):
     """Per Gaussian, the largest transmittance in front of it over the pixels where it is blended
     (0 where blended nowhere); visible in the keyframe sense (Sec. 3.2) when it exceeds 0.5."""

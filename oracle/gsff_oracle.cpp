@@ -23,6 +23,10 @@
 //                        of the Sobel test, so the decision matches bit for bit.
 //   ora_tracking_grad    cotangents and value of the tracking loss (Eq. 5).
 //   ora_pose_update      Adam on the pose tangent and T <- Exp(delta) T.
+//   ora_semantic_ce      Eq. 8 cross-entropy of per-pixel logits and its gradient.
+//   ora_label_logits_b32 Eq. 11 logits f . q(l) replayed in binary32 with the
+//                        GPU's order of fused multiply-adds (for the argmax).
+//   ora_label_probs      Eq. 11 probabilities in double.
 //   ora_render_bwd       adjoint of Eq. 2-3 per pixel from the stored list of
 //                        blended Gaussians (no division by 1-alpha).
 //   ora_project_bwd_f64  adjoint of the projection and the Lie-algebra pose
@@ -950,6 +954,61 @@ int ora_pose_update(double* pose, const double* g, double* m, double* v, int ste
   }
   const double tn = std::sqrt(td[0] * td[0] + td[1] * td[1] + td[2] * td[2]);
   return (tn < tol_t && phi < tol_r) ? 1 : 0;
+}
+
+
+// ---- semantics (Sec. 3.3) -------------------------------------------------------
+
+// Eq. 8 with F_p read as logits: loss = (1/HW) sum_p [log sum_c exp F_p(c) - F_p(l_p)],
+// grad = (softmax(F_p) - onehot(l_p)) / HW; labels outside [0, N) are ignored.
+// Layout: hwc = 0 -> F[c * HW + p], 1 -> F[p * N + c].
+double ora_semantic_ce(int W, int H, int N, int hwc, const double* F, const int32_t* labels, double* grad) {
+  const size_t HW = (size_t)W * H;
+  auto at = [&](size_t p, int c) { return hwc ? p * (size_t)N + c : (size_t)c * HW + p; };
+  double loss = 0.0;
+  for (size_t p = 0; p < HW; ++p) {
+    const int lab = labels[p];
+    if (lab < 0 || lab >= N) {
+      for (int c = 0; c < N; ++c) grad[at(p, c)] = 0.0;
+      continue;
+    }
+    double mx = -INFINITY;
+    for (int c = 0; c < N; ++c) mx = std::max(mx, F[at(p, c)]);
+    double sum = 0.0;
+    for (int c = 0; c < N; ++c) sum += std::exp(F[at(p, c)] - mx);
+    loss += (mx + std::log(sum) - F[at(p, lab)]) / (double)HW;
+    for (int c = 0; c < N; ++c)
+      grad[at(p, c)] = (std::exp(F[at(p, c)] - mx) / sum - (c == lab ? 1.0 : 0.0)) / (double)HW;
+  }
+  return loss;
+}
+
+// Eq. 11 logits in binary32: z_l = fma(f[M-1], q_l[M-1], ... fma(f[0], q_l[0], 0)),
+// one rounding per fused multiply-add in channel order.
+void ora_label_logits_b32(long long npix, int M, int L, const float* f, const float* q, float* z) {
+  for (long long p = 0; p < npix; ++p)
+    for (int l = 0; l < L; ++l) {
+      float acc = 0.f;
+      for (int c = 0; c < M; ++c) acc = std::fmaf(f[p * M + c], q[(size_t)l * M + c], acc);
+      z[p * L + l] = acc;
+    }
+}
+
+// Eq. 11 probabilities in double.
+void ora_label_probs(long long npix, int M, int L, const double* f, const double* q, double* probs) {
+  std::vector<double> z((size_t)L);
+  for (long long p = 0; p < npix; ++p) {
+    double mx = -INFINITY;
+    for (int l = 0; l < L; ++l) {
+      double acc = 0.0;
+      for (int c = 0; c < M; ++c) acc += f[p * M + c] * q[(size_t)l * M + c];
+      z[l] = acc;
+      mx = std::max(mx, acc);
+    }
+    double sum = 0.0;
+    for (int l = 0; l < L; ++l) sum += std::exp(z[l] - mx);
+    for (int l = 0; l < L; ++l) probs[p * L + l] = std::exp(z[l] - mx) / sum;
+  }
 }
 
 }  // extern "C"

@@ -37,7 +37,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
-           "gs_pose_update")
+           "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs")
 
 
 class GsffError(RuntimeError):
@@ -117,6 +117,12 @@ def lib():
     L.gs_tracking_loss_grad.restype = ctypes.c_int
     L.gs_pose_update.argtypes = [_vp] * 4 + [_i32] + [_f] * 7 + [_vp, _vp]
     L.gs_pose_update.restype = ctypes.c_int
+    L.gs_semantic_ce_grad.argtypes = [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]
+    L.gs_semantic_ce_grad.restype = ctypes.c_int
+    L.gs_argmax_labels.argtypes = [_i32, _i32, _i32, _i32, _vp, _vp, _vp]
+    L.gs_argmax_labels.restype = ctypes.c_int
+    L.gs_label_probs.argtypes = [_i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp]
+    L.gs_label_probs.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
     L.gs_render_bwd_workspace_bytes.restype = _sz
     L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +
@@ -284,6 +290,49 @@ def pose_update(pose, d_pose, m, v, step, lr_trans=1e-3, lr_rot=3e-3, beta1=0.9,
     _check(lib().gs_pose_update(_ptr(pose), _ptr(d_pose), _ptr(m), _ptr(v), int(step), float(lr_trans),
                                 float(lr_rot), float(beta1), float(beta2), float(eps), float(tol_trans),
                                 float(tol_rot), _ptr(converged), _stream(stream)), "gs_pose_update")
+
+
+def _feat_shape(feat, layout):
+    _need(feat, torch.float32, "feat")
+    if layout == GS_LAYOUT_CHW:
+        N, H, W = feat.shape
+    else:
+        H, W, N = feat.shape
+    return N, H, W
+
+
+def semantic_ce_grad(feat, labels, layout=GS_LAYOUT_CHW, grad=None, loss=None, stream=None):
+    """gs_semantic_ce_grad (Eq. 8): the softmax cross-entropy cotangent of a rendered map; labels < 0 ignored."""
+    N, H, W = _feat_shape(feat, layout)
+    _need(labels, torch.int32, "labels", (H, W))
+    g = grad if grad is not None else torch.empty_like(feat)
+    _check(lib().gs_semantic_ce_grad(W, H, N, layout, _ptr(feat), _ptr(labels), _ptr(g), _ptr(loss),
+                                     _stream(stream)), "gs_semantic_ce_grad")
+    return g
+
+
+def argmax_labels(feat, layout=GS_LAYOUT_CHW, out=None, stream=None):
+    """gs_argmax_labels (Eq. 9): int32 [H,W] labels, ties to the lowest channel."""
+    N, H, W = _feat_shape(feat, layout)
+    o = out if out is not None else torch.empty(H, W, dtype=torch.int32, device=feat.device)
+    _check(lib().gs_argmax_labels(W, H, N, layout, _ptr(feat), _ptr(o), _stream(stream)), "gs_argmax_labels")
+    return o
+
+
+def label_probs(feat, queries, probs=True, labels=True, stream=None):
+    """gs_label_probs (Eq. 11): (probs [npix, L], labels [npix]) of pixel features [npix, M] against
+    queries [L, M]; either output can be skipped."""
+    _need(feat, torch.float32, "feat")
+    _need(queries, torch.float32, "queries")
+    npix, M = feat.shape
+    L = queries.shape[0]
+    if queries.shape[1] != M:
+        raise GsffError("queries must be [L, M] with the features' M")
+    pr = torch.empty(npix, L, device=feat.device) if probs else None
+    lb = torch.empty(npix, dtype=torch.int32, device=feat.device) if labels else None
+    _check(lib().gs_label_probs(npix, M, L, _ptr(feat), _ptr(queries), _ptr(pr), _ptr(lb), _stream(stream)),
+           "gs_label_probs")
+    return pr, lb
 
 
 def visibility_iou(vis_a, vis_b, counts=None, stream=None):

@@ -111,3 +111,34 @@ def test_tracking_pins_catch_planted_mistake(tmp_path, name):
         except AssertionError:
             failed.append(tname)
     assert failed, f"no pin caught: {name}"
+
+
+# planted slips in the semantic pieces, caught by tests/test_oracle_semantic.py
+SEMANTIC_MUTATIONS = {
+    "cross-entropy gradient without 1/HW": (
+        "grad[at(p, c)] = (std::exp(F[at(p, c)] - mx) / sum - (c == lab ? 1.0 : 0.0)) / (double)HW;",
+        "grad[at(p, c)] = (std::exp(F[at(p, c)] - mx) / sum - (c == lab ? 1.0 : 0.0));"),
+    "cross-entropy sign": (
+        "loss += (mx + std::log(sum) - F[at(p, lab)]) / (double)HW;",
+        "loss += (F[at(p, lab)] - mx - std::log(sum)) / (double)HW;"),
+    "logits with a separate multiply and add": (
+        "for (int c = 0; c < M; ++c) acc = std::fmaf(f[p * M + c], q[(size_t)l * M + c], acc);",
+        "for (int c = 0; c < M; ++c) { const float pr = f[p * M + c] * q[(size_t)l * M + c]; acc = acc + pr; }"),
+    "label probabilities not normalised": (
+        "for (int l = 0; l < L; ++l) probs[p * L + l] = std::exp(z[l] - mx) / sum;",
+        "for (int l = 0; l < L; ++l) probs[p * L + l] = std::exp(z[l] - mx);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SEMANTIC_MUTATIONS))
+def test_semantic_pins_catch_planted_mistake(tmp_path, name):
+    import tests.test_oracle_semantic as spins
+    old, new = SEMANTIC_MUTATIONS[name]
+    mut = _load_mutant(tmp_path, name, old, new)
+    failed = []
+    for tname in sorted(n for n in dir(spins) if n.startswith("test_")):
+        try:
+            getattr(spins, tname)(mut)
+        except AssertionError:
+            failed.append(tname)
+    assert failed, f"no pin caught: {name}"
