@@ -829,6 +829,23 @@ def run_forms(args):
         torch.cuda.synchronize()
         lq_ms.append(a.elapsed_time(b))
     lq = float(np.median(lq_ms))
+    # the same labels straight from the latent render (gs_decoder_labels_tc: the 512-d field is never formed)
+
+    def labels_fused(k):
+        fw = lat_ras.forward(frame_camera(k), *scene, trn.lat)
+        dec.labels_tc(fw["feat"].reshape(HW, 16), queries)
+
+    def labels_two_step(k):
+        inf_dec(k)
+        g.label_probs(y_out, queries)
+
+    lab_forms = {}
+    for name, fn in (("latent16_decoder_then_label_probs", labels_two_step), ("latent16_labels_fused", labels_fused)):
+        for k in frames[:args.warmup]:
+            fn(k)
+        ms, _ = _time_frames(fn, timed, flush, stream)
+        _, per = _time_frames(fn, timed[:3], flush, stream, trace=True)
+        lab_forms[name] = {"ms_per_frame": float(np.mean(ms)), "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
     dk = forms["latent16_decoder"]["kernel_ms_per_frame"].get("k_decoder_fwd_tc", float("nan"))
     flops = 2.0 * HW * (16 * 128 + 128 * 512)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
@@ -841,7 +858,8 @@ def run_forms(args):
         "held_out_quality_vs_plain_512": quality, "held_out_poses": n_held, "train_poses": n_train,
         "train_steps": args.train_steps, "train_seconds": train_s, "train_samples_per_step": 65536,
         "label_query": {"labels": 32, "ms": lq, "feature_read_GBps": HW * N_WIDE * 4 / (lq * 1e-3) / 1e9,
-                        "fp32_TFLOPs": 2.0 * HW * N_WIDE * 32 / (lq * 1e-3) / 1e12},
+                        "fp32_TFLOPs": 2.0 * HW * N_WIDE * 32 / (lq * 1e-3) / 1e12,
+                        "label_frames": lab_forms},
         "roofline": {"bound": "tensor", "kernel": "k_decoder_fwd_tc", "achieved": flops / (dk * 1e-3) / 1e12,
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": flops / (dk * 1e-3) / 1e12 / bf16_peak,
                      "output_write_GBps": HW * N_WIDE * 4 / (dk * 1e-3) / 1e9, "traffic": None},

@@ -360,6 +360,19 @@ gs_status gs_decoder_train(const gs_decoder* dec, int64_t nsample, int64_t npix,
 gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, const float* z, float* y, int32_t* status,
                             void* stream);
 
+/* Label read-out of the decoded field without forming it (Eq. 9 composed
+ * with Eq. 11): since y = W2^T h + b2, the logit of query l is
+ * y . q(l) = h . G(:, l) + c(l) with G = W2 q^T and c = b2 . q^T, so per
+ * pixel the 16-d latent z [npix, 16] goes through W1, the GELU (rounded to
+ * bf16) and one tcgen05 product with G (folded in fp32, rounded to bf16);
+ * probs [npix, L] (may be NULL) = softmax_l, labels [npix] (may be NULL) =
+ * argmax_l (ties: lowest l). queries [L, 512], 1 <= L <= 64; din = 16,
+ * dh = 128, dout = 512. Device errors are OR-ed into *status (may be NULL).
+ */
+gs_status gs_decoder_labels_tc(const gs_decoder* dec, int64_t npix, const float* z, int32_t L,
+                               const float* queries, float* probs, int32_t* labels, int32_t* status,
+                               void* stream);
+
 /* Adam (Kingma and Ba 2015) with bias correction on n parameters at step
  * `step` (>= 1); param_bf16 (may be NULL) receives the updated parameters
  * rounded to bf16 (stored as fp32), the copy the decoder multiplies with. */

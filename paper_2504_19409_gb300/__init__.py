@@ -37,7 +37,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
-           "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs")
+           "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc")
 
 
 class GsffError(RuntimeError):
@@ -123,6 +123,8 @@ def lib():
     L.gs_argmax_labels.restype = ctypes.c_int
     L.gs_label_probs.argtypes = [_i64, _i32, _i32, _vp, _vp, _vp, _vp, _vp]
     L.gs_label_probs.restype = ctypes.c_int
+    L.gs_decoder_labels_tc.argtypes = [ctypes.POINTER(GsDecoder), _i64, _vp, _i32, _vp, _vp, _vp, _vp, _vp]
+    L.gs_decoder_labels_tc.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
     L.gs_render_bwd_workspace_bytes.restype = _sz
     L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +

@@ -981,6 +981,237 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 }  // namespace
+
+// Label read-out straight from the latent render (Eq. 9 composed with
+// Eq. 11): with y = W2^T h + b2, the logit of label l is
+//   y . q(l) = h . G(:, l) + c(l),   G = W2 q^T [128 x L],   c = b2 . q^T,
+// so the 512-d features never have to be formed. Per 128-pixel tile:
+//   D1 [128 x 128] = z W1 (one K=16 MMA), h = gelu(D1 + b1) -> bf16 -> H,
+//   D3 [128 x Lp] = H G   (8 K=16 MMAs, Lp = L rounded up to 16, G in bf16),
+//   then per pixel row: logits D3 + c over the first L columns, argmax and
+//   softmax. Each CTA folds G and c once (fp32 dot products over the 512
+//   channels, from the queries staged in shared memory).
+// Layouts (validated rule: LBO along K, SBO along M/N):
+//   G : (n/8)*128 + (k/8)*(Lp*16) + (k%8)*16 + (n%8)*2   LBO Lp*16, SBO 128
+// D3 reuses tensor-memory columns [0, Lp) of D1 once the GELU has read D1.
+namespace {
+
+constexpr int kDecLabMax = 64;
+
+struct DecLabSmem {
+  uint8_t H[128 * 128 * 2];          // 32 KB
+  uint8_t W1[16 * 128 * 2];          // 4 KB
+  uint8_t Z[128 * 16 * 2];           // 4 KB
+  uint8_t G[128 * kDecLabMax * 2];   // 16 KB
+  float qs[kDecLabMax * 512];        // 128 KB: the queries, fp32
+  float b1[128];
+  float b2[512];
+  float cq[kDecLabMax];
+  unsigned long long mbar;
+  uint32_t tmem;
+};
+
+struct DecLabParams {
+  long long npix;
+  int L, Lp;
+  const float* z;
+  const float* W1;
+  const float* b1;
+  const float* W2;
+  const float* b2;
+  const float* q;
+  float* probs;
+  int32_t* labels;
+  int32_t* status;
+};
+
+__global__ void __launch_bounds__(512, 1) k_decoder_labels_tc(const DecLabParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  DecLabSmem& S = *reinterpret_cast<DecLabSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lg = warp & 3, cq = warp >> 2;
+  const int row = 32 * lg + lane;
+  const int L = p.L, Lp = p.Lp;
+
+  for (int e = tid; e < 16 * 128; e += 512) {
+    const int k = e / 128, n = e % 128;
+    *reinterpret_cast<__nv_bfloat16*>(S.W1 + (n >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 + (n & 7) * 2) =
+        __float2bfloat16_rn(p.W1[e]);
+  }
+  for (int e = tid; e < 128; e += 512) S.b1[e] = p.b1[e];
+  for (int e = tid; e < 512; e += 512) S.b2[e] = p.b2[e];
+  for (int e = tid; e < L * 512; e += 512) S.qs[e] = p.q[e];
+  __syncthreads();
+  // fold: G[k][l] = W2[k, :] . q[l, :] (0 for padded columns), c[l] = b2 . q[l, :].
+  // Thread (k = tid % 128, group g = tid / 128) takes labels g, g + 4, ...: it
+  // streams its W2 row once and reuses it for all of them (the label index is
+  // the same across a warp, so the query reads are broadcasts).
+  {
+    constexpr int PER = kDecLabMax / 4;
+    const int k = tid & 127, g4 = tid >> 7;
+    float acc[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) acc[i] = 0.f;
+    const float4* w = reinterpret_cast<const float4*>(p.W2 + (size_t)k * 512);
+#pragma unroll 4
+    for (int j = 0; j < 128; ++j) {
+      const float4 a = __ldg(w + j);
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int l = g4 + 4 * i;
+        if (l < L) {
+          const float4 b = *reinterpret_cast<const float4*>(S.qs + (size_t)l * 512 + 4 * j);
+          acc[i] = fmaf(a.x, b.x, acc[i]);
+          acc[i] = fmaf(a.y, b.y, acc[i]);
+          acc[i] = fmaf(a.z, b.z, acc[i]);
+          acc[i] = fmaf(a.w, b.w, acc[i]);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int l = g4 + 4 * i;
+      if (l < Lp)
+        *reinterpret_cast<__nv_bfloat16*>(S.G + (l >> 3) * 128 + (k >> 3) * (Lp * 16) + (k & 7) * 16 + (l & 7) * 2) =
+            __float2bfloat16_rn(l < L ? acc[i] : 0.f);
+    }
+  }
+  for (int l = tid; l < L; l += 512) {
+    float acc = 0.f;
+    for (int j = 0; j < 512; ++j) acc = fmaf(S.b2[j], S.qs[l * 512 + j], acc);
+    S.cq[l] = acc;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = S.tmem;
+  const uint32_t idesc1 = idesc_bf16(128, 128, 1), idesc3 = idesc_bf16(128, Lp, 1);
+  const long long ntiles = (p.npix + 127) / 128;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const long long base = t * 128;
+    if (cq < 2) {
+      const long long pix = base + row;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      if (pix < p.npix) {
+        const float4 a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * cq);
+        const float4 b = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * cq + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      }
+      uint32_t pk[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      *reinterpret_cast<uint4*>(S.Z + (row >> 3) * 256 + cq * 128 + (row & 7) * 16) =
+          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      mma_bf16(tmem, smem_desc(smem_u32(S.Z), 128, 256), smem_desc(smem_u32(S.W1), 2048, 128), idesc1, 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.mbar)));
+    }
+    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar), phase)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cq), v);
+      uint32_t pk[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float h0 = gelu_exact(v[2 * i] + S.b1[32 * cq + 2 * i]);
+        const float h1 = gelu_exact(v[2 * i + 1] + S.b1[32 * cq + 2 * i + 1]);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(h0, h1);
+        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(S.H + (row >> 3) * 2048 + (4 * cq + c) * 128 + (row & 7) * 16) =
+            make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_u32(S.H), g0 = smem_u32(S.G);
+#pragma unroll
+      for (int k16 = 0; k16 < 8; ++k16)
+        mma_bf16(tmem, smem_desc(a0 + k16 * 256, 128, 2048),
+                 smem_desc(g0 + (uint32_t)k16 * 2u * (uint32_t)(Lp * 16), (uint32_t)(Lp * 16), 128), idesc3,
+                 k16 > 0 ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.mbar)));
+    }
+    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar), phase)) != 0;
+    phase ^= 1u;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (cq == 0) {
+      // warps 0-3: one pixel row each, all L logits
+      float zl[kDecLabMax];
+      tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16), *reinterpret_cast<float(*)[32]>(zl));
+      if (Lp > 32) tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + 32u, *reinterpret_cast<float(*)[32]>(zl + 32));
+      const long long pix = base + row;
+      float mx = -INFINITY;
+      int arg = 0;
+#pragma unroll
+      for (int l = 0; l < kDecLabMax; ++l)
+        if (l < L) {
+          zl[l] += S.cq[l];
+          if (zl[l] > mx) {
+            mx = zl[l];
+            arg = l;
+          }
+        }
+      if (pix < p.npix) {
+        if (p.labels) p.labels[pix] = arg;
+        if (p.probs) {
+          float sum = 0.f;
+#pragma unroll
+          for (int l = 0; l < kDecLabMax; ++l)
+            if (l < L) {
+              zl[l] = expf(zl[l] - mx);
+              sum += zl[l];
+            }
+          const float is = 1.f / sum;
+#pragma unroll
+          for (int l = 0; l < kDecLabMax; ++l)
+            if (l < L) p.probs[pix * L + l] = zl[l] * is;
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (!ok && tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
+  if (!ok) mbar_wait(smem_u32(&S.mbar), phase ^ 1u);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+}  // namespace
 }  // namespace gsff
 
 extern "C" gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, const float* z, float* y, int32_t* status,
@@ -1027,5 +1258,47 @@ extern "C" gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GS_TRACE("k_decoder_fwd_tc", st);
   k_decoder_fwd_tc<<<blocks, 512, smem, st>>>(p, ymap);
+  return last_launch_status();
+}
+
+extern "C" gs_status gs_decoder_labels_tc(const gs_decoder* dec, int64_t npix, const float* z, int32_t L,
+                                          const float* queries, float* probs, int32_t* labels, int32_t* status,
+                                          void* stream) {
+  using namespace gsff;
+  if (!dec || dec->din != 16 || dec->dh != 128 || dec->dout != 512 || !dec->W1 || !dec->b1 || !dec->W2 || !dec->b2)
+    return GS_ERR_UNSUPPORTED;
+  if (npix < 0 || L <= 0 || L > kDecLabMax || !queries || (!probs && !labels) || (npix > 0 && !z) ||
+      !aligned(z, 16) || !aligned(dec->W2, 16))
+    return GS_ERR_INVALID_ARG;
+  if (npix == 0) return GS_OK;
+  DecLabParams p;
+  p.npix = npix;
+  p.L = L;
+  p.Lp = (L + 15) / 16 * 16;
+  p.z = z;
+  p.W1 = dec->W1;
+  p.b1 = dec->b1;
+  p.W2 = dec->W2;
+  p.b2 = dec->b2;
+  p.q = queries;
+  p.probs = probs;
+  p.labels = labels;
+  p.status = status;
+  const size_t smem = sizeof(DecLabSmem) + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_decoder_labels_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return GS_ERR_CUDA;
+    attr_set = true;
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (npix + 127) / 128;
+  const unsigned blocks = (unsigned)(ntiles < sms ? ntiles : sms);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GS_TRACE("k_decoder_labels_tc", st);
+  k_decoder_labels_tc<<<blocks, 512, smem, st>>>(p);
   return last_launch_status();
 }

@@ -77,6 +77,17 @@ class Decoder:
                "gs_decoder_fwd_tc")
         return y
 
+    def labels_tc(self, z: torch.Tensor, queries: torch.Tensor, probs=True, labels=True, status=None, stream=None):
+        """Eq. 11 label probabilities / labels of the decoded field straight from the latents z [n, 16]
+        (the 512-d features are never formed): returns (probs [n, L] or None, labels [n] or None)."""
+        n, L = z.shape[0], queries.shape[0]
+        pr = torch.empty(n, L, device=self.device) if probs else None
+        lb = torch.empty(n, dtype=torch.int32, device=self.device) if labels else None
+        d = self.struct()
+        _check(lib().gs_decoder_labels_tc(ctypes.byref(d), n, _ptr(z), L, _ptr(queries.contiguous()), _ptr(pr),
+                                          _ptr(lb), _ptr(status), _stream(stream)), "gs_decoder_labels_tc")
+        return pr, lb
+
     def zero_grad(self):
         for g in self.grads.values():
             g.zero_()

@@ -188,3 +188,45 @@ def test_decoder_tensor_core_forward_within_bound(dec_mod, ora):
     err = np.abs(_np(y) - ref)
     assert (err <= bound).all(), float((err / bound).max())
     assert (err / bound).max() > 0.01
+
+
+def test_decoder_labels_from_latents_within_bound(dec_mod, ora):
+    """gs_decoder_labels_tc against the oracle's decoded field dotted with the
+    queries: z rounded to bf16 (as in the tensor-core decoder), the hidden
+    layer h and the folded G = W2 q^T rounded to bf16, so each logit lies
+    within 2^-8 sum_k |h_k| |G_kl| + 1e-5 (sum_k |h_k| |G_kl| + |c_l|) + 1e-6 of
+    the exact one. Labels must agree wherever the oracle's two largest logits
+    are more than twice that apart; probabilities within twice the pixel's
+    largest bound."""
+    from math import erf, sqrt
+    dec = dec_mod.Decoder(seed=17)
+    dec.params["b1"].normal_(0, 0.2)
+    dec.params["b2"].normal_(0, 0.2)
+    rng = np.random.default_rng(18)
+    n, L = 1000 + 37, 24
+    z = torch.tensor(rng.normal(size=(n, 16)).astype(np.float32), device="cuda")
+    q = torch.tensor((rng.normal(size=(L, 512)) / np.sqrt(512) * 4).astype(np.float32), device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    probs, labels = dec.labels_tc(z, q, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    zb = z.to(torch.bfloat16).double().cpu().numpy()
+    W1, b1, W2, b2 = _np(dec.work["W1"]), _np(dec.params["b1"]), _np(dec.work["W2"]), _np(dec.params["b2"])
+    qn = _np(q)
+    y = ora.decoder_fwd(zb, W1, b1, W2, b2)
+    logits = y @ qn.T
+    h = zb @ W1 + b1
+    h = 0.5 * h * (1 + np.vectorize(erf)(h / sqrt(2)))
+    G, c = W2 @ qn.T, b2 @ qn.T
+    hg = np.abs(h) @ np.abs(G)
+    bound = 2.0 ** -8 * hg + 1e-5 * (hg + np.abs(c)) + 1e-6
+    srt = np.sort(logits, axis=1)
+    sure = (srt[:, -1] - srt[:, -2]) > 2 * bound.max(axis=1)
+    assert sure.mean() > 0.9
+    assert np.array_equal(labels.cpu().numpy()[sure], np.argmax(logits, axis=1)[sure])
+    e = np.exp(logits - logits.max(1, keepdims=True))
+    p_ref = e / e.sum(1, keepdims=True)
+    err = np.abs(probs.cpu().numpy() - p_ref)
+    assert (err <= 2 * bound.max(axis=1, keepdims=True) + 1e-6).all(), float(err.max())
+    _, lab_only = dec.labels_tc(z, q, probs=False)
+    assert torch.equal(lab_only, labels)

@@ -38,7 +38,8 @@ def _render(gs, cam, scene, P):
 
 def test_device_pose_equals_host_pose(gs, sg, room):
     """The same R, t given through gs_camera.pose_dev: projection and
-    images bit-identical, pose gradient identical."""
+    images bit-identical, pose gradient equal up to the order of float
+    atomics; the pose-only adjoint gives the full adjoint's pose gradient."""
     sc, scene = room
     cam = sg.room_trajectory(21).as_f32()
     pose = _t(np.concatenate([cam.R.reshape(9), cam.t]).astype(np.float32))
@@ -60,9 +61,11 @@ def test_device_pose_equals_host_pose(gs, sg, room):
         only = ras.render_pose_grad(c, scene[0], scene[1], scene[2], scene[4], g_rgb, None,
                                     dict(pose=torch.zeros(6, device="cuda")))["pose"]
         torch.cuda.synchronize()
-        assert torch.allclose(full, only, rtol=1e-5, atol=1e-9 * float(full.abs().max()))
+        # the pose tangent sums large terms of both signs over the Gaussians, in
+        # atomic order: compare normwise (1e-5), as the other gradient checks do
+        assert float(torch.linalg.norm(full - only)) <= 1e-5 * float(torch.linalg.norm(full))
         poses.append(full)
-    assert torch.allclose(poses[0], poses[1], rtol=1e-5, atol=1e-9 * float(poses[0].abs().max()))
+    assert float(torch.linalg.norm(poses[0] - poses[1])) <= 1e-5 * float(torch.linalg.norm(poses[0]))
 
 
 @pytest.mark.parametrize("tau", [0.005, 0.02, 0.08])
