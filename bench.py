@@ -154,8 +154,8 @@ def algorithmic_flops(stats):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/render_fwd_bwd_room300k_N16_full.md, keyed to
 # the source it was taken on (null once render.cu changes).
-NCU_TRAFFIC = {"k_render_bwd": (99_159_552 + 3_572_992, "9335d006c9954fb7"),
-               "k_render_fwd": (19_293_952 + 24_538_880, "9335d006c9954fb7")}
+NCU_TRAFFIC = {"k_render_bwd": (99_178_752 + 4_075_264, "5b54a841ca877189"),
+               "k_render_fwd": (19_341_824 + 24_354_816, "5b54a841ca877189")}
 
 
 def ncu_traffic(kernel):
