@@ -287,6 +287,30 @@ gs_status gs_pose_update(float* pose_dev, const float* d_pose, float* adam_m, fl
                          float tol_trans, float tol_rot, int32_t* converged, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * View-dependent colour from spherical harmonics (Sec. 3.1: third-order SH
+ * coefficients per Gaussian).
+ *
+ * gs_sh_colors -- colors [P,3] = max(0, sum_k sh[g][k][c] Y_k(d) + 0.5) per
+ * Gaussian and channel, with d the unit direction from the camera centre
+ * C = -R^T t (the pose of cam, or cam->pose_dev) to means[g]; sh [P, K, 3]
+ * (coefficient-major, K = (degree + 1)^2, degree 0..3); k = l^2 + l + m;
+ * Y_k the real SH basis with the Condon-Shortley phase. The result is the
+ * colors input of gs_render_fwd / gs_render_bwd.
+ */
+gs_status gs_sh_colors(const gs_camera* cam, int32_t P, int32_t degree, const float* means, const float* sh,
+                       float* colors, void* stream);
+
+/* gs_sh_colors_bwd -- adjoint of gs_sh_colors for d_colors [P,3] (the d_colors
+ * of gs_render_bwd); ACCUMULATES d_sh [P, K, 3], d_means [P,3] (through the
+ * view direction) and d_pose [6] (the camera centre moves with rho only at
+ * first order: d rho += R sum_g dL/dmu_g|_view); each output may be NULL.
+ * Clamped channels pass no gradient.
+ */
+gs_status gs_sh_colors_bwd(const gs_camera* cam, int32_t P, int32_t degree, const float* means,
+                           const float* sh, const float* d_colors, float* d_sh, float* d_means,
+                           float* d_pose, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Semantic supervision and read-out of the feature field (Sec. 3.3).
  *
  * gs_semantic_ce_grad -- the ground-truth loss of Eq. 8 on the rendered map

@@ -196,6 +196,35 @@ def label_probs(f, q):
     return out
 
 
+def sh_colors(cam, means, sh):
+    """View-dependent colours [P,3] from SH coefficients sh [P, K, 3] (K = (lmax+1)^2) in double."""
+    sh = _f64(sh)
+    P, K = sh.shape[0], sh.shape[1]
+    lmax = int(round(K ** 0.5)) - 1
+    out = np.zeros((P, 3))
+    lib().ora_sh_colors(_p(cam_array(cam)), ctypes.c_int(P), ctypes.c_int(lmax), _p(_f64(means)), _p(sh), _p(out))
+    return out
+
+
+def sh_colors_bwd(cam, means, sh, d_colors):
+    """(d_sh [P,K,3], d_means [P,3], d_pose [6]) of the SH colours in double."""
+    sh = _f64(sh)
+    P, K = sh.shape[0], sh.shape[1]
+    lmax = int(round(K ** 0.5)) - 1
+    d_sh, d_means, d_pose = np.zeros_like(sh), np.zeros((P, 3)), np.zeros(6)
+    lib().ora_sh_colors_bwd(_p(cam_array(cam)), ctypes.c_int(P), ctypes.c_int(lmax), _p(_f64(means)), _p(sh),
+                            _p(_f64(d_colors)), _p(d_sh), _p(d_means), _p(d_pose))
+    return d_sh, d_means, d_pose
+
+
+def sh_basis(dirs, lmax=3):
+    """Real SH basis values [n, (lmax+1)^2] at unit directions dirs [n,3]."""
+    dirs = _f64(dirs)
+    out = np.zeros((dirs.shape[0], (lmax + 1) ** 2))
+    lib().ora_sh_basis(ctypes.c_int(dirs.shape[0]), ctypes.c_int(lmax), _p(dirs), _p(out))
+    return out
+
+
 def visibility(cam, ranges, gids, uv, conic, opacity):
     """Per Gaussian, the largest transmittance in front of it over the pixels where it is blended
     (0 where blended nowhere); visible in the keyframe sense (Sec. 3.2) when it exceeds 0.5."""

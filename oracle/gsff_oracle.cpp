@@ -27,6 +27,9 @@
 //   ora_label_logits_b32 Eq. 11 logits f . q(l) replayed in binary32 with the
 //                        GPU's order of fused multiply-adds (for the argmax).
 //   ora_label_probs      Eq. 11 probabilities in double.
+//   ora_sh_colors        view-dependent colour from SH coefficients (Sec. 3.1),
+//                        the basis from Legendre recurrences, its gradient by
+//                        forward-mode dual numbers; ora_sh_colors_bwd its adjoint.
 //   ora_render_bwd       adjoint of Eq. 2-3 per pixel from the stored list of
 //                        blended Gaussians (no division by 1-alpha).
 //   ora_project_bwd_f64  adjoint of the projection and the Lie-algebra pose
@@ -1009,6 +1012,151 @@ void ora_label_probs(long long npix, int M, int L, const double* f, const double
     for (int l = 0; l < L; ++l) sum += std::exp(z[l] - mx);
     for (int l = 0; l < L; ++l) probs[p * L + l] = std::exp(z[l] - mx) / sum;
   }
+}
+
+
+// ---- spherical-harmonic colour (Sec. 3.1) ---------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// value and the three partial derivatives with respect to the Gaussian's mean
+struct Dual {
+  double v, d[3];
+};
+Dual dconst(double c) { return {c, {0, 0, 0}}; }
+Dual operator+(Dual a, Dual b) { return {a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}}; }
+Dual operator-(Dual a, Dual b) { return {a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}}; }
+Dual operator*(Dual a, Dual b) {
+  return {a.v * b.v, {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1], a.d[2] * b.v + a.v * b.d[2]}};
+}
+Dual operator*(double c, Dual a) { return {c * a.v, {c * a.d[0], c * a.d[1], c * a.d[2]}}; }
+Dual dsqrt(Dual a) {
+  const double r = std::sqrt(a.v);
+  return {r, {a.d[0] / (2 * r), a.d[1] / (2 * r), a.d[2] / (2 * r)}};
+}
+Dual ddiv(Dual a, Dual b) {
+  const double q = a.v / b.v;
+  return {q, {(a.d[0] - q * b.d[0]) / b.v, (a.d[1] - q * b.d[1]) / b.v, (a.d[2] - q * b.d[2]) / b.v}};
+}
+
+double fact(int n) {
+  double f = 1;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+// Real SH Y_k, k = l^2 + l + m, l <= lmax, at the unit direction (x, y, z):
+// N_l^m Pbar_l^|m|(z) {sqrt2 Re (x + i y)^m | 1 | sqrt2 Im (x + i y)^|m|},
+// Pbar_l^m = P_l^m / (1 - z^2)^(m/2) (Condon-Shortley phase included) from
+// the three-term recurrence in l, N_l^m = sqrt((2l + 1) (l - m)! / (4 pi (l + m)!)).
+void sh_real_basis(int lmax, Dual x, Dual y, Dual z, Dual* Y) {
+  const double pi = 3.14159265358979323846;
+  Dual re[4], im[4];  // (x + i y)^m
+  re[0] = dconst(1);
+  im[0] = dconst(0);
+  for (int m = 1; m <= lmax; ++m) {
+    re[m] = re[m - 1] * x - im[m - 1] * y;
+    im[m] = re[m - 1] * y + im[m - 1] * x;
+  }
+  for (int m = 0; m <= lmax; ++m) {
+    Dual P[4];
+    double dfact = 1;  // (2m - 1)!!
+    for (int i = 1; i <= 2 * m - 1; i += 2) dfact *= i;
+    P[m] = dconst(((m % 2) ? -1.0 : 1.0) * dfact);
+    if (m + 1 <= lmax) P[m + 1] = (double)(2 * m + 1) * (z * P[m]);
+    for (int l = m + 2; l <= lmax; ++l)
+      P[l] = (1.0 / (l - m)) * ((double)(2 * l - 1) * (z * P[l - 1]) - (double)(l + m - 1) * P[l - 2]);
+    for (int l = m; l <= lmax; ++l) {
+      const double N = std::sqrt((2 * l + 1) / (4 * pi) * fact(l - m) / fact(l + m));
+      if (m == 0) {
+        Y[l * l + l] = N * P[l];
+      } else {
+        Y[l * l + l + m] = (std::sqrt(2.0) * N) * (P[l] * re[m]);
+        Y[l * l + l - m] = (std::sqrt(2.0) * N) * (P[l] * im[m]);
+      }
+    }
+  }
+}
+
+// Y_k(d(mu)) with d = (mu - C) / |mu - C| and its gradient in mu.
+void sh_at_mean(const double* C, const double* mu, int lmax, Dual* Y) {
+  Dual v[3];
+  for (int i = 0; i < 3; ++i) v[i] = {mu[i] - C[i], {i == 0 ? 1.0 : 0.0, i == 1 ? 1.0 : 0.0, i == 2 ? 1.0 : 0.0}};
+  const Dual len = dsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  sh_real_basis(lmax, ddiv(v[0], len), ddiv(v[1], len), ddiv(v[2], len), Y);
+}
+
+void camera_centre(const double* cam, double* C) {
+  const double* R = cam + 6;
+  const double* t = cam + 15;
+  for (int i = 0; i < 3; ++i) C[i] = -(R[i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2]);
+}
+
+}  // namespace
+
+extern "C" {
+
+// The real SH basis Y_k at n unit directions: out [n, (lmax + 1)^2].
+void ora_sh_basis(int n, int lmax, const double* dirs, double* out) {
+  const int K = (lmax + 1) * (lmax + 1);
+  Dual Y[16];
+  for (int i = 0; i < n; ++i) {
+    sh_real_basis(lmax, dconst(dirs[3 * i]), dconst(dirs[3 * i + 1]), dconst(dirs[3 * i + 2]), Y);
+    for (int k = 0; k < K; ++k) out[(size_t)i * K + k] = Y[k].v;
+  }
+}
+
+// colours [P,3] = max(0, sum_k sh[g][k][c] Y_k(d) + 0.5); sh [P, K, 3], K = (lmax + 1)^2.
+void ora_sh_colors(const double* cam, int P, int lmax, const double* means, const double* sh, double* colors) {
+  double C[3];
+  camera_centre(cam, C);
+  const int K = (lmax + 1) * (lmax + 1);
+  Dual Y[16];
+  for (int g = 0; g < P; ++g) {
+    sh_at_mean(C, means + 3 * g, lmax, Y);
+    for (int c = 0; c < 3; ++c) {
+      double v = 0.5;
+      for (int k = 0; k < K; ++k) v += sh[((size_t)g * K + k) * 3 + c] * Y[k].v;
+      colors[3 * g + c] = std::max(v, 0.0);
+    }
+  }
+}
+
+// Adjoint: d_sh += Y dcol, d_means += sum_k w_k dY_k/dmu (w_k = sum_c sh dcol),
+// d_pose[0..2] += R sum_g (view part of dL/dmu_g) (the centre moves with rho).
+void ora_sh_colors_bwd(const double* cam, int P, int lmax, const double* means, const double* sh,
+                       const double* d_colors, double* d_sh, double* d_means, double* d_pose) {
+  double C[3];
+  camera_centre(cam, C);
+  const double* R = cam + 6;
+  const int K = (lmax + 1) * (lmax + 1);
+  Dual Y[16];
+  double sum_dmu[3] = {0, 0, 0};
+  for (int g = 0; g < P; ++g) {
+    sh_at_mean(C, means + 3 * g, lmax, Y);
+    double dc[3];
+    for (int c = 0; c < 3; ++c) {
+      double v = 0.5;
+      for (int k = 0; k < K; ++k) v += sh[((size_t)g * K + k) * 3 + c] * Y[k].v;
+      dc[c] = v < 0 ? 0.0 : d_colors[3 * g + c];
+    }
+    double dmu[3] = {0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+      double w = 0;
+      for (int c = 0; c < 3; ++c) {
+        d_sh[((size_t)g * K + k) * 3 + c] += Y[k].v * dc[c];
+        w += sh[((size_t)g * K + k) * 3 + c] * dc[c];
+      }
+      for (int i = 0; i < 3; ++i) dmu[i] += w * Y[k].d[i];
+    }
+    for (int i = 0; i < 3; ++i) {
+      d_means[3 * g + i] += dmu[i];
+      sum_dmu[i] += dmu[i];
+    }
+  }
+  for (int i = 0; i < 3; ++i) d_pose[i] += R[3 * i] * sum_dmu[0] + R[3 * i + 1] * sum_dmu[1] + R[3 * i + 2] * sum_dmu[2];
 }
 
 }  // extern "C"

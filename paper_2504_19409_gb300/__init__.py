@@ -37,7 +37,8 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_trace_reset", "gs_trace_count", "gs_trace_get", "gs_status_string", "gs_version",
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
-           "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc")
+           "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
+           "gs_sh_colors", "gs_sh_colors_bwd")
 
 
 class GsffError(RuntimeError):
@@ -125,6 +126,10 @@ def lib():
     L.gs_label_probs.restype = ctypes.c_int
     L.gs_decoder_labels_tc.argtypes = [ctypes.POINTER(GsDecoder), _i64, _vp, _i32, _vp, _vp, _vp, _vp, _vp]
     L.gs_decoder_labels_tc.restype = ctypes.c_int
+    L.gs_sh_colors.argtypes = [cam_p, _i32, _i32, _vp, _vp, _vp, _vp]
+    L.gs_sh_colors.restype = ctypes.c_int
+    L.gs_sh_colors_bwd.argtypes = [cam_p, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.gs_sh_colors_bwd.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
     L.gs_render_bwd_workspace_bytes.restype = _sz
     L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +
@@ -292,6 +297,31 @@ def pose_update(pose, d_pose, m, v, step, lr_trans=1e-3, lr_rot=3e-3, beta1=0.9,
     _check(lib().gs_pose_update(_ptr(pose), _ptr(d_pose), _ptr(m), _ptr(v), int(step), float(lr_trans),
                                 float(lr_rot), float(beta1), float(beta2), float(eps), float(tol_trans),
                                 float(tol_rot), _ptr(converged), _stream(stream)), "gs_pose_update")
+
+
+def sh_colors(cam, means, sh, out=None, stream=None):
+    """gs_sh_colors: view-dependent colours [P,3] from SH coefficients sh [P, K, 3] (K = 1, 4, 9 or 16)."""
+    P, K = sh.shape[0], sh.shape[1]
+    deg = {1: 0, 4: 1, 9: 2, 16: 3}.get(K)
+    if deg is None or sh.shape[2] != 3:
+        raise GsffError("sh must be [P, K, 3] with K in (1, 4, 9, 16)")
+    _need(sh, torch.float32, "sh")
+    _need(means, torch.float32, "means", (P, 3))
+    o = out if out is not None else torch.empty(P, 3, device=sh.device)
+    c = camera_struct(cam)
+    _check(lib().gs_sh_colors(ctypes.byref(c), P, deg, _ptr(means), _ptr(sh), _ptr(o), _stream(stream)),
+           "gs_sh_colors")
+    return o
+
+
+def sh_colors_bwd(cam, means, sh, d_colors, d_sh=None, d_means=None, d_pose=None, stream=None):
+    """gs_sh_colors_bwd: accumulates into d_sh [P,K,3], d_means [P,3], d_pose [6] (any may be None)."""
+    P, K = sh.shape[0], sh.shape[1]
+    deg = {1: 0, 4: 1, 9: 2, 16: 3}[K]
+    _need(d_colors, torch.float32, "d_colors", (P, 3))
+    c = camera_struct(cam)
+    _check(lib().gs_sh_colors_bwd(ctypes.byref(c), P, deg, _ptr(means), _ptr(sh), _ptr(d_colors), _ptr(d_sh),
+                                  _ptr(d_means), _ptr(d_pose), _stream(stream)), "gs_sh_colors_bwd")
 
 
 def _feat_shape(feat, layout):

@@ -142,3 +142,38 @@ def test_semantic_pins_catch_planted_mistake(tmp_path, name):
         except AssertionError:
             failed.append(tname)
     assert failed, f"no pin caught: {name}"
+
+
+# planted slips in the spherical-harmonic colour, caught by tests/test_oracle_sh.py
+SH_MUTATIONS = {
+    "camera centre sign": (
+        "for (int i = 0; i < 3; ++i) C[i] = -(R[i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2]);",
+        "for (int i = 0; i < 3; ++i) C[i] = (R[i] * t[0] + R[3 + i] * t[1] + R[6 + i] * t[2]);"),
+    "sqrt2 dropped for m != 0": (
+        "Y[l * l + l + m] = (std::sqrt(2.0) * N) * (P[l] * re[m]);",
+        "Y[l * l + l + m] = N * (P[l] * re[m]);"),
+    "Legendre recurrence coefficient": (
+        "P[l] = (1.0 / (l - m)) * ((double)(2 * l - 1) * (z * P[l - 1]) - (double)(l + m - 1) * P[l - 2]);",
+        "P[l] = (1.0 / (l - m)) * ((double)(2 * l - 1) * (z * P[l - 1]) - (double)(l + m) * P[l - 2]);"),
+    "pose gradient without R": (
+        "for (int i = 0; i < 3; ++i) d_pose[i] += R[3 * i] * sum_dmu[0] + R[3 * i + 1] * sum_dmu[1] + R[3 * i + 2] * sum_dmu[2];",
+        "for (int i = 0; i < 3; ++i) d_pose[i] += sum_dmu[i];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SH_MUTATIONS))
+def test_sh_pins_catch_planted_mistake(tmp_path, sg, name):
+    import inspect
+
+    import tests.test_oracle_sh as shpins
+    old, new = SH_MUTATIONS[name]
+    mut = _load_mutant(tmp_path, name, old, new)
+    failed = []
+    for tname in sorted(n for n in dir(shpins) if n.startswith("test_")):
+        fn = getattr(shpins, tname)
+        kw = {"sg": sg} if "sg" in inspect.signature(fn).parameters else {}
+        try:
+            fn(mut, **kw)
+        except AssertionError:
+            failed.append(tname)
+    assert failed, f"no pin caught: {name}"
