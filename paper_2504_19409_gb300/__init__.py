@@ -479,10 +479,17 @@ class Rasterizer:
             shape = (N, height, width) if layout == GS_LAYOUT_CHW else (height, width, N)
             self.fwd["feat"] = torch.empty(shape, device=dev)
         self.bwd_ws = torch.empty(max(render_bwd_workspace_bytes(P), 256), dtype=torch.uint8, device=dev)
-        self.grads = dict(means=torch.zeros(P, 3, device=dev), scales=torch.zeros(P, 3, device=dev),
-                          quats=torch.zeros(P, 4, device=dev), opacity=torch.zeros(P, device=dev),
-                          colors=torch.zeros(P, 3, device=dev), feats=torch.zeros(P, max(N, 1), device=dev)[:, :N],
-                          pose=torch.zeros(6, device=dev))
+        # all gradient outputs are views of one buffer (each part starting on a 256-byte boundary), so
+        # zeroing them before an adjoint is a single fill
+        shapes = dict(means=(P, 3), scales=(P, 3), quats=(P, 4), opacity=(P,), colors=(P, 3), feats=(P, max(N, 1)),
+                      pose=(6,))
+        offs, n = {}, 0
+        for k, shp in shapes.items():
+            offs[k] = n
+            n += (int(np.prod(shp)) + 63) // 64 * 64
+        self.grad_arena = torch.zeros(n, device=dev)
+        self.grads = {k: self.grad_arena[offs[k]:offs[k] + int(np.prod(shp))].view(shp) for k, shp in shapes.items()}
+        self.grads["feats"] = self.grads["feats"][:, :N]
 
     def _alloc_sort(self):
         dev = self.device
@@ -513,8 +520,7 @@ class Rasterizer:
     def backward(self, cam, means, scales, quats, colors, feats=None, g_rgb=None, g_depth=None, g_alpha=None,
                  g_feat=None, bg=None, coupled=False, zero=True, stream=None):
         if zero:
-            for t in self.grads.values():
-                t.zero_()
+            self.grad_arena.zero_()
         render_bwd(cam, means, scales, quats, colors, feats, self.proj, self.sort, self.fwd, g_rgb, g_depth, g_alpha,
                    g_feat, flags=self.flags, layout=self.layout, bg=bg, coupled=coupled, grads=self.grads,
                    workspace=self.bwd_ws, status=self.status, stream=stream)
