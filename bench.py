@@ -132,6 +132,7 @@ def algorithmic_bytes(stats):
         "k_project": P * (44 + 48),
         "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12),
         "k_render_bwd": I * 4 + Pv * rec + HW * (8 + (5 + N) * 4) + Pv * (24 + (4 + N) * 4),
+        "k_render_bwd_mma": I * 4 + Pv * rec + HW * (8 + (5 + N) * 4) + Pv * (24 + (4 + N) * 4),
         "k_project_bwd": P * (40 + 24) + Pv * 40,
     }
 
@@ -148,7 +149,8 @@ def algorithmic_bytes(stats):
 #     pixels -> 55 + 10 + 2N.
 def algorithmic_flops(stats):
     E, B, N = stats["evaluated"], stats["blends"], N_FEAT
-    return {"k_render_fwd": 14 * E + (11 + 2 * N) * B, "k_render_bwd": 14 * E + (65 + 2 * N) * B}
+    bwd = 14 * E + (65 + 2 * N) * B
+    return {"k_render_fwd": 14 * E + (11 + 2 * N) * B, "k_render_bwd": bwd, "k_render_bwd_mma": bwd}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu

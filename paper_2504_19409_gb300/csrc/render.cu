@@ -29,6 +29,8 @@
 //       so that lane l ends up owning the warp sum of channel l;
 //   (2) across the warps through shared memory after each batch.
 
+#include <atomic>
+
 #include "gsff_internal.cuh"
 
 namespace gsff {
@@ -547,6 +549,369 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint with the per-tile pixel sums on tensor cores (decoupled features,
+// N <= 16; the coupled and wider forms use k_render_bwd above).
+//
+// Every per-Gaussian output of a tile is a sum over the tile's pixels of a
+// per-pair weight times a per-pixel row:
+//   colour, depth, features:  sum_p w_p g_p[c]       (w = alpha T, g = cotangent)
+//   u, v, conic, opacity:     sums of dp_p times 1, x, y, x^2, xy, y^2
+//                             (dp = dL/dalpha alpha, x and y the pixel centre
+//                             relative to the warp block's centre), from which
+//                             sum dx dp, sum dx^2 dp, ... follow with dx = u - x
+//                             and the opacity term is sum dp / o.
+// The walk therefore only writes w and dp for each (Gaussian, pixel) into
+// shared memory; after every 16 Gaussians it walked (and at the end of each
+// batch) a warp contracts its 16 x 64 tiles (Gaussians x its pixels) with
+// mma.sync:
+//   W . G  with W and G split into bf16 hi + lo (hi.hi + hi.lo + lo.hi), ~2^-16;
+//   dP . M with dP split into tf32 hi + lo and the monomials M exact in tf32.
+// That replaces, per Gaussian and warp, 20 multiply-adds per pixel and a
+// 32-channel shuffle transposition.
+namespace mma_bwd {
+constexpr int kBB = 32;           // Gaussians per shared-memory batch
+constexpr int kRows = 16;         // Gaussians per warp contraction (MMA M)
+constexpr int kWStride = 72;      // bf16 per W row: 64 pixels + 8 (rows 144 B apart: conflict-free ldmatrix)
+constexpr int kPStride = 68;      // floats per dP row: 64 pixels + 4 (272 B)
+constexpr int kNW = 4;            // warps (8 x 8 pixel blocks) per tile
+constexpr int kThreads = 32 * kNW;
+constexpr int kMom = 6;           // moments of dp: 1, x, y, xx, xy, yy
+}  // namespace mma_bwd
+
+template <int NC>
+struct MmaBwdShape {
+  static constexpr int NCH = NC + 4;          // contracted channels: features, r, g, b, depth
+  static constexpr int NT = (NCH + 7) / 8;    // n-tiles of 8 channels
+  static constexpr int SR = mma_bwd::kMom + NCH;  // per-Gaussian sums kept per warp
+  static constexpr size_t kWBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kWStride * 2;
+  static constexpr size_t kPBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kPStride * 4;
+  static constexpr size_t kRedBytes = (size_t)mma_bwd::kNW * mma_bwd::kBB * SR * 4;
+  static constexpr size_t kSmem = 2 * kWBytes + kPBytes + kRedBytes;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_m16n8k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_tf32_m16n8k8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// (x0, x1) -> bf16x2 hi and lo parts (x0 in the low half): x = hi + lo + O(2^-16 x).
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Cotangent row entry c of pixel (px, py): features 0..NC-1, then r, g, b, depth.
+template <int NC>
+__device__ __forceinline__ float cot_entry(const BwdParams& p, int c, int px, int py) {
+  if (px >= p.cam.W || py >= p.cam.H) return 0.f;
+  const size_t HW = (size_t)p.cam.W * p.cam.H;
+  const size_t pix = (size_t)py * p.cam.W + px;
+  if (c < NC) {
+    if (!p.g_feat || c >= p.N) return 0.f;
+    return p.hwc ? p.g_feat[pix * p.N + c] : p.g_feat[(size_t)c * HW + pix];
+  }
+  c -= NC;
+  if (c < 3) return p.g_rgb ? p.g_rgb[(size_t)c * HW + pix] : 0.f;
+  if (c == 3) return p.g_depth ? p.g_depth[pix] : 0.f;
+  return 0.f;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const BwdParams p) {
+  using namespace mma_bwd;
+  using S = MmaBwdShape<NC>;
+  constexpr int NT = S::NT, SR = S::SR, NCH = S::NCH;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __nv_bfloat16* s_wh = reinterpret_cast<__nv_bfloat16*>(smem_raw);                   // [kNW][kRows][kWStride]
+  __nv_bfloat16* s_wl = reinterpret_cast<__nv_bfloat16*>(smem_raw + S::kWBytes);      // same
+  float* s_p = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes);                     // [kNW][kRows][kPStride]
+  float* s_red = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes + S::kPBytes);     // [kNW][kBB][SR]
+  __shared__ float2 s_mono[8][32];  // B fragments of the monomials: [8-pixel step][lane]
+  __shared__ float2 s_uv[kBB];
+  __shared__ float4 s_co[kBB];
+  __shared__ float4 s_cd[kBB];
+  __shared__ uint32_t s_gid[kBB];
+  __shared__ uint8_t s_wmask[kBB];
+  __shared__ int s_maxlast;
+
+  const int tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int g8 = lane >> 2, t4 = lane & 3;  // MMA fragment row group and column pair
+  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
+  int px[2], py[2];
+  thread_pixels<2>(tx, ty, px, py);
+  const int2 rg = p.ranges[tile];
+  const size_t HW = (size_t)p.cam.W * p.cam.H;
+
+  if (threadIdx.x == 0) s_maxlast = 0;
+  // monomial g of pixel k (k = 8 s + t and 8 s + t + 4 for lane (g, t)), pixel k of a
+  // warp being pixel (k & 1) of lane k >> 1: x = (lane_k & 7) - 3.5, y = (lane_k >> 3) + 4 (k & 1) - 3.5
+  for (int e = threadIdx.x; e < 8 * 32; e += kThreads) {
+    const int s = e >> 5, l = e & 31, g = l >> 2, t = l & 3;
+    float m[2];
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const int k = 8 * s + t + 4 * hf, lk = k >> 1;
+      const float x = (float)(lk & 7) - 3.5f, y = (float)((lk >> 3) + 4 * (k & 1)) - 3.5f;
+      m[hf] = g == 0 ? 1.f : g == 1 ? x : g == 2 ? y : g == 3 ? x * x : g == 4 ? x * y : g == 5 ? y * y : 0.f;
+    }
+    s_mono[s][l] = make_float2(m[0], m[1]);
+  }
+  __syncthreads();
+  float T[2], pxc[2], pyc[2], gC0[2], gC1[2], gC2[2], gD[2], gAb[2];
+  float Bc0[2], Bc1[2], Bc2[2], Bd[2], Sx[2];
+  int last[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const bool inside = px[q] < p.cam.W && py[q] < p.cam.H;
+    const size_t pix = inside ? (size_t)py[q] * p.cam.W + px[q] : 0;
+    pxc[q] = (float)px[q] + 0.5f;
+    pyc[q] = (float)py[q] + 0.5f;
+    T[q] = 1.f;
+    last[q] = 0;
+    gC0[q] = gC1[q] = gC2[q] = gD[q] = 0.f;
+    float gA = 0.f;
+    Bc0[q] = Bc1[q] = Bc2[q] = Bd[q] = 0.f;
+    Sx[q] = 1.f;
+    if (inside) {
+      T[q] = p.T_final[pix];
+      last[q] = p.last_idx[pix];
+      if (p.g_rgb) {
+        gC0[q] = p.g_rgb[pix];
+        gC1[q] = p.g_rgb[HW + pix];
+        gC2[q] = p.g_rgb[2 * HW + pix];
+      }
+      if (p.g_depth) gD[q] = p.g_depth[pix];
+      if (p.g_alpha) gA = p.g_alpha[pix];
+      if (last[q] > 0) atomicMax(&s_maxlast, last[q]);
+    }
+    gAb[q] = gA - (p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q]);
+  }
+  // B fragments of the cotangent matrix (k = this warp's 64 pixels, n = channels),
+  // split into bf16 hi / lo, held for the whole tile
+  uint32_t bh[NT][4][2], bl[NT][4][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int lk = 8 * s + t4 + 4 * hf;
+        const int qx = tx * kTile + (wid & 1) * 8 + (lk & 7);
+        const int qy = ty * kTile + (wid >> 1) * 8 + (lk >> 3);
+        const float v0 = cot_entry<NC>(p, 8 * nt + g8, qx, qy);
+        const float v1 = cot_entry<NC>(p, 8 * nt + g8, qx, qy + 4);
+        split_bf16x2(v0, v1, bh[nt][s][hf], bl[nt][s][hf]);
+      }
+  __syncthreads();
+  const int maxlast = s_maxlast;
+
+  __nv_bfloat16* wh_w = s_wh + wid * kRows * kWStride;
+  __nv_bfloat16* wl_w = s_wl + wid * kRows * kWStride;
+  float* p_w = s_p + wid * kRows * kPStride;
+  // ldmatrix row addresses: lane i supplies row (i & 7) + 8 ((i >> 3) & 1) of
+  // the 16-row tile, at column block (i >> 4)
+  const int lrow = (lane & 7) + 8 * ((lane >> 3) & 1), lcol = lane >> 4;
+  const uint32_t a_wh = smem_u32(wh_w + lrow * kWStride + 8 * lcol);
+  const uint32_t a_wl = smem_u32(wl_w + lrow * kWStride + 8 * lcol);
+  const uint32_t a_p = smem_u32(p_w + lrow * kPStride + 4 * lcol);
+
+  // Rows of the warp's tiles are filled in walk order; lane r remembers the
+  // batch index of the Gaussian in row r. A flush contracts the filled rows
+  // (rows past `rows` hold stale values; their sums are not stored).
+  int rows = 0, row_j = 0;
+  auto flush = [&]() {
+    __syncwarp();
+    float dW[NT][4], dP[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) dW[nt][0] = dW[nt][1] = dW[nt][2] = dW[nt][3] = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      uint32_t ah[4], al[4];
+      ldsm_x4(ah, a_wh + 32 * s);
+      ldsm_x4(al, a_wl + 32 * s);
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        mma_bf16_m16n8k16(dW[nt], al, bh[nt][s][0], bh[nt][s][1]);
+        mma_bf16_m16n8k16(dW[nt], ah, bl[nt][s][0], bl[nt][s][1]);
+        mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      uint32_t a[4], ahi[4], alo[4];
+      ldsm_x4(a, a_p + 32 * s);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        // tf32 hi = the top 19 bits; lo = the exact remainder, truncated likewise
+        ahi[e] = a[e] & 0xffffe000u;
+        alo[e] = __float_as_uint(__uint_as_float(a[e]) - __uint_as_float(ahi[e])) & 0xffffe000u;
+      }
+      const float2 m = s_mono[s][lane];
+      mma_tf32_m16n8k8(dP, alo, __float_as_uint(m.x), __float_as_uint(m.y));
+      mma_tf32_m16n8k8(dP, ahi, __float_as_uint(m.x), __float_as_uint(m.y));
+    }
+    // rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1 of each product
+    const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
+    if (g8 < rows) {
+      float* r0 = s_red + ((size_t)wid * kBB + j0) * SR;
+      if (2 * t4 < kMom) *reinterpret_cast<float2*>(r0 + 2 * t4) = make_float2(dP[0], dP[1]);
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+        if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r0 + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][0], dW[nt][1]);
+    }
+    if (g8 + 8 < rows) {
+      float* r1 = s_red + ((size_t)wid * kBB + j1) * SR;
+      if (2 * t4 < kMom) *reinterpret_cast<float2*>(r1 + 2 * t4) = make_float2(dP[2], dP[3]);
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+        if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r1 + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][2], dW[nt][3]);
+    }
+    __syncwarp();
+    rows = 0;
+  };
+
+  for (int hi = rg.x + maxlast; hi > rg.x; hi -= kBB) {
+    const int lo = max(rg.x, hi - kBB);
+    const int n = hi - lo;
+    if ((int)threadIdx.x < n) {
+      const uint32_t g = p.gids[lo + threadIdx.x];
+      const float4 co = p.co[g];
+      const float2 u = p.uv[g];
+      s_gid[threadIdx.x] = g;
+      s_uv[threadIdx.x] = u;
+      s_co[threadIdx.x] = co;
+      s_wmask[threadIdx.x] = (uint8_t)warp_block_mask<kNW, 8, true>(u, co, tx, ty);
+      s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
+    }
+    __syncthreads();
+    // walk: this warp's Gaussians of the batch in reverse list order
+    uint32_t bits = __ballot_sync(0xffffffffu, lane < n && ((s_wmask[lane] >> wid) & 1u));
+    while (bits) {
+      const int j = 31 - __clz(bits);
+      bits &= ~(1u << j);
+      const int pos = lo + j - rg.x;
+      const float2 uj = s_uv[j];
+      const float4 cj = s_co[j];
+      const float4 cd = s_cd[j];
+      float wq[2] = {0.f, 0.f}, dpq[2] = {0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        PairAlpha pa;
+        const float dx = uj.x - pxc[q], dy = uj.y - pyc[q];
+        if (!(pos < last[q] && pair_alpha(cj, dx, dy, pa))) continue;
+        const float om = 1.f - pa.alpha;
+        T[q] = __fdividef(T[q], om);
+        wq[q] = pa.alpha * T[q];
+        const float da = T[q] * ((cd.x - Bc0[q]) * gC0[q] + (cd.y - Bc1[q]) * gC1[q] + (cd.z - Bc2[q]) * gC2[q] +
+                                 (cd.w - Bd[q]) * gD[q]) +
+                         T[q] * Sx[q] * gAb[q];
+        Bc0[q] = pa.alpha * cd.x + om * Bc0[q];
+        Bc1[q] = pa.alpha * cd.y + om * Bc1[q];
+        Bc2[q] = pa.alpha * cd.z + om * Bc2[q];
+        Bd[q] = pa.alpha * cd.w + om * Bd[q];
+        Sx[q] *= om;
+        if (!pa.clamped) dpq[q] = da * pa.alpha;
+      }
+      uint32_t whi, wlo;
+      split_bf16x2(wq[0], wq[1], whi, wlo);
+      reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
+      reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = wlo;
+      reinterpret_cast<float2*>(p_w + rows * kPStride)[lane] = make_float2(dpq[0], dpq[1]);
+      if (lane == rows) row_j = j;
+      if (++rows == kRows) flush();
+    }
+    if (rows > 0) flush();
+    __syncthreads();
+    if (wid < kNW - 1) {
+      // colour, depth and feature sums: the warps that walked Gaussian j, one atomic each
+      for (int e = threadIdx.x; e < n * NCH; e += kThreads - 32) {
+        const int j = e / NCH, c = e - j * NCH;
+        const uint32_t wm = s_wmask[j];
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kNW; ++w)
+          if ((wm >> w) & 1u) sum += s_red[((size_t)w * kBB + j) * SR + kMom + c];
+        if (sum == 0.f) continue;
+        const uint32_t g = s_gid[j];
+        float* dst;
+        if (c < NC) {
+          if (c >= p.N || !p.d_feats) continue;
+          dst = p.d_feats + (size_t)g * p.N + c;
+        } else if (c < NC + 3) {
+          if (!p.d_colors) continue;
+          dst = p.d_colors + 3 * (size_t)g + (c - NC);
+        } else {
+          dst = p.d_depth + g;
+        }
+        atomicAdd(dst, sum);
+      }
+    } else if (lane < n) {
+      // u, v, conic and opacity of Gaussian `lane` from the warps' moments:
+      // with (uu, vv) = u - block centre and dx = uu - x,
+      //   sum dx dp = uu M0 - Mx,  sum dx^2 dp = uu^2 M0 - 2 uu Mx + Mxx, ...
+      const int j = lane;
+      const uint32_t wm = s_wmask[j];
+      const float2 u = s_uv[j];
+      const float4 co = s_co[j];
+      float ox = 0.f, oy = 0.f, oxx = 0.f, oxy = 0.f, oyy = 0.f, m0 = 0.f;
+#pragma unroll
+      for (int w = 0; w < kNW; ++w) {
+        if (!((wm >> w) & 1u)) continue;
+        const float* M = s_red + ((size_t)w * kBB + j) * SR;
+        const float2 a = *reinterpret_cast<const float2*>(M);
+        const float2 b = *reinterpret_cast<const float2*>(M + 2);
+        const float2 c = *reinterpret_cast<const float2*>(M + 4);  // (M0, Mx), (My, Mxx), (Mxy, Myy)
+        const float uu = u.x - (float)(tx * kTile + (w & 1) * 8 + 4);
+        const float vv = u.y - (float)(ty * kTile + (w >> 1) * 8 + 4);
+        ox += uu * a.x - a.y;
+        oy += vv * a.x - b.x;
+        oxx += uu * (uu * a.x - 2.f * a.y) + b.y;
+        oxy += uu * (vv * a.x - b.x) - vv * a.y + c.x;
+        oyy += vv * (vv * a.x - 2.f * b.x) + c.y;
+        m0 += a.x;
+      }
+      const uint32_t g = s_gid[j];
+      const float out[6] = {-(co.x * ox + co.y * oy), -(co.y * ox + co.z * oy), -0.5f * oxx, -oxy, -0.5f * oyy,
+                            m0 / co.w};
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (out[k] != 0.f) atomicAdd(p.d_uv + 2 * (size_t)g + k, out[k]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (out[2 + k] != 0.f) atomicAdd(p.d_conic + 3 * (size_t)g + k, out[2 + k]);
+      if (p.d_opacity && out[5] != 0.f) atomicAdd(p.d_opacity + g, out[5]);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
@@ -590,6 +955,25 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
   return last_launch_status();
 }
 
+// The tensor-core adjoint takes its tiles (48 KB) in dynamic shared memory; the
+// limit is raised once per device.
+template <int NC>
+gs_status launch_bwd_mma(const BwdParams& p, unsigned tiles, cudaStream_t st) {
+  constexpr size_t smem = MmaBwdShape<NC>::kSmem;
+  static std::atomic<uint64_t> attr_done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_done.load() & bit)) {
+    if (cudaFuncSetAttribute(k_render_bwd_mma<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return GS_ERR_CUDA;
+    attr_done.fetch_or(bit);
+  }
+  k_render_bwd_mma<NC><<<tiles, mma_bwd::kThreads, smem, st>>>(p);
+  return last_launch_status();
+}
+
 gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
@@ -622,12 +1006,14 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32
   p.d_colors = d_colors;
   p.d_feats = d_feats;
   const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
+  if (N <= 16 && !coupled) {
+    GS_TRACE("k_render_bwd_mma", st);
+    if (N <= 0) return launch_bwd_mma<0>(p, tiles, st);
+    return launch_bwd_mma<16>(p, tiles, st);
+  }
   GS_TRACE("k_render_bwd", st);
-  if (N <= 0) {
-    k_render_bwd<0, false, 2><<<dim3(tiles, 1), kTilePix / 2, 0, st>>>(p);
-  } else if (N <= 16) {
-    if (coupled) k_render_bwd<16, true, 1><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
-    else k_render_bwd<16, false, 2><<<dim3(tiles, 1), kTilePix / 2, 0, st>>>(p);
+  if (N <= 16) {
+    k_render_bwd<16, true, 1><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
   } else {
     const dim3 grid(tiles, (N + 31) / 32);
     if (coupled) k_render_bwd<32, true, 1><<<grid, kTilePix, 0, st>>>(p);

@@ -19,6 +19,12 @@ GOLD = 0x9E3779B97F4A7C15
 M64 = (1 << 64) - 1
 
 
+def _normal_(t, sd, seed):
+    """Fill t with N(0, sd^2) draws of a seeded numpy generator (independent of
+    the torch generators' state, hence of which tests ran before)."""
+    t.copy_(torch.from_numpy(np.random.default_rng(seed).normal(0.0, sd, size=tuple(t.shape)).astype(np.float32)))
+
+
 def _splitmix(z):
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9 & M64
     z = (z ^ (z >> 27)) * 0x94D049BB133111EB & M64
@@ -45,8 +51,8 @@ def _np(t):
 
 def test_decoder_forward_matches_oracle(dec_mod, ora):
     dec = dec_mod.Decoder(seed=3)
-    dec.params["b1"].normal_(0, 0.1)
-    dec.params["b2"].normal_(0, 0.1)
+    _normal_(dec.params["b1"], 0.1, 101)
+    _normal_(dec.params["b2"], 0.1, 102)
     rng = np.random.default_rng(4)
     z = torch.tensor(rng.normal(size=(3000, 16)).astype(np.float32), device="cuda")
     y = dec.forward(z)
@@ -60,7 +66,7 @@ def test_decoder_forward_matches_oracle(dec_mod, ora):
 
 def test_decoder_training_gradients_match_oracle(dec_mod, ora):
     dec = dec_mod.Decoder(seed=5)
-    dec.params["b1"].normal_(0, 0.1)
+    _normal_(dec.params["b1"], 0.1, 103)
     rng = np.random.default_rng(6)
     npix, S, seed = 2500, 2000, 77
     z = torch.tensor(rng.normal(size=(npix, 16)).astype(np.float32), device="cuda")
@@ -168,8 +174,8 @@ def test_decoder_tensor_core_forward_within_bound(dec_mod, ora):
     output (2^-8 = twice bf16's unit roundoff)."""
     from math import erf, sqrt
     dec = dec_mod.Decoder(seed=13)
-    dec.params["b1"].normal_(0, 0.2)
-    dec.params["b2"].normal_(0, 0.2)
+    _normal_(dec.params["b1"], 0.2, 104)
+    _normal_(dec.params["b2"], 0.2, 105)
     rng = np.random.default_rng(14)
     n = 1000 + 37  # a ragged last tile
     z = torch.tensor(rng.normal(size=(n, 16)).astype(np.float32), device="cuda")
@@ -200,8 +206,8 @@ def test_decoder_labels_from_latents_within_bound(dec_mod, ora):
     largest bound."""
     from math import erf, sqrt
     dec = dec_mod.Decoder(seed=17)
-    dec.params["b1"].normal_(0, 0.2)
-    dec.params["b2"].normal_(0, 0.2)
+    _normal_(dec.params["b1"], 0.2, 106)
+    _normal_(dec.params["b2"], 0.2, 107)
     rng = np.random.default_rng(18)
     n, L = 1000 + 37, 24
     z = torch.tensor(rng.normal(size=(n, 16)).astype(np.float32), device="cuda")
