@@ -577,17 +577,27 @@ constexpr int kPStride = 68;      // floats per dP row: 64 pixels + 4 (272 B)
 constexpr int kNW = 4;            // warps (8 x 8 pixel blocks) per tile
 constexpr int kThreads = 32 * kNW;
 constexpr int kMom = 6;           // moments of dp: 1, x, y, xx, xy, yy
+constexpr int kNBuf = 3;          // batch buffers: walked, being staged, still named by the last batch's sums
 }  // namespace mma_bwd
+
+// One batch of a tile's list in shared memory.
+struct BwdBatch {
+  float4 co[mma_bwd::kBB];  // conic A, B, C and opacity
+  float4 cd[mma_bwd::kBB];  // colour r, g, b and depth
+  float2 uv[mma_bwd::kBB];
+  uint32_t gid[mma_bwd::kBB];
+  uint8_t wmask[mma_bwd::kBB];  // bit w: warp w's pixel block passes the skip test
+};
 
 template <int NC>
 struct MmaBwdShape {
   static constexpr int NCH = NC + 4;          // contracted channels: features, r, g, b, depth
   static constexpr int NT = (NCH + 7) / 8;    // n-tiles of 8 channels
-  static constexpr int SR = mma_bwd::kMom + NCH;  // per-Gaussian sums kept per warp
+  static constexpr int SR = mma_bwd::kMom + NCH;  // per-Gaussian sums: u, v, A, B, C, opacity, then NCH
   static constexpr size_t kWBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kWStride * 2;
   static constexpr size_t kPBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kPStride * 4;
-  static constexpr size_t kRedBytes = (size_t)mma_bwd::kNW * mma_bwd::kBB * SR * 4;
-  static constexpr size_t kSmem = 2 * kWBytes + kPBytes + kRedBytes;
+  static constexpr size_t kAccBytes = (size_t)2 * mma_bwd::kBB * SR * 4;
+  static constexpr size_t kSmem = 2 * kWBytes + kPBytes + kAccBytes;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -626,20 +636,32 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, u
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Cotangent row entry c of pixel (px, py): features 0..NC-1, then r, g, b, depth.
-template <int NC>
-__device__ __forceinline__ float cot_entry(const BwdParams& p, int c, int px, int py) {
-  if (px >= p.cam.W || py >= p.cam.H) return 0.f;
-  const size_t HW = (size_t)p.cam.W * p.cam.H;
-  const size_t pix = (size_t)py * p.cam.W + px;
-  if (c < NC) {
-    if (!p.g_feat || c >= p.N) return 0.f;
-    return p.hwc ? p.g_feat[pix * p.N + c] : p.g_feat[(size_t)c * HW + pix];
-  }
-  c -= NC;
-  if (c < 3) return p.g_rgb ? p.g_rgb[(size_t)c * HW + pix] : 0.f;
-  if (c == 3) return p.g_depth ? p.g_depth[pix] : 0.f;
-  return 0.f;
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Starts the copies of Gaussian g's record into slot i of a batch.
+__device__ __forceinline__ void stage_batch(const BwdParams& p, BwdBatch& b, int i, uint32_t g) {
+  b.gid[i] = g;
+  cp_async16(&b.co[i], p.co + g);
+  cp_async8(&b.uv[i], p.uv + g);
+  float* cd = reinterpret_cast<float*>(&b.cd[i]);
+  cp_async4(cd + 0, p.colors + 3 * (size_t)g);
+  cp_async4(cd + 1, p.colors + 3 * (size_t)g + 1);
+  cp_async4(cd + 2, p.colors + 3 * (size_t)g + 2);
+  cp_async4(cd + 3, p.depth + g);
+}
+
+// After the slot's copies landed: the warp skip tests of its Gaussian.
+__device__ __forceinline__ void finish_batch(BwdBatch& b, int i, int tx, int ty) {
+  b.wmask[i] = (uint8_t)warp_block_mask<mma_bwd::kNW, 8, true>(b.uv[i], b.co[i], tx, ty);
 }
 
 template <int NC>
@@ -651,13 +673,9 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   __nv_bfloat16* s_wh = reinterpret_cast<__nv_bfloat16*>(smem_raw);                   // [kNW][kRows][kWStride]
   __nv_bfloat16* s_wl = reinterpret_cast<__nv_bfloat16*>(smem_raw + S::kWBytes);      // same
   float* s_p = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes);                     // [kNW][kRows][kPStride]
-  float* s_red = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes + S::kPBytes);     // [kNW][kBB][SR]
+  float* s_acc = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes + S::kPBytes);     // [2][kBB][SR]
   __shared__ float2 s_mono[8][32];  // B fragments of the monomials: [8-pixel step][lane]
-  __shared__ float2 s_uv[kBB];
-  __shared__ float4 s_co[kBB];
-  __shared__ float4 s_cd[kBB];
-  __shared__ uint32_t s_gid[kBB];
-  __shared__ uint8_t s_wmask[kBB];
+  __shared__ BwdBatch s_b[kNBuf];
   __shared__ int s_maxlast;
 
   const int tile = blockIdx.x;
@@ -683,6 +701,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     }
     s_mono[s][l] = make_float2(m[0], m[1]);
   }
+  for (int e = threadIdx.x; e < 2 * kBB * SR; e += kThreads) s_acc[e] = 0.f;
   __syncthreads();
   float T[2], pxc[2], pyc[2], gC0[2], gC1[2], gC2[2], gD[2], gAb[2];
   float Bc0[2], Bc1[2], Bc2[2], Bd[2], Sx[2];
@@ -714,23 +733,60 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     gAb[q] = gA - (p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q]);
   }
   // B fragments of the cotangent matrix (k = this warp's 64 pixels, n = channels),
-  // split into bf16 hi / lo, held for the whole tile
+  // split into bf16 hi / lo, held for the whole tile. Row k = 16 s + 2 t + 8 hf + q
+  // of step s is the pixel at column t + 4 hf, row s + 4 q of the warp block.
   uint32_t bh[NT][4][2], bl[NT][4][2];
+  {
+    const int bx = tx * kTile + (wid & 1) * 8, by = ty * kTile + (wid >> 1) * 8;
 #pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        const int lk = 8 * s + t4 + 4 * hf;
-        const int qx = tx * kTile + (wid & 1) * 8 + (lk & 7);
-        const int qy = ty * kTile + (wid >> 1) * 8 + (lk >> 3);
-        const float v0 = cot_entry<NC>(p, 8 * nt + g8, qx, qy);
-        const float v1 = cot_entry<NC>(p, 8 * nt + g8, qx, qy + 4);
-        split_bf16x2(v0, v1, bh[nt][s][hf], bl[nt][s][hf]);
+    for (int nt = 0; nt < NT; ++nt) {
+      const int c = 8 * nt + g8;
+      const float* plane = nullptr;  // channel c of the cotangent, indexed by pixel * pstride
+      size_t pstride = 1;
+      if (c < NC) {
+        if (p.g_feat && c < p.N) {
+          plane = p.hwc ? p.g_feat + c : p.g_feat + (size_t)c * HW;
+          pstride = p.hwc ? (size_t)p.N : 1;
+        }
+      } else if (c < NC + 3) {
+        if (p.g_rgb) plane = p.g_rgb + (size_t)(c - NC) * HW;
+      } else if (c == NC + 3) {
+        plane = p.g_depth;
       }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int qx = bx + t4 + 4 * hf;
+          float v[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int qy = by + s + 4 * q;
+            v[q] = (plane && qx < p.cam.W && qy < p.cam.H) ? plane[((size_t)qy * p.cam.W + qx) * pstride] : 0.f;
+          }
+          split_bf16x2(v[0], v[1], bh[nt][s][hf], bl[nt][s][hf]);
+        }
+    }
+  }
   __syncthreads();
   const int maxlast = s_maxlast;
+  // batches of the list, back to front: batch b holds positions [lo_b, hi_b)
+  const int nb = (maxlast + kBB - 1) / kBB;
+  auto batch_hi = [&](int b) { return rg.x + maxlast - b * kBB; };
+  auto batch_lo = [&](int b) { return max(rg.x, batch_hi(b) - kBB); };
+  // Batches are staged by warp 0 one batch ahead with cp.async (ids read two
+  // batches ahead), so each batch costs the block a single barrier.
+  uint32_t g_next = 0;
+  if (wid == 0 && nb > 0) {
+    const int lo0 = batch_lo(0);
+    if (lane < batch_hi(0) - lo0) {
+      stage_batch(p, s_b[0], lane, p.gids[lo0 + lane]);
+      cp_async_wait_all();
+      finish_batch(s_b[0], lane, tx, ty);
+    }
+    if (nb > 1 && lane < batch_hi(1) - batch_lo(1)) g_next = p.gids[batch_lo(1) + lane];
+  }
+  __syncthreads();
 
   __nv_bfloat16* wh_w = s_wh + wid * kRows * kWStride;
   __nv_bfloat16* wl_w = s_wl + wid * kRows * kWStride;
@@ -741,174 +797,197 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   const uint32_t a_wh = smem_u32(wh_w + lrow * kWStride + 8 * lcol);
   const uint32_t a_wl = smem_u32(wl_w + lrow * kWStride + 8 * lcol);
   const uint32_t a_p = smem_u32(p_w + lrow * kPStride + 4 * lcol);
+  const float cxw = (float)(tx * kTile + (wid & 1) * 8 + 4), cyw = (float)(ty * kTile + (wid >> 1) * 8 + 4);
 
-  // Rows of the warp's tiles are filled in walk order; lane r remembers the
-  // batch index of the Gaussian in row r. A flush contracts the filled rows
-  // (rows past `rows` hold stale values; their sums are not stored).
-  int rows = 0, row_j = 0;
-  auto flush = [&]() {
-    __syncwarp();
-    float dW[NT][4], dP[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) dW[nt][0] = dW[nt][1] = dW[nt][2] = dW[nt][3] = 0.f;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      uint32_t ah[4], al[4];
-      ldsm_x4(ah, a_wh + 32 * s);
-      ldsm_x4(al, a_wl + 32 * s);
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        mma_bf16_m16n8k16(dW[nt], al, bh[nt][s][0], bh[nt][s][1]);
-        mma_bf16_m16n8k16(dW[nt], ah, bl[nt][s][0], bl[nt][s][1]);
-        mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      uint32_t a[4], ahi[4], alo[4];
-      ldsm_x4(a, a_p + 32 * s);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        // tf32 hi = the top 19 bits; lo = the exact remainder, truncated likewise
-        ahi[e] = a[e] & 0xffffe000u;
-        alo[e] = __float_as_uint(__uint_as_float(a[e]) - __uint_as_float(ahi[e])) & 0xffffe000u;
-      }
-      const float2 m = s_mono[s][lane];
-      mma_tf32_m16n8k8(dP, alo, __float_as_uint(m.x), __float_as_uint(m.y));
-      mma_tf32_m16n8k8(dP, ahi, __float_as_uint(m.x), __float_as_uint(m.y));
-    }
-    // rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1 of each product
-    const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
-    if (g8 < rows) {
-      float* r0 = s_red + ((size_t)wid * kBB + j0) * SR;
-      if (2 * t4 < kMom) *reinterpret_cast<float2*>(r0 + 2 * t4) = make_float2(dP[0], dP[1]);
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt)
-        if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r0 + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][0], dW[nt][1]);
-    }
-    if (g8 + 8 < rows) {
-      float* r1 = s_red + ((size_t)wid * kBB + j1) * SR;
-      if (2 * t4 < kMom) *reinterpret_cast<float2*>(r1 + 2 * t4) = make_float2(dP[2], dP[3]);
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt)
-        if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r1 + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][2], dW[nt][3]);
-    }
-    __syncwarp();
-    rows = 0;
-  };
+  for (int b = 0; b < nb; ++b) {
+    const BwdBatch& B = s_b[b % kNBuf];
+    float* acc = s_acc + (b & 1) * kBB * SR;
+    const int lo = batch_lo(b), n = batch_hi(b) - lo;
+    const bool stage = wid == 0 && b + 1 < nb && lane < batch_hi(b + 1) - batch_lo(b + 1);
+    if (stage) stage_batch(p, s_b[(b + 1) % kNBuf], lane, g_next);
+    if (wid == 0 && b + 2 < nb && lane < batch_hi(b + 2) - batch_lo(b + 2)) g_next = p.gids[batch_lo(b + 2) + lane];
 
-  for (int hi = rg.x + maxlast; hi > rg.x; hi -= kBB) {
-    const int lo = max(rg.x, hi - kBB);
-    const int n = hi - lo;
-    if ((int)threadIdx.x < n) {
-      const uint32_t g = p.gids[lo + threadIdx.x];
-      const float4 co = p.co[g];
-      const float2 u = p.uv[g];
-      s_gid[threadIdx.x] = g;
-      s_uv[threadIdx.x] = u;
-      s_co[threadIdx.x] = co;
-      s_wmask[threadIdx.x] = (uint8_t)warp_block_mask<kNW, 8, true>(u, co, tx, ty);
-      s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
-    }
-    __syncthreads();
-    // walk: this warp's Gaussians of the batch in reverse list order
-    uint32_t bits = __ballot_sync(0xffffffffu, lane < n && ((s_wmask[lane] >> wid) & 1u));
+    // Rows of the warp's tiles are filled in walk order; lane r remembers the
+    // batch index of the Gaussian in row r. A flush contracts the filled rows
+    // (rows past `rows` hold stale values; their sums are not used) and adds
+    // them into the block's sums.
+    int rows = 0, row_j = 0;
+    auto flush = [&]() {
+      __syncwarp();
+      float dW[NT][4], dP[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) dW[nt][0] = dW[nt][1] = dW[nt][2] = dW[nt][3] = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        uint32_t ah[4], al[4];
+        ldsm_x4(ah, a_wh + 32 * s);
+        ldsm_x4(al, a_wl + 32 * s);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma_bf16_m16n8k16(dW[nt], al, bh[nt][s][0], bh[nt][s][1]);
+          mma_bf16_m16n8k16(dW[nt], ah, bl[nt][s][0], bl[nt][s][1]);
+          mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        uint32_t a[4], ahi[4], alo[4];
+        ldsm_x4(a, a_p + 32 * s);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          // tf32 hi = the top 19 bits; lo = the exact remainder, truncated likewise
+          ahi[e] = a[e] & 0xffffe000u;
+          alo[e] = __float_as_uint(__uint_as_float(a[e]) - __uint_as_float(ahi[e])) & 0xffffe000u;
+        }
+        const float2 m = s_mono[s][lane];
+        mma_tf32_m16n8k8(dP, alo, __float_as_uint(m.x), __float_as_uint(m.y));
+        mma_tf32_m16n8k8(dP, ahi, __float_as_uint(m.x), __float_as_uint(m.y));
+      }
+      __syncwarp();
+      // D rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1
+      const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
+      if (g8 < rows) {
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int c = 8 * nt + 2 * t4;
+          if (c < NCH) {
+            atomicAdd(acc + j0 * SR + kMom + c, dW[nt][0]);
+            atomicAdd(acc + j0 * SR + kMom + c + 1, dW[nt][1]);
+          }
+        }
+      }
+      if (g8 + 8 < rows) {
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int c = 8 * nt + 2 * t4;
+          if (c < NCH) {
+            atomicAdd(acc + j1 * SR + kMom + c, dW[nt][2]);
+            atomicAdd(acc + j1 * SR + kMom + c + 1, dW[nt][3]);
+          }
+        }
+      }
+      // moments: lanes t4 = 0, 1, 2 of a quad hold columns (M0, Mx), (My, Mxx),
+      // (Mxy, Myy); lane t4 = 0 converts row g8, lane t4 = 1 row g8 + 8 into
+      // u, v, conic and opacity with (uu, vv) = u - block centre, dx = uu - x:
+      //   sum dx dp = uu M0 - Mx,  sum dx^2 dp = uu^2 M0 - 2 uu Mx + Mxx, ...
+      const int qb = lane & ~3;
+      const bool second = t4 == 1;
+      float m[kMom];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float a0 = __shfl_sync(0xffffffffu, dP[0], qb + k), a1 = __shfl_sync(0xffffffffu, dP[1], qb + k);
+        const float c0 = __shfl_sync(0xffffffffu, dP[2], qb + k), c1 = __shfl_sync(0xffffffffu, dP[3], qb + k);
+        m[2 * k] = second ? c0 : a0;
+        m[2 * k + 1] = second ? c1 : a1;
+      }
+      if (t4 < 2 && g8 + 8 * t4 < rows) {
+        const int j = second ? j1 : j0;
+        const float2 u = B.uv[j];
+        const float4 co = B.co[j];
+        const float uu = u.x - cxw, vv = u.y - cyw;
+        const float ox = uu * m[0] - m[1], oy = vv * m[0] - m[2];
+        float* a = acc + j * SR;
+        atomicAdd(a + 0, -(co.x * ox + co.y * oy));
+        atomicAdd(a + 1, -(co.y * ox + co.z * oy));
+        atomicAdd(a + 2, -0.5f * (uu * (uu * m[0] - 2.f * m[1]) + m[3]));
+        atomicAdd(a + 3, -(uu * (vv * m[0] - m[2]) - vv * m[1] + m[4]));
+        atomicAdd(a + 4, -0.5f * (vv * (vv * m[0] - 2.f * m[2]) + m[5]));
+        atomicAdd(a + 5, m[0] / co.w);
+      }
+      rows = 0;
+    };
+
+    // walk: this warp's Gaussians of the batch in reverse list order, two at a
+    // time. Both pairs' alphas are formed first (four independent chains); a
+    // pair that does not blend takes alpha = 0, for which every update below
+    // is an exact identity (T / 1, 0 c + 1 B, S 1) and w = dp = 0.
+    uint32_t bits = __ballot_sync(0xffffffffu, lane < n && ((B.wmask[lane] >> wid) & 1u));
     while (bits) {
-      const int j = 31 - __clz(bits);
-      bits &= ~(1u << j);
-      const int pos = lo + j - rg.x;
-      const float2 uj = s_uv[j];
-      const float4 cj = s_co[j];
-      const float4 cd = s_cd[j];
-      float wq[2] = {0.f, 0.f}, dpq[2] = {0.f, 0.f};
+      if (rows > kRows - 2) flush();
+      const int j1 = 31 - __clz(bits);
+      bits &= ~(1u << j1);
+      const bool two = bits != 0;
+      const int j2 = two ? 31 - __clz(bits) : j1;
+      bits &= ~(1u << j2);
+      const int jg[2] = {j1, j2};
+      float al[2][2];
+      bool cl[2][2];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        PairAlpha pa;
-        const float dx = uj.x - pxc[q], dy = uj.y - pyc[q];
-        if (!(pos < last[q] && pair_alpha(cj, dx, dy, pa))) continue;
-        const float om = 1.f - pa.alpha;
-        T[q] = __fdividef(T[q], om);
-        wq[q] = pa.alpha * T[q];
-        const float da = T[q] * ((cd.x - Bc0[q]) * gC0[q] + (cd.y - Bc1[q]) * gC1[q] + (cd.z - Bc2[q]) * gC2[q] +
-                                 (cd.w - Bd[q]) * gD[q]) +
-                         T[q] * Sx[q] * gAb[q];
-        Bc0[q] = pa.alpha * cd.x + om * Bc0[q];
-        Bc1[q] = pa.alpha * cd.y + om * Bc1[q];
-        Bc2[q] = pa.alpha * cd.z + om * Bc2[q];
-        Bd[q] = pa.alpha * cd.w + om * Bd[q];
-        Sx[q] *= om;
-        if (!pa.clamped) dpq[q] = da * pa.alpha;
+      for (int k = 0; k < 2; ++k) {
+        const float2 uj = B.uv[jg[k]];
+        const float4 cj = B.co[jg[k]];
+        const int pos = lo + jg[k] - rg.x;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          PairAlpha pa;
+          const bool ok = (k == 0 || two) && pos < last[q] && pair_alpha(cj, uj.x - pxc[q], uj.y - pyc[q], pa);
+          al[k][q] = ok ? pa.alpha : 0.f;
+          cl[k][q] = ok && pa.clamped;
+        }
       }
-      uint32_t whi, wlo;
-      split_bf16x2(wq[0], wq[1], whi, wlo);
-      reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
-      reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = wlo;
-      reinterpret_cast<float2*>(p_w + rows * kPStride)[lane] = make_float2(dpq[0], dpq[1]);
-      if (lane == rows) row_j = j;
-      if (++rows == kRows) flush();
+      float wq[2][2], dpq[2][2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float4 cd = B.cd[jg[k]];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float a = al[k][q], om = 1.f - a;
+          T[q] = __fdividef(T[q], om);
+          wq[k][q] = a * T[q];
+          const float da = T[q] * ((cd.x - Bc0[q]) * gC0[q] + (cd.y - Bc1[q]) * gC1[q] + (cd.z - Bc2[q]) * gC2[q] +
+                                   (cd.w - Bd[q]) * gD[q]) +
+                           T[q] * Sx[q] * gAb[q];
+          Bc0[q] = a * cd.x + om * Bc0[q];
+          Bc1[q] = a * cd.y + om * Bc1[q];
+          Bc2[q] = a * cd.z + om * Bc2[q];
+          Bd[q] = a * cd.w + om * Bd[q];
+          Sx[q] *= om;
+          dpq[k][q] = cl[k][q] ? 0.f : da * a;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !two) break;
+        uint32_t whi, wlo;
+        split_bf16x2(wq[k][0], wq[k][1], whi, wlo);
+        reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
+        reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = wlo;
+        reinterpret_cast<float2*>(p_w + rows * kPStride)[lane] = make_float2(dpq[k][0], dpq[k][1]);
+        if (lane == rows) row_j = jg[k];
+        ++rows;
+      }
     }
     if (rows > 0) flush();
-    __syncthreads();
-    if (wid < kNW - 1) {
-      // colour, depth and feature sums: the warps that walked Gaussian j, one atomic each
-      for (int e = threadIdx.x; e < n * NCH; e += kThreads - 32) {
-        const int j = e / NCH, c = e - j * NCH;
-        const uint32_t wm = s_wmask[j];
-        float sum = 0.f;
-#pragma unroll
-        for (int w = 0; w < kNW; ++w)
-          if ((wm >> w) & 1u) sum += s_red[((size_t)w * kBB + j) * SR + kMom + c];
-        if (sum == 0.f) continue;
-        const uint32_t g = s_gid[j];
-        float* dst;
-        if (c < NC) {
-          if (c >= p.N || !p.d_feats) continue;
-          dst = p.d_feats + (size_t)g * p.N + c;
-        } else if (c < NC + 3) {
-          if (!p.d_colors) continue;
-          dst = p.d_colors + 3 * (size_t)g + (c - NC);
-        } else {
-          dst = p.d_depth + g;
-        }
-        atomicAdd(dst, sum);
-      }
-    } else if (lane < n) {
-      // u, v, conic and opacity of Gaussian `lane` from the warps' moments:
-      // with (uu, vv) = u - block centre and dx = uu - x,
-      //   sum dx dp = uu M0 - Mx,  sum dx^2 dp = uu^2 M0 - 2 uu Mx + Mxx, ...
-      const int j = lane;
-      const uint32_t wm = s_wmask[j];
-      const float2 u = s_uv[j];
-      const float4 co = s_co[j];
-      float ox = 0.f, oy = 0.f, oxx = 0.f, oxy = 0.f, oyy = 0.f, m0 = 0.f;
-#pragma unroll
-      for (int w = 0; w < kNW; ++w) {
-        if (!((wm >> w) & 1u)) continue;
-        const float* M = s_red + ((size_t)w * kBB + j) * SR;
-        const float2 a = *reinterpret_cast<const float2*>(M);
-        const float2 b = *reinterpret_cast<const float2*>(M + 2);
-        const float2 c = *reinterpret_cast<const float2*>(M + 4);  // (M0, Mx), (My, Mxx), (Mxy, Myy)
-        const float uu = u.x - (float)(tx * kTile + (w & 1) * 8 + 4);
-        const float vv = u.y - (float)(ty * kTile + (w >> 1) * 8 + 4);
-        ox += uu * a.x - a.y;
-        oy += vv * a.x - b.x;
-        oxx += uu * (uu * a.x - 2.f * a.y) + b.y;
-        oxy += uu * (vv * a.x - b.x) - vv * a.y + c.x;
-        oyy += vv * (vv * a.x - 2.f * b.x) + c.y;
-        m0 += a.x;
-      }
-      const uint32_t g = s_gid[j];
-      const float out[6] = {-(co.x * ox + co.y * oy), -(co.y * ox + co.z * oy), -0.5f * oxx, -oxy, -0.5f * oyy,
-                            m0 / co.w};
-#pragma unroll
-      for (int k = 0; k < 2; ++k)
-        if (out[k] != 0.f) atomicAdd(p.d_uv + 2 * (size_t)g + k, out[k]);
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (out[2 + k] != 0.f) atomicAdd(p.d_conic + 3 * (size_t)g + k, out[2 + k]);
-      if (p.d_opacity && out[5] != 0.f) atomicAdd(p.d_opacity + g, out[5]);
+    if (stage) {
+      cp_async_wait_all();
+      finish_batch(s_b[(b + 1) % kNBuf], lane, tx, ty);
     }
     __syncthreads();
+    // one global atomic per (Gaussian, output) of the batch; the sums are
+    // cleared for the batch after next
+    for (int e = threadIdx.x; e < n * SR; e += kThreads) {
+      const float v = acc[e];
+      if (v == 0.f) continue;
+      acc[e] = 0.f;
+      const int j = e / SR, c = e - j * SR;
+      const uint32_t g = B.gid[j];
+      float* dst;
+      if (c < 2) dst = p.d_uv + 2 * (size_t)g + c;
+      else if (c < 5) dst = p.d_conic + 3 * (size_t)g + (c - 2);
+      else if (c == 5) {
+        if (!p.d_opacity) continue;
+        dst = p.d_opacity + g;
+      } else if (c < kMom + NC) {
+        if (c - kMom >= p.N || !p.d_feats) continue;
+        dst = p.d_feats + (size_t)g * p.N + (c - kMom);
+      } else if (c < kMom + NC + 3) {
+        if (!p.d_colors) continue;
+        dst = p.d_colors + 3 * (size_t)g + (c - kMom - NC);
+      } else {
+        dst = p.d_depth + g;
+      }
+      atomicAdd(dst, v);
+    }
   }
 }
 
