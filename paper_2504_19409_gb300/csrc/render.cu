@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
 // batch) a warp contracts its 16 x 64 tiles (Gaussians x its pixels) with
 // mma.sync:
 //   W . G  with W and G split into bf16 hi + lo (hi.hi + hi.lo + lo.hi), ~2^-16;
-//   dP . M with dP split into tf32 hi + lo and the monomials M exact in tf32.
+//   dP . M with dP split into tf32 hi + lo (~2^-22) and the monomials M exact in tf32.
 // That replaces, per Gaussian and warp, 20 multiply-adds per pixel and a
 // 32-channel shuffle transposition.
 namespace mma_bwd {
@@ -625,6 +625,17 @@ __device__ __forceinline__ void mma_tf32_m16n8k8(float (&d)[4], const uint32_t (
       "{%0, %1, %2, %3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// x rounded to tf32 (10 stored significand bits; the low 13 bits cleared),
+// to nearest with ties away from zero: half an ulp is added to the magnitude
+// bits before truncation (a carry into the exponent is the correct result).
+__device__ __forceinline__ uint32_t round_tf32(uint32_t bits) { return (bits + 0x1000u) & 0xffffe000u; }
+
+// x -> tf32 hi + lo with x = hi + lo + O(2^-22 x) (x - hi is exact in fp32).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = round_tf32(__float_as_uint(x));
+  lo = round_tf32(__float_as_uint(x - __uint_as_float(hi)));
 }
 
 // (x0, x1) -> bf16x2 hi and lo parts (x0 in the low half): x = hi + lo + O(2^-16 x).
@@ -834,11 +845,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         uint32_t a[4], ahi[4], alo[4];
         ldsm_x4(a, a_p + 32 * s);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          // tf32 hi = the top 19 bits; lo = the exact remainder, truncated likewise
-          ahi[e] = a[e] & 0xffffe000u;
-          alo[e] = __float_as_uint(__uint_as_float(a[e]) - __uint_as_float(ahi[e])) & 0xffffe000u;
-        }
+        for (int e = 0; e < 4; ++e) split_tf32(__uint_as_float(a[e]), ahi[e], alo[e]);
         const float2 m = s_mono[s][lane];
         mma_tf32_m16n8k8(dP, alo, __float_as_uint(m.x), __float_as_uint(m.y));
         mma_tf32_m16n8k8(dP, ahi, __float_as_uint(m.x), __float_as_uint(m.y));
