@@ -125,14 +125,18 @@ def algorithmic_bytes(stats):
     and each visible Gaussian's record once (uv 8 + conic/opacity 16 + colour
     12 + depth 4 + features 4N) and writes (5+N)*4 + 12 B per pixel; the
     adjoint reads the same plus the per-pixel state (8 B) and cotangents
-    ((5+N)*4 B) and writes 24 + (4+N)*4 B of gradients per visible Gaussian."""
+    ((5+N)*4 B) and writes 24 + (4+N)*4 B of gradients per visible Gaussian.
+    With the L1 loss fused (this step), the forward also reads the targets
+    ((4+N)*4 B per pixel) and writes the cotangent sign words (8 B per
+    pixel), which the adjoint (k_render_bwd_mma) reads instead of cotangent
+    images."""
     P, Pv, I, HW, N = stats["P"], stats["P_vis"], stats["I"], WIDTH * HEIGHT, N_FEAT
     rec = 8 + 16 + 12 + 4 + 4 * N
     return {
         "k_project": P * (44 + 48),
-        "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12),
+        "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12) + HW * ((4 + N) * 4 + 8),
         "k_render_bwd": I * 4 + Pv * rec + HW * (8 + (5 + N) * 4) + Pv * (24 + (4 + N) * 4),
-        "k_render_bwd_mma": I * 4 + Pv * rec + HW * (8 + (5 + N) * 4) + Pv * (24 + (4 + N) * 4),
+        "k_render_bwd_mma": I * 4 + Pv * rec + HW * (8 + 8) + Pv * (24 + (4 + N) * 4),
         "k_project_bwd": P * (40 + 24) + Pv * 40,
     }
 
@@ -202,16 +206,15 @@ def run_ours(args, rank, world, local_rank):
     ras.check_status()
     HW = WIDTH * HEIGHT
     scales_l1 = {"rgb": 1.0 / (3 * HW), "depth": 1.0 / HW, "feat": 1.0 / (N_FEAT * HW)}
-    grads_in = {n: torch.empty_like(targets[my_frames[0]][n]) for n in ("rgb", "depth", "feat")}
     loss = torch.zeros(1, device=dev)
 
     def step(k):
+        # forward with the L1 loss against the frame's targets (evaluated in the
+        # compositing epilogue), then its adjoint with the pose gradient
         cam = frame_camera(k)
-        fw = ras.forward(cam, means, scales, quats, opac, cols, feats)
-        for n in ("rgb", "depth", "feat"):
-            g.l1_loss_grad(fw[n], targets[k][n], scales_l1[n], grad=grads_in[n], loss=loss)
-        return ras.backward(cam, means, scales, quats, cols, feats, grads_in["rgb"], grads_in["depth"], None,
-                            grads_in["feat"])
+        ras.forward(cam, means, scales, quats, opac, cols, feats, l1_targets=targets[k], l1_weights=scales_l1,
+                    l1_loss=loss)
+        return ras.backward_l1(cam, means, scales, quats, cols, feats, scales_l1)
 
     stream = torch.cuda.current_stream()
     for i in range(args.warmup):
@@ -284,10 +287,8 @@ def run_ours(args, rank, world, local_rank):
         cam = frame_camera(k)
         m, s_, q, o, c, f = d_params
         loss.zero_()
-        fw = ras.forward(cam, m, s_, q, o, c, f)
-        for n in ("rgb", "depth", "feat"):
-            g.l1_loss_grad(fw[n], d_tgt[n], scales_l1[n], grad=grads_in[n], loss=loss)
-        gr = ras.backward(cam, m, s_, q, c, f, grads_in["rgb"], grads_in["depth"], None, grads_in["feat"])
+        ras.forward(cam, m, s_, q, o, c, f, l1_targets=d_tgt, l1_weights=scales_l1, l1_loss=loss)
+        gr = ras.backward_l1(cam, m, s_, q, c, f, scales_l1)
         out_pose.copy_(gr["pose"], non_blocking=True)
         out_loss.copy_(loss, non_blocking=True)
 

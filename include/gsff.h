@@ -231,6 +231,54 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
                         float* d_pose, int32_t* status, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * L1 image loss fused into compositing: the colour and depth L1 terms of the
+ * mapping loss (Sec. 3.2) and the feature L1 term (Eq. 10 on the rendered
+ * field),
+ *   L = w_rgb sum |rgb - rgb*| + w_depth sum |D - D*| + w_feat sum |F - F*|
+ * (sums over pixels and channels), with dL/dpred = w sign(pred - target),
+ * sign(0) = 0 -- the values gs_l1_loss_grad writes, never stored as floats.
+ *
+ * gs_render_fwd_l1 -- gs_render_fwd (same arguments and outputs) that also
+ * adds L to *loss (device float, atomic; the caller zeroes it; may be NULL)
+ * and writes l1_signs [H*W][2] (uint32): for each pixel, word 0 has bit c set
+ * where the cotangent of channel c is nonzero and word 1 where it is
+ * negative; bits 0..15 are features 0..15, bits 16, 17, 18 red, green, blue
+ * and bit 19 depth. A NULL target drops its term (its bits stay 0).
+ * gs_render_bwd_l1 -- gs_render_bwd (same arguments and outputs, no
+ * cotangent images, no alpha cotangent) whose cotangents are w sign(...)
+ * rebuilt from the l1_signs of the forward it differentiates and the weights
+ * of l1 (its targets and loss are not used).
+ * Both: features with N <= 16 on the fp32 path and decoupled feature
+ * gradients; other configurations return GS_ERR_UNSUPPORTED (use
+ * gs_l1_loss_grad with gs_render_fwd / gs_render_bwd there).
+ */
+typedef struct {
+  const float* target_rgb;    /* [3,H,W] */
+  const float* target_depth;  /* [H,W] */
+  const float* target_feat;   /* layout of out_feat */
+  float w_rgb, w_depth, w_feat;
+  float* loss;
+} gs_l1_terms;
+
+gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_ranges,
+                           const uint32_t* gids, const float* uv, const float* conic_opacity,
+                           const float* depth, const float* colors, const void* feats, int32_t N,
+                           int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
+                           float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
+                           float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
+                           const gs_l1_terms* l1, uint32_t* l1_signs, int32_t* status, void* stream);
+
+gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, const float* scales,
+                           const float* quats, const float* colors, const void* feats, int32_t N,
+                           int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
+                           const int32_t* tile_ranges, const uint32_t* gids, const float* uv,
+                           const float* conic_opacity, const float* depth, const float* T_final,
+                           const int32_t* last_idx, const gs_l1_terms* l1, const uint32_t* l1_signs,
+                           void* workspace, size_t workspace_bytes, float* d_means, float* d_scales,
+                           float* d_quats, float* d_opacity, float* d_colors, float* d_feats,
+                           float* d_pose, int32_t* status, void* stream);
+
+/* ---------------------------------------------------------------------------
  * gs_l1_loss_grad -- the L1 photometric term of the tracking and mapping
  * losses (Eq. 5, Eq. 7): grad[i] = scale * sign(pred[i] - target[i]) (sign(0)
  * = 0) and *loss_sum += scale * sum |pred - target| (device float, atomic).

@@ -38,7 +38,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
-           "gs_sh_colors", "gs_sh_colors_bwd")
+           "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1")
 
 
 class GsffError(RuntimeError):
@@ -55,6 +55,28 @@ class GsCamera(ctypes.Structure):
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("near_z", ctypes.c_float),
                 ("pose_dev", ctypes.c_void_p)]
+
+
+class GsL1Terms(ctypes.Structure):
+    _fields_ = [("target_rgb", ctypes.c_void_p), ("target_depth", ctypes.c_void_p), ("target_feat", ctypes.c_void_p),
+                ("w_rgb", ctypes.c_float), ("w_depth", ctypes.c_float), ("w_feat", ctypes.c_float),
+                ("loss", ctypes.c_void_p)]
+
+
+def l1_terms(targets=None, weights=None, loss=None) -> GsL1Terms:
+    """The gs_l1_terms of an L1 loss: targets and weights are dicts with any of "rgb", "depth", "feat"."""
+    t = GsL1Terms()
+    for k, v in (targets or {}).items():
+        if v is None:
+            continue
+        _need(v, torch.float32, "target " + k)
+        setattr(t, "target_" + k, v.data_ptr())
+        setattr(t, "w_" + k, float(weights[k]))
+    if targets is None:
+        for k, w in (weights or {}).items():
+            setattr(t, "w_" + k, float(w))
+    t.loss = None if loss is None else loss.data_ptr()
+    return t
 
 
 def camera_struct(cam) -> GsCamera:
@@ -135,6 +157,12 @@ def lib():
     L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +
                                 [_i32, _vp, _sz] + [_vp] * 9)
     L.gs_render_bwd.restype = ctypes.c_int
+    L.gs_render_fwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 7 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
+                                   [ctypes.POINTER(GsL1Terms), _vp, _vp, _vp])
+    L.gs_render_fwd_l1.restype = ctypes.c_int
+    L.gs_render_bwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 7 +
+                                   [ctypes.POINTER(GsL1Terms), _vp, _vp, _sz] + [_vp] * 9)
+    L.gs_render_bwd_l1.restype = ctypes.c_int
     L.gs_l1_loss_grad.argtypes = [_i64, _vp, _vp, _f32, _vp, _vp, _vp]
     L.gs_l1_loss_grad.restype = ctypes.c_int
     L.gs_trace_enable.argtypes = [_i32]
@@ -231,10 +259,12 @@ def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=
 
 
 def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT_CHW, bg=None, out=None,
-               status=None, stream=None, visible=None):
+               status=None, stream=None, visible=None, l1_targets=None, l1_weights=None, l1_loss=None):
     """gs_render_fwd: returns dict(rgb [3,H,W], depth [H,W], alpha [H,W], feat, T_final, last_idx, n_contrib).
     `visible` (uint8 [P], optional) receives 1 for every Gaussian blended with T > 0.5 in front of it;
-    the caller zeroes it."""
+    the caller zeroes it. With l1_targets (dict with any of "rgb", "depth", "feat") and l1_weights:
+    gs_render_fwd_l1, which also adds the weighted L1 loss to l1_loss and leaves the cotangent signs in
+    out["l1_signs"] (int32 [H*W, 2]) for render_bwd_l1."""
     H, W = cam.height, cam.width
     dev = colors.device
     P = colors.shape[0]
@@ -255,12 +285,19 @@ def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT
     bgc = (ctypes.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
     st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
     c = camera_struct(cam)
-    _check(lib().gs_render_fwd(ctypes.byref(c), P, _ptr(sort["tile_ranges"]), _ptr(sort["gids"]), _ptr(proj["uv"]),
-                               _ptr(proj["conic_opacity"]), _ptr(proj["depth"]), _ptr(colors),
-                               _ptr(feats) if feat_on else None, N if feat_on else 0, dtype, layout, flags,
-                               ctypes.cast(bgc, _vp), _ptr(o["rgb"]), _ptr(o["depth"]), _ptr(o["alpha"]),
-                               _ptr(o.get("feat")) if feat_on else None, _ptr(o["T_final"]), _ptr(o["last_idx"]),
-                               _ptr(o["n_contrib"]), _ptr(visible), _ptr(st), _stream(stream)), "gs_render_fwd")
+    args = (ctypes.byref(c), P, _ptr(sort["tile_ranges"]), _ptr(sort["gids"]), _ptr(proj["uv"]),
+            _ptr(proj["conic_opacity"]), _ptr(proj["depth"]), _ptr(colors), _ptr(feats) if feat_on else None,
+            N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(o["rgb"]), _ptr(o["depth"]),
+            _ptr(o["alpha"]), _ptr(o.get("feat")) if feat_on else None, _ptr(o["T_final"]), _ptr(o["last_idx"]),
+            _ptr(o["n_contrib"]), _ptr(visible))
+    if l1_targets is None:
+        _check(lib().gs_render_fwd(*args, _ptr(st), _stream(stream)), "gs_render_fwd")
+        return o
+    if o.get("l1_signs") is None:
+        o["l1_signs"] = torch.empty(H * W, 2, dtype=torch.int32, device=dev)
+    terms = l1_terms({k: v for k, v in l1_targets.items() if feat_on or k != "feat"}, l1_weights, l1_loss)
+    _check(lib().gs_render_fwd_l1(*args, ctypes.byref(terms), _ptr(o["l1_signs"]), _ptr(st), _stream(stream)),
+           "gs_render_fwd_l1")
     return o
 
 
@@ -418,6 +455,40 @@ def render_bwd(cam, means, scales, quats, colors, feats, proj, sort, fwd, g_rgb=
     return g
 
 
+def render_bwd_l1(cam, means, scales, quats, colors, feats, proj, sort, fwd, weights, flags=None,
+                  layout=GS_LAYOUT_CHW, bg=None, grads=None, workspace=None, status=None, stream=None):
+    """gs_render_bwd_l1: the adjoint of the L1 loss evaluated by render_fwd(..., l1_targets=...), its
+    cotangents rebuilt from fwd["l1_signs"] and weights (dict with "rgb", "depth", "feat"). Gradients as
+    render_bwd."""
+    P = means.shape[0]
+    dev = means.device
+    N = 0 if feats is None else feats.shape[1]
+    if flags is None:
+        flags = GS_FEAT_ON if N > 0 else GS_FEAT_OFF
+    feat_on = bool(flags & GS_FEAT_ON)
+    dtype = GS_BF16 if (feats is not None and feats.dtype == torch.bfloat16) else GS_F32
+    g = grads if grads is not None else dict(
+        means=torch.zeros(P, 3, device=dev), scales=torch.zeros(P, 3, device=dev),
+        quats=torch.zeros(P, 4, device=dev), opacity=torch.zeros(P, device=dev),
+        colors=torch.zeros(P, 3, device=dev), feats=torch.zeros(P, max(N, 1), device=dev)[:, :N],
+        pose=torch.zeros(6, device=dev))
+    ws = workspace if workspace is not None else torch.empty(max(render_bwd_workspace_bytes(P), 256),
+                                                             dtype=torch.uint8, device=dev)
+    bgc = (ctypes.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    terms = l1_terms(None, {k: weights.get(k, 0.0) for k in ("rgb", "depth", "feat")})
+    c = camera_struct(cam)
+    _check(lib().gs_render_bwd_l1(
+        ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(colors), _ptr(feats) if feat_on else None,
+        N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(sort["tile_ranges"]),
+        _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
+        _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), ctypes.byref(terms), _ptr(fwd["l1_signs"]), _ptr(ws), ws.numel(),
+        _ptr(g.get("means")), _ptr(g.get("scales")), _ptr(g.get("quats")), _ptr(g.get("opacity")),
+        _ptr(g.get("colors")), _ptr(g["feats"]) if feat_on else None, _ptr(g["pose"]), _ptr(st), _stream(stream)),
+        "gs_render_bwd_l1")
+    return g
+
+
 def l1_loss_grad(pred, target, scale, grad=None, loss=None, stream=None):
     """gs_l1_loss_grad: grad = scale sign(pred - target); loss += scale sum |pred - target|."""
     _need(pred, torch.float32, "pred")
@@ -509,12 +580,15 @@ class Rasterizer:
             self._alloc_sort()
         return need
 
-    def forward(self, cam, means, scales, quats, opacity, colors, feats=None, bg=None, stream=None, visible=None):
+    def forward(self, cam, means, scales, quats, opacity, colors, feats=None, bg=None, stream=None, visible=None,
+                l1_targets=None, l1_weights=None, l1_loss=None):
+        """Project, bin and composite; with l1_targets also the L1 loss of the images (see render_fwd)."""
         project(cam, means, scales, quats, opacity, out=self.proj, stream=stream)
         bin_sort(cam, self.proj, self.capacity, workspace=self.sort_ws, out=self.sort, status=self.status,
                  stream=stream)
         render_fwd(cam, self.proj, self.sort, colors, feats, flags=self.flags, layout=self.layout, bg=bg,
-                   out=self.fwd, status=self.status, stream=stream, visible=visible)
+                   out=self.fwd, status=self.status, stream=stream, visible=visible, l1_targets=l1_targets,
+                   l1_weights=l1_weights, l1_loss=l1_loss)
         return self.fwd
 
     def backward(self, cam, means, scales, quats, colors, feats=None, g_rgb=None, g_depth=None, g_alpha=None,
@@ -524,6 +598,16 @@ class Rasterizer:
         render_bwd(cam, means, scales, quats, colors, feats, self.proj, self.sort, self.fwd, g_rgb, g_depth, g_alpha,
                    g_feat, flags=self.flags, layout=self.layout, bg=bg, coupled=coupled, grads=self.grads,
                    workspace=self.bwd_ws, status=self.status, stream=stream)
+        return self.grads
+
+    def backward_l1(self, cam, means, scales, quats, colors, feats, weights, bg=None, zero=True, stream=None):
+        """The adjoint of the L1 loss that the last forward(..., l1_targets=...) evaluated
+        (gs_render_bwd_l1)."""
+        if zero:
+            self.grad_arena.zero_()
+        render_bwd_l1(cam, means, scales, quats, colors, feats, self.proj, self.sort, self.fwd, weights,
+                      flags=self.flags, layout=self.layout, bg=bg, grads=self.grads, workspace=self.bwd_ws,
+                      status=self.status, stream=stream)
         return self.grads
 
     def render_pose_grad(self, cam, means, scales, quats, colors, g_rgb, g_depth, grads, stream=None):

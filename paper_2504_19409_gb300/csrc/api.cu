@@ -23,13 +23,13 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
-                            int32_t* n_contrib, uint8_t* visible, cudaStream_t st);
+                            int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1, cudaStream_t st);
 gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
                             const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
                             int coupled, float* d_uv, float* d_conic, float* d_depth, float* d_opacity,
-                            float* d_colors, float* d_feats, cudaStream_t st);
+                            float* d_colors, float* d_feats, const L1Bwd* l1, cudaStream_t st);
 
 // ---- tracing -----------------------------------------------------------------
 namespace {
@@ -209,12 +209,13 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                          S(stream));
 }
 
-gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const uint32_t* gids,
-                        const float* uv, const float* conic_opacity, const float* depth, const float* colors,
-                        const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
-                        const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
-                        float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
-                        int32_t* status, void* stream) {
+namespace {
+gs_status render_fwd_impl(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const uint32_t* gids,
+                          const float* uv, const float* conic_opacity, const float* depth, const float* colors,
+                          const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
+                          const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
+                          float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1,
+                          int32_t* status, void* stream) {
   if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
   if (!tile_ranges || !gids || !out_rgb || !out_depth || !out_alpha || !T_final || !last_idx || !n_contrib)
     return GS_ERR_INVALID_ARG;
@@ -232,19 +233,56 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
   const float* b = bg ? bg : kBlack;
   const CamF k = make_cam(*cam);
   if (feat_on && (flags & GS_FEAT_TENSOR_CORE)) {
+    if (l1) return GS_ERR_UNSUPPORTED;
     if (feat_dtype != GS_BF16 || layout != GS_LAYOUT_HWC || N % 64 != 0 || N > 512) return GS_ERR_UNSUPPORTED;
     // geometry channels and the saved state on the SIMT kernel, features on tcgen05
     gs_status st = launch_render_fwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, nullptr, 0, 0, 1, b,
                                      out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, visible,
-                                     S(stream));
+                                     nullptr, S(stream));
     if (st != GS_OK) return st;
     return launch_render_fwd_tc(k, tile_ranges, gids, uv, conic_opacity,
                                 static_cast<const __nv_bfloat16*>(feats), last_idx, N, out_feat, status,
                                 S(stream));
   }
+  if (l1 && n > 16) return GS_ERR_UNSUPPORTED;
   return launch_render_fwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, n,
                            feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, out_rgb, out_depth, out_alpha, out_feat,
-                           T_final, last_idx, n_contrib, visible, S(stream));
+                           T_final, last_idx, n_contrib, visible, l1, S(stream));
+}
+}  // namespace
+
+gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const uint32_t* gids,
+                        const float* uv, const float* conic_opacity, const float* depth, const float* colors,
+                        const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
+                        const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
+                        float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
+                        int32_t* status, void* stream) {
+  return render_fwd_impl(cam, P, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, N, feat_dtype, layout,
+                         flags, bg, out_rgb, out_depth, out_alpha, out_feat, T_final, last_idx, n_contrib, visible,
+                         nullptr, status, stream);
+}
+
+gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const uint32_t* gids,
+                           const float* uv, const float* conic_opacity, const float* depth, const float* colors,
+                           const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
+                           const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
+                           float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
+                           const gs_l1_terms* l1, uint32_t* l1_signs, int32_t* status, void* stream) {
+  if (!l1 || !l1_signs || !aligned(l1_signs, 8)) return GS_ERR_INVALID_ARG;
+  const bool feat_on = (flags & GS_FEAT_ON) != 0;
+  L1Fwd in{};
+  in.on = 1;
+  in.target[0] = l1->target_rgb;
+  in.target[1] = l1->target_depth;
+  in.target[2] = feat_on ? l1->target_feat : nullptr;
+  in.w[0] = l1->w_rgb;
+  in.w[1] = l1->w_depth;
+  in.w[2] = l1->w_feat;
+  in.loss = l1->loss;
+  in.signs = reinterpret_cast<uint2*>(l1_signs);
+  return render_fwd_impl(cam, P, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, N, feat_dtype, layout,
+                         flags, bg, out_rgb, out_depth, out_alpha, out_feat, T_final, last_idx, n_contrib, visible,
+                         &in, status, stream);
 }
 
 size_t gs_render_bwd_workspace_bytes(int32_t P) {
@@ -253,15 +291,16 @@ size_t gs_render_bwd_workspace_bytes(int32_t P) {
   return align_up((size_t)P * 2 * 4, 256) + align_up((size_t)P * 3 * 4, 256) + align_up((size_t)P * 4, 256);
 }
 
-gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales, const float* quats,
-                        const float* colors, const void* feats, int32_t N, int32_t feat_dtype, int32_t layout,
-                        int32_t flags, const float* bg, const int32_t* tile_ranges, const uint32_t* gids,
-                        const float* uv, const float* conic_opacity, const float* depth, const float* T_final,
-                        const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth, const float* dL_dalpha,
-                        const float* dL_dfeat, int32_t feat_grad_mode, void* workspace, size_t workspace_bytes,
-                        float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_colors,
-                        float* d_feats, float* d_pose, int32_t* status, void* stream) {
-  (void)status;
+namespace {
+gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, const float* scales,
+                          const float* quats, const float* colors, const void* feats, int32_t N, int32_t feat_dtype,
+                          int32_t layout, int32_t flags, const float* bg, const int32_t* tile_ranges,
+                          const uint32_t* gids, const float* uv, const float* conic_opacity, const float* depth,
+                          const float* T_final, const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
+                          const float* dL_dalpha, const float* dL_dfeat, const L1Bwd* l1, int32_t feat_grad_mode,
+                          void* workspace, size_t workspace_bytes, float* d_means, float* d_scales, float* d_quats,
+                          float* d_opacity, float* d_colors, float* d_feats, float* d_pose, int32_t* status,
+                          void* stream) {
   if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
   if (!tile_ranges || !gids || !T_final || !last_idx || !workspace) return GS_ERR_INVALID_ARG;
   if (P > 0 && (!means || !scales || !quats || !colors || !uv || !conic_opacity || !depth)) return GS_ERR_INVALID_ARG;
@@ -284,6 +323,7 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
   if (tc && (coupled || feat_dtype != GS_BF16 || layout != GS_LAYOUT_HWC || N % 128 != 0 || N > 512))
     return GS_ERR_UNSUPPORTED;
   if (tc && ((dL_dfeat && !aligned(dL_dfeat, 16)) || !aligned(d_feats, 16))) return GS_ERR_INVALID_ARG;
+  if (l1 && (tc || coupled || n > 16)) return GS_ERR_UNSUPPORTED;
   const float* b = bg ? bg : kBlack;
   const CamF k = make_cam(*cam);
   char* ws = static_cast<char*>(workspace);
@@ -296,7 +336,7 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
   gs_status st = launch_render_bwd(k, tile_ranges, gids, uv, conic_opacity, depth, colors, feats, tc ? 0 : n,
                                    feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, T_final, last_idx, dL_drgb,
                                    dL_ddepth, dL_dalpha, (feat_on && !tc) ? dL_dfeat : nullptr, coupled ? 1 : 0, w_uv,
-                                   w_conic, w_depth, d_opacity, d_colors, d_feats, S(stream));
+                                   w_conic, w_depth, d_opacity, d_colors, d_feats, l1, S(stream));
   if (st != GS_OK) return st;
   if (tc && dL_dfeat) {
     st = launch_render_bwd_feat_tc(k, tile_ranges, gids, uv, conic_opacity, last_idx, dL_dfeat, N, d_feats, status,
@@ -305,6 +345,42 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
   }
   launch_project_bwd(k, P, means, scales, quats, w_uv, w_conic, w_depth, d_means, d_scales, d_quats, d_pose, S(stream));
   return last_launch_status();
+}
+}  // namespace
+
+gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales, const float* quats,
+                        const float* colors, const void* feats, int32_t N, int32_t feat_dtype, int32_t layout,
+                        int32_t flags, const float* bg, const int32_t* tile_ranges, const uint32_t* gids,
+                        const float* uv, const float* conic_opacity, const float* depth, const float* T_final,
+                        const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth, const float* dL_dalpha,
+                        const float* dL_dfeat, int32_t feat_grad_mode, void* workspace, size_t workspace_bytes,
+                        float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_colors,
+                        float* d_feats, float* d_pose, int32_t* status, void* stream) {
+  return render_bwd_impl(cam, P, means, scales, quats, colors, feats, N, feat_dtype, layout, flags, bg, tile_ranges,
+                         gids, uv, conic_opacity, depth, T_final, last_idx, dL_drgb, dL_ddepth, dL_dalpha, dL_dfeat,
+                         nullptr, feat_grad_mode, workspace, workspace_bytes, d_means, d_scales, d_quats, d_opacity,
+                         d_colors, d_feats, d_pose, status, stream);
+}
+
+gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, const float* scales,
+                           const float* quats, const float* colors, const void* feats, int32_t N, int32_t feat_dtype,
+                           int32_t layout, int32_t flags, const float* bg, const int32_t* tile_ranges,
+                           const uint32_t* gids, const float* uv, const float* conic_opacity, const float* depth,
+                           const float* T_final, const int32_t* last_idx, const gs_l1_terms* l1,
+                           const uint32_t* l1_signs, void* workspace, size_t workspace_bytes, float* d_means,
+                           float* d_scales, float* d_quats, float* d_opacity, float* d_colors, float* d_feats,
+                           float* d_pose, int32_t* status, void* stream) {
+  if (!l1 || !l1_signs || !aligned(l1_signs, 8)) return GS_ERR_INVALID_ARG;
+  L1Bwd in{};
+  in.on = 1;
+  in.signs = reinterpret_cast<const uint2*>(l1_signs);
+  in.w[0] = l1->w_rgb;
+  in.w[1] = l1->w_depth;
+  in.w[2] = l1->w_feat;
+  return render_bwd_impl(cam, P, means, scales, quats, colors, feats, N, feat_dtype, layout, flags, bg, tile_ranges,
+                         gids, uv, conic_opacity, depth, T_final, last_idx, nullptr, nullptr, nullptr, nullptr, &in,
+                         GS_FEAT_GRAD_DECOUPLED, workspace, workspace_bytes, d_means, d_scales, d_quats, d_opacity,
+                         d_colors, d_feats, d_pose, status, stream);
 }
 
 gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, float scale, float* grad,

@@ -88,6 +88,25 @@ __device__ __forceinline__ bool pair_alpha(float4 co, float dx, float dy, PairAl
   return r.alpha >= kAlphaMin;
 }
 
+// L1 image loss fused into compositing (class 0 rgb, 1 depth, 2 features).
+// The forward evaluates w |pred - target| and stores, per pixel, which
+// cotangents w sign(pred - target) are nonzero (word x) and negative (word y),
+// bit c for feature c < 16, bits 16, 17, 18 for r, g, b and 19 for depth; the
+// adjoint rebuilds the cotangents from those bits and the weights.
+constexpr int kL1BitRgb = 16, kL1BitDepth = 19;
+struct L1Fwd {
+  int on;
+  const float* target[3];  // null: the class has no term
+  float w[3];
+  float* loss;             // device float or null
+  uint2* signs;            // [H W]
+};
+struct L1Bwd {
+  int on;
+  const uint2* signs;
+  float w[3];
+};
+
 // ---- tracing (api.cu) -----------------------------------------------------
 void trace_begin(const char* name, cudaStream_t s);
 void trace_end(cudaStream_t s);

@@ -55,6 +55,7 @@ struct FwdParams {
   int* last_idx;
   int* n_contrib;
   uint8_t* visible;  // [P] or null: set to 1 when blended with T > 0.5 in front (Sec. 3.2)
+  L1Fwd l1;          // L1 loss against targets, evaluated in the epilogue (N <= 16)
 };
 
 
@@ -192,11 +193,13 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   __shared__ float4 s_cd[kTilePix];
   __shared__ float s_f[kTilePix][NCs];
   __shared__ uint32_t s_gid[VIS ? kTilePix : 1];
+  __shared__ float s_lsum;
 
   const int tile = blockIdx.x;
   const int chunk = blockIdx.y;
   const bool geom = chunk == 0;
   const bool mark = VIS && geom;
+  if (threadIdx.x == 0) s_lsum = 0.f;
   const unsigned lanes_below = (1u << (threadIdx.x & 31)) - 1u;
   const int c0 = chunk * NC;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
@@ -270,36 +273,69 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
       }
     }
   }
-  if (!inside) return;
   const size_t HW = (size_t)p.cam.W * p.cam.H;
-  const size_t pix = (size_t)py * p.cam.W + px;
-  if (geom) {
-    p.out_rgb[pix] = ac0 + T * p.bg[0];
-    p.out_rgb[HW + pix] = ac1 + T * p.bg[1];
-    p.out_rgb[2 * HW + pix] = ac2 + T * p.bg[2];
-    p.out_depth[pix] = ad;
-    p.out_alpha[pix] = 1.f - T;
-    p.T_final[pix] = T;
-    p.last_idx[pix] = last;
-    p.n_contrib[pix] = cnt;
-  }
-  if (NC > 0) {
-    const int nch = min(NC, p.N - c0);
-    if (p.hwc) {
-      float* dst = p.out_feat + pix * p.N + c0;
-      if ((p.N & 3) == 0 && nch == NC) {
+  const size_t pix = inside ? (size_t)py * p.cam.W + px : 0;
+  float lsum = 0.f;
+  if (inside) {
+    const float r0 = ac0 + T * p.bg[0], r1 = ac1 + T * p.bg[1], r2 = ac2 + T * p.bg[2];
+    if (geom) {
+      p.out_rgb[pix] = r0;
+      p.out_rgb[HW + pix] = r1;
+      p.out_rgb[2 * HW + pix] = r2;
+      p.out_depth[pix] = ad;
+      p.out_alpha[pix] = 1.f - T;
+      p.T_final[pix] = T;
+      p.last_idx[pix] = last;
+      p.n_contrib[pix] = cnt;
+    }
+    if (NC > 0) {
+      const int nch = min(NC, p.N - c0);
+      if (p.hwc) {
+        float* dst = p.out_feat + pix * p.N + c0;
+        if ((p.N & 3) == 0 && nch == NC) {
 #pragma unroll
-        for (int c = 0; c < NCs; c += 4) *reinterpret_cast<float4*>(dst + c) = make_float4(af[c], af[c + 1], af[c + 2], af[c + 3]);
+          for (int c = 0; c < NCs; c += 4) *reinterpret_cast<float4*>(dst + c) = make_float4(af[c], af[c + 1], af[c + 2], af[c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < NCs; ++c)
+            if (c < nch) dst[c] = af[c];
+        }
       } else {
 #pragma unroll
         for (int c = 0; c < NCs; ++c)
-          if (c < nch) dst[c] = af[c];
+          if (c < nch) p.out_feat[(size_t)(c0 + c) * HW + pix] = af[c];
       }
-    } else {
-#pragma unroll
-      for (int c = 0; c < NCs; ++c)
-        if (c < nch) p.out_feat[(size_t)(c0 + c) * HW + pix] = af[c];
     }
+    if (p.l1.on) {
+      // L1 terms of this pixel; cotangent signs as bits (see L1Fwd)
+      uint32_t nz = 0, ng = 0;
+      auto term = [&](float pred, float target, float w, int bit) {
+        const float d = pred - target;
+        lsum += w * fabsf(d);
+        nz |= (d != 0.f ? 1u : 0u) << bit;
+        ng |= (d < 0.f ? 1u : 0u) << bit;
+      };
+      if (p.l1.target[0]) {
+        term(r0, p.l1.target[0][pix], p.l1.w[0], kL1BitRgb);
+        term(r1, p.l1.target[0][HW + pix], p.l1.w[0], kL1BitRgb + 1);
+        term(r2, p.l1.target[0][2 * HW + pix], p.l1.w[0], kL1BitRgb + 2);
+      }
+      if (p.l1.target[1]) term(ad, p.l1.target[1][pix], p.l1.w[1], kL1BitDepth);
+      if (NC > 0 && p.l1.target[2]) {
+        const int nch = min(NC, p.N);
+#pragma unroll
+        for (int c = 0; c < NCs; ++c)
+          if (c < nch) term(af[c], p.l1.target[2][p.hwc ? pix * p.N + c : (size_t)c * HW + pix], p.l1.w[2], c);
+      }
+      p.l1.signs[pix] = make_uint2(nz, ng);
+    }
+  }
+  if (p.l1.on && p.l1.loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.f) atomicAdd(&s_lsum, lsum);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_lsum != 0.f) atomicAdd(p.l1.loss, s_lsum);
   }
 }
 
@@ -327,6 +363,7 @@ struct BwdParams {
   float* d_opacity;
   float* d_colors;
   float* d_feats;
+  L1Bwd l1;  // cotangents rebuilt from the forward's L1 sign bits (tensor-core adjoint only)
 };
 
 // Lane l ends up with the warp-wide sum of v[l] (see the file comment).
@@ -627,6 +664,11 @@ __device__ __forceinline__ void mma_tf32_m16n8k8(float (&d)[4], const uint32_t (
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// L1 cotangent w sign(...) of bit b of a pixel's sign words (see L1Fwd).
+__device__ __forceinline__ float l1_cot(uint2 sg, int b, float w) {
+  return ((sg.x >> b) & 1u) ? (((sg.y >> b) & 1u) ? -w : w) : 0.f;
+}
+
 // x rounded to tf32 (10 stored significand bits; the low 13 bits cleared),
 // to nearest with ties away from zero: half an ulp is added to the magnitude
 // bits before truncation (a carry into the exponent is the correct result).
@@ -732,13 +774,21 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     if (inside) {
       T[q] = p.T_final[pix];
       last[q] = p.last_idx[pix];
-      if (p.g_rgb) {
-        gC0[q] = p.g_rgb[pix];
-        gC1[q] = p.g_rgb[HW + pix];
-        gC2[q] = p.g_rgb[2 * HW + pix];
+      if (p.l1.on) {
+        const uint2 sg = p.l1.signs[pix];
+        gC0[q] = l1_cot(sg, kL1BitRgb, p.l1.w[0]);
+        gC1[q] = l1_cot(sg, kL1BitRgb + 1, p.l1.w[0]);
+        gC2[q] = l1_cot(sg, kL1BitRgb + 2, p.l1.w[0]);
+        gD[q] = l1_cot(sg, kL1BitDepth, p.l1.w[1]);
+      } else {
+        if (p.g_rgb) {
+          gC0[q] = p.g_rgb[pix];
+          gC1[q] = p.g_rgb[HW + pix];
+          gC2[q] = p.g_rgb[2 * HW + pix];
+        }
+        if (p.g_depth) gD[q] = p.g_depth[pix];
+        if (p.g_alpha) gA = p.g_alpha[pix];
       }
-      if (p.g_depth) gD[q] = p.g_depth[pix];
-      if (p.g_alpha) gA = p.g_alpha[pix];
       if (last[q] > 0) atomicMax(&s_maxlast, last[q]);
     }
     gAb[q] = gA - (p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q]);
@@ -749,34 +799,72 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   uint32_t bh[NT][4][2], bl[NT][4][2];
   {
     const int bx = tx * kTile + (wid & 1) * 8, by = ty * kTile + (wid >> 1) * 8;
+    if (p.l1.on) {
+      // cotangents w sign(...) from the forward's sign bits: each of this lane's
+      // 16 pixels is read once for all n-tiles
+      int bit[NT];
+      float w[NT];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const int c = 8 * nt + g8;
-      const float* plane = nullptr;  // channel c of the cotangent, indexed by pixel * pstride
-      size_t pstride = 1;
-      if (c < NC) {
-        if (p.g_feat && c < p.N) {
-          plane = p.hwc ? p.g_feat + c : p.g_feat + (size_t)c * HW;
-          pstride = p.hwc ? (size_t)p.N : 1;
+      for (int nt = 0; nt < NT; ++nt) {
+        const int c = 8 * nt + g8;
+        bit[nt] = -1;
+        w[nt] = 0.f;
+        if (c < NC) {
+          if (c < p.N) bit[nt] = c, w[nt] = p.l1.w[2];
+        } else if (c < NC + 3) {
+          bit[nt] = kL1BitRgb + (c - NC), w[nt] = p.l1.w[0];
+        } else if (c == NC + 3) {
+          bit[nt] = kL1BitDepth, w[nt] = p.l1.w[1];
         }
-      } else if (c < NC + 3) {
-        if (p.g_rgb) plane = p.g_rgb + (size_t)(c - NC) * HW;
-      } else if (c == NC + 3) {
-        plane = p.g_depth;
       }
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf) {
           const int qx = bx + t4 + 4 * hf;
-          float v[2];
+          uint2 sg[2];
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const int qy = by + s + 4 * q;
-            v[q] = (plane && qx < p.cam.W && qy < p.cam.H) ? plane[((size_t)qy * p.cam.W + qx) * pstride] : 0.f;
+            sg[q] = (qx < p.cam.W && qy < p.cam.H) ? p.l1.signs[(size_t)qy * p.cam.W + qx] : make_uint2(0u, 0u);
           }
-          split_bf16x2(v[0], v[1], bh[nt][s][hf], bl[nt][s][hf]);
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            const float v0 = bit[nt] >= 0 ? l1_cot(sg[0], bit[nt], w[nt]) : 0.f;
+            const float v1 = bit[nt] >= 0 ? l1_cot(sg[1], bit[nt], w[nt]) : 0.f;
+            split_bf16x2(v0, v1, bh[nt][s][hf], bl[nt][s][hf]);
+          }
         }
+    } else {
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int c = 8 * nt + g8;
+        const float* plane = nullptr;  // channel c of the cotangent, indexed by pixel * pstride
+        size_t pstride = 1;
+        if (c < NC) {
+          if (p.g_feat && c < p.N) {
+            plane = p.hwc ? p.g_feat + c : p.g_feat + (size_t)c * HW;
+            pstride = p.hwc ? (size_t)p.N : 1;
+          }
+        } else if (c < NC + 3) {
+          if (p.g_rgb) plane = p.g_rgb + (size_t)(c - NC) * HW;
+        } else if (c == NC + 3) {
+          plane = p.g_depth;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf) {
+            const int qx = bx + t4 + 4 * hf;
+            float v[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int qy = by + s + 4 * q;
+              v[q] = (plane && qx < p.cam.W && qy < p.cam.H) ? plane[((size_t)qy * p.cam.W + qx) * pstride] : 0.f;
+            }
+            split_bf16x2(v[0], v[1], bh[nt][s][hf], bl[nt][s][hf]);
+          }
+      }
     }
   }
   __syncthreads();
@@ -1004,8 +1092,10 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
-                            int32_t* n_contrib, uint8_t* visible, cudaStream_t st) {
+                            int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1, cudaStream_t st) {
   FwdParams p;
+  p.l1 = l1 ? *l1 : L1Fwd{};
+  if (p.l1.on && N > 16) return GS_ERR_UNSUPPORTED;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.gids = gids;
@@ -1065,8 +1155,10 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
                             const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
                             int coupled, float* d_uv, float* d_conic, float* d_depth, float* d_opacity,
-                            float* d_colors, float* d_feats, cudaStream_t st) {
+                            float* d_colors, float* d_feats, const L1Bwd* l1, cudaStream_t st) {
   BwdParams p;
+  p.l1 = l1 ? *l1 : L1Bwd{};
+  if (p.l1.on && (N > 16 || coupled)) return GS_ERR_UNSUPPORTED;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.gids = gids;
