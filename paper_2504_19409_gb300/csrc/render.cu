@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
 // That replaces, per Gaussian and warp, 20 multiply-adds per pixel and a
 // 32-channel shuffle transposition.
 namespace mma_bwd {
-constexpr int kBB = 32;           // Gaussians per shared-memory batch
+constexpr int kBB = 16;           // Gaussians per shared-memory batch (= the rows of one contraction)
 constexpr int kRows = 16;         // Gaussians per warp contraction (MMA M)
 constexpr int kWStride = 72;      // bf16 per W row: 64 pixels + 8 (rows 144 B apart: conflict-free ldmatrix)
 constexpr int kPStride = 68;      // floats per dP row: 64 pixels + 4 (272 B)
@@ -633,8 +633,8 @@ struct MmaBwdShape {
   static constexpr int SR = mma_bwd::kMom + NCH;  // per-Gaussian sums: u, v, A, B, C, opacity, then NCH
   static constexpr size_t kWBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kWStride * 2;
   static constexpr size_t kPBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kPStride * 4;
-  static constexpr size_t kAccBytes = (size_t)2 * mma_bwd::kBB * SR * 4;
-  static constexpr size_t kSmem = 2 * kWBytes + kPBytes + kAccBytes;
+  static constexpr size_t kRedBytes = (size_t)2 * mma_bwd::kNW * mma_bwd::kBB * SR * 4;
+  static constexpr size_t kSmem = 2 * kWBytes + kPBytes + kRedBytes;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   __nv_bfloat16* s_wh = reinterpret_cast<__nv_bfloat16*>(smem_raw);                   // [kNW][kRows][kWStride]
   __nv_bfloat16* s_wl = reinterpret_cast<__nv_bfloat16*>(smem_raw + S::kWBytes);      // same
   float* s_p = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes);                     // [kNW][kRows][kPStride]
-  float* s_acc = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes + S::kPBytes);     // [2][kBB][SR]
+  float* s_red = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes + S::kPBytes);     // [2][kNW][kBB][SR]
   __shared__ float2 s_mono[8][32];  // B fragments of the monomials: [8-pixel step][lane]
   __shared__ BwdBatch s_b[kNBuf];
   __shared__ int s_maxlast;
@@ -754,7 +754,6 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     }
     s_mono[s][l] = make_float2(m[0], m[1]);
   }
-  for (int e = threadIdx.x; e < 2 * kBB * SR; e += kThreads) s_acc[e] = 0.f;
   __syncthreads();
   float T[2], pxc[2], pyc[2], gC0[2], gC1[2], gC2[2], gD[2], gAb[2];
   float Bc0[2], Bc1[2], Bc2[2], Bd[2], Sx[2];
@@ -800,23 +799,33 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   {
     const int bx = tx * kTile + (wid & 1) * 8, by = ty * kTile + (wid >> 1) * 8;
     if (p.l1.on) {
-      // cotangents w sign(...) from the forward's sign bits: each of this lane's
-      // 16 pixels is read once for all n-tiles
+      // cotangents w sign(...) from the forward's sign bits. The bf16 hi / lo of
+      // -w are those of w with the sign flipped, so each n-tile's split is made
+      // once and a value costs a few bit operations; each of this lane's 16
+      // pixels is read once for all n-tiles.
       int bit[NT];
-      float w[NT];
+      uint32_t hw[NT], lw[NT];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const int c = 8 * nt + g8;
-        bit[nt] = -1;
-        w[nt] = 0.f;
+        float w = 0.f;
+        bit[nt] = 0;
         if (c < NC) {
-          if (c < p.N) bit[nt] = c, w[nt] = p.l1.w[2];
+          if (c < p.N) bit[nt] = c, w = p.l1.w[2];
         } else if (c < NC + 3) {
-          bit[nt] = kL1BitRgb + (c - NC), w[nt] = p.l1.w[0];
+          bit[nt] = kL1BitRgb + (c - NC), w = p.l1.w[0];
         } else if (c == NC + 3) {
-          bit[nt] = kL1BitDepth, w[nt] = p.l1.w[1];
+          bit[nt] = kL1BitDepth, w = p.l1.w[1];
         }
+        const __nv_bfloat16 h = __float2bfloat16_rn(w);
+        hw[nt] = __bfloat16_as_ushort(h);
+        lw[nt] = __bfloat16_as_ushort(__float2bfloat16_rn(w - __bfloat162float(h)));
       }
+      // the bf16 bits of w sign(...) from a pixel's sign words
+      auto half = [](uint2 sg, int b, uint32_t v) -> uint32_t {
+        const uint32_t nz = (sg.x >> b) & 1u, ng = (sg.y >> b) & 1u;
+        return (v ^ (ng << 15)) & (0u - nz) & 0xffffu;
+      };
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -830,9 +839,8 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
           }
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
-            const float v0 = bit[nt] >= 0 ? l1_cot(sg[0], bit[nt], w[nt]) : 0.f;
-            const float v1 = bit[nt] >= 0 ? l1_cot(sg[1], bit[nt], w[nt]) : 0.f;
-            split_bf16x2(v0, v1, bh[nt][s][hf], bl[nt][s][hf]);
+            bh[nt][s][hf] = half(sg[0], bit[nt], hw[nt]) | (half(sg[1], bit[nt], hw[nt]) << 16);
+            bl[nt][s][hf] = half(sg[0], bit[nt], lw[nt]) | (half(sg[1], bit[nt], lw[nt]) << 16);
           }
         }
     } else {
@@ -896,109 +904,24 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   const uint32_t a_wh = smem_u32(wh_w + lrow * kWStride + 8 * lcol);
   const uint32_t a_wl = smem_u32(wl_w + lrow * kWStride + 8 * lcol);
   const uint32_t a_p = smem_u32(p_w + lrow * kPStride + 4 * lcol);
-  const float cxw = (float)(tx * kTile + (wid & 1) * 8 + 4), cyw = (float)(ty * kTile + (wid >> 1) * 8 + 4);
 
   for (int b = 0; b < nb; ++b) {
     const BwdBatch& B = s_b[b % kNBuf];
-    float* acc = s_acc + (b & 1) * kBB * SR;
+    float* red = s_red + (b & 1) * kNW * kBB * SR;  // [kNW][kBB][SR] of this batch
     const int lo = batch_lo(b), n = batch_hi(b) - lo;
     const bool stage = wid == 0 && b + 1 < nb && lane < batch_hi(b + 1) - batch_lo(b + 1);
     if (stage) stage_batch(p, s_b[(b + 1) % kNBuf], lane, g_next);
     if (wid == 0 && b + 2 < nb && lane < batch_hi(b + 2) - batch_lo(b + 2)) g_next = p.gids[batch_lo(b + 2) + lane];
 
-    // Rows of the warp's tiles are filled in walk order; lane r remembers the
-    // batch index of the Gaussian in row r. A flush contracts the filled rows
-    // (rows past `rows` hold stale values; their sums are not used) and adds
-    // them into the block's sums.
-    int rows = 0, row_j = 0;
-    auto flush = [&]() {
-      __syncwarp();
-      float dW[NT][4], dP[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt) dW[nt][0] = dW[nt][1] = dW[nt][2] = dW[nt][3] = 0.f;
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        uint32_t ah[4], al[4];
-        ldsm_x4(ah, a_wh + 32 * s);
-        ldsm_x4(al, a_wl + 32 * s);
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          mma_bf16_m16n8k16(dW[nt], al, bh[nt][s][0], bh[nt][s][1]);
-          mma_bf16_m16n8k16(dW[nt], ah, bl[nt][s][0], bl[nt][s][1]);
-          mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        uint32_t a[4], ahi[4], alo[4];
-        ldsm_x4(a, a_p + 32 * s);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) split_tf32(__uint_as_float(a[e]), ahi[e], alo[e]);
-        const float2 m = s_mono[s][lane];
-        mma_tf32_m16n8k8(dP, alo, __float_as_uint(m.x), __float_as_uint(m.y));
-        mma_tf32_m16n8k8(dP, ahi, __float_as_uint(m.x), __float_as_uint(m.y));
-      }
-      __syncwarp();
-      // D rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1
-      const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
-      if (g8 < rows) {
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const int c = 8 * nt + 2 * t4;
-          if (c < NCH) {
-            atomicAdd(acc + j0 * SR + kMom + c, dW[nt][0]);
-            atomicAdd(acc + j0 * SR + kMom + c + 1, dW[nt][1]);
-          }
-        }
-      }
-      if (g8 + 8 < rows) {
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const int c = 8 * nt + 2 * t4;
-          if (c < NCH) {
-            atomicAdd(acc + j1 * SR + kMom + c, dW[nt][2]);
-            atomicAdd(acc + j1 * SR + kMom + c + 1, dW[nt][3]);
-          }
-        }
-      }
-      // moments: lanes t4 = 0, 1, 2 of a quad hold columns (M0, Mx), (My, Mxx),
-      // (Mxy, Myy); lane t4 = 0 converts row g8, lane t4 = 1 row g8 + 8 into
-      // u, v, conic and opacity with (uu, vv) = u - block centre, dx = uu - x:
-      //   sum dx dp = uu M0 - Mx,  sum dx^2 dp = uu^2 M0 - 2 uu Mx + Mxx, ...
-      const int qb = lane & ~3;
-      const bool second = t4 == 1;
-      float m[kMom];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float a0 = __shfl_sync(0xffffffffu, dP[0], qb + k), a1 = __shfl_sync(0xffffffffu, dP[1], qb + k);
-        const float c0 = __shfl_sync(0xffffffffu, dP[2], qb + k), c1 = __shfl_sync(0xffffffffu, dP[3], qb + k);
-        m[2 * k] = second ? c0 : a0;
-        m[2 * k + 1] = second ? c1 : a1;
-      }
-      if (t4 < 2 && g8 + 8 * t4 < rows) {
-        const int j = second ? j1 : j0;
-        const float2 u = B.uv[j];
-        const float4 co = B.co[j];
-        const float uu = u.x - cxw, vv = u.y - cyw;
-        const float ox = uu * m[0] - m[1], oy = vv * m[0] - m[2];
-        float* a = acc + j * SR;
-        atomicAdd(a + 0, -(co.x * ox + co.y * oy));
-        atomicAdd(a + 1, -(co.y * ox + co.z * oy));
-        atomicAdd(a + 2, -0.5f * (uu * (uu * m[0] - 2.f * m[1]) + m[3]));
-        atomicAdd(a + 3, -(uu * (vv * m[0] - m[2]) - vv * m[1] + m[4]));
-        atomicAdd(a + 4, -0.5f * (vv * (vv * m[0] - 2.f * m[2]) + m[5]));
-        atomicAdd(a + 5, m[0] / co.w);
-      }
-      rows = 0;
-    };
-
     // walk: this warp's Gaussians of the batch in reverse list order, two at a
     // time. Both pairs' alphas are formed first (four independent chains); a
     // pair that does not blend takes alpha = 0, for which every update below
-    // is an exact identity (T / 1, 0 c + 1 B, S 1) and w = dp = 0.
+    // is an exact identity (T / 1, 0 c + 1 B, S 1) and w = dp = 0. Rows of the
+    // warp's tiles are filled in walk order; lane r remembers the batch index
+    // of the Gaussian in row r.
+    int rows = 0, row_j = 0;
     uint32_t bits = __ballot_sync(0xffffffffu, lane < n && ((B.wmask[lane] >> wid) & 1u));
     while (bits) {
-      if (rows > kRows - 2) flush();
       const int j1 = 31 - __clz(bits);
       bits &= ~(1u << j1);
       const bool two = bits != 0;
@@ -1052,36 +975,118 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         ++rows;
       }
     }
-    if (rows > 0) flush();
+    if (rows > 0) {
+      // contraction of the filled rows (rows past `rows` hold stale values:
+      // their sums are not stored) into this warp's sums of the batch
+      __syncwarp();
+      float dW[NT][4], dP[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) dW[nt][0] = dW[nt][1] = dW[nt][2] = dW[nt][3] = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        uint32_t ah[4], al4[4];
+        ldsm_x4(ah, a_wh + 32 * s);
+        ldsm_x4(al4, a_wl + 32 * s);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma_bf16_m16n8k16(dW[nt], al4, bh[nt][s][0], bh[nt][s][1]);
+          mma_bf16_m16n8k16(dW[nt], ah, bl[nt][s][0], bl[nt][s][1]);
+          mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        uint32_t a[4], ahi[4], alo[4];
+        ldsm_x4(a, a_p + 32 * s);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32(__uint_as_float(a[e]), ahi[e], alo[e]);
+        const float2 m = s_mono[s][lane];
+        mma_tf32_m16n8k8(dP, alo, __float_as_uint(m.x), __float_as_uint(m.y));
+        mma_tf32_m16n8k8(dP, ahi, __float_as_uint(m.x), __float_as_uint(m.y));
+      }
+      // D rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1: moments, then the W channels
+      const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
+      if (g8 < rows) {
+        float* r = red + ((size_t)wid * kBB + j0) * SR;
+        if (2 * t4 < kMom) *reinterpret_cast<float2*>(r + 2 * t4) = make_float2(dP[0], dP[1]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+          if (8 * nt + 2 * t4 < NCH)
+            *reinterpret_cast<float2*>(r + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][0], dW[nt][1]);
+      }
+      if (g8 + 8 < rows) {
+        float* r = red + ((size_t)wid * kBB + j1) * SR;
+        if (2 * t4 < kMom) *reinterpret_cast<float2*>(r + 2 * t4) = make_float2(dP[2], dP[3]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+          if (8 * nt + 2 * t4 < NCH)
+            *reinterpret_cast<float2*>(r + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][2], dW[nt][3]);
+      }
+    }
     if (stage) {
       cp_async_wait_all();
       finish_batch(s_b[(b + 1) % kNBuf], lane, tx, ty);
     }
     __syncthreads();
-    // one global atomic per (Gaussian, output) of the batch; the sums are
-    // cleared for the batch after next
-    for (int e = threadIdx.x; e < n * SR; e += kThreads) {
-      const float v = acc[e];
-      if (v == 0.f) continue;
-      acc[e] = 0.f;
-      const int j = e / SR, c = e - j * SR;
-      const uint32_t g = B.gid[j];
-      float* dst;
-      if (c < 2) dst = p.d_uv + 2 * (size_t)g + c;
-      else if (c < 5) dst = p.d_conic + 3 * (size_t)g + (c - 2);
-      else if (c == 5) {
-        if (!p.d_opacity) continue;
-        dst = p.d_opacity + g;
-      } else if (c < kMom + NC) {
-        if (c - kMom >= p.N || !p.d_feats) continue;
-        dst = p.d_feats + (size_t)g * p.N + (c - kMom);
-      } else if (c < kMom + NC + 3) {
-        if (!p.d_colors) continue;
-        dst = p.d_colors + 3 * (size_t)g + (c - kMom - NC);
-      } else {
-        dst = p.d_depth + g;
+    // the block's sums of the batch: rows of warps that did not walk Gaussian j
+    // are stale and skipped; one global atomic per (Gaussian, output)
+    if (wid < kNW - 1) {
+      for (int e = threadIdx.x; e < n * NCH; e += kThreads - 32) {
+        const int j = e / NCH, c = e - j * NCH;
+        const uint32_t wm = B.wmask[j];
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kNW; ++w)
+          if ((wm >> w) & 1u) sum += red[((size_t)w * kBB + j) * SR + kMom + c];
+        if (sum == 0.f) continue;
+        const uint32_t g = B.gid[j];
+        float* dst;
+        if (c < NC) {
+          if (c >= p.N || !p.d_feats) continue;
+          dst = p.d_feats + (size_t)g * p.N + c;
+        } else if (c < NC + 3) {
+          if (!p.d_colors) continue;
+          dst = p.d_colors + 3 * (size_t)g + (c - NC);
+        } else {
+          dst = p.d_depth + g;
+        }
+        atomicAdd(dst, sum);
       }
-      atomicAdd(dst, v);
+    } else if (lane < n) {
+      // u, v, conic and opacity of Gaussian `lane` from each warp's moments:
+      // with (uu, vv) = u - block centre and dx = uu - x,
+      //   sum dx dp = uu M0 - Mx,  sum dx^2 dp = uu^2 M0 - 2 uu Mx + Mxx, ...
+      const int j = lane;
+      const uint32_t wm = B.wmask[j];
+      const float2 u = B.uv[j];
+      const float4 co = B.co[j];
+      float ox = 0.f, oy = 0.f, oxx = 0.f, oxy = 0.f, oyy = 0.f, m0 = 0.f;
+#pragma unroll
+      for (int w = 0; w < kNW; ++w) {
+        if (!((wm >> w) & 1u)) continue;
+        const float* M = red + ((size_t)w * kBB + j) * SR;
+        const float2 a = *reinterpret_cast<const float2*>(M);      // M0, Mx
+        const float2 bq = *reinterpret_cast<const float2*>(M + 2);  // My, Mxx
+        const float2 c = *reinterpret_cast<const float2*>(M + 4);   // Mxy, Myy
+        const float uu = u.x - (float)(tx * kTile + (w & 1) * 8 + 4);
+        const float vv = u.y - (float)(ty * kTile + (w >> 1) * 8 + 4);
+        ox += uu * a.x - a.y;
+        oy += vv * a.x - bq.x;
+        oxx += uu * (uu * a.x - 2.f * a.y) + bq.y;
+        oxy += uu * (vv * a.x - bq.x) - vv * a.y + c.x;
+        oyy += vv * (vv * a.x - 2.f * bq.x) + c.y;
+        m0 += a.x;
+      }
+      const uint32_t g = B.gid[j];
+      const float out[6] = {-(co.x * ox + co.y * oy), -(co.y * ox + co.z * oy), -0.5f * oxx, -oxy, -0.5f * oyy,
+                            m0 / co.w};
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (out[k] != 0.f) atomicAdd(p.d_uv + 2 * (size_t)g + k, out[k]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (out[2 + k] != 0.f) atomicAdd(p.d_conic + 3 * (size_t)g + k, out[2 + k]);
+      if (p.d_opacity && out[5] != 0.f) atomicAdd(p.d_opacity + g, out[5]);
     }
   }
 }
