@@ -717,7 +717,10 @@ __device__ __forceinline__ void finish_batch(BwdBatch& b, int i, int tx, int ty)
   b.wmask[i] = (uint8_t)warp_block_mask<mma_bwd::kNW, 8, true>(b.uv[i], b.co[i], tx, ty);
 }
 
-template <int NC>
+// L1: the cotangents are w sign(...) from the forward's sign words (p.l1); the
+// cotangent operand is then the exact signs (bf16 +-1, 0) and each sum is
+// scaled by its class weight at the end, so W . G takes two products.
+template <int NC, bool L1>
 __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const BwdParams p) {
   using namespace mma_bwd;
   using S = MmaBwdShape<NC>;
@@ -773,7 +776,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     if (inside) {
       T[q] = p.T_final[pix];
       last[q] = p.last_idx[pix];
-      if (p.l1.on) {
+      if constexpr (L1) {
         const uint2 sg = p.l1.signs[pix];
         gC0[q] = l1_cot(sg, kL1BitRgb, p.l1.w[0]);
         gC1[q] = l1_cot(sg, kL1BitRgb + 1, p.l1.w[0]);
@@ -795,36 +798,30 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   // B fragments of the cotangent matrix (k = this warp's 64 pixels, n = channels),
   // split into bf16 hi / lo, held for the whole tile. Row k = 16 s + 2 t + 8 hf + q
   // of step s is the pixel at column t + 4 hf, row s + 4 q of the warp block.
-  uint32_t bh[NT][4][2], bl[NT][4][2];
+  uint32_t bh[NT][4][2], bl[L1 ? 1 : NT][4][2];
   {
     const int bx = tx * kTile + (wid & 1) * 8, by = ty * kTile + (wid >> 1) * 8;
-    if (p.l1.on) {
-      // cotangents w sign(...) from the forward's sign bits. The bf16 hi / lo of
-      // -w are those of w with the sign flipped, so each n-tile's split is made
-      // once and a value costs a few bit operations; each of this lane's 16
-      // pixels is read once for all n-tiles.
+    if constexpr (L1) {
+      // the signs of w sign(...) from the forward's sign words as exact bf16
+      // (+1 = 0x3f80); each of this lane's 16 pixels is read once
       int bit[NT];
-      uint32_t hw[NT], lw[NT];
+      uint32_t on[NT];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const int c = 8 * nt + g8;
-        float w = 0.f;
         bit[nt] = 0;
+        on[nt] = 0u;
         if (c < NC) {
-          if (c < p.N) bit[nt] = c, w = p.l1.w[2];
+          if (c < p.N) bit[nt] = c, on[nt] = 0xffffu;
         } else if (c < NC + 3) {
-          bit[nt] = kL1BitRgb + (c - NC), w = p.l1.w[0];
+          bit[nt] = kL1BitRgb + (c - NC), on[nt] = 0xffffu;
         } else if (c == NC + 3) {
-          bit[nt] = kL1BitDepth, w = p.l1.w[1];
+          bit[nt] = kL1BitDepth, on[nt] = 0xffffu;
         }
-        const __nv_bfloat16 h = __float2bfloat16_rn(w);
-        hw[nt] = __bfloat16_as_ushort(h);
-        lw[nt] = __bfloat16_as_ushort(__float2bfloat16_rn(w - __bfloat162float(h)));
       }
-      // the bf16 bits of w sign(...) from a pixel's sign words
-      auto half = [](uint2 sg, int b, uint32_t v) -> uint32_t {
+      auto half = [](uint2 sg, int b, uint32_t en) -> uint32_t {
         const uint32_t nz = (sg.x >> b) & 1u, ng = (sg.y >> b) & 1u;
-        return (v ^ (ng << 15)) & (0u - nz) & 0xffffu;
+        return (0x3f80u ^ (ng << 15)) & (0u - nz) & en;
       };
 #pragma unroll
       for (int s = 0; s < 4; ++s)
@@ -838,10 +835,8 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
             sg[q] = (qx < p.cam.W && qy < p.cam.H) ? p.l1.signs[(size_t)qy * p.cam.W + qx] : make_uint2(0u, 0u);
           }
 #pragma unroll
-          for (int nt = 0; nt < NT; ++nt) {
-            bh[nt][s][hf] = half(sg[0], bit[nt], hw[nt]) | (half(sg[1], bit[nt], hw[nt]) << 16);
-            bl[nt][s][hf] = half(sg[0], bit[nt], lw[nt]) | (half(sg[1], bit[nt], lw[nt]) << 16);
-          }
+          for (int nt = 0; nt < NT; ++nt)
+            bh[nt][s][hf] = half(sg[0], bit[nt], on[nt]) | (half(sg[1], bit[nt], on[nt]) << 16);
         }
     } else {
 #pragma unroll
@@ -870,7 +865,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
               const int qy = by + s + 4 * q;
               v[q] = (plane && qx < p.cam.W && qy < p.cam.H) ? plane[((size_t)qy * p.cam.W + qx) * pstride] : 0.f;
             }
-            split_bf16x2(v[0], v[1], bh[nt][s][hf], bl[nt][s][hf]);
+            if constexpr (!L1) split_bf16x2(v[0], v[1], bh[nt][s][hf], bl[nt][s][hf]);
           }
       }
     }
@@ -990,7 +985,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
           mma_bf16_m16n8k16(dW[nt], al4, bh[nt][s][0], bh[nt][s][1]);
-          mma_bf16_m16n8k16(dW[nt], ah, bl[nt][s][0], bl[nt][s][1]);
+          if constexpr (!L1) mma_bf16_m16n8k16(dW[nt], ah, bl[L1 ? 0 : nt][s][0], bl[L1 ? 0 : nt][s][1]);
           mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
         }
       }
@@ -1041,16 +1036,20 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         if (sum == 0.f) continue;
         const uint32_t g = B.gid[j];
         float* dst;
+        float scale = 1.f;
         if (c < NC) {
           if (c >= p.N || !p.d_feats) continue;
           dst = p.d_feats + (size_t)g * p.N + c;
+          scale = p.l1.w[2];
         } else if (c < NC + 3) {
           if (!p.d_colors) continue;
           dst = p.d_colors + 3 * (size_t)g + (c - NC);
+          scale = p.l1.w[0];
         } else {
           dst = p.d_depth + g;
+          scale = p.l1.w[1];
         }
-        atomicAdd(dst, sum);
+        atomicAdd(dst, L1 ? sum * scale : sum);
       }
     } else if (lane < n) {
       // u, v, conic and opacity of Gaussian `lane` from each warp's moments:
@@ -1138,7 +1137,7 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
 
 // The tensor-core adjoint takes its tiles (48 KB) in dynamic shared memory; the
 // limit is raised once per device.
-template <int NC>
+template <int NC, bool L1>
 gs_status launch_bwd_mma(const BwdParams& p, unsigned tiles, cudaStream_t st) {
   constexpr size_t smem = MmaBwdShape<NC>::kSmem;
   static std::atomic<uint64_t> attr_done{0};
@@ -1146,12 +1145,12 @@ gs_status launch_bwd_mma(const BwdParams& p, unsigned tiles, cudaStream_t st) {
   if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
   const uint64_t bit = 1ull << (dev & 63);
   if (!(attr_done.load() & bit)) {
-    if (cudaFuncSetAttribute(k_render_bwd_mma<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(k_render_bwd_mma<NC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return GS_ERR_CUDA;
     attr_done.fetch_or(bit);
   }
-  k_render_bwd_mma<NC><<<tiles, mma_bwd::kThreads, smem, st>>>(p);
+  k_render_bwd_mma<NC, L1><<<tiles, mma_bwd::kThreads, smem, st>>>(p);
   return last_launch_status();
 }
 
@@ -1191,8 +1190,8 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32
   const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
   if (N <= 16 && !coupled) {
     GS_TRACE("k_render_bwd_mma", st);
-    if (N <= 0) return launch_bwd_mma<0>(p, tiles, st);
-    return launch_bwd_mma<16>(p, tiles, st);
+    if (p.l1.on) return N <= 0 ? launch_bwd_mma<0, true>(p, tiles, st) : launch_bwd_mma<16, true>(p, tiles, st);
+    return N <= 0 ? launch_bwd_mma<0, false>(p, tiles, st) : launch_bwd_mma<16, false>(p, tiles, st);
   }
   GS_TRACE("k_render_bwd", st);
   if (N <= 16) {

@@ -6,9 +6,11 @@ two-step path (gs_l1_loss_grad, then gs_render_bwd).
 The cotangent signs are decisions on the same binary32 images on both sides,
 so the oracle is given exactly the cotangents w sign(pred - target) of the
 GPU's forward images; gradients then meet the adjoint's bars (normwise 1e-4,
-cosine 0.99999). Against the two-step path, which forms the same cotangents,
-the gradients agree to the order of float atomics (normwise 1e-6) and the
-loss to 1e-5 (relative; fp32 sums in another order).
+cosine 0.99999). Against the two-step path, which forms the same cotangents
+as floats, the gradients agree to 1e-5 normwise: the fused adjoint multiplies
+exact +-1 signs on the tensor cores and applies w after the sum, the two-step
+one multiplies w split into bf16 hi + lo (about 2^-16 per term). The loss
+agrees to 1e-5 (relative; fp32 sums in another order).
 """
 import numpy as np
 import pytest
@@ -113,7 +115,7 @@ def test_fused_l1_matches_two_step_and_oracle(gs, ora, sg, case):
     for k in CLASSES:
         if k == "feats" and N == 0:
             continue
-        assert _normwise(got[k], ref[k]) <= 1e-6, k
+        assert _normwise(got[k], ref[k]) <= 1e-5, k
     # the oracle, given the same cotangents
     cot = []
     for k in ("rgb", "depth", "feat"):
@@ -148,7 +150,7 @@ def test_fused_l1_room_frame(gs, sg):
     assert int(srt["status"].item()) == 0
     assert abs(loss.item() - ref_loss.item()) <= 1e-5 * ref_loss.item()
     for k in CLASSES:
-        assert _normwise(got[k], ref[k]) <= 1e-6, k
+        assert _normwise(got[k], ref[k]) <= 1e-5, k
 
 
 def test_fused_l1_rejects_unsupported(gs, sg):
