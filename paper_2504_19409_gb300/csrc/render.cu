@@ -587,33 +587,27 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint with the per-tile pixel sums on tensor cores (decoupled features,
-// N <= 16; the coupled and wider forms use k_render_bwd above).
+// Adjoint with the colour, depth and feature sums on tensor cores (decoupled
+// features, N <= 16; the coupled and wider forms use k_render_bwd above).
 //
-// Every per-Gaussian output of a tile is a sum over the tile's pixels of a
-// per-pair weight times a per-pixel row:
-//   colour, depth, features:  sum_p w_p g_p[c]       (w = alpha T, g = cotangent)
-//   u, v, conic, opacity:     sums of dp_p times 1, x, y, x^2, xy, y^2
-//                             (dp = dL/dalpha alpha, x and y the pixel centre
-//                             relative to the warp block's centre), from which
-//                             sum dx dp, sum dx^2 dp, ... follow with dx = u - x
-//                             and the opacity term is sum dp / o.
-// The walk therefore only writes w and dp for each (Gaussian, pixel) into
-// shared memory; after every 16 Gaussians it walked (and at the end of each
-// batch) a warp contracts its 16 x 64 tiles (Gaussians x its pixels) with
-// mma.sync:
-//   W . G  with W and G split into bf16 hi + lo (hi.hi + hi.lo + lo.hi), ~2^-16;
-//   dP . M with dP split into tf32 hi + lo (~2^-22) and the monomials M exact in tf32.
-// That replaces, per Gaussian and warp, 20 multiply-adds per pixel and a
-// 32-channel shuffle transposition.
+// A Gaussian's colour, depth and feature gradients over a tile are
+// sum_p w_p g_p[c] (w = alpha T, g the pixel's cotangent): for a warp, a
+// [Gaussians x 64 pixels] . [64 pixels x channels] contraction. The walk
+// stores w per (Gaussian, pixel) in shared memory, and after every 16
+// Gaussians it walked a warp multiplies its 16 x 64 tile with mma.sync (bf16;
+// W split into hi + lo, G into hi + lo, or G = the exact signs +-1 with the
+// L1 weight applied after the sum). The u, v, conic and opacity gradients are
+// summed per pixel in fp32 (six values: dp, dx dp, dy dp, dx^2 dp, dx dy dp,
+// dy^2 dp with dp = dL/dalpha alpha) and reduced over the warp by an 8-value
+// shuffle transposition. This replaces, per Gaussian and warp, 20
+// multiply-adds per pixel and a 32-channel transposition.
 namespace mma_bwd {
-constexpr int kBB = 16;           // Gaussians per shared-memory batch (= the rows of one contraction)
+constexpr int kBB = 32;           // Gaussians per shared-memory batch
 constexpr int kRows = 16;         // Gaussians per warp contraction (MMA M)
 constexpr int kWStride = 72;      // bf16 per W row: 64 pixels + 8 (rows 144 B apart: conflict-free ldmatrix)
-constexpr int kPStride = 68;      // floats per dP row: 64 pixels + 4 (272 B)
 constexpr int kNW = 4;            // warps (8 x 8 pixel blocks) per tile
 constexpr int kThreads = 32 * kNW;
-constexpr int kMom = 6;           // moments of dp: 1, x, y, xx, xy, yy
+constexpr int kGeo = 6;           // geometric sums: dp, dx dp, dy dp, dx^2 dp, dx dy dp, dy^2 dp
 constexpr int kNBuf = 3;          // batch buffers: walked, being staged, still named by the last batch's sums
 }  // namespace mma_bwd
 
@@ -630,11 +624,10 @@ template <int NC>
 struct MmaBwdShape {
   static constexpr int NCH = NC + 4;          // contracted channels: features, r, g, b, depth
   static constexpr int NT = (NCH + 7) / 8;    // n-tiles of 8 channels
-  static constexpr int SR = mma_bwd::kMom + NCH;  // per-Gaussian sums: u, v, A, B, C, opacity, then NCH
+  static constexpr int SR = mma_bwd::kGeo + NCH;  // per (warp, Gaussian) sums: the six geometric, then NCH
   static constexpr size_t kWBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kWStride * 2;
-  static constexpr size_t kPBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kPStride * 4;
   static constexpr size_t kRedBytes = (size_t)2 * mma_bwd::kNW * mma_bwd::kBB * SR * 4;
-  static constexpr size_t kSmem = 2 * kWBytes + kPBytes + kRedBytes;
+  static constexpr size_t kSmem = 2 * kWBytes + kRedBytes;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -656,28 +649,9 @@ __device__ __forceinline__ void mma_bf16_m16n8k16(float (&d)[4], const uint32_t 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ void mma_tf32_m16n8k8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // L1 cotangent w sign(...) of bit b of a pixel's sign words (see L1Fwd).
 __device__ __forceinline__ float l1_cot(uint2 sg, int b, float w) {
   return ((sg.x >> b) & 1u) ? (((sg.y >> b) & 1u) ? -w : w) : 0.f;
-}
-
-// x rounded to tf32 (10 stored significand bits; the low 13 bits cleared),
-// to nearest with ties away from zero: half an ulp is added to the magnitude
-// bits before truncation (a carry into the exponent is the correct result).
-__device__ __forceinline__ uint32_t round_tf32(uint32_t bits) { return (bits + 0x1000u) & 0xffffe000u; }
-
-// x -> tf32 hi + lo with x = hi + lo + O(2^-22 x) (x - hi is exact in fp32).
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = round_tf32(__float_as_uint(x));
-  lo = round_tf32(__float_as_uint(x - __uint_as_float(hi)));
 }
 
 // (x0, x1) -> bf16x2 hi and lo parts (x0 in the low half): x = hi + lo + O(2^-16 x).
@@ -687,6 +661,25 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, u
   const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Lane l ends up with the warp-wide sum of v[l & 7]: three halving steps over
+// lane bits 2, 1, 0 (4 + 2 + 1 shuffles), then two butterfly steps over bits 3, 4.
+__device__ __forceinline__ float transpose_reduce8(float (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 4; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      const float send = upper ? v[k] : v[k + s];
+      const float keep = upper ? v[k + s] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 8);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
+  return v[0];
 }
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -728,9 +721,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __nv_bfloat16* s_wh = reinterpret_cast<__nv_bfloat16*>(smem_raw);                   // [kNW][kRows][kWStride]
   __nv_bfloat16* s_wl = reinterpret_cast<__nv_bfloat16*>(smem_raw + S::kWBytes);      // same
-  float* s_p = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes);                     // [kNW][kRows][kPStride]
-  float* s_red = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes + S::kPBytes);     // [2][kNW][kBB][SR]
-  __shared__ float2 s_mono[8][32];  // B fragments of the monomials: [8-pixel step][lane]
+  float* s_red = reinterpret_cast<float*>(smem_raw + 2 * S::kWBytes);                   // [2][kNW][kBB][SR]
   __shared__ BwdBatch s_b[kNBuf];
   __shared__ int s_maxlast;
 
@@ -744,19 +735,6 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   const size_t HW = (size_t)p.cam.W * p.cam.H;
 
   if (threadIdx.x == 0) s_maxlast = 0;
-  // monomial g of pixel k (k = 8 s + t and 8 s + t + 4 for lane (g, t)), pixel k of a
-  // warp being pixel (k & 1) of lane k >> 1: x = (lane_k & 7) - 3.5, y = (lane_k >> 3) + 4 (k & 1) - 3.5
-  for (int e = threadIdx.x; e < 8 * 32; e += kThreads) {
-    const int s = e >> 5, l = e & 31, g = l >> 2, t = l & 3;
-    float m[2];
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      const int k = 8 * s + t + 4 * hf, lk = k >> 1;
-      const float x = (float)(lk & 7) - 3.5f, y = (float)((lk >> 3) + 4 * (k & 1)) - 3.5f;
-      m[hf] = g == 0 ? 1.f : g == 1 ? x : g == 2 ? y : g == 3 ? x * x : g == 4 ? x * y : g == 5 ? y * y : 0.f;
-    }
-    s_mono[s][l] = make_float2(m[0], m[1]);
-  }
   __syncthreads();
   float T[2], pxc[2], pyc[2], gC0[2], gC1[2], gC2[2], gD[2], gAb[2];
   float Bc0[2], Bc1[2], Bc2[2], Bd[2], Sx[2];
@@ -796,8 +774,8 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     gAb[q] = gA - (p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q]);
   }
   // B fragments of the cotangent matrix (k = this warp's 64 pixels, n = channels),
-  // split into bf16 hi / lo, held for the whole tile. Row k = 16 s + 2 t + 8 hf + q
-  // of step s is the pixel at column t + 4 hf, row s + 4 q of the warp block.
+  // held for the whole tile. Row k = 16 s + 2 t + 8 hf + q of step s is the
+  // pixel at column t + 4 hf, row s + 4 q of the warp block.
   uint32_t bh[NT][4][2], bl[L1 ? 1 : NT][4][2];
   {
     const int bx = tx * kTile + (wid & 1) * 8, by = ty * kTile + (wid >> 1) * 8;
@@ -865,7 +843,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
               const int qy = by + s + 4 * q;
               v[q] = (plane && qx < p.cam.W && qy < p.cam.H) ? plane[((size_t)qy * p.cam.W + qx) * pstride] : 0.f;
             }
-            if constexpr (!L1) split_bf16x2(v[0], v[1], bh[nt][s][hf], bl[nt][s][hf]);
+            if constexpr (!L1) split_bf16x2(v[0], v[1], bh[nt][s][hf], bl[L1 ? 0 : nt][s][hf]);
           }
       }
     }
@@ -892,13 +870,11 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
 
   __nv_bfloat16* wh_w = s_wh + wid * kRows * kWStride;
   __nv_bfloat16* wl_w = s_wl + wid * kRows * kWStride;
-  float* p_w = s_p + wid * kRows * kPStride;
   // ldmatrix row addresses: lane i supplies row (i & 7) + 8 ((i >> 3) & 1) of
   // the 16-row tile, at column block (i >> 4)
   const int lrow = (lane & 7) + 8 * ((lane >> 3) & 1), lcol = lane >> 4;
   const uint32_t a_wh = smem_u32(wh_w + lrow * kWStride + 8 * lcol);
   const uint32_t a_wl = smem_u32(wl_w + lrow * kWStride + 8 * lcol);
-  const uint32_t a_p = smem_u32(p_w + lrow * kPStride + 4 * lcol);
 
   for (int b = 0; b < nb; ++b) {
     const BwdBatch& B = s_b[b % kNBuf];
@@ -908,73 +884,12 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     if (stage) stage_batch(p, s_b[(b + 1) % kNBuf], lane, g_next);
     if (wid == 0 && b + 2 < nb && lane < batch_hi(b + 2) - batch_lo(b + 2)) g_next = p.gids[batch_lo(b + 2) + lane];
 
-    // walk: this warp's Gaussians of the batch in reverse list order, two at a
-    // time. Both pairs' alphas are formed first (four independent chains); a
-    // pair that does not blend takes alpha = 0, for which every update below
-    // is an exact identity (T / 1, 0 c + 1 B, S 1) and w = dp = 0. Rows of the
-    // warp's tiles are filled in walk order; lane r remembers the batch index
-    // of the Gaussian in row r.
-    int rows = 0, row_j = 0;
-    uint32_t bits = __ballot_sync(0xffffffffu, lane < n && ((B.wmask[lane] >> wid) & 1u));
-    while (bits) {
-      const int j1 = 31 - __clz(bits);
-      bits &= ~(1u << j1);
-      const bool two = bits != 0;
-      const int j2 = two ? 31 - __clz(bits) : j1;
-      bits &= ~(1u << j2);
-      const int jg[2] = {j1, j2};
-      float al[2][2];
-      bool cl[2][2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const float2 uj = B.uv[jg[k]];
-        const float4 cj = B.co[jg[k]];
-        const int pos = lo + jg[k] - rg.x;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          PairAlpha pa;
-          const bool ok = (k == 0 || two) && pos < last[q] && pair_alpha(cj, uj.x - pxc[q], uj.y - pyc[q], pa);
-          al[k][q] = ok ? pa.alpha : 0.f;
-          cl[k][q] = ok && pa.clamped;
-        }
-      }
-      float wq[2][2], dpq[2][2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const float4 cd = B.cd[jg[k]];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const float a = al[k][q], om = 1.f - a;
-          T[q] = __fdividef(T[q], om);
-          wq[k][q] = a * T[q];
-          const float da = T[q] * ((cd.x - Bc0[q]) * gC0[q] + (cd.y - Bc1[q]) * gC1[q] + (cd.z - Bc2[q]) * gC2[q] +
-                                   (cd.w - Bd[q]) * gD[q]) +
-                           T[q] * Sx[q] * gAb[q];
-          Bc0[q] = a * cd.x + om * Bc0[q];
-          Bc1[q] = a * cd.y + om * Bc1[q];
-          Bc2[q] = a * cd.z + om * Bc2[q];
-          Bd[q] = a * cd.w + om * Bd[q];
-          Sx[q] *= om;
-          dpq[k][q] = cl[k][q] ? 0.f : da * a;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (k == 1 && !two) break;
-        uint32_t whi, wlo;
-        split_bf16x2(wq[k][0], wq[k][1], whi, wlo);
-        reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
-        reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = wlo;
-        reinterpret_cast<float2*>(p_w + rows * kPStride)[lane] = make_float2(dpq[k][0], dpq[k][1]);
-        if (lane == rows) row_j = jg[k];
-        ++rows;
-      }
-    }
-    if (rows > 0) {
-      // contraction of the filled rows (rows past `rows` hold stale values:
-      // their sums are not stored) into this warp's sums of the batch
+    // Contraction of the filled rows of the warp's W tile (rows past `rows`
+    // hold stale values: their sums are not stored) into this warp's sums.
+    int rows = 0, row_j = 0;  // lane r: batch index of the Gaussian in W row r
+    auto flush = [&]() {
       __syncwarp();
-      float dW[NT][4], dP[4] = {0.f, 0.f, 0.f, 0.f};
+      float dW[NT][4];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) dW[nt][0] = dW[nt][1] = dW[nt][2] = dW[nt][3] = 0.f;
 #pragma unroll
@@ -989,34 +904,106 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
           mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
         }
       }
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        uint32_t a[4], ahi[4], alo[4];
-        ldsm_x4(a, a_p + 32 * s);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) split_tf32(__uint_as_float(a[e]), ahi[e], alo[e]);
-        const float2 m = s_mono[s][lane];
-        mma_tf32_m16n8k8(dP, alo, __float_as_uint(m.x), __float_as_uint(m.y));
-        mma_tf32_m16n8k8(dP, ahi, __float_as_uint(m.x), __float_as_uint(m.y));
-      }
-      // D rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1: moments, then the W channels
+      // D rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1
       const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
       if (g8 < rows) {
-        float* r = red + ((size_t)wid * kBB + j0) * SR;
-        if (2 * t4 < kMom) *reinterpret_cast<float2*>(r + 2 * t4) = make_float2(dP[0], dP[1]);
+        float* r = red + ((size_t)wid * kBB + j0) * SR + kGeo;
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
-          if (8 * nt + 2 * t4 < NCH)
-            *reinterpret_cast<float2*>(r + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][0], dW[nt][1]);
+          if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r + 8 * nt + 2 * t4) = make_float2(dW[nt][0], dW[nt][1]);
       }
       if (g8 + 8 < rows) {
-        float* r = red + ((size_t)wid * kBB + j1) * SR;
-        if (2 * t4 < kMom) *reinterpret_cast<float2*>(r + 2 * t4) = make_float2(dP[2], dP[3]);
+        float* r = red + ((size_t)wid * kBB + j1) * SR + kGeo;
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
-          if (8 * nt + 2 * t4 < NCH)
-            *reinterpret_cast<float2*>(r + kMom + 8 * nt + 2 * t4) = make_float2(dW[nt][2], dW[nt][3]);
+          if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r + 8 * nt + 2 * t4) = make_float2(dW[nt][2], dW[nt][3]);
       }
+      __syncwarp();
+      rows = 0;
+    };
+
+    // walk: this warp's Gaussians of the batch in reverse list order, two at a
+    // time. Both pairs' alphas are formed first (four independent chains); a
+    // pair that does not blend takes alpha = 0, for which every update below
+    // is an exact identity (T / 1, 0 c + 1 B, S 1) and w = dp = 0.
+    const uint32_t walked = __ballot_sync(0xffffffffu, lane < n && ((B.wmask[lane] >> wid) & 1u));
+    uint32_t cut = 0;  // at most 16 rows per contraction: split below the 16th walked from the top
+    if (__popc(walked) > kRows) {
+      uint32_t t = walked;
+      for (int i = 0; i < kRows - 1; ++i) t &= ~(1u << (31 - __clz(t)));
+      cut = 31 - __clz(t);
+    }
+#pragma unroll 1
+    for (int chunk = 0; chunk < 2; ++chunk) {
+      uint32_t bits = chunk == 0 ? walked & ~((1u << cut) - 1u) : walked & ((1u << cut) - 1u);
+      if (bits == 0) break;
+      while (bits) {
+        const int j1 = 31 - __clz(bits);
+        bits &= ~(1u << j1);
+        const bool two = bits != 0;
+        const int j2 = two ? 31 - __clz(bits) : j1;
+        bits &= ~(1u << j2);
+        const int jg[2] = {j1, j2};
+        float al[2][2], dxq[2][2], dyq[2][2];
+        bool cl[2][2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const float2 uj = B.uv[jg[k]];
+          const float4 cj = B.co[jg[k]];
+          const int pos = lo + jg[k] - rg.x;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            PairAlpha pa;
+            dxq[k][q] = uj.x - pxc[q];
+            dyq[k][q] = uj.y - pyc[q];
+            const bool ok = (k == 0 || two) && pos < last[q] && pair_alpha(cj, dxq[k][q], dyq[k][q], pa);
+            al[k][q] = ok ? pa.alpha : 0.f;
+            cl[k][q] = ok && pa.clamped;
+          }
+        }
+        float wq[2][2], geo[2][8];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const float4 cd = B.cd[jg[k]];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) geo[k][e] = 0.f;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float a = al[k][q], om = 1.f - a;
+            T[q] = __fdividef(T[q], om);
+            wq[k][q] = a * T[q];
+            const float da = T[q] * ((cd.x - Bc0[q]) * gC0[q] + (cd.y - Bc1[q]) * gC1[q] + (cd.z - Bc2[q]) * gC2[q] +
+                                     (cd.w - Bd[q]) * gD[q]) +
+                             T[q] * Sx[q] * gAb[q];
+            Bc0[q] = a * cd.x + om * Bc0[q];
+            Bc1[q] = a * cd.y + om * Bc1[q];
+            Bc2[q] = a * cd.z + om * Bc2[q];
+            Bd[q] = a * cd.w + om * Bd[q];
+            Sx[q] *= om;
+            const float dp = cl[k][q] ? 0.f : da * a;
+            const float xdp = dxq[k][q] * dp, ydp = dyq[k][q] * dp;
+            geo[k][0] += dp;
+            geo[k][1] += xdp;
+            geo[k][2] += ydp;
+            geo[k][3] += dxq[k][q] * xdp;
+            geo[k][4] += dyq[k][q] * xdp;
+            geo[k][5] += dyq[k][q] * ydp;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (k == 1 && !two) break;
+          const float gsum = transpose_reduce8(geo[k]);
+          if (lane < kGeo) red[((size_t)wid * kBB + jg[k]) * SR + lane] = gsum;
+          uint32_t whi, wlo;
+          split_bf16x2(wq[k][0], wq[k][1], whi, wlo);
+          reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
+          reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = wlo;
+          if (lane == rows) row_j = jg[k];
+          ++rows;
+        }
+      }
+      flush();
     }
     if (stage) {
       cp_async_wait_all();
@@ -1032,7 +1019,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         float sum = 0.f;
 #pragma unroll
         for (int w = 0; w < kNW; ++w)
-          if ((wm >> w) & 1u) sum += red[((size_t)w * kBB + j) * SR + kMom + c];
+          if ((wm >> w) & 1u) sum += red[((size_t)w * kBB + j) * SR + kGeo + c];
         if (sum == 0.f) continue;
         const uint32_t g = B.gid[j];
         float* dst;
@@ -1052,33 +1039,27 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         atomicAdd(dst, L1 ? sum * scale : sum);
       }
     } else if (lane < n) {
-      // u, v, conic and opacity of Gaussian `lane` from each warp's moments:
-      // with (uu, vv) = u - block centre and dx = uu - x,
-      //   sum dx dp = uu M0 - Mx,  sum dx^2 dp = uu^2 M0 - 2 uu Mx + Mxx, ...
+      // u, v, conic and opacity of Gaussian `lane`: v_u = -sum (A dx + B dy) dp,
+      // v_v = -sum (B dx + C dy) dp, v_A = -sum dx^2 dp / 2, v_B = -sum dx dy dp,
+      // v_C = -sum dy^2 dp / 2 (dx = u - pixel centre), v_o = sum dp / o
       const int j = lane;
       const uint32_t wm = B.wmask[j];
-      const float2 u = B.uv[j];
-      const float4 co = B.co[j];
-      float ox = 0.f, oy = 0.f, oxx = 0.f, oxy = 0.f, oyy = 0.f, m0 = 0.f;
+      float sdp = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
 #pragma unroll
       for (int w = 0; w < kNW; ++w) {
         if (!((wm >> w) & 1u)) continue;
         const float* M = red + ((size_t)w * kBB + j) * SR;
-        const float2 a = *reinterpret_cast<const float2*>(M);      // M0, Mx
-        const float2 bq = *reinterpret_cast<const float2*>(M + 2);  // My, Mxx
-        const float2 c = *reinterpret_cast<const float2*>(M + 4);   // Mxy, Myy
-        const float uu = u.x - (float)(tx * kTile + (w & 1) * 8 + 4);
-        const float vv = u.y - (float)(ty * kTile + (w >> 1) * 8 + 4);
-        ox += uu * a.x - a.y;
-        oy += vv * a.x - bq.x;
-        oxx += uu * (uu * a.x - 2.f * a.y) + bq.y;
-        oxy += uu * (vv * a.x - bq.x) - vv * a.y + c.x;
-        oyy += vv * (vv * a.x - 2.f * bq.x) + c.y;
-        m0 += a.x;
+        sdp += M[0];
+        sx += M[1];
+        sy += M[2];
+        sxx += M[3];
+        sxy += M[4];
+        syy += M[5];
       }
+      const float4 co = B.co[j];
       const uint32_t g = B.gid[j];
-      const float out[6] = {-(co.x * ox + co.y * oy), -(co.y * ox + co.z * oy), -0.5f * oxx, -oxy, -0.5f * oyy,
-                            m0 / co.w};
+      const float out[6] = {-(co.x * sx + co.y * sy), -(co.y * sx + co.z * sy), -0.5f * sxx, -sxy, -0.5f * syy,
+                            sdp / co.w};
 #pragma unroll
       for (int k = 0; k < 2; ++k)
         if (out[k] != 0.f) atomicAdd(p.d_uv + 2 * (size_t)g + k, out[k]);
