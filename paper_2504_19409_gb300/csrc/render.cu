@@ -624,7 +624,8 @@ template <int NC>
 struct MmaBwdShape {
   static constexpr int NCH = NC + 4;          // contracted channels: features, r, g, b, depth
   static constexpr int NT = (NCH + 7) / 8;    // n-tiles of 8 channels
-  static constexpr int SR = mma_bwd::kGeo + NCH;  // per (warp, Gaussian) sums: the six geometric, then NCH
+  static constexpr int NG = NC / 4 + 1;       // output groups: features by 4, then r, g, b, depth
+  static constexpr int SR = NCH + mma_bwd::kGeo + 2;  // per (warp, Gaussian) sums: NCH channels, the six geometric, pad
   static constexpr size_t kWBytes = (size_t)mma_bwd::kNW * mma_bwd::kRows * mma_bwd::kWStride * 2;
   static constexpr size_t kRedBytes = (size_t)2 * mma_bwd::kNW * mma_bwd::kBB * SR * 4;
   static constexpr size_t kSmem = 2 * kWBytes + kRedBytes;
@@ -717,7 +718,8 @@ template <int NC, bool L1>
 __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const BwdParams p) {
   using namespace mma_bwd;
   using S = MmaBwdShape<NC>;
-  constexpr int NT = S::NT, SR = S::SR, NCH = S::NCH;
+  constexpr int NT = S::NT, SR = S::SR, NCH = S::NCH, NG = S::NG;
+  static_assert(NC % 4 == 0 && SR % 4 == 0, "16-byte groups of per-warp sums");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __nv_bfloat16* s_wh = reinterpret_cast<__nv_bfloat16*>(smem_raw);                   // [kNW][kRows][kWStride]
   __nv_bfloat16* s_wl = reinterpret_cast<__nv_bfloat16*>(smem_raw + S::kWBytes);      // same
@@ -907,13 +909,13 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       // D rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1
       const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
       if (g8 < rows) {
-        float* r = red + ((size_t)wid * kBB + j0) * SR + kGeo;
+        float* r = red + ((size_t)wid * kBB + j0) * SR;
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
           if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r + 8 * nt + 2 * t4) = make_float2(dW[nt][0], dW[nt][1]);
       }
       if (g8 + 8 < rows) {
-        float* r = red + ((size_t)wid * kBB + j1) * SR + kGeo;
+        float* r = red + ((size_t)wid * kBB + j1) * SR;
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
           if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r + 8 * nt + 2 * t4) = make_float2(dW[nt][2], dW[nt][3]);
@@ -994,7 +996,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         for (int k = 0; k < 2; ++k) {
           if (k == 1 && !two) break;
           const float gsum = transpose_reduce8(geo[k]);
-          if (lane < kGeo) red[((size_t)wid * kBB + jg[k]) * SR + lane] = gsum;
+          if (lane < kGeo) red[((size_t)wid * kBB + jg[k]) * SR + NCH + lane] = gsum;
           uint32_t whi, wlo;
           split_bf16x2(wq[k][0], wq[k][1], whi, wlo);
           reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
@@ -1013,30 +1015,45 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     // the block's sums of the batch: rows of warps that did not walk Gaussian j
     // are stale and skipped; one global atomic per (Gaussian, output)
     if (wid < kNW - 1) {
-      for (int e = threadIdx.x; e < n * NCH; e += kThreads - 32) {
-        const int j = e / NCH, c = e - j * NCH;
+      // groups of 4 outputs: 16-byte loads of the warps' sums and, for the
+      // features, one vector atomic per group
+      const bool vec = NC > 0 && p.d_feats && (p.N & 3) == 0 && ((uintptr_t)p.d_feats & 15u) == 0;
+      for (int e = threadIdx.x; e < n * NG; e += kThreads - 32) {
+        const int j = e / NG, gq = e - j * NG;
         const uint32_t wm = B.wmask[j];
-        float sum = 0.f;
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < kNW; ++w)
-          if ((wm >> w) & 1u) sum += red[((size_t)w * kBB + j) * SR + kGeo + c];
-        if (sum == 0.f) continue;
+          if ((wm >> w) & 1u) {
+            const float4 v = *reinterpret_cast<const float4*>(red + ((size_t)w * kBB + j) * SR + 4 * gq);
+            sum.x += v.x;
+            sum.y += v.y;
+            sum.z += v.z;
+            sum.w += v.w;
+          }
         const uint32_t g = B.gid[j];
-        float* dst;
-        float scale = 1.f;
-        if (c < NC) {
-          if (c >= p.N || !p.d_feats) continue;
-          dst = p.d_feats + (size_t)g * p.N + c;
-          scale = p.l1.w[2];
-        } else if (c < NC + 3) {
-          if (!p.d_colors) continue;
-          dst = p.d_colors + 3 * (size_t)g + (c - NC);
-          scale = p.l1.w[0];
+        if (gq < NC / 4) {
+          if (!p.d_feats) continue;
+          if (L1) sum = make_float4(sum.x * p.l1.w[2], sum.y * p.l1.w[2], sum.z * p.l1.w[2], sum.w * p.l1.w[2]);
+          const int c = 4 * gq;
+          if (vec && c + 4 <= p.N) {
+            if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
+              atomicAdd(reinterpret_cast<float4*>(p.d_feats + (size_t)g * p.N + c), sum);
+          } else {
+            const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (c + k < p.N && sv[k] != 0.f) atomicAdd(p.d_feats + (size_t)g * p.N + c + k, sv[k]);
+          }
         } else {
-          dst = p.d_depth + g;
-          scale = p.l1.w[1];
+          const float wc = L1 ? p.l1.w[0] : 1.f, wd = L1 ? p.l1.w[1] : 1.f;
+          if (p.d_colors) {
+            if (sum.x != 0.f) atomicAdd(p.d_colors + 3 * (size_t)g, sum.x * wc);
+            if (sum.y != 0.f) atomicAdd(p.d_colors + 3 * (size_t)g + 1, sum.y * wc);
+            if (sum.z != 0.f) atomicAdd(p.d_colors + 3 * (size_t)g + 2, sum.z * wc);
+          }
+          if (sum.w != 0.f) atomicAdd(p.d_depth + g, sum.w * wd);
         }
-        atomicAdd(dst, L1 ? sum * scale : sum);
       }
     } else if (lane < n) {
       // u, v, conic and opacity of Gaussian `lane`: v_u = -sum (A dx + B dy) dp,
@@ -1048,7 +1065,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
 #pragma unroll
       for (int w = 0; w < kNW; ++w) {
         if (!((wm >> w) & 1u)) continue;
-        const float* M = red + ((size_t)w * kBB + j) * SR;
+        const float* M = red + ((size_t)w * kBB + j) * SR + NCH;
         sdp += M[0];
         sx += M[1];
         sy += M[2];
