@@ -279,15 +279,24 @@ def run_ours(args, rank, world, local_rank):
         t.numel() * t.element_size() for t in host_tgt[e2e_frames[0]].values())
     d2h = 6 * 4 + 4
 
+    side = torch.cuda.Stream(device=dev)
+    tgt_ready = torch.cuda.Event()
+
     def e2e_step(k):
+        # the frame's targets are copied on a side stream, overlapped with the
+        # parameter copy, projection and binning; compositing waits for them
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for n in ("rgb", "depth", "feat"):
+                d_tgt[n].copy_(host_tgt[k][n], non_blocking=True)
+            tgt_ready.record(side)
         for d, h in zip(d_params, host_params):
             d.copy_(h, non_blocking=True)
-        for n in ("rgb", "depth", "feat"):
-            d_tgt[n].copy_(host_tgt[k][n], non_blocking=True)
         cam = frame_camera(k)
         m, s_, q, o, c, f = d_params
         loss.zero_()
-        ras.forward(cam, m, s_, q, o, c, f, l1_targets=d_tgt, l1_weights=scales_l1, l1_loss=loss)
+        ras.forward(cam, m, s_, q, o, c, f, l1_targets=d_tgt, l1_weights=scales_l1, l1_loss=loss,
+                    wait_event=tgt_ready)
         gr = ras.backward_l1(cam, m, s_, q, c, f, scales_l1)
         out_pose.copy_(gr["pose"], non_blocking=True)
         out_loss.copy_(loss, non_blocking=True)

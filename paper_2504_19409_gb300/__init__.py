@@ -581,11 +581,18 @@ class Rasterizer:
         return need
 
     def forward(self, cam, means, scales, quats, opacity, colors, feats=None, bg=None, stream=None, visible=None,
-                l1_targets=None, l1_weights=None, l1_loss=None):
-        """Project, bin and composite; with l1_targets also the L1 loss of the images (see render_fwd)."""
+                l1_targets=None, l1_weights=None, l1_loss=None, wait_event=None):
+        """Project, bin and composite; with l1_targets also the L1 loss of the images (see render_fwd).
+        wait_event (a torch.cuda.Event or a list of them, e.g. recorded after copying the colours and
+        targets on other streams) is waited for only before compositing, so projection and binning
+        overlap with it."""
         project(cam, means, scales, quats, opacity, out=self.proj, stream=stream)
         bin_sort(cam, self.proj, self.capacity, workspace=self.sort_ws, out=self.sort, status=self.status,
                  stream=stream)
+        if wait_event is not None:
+            st = stream if stream is not None else torch.cuda.current_stream(self.device)
+            for ev in (wait_event if isinstance(wait_event, (list, tuple)) else (wait_event,)):
+                st.wait_event(ev)
         render_fwd(cam, self.proj, self.sort, colors, feats, flags=self.flags, layout=self.layout, bg=bg,
                    out=self.fwd, status=self.status, stream=stream, visible=visible, l1_targets=l1_targets,
                    l1_weights=l1_weights, l1_loss=l1_loss)
