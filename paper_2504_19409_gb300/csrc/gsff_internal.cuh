@@ -68,24 +68,43 @@ __device__ __forceinline__ void flag_status(int32_t* status, gs_status s) {
   if (status) atomicOr(status, 1 << (int)s);
 }
 
-// alpha of one (pixel, Gaussian) pair. The sequence is fixed (explicit
-// roundings, explicit fused multiply-adds) so the forward and the backward
-// kernels take identical skip decisions.
+// alpha of one (pixel, Gaussian) pair, o exp(-(A dx^2 + 2 B dx dy + C dy^2) / 2)
+// clamped to 0.99. It is evaluated in base 2 from the conic scaled by log2(e)
+// (conic_q, which a kernel may compute once per Gaussian): the exponent
+// dx (qA dx + qB dy) + qC dy^2 takes five multiplies / fused multiply-adds and
+// one ex2. The sequence is fixed (explicit roundings and fused multiply-adds),
+// and pair_alpha computes conic_q itself with the same operations, so every
+// kernel takes identical skip decisions and alphas.
 struct PairAlpha {
-  float power, G, alpha;
+  float G, alpha;  // G = exp(power)
   bool clamped;
 };
 
-__device__ __forceinline__ bool pair_alpha(float4 co, float dx, float dy, PairAlpha& r) {
-  const float hx = __fmul_rn(dx, dx), hy = __fmul_rn(dy, dy), hxy = __fmul_rn(dx, dy);
-  const float s = __fmaf_rn(co.x, hx, __fmul_rn(co.z, hy));
-  r.power = __fmaf_rn(-0.5f, s, -__fmul_rn(co.y, hxy));
-  if (r.power > 0.f) return false;
-  r.G = __expf(r.power);
-  const float a = __fmul_rn(co.w, r.G);
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float4 conic_q(float4 co) {
+  return make_float4(__fmul_rn(-0.5f * kLog2e, co.x), __fmul_rn(-kLog2e, co.y), __fmul_rn(-0.5f * kLog2e, co.z), co.w);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ bool pair_alpha_q(float4 q, float dx, float dy, PairAlpha& r) {
+  const float u = __fmaf_rn(q.y, dy, __fmul_rn(q.x, dx));
+  const float p2 = __fmaf_rn(dx, u, __fmul_rn(__fmul_rn(q.z, dy), dy));
+  if (p2 > 0.f) return false;
+  r.G = ex2_approx(p2);
+  const float a = __fmul_rn(q.w, r.G);
   r.clamped = a > kAlphaMax;
   r.alpha = r.clamped ? kAlphaMax : a;
   return r.alpha >= kAlphaMin;
+}
+
+__device__ __forceinline__ bool pair_alpha(float4 co, float dx, float dy, PairAlpha& r) {
+  return pair_alpha_q(conic_q(co), dx, dy, r);
 }
 
 // L1 image loss fused into compositing (class 0 rgb, 1 depth, 2 features).

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
       const float4 co = p.co[g];
       const float2 u = p.uv[g];
       s_uv[threadIdx.x] = u;
-      s_co[threadIdx.x] = co;
+      s_co[threadIdx.x] = conic_q(co);  // the walk's alphas take the base-2 form
       // the skip tests of all 8 warp blocks (2 columns x 4 rows of 8x4 pixels)
       s_wmask[threadIdx.x] = (uint8_t)warp_block_mask<8, 4, false>(u, co, tx, ty);
       if (VIS) s_gid[threadIdx.x] = g;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
         if (done) continue;
         const float2 uj = s_uv[j];
         PairAlpha pa;
-        if (!pair_alpha(s_co[j], uj.x - pxc, uj.y - pyc, pa)) continue;
+        if (!pair_alpha_q(s_co[j], uj.x - pxc, uj.y - pyc, pa)) continue;
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, pa.alpha));
         if (Tn < kTStop) {
           done = true;
@@ -614,6 +614,7 @@ constexpr int kNBuf = 3;          // batch buffers: walked, being staged, still 
 // One batch of a tile's list in shared memory.
 struct BwdBatch {
   float4 co[mma_bwd::kBB];  // conic A, B, C and opacity
+  float4 q[mma_bwd::kBB];   // the same in base-2 form (conic_q)
   float4 cd[mma_bwd::kBB];  // colour r, g, b and depth
   float2 uv[mma_bwd::kBB];
   uint32_t gid[mma_bwd::kBB];
@@ -709,6 +710,7 @@ __device__ __forceinline__ void stage_batch(const BwdParams& p, BwdBatch& b, int
 // After the slot's copies landed: the warp skip tests of its Gaussian.
 __device__ __forceinline__ void finish_batch(BwdBatch& b, int i, int tx, int ty) {
   b.wmask[i] = (uint8_t)warp_block_mask<mma_bwd::kNW, 8, true>(b.uv[i], b.co[i], tx, ty);
+  b.q[i] = conic_q(b.co[i]);
 }
 
 // L1: the cotangents are w sign(...) from the forward's sign words (p.l1); the
@@ -951,14 +953,14 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const float2 uj = B.uv[jg[k]];
-          const float4 cj = B.co[jg[k]];
+          const float4 cj = B.q[jg[k]];
           const int pos = lo + jg[k] - rg.x;
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             PairAlpha pa;
             dxq[k][q] = uj.x - pxc[q];
             dyq[k][q] = uj.y - pyc[q];
-            const bool ok = (k == 0 || two) && pos < last[q] && pair_alpha(cj, dxq[k][q], dyq[k][q], pa);
+            const bool ok = (k == 0 || two) && pos < last[q] && pair_alpha_q(cj, dxq[k][q], dyq[k][q], pa);
             al[k][q] = ok ? pa.alpha : 0.f;
             cl[k][q] = ok && pa.clamped;
           }
