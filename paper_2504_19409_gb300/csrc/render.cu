@@ -740,8 +740,12 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
 
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
-  float T[2], pxc[2], pyc[2], gC0[2], gC1[2], gC2[2], gD[2], gAb[2];
-  float Bc0[2], Bc1[2], Bc2[2], Bd[2], Sx[2];
+  // Per pixel: T recovered backwards, the colour / depth cotangent g and
+  // J = sum_c B_c g_c - S gAb, where B_c are the suffix sums of the channels
+  // behind the current Gaussian, S the transmittance product behind it and
+  // gAb = dL/dA - bg . g. Then dL/dalpha_i = T_i (c_i . g - J) and
+  // J <- alpha c_i . g + (1 - alpha) J (both B_c and S follow that recurrence).
+  float T[2], pxc[2], pyc[2], gC0[2], gC1[2], gC2[2], gD[2], J[2];
   int last[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
@@ -753,8 +757,6 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     last[q] = 0;
     gC0[q] = gC1[q] = gC2[q] = gD[q] = 0.f;
     float gA = 0.f;
-    Bc0[q] = Bc1[q] = Bc2[q] = Bd[q] = 0.f;
-    Sx[q] = 1.f;
     if (inside) {
       T[q] = p.T_final[pix];
       last[q] = p.last_idx[pix];
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       }
       if (last[q] > 0) atomicMax(&s_maxlast, last[q]);
     }
-    gAb[q] = gA - (p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q]);
+    J[q] = -(gA - (p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q]));  // B_c = 0, S = 1
   }
   // B fragments of the cotangent matrix (k = this warp's 64 pixels, n = channels),
   // held for the whole tile. Row k = 16 s + 2 t + 8 hf + q of step s is the
@@ -929,7 +931,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     // walk: this warp's Gaussians of the batch in reverse list order, two at a
     // time. Both pairs' alphas are formed first (four independent chains); a
     // pair that does not blend takes alpha = 0, for which every update below
-    // is an exact identity (T / 1, 0 c + 1 B, S 1) and w = dp = 0.
+    // is an exact identity (T / 1, 0 cg + 1 J) and w = dp = 0.
     const uint32_t walked = __ballot_sync(0xffffffffu, lane < n && ((B.wmask[lane] >> wid) & 1u));
     uint32_t cut = 0;  // at most 16 rows per contraction: split below the 16th walked from the top
     if (__popc(walked) > kRows) {
@@ -976,14 +978,9 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
             const float a = al[k][q], om = 1.f - a;
             T[q] = __fdividef(T[q], om);
             wq[k][q] = a * T[q];
-            const float da = T[q] * ((cd.x - Bc0[q]) * gC0[q] + (cd.y - Bc1[q]) * gC1[q] + (cd.z - Bc2[q]) * gC2[q] +
-                                     (cd.w - Bd[q]) * gD[q]) +
-                             T[q] * Sx[q] * gAb[q];
-            Bc0[q] = a * cd.x + om * Bc0[q];
-            Bc1[q] = a * cd.y + om * Bc1[q];
-            Bc2[q] = a * cd.z + om * Bc2[q];
-            Bd[q] = a * cd.w + om * Bd[q];
-            Sx[q] *= om;
+            const float cg = cd.x * gC0[q] + cd.y * gC1[q] + cd.z * gC2[q] + cd.w * gD[q];
+            const float da = T[q] * (cg - J[q]);
+            J[q] = a * cg + om * J[q];
             const float dp = cl[k][q] ? 0.f : da * a;
             const float xdp = dxq[k][q] * dp, ydp = dyq[k][q] * dp;
             geo[k][0] += dp;
