@@ -36,6 +36,7 @@ namespace gsff {
 namespace {
 
 constexpr int kScanChunk = 256;   // Gaussians per chunk of the touched-count scan / emission
+constexpr int kEmitThreads = 1024;  // threads sharing a chunk's instances in k_emit
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 8;       // keys per thread
 constexpr int kRsChunk = kRsThreads * kRsItems;  // 2048 keys per block
@@ -208,12 +209,14 @@ __global__ void __launch_bounds__(1024) k_scan_top(int nchunks, long long* __res
   }
 }
 
-// Each block: 256 consecutive depth-ordered Gaussians (one per thread). The
-// block's instances [0, total) are spread evenly over its threads; instance
+// Each block: 256 consecutive depth-ordered Gaussians (one per thread of the
+// first eight warps). The block's instances [0, total) are spread evenly over
+// all 1024 of its threads (culled Gaussians sort last, so only a few chunks
+// hold instances and each needs many threads); instance
 // i belongs to the Gaussian k with off[k] <= i < off[k+1] (binary search in
 // shared memory) and is tile (i - off[k]) of its rectangle, row-major.
 // Writes are contiguous.
-__global__ void __launch_bounds__(256) k_emit(int P, const uint32_t* __restrict__ order,
+__global__ void __launch_bounds__(kEmitThreads) k_emit(int P, const uint32_t* __restrict__ order,
                                               const int* __restrict__ touched, const int4* __restrict__ rect,
                                               const long long* __restrict__ partial, int tiles_x, long long capacity,
                                               int npass, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals,
@@ -226,16 +229,18 @@ __global__ void __launch_bounds__(256) k_emit(int P, const uint32_t* __restrict_
   const int r = blockIdx.x * kScanChunk + threadIdx.x;
   uint32_t g = 0;
   int n = 0;
-  if (r < P) {
+  if (threadIdx.x < kScanChunk && r < P) {
     g = order[r];
     n = touched[g];
   }
   for (int i = threadIdx.x; i < kMaxTilePasses * kRadix; i += blockDim.x) (&s_th[0][0])[i] = 0;
-  s_g[threadIdx.x] = g;
-  if (n > 0) s_rc[threadIdx.x] = rect[g];
+  if (threadIdx.x < kScanChunk) {
+    s_g[threadIdx.x] = g;
+    if (n > 0) s_rc[threadIdx.x] = rect[g];
+  }
   int total;
-  const int ex = block_exclusive_scan(n, s_warp, total);
-  s_off[threadIdx.x] = ex;
+  const int ex = block_exclusive_scan(n, s_warp, total);  // threads past the chunk add 0
+  if (threadIdx.x < kScanChunk) s_off[threadIdx.x] = ex;
   if (threadIdx.x == 0) s_off[kScanChunk] = total;
   __syncthreads();
   const long long base = partial[blockIdx.x];
@@ -258,10 +263,11 @@ __global__ void __launch_bounds__(256) k_emit(int P, const uint32_t* __restrict_
     }
   }
   __syncthreads();
-  for (int p = 0; p < npass; ++p) {
-    const uint32_t v = s_th[p][threadIdx.x];
-    if (v) atomicAdd(&os->hist[kDepthPasses + p][threadIdx.x], v);
-  }
+  if (threadIdx.x < kRadix)
+    for (int p = 0; p < npass; ++p) {
+      const uint32_t v = s_th[p][threadIdx.x];
+      if (v) atomicAdd(&os->hist[kDepthPasses + p][threadIdx.x], v);
+    }
 }
 
 // ---- one LSD radix pass over (u32 key, u32 value) ------------------------------
@@ -514,7 +520,7 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   }
   {
     GS_TRACE("k_emit", st);
-    k_emit<<<L.nscan, 256, 0, st>>>(P, dv, touched, reinterpret_cast<const int4*>(rect), partial, cam.tiles_x,
+    k_emit<<<L.nscan, kEmitThreads, 0, st>>>(P, dv, touched, reinterpret_cast<const int4*>(rect), partial, cam.tiles_x,
                                     capacity, npass, kb[0], vb[0], os);
   }
   unsigned long long* lb_t = lb + kDepthPasses * lb_pass_p;
