@@ -37,6 +37,7 @@ namespace {
 
 constexpr int kScanChunk = 256;   // Gaussians per chunk of the touched-count scan / emission
 constexpr int kEmitThreads = 1024;  // threads sharing a chunk's instances in k_emit
+constexpr int kDkThreads = 1024;    // threads of k_depth_keys (kRsChunk keys per block)
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 8;       // keys per thread
 constexpr int kRsChunk = kRsThreads * kRsItems;  // 2048 keys per block
@@ -113,7 +114,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& tot
 // One block per kRsChunk Gaussians. Culled Gaussians get the largest key. The
 // block also adds its digit counts for the four depth passes to the frame's
 // histograms (culled keys are 0xFFFFFFFF: digit 255 in every pass).
-__global__ void __launch_bounds__(kRsThreads) k_depth_keys(int P, const float* __restrict__ depth,
+__global__ void __launch_bounds__(kDkThreads) k_depth_keys(int P, const float* __restrict__ depth,
                                                            const int* __restrict__ touched, uint32_t* __restrict__ dk,
                                                            uint32_t* __restrict__ dv, SortCtrl* __restrict__ ctrl,
                                                            OsCtrl* __restrict__ os) {
@@ -126,8 +127,8 @@ __global__ void __launch_bounds__(kRsThreads) k_depth_keys(int P, const float* _
   const int base = blockIdx.x * kRsChunk;
   uint32_t ncull = 0;
 #pragma unroll
-  for (int r = 0; r < kRsItems; ++r) {
-    const int g = base + r * kRsThreads + threadIdx.x;
+  for (int r = 0; r < kRsChunk / kDkThreads; ++r) {
+    const int g = base + r * kDkThreads + threadIdx.x;
     bool culled = false;
     if (g < P) {
       const bool vis = touched[g] > 0;
@@ -145,10 +146,12 @@ __global__ void __launch_bounds__(kRsThreads) k_depth_keys(int P, const float* _
   if ((threadIdx.x & 31) == 0 && ncull) atomicAdd(&s_cull, ncull);
   __syncthreads();
   const int d = threadIdx.x;
+  if (d < kRadix) {
 #pragma unroll
-  for (int p = 0; p < kDepthPasses; ++p) {
-    const uint32_t v = s_h[p][d] + (d == kRadix - 1 ? s_cull : 0u);
-    if (v) atomicAdd(&os->hist[p][d], v);
+    for (int p = 0; p < kDepthPasses; ++p) {
+      const uint32_t v = s_h[p][d] + (d == kRadix - 1 ? s_cull : 0u);
+      if (v) atomicAdd(&os->hist[p][d], v);
+    }
   }
 }
 
@@ -493,7 +496,7 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   if (cudaMemsetAsync(os, 0, (L.lb - L.os) + L.lb_bytes, st) != cudaSuccess) return GS_ERR_CUDA;
   {
     GS_TRACE("k_depth_keys", st);
-    k_depth_keys<<<L.nblk_p, kRsThreads, 0, st>>>(P, depth, touched, dk, dv, ctrl, os);
+    k_depth_keys<<<L.nblk_p, kDkThreads, 0, st>>>(P, depth, touched, dk, dv, ctrl, os);
   }
   // 1. depth sort: 4 passes, ending in (dk, dv)
   os_pass(dk, dv, dk2, dv2, n_gauss, 0, 0, L.nblk_p, os, lb, status, st);
