@@ -75,12 +75,14 @@ def _normwise(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("case", ["chw_bg", "hwc", "features_off", "rgb_only"])
+@pytest.mark.parametrize("case", ["chw_bg", "hwc", "features_off", "rgb_only", "n5_chw", "n8_hwc"])
 def test_fused_l1_matches_two_step_and_oracle(gs, ora, sg, case):
-    N = 0 if case == "features_off" else 16
+    """N = 16, 0, 5 (scalar feature-gradient path, rows not 16-byte aligned)
+    and 8 (HWC; vector path for the first two channel groups)."""
+    N = {"features_off": 0, "n5_chw": 5, "n8_hwc": 8}.get(case, 16)
     sc, cam = sg.small_case(seed=4, N=N)
     cam = cam.as_f32()
-    layout = gs.GS_LAYOUT_HWC if case == "hwc" else gs.GS_LAYOUT_CHW
+    layout = gs.GS_LAYOUT_HWC if case in ("hwc", "n8_hwc") else gs.GS_LAYOUT_CHW
     bg = (0.1, 0.3, 0.2) if case == "chw_bg" else None
     args, proj, srt, fw = _setup(gs, cam, sc, layout, bg)
     rng = np.random.default_rng(40 + len(case))
