@@ -228,6 +228,21 @@ def test_hwc_layout_and_bf16_features(gs, ora, sg):
     check_grads(g["grads"], o["grads"], ("means", "opacity", "feats", "pose"))
 
 
+@pytest.mark.parametrize("N,layout,bf16", [(5, 0, False), (12, 1, True)])
+def test_partial_feature_counts(gs, ora, sg, N, layout, bf16):
+    """Fewer than 16 channels on the N <= 16 kernels: 5 (rows not 16-byte
+    aligned, scalar feature-gradient adds) and 12 in HWC layout from bf16
+    features."""
+    sc, cam = sg.small_case(seed=6, N=N)
+    cam = cam.as_f32()
+    feats = torch.from_numpy(sc.feats).to(torch.bfloat16).float().numpy().astype(np.float64) if bf16 else None
+    cot = tuple(x.astype(np.float32) for x in sg.random_linear_functional(60 + N, cam.height, cam.width, N))
+    g = gpu_frame(gs, cam, sc, layout=layout, feat_bf16=bf16, grads=cot)
+    o = oracle_frame(ora, cam, sc, feats=feats, grads=tuple(x.astype(np.float64) for x in cot))
+    check_images(g, o, N, layout=layout, feats=sc.feats)
+    check_grads(g["grads"], o["grads"], ("means", "scales", "quats", "opacity", "colors", "feats", "pose"))
+
+
 # ---- edge cases -----------------------------------------------------------------------
 
 def test_ragged_image_and_features_off(gs, ora, sg):
