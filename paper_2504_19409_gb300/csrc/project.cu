@@ -157,14 +157,40 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 //   u = fx x/z + cx, depth = z, mu_c = W mu + t
 //   pose (left perturbation, Eq. 4): drho = dmu_c,
 //   dtheta = mu_c x dmu_c + sum_k W_k x dW_k.
+// Only the Gaussians that received an image gradient (a small share of a
+// frame's) have work: each block first queues those among its kPbPer * 256
+// Gaussians in shared memory, then processes the queue densely.
+constexpr int kPbPer = 4;
 __global__ void __launch_bounds__(256) k_project_bwd(
     const CamF cam, int P, const float* __restrict__ means, const float* __restrict__ scales,
     const float* __restrict__ quats, const float2* __restrict__ d_uv, const float* __restrict__ d_conic,
     const float* __restrict__ d_depth, float* __restrict__ d_means, float* __restrict__ d_scales,
     float* __restrict__ d_quats, float* __restrict__ d_pose) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ int s_q[kPbPer * 256];
+  __shared__ int s_n;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kPbPer * 256;
+#pragma unroll
+  for (int r = 0; r < kPbPer; ++r) {
+    const int g = base + r * 256 + threadIdx.x;
+    bool any = false;
+    if (g < P) {
+      const float2 duv = d_uv[g];
+      any = (duv.x != 0.f) | (duv.y != 0.f) | (d_conic[3 * g] != 0.f) | (d_conic[3 * g + 1] != 0.f) |
+            (d_conic[3 * g + 2] != 0.f) | (d_depth[g] != 0.f);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, any);
+    int at = 0;
+    if ((threadIdx.x & 31) == 0 && bal) at = atomicAdd(&s_n, __popc(bal));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (any) s_q[at + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = g;
+  }
+  __syncthreads();
+  const int nq = s_n;
   float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (g < P) {
+  for (int e = threadIdx.x; e < nq; e += 256) {
+    const int g = s_q[e];
     const float2 duv = d_uv[g];
     const float dA = d_conic[3 * g], dB = d_conic[3 * g + 1], dC = d_conic[3 * g + 2];
     const float dd = d_depth[g];
@@ -174,8 +200,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(
     const float x = R[0] * m0 + R[1] * m1 + R[2] * m2 + tc[0];
     const float y = R[3] * m0 + R[4] * m1 + R[5] * m2 + tc[1];
     const float z = R[6] * m0 + R[7] * m1 + R[8] * m2 + tc[2];
-    const bool any = (duv.x != 0.f) | (duv.y != 0.f) | (dA != 0.f) | (dB != 0.f) | (dC != 0.f) | (dd != 0.f);
-    if (any && z > cam.near_z) {
+    if (z > cam.near_z) {
       const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
       const float4 q4 = reinterpret_cast<const float4*>(quats)[g];
       const float qnorm = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
@@ -304,9 +329,9 @@ __global__ void __launch_bounds__(256) k_project_bwd(
         d_means[3 * g + 1] += R[1] * dx + R[4] * dy + R[7] * dz;
         d_means[3 * g + 2] += R[2] * dx + R[5] * dy + R[8] * dz;
       }
-      pose[0] = dx;
-      pose[1] = dy;
-      pose[2] = dz;
+      pose[0] += dx;
+      pose[1] += dy;
+      pose[2] += dz;
       float3 th = cross3(make_float3(x, y, z), make_float3(dx, dy, dz));
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -315,9 +340,9 @@ __global__ void __launch_bounds__(256) k_project_bwd(
         th.y += c3.y;
         th.z += c3.z;
       }
-      pose[3] = th.x;
-      pose[4] = th.y;
-      pose[5] = th.z;
+      pose[3] += th.x;
+      pose[4] += th.y;
+      pose[5] += th.z;
     }
   }
   // block reduction of the pose partials
@@ -354,7 +379,7 @@ void launch_project_bwd(const CamF& cam, int P, const float* means, const float*
                         float* d_scales, float* d_quats, float* d_pose, cudaStream_t st) {
   if (P <= 0) return;
   GS_TRACE("k_project_bwd", st);
-  k_project_bwd<<<(P + 255) / 256, 256, 0, st>>>(cam, P, means, scales, quats,
+  k_project_bwd<<<(P + kPbPer * 256 - 1) / (kPbPer * 256), 256, 0, st>>>(cam, P, means, scales, quats,
                                                  reinterpret_cast<const float2*>(d_uv), d_conic, d_depth, d_means,
                                                  d_scales, d_quats, d_pose);
 }
