@@ -187,6 +187,7 @@ __device__ __forceinline__ void load_feat_row(const void* feats, int bf16, int N
 template <int NC, bool VIS>
 __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   constexpr int NCs = NC > 0 ? NC : 1;
+  static_assert(NC % 2 == 0, "channels are blended in pairs");
   __shared__ float2 s_uv[kTilePix];
   __shared__ uint8_t s_wmask[kTilePix];  // bit w: warp w's pixel block passes the skip test
   __shared__ float4 s_co[kTilePix];
@@ -258,15 +259,19 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
           // visible (T in front > 0.5): the lowest lane of those here writes
           if ((__activemask() & lanes_below) == 0) p.visible[s_gid[j]] = 1;
         }
+        // packed two-lane FMAs (each lane rounds as fmaf): half the issue slots
+        const float2 w2 = make_float2(w, w);
         if (geom) {
           const float4 cd = s_cd[j];
-          ac0 = __fmaf_rn(w, cd.x, ac0);
-          ac1 = __fmaf_rn(w, cd.y, ac1);
-          ac2 = __fmaf_rn(w, cd.z, ac2);
-          ad = __fmaf_rn(w, cd.w, ad);
+          const float2 a01 = __ffma2_rn(w2, make_float2(cd.x, cd.y), make_float2(ac0, ac1));
+          const float2 a23 = __ffma2_rn(w2, make_float2(cd.z, cd.w), make_float2(ac2, ad));
+          ac0 = a01.x, ac1 = a01.y, ac2 = a23.x, ad = a23.y;
         }
 #pragma unroll
-        for (int c = 0; c < NC; ++c) af[c] = __fmaf_rn(w, s_f[j][c], af[c]);
+        for (int c = 0; c < NC; c += 2) {
+          const float2 f = __ffma2_rn(w2, make_float2(s_f[j][c], s_f[j][c + 1]), make_float2(af[c], af[c + 1]));
+          af[c] = f.x, af[c + 1] = f.y;
+        }
         T = Tn;
         last = start + j + 1 - rg.x;
         ++cnt;
@@ -856,6 +861,12 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   }
   __syncthreads();
   const int maxlast = s_maxlast;
+  // the walk's per-pixel state, pixel q in lane q of packed operands
+  float2 T2 = make_float2(T[0], T[1]), J2 = make_float2(J[0], J[1]);
+  const float2 gC02 = make_float2(gC0[0], gC0[1]), gC12 = make_float2(gC1[0], gC1[1]);
+  const float2 gC22 = make_float2(gC2[0], gC2[1]), gD2 = make_float2(gD[0], gD[1]);
+  const float2 npx2 = make_float2(-pxc[0], -pxc[1]), npy2 = make_float2(-pyc[0], -pyc[1]);
+  const float2 one2 = make_float2(1.f, 1.f);
   // batches of the list, back to front: batch b holds positions [lo_b, hi_b)
   const int nb = (maxlast + kBB - 1) / kBB;
   auto batch_hi = [&](int b) { return rg.x + maxlast - b * kBB; };
@@ -950,46 +961,56 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         const int j2 = two ? 31 - __clz(bits) : j1;
         bits &= ~(1u << j2);
         const int jg[2] = {j1, j2};
-        float al[2][2], dxq[2][2], dyq[2][2];
+        // the two pixels of this thread ride in the two lanes of packed
+        // fp32 operations (each lane rounds as the scalar operation does)
+        float2 al[2], dx2[2], dy2[2];
         bool cl[2][2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const float2 uj = B.uv[jg[k]];
           const float4 cj = B.q[jg[k]];
           const int pos = lo + jg[k] - rg.x;
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            PairAlpha pa;
-            dxq[k][q] = uj.x - pxc[q];
-            dyq[k][q] = uj.y - pyc[q];
-            const bool ok = (k == 0 || two) && pos < last[q] && pair_alpha_q(cj, dxq[k][q], dyq[k][q], pa);
-            al[k][q] = ok ? pa.alpha : 0.f;
-            cl[k][q] = ok && pa.clamped;
-          }
+          // pair_alpha_q for both pixels
+          dx2[k] = __fadd2_rn(make_float2(uj.x, uj.x), npx2);
+          dy2[k] = __fadd2_rn(make_float2(uj.y, uj.y), npy2);
+          const float2 u = __ffma2_rn(make_float2(cj.y, cj.y), dy2[k], __fmul2_rn(make_float2(cj.x, cj.x), dx2[k]));
+          const float2 e = __ffma2_rn(dx2[k], u, __fmul2_rn(__fmul2_rn(make_float2(cj.z, cj.z), dy2[k]), dy2[k]));
+          const float2 a = __fmul2_rn(make_float2(cj.w, cj.w), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+          const bool live = k == 0 || two;
+          const bool ok0 = live && pos < last[0] && !(e.x > 0.f), ok1 = live && pos < last[1] && !(e.y > 0.f);
+          cl[k][0] = a.x > kAlphaMax;
+          cl[k][1] = a.y > kAlphaMax;
+          const float a0 = cl[k][0] ? kAlphaMax : a.x, a1 = cl[k][1] ? kAlphaMax : a.y;
+          const bool b0 = ok0 && a0 >= kAlphaMin, b1 = ok1 && a1 >= kAlphaMin;
+          al[k] = make_float2(b0 ? a0 : 0.f, b1 ? a1 : 0.f);
+          cl[k][0] = b0 && cl[k][0];
+          cl[k][1] = b1 && cl[k][1];
         }
-        float wq[2][2], geo[2][8];
+        float2 wq[2];
+        float geo[2][8];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const float4 cd = B.cd[jg[k]];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) geo[k][e] = 0.f;
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const float a = al[k][q], om = 1.f - a;
-            T[q] = __fdividef(T[q], om);
-            wq[k][q] = a * T[q];
-            const float cg = cd.x * gC0[q] + cd.y * gC1[q] + cd.z * gC2[q] + cd.w * gD[q];
-            const float da = T[q] * (cg - J[q]);
-            J[q] = a * cg + om * J[q];
-            const float dp = cl[k][q] ? 0.f : da * a;
-            const float xdp = dxq[k][q] * dp, ydp = dyq[k][q] * dp;
-            geo[k][0] += dp;
-            geo[k][1] += xdp;
-            geo[k][2] += ydp;
-            geo[k][3] += dxq[k][q] * xdp;
-            geo[k][4] += dyq[k][q] * xdp;
-            geo[k][5] += dyq[k][q] * ydp;
-          }
+          const float2 a = al[k], om = __fadd2_rn(one2, make_float2(-a.x, -a.y));
+          T2 = make_float2(__fdividef(T2.x, om.x), __fdividef(T2.y, om.y));
+          wq[k] = __fmul2_rn(a, T2);
+          const float2 cg = __ffma2_rn(make_float2(cd.w, cd.w), gD2,
+                                       __ffma2_rn(make_float2(cd.z, cd.z), gC22,
+                                                  __ffma2_rn(make_float2(cd.y, cd.y), gC12,
+                                                             __fmul2_rn(make_float2(cd.x, cd.x), gC02))));
+          const float2 da = __fmul2_rn(T2, __fadd2_rn(cg, make_float2(-J2.x, -J2.y)));
+          J2 = __ffma2_rn(a, cg, __fmul2_rn(om, J2));
+          float2 dp = __fmul2_rn(da, a);
+          dp = make_float2(cl[k][0] ? 0.f : dp.x, cl[k][1] ? 0.f : dp.y);
+          const float2 xdp = __fmul2_rn(dx2[k], dp), ydp = __fmul2_rn(dy2[k], dp);
+          const float2 xx = __fmul2_rn(dx2[k], xdp), yx = __fmul2_rn(dy2[k], xdp), yy = __fmul2_rn(dy2[k], ydp);
+          geo[k][0] = dp.x + dp.y;
+          geo[k][1] = xdp.x + xdp.y;
+          geo[k][2] = ydp.x + ydp.y;
+          geo[k][3] = xx.x + xx.y;
+          geo[k][4] = yx.x + yx.y;
+          geo[k][5] = yy.x + yy.y;
+          geo[k][6] = geo[k][7] = 0.f;
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -997,7 +1018,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
           const float gsum = transpose_reduce8(geo[k]);
           if (lane < kGeo) red[((size_t)wid * kBB + jg[k]) * SR + NCH + lane] = gsum;
           uint32_t whi, wlo;
-          split_bf16x2(wq[k][0], wq[k][1], whi, wlo);
+          split_bf16x2(wq[k].x, wq[k].y, whi, wlo);
           reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
           reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = wlo;
           if (lane == rows) row_j = jg[k];
