@@ -345,6 +345,214 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Forward compositing with two pixels per thread (N <= 16): 128 threads per
+// tile, each warp owning an 8 x 8 pixel block and each thread two pixels of
+// one column, 4 rows apart. Per pixel the operations and their order are
+// those of k_render_fwd (identical bits); what the two pixels share is done
+// once: the Gaussian's records, its skip bit, its dx and q.x dx, and the
+// alpha arithmetic runs on packed two-lane fp32 operands.
+constexpr int kFwd2Threads = kTilePix / 2;
+
+template <int NC, bool VIS>
+__global__ void __launch_bounds__(kFwd2Threads, 6) k_render_fwd2(const FwdParams p) {
+  constexpr int NCs = NC > 0 ? NC : 2;
+  constexpr int kB = 2 * kFwd2Threads;  // Gaussians per shared-memory batch
+  static_assert(NC % 2 == 0 && NC <= 16, "channels are blended in pairs; one 16-channel chunk");
+  __shared__ float2 s_uv[kB];
+  __shared__ uint8_t s_wmask[kB];  // bit w: warp w's pixel block passes the skip test
+  __shared__ float4 s_co[kB];
+  __shared__ float4 s_cd[kB];
+  __shared__ __align__(16) float s_f[kB][NCs];
+  __shared__ uint32_t s_gid[VIS ? kB : 1];
+  __shared__ float s_lsum;
+
+  const int tile = blockIdx.x;
+  if (threadIdx.x == 0) s_lsum = 0.f;
+  const unsigned lanes_below = (1u << (threadIdx.x & 31)) - 1u;
+  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
+  int px[2], py[2];
+  thread_pixels<2>(tx, ty, px, py);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float pxc = (float)px[0] + 0.5f;  // both pixels lie in one column
+  const float2 npy2 = make_float2(-((float)py[0] + 0.5f), -((float)py[1] + 0.5f));
+  const int2 rg = p.ranges[tile];
+
+  float T[2] = {1.f, 1.f};
+  float ac[2][4];
+  float af[2][NCs];
+  int last[2] = {0, 0}, cnt[2] = {0, 0};
+  bool done[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    done[q] = !(px[q] < p.cam.W && py[q] < p.cam.H);
+    ac[q][0] = ac[q][1] = ac[q][2] = ac[q][3] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCs; ++c) af[q][c] = 0.f;
+  }
+
+  for (int start = rg.x; start < rg.y; start += kB) {
+    if (__syncthreads_count(done[0] && done[1]) == kFwd2Threads) break;
+#pragma unroll
+    for (int i = threadIdx.x; i < kB; i += kFwd2Threads) {
+      const int idx = start + i;
+      if (idx < rg.y) {
+        const uint32_t g = p.gids[idx];
+        const float4 co = p.co[g];
+        const float2 u = p.uv[g];
+        s_uv[i] = u;
+        s_co[i] = conic_q(co);
+        s_wmask[i] = (uint8_t)warp_block_mask<4, 8, true>(u, co, tx, ty);
+        if (VIS) s_gid[i] = g;
+        s_cd[i] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
+        if (NC > 0) load_feat_row<NCs>(p.feats, p.bf16, p.N, g, 0, s_f[i]);
+      }
+    }
+    __syncthreads();
+    const int n = min(kB, rg.y - start);
+    for (int base = 0; base < n; base += 32) {
+      if (__all_sync(0xffffffffu, done[0] && done[1])) break;
+      const int jj = base + lane;
+      uint32_t bits = __ballot_sync(0xffffffffu, jj < n && ((s_wmask[jj] >> wid) & 1u));
+      while (bits) {
+        const int j = base + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        if (done[0] && done[1]) continue;
+        const float2 uj = s_uv[j];
+        const float4 qc = s_co[j];
+        // pair_alpha_q for both pixels (dx is shared)
+        const float dx = __fsub_rn(uj.x, pxc);
+        const float2 dy = __fadd2_rn(make_float2(uj.y, uj.y), npy2);
+        const float qxdx = __fmul_rn(qc.x, dx);
+        const float2 u = __ffma2_rn(make_float2(qc.y, qc.y), dy, make_float2(qxdx, qxdx));
+        const float2 e = __ffma2_rn(make_float2(dx, dx), u, __fmul2_rn(__fmul2_rn(make_float2(qc.z, qc.z), dy), dy));
+        const float2 a = __fmul2_rn(make_float2(qc.w, qc.w), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+        const float ev[2] = {e.x, e.y}, av[2] = {a.x, a.y};
+        bool bl[2];
+        float w[2], Tn[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float alpha = av[q] > kAlphaMax ? kAlphaMax : av[q];
+          bl[q] = !done[q] && !(ev[q] > 0.f) && alpha >= kAlphaMin;
+          Tn[q] = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+          if (bl[q] && Tn[q] < kTStop) {
+            done[q] = true;
+            bl[q] = false;
+          }
+          w[q] = __fmul_rn(alpha, T[q]);
+        }
+        if (!(bl[0] || bl[1])) continue;
+        if (VIS && ((bl[0] && T[0] > 0.5f) || (bl[1] && T[1] > 0.5f))) {
+          // visible (T in front > 0.5): the lowest lane of those here writes
+          if ((__activemask() & lanes_below) == 0) p.visible[s_gid[j]] = 1;
+        }
+        // packed two-lane FMAs over channel pairs (each lane rounds as fmaf);
+        // a pixel that does not blend this Gaussian skips its updates
+        const float2 w20 = make_float2(w[0], w[0]), w21 = make_float2(w[1], w[1]);
+        {
+          const float4 cd = s_cd[j];
+          if (bl[0]) {
+            const float2 a01 = __ffma2_rn(w20, make_float2(cd.x, cd.y), make_float2(ac[0][0], ac[0][1]));
+            const float2 a23 = __ffma2_rn(w20, make_float2(cd.z, cd.w), make_float2(ac[0][2], ac[0][3]));
+            ac[0][0] = a01.x, ac[0][1] = a01.y, ac[0][2] = a23.x, ac[0][3] = a23.y;
+          }
+          if (bl[1]) {
+            const float2 a01 = __ffma2_rn(w21, make_float2(cd.x, cd.y), make_float2(ac[1][0], ac[1][1]));
+            const float2 a23 = __ffma2_rn(w21, make_float2(cd.z, cd.w), make_float2(ac[1][2], ac[1][3]));
+            ac[1][0] = a01.x, ac[1][1] = a01.y, ac[1][2] = a23.x, ac[1][3] = a23.y;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; c += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(&s_f[j][c]);
+          if (bl[0]) {
+            const float2 r0 = __ffma2_rn(w20, make_float2(v.x, v.y), make_float2(af[0][c], af[0][c + 1]));
+            const float2 r1 = __ffma2_rn(w20, make_float2(v.z, v.w), make_float2(af[0][c + 2], af[0][c + 3]));
+            af[0][c] = r0.x, af[0][c + 1] = r0.y, af[0][c + 2] = r1.x, af[0][c + 3] = r1.y;
+          }
+          if (bl[1]) {
+            const float2 r0 = __ffma2_rn(w21, make_float2(v.x, v.y), make_float2(af[1][c], af[1][c + 1]));
+            const float2 r1 = __ffma2_rn(w21, make_float2(v.z, v.w), make_float2(af[1][c + 2], af[1][c + 3]));
+            af[1][c] = r0.x, af[1][c + 1] = r0.y, af[1][c + 2] = r1.x, af[1][c + 3] = r1.y;
+          }
+        }
+        const int pos = start + j + 1 - rg.x;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+          if (bl[q]) {
+            T[q] = Tn[q];
+            last[q] = pos;
+            ++cnt[q];
+          }
+      }
+    }
+  }
+  const size_t HW = (size_t)p.cam.W * p.cam.H;
+  float lsum = 0.f;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (!(px[q] < p.cam.W && py[q] < p.cam.H)) continue;
+    const size_t pix = (size_t)py[q] * p.cam.W + px[q];
+    const float r0 = ac[q][0] + T[q] * p.bg[0], r1 = ac[q][1] + T[q] * p.bg[1], r2 = ac[q][2] + T[q] * p.bg[2];
+    p.out_rgb[pix] = r0;
+    p.out_rgb[HW + pix] = r1;
+    p.out_rgb[2 * HW + pix] = r2;
+    p.out_depth[pix] = ac[q][3];
+    p.out_alpha[pix] = 1.f - T[q];
+    p.T_final[pix] = T[q];
+    p.last_idx[pix] = last[q];
+    p.n_contrib[pix] = cnt[q];
+    if (NC > 0) {
+      const int nch = min(NC, p.N);
+      if (p.hwc) {
+        float* dst = p.out_feat + pix * p.N;
+        if ((p.N & 3) == 0 && nch == NC) {
+#pragma unroll
+          for (int c = 0; c < NCs; c += 4)
+            *reinterpret_cast<float4*>(dst + c) = make_float4(af[q][c], af[q][c + 1], af[q][c + 2], af[q][c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < NCs; ++c)
+            if (c < nch) dst[c] = af[q][c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NCs; ++c)
+          if (c < nch) p.out_feat[(size_t)c * HW + pix] = af[q][c];
+      }
+    }
+    if (p.l1.on) {
+      uint32_t nz = 0, ng = 0;
+      auto term = [&](float pred, float target, float wt, int bit) {
+        const float d = pred - target;
+        lsum += wt * fabsf(d);
+        nz |= (d != 0.f ? 1u : 0u) << bit;
+        ng |= (d < 0.f ? 1u : 0u) << bit;
+      };
+      if (p.l1.target[0]) {
+        term(r0, p.l1.target[0][pix], p.l1.w[0], kL1BitRgb);
+        term(r1, p.l1.target[0][HW + pix], p.l1.w[0], kL1BitRgb + 1);
+        term(r2, p.l1.target[0][2 * HW + pix], p.l1.w[0], kL1BitRgb + 2);
+      }
+      if (p.l1.target[1]) term(ac[q][3], p.l1.target[1][pix], p.l1.w[1], kL1BitDepth);
+      if (NC > 0 && p.l1.target[2]) {
+        const int nch = min(NC, p.N);
+#pragma unroll
+        for (int c = 0; c < NCs; ++c)
+          if (c < nch) term(af[q][c], p.l1.target[2][p.hwc ? pix * p.N + c : (size_t)c * HW + pix], p.l1.w[2], c);
+      }
+      p.l1.signs[pix] = make_uint2(nz, ng);
+    }
+  }
+  if (p.l1.on && p.l1.loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.f) atomicAdd(&s_lsum, lsum);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_lsum != 0.f) atomicAdd(p.l1.loss, s_lsum);
+  }
+}
+
+// ---------------------------------------------------------------------------
 struct BwdParams {
   CamF cam;
   const int2* ranges;
@@ -1142,12 +1350,12 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
   GS_TRACE("k_render_fwd", st);
   const dim3 grid(tiles, N <= 16 ? 1 : (N + 31) / 32);
   if (visible) {
-    if (N <= 0) k_render_fwd<0, true><<<grid, kTilePix, 0, st>>>(p);
-    else if (N <= 16) k_render_fwd<16, true><<<grid, kTilePix, 0, st>>>(p);
+    if (N <= 0) k_render_fwd2<0, true><<<grid, kFwd2Threads, 0, st>>>(p);
+    else if (N <= 16) k_render_fwd2<16, true><<<grid, kFwd2Threads, 0, st>>>(p);
     else k_render_fwd<32, true><<<grid, kTilePix, 0, st>>>(p);
   } else {
-    if (N <= 0) k_render_fwd<0, false><<<grid, kTilePix, 0, st>>>(p);
-    else if (N <= 16) k_render_fwd<16, false><<<grid, kTilePix, 0, st>>>(p);
+    if (N <= 0) k_render_fwd2<0, false><<<grid, kFwd2Threads, 0, st>>>(p);
+    else if (N <= 16) k_render_fwd2<16, false><<<grid, kFwd2Threads, 0, st>>>(p);
     else k_render_fwd<32, false><<<grid, kTilePix, 0, st>>>(p);
   }
   return last_launch_status();
