@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
 constexpr int kFwd2Threads = kTilePix / 2;
 
 template <int NC, bool VIS>
-__global__ void __launch_bounds__(kFwd2Threads, 6) k_render_fwd2(const FwdParams p) {
+__global__ void __launch_bounds__(kFwd2Threads, 5) k_render_fwd2(const FwdParams p) {
   constexpr int NCs = NC > 0 ? NC : 2;
   constexpr int kB = 2 * kFwd2Threads;  // Gaussians per shared-memory batch
   static_assert(NC % 2 == 0 && NC <= 16, "channels are blended in pairs; one 16-channel chunk");
@@ -413,76 +413,91 @@ __global__ void __launch_bounds__(kFwd2Threads, 6) k_render_fwd2(const FwdParams
       if (__all_sync(0xffffffffu, done[0] && done[1])) break;
       const int jj = base + lane;
       uint32_t bits = __ballot_sync(0xffffffffu, jj < n && ((s_wmask[jj] >> wid) & 1u));
+      // two Gaussians per iteration: their alphas first (four independent
+      // chains), then the blends in list order
       while (bits) {
-        const int j = base + __ffs(bits) - 1;
+        const int j1 = base + __ffs(bits) - 1;
         bits &= bits - 1u;
+        const bool two = bits != 0;
+        const int j2 = two ? base + __ffs(bits) - 1 : j1;
+        if (two) bits &= bits - 1u;
         if (done[0] && done[1]) continue;
-        const float2 uj = s_uv[j];
-        const float4 qc = s_co[j];
-        // pair_alpha_q for both pixels (dx is shared)
-        const float dx = __fsub_rn(uj.x, pxc);
-        const float2 dy = __fadd2_rn(make_float2(uj.y, uj.y), npy2);
-        const float qxdx = __fmul_rn(qc.x, dx);
-        const float2 u = __ffma2_rn(make_float2(qc.y, qc.y), dy, make_float2(qxdx, qxdx));
-        const float2 e = __ffma2_rn(make_float2(dx, dx), u, __fmul2_rn(__fmul2_rn(make_float2(qc.z, qc.z), dy), dy));
-        const float2 a = __fmul2_rn(make_float2(qc.w, qc.w), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
-        const float ev[2] = {e.x, e.y}, av[2] = {a.x, a.y};
-        bool bl[2];
-        float w[2], Tn[2];
+        const int jg[2] = {j1, j2};
+        float2 ea[2], aa[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const float alpha = av[q] > kAlphaMax ? kAlphaMax : av[q];
-          bl[q] = !done[q] && !(ev[q] > 0.f) && alpha >= kAlphaMin;
-          Tn[q] = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
-          if (bl[q] && Tn[q] < kTStop) {
-            done[q] = true;
-            bl[q] = false;
-          }
-          w[q] = __fmul_rn(alpha, T[q]);
-        }
-        if (!(bl[0] || bl[1])) continue;
-        if (VIS && ((bl[0] && T[0] > 0.5f) || (bl[1] && T[1] > 0.5f))) {
-          // visible (T in front > 0.5): the lowest lane of those here writes
-          if ((__activemask() & lanes_below) == 0) p.visible[s_gid[j]] = 1;
-        }
-        // packed two-lane FMAs over channel pairs (each lane rounds as fmaf);
-        // a pixel that does not blend this Gaussian skips its updates
-        const float2 w20 = make_float2(w[0], w[0]), w21 = make_float2(w[1], w[1]);
-        {
-          const float4 cd = s_cd[j];
-          if (bl[0]) {
-            const float2 a01 = __ffma2_rn(w20, make_float2(cd.x, cd.y), make_float2(ac[0][0], ac[0][1]));
-            const float2 a23 = __ffma2_rn(w20, make_float2(cd.z, cd.w), make_float2(ac[0][2], ac[0][3]));
-            ac[0][0] = a01.x, ac[0][1] = a01.y, ac[0][2] = a23.x, ac[0][3] = a23.y;
-          }
-          if (bl[1]) {
-            const float2 a01 = __ffma2_rn(w21, make_float2(cd.x, cd.y), make_float2(ac[1][0], ac[1][1]));
-            const float2 a23 = __ffma2_rn(w21, make_float2(cd.z, cd.w), make_float2(ac[1][2], ac[1][3]));
-            ac[1][0] = a01.x, ac[1][1] = a01.y, ac[1][2] = a23.x, ac[1][3] = a23.y;
-          }
+        for (int k = 0; k < 2; ++k) {
+          // pair_alpha_q for both pixels (dx is shared)
+          const float2 uj = s_uv[jg[k]];
+          const float4 qc = s_co[jg[k]];
+          const float dx = __fsub_rn(uj.x, pxc);
+          const float2 dy = __fadd2_rn(make_float2(uj.y, uj.y), npy2);
+          const float qxdx = __fmul_rn(qc.x, dx);
+          const float2 u = __ffma2_rn(make_float2(qc.y, qc.y), dy, make_float2(qxdx, qxdx));
+          ea[k] = __ffma2_rn(make_float2(dx, dx), u, __fmul2_rn(__fmul2_rn(make_float2(qc.z, qc.z), dy), dy));
+          aa[k] = __fmul2_rn(make_float2(qc.w, qc.w), make_float2(ex2_approx(ea[k].x), ex2_approx(ea[k].y)));
         }
 #pragma unroll
-        for (int c = 0; c < NC; c += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(&s_f[j][c]);
-          if (bl[0]) {
-            const float2 r0 = __ffma2_rn(w20, make_float2(v.x, v.y), make_float2(af[0][c], af[0][c + 1]));
-            const float2 r1 = __ffma2_rn(w20, make_float2(v.z, v.w), make_float2(af[0][c + 2], af[0][c + 3]));
-            af[0][c] = r0.x, af[0][c + 1] = r0.y, af[0][c + 2] = r1.x, af[0][c + 3] = r1.y;
-          }
-          if (bl[1]) {
-            const float2 r0 = __ffma2_rn(w21, make_float2(v.x, v.y), make_float2(af[1][c], af[1][c + 1]));
-            const float2 r1 = __ffma2_rn(w21, make_float2(v.z, v.w), make_float2(af[1][c + 2], af[1][c + 3]));
-            af[1][c] = r0.x, af[1][c + 1] = r0.y, af[1][c + 2] = r1.x, af[1][c + 3] = r1.y;
-          }
-        }
-        const int pos = start + j + 1 - rg.x;
+        for (int k = 0; k < 2; ++k) {
+          if (k == 1 && !two) break;
+          const int j = jg[k];
+          const float ev[2] = {ea[k].x, ea[k].y}, av[2] = {aa[k].x, aa[k].y};
+          bool bl[2];
+          float w[2], Tn[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-          if (bl[q]) {
-            T[q] = Tn[q];
-            last[q] = pos;
-            ++cnt[q];
+          for (int q = 0; q < 2; ++q) {
+            const float alpha = av[q] > kAlphaMax ? kAlphaMax : av[q];
+            bl[q] = !done[q] && !(ev[q] > 0.f) && alpha >= kAlphaMin;
+            Tn[q] = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
+            if (bl[q] && Tn[q] < kTStop) {
+              done[q] = true;
+              bl[q] = false;
+            }
+            w[q] = __fmul_rn(alpha, T[q]);
           }
+          if (!(bl[0] || bl[1])) continue;
+          if (VIS && ((bl[0] && T[0] > 0.5f) || (bl[1] && T[1] > 0.5f))) {
+            // visible (T in front > 0.5): the lowest lane of those here writes
+            if ((__activemask() & lanes_below) == 0) p.visible[s_gid[j]] = 1;
+          }
+          // packed two-lane FMAs over channel pairs (each lane rounds as
+          // fmaf); a pixel that does not blend this Gaussian skips its updates
+          const float2 w20 = make_float2(w[0], w[0]), w21 = make_float2(w[1], w[1]);
+          {
+            const float4 cd = s_cd[j];
+            if (bl[0]) {
+              const float2 a01 = __ffma2_rn(w20, make_float2(cd.x, cd.y), make_float2(ac[0][0], ac[0][1]));
+              const float2 a23 = __ffma2_rn(w20, make_float2(cd.z, cd.w), make_float2(ac[0][2], ac[0][3]));
+              ac[0][0] = a01.x, ac[0][1] = a01.y, ac[0][2] = a23.x, ac[0][3] = a23.y;
+            }
+            if (bl[1]) {
+              const float2 a01 = __ffma2_rn(w21, make_float2(cd.x, cd.y), make_float2(ac[1][0], ac[1][1]));
+              const float2 a23 = __ffma2_rn(w21, make_float2(cd.z, cd.w), make_float2(ac[1][2], ac[1][3]));
+              ac[1][0] = a01.x, ac[1][1] = a01.y, ac[1][2] = a23.x, ac[1][3] = a23.y;
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < NC; c += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(&s_f[j][c]);
+            if (bl[0]) {
+              const float2 r0 = __ffma2_rn(w20, make_float2(v.x, v.y), make_float2(af[0][c], af[0][c + 1]));
+              const float2 r1 = __ffma2_rn(w20, make_float2(v.z, v.w), make_float2(af[0][c + 2], af[0][c + 3]));
+              af[0][c] = r0.x, af[0][c + 1] = r0.y, af[0][c + 2] = r1.x, af[0][c + 3] = r1.y;
+            }
+            if (bl[1]) {
+              const float2 r0 = __ffma2_rn(w21, make_float2(v.x, v.y), make_float2(af[1][c], af[1][c + 1]));
+              const float2 r1 = __ffma2_rn(w21, make_float2(v.z, v.w), make_float2(af[1][c + 2], af[1][c + 3]));
+              af[1][c] = r0.x, af[1][c + 1] = r0.y, af[1][c + 2] = r1.x, af[1][c + 3] = r1.y;
+            }
+          }
+          const int pos = start + j + 1 - rg.x;
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            if (bl[q]) {
+              T[q] = Tn[q];
+              last[q] = pos;
+              ++cnt[q];
+            }
+        }
       }
     }
   }
