@@ -831,7 +831,8 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
 // multiply-adds per pixel and a 32-channel transposition.
 namespace mma_bwd {
 constexpr int kBB = 32;           // Gaussians per shared-memory batch
-constexpr int kRows = 16;         // Gaussians per warp contraction (MMA M)
+constexpr int kRows = 16;         // rows of a warp's contraction tile (MMA M)
+constexpr int kGRows = 8;         // Gaussians per contraction: w in rows 0..7, dp in rows 8..15
 constexpr int kWStride = 72;      // bf16 per W row: 64 pixels + 8 (rows 144 B apart: conflict-free ldmatrix)
 constexpr int kNW = 4;            // warps (8 x 8 pixel blocks) per tile
 constexpr int kThreads = 32 * kNW;
@@ -891,25 +892,6 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, u
   const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
-// Lane l ends up with the warp-wide sum of v[l & 7]: three halving steps over
-// lane bits 2, 1, 0 (4 + 2 + 1 shuffles), then two butterfly steps over bits 3, 4.
-__device__ __forceinline__ float transpose_reduce8(float (&v)[8]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 4; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-#pragma unroll
-    for (int k = 0; k < s; ++k) {
-      const float send = upper ? v[k] : v[k + s];
-      const float keep = upper ? v[k + s] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-    }
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 8);
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
-  return v[0];
 }
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -1082,6 +1064,25 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       }
     }
   }
+  // B fragment of the pixel monomials 1, x, y, x^2, x y, y^2 (n = 0..5; 6, 7
+  // are zero), x and y the pixel centre minus the warp block's centre:
+  // half-integers in [-3.5, 3.5], so all six are exact in bf16. The walk's dp
+  // rows contracted against it give the block's geometric moments.
+  uint32_t bm[4][2];
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const float x = (float)(t4 + 4 * hf) - 3.5f;
+      float m[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float y = (float)(s + 4 * q) - 3.5f;
+        m[q] = g8 == 0 ? 1.f : g8 == 1 ? x : g8 == 2 ? y : g8 == 3 ? x * x : g8 == 4 ? x * y : g8 == 5 ? y * y : 0.f;
+      }
+      const __nv_bfloat162 v = __floats2bfloat162_rn(m[0], m[1]);
+      bm[s][hf] = *reinterpret_cast<const uint32_t*>(&v);
+    }
   __syncthreads();
   const int maxlast = s_maxlast;
   // the walk's per-pixel state, pixel q in lane q of packed operands
@@ -1124,12 +1125,14 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     if (stage) stage_batch(p, s_b[(b + 1) % kNBuf], lane, g_next);
     if (wid == 0 && b + 2 < nb && lane < batch_hi(b + 2) - batch_lo(b + 2)) g_next = p.gids[batch_lo(b + 2) + lane];
 
-    // Contraction of the filled rows of the warp's W tile (rows past `rows`
-    // hold stale values: their sums are not stored) into this warp's sums.
-    int rows = 0, row_j = 0;  // lane r: batch index of the Gaussian in W row r
+    // Contraction of the warp's tile: rows r < 8 hold w of the r-th Gaussian
+    // walked since the last contraction and rows 8 + r its dp. The cotangent
+    // n-tiles take rows r (W . G), the monomial n-tile rows 8 + r (dp . m);
+    // the other products and rows past `rows` (stale values) are not stored.
+    int rows = 0, row_j = 0;  // lane r: batch index of the Gaussian in rows r and 8 + r
     auto flush = [&]() {
       __syncwarp();
-      float dW[NT][4];
+      float dW[NT][4], dM[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) dW[nt][0] = dW[nt][1] = dW[nt][2] = dW[nt][3] = 0.f;
 #pragma unroll
@@ -1143,20 +1146,17 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
           if constexpr (!L1) mma_bf16_m16n8k16(dW[nt], ah, bl[L1 ? 0 : nt][s][0], bl[L1 ? 0 : nt][s][1]);
           mma_bf16_m16n8k16(dW[nt], ah, bh[nt][s][0], bh[nt][s][1]);
         }
+        mma_bf16_m16n8k16(dM, al4, bm[s][0], bm[s][1]);
+        mma_bf16_m16n8k16(dM, ah, bm[s][0], bm[s][1]);
       }
-      // D rows g8 and g8 + 8, columns 2 t4 and 2 t4 + 1
-      const int j0 = __shfl_sync(0xffffffffu, row_j, g8), j1 = __shfl_sync(0xffffffffu, row_j, g8 + 8);
+      // D rows g8 (W . G, columns 2 t4 and 2 t4 + 1) and g8 + 8 (dp . m)
+      const int j0 = __shfl_sync(0xffffffffu, row_j, g8);
       if (g8 < rows) {
         float* r = red + ((size_t)wid * kBB + j0) * SR;
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
           if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r + 8 * nt + 2 * t4) = make_float2(dW[nt][0], dW[nt][1]);
-      }
-      if (g8 + 8 < rows) {
-        float* r = red + ((size_t)wid * kBB + j1) * SR;
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-          if (8 * nt + 2 * t4 < NCH) *reinterpret_cast<float2*>(r + 8 * nt + 2 * t4) = make_float2(dW[nt][2], dW[nt][3]);
+        if (2 * t4 < kGeo) *reinterpret_cast<float2*>(r + NCH + 2 * t4) = make_float2(dM[2], dM[3]);
       }
       __syncwarp();
       rows = 0;
@@ -1165,91 +1165,69 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     // walk: this warp's Gaussians of the batch in reverse list order, two at a
     // time. Both pairs' alphas are formed first (four independent chains); a
     // pair that does not blend takes alpha = 0, for which every update below
-    // is an exact identity (T / 1, 0 cg + 1 J) and w = dp = 0.
-    const uint32_t walked = __ballot_sync(0xffffffffu, lane < n && ((B.wmask[lane] >> wid) & 1u));
-    uint32_t cut = 0;  // at most 16 rows per contraction: split below the 16th walked from the top
-    if (__popc(walked) > kRows) {
-      uint32_t t = walked;
-      for (int i = 0; i < kRows - 1; ++i) t &= ~(1u << (31 - __clz(t)));
-      cut = 31 - __clz(t);
-    }
-#pragma unroll 1
-    for (int chunk = 0; chunk < 2; ++chunk) {
-      uint32_t bits = chunk == 0 ? walked & ~((1u << cut) - 1u) : walked & ((1u << cut) - 1u);
-      if (bits == 0) break;
-      while (bits) {
-        const int j1 = 31 - __clz(bits);
-        bits &= ~(1u << j1);
-        const bool two = bits != 0;
-        const int j2 = two ? 31 - __clz(bits) : j1;
-        bits &= ~(1u << j2);
-        const int jg[2] = {j1, j2};
-        // the two pixels of this thread ride in the two lanes of packed
-        // fp32 operations (each lane rounds as the scalar operation does)
-        float2 al[2], dx2[2], dy2[2];
-        bool cl[2][2];
+    // is an exact identity (T / 1, 0 cg + 1 J) and w = dp = 0. After every
+    // eight Gaussians the tile is contracted (pairs never straddle: rows stay
+    // even until the last, single Gaussian).
+    uint32_t bits = __ballot_sync(0xffffffffu, lane < n && ((B.wmask[lane] >> wid) & 1u));
+    while (bits) {
+      const int j1 = 31 - __clz(bits);
+      bits &= ~(1u << j1);
+      const bool two = bits != 0;
+      const int j2 = two ? 31 - __clz(bits) : j1;
+      bits &= ~(1u << j2);
+      const int jg[2] = {j1, j2};
+      // the two pixels of this thread ride in the two lanes of packed
+      // fp32 operations (each lane rounds as the scalar operation does)
+      float2 al[2];
+      bool cl[2][2];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const float2 uj = B.uv[jg[k]];
-          const float4 cj = B.q[jg[k]];
-          const int pos = lo + jg[k] - rg.x;
-          // pair_alpha_q for both pixels
-          dx2[k] = __fadd2_rn(make_float2(uj.x, uj.x), npx2);
-          dy2[k] = __fadd2_rn(make_float2(uj.y, uj.y), npy2);
-          const float2 u = __ffma2_rn(make_float2(cj.y, cj.y), dy2[k], __fmul2_rn(make_float2(cj.x, cj.x), dx2[k]));
-          const float2 e = __ffma2_rn(dx2[k], u, __fmul2_rn(__fmul2_rn(make_float2(cj.z, cj.z), dy2[k]), dy2[k]));
-          const float2 a = __fmul2_rn(make_float2(cj.w, cj.w), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
-          const bool live = k == 0 || two;
-          const bool ok0 = live && pos < last[0] && !(e.x > 0.f), ok1 = live && pos < last[1] && !(e.y > 0.f);
-          cl[k][0] = a.x > kAlphaMax;
-          cl[k][1] = a.y > kAlphaMax;
-          const float a0 = cl[k][0] ? kAlphaMax : a.x, a1 = cl[k][1] ? kAlphaMax : a.y;
-          const bool b0 = ok0 && a0 >= kAlphaMin, b1 = ok1 && a1 >= kAlphaMin;
-          al[k] = make_float2(b0 ? a0 : 0.f, b1 ? a1 : 0.f);
-          cl[k][0] = b0 && cl[k][0];
-          cl[k][1] = b1 && cl[k][1];
-        }
-        float2 wq[2];
-        float geo[2][8];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const float4 cd = B.cd[jg[k]];
-          const float2 a = al[k], om = __fadd2_rn(one2, make_float2(-a.x, -a.y));
-          T2 = make_float2(__fdividef(T2.x, om.x), __fdividef(T2.y, om.y));
-          wq[k] = __fmul2_rn(a, T2);
-          const float2 cg = __ffma2_rn(make_float2(cd.w, cd.w), gD2,
-                                       __ffma2_rn(make_float2(cd.z, cd.z), gC22,
-                                                  __ffma2_rn(make_float2(cd.y, cd.y), gC12,
-                                                             __fmul2_rn(make_float2(cd.x, cd.x), gC02))));
-          const float2 da = __fmul2_rn(T2, __fadd2_rn(cg, make_float2(-J2.x, -J2.y)));
-          J2 = __ffma2_rn(a, cg, __fmul2_rn(om, J2));
-          float2 dp = __fmul2_rn(da, a);
-          dp = make_float2(cl[k][0] ? 0.f : dp.x, cl[k][1] ? 0.f : dp.y);
-          const float2 xdp = __fmul2_rn(dx2[k], dp), ydp = __fmul2_rn(dy2[k], dp);
-          const float2 xx = __fmul2_rn(dx2[k], xdp), yx = __fmul2_rn(dy2[k], xdp), yy = __fmul2_rn(dy2[k], ydp);
-          geo[k][0] = dp.x + dp.y;
-          geo[k][1] = xdp.x + xdp.y;
-          geo[k][2] = ydp.x + ydp.y;
-          geo[k][3] = xx.x + xx.y;
-          geo[k][4] = yx.x + yx.y;
-          geo[k][5] = yy.x + yy.y;
-          geo[k][6] = geo[k][7] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          if (k == 1 && !two) break;
-          const float gsum = transpose_reduce8(geo[k]);
-          if (lane < kGeo) red[((size_t)wid * kBB + jg[k]) * SR + NCH + lane] = gsum;
-          uint32_t whi, wlo;
-          split_bf16x2(wq[k].x, wq[k].y, whi, wlo);
-          reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = whi;
-          reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = wlo;
-          if (lane == rows) row_j = jg[k];
-          ++rows;
-        }
+      for (int k = 0; k < 2; ++k) {
+        const float2 uj = B.uv[jg[k]];
+        const float4 cj = B.q[jg[k]];
+        const int pos = lo + jg[k] - rg.x;
+        // pair_alpha_q for both pixels
+        const float2 dx2 = __fadd2_rn(make_float2(uj.x, uj.x), npx2);
+        const float2 dy2 = __fadd2_rn(make_float2(uj.y, uj.y), npy2);
+        const float2 u = __ffma2_rn(make_float2(cj.y, cj.y), dy2, __fmul2_rn(make_float2(cj.x, cj.x), dx2));
+        const float2 e = __ffma2_rn(dx2, u, __fmul2_rn(__fmul2_rn(make_float2(cj.z, cj.z), dy2), dy2));
+        const float2 a = __fmul2_rn(make_float2(cj.w, cj.w), make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+        const bool live = k == 0 || two;
+        const bool ok0 = live && pos < last[0] && !(e.x > 0.f), ok1 = live && pos < last[1] && !(e.y > 0.f);
+        cl[k][0] = a.x > kAlphaMax;
+        cl[k][1] = a.y > kAlphaMax;
+        const float a0 = cl[k][0] ? kAlphaMax : a.x, a1 = cl[k][1] ? kAlphaMax : a.y;
+        const bool b0 = ok0 && a0 >= kAlphaMin, b1 = ok1 && a1 >= kAlphaMin;
+        al[k] = make_float2(b0 ? a0 : 0.f, b1 ? a1 : 0.f);
+        cl[k][0] = b0 && cl[k][0];
+        cl[k][1] = b1 && cl[k][1];
       }
-      flush();
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !two) break;
+        const float4 cd = B.cd[jg[k]];
+        const float2 a = al[k], om = __fadd2_rn(one2, make_float2(-a.x, -a.y));
+        T2 = make_float2(__fdividef(T2.x, om.x), __fdividef(T2.y, om.y));
+        const float2 wq = __fmul2_rn(a, T2);
+        const float2 cg = __ffma2_rn(make_float2(cd.w, cd.w), gD2,
+                                     __ffma2_rn(make_float2(cd.z, cd.z), gC22,
+                                                __ffma2_rn(make_float2(cd.y, cd.y), gC12,
+                                                           __fmul2_rn(make_float2(cd.x, cd.x), gC02))));
+        const float2 da = __fmul2_rn(T2, __fadd2_rn(cg, make_float2(-J2.x, -J2.y)));
+        J2 = __ffma2_rn(a, cg, __fmul2_rn(om, J2));
+        const float2 dp = __fmul2_rn(da, a);
+        uint32_t hi, lo2;
+        split_bf16x2(wq.x, wq.y, hi, lo2);
+        reinterpret_cast<uint32_t*>(wh_w + rows * kWStride)[lane] = hi;
+        reinterpret_cast<uint32_t*>(wl_w + rows * kWStride)[lane] = lo2;
+        split_bf16x2(cl[k][0] ? 0.f : dp.x, cl[k][1] ? 0.f : dp.y, hi, lo2);
+        reinterpret_cast<uint32_t*>(wh_w + (rows + kGRows) * kWStride)[lane] = hi;
+        reinterpret_cast<uint32_t*>(wl_w + (rows + kGRows) * kWStride)[lane] = lo2;
+        if (lane == rows) row_j = jg[k];
+        ++rows;
+      }
+      if (rows == kGRows) flush();
     }
+    if (rows > 0) flush();
     if (stage) {
       cp_async_wait_all();
       finish_batch(s_b[(b + 1) % kNBuf], lane, tx, ty);
@@ -1302,19 +1280,24 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       // u, v, conic and opacity of Gaussian `lane`: v_u = -sum (A dx + B dy) dp,
       // v_v = -sum (B dx + C dy) dp, v_A = -sum dx^2 dp / 2, v_B = -sum dx dy dp,
       // v_C = -sum dy^2 dp / 2 (dx = u - pixel centre), v_o = sum dp / o
+      // from each warp's moments m = sum dp (1, x, y, x^2, x y, y^2), x, y
+      // relative to its block's centre c: with (du, dv) = u - c, dx = du - x
       const int j = lane;
       const uint32_t wm = B.wmask[j];
+      const float2 uj = B.uv[j];
       float sdp = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
 #pragma unroll
       for (int w = 0; w < kNW; ++w) {
         if (!((wm >> w) & 1u)) continue;
         const float* M = red + ((size_t)w * kBB + j) * SR + NCH;
+        const float du = uj.x - (float)(tx * kTile + (w & 1) * 8 + 4);
+        const float dv = uj.y - (float)(ty * kTile + (w >> 1) * 8 + 4);
         sdp += M[0];
-        sx += M[1];
-        sy += M[2];
-        sxx += M[3];
-        sxy += M[4];
-        syy += M[5];
+        sx += du * M[0] - M[1];
+        sy += dv * M[0] - M[2];
+        sxx += du * (du * M[0] - 2.f * M[1]) + M[3];
+        sxy += du * (dv * M[0] - M[2]) - dv * M[1] + M[4];
+        syy += dv * (dv * M[0] - 2.f * M[2]) + M[5];
       }
       const float4 co = B.co[j];
       const uint32_t g = B.gid[j];
