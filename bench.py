@@ -160,8 +160,8 @@ def algorithmic_flops(stats):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/render_fwd_bwd_room300k_N16_full.md, keyed to
 # the source it was taken on (null once render.cu changes).
-NCU_TRAFFIC = {"k_render_bwd_mma": (40_126_208 + 7_168, "1427e4ecb394eec5"),
-               "k_render_fwd": (86_224_640 + 48_075_264, "1427e4ecb394eec5")}
+NCU_TRAFFIC = {"k_render_bwd_mma": (40_132_864 + 9_728, "36fc813124e648b8"),
+               "k_render_fwd": (86_089_984 + 47_798_272, "36fc813124e648b8")}
 
 
 def ncu_traffic(kernel):
