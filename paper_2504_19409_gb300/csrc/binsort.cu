@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(kDkThreads) k_depth_keys(int P, const float* _
                                                            const int* __restrict__ touched, uint32_t* __restrict__ dk,
                                                            uint32_t* __restrict__ dv, SortCtrl* __restrict__ ctrl,
                                                            OsCtrl* __restrict__ os) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_h[kDepthPasses][kRadix];
   __shared__ uint32_t s_cull;
   for (int i = threadIdx.x; i < kDepthPasses * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
@@ -159,6 +161,8 @@ __global__ void __launch_bounds__(kDkThreads) k_depth_keys(int P, const float* _
 __global__ void __launch_bounds__(256) k_scan_partials(int P, const uint32_t* __restrict__ order,
                                                        const int* __restrict__ touched,
                                                        long long* __restrict__ partial) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int s_warp[32];
   const int r = blockIdx.x * kScanChunk + threadIdx.x;
   const int v = r < P ? touched[order[r]] : 0;
@@ -171,6 +175,8 @@ __global__ void __launch_bounds__(256) k_scan_partials(int P, const uint32_t* __
 __global__ void __launch_bounds__(1024) k_scan_top(int nchunks, long long* __restrict__ partial, long long capacity,
                                                    SortCtrl* __restrict__ ctrl, long long* __restrict__ n_out,
                                                    int32_t* __restrict__ status) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ long long s_carry;
   __shared__ long long s_warp[32];
   if (threadIdx.x == 0) s_carry = 0;
@@ -224,6 +230,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(int P, const uint32_t* __
                                               const long long* __restrict__ partial, int tiles_x, long long capacity,
                                               int npass, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals,
                                               OsCtrl* __restrict__ os) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_th[kMaxTilePasses][kRadix];  // digit counts of the written tile keys
   __shared__ int s_off[kScanChunk + 1];
   __shared__ uint32_t s_g[kScanChunk];
@@ -308,6 +316,8 @@ __global__ void __launch_bounds__(kRsThreads) k_os_scatter(const uint32_t* __res
                                                            const long long* __restrict__ n_ptr, int shift,
                                                            const uint32_t* __restrict__ hist, uint32_t* ticket,
                                                            unsigned long long* lb, int32_t* __restrict__ status) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_hist[kRsWarps][kRadix];
   __shared__ int s_warp[32];
   __shared__ uint32_t s_chunk;
@@ -401,6 +411,8 @@ __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict_
                                                      const float* __restrict__ depth, const SortCtrl* __restrict__ ctrl,
                                                      int num_tiles, int2* __restrict__ ranges,
                                                      unsigned long long* __restrict__ keys64) {
+  pdl_wait();
+  pdl_trigger();
   const long long n = ctrl->n_eff;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const uint32_t t = tkeys[i];
@@ -458,7 +470,7 @@ SortLayout sort_layout(int P, long long capacity, int num_tiles) {
 void os_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, const long long* n_ptr,
              int shift, int pass, int nblk, OsCtrl* os, unsigned long long* lb, int32_t* status, cudaStream_t st) {
   GS_TRACE("k_os_scatter", st);
-  k_os_scatter<<<nblk, kRsThreads, 0, st>>>(kin, vin, kout, vout, n_ptr, shift, os->hist[pass], &os->ticket[pass],
+  launch_pdl(k_os_scatter, nblk, kRsThreads, 0, st, kin, vin, kout, vout, n_ptr, shift, os->hist[pass], &os->ticket[pass],
                                             lb, status);
 }
 
@@ -496,7 +508,7 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   if (cudaMemsetAsync(os, 0, (L.lb - L.os) + L.lb_bytes, st) != cudaSuccess) return GS_ERR_CUDA;
   {
     GS_TRACE("k_depth_keys", st);
-    k_depth_keys<<<L.nblk_p, kDkThreads, 0, st>>>(P, depth, touched, dk, dv, ctrl, os);
+    launch_pdl(k_depth_keys, L.nblk_p, kDkThreads, 0, st, P, depth, touched, dk, dv, ctrl, os);
   }
   // 1. depth sort: 4 passes, ending in (dk, dv)
   os_pass(dk, dv, dk2, dv2, n_gauss, 0, 0, L.nblk_p, os, lb, status, st);
@@ -506,11 +518,11 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   // 2. scan + emission in depth order
   {
     GS_TRACE("k_scan_partials", st);
-    k_scan_partials<<<L.nscan, 256, 0, st>>>(P, dv, touched, partial);
+    launch_pdl(k_scan_partials, L.nscan, 256, 0, st, P, dv, touched, partial);
   }
   {
     GS_TRACE("k_scan_top", st);
-    k_scan_top<<<1, 1024, 0, st>>>(L.nscan, partial, capacity, ctrl, reinterpret_cast<long long*>(n_out), status);
+    launch_pdl(k_scan_top, 1, 1024, 0, st, L.nscan, partial, capacity, ctrl, reinterpret_cast<long long*>(n_out), status);
   }
   // 3. tile sort: passes ping-pong so that the last one lands in (tk, gids)
   const int npass = L.npass_t;
@@ -523,7 +535,7 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   }
   {
     GS_TRACE("k_emit", st);
-    k_emit<<<L.nscan, kEmitThreads, 0, st>>>(P, dv, touched, reinterpret_cast<const int4*>(rect), partial, cam.tiles_x,
+    launch_pdl(k_emit, L.nscan, kEmitThreads, 0, st, P, dv, touched, reinterpret_cast<const int4*>(rect), partial, cam.tiles_x,
                                     capacity, npass, kb[0], vb[0], os);
   }
   unsigned long long* lb_t = lb + kDepthPasses * lb_pass_p;
@@ -535,7 +547,7 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
     int nb = (int)((capacity + 255) / 256);
     if (nb > 4096) nb = 4096;
     if (nb < 1) nb = 1;
-    k_tile_ranges<<<nb, 256, 0, st>>>(tk, gids, depth, ctrl, num_tiles, reinterpret_cast<int2*>(ranges), keys64);
+    launch_pdl(k_tile_ranges, nb, 256, 0, st, tk, gids, depth, ctrl, num_tiles, reinterpret_cast<int2*>(ranges), keys64);
   }
   return last_launch_status();
 }

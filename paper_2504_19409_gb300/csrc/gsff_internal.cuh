@@ -5,9 +5,36 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "gsff.h"
 
 namespace gsff {
+
+// Programmatic dependent launch. A kernel started by launch_pdl may be
+// scheduled while the previous kernel of its stream is still draining; every
+// kernel of the frame's chain calls pdl_wait() before its first global memory
+// access (it returns once the previous grid has completed and its writes are
+// visible, and at once for a kernel launched without the attribute), then
+// pdl_trigger() so that the next kernel can be scheduled in turn.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // 3DGS rules the paper's renderer builds on (Sec. 3.1); the paper does not
 // print their values.

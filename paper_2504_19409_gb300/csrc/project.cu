@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(256) k_project(const CamF cam, int P, const fl
                                                  float4* __restrict__ co, float* __restrict__ depth,
                                                  int4* __restrict__ rect, int* __restrict__ touched,
                                                  unsigned long long* __restrict__ n_inst) {
+  pdl_wait();
+  pdl_trigger();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   int count = 0;
   if (g < P) {
@@ -166,6 +168,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(
     const float* __restrict__ quats, const float2* __restrict__ d_uv, const float* __restrict__ d_conic,
     const float* __restrict__ d_depth, float* __restrict__ d_means, float* __restrict__ d_scales,
     float* __restrict__ d_quats, float* __restrict__ d_pose) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int s_q[kPbPer * 256];
   __shared__ int s_n;
   if (threadIdx.x == 0) s_n = 0;
@@ -369,7 +373,7 @@ void launch_project(const CamF& cam, int P, const float* means, const float* sca
                     int64_t* n_inst, cudaStream_t st) {
   if (P <= 0) return;
   GS_TRACE("k_project", st);
-  k_project<<<(P + 255) / 256, 256, 0, st>>>(cam, P, means, scales, quats, opacity, reinterpret_cast<float2*>(uv),
+  launch_pdl(k_project, (P + 255) / 256, 256, 0, st, cam, P, means, scales, quats, opacity, reinterpret_cast<float2*>(uv),
                                              reinterpret_cast<float4*>(co), depth, reinterpret_cast<int4*>(rect),
                                              touched, reinterpret_cast<unsigned long long*>(n_inst));
 }
@@ -379,7 +383,7 @@ void launch_project_bwd(const CamF& cam, int P, const float* means, const float*
                         float* d_scales, float* d_quats, float* d_pose, cudaStream_t st) {
   if (P <= 0) return;
   GS_TRACE("k_project_bwd", st);
-  k_project_bwd<<<(P + kPbPer * 256 - 1) / (kPbPer * 256), 256, 0, st>>>(cam, P, means, scales, quats,
+  launch_pdl(k_project_bwd, (P + kPbPer * 256 - 1) / (kPbPer * 256), 256, 0, st, cam, P, means, scales, quats,
                                                  reinterpret_cast<const float2*>(d_uv), d_conic, d_depth, d_means,
                                                  d_scales, d_quats, d_pose);
 }

@@ -186,6 +186,8 @@ __device__ __forceinline__ void load_feat_row(const void* feats, int bf16, int N
 
 template <int NC, bool VIS>
 __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int NCs = NC > 0 ? NC : 1;
   static_assert(NC % 2 == 0, "channels are blended in pairs");
   __shared__ float2 s_uv[kTilePix];
@@ -355,6 +357,8 @@ constexpr int kFwd2Threads = kTilePix / 2;
 
 template <int NC, bool VIS>
 __global__ void __launch_bounds__(kFwd2Threads, 5) k_render_fwd2(const FwdParams p) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int NCs = NC > 0 ? NC : 2;
   constexpr int kB = 2 * kFwd2Threads;  // Gaussians per shared-memory batch
   static_assert(NC % 2 == 0 && NC <= 16, "channels are blended in pairs; one 16-channel chunk");
@@ -928,6 +932,8 @@ __device__ __forceinline__ void finish_batch(BwdBatch& b, int i, int tx, int ty)
 // scaled by its class weight at the end, so W . G takes two products.
 template <int NC, bool L1>
 __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const BwdParams p) {
+  pdl_wait();
+  pdl_trigger();
   using namespace mma_bwd;
   using S = MmaBwdShape<NC>;
   constexpr int NT = S::NT, SR = S::SR, NCH = S::NCH, NG = S::NG;
@@ -1348,13 +1354,13 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
   GS_TRACE("k_render_fwd", st);
   const dim3 grid(tiles, N <= 16 ? 1 : (N + 31) / 32);
   if (visible) {
-    if (N <= 0) k_render_fwd2<0, true><<<grid, kFwd2Threads, 0, st>>>(p);
-    else if (N <= 16) k_render_fwd2<16, true><<<grid, kFwd2Threads, 0, st>>>(p);
-    else k_render_fwd<32, true><<<grid, kTilePix, 0, st>>>(p);
+    if (N <= 0) launch_pdl(k_render_fwd2<0, true>, grid, kFwd2Threads, 0, st, p);
+    else if (N <= 16) launch_pdl(k_render_fwd2<16, true>, grid, kFwd2Threads, 0, st, p);
+    else launch_pdl(k_render_fwd<32, true>, grid, kTilePix, 0, st, p);
   } else {
-    if (N <= 0) k_render_fwd2<0, false><<<grid, kFwd2Threads, 0, st>>>(p);
-    else if (N <= 16) k_render_fwd2<16, false><<<grid, kFwd2Threads, 0, st>>>(p);
-    else k_render_fwd<32, false><<<grid, kTilePix, 0, st>>>(p);
+    if (N <= 0) launch_pdl(k_render_fwd2<0, false>, grid, kFwd2Threads, 0, st, p);
+    else if (N <= 16) launch_pdl(k_render_fwd2<16, false>, grid, kFwd2Threads, 0, st, p);
+    else launch_pdl(k_render_fwd<32, false>, grid, kTilePix, 0, st, p);
   }
   return last_launch_status();
 }
@@ -1374,7 +1380,7 @@ gs_status launch_bwd_mma(const BwdParams& p, unsigned tiles, cudaStream_t st) {
       return GS_ERR_CUDA;
     attr_done.fetch_or(bit);
   }
-  k_render_bwd_mma<NC, L1><<<tiles, mma_bwd::kThreads, smem, st>>>(p);
+  launch_pdl(k_render_bwd_mma<NC, L1>, tiles, mma_bwd::kThreads, smem, st, p);
   return last_launch_status();
 }
 
