@@ -151,6 +151,20 @@ gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const float* depth
                              int32_t* tile_ranges, int64_t* n_instances, int32_t* status, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_tile_order -- a launch order for the compositing kernels: the tiles by
+ * descending length of their lists, so that the longest tiles start first
+ * and the shortest fill the end of the grid. The paper has no counterpart
+ * (a scheduling aid; no result depends on it).
+ * In:  tile_ranges [num_tiles,2] from gs_bin_sort.
+ * Out: tile_order [num_tiles] (int32), a permutation of 0..num_tiles-1 in
+ *      which the lengths fall in non-increasing buckets of 8 instances
+ *      (lengths of 8184 and more share the first bucket); the order within
+ *      a bucket is unspecified.
+ * The render calls take it as tile_order (NULL = tiles in index order).
+ */
+gs_status gs_tile_order(int32_t num_tiles, const int32_t* tile_ranges, int32_t* tile_order, void* stream);
+
+/* ---------------------------------------------------------------------------
  * gs_render_fwd -- front-to-back alpha compositing per pixel (Eq. 2-3).
  *
  * For pixel p in tile k, walking k's list in order with T = 1:
@@ -172,9 +186,12 @@ gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const float* depth
  * feature channels are computed per half tile as the product of a 128 x 32
  * weight matrix per step of 32 Gaussians (w = alpha T, rounded to bf16) and
  * the 32 x N bf16 feature rows on tcgen05 tensor cores, fp32 accumulation.
+ * tile_order: NULL, or a permutation of the tiles (gs_tile_order) giving the
+ * order in which tile blocks are launched; the outputs do not depend on it
+ * (in the adjoints, only the summation order of the per-tile float atomics).
  */
 gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges,
-                        const uint32_t* gids, const float* uv, const float* conic_opacity,
+                        const int32_t* tile_order, const uint32_t* gids, const float* uv, const float* conic_opacity,
                         const float* depth, const float* colors, const void* feats, int32_t N,
                         int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
                         float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
@@ -222,9 +239,9 @@ size_t gs_render_bwd_workspace_bytes(int32_t P);
 gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales,
                         const float* quats, const float* colors, const void* feats, int32_t N,
                         int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
-                        const int32_t* tile_ranges, const uint32_t* gids, const float* uv,
-                        const float* conic_opacity, const float* depth, const float* T_final,
-                        const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
+                        const int32_t* tile_ranges, const int32_t* tile_order, const uint32_t* gids,
+                        const float* uv, const float* conic_opacity, const float* depth,
+                        const float* T_final, const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
                         const float* dL_dalpha, const float* dL_dfeat, int32_t feat_grad_mode,
                         void* workspace, size_t workspace_bytes, float* d_means, float* d_scales,
                         float* d_quats, float* d_opacity, float* d_colors, float* d_feats,
@@ -261,7 +278,7 @@ typedef struct {
 } gs_l1_terms;
 
 gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_ranges,
-                           const uint32_t* gids, const float* uv, const float* conic_opacity,
+                           const int32_t* tile_order, const uint32_t* gids, const float* uv, const float* conic_opacity,
                            const float* depth, const float* colors, const void* feats, int32_t N,
                            int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
                            float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
@@ -271,9 +288,9 @@ gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_
 gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, const float* scales,
                            const float* quats, const float* colors, const void* feats, int32_t N,
                            int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
-                           const int32_t* tile_ranges, const uint32_t* gids, const float* uv,
-                           const float* conic_opacity, const float* depth, const float* T_final,
-                           const int32_t* last_idx, const gs_l1_terms* l1, const uint32_t* l1_signs,
+                           const int32_t* tile_ranges, const int32_t* tile_order, const uint32_t* gids,
+                           const float* uv, const float* conic_opacity, const float* depth,
+                           const float* T_final, const int32_t* last_idx, const gs_l1_terms* l1, const uint32_t* l1_signs,
                            void* workspace, size_t workspace_bytes, float* d_means, float* d_scales,
                            float* d_quats, float* d_opacity, float* d_colors, float* d_feats,
                            float* d_pose, int32_t* status, void* stream);

@@ -38,7 +38,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
-           "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1")
+           "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order")
 
 
 class GsffError(RuntimeError):
@@ -129,7 +129,9 @@ def lib():
     L.gs_bin_sort.restype = ctypes.c_int
     L.gs_bin_sort_static.argtypes = [cam_p, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_bin_sort_static.restype = ctypes.c_int
-    L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 7 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)
+    L.gs_tile_order.argtypes = [_i32, _vp, _vp, _vp]
+    L.gs_tile_order.restype = ctypes.c_int
+    L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 8 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)
     L.gs_render_fwd.restype = ctypes.c_int
     L.gs_visibility_iou.argtypes = [_i32, _vp, _vp, _vp, _vp]
     L.gs_visibility_iou.restype = ctypes.c_int
@@ -154,13 +156,13 @@ def lib():
     L.gs_sh_colors_bwd.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
     L.gs_render_bwd_workspace_bytes.restype = _sz
-    L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 11 +
+    L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 12 +
                                 [_i32, _vp, _sz] + [_vp] * 9)
     L.gs_render_bwd.restype = ctypes.c_int
-    L.gs_render_fwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 7 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
+    L.gs_render_fwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 8 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
                                    [ctypes.POINTER(GsL1Terms), _vp, _vp, _vp])
     L.gs_render_fwd_l1.restype = ctypes.c_int
-    L.gs_render_bwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 7 +
+    L.gs_render_bwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
                                    [ctypes.POINTER(GsL1Terms), _vp, _vp, _sz] + [_vp] * 9)
     L.gs_render_bwd_l1.restype = ctypes.c_int
     L.gs_l1_loss_grad.argtypes = [_i64, _vp, _vp, _f32, _vp, _vp, _vp]
@@ -236,8 +238,10 @@ def bin_sort_workspace_bytes(P: int, capacity: int, num_tiles: int) -> int:
     return int(lib().gs_bin_sort_workspace_bytes(P, capacity, num_tiles))
 
 
-def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=None):
-    """gs_bin_sort: returns dict(keys [cap] int64, gids [cap] int32, tile_ranges [T,2], n_instances [1])."""
+def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=None, tile_order=True):
+    """gs_bin_sort: returns dict(keys [cap] int64, gids [cap] int32, tile_ranges [T,2], n_instances [1]);
+    with tile_order also gs_tile_order's launch order of the tiles (tile_order [T] int32), which the
+    render calls then use."""
     P = proj["depth"].shape[0]
     dev = proj["depth"].device
     T = ((cam.width + TILE - 1) // TILE) * ((cam.height + TILE - 1) // TILE)
@@ -254,6 +258,11 @@ def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=
                              _ptr(proj["tiles_touched"]), int(capacity), _ptr(ws), ws.numel(), _ptr(o["keys"]),
                              _ptr(o["gids"]), _ptr(o["tile_ranges"]), _ptr(o["n_instances"]), _ptr(st),
                              _stream(stream)), "gs_bin_sort")
+    if tile_order:
+        if o.get("tile_order") is None:
+            o["tile_order"] = torch.empty(T, dtype=torch.int32, device=dev)
+        _check(lib().gs_tile_order(T, _ptr(o["tile_ranges"]), _ptr(o["tile_order"]), _stream(stream)),
+               "gs_tile_order")
     o["status"] = st
     return o
 
@@ -285,7 +294,8 @@ def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT
     bgc = (ctypes.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
     st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
     c = camera_struct(cam)
-    args = (ctypes.byref(c), P, _ptr(sort["tile_ranges"]), _ptr(sort["gids"]), _ptr(proj["uv"]),
+    args = (ctypes.byref(c), P, _ptr(sort["tile_ranges"]), _ptr(sort.get("tile_order")), _ptr(sort["gids"]),
+            _ptr(proj["uv"]),
             _ptr(proj["conic_opacity"]), _ptr(proj["depth"]), _ptr(colors), _ptr(feats) if feat_on else None,
             N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(o["rgb"]), _ptr(o["depth"]),
             _ptr(o["alpha"]), _ptr(o.get("feat")) if feat_on else None, _ptr(o["T_final"]), _ptr(o["last_idx"]),
@@ -445,6 +455,7 @@ def render_bwd(cam, means, scales, quats, colors, feats, proj, sort, fwd, g_rgb=
     _check(lib().gs_render_bwd(
         ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(colors), _ptr(feats) if feat_on else None,
         N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(sort["tile_ranges"]),
+        _ptr(sort.get("tile_order")),
         _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
         _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), _ptr(g_rgb), _ptr(g_depth), _ptr(g_alpha),
         _ptr(g_feat) if feat_on else None, GS_FEAT_GRAD_COUPLED if coupled else GS_FEAT_GRAD_DECOUPLED,
@@ -481,6 +492,7 @@ def render_bwd_l1(cam, means, scales, quats, colors, feats, proj, sort, fwd, wei
     _check(lib().gs_render_bwd_l1(
         ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(colors), _ptr(feats) if feat_on else None,
         N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(sort["tile_ranges"]),
+        _ptr(sort.get("tile_order")),
         _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
         _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), ctypes.byref(terms), _ptr(fwd["l1_signs"]), _ptr(ws), ws.numel(),
         _ptr(g.get("means")), _ptr(g.get("scales")), _ptr(g.get("quats")), _ptr(g.get("opacity")),
@@ -569,6 +581,7 @@ class Rasterizer:
         self.sort = dict(keys=torch.empty(self.capacity, dtype=torch.int64, device=dev),
                          gids=torch.empty(self.capacity, dtype=torch.int32, device=dev),
                          tile_ranges=torch.empty(self.T, 2, dtype=torch.int32, device=dev),
+                         tile_order=torch.empty(self.T, dtype=torch.int32, device=dev),
                          n_instances=torch.zeros(1, dtype=torch.int64, device=dev))
 
     def ensure_capacity(self, cam, means, scales, quats, opacity, slack=1.25):

@@ -552,4 +552,63 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   return last_launch_status();
 }
 
+// ---------------------------------------------------------------------------
+// Launch order of the compositing kernels' tile blocks: tiles by descending
+// list length, as a counting sort over buckets of 8 instances in one block
+// (a histogram in shared memory, a block scan, then a scatter through one
+// cursor per bucket, whose order within a bucket follows the atomics).
+namespace {
+constexpr int kToThreads = 1024;
+constexpr int kToBuckets = 1024;  // one per thread
+constexpr int kToShift = 3;       // 8 instances per bucket
+static_assert(kToBuckets == kToThreads, "one bucket per thread in the scan");
+
+__device__ __forceinline__ int tile_bucket(int2 r) {
+  return (kToBuckets - 1) - min((r.y - r.x) >> kToShift, kToBuckets - 1);
+}
+
+__global__ void __launch_bounds__(kToThreads) k_tile_order(const int2* __restrict__ ranges, int T,
+                                                          int32_t* __restrict__ order) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ int s_h[kToBuckets];
+  __shared__ int s_w[kToThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  s_h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += kToThreads) atomicAdd(&s_h[tile_bucket(ranges[t])], 1);
+  __syncthreads();
+  // exclusive scan of the bucket counts: warps, then the warp totals
+  const int v = s_h[threadIdx.x];
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const int w = s_w[lane];
+    int xw = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, xw, o);
+      if (lane >= o) xw += y;
+    }
+    s_w[lane] = xw - w;
+  }
+  __syncthreads();
+  s_h[threadIdx.x] = s_w[wid] + x - v;
+  __syncthreads();
+  for (int t = threadIdx.x; t < T; t += kToThreads) order[atomicAdd(&s_h[tile_bucket(ranges[t])], 1)] = t;
+}
+}  // namespace
+
+gs_status launch_tile_order(int T, const int32_t* ranges, int32_t* order, cudaStream_t st) {
+  GS_TRACE("k_tile_order", st);
+  launch_pdl(k_tile_order, 1, kToThreads, 0, st, reinterpret_cast<const int2*>(ranges), T, order);
+  return last_launch_status();
+}
+
 }  // namespace gsff

@@ -39,6 +39,7 @@ namespace {
 struct FwdParams {
   CamF cam;
   const int2* ranges;
+  const int* order;  // launch order of the tiles, or null
   const uint32_t* gids;
   const float2* uv;
   const float4* co;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
   __shared__ uint32_t s_gid[VIS ? kTilePix : 1];
   __shared__ float s_lsum;
 
-  const int tile = blockIdx.x;
+  const int tile = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int chunk = blockIdx.y;
   const bool geom = chunk == 0;
   const bool mark = VIS && geom;
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(kFwd2Threads, 5) k_render_fwd2(const FwdParams
   __shared__ uint32_t s_gid[VIS ? kB : 1];
   __shared__ float s_lsum;
 
-  const int tile = blockIdx.x;
+  const int tile = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   if (threadIdx.x == 0) s_lsum = 0.f;
   const unsigned lanes_below = (1u << (threadIdx.x & 31)) - 1u;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
@@ -575,6 +576,7 @@ __global__ void __launch_bounds__(kFwd2Threads, 5) k_render_fwd2(const FwdParams
 struct BwdParams {
   CamF cam;
   const int2* ranges;
+  const int* order;  // launch order of the tiles, or null
   const uint32_t* gids;
   const float2* uv;
   const float4* co;
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
   __shared__ uint32_t s_gid[BB];
   __shared__ int s_maxlast;
 
-  const int tile = blockIdx.x;
+  const int tile = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int chunk = blockIdx.y;
   const bool geom = chunk == 0;
   const int c0 = chunk * NC;
@@ -945,7 +947,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   __shared__ BwdBatch s_b[kNBuf];
   __shared__ int s_maxlast;
 
-  const int tile = blockIdx.x;
+  const int tile = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g8 = lane >> 2, t4 = lane & 3;  // MMA fragment row group and column pair
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
@@ -1322,7 +1324,8 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
 
 }  // namespace
 
-gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
+                            const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
@@ -1332,6 +1335,7 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const uint32
   if (p.l1.on && N > 16) return GS_ERR_UNSUPPORTED;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.order = order;
   p.gids = gids;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);
@@ -1384,7 +1388,8 @@ gs_status launch_bwd_mma(const BwdParams& p, unsigned tiles, cudaStream_t st) {
   return last_launch_status();
 }
 
-gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
+                            const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
                             const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
@@ -1395,6 +1400,7 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const uint32
   if (p.l1.on && (N > 16 || coupled)) return GS_ERR_UNSUPPORTED;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.order = order;
   p.gids = gids;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);

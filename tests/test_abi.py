@@ -55,6 +55,9 @@ def test_invalid_arguments_rejected_synchronously(built):
     assert L.gs_bin_sort(ctypes.byref(cam), 5, None, None, None, 0, None, 0, None, None, None, None, None,
                          None) == g.GS_ERR_INVALID_ARG
     assert L.gs_l1_loss_grad(-1, None, None, 1.0, None, None, None) == g.GS_ERR_INVALID_ARG
+    assert L.gs_tile_order(-1, None, None, None) == g.GS_ERR_INVALID_ARG
+    assert L.gs_tile_order(4, None, None, None) == g.GS_ERR_INVALID_ARG
+    assert L.gs_tile_order(0, None, None, None) == g.GS_OK
 
 
 def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
