@@ -280,27 +280,35 @@ def run_ours(args, rank, world, local_rank):
     d2h = 6 * 4 + 4
 
     side = torch.cuda.Stream(device=dev)
+    params_in = torch.cuda.Event()
     tgt_ready = torch.cuda.Event()
 
     def e2e_step(k):
-        # the frame's targets are copied on a side stream, overlapped with the
-        # parameter copy, projection and binning; compositing waits for them
-        side.wait_stream(stream)
+        # The host-to-device link (~210 GB/s) carries 101 MB per step, so the
+        # copies are ordered by need: the Gaussian parameters first, then the
+        # frame's targets on a side stream while projection, binning and the
+        # forward walk run; the L1 pass over the rendered images (gs_l1_signs,
+        # the fused epilogue's terms as a separate pass) waits for them.
+        for d, h in zip(d_params, host_params):
+            d.copy_(h, non_blocking=True)
+        params_in.record(stream)
+        side.wait_event(params_in)
         with torch.cuda.stream(side):
             for n in ("rgb", "depth", "feat"):
                 d_tgt[n].copy_(host_tgt[k][n], non_blocking=True)
             tgt_ready.record(side)
-        for d, h in zip(d_params, host_params):
-            d.copy_(h, non_blocking=True)
         cam = frame_camera(k)
         m, s_, q, o, c, f = d_params
         loss.zero_()
-        ras.forward(cam, m, s_, q, o, c, f, l1_targets=d_tgt, l1_weights=scales_l1, l1_loss=loss,
-                    wait_event=tgt_ready)
+        ras.forward(cam, m, s_, q, o, c, f)
+        ras.l1_loss(cam, d_tgt, scales_l1, loss, wait_event=tgt_ready)
         gr = ras.backward_l1(cam, m, s_, q, c, f, scales_l1)
         out_pose.copy_(gr["pose"], non_blocking=True)
         out_loss.copy_(loss, non_blocking=True)
 
+    for i in range(args.warmup):
+        e2e_step(e2e_frames[i % len(e2e_frames)])
+    torch.cuda.synchronize()
     e2e_ms = []
     for i in range(args.steps):
         k = e2e_frames[i % len(e2e_frames)]

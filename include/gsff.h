@@ -296,6 +296,22 @@ gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, 
                            float* d_pose, int32_t* status, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_l1_signs -- the L1 terms of gs_render_fwd_l1 as a separate pass over
+ * images that gs_render_fwd rendered: adds L to *l1->loss (the caller zeroes
+ * it; may be NULL) and writes l1_signs [H*W][2] exactly as gs_render_fwd_l1
+ * writes them for the same images (each image holds the value the fused
+ * epilogue compares), for gs_render_bwd_l1. The paper has no counterpart:
+ * with targets still being copied from the host, the forward can run
+ * before they arrive and only this pass waits for them.
+ * rgb [3,H,W], depth [H,W], feat [N,H,W] (CHW) or [H,W,N] (HWC), N <= 16
+ * (GS_ERR_UNSUPPORTED above; 0 = no feature term); an image may be NULL when
+ * its target is NULL.
+ */
+gs_status gs_l1_signs(int32_t width, int32_t height, int32_t N, int32_t layout, const float* rgb,
+                      const float* depth, const float* feat, const gs_l1_terms* l1, uint32_t* l1_signs,
+                      void* stream);
+
+/* ---------------------------------------------------------------------------
  * gs_l1_loss_grad -- the L1 photometric term of the tracking and mapping
  * losses (Eq. 5, Eq. 7): grad[i] = scale * sign(pred[i] - target[i]) (sign(0)
  * = 0) and *loss_sum += scale * sum |pred - target| (device float, atomic).

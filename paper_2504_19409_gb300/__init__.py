@@ -38,7 +38,8 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_bin_sort_static", "gs_decoder_workspace_bytes", "gs_decoder_fwd", "gs_decoder_train",
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
-           "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order")
+           "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
+           "gs_l1_signs")
 
 
 class GsffError(RuntimeError):
@@ -165,6 +166,8 @@ def lib():
     L.gs_render_bwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
                                    [ctypes.POINTER(GsL1Terms), _vp, _vp, _sz] + [_vp] * 9)
     L.gs_render_bwd_l1.restype = ctypes.c_int
+    L.gs_l1_signs.argtypes = [_i32, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(GsL1Terms), _vp, _vp]
+    L.gs_l1_signs.restype = ctypes.c_int
     L.gs_l1_loss_grad.argtypes = [_i64, _vp, _vp, _f32, _vp, _vp, _vp]
     L.gs_l1_loss_grad.restype = ctypes.c_int
     L.gs_trace_enable.argtypes = [_i32]
@@ -424,6 +427,21 @@ def visibility_iou(vis_a, vis_b, counts=None, stream=None):
     return c
 
 
+def l1_signs(cam, fwd, l1_targets, l1_weights, l1_loss=None, layout=GS_LAYOUT_CHW, stream=None):
+    """gs_l1_signs: the L1 terms of render_fwd(..., l1_targets=...) as a pass over the images of a plain
+    render_fwd (fwd), for targets that arrive after the forward ran: adds the loss to l1_loss and leaves
+    the cotangent signs in fwd["l1_signs"] for render_bwd_l1, exactly as the fused forward would."""
+    H, W = cam.height, cam.width
+    feat = fwd.get("feat")
+    N = 0 if feat is None else (feat.shape[0] if layout == GS_LAYOUT_CHW else feat.shape[2])
+    if fwd.get("l1_signs") is None:
+        fwd["l1_signs"] = torch.empty(H * W, 2, dtype=torch.int32, device=fwd["rgb"].device)
+    terms = l1_terms({k: v for k, v in l1_targets.items() if N > 0 or k != "feat"}, l1_weights, l1_loss)
+    _check(lib().gs_l1_signs(W, H, N, layout, _ptr(fwd["rgb"]), _ptr(fwd["depth"]), _ptr(feat), ctypes.byref(terms),
+                             _ptr(fwd["l1_signs"]), _stream(stream)), "gs_l1_signs")
+    return fwd
+
+
 def render_bwd_workspace_bytes(P: int) -> int:
     return int(lib().gs_render_bwd_workspace_bytes(P))
 
@@ -619,6 +637,16 @@ class Rasterizer:
                    g_feat, flags=self.flags, layout=self.layout, bg=bg, coupled=coupled, grads=self.grads,
                    workspace=self.bwd_ws, status=self.status, stream=stream)
         return self.grads
+
+    def l1_loss(self, cam, l1_targets, l1_weights, l1_loss=None, wait_event=None, stream=None):
+        """The L1 terms of the last forward's images (gs_l1_signs), for targets copied while the forward
+        ran: waits for wait_event (an event or a list of them) first; backward_l1 then differentiates it."""
+        if wait_event is not None:
+            st = stream if stream is not None else torch.cuda.current_stream(self.device)
+            for ev in (wait_event if isinstance(wait_event, (list, tuple)) else (wait_event,)):
+                st.wait_event(ev)
+        l1_signs(cam, self.fwd, l1_targets, l1_weights, l1_loss, layout=self.layout, stream=stream)
+        return self.fwd
 
     def backward_l1(self, cam, means, scales, quats, colors, feats, weights, bg=None, zero=True, stream=None):
         """The adjoint of the L1 loss that the last forward(..., l1_targets=...) evaluated

@@ -112,6 +112,49 @@ __global__ void __launch_bounds__(256) k_l1_grad(long long n, const float* __res
   }
 }
 
+// The L1 terms of gs_render_fwd_l1's epilogue as a pass over rendered images,
+// one thread per pixel: the same differences pred - target (the images hold
+// the epilogue's values), hence the same sign words; the loss adds w |d| per
+// term, summed per block and added with one atomic.
+__global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, const float* __restrict__ rgb,
+                                                  const float* __restrict__ depth, const float* __restrict__ feat,
+                                                  const L1Fwd l1) {
+  pdl_wait();
+  pdl_trigger();
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float lsum = 0.f;
+  if (pix < HW) {
+    uint32_t nz = 0, ng = 0;
+    auto term = [&](float pred, float target, float w, int bit) {
+      const float d = pred - target;
+      lsum += w * fabsf(d);
+      nz |= (d != 0.f ? 1u : 0u) << bit;
+      ng |= (d < 0.f ? 1u : 0u) << bit;
+    };
+    if (l1.target[0])
+      for (int c = 0; c < 3; ++c) term(rgb[c * HW + pix], l1.target[0][c * HW + pix], l1.w[0], kL1BitRgb + c);
+    if (l1.target[1]) term(depth[pix], l1.target[1][pix], l1.w[1], kL1BitDepth);
+    if (l1.target[2])
+      for (int c = 0; c < N; ++c) {
+        const long long i = hwc ? pix * N + c : c * HW + pix;
+        term(feat[i], l1.target[2][i], l1.w[2], c);
+      }
+    l1.signs[pix] = make_uint2(nz, ng);
+  }
+  if (l1.loss) {
+    __shared__ float s_part[8];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b = 0.f;
+      for (int w = 0; w < 8; ++w) b += s_part[w];
+      if (b != 0.f) atomicAdd(l1.loss, b);
+    }
+  }
+}
+
 // counts[0] += |{g : a_g != 0 and b_g != 0}|, counts[1] += |{g : a_g != 0 or b_g != 0}|.
 __global__ void __launch_bounds__(256) k_vis_iou(int P, const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
                                                  unsigned long long* __restrict__ counts) {
@@ -409,6 +452,30 @@ gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, flo
   if (blocks > 152 * 16) blocks = 152 * 16;
   GS_TRACE("k_l1_grad", S(stream));
   k_l1_grad<<<(unsigned)blocks, 256, 0, S(stream)>>>(n, pred, target, scale, grad, loss_sum, vec);
+  return last_launch_status();
+}
+
+gs_status gs_l1_signs(int32_t width, int32_t height, int32_t N, int32_t layout, const float* rgb, const float* depth,
+                      const float* feat, const gs_l1_terms* l1, uint32_t* l1_signs, void* stream) {
+  if (width <= 0 || height <= 0 || N < 0 || !l1 || !l1_signs || !aligned(l1_signs, 8)) return GS_ERR_INVALID_ARG;
+  if (layout != GS_LAYOUT_CHW && layout != GS_LAYOUT_HWC) return GS_ERR_INVALID_ARG;
+  if (N > 16) return GS_ERR_UNSUPPORTED;
+  if ((l1->target_rgb && !rgb) || (l1->target_depth && !depth) || (N > 0 && l1->target_feat && !feat))
+    return GS_ERR_INVALID_ARG;
+  L1Fwd in{};
+  in.on = 1;
+  in.target[0] = l1->target_rgb;
+  in.target[1] = l1->target_depth;
+  in.target[2] = N > 0 ? l1->target_feat : nullptr;
+  in.w[0] = l1->w_rgb;
+  in.w[1] = l1->w_depth;
+  in.w[2] = l1->w_feat;
+  in.loss = l1->loss;
+  in.signs = reinterpret_cast<uint2*>(l1_signs);
+  const long long HW = (long long)width * height;
+  GS_TRACE("k_l1_signs", S(stream));
+  launch_pdl(k_l1_signs, (unsigned)((HW + 255) / 256), 256, 0, S(stream), HW, N, layout == GS_LAYOUT_HWC ? 1 : 0, rgb,
+             depth, feat, in);
   return last_launch_status();
 }
 

@@ -168,3 +168,36 @@ def test_fused_l1_rejects_unsupported(gs, sg):
     fw["l1_signs"] = torch.zeros(cam.height * cam.width, 2, dtype=torch.int32, device="cuda")
     with pytest.raises(gs.GsffError):
         gs.render_bwd_l1(cam, means, scales, quats, cols, feats, proj, srt, fw, {"rgb": 1.0})
+
+
+@pytest.mark.parametrize("case", ["chw_bg", "hwc", "features_off", "rgb_only", "n5_chw", "n8_hwc", "room"])
+def test_separate_l1_pass_equals_fused_epilogue(gs, sg, case):
+    """gs_l1_signs over a plain forward's images writes the fused forward's
+    sign words bit for bit (the same binary32 differences) and the same loss
+    to 1e-5 (fp32 sums in another order); the adjoint from its words then
+    equals the fused pair's."""
+    N = {"features_off": 0, "n5_chw": 5, "n8_hwc": 8}.get(case, 16)
+    if case == "room":
+        sc, _ = sg.room_case()
+        cam = sg.room_trajectory(11).as_f32()
+    else:
+        sc, cam = sg.small_case(seed=4, N=N)
+        cam = cam.as_f32()
+    layout = gs.GS_LAYOUT_HWC if case in ("hwc", "n8_hwc") else gs.GS_LAYOUT_CHW
+    bg = (0.1, 0.3, 0.2) if case == "chw_bg" else None
+    args, proj, srt, fw = _setup(gs, cam, sc, layout, bg)
+    targets = _targets(fw, np.random.default_rng(70 + len(case)), drop=("depth", "feat") if case == "rgb_only" else ())
+    HW = cam.width * cam.height
+    weights = {"rgb": 0.9 / (3 * HW), "depth": 0.1 / HW, "feat": 1.0 / (max(N, 1) * HW)}
+    got, loss, fw2 = _fused(gs, cam, args, proj, srt, targets, weights, layout, bg)
+    loss_sep = torch.zeros(1, device="cuda")
+    gs.l1_signs(cam, fw, targets, weights, loss_sep, layout=layout)
+    means, scales, quats, cols, feats = args
+    sep = gs.render_bwd_l1(cam, means, scales, quats, cols, feats, proj, srt, fw, weights, layout=layout, bg=bg)
+    torch.cuda.synchronize()
+    assert torch.equal(fw["l1_signs"], fw2["l1_signs"])
+    assert abs(loss_sep.item() - loss.item()) <= 1e-5 * loss.item()
+    for k in CLASSES:
+        if k == "feats" and N == 0:
+            continue
+        assert _normwise(sep[k], got[k]) <= 1e-6, k
