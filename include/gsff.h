@@ -189,9 +189,17 @@ gs_status gs_tile_order(int32_t num_tiles, const int32_t* tile_ranges, int32_t* 
  * tile_order: NULL, or a permutation of the tiles (gs_tile_order) giving the
  * order in which tile blocks are launched; the outputs do not depend on it
  * (in the adjoints, only the summation order of the per-tile float atomics).
+ * inst_masks: NULL, or [capacity] bytes indexed like gids: for every instance
+ * it loads, the forward writes which of the tile's four 8x8 pixel blocks the
+ * instance's Gaussian can reach (bit b: block b, 2 across by 2 down; the
+ * conservative alpha >= 1/255 test). gs_render_bwd of the same frame (same
+ * projection, lists and forward) reads them instead of testing again; its
+ * masks must come from that forward (NULL there: computed in the adjoint).
+ * They change no result, only which pixel blocks skip a Gaussian.
  */
 gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges,
-                        const int32_t* tile_order, const uint32_t* gids, const float* uv, const float* conic_opacity,
+                        const int32_t* tile_order, const uint32_t* gids, uint8_t* inst_masks,
+                        const float* uv, const float* conic_opacity,
                         const float* depth, const float* colors, const void* feats, int32_t N,
                         int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
                         float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
@@ -240,7 +248,7 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
                         const float* quats, const float* colors, const void* feats, int32_t N,
                         int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
                         const int32_t* tile_ranges, const int32_t* tile_order, const uint32_t* gids,
-                        const float* uv, const float* conic_opacity, const float* depth,
+                        const uint8_t* inst_masks, const float* uv, const float* conic_opacity, const float* depth,
                         const float* T_final, const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
                         const float* dL_dalpha, const float* dL_dfeat, int32_t feat_grad_mode,
                         void* workspace, size_t workspace_bytes, float* d_means, float* d_scales,
@@ -278,7 +286,8 @@ typedef struct {
 } gs_l1_terms;
 
 gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_ranges,
-                           const int32_t* tile_order, const uint32_t* gids, const float* uv, const float* conic_opacity,
+                           const int32_t* tile_order, const uint32_t* gids, uint8_t* inst_masks,
+                           const float* uv, const float* conic_opacity,
                            const float* depth, const float* colors, const void* feats, int32_t N,
                            int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
                            float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
@@ -289,7 +298,8 @@ gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, 
                            const float* quats, const float* colors, const void* feats, int32_t N,
                            int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
                            const int32_t* tile_ranges, const int32_t* tile_order, const uint32_t* gids,
-                           const float* uv, const float* conic_opacity, const float* depth,
+                           const uint8_t* inst_masks, const float* uv, const float* conic_opacity,
+                           const float* depth,
                            const float* T_final, const int32_t* last_idx, const gs_l1_terms* l1, const uint32_t* l1_signs,
                            void* workspace, size_t workspace_bytes, float* d_means, float* d_scales,
                            float* d_quats, float* d_opacity, float* d_colors, float* d_feats,

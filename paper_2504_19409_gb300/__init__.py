@@ -132,7 +132,7 @@ def lib():
     L.gs_bin_sort_static.restype = ctypes.c_int
     L.gs_tile_order.argtypes = [_i32, _vp, _vp, _vp]
     L.gs_tile_order.restype = ctypes.c_int
-    L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 8 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)
+    L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 9 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)
     L.gs_render_fwd.restype = ctypes.c_int
     L.gs_visibility_iou.argtypes = [_i32, _vp, _vp, _vp, _vp]
     L.gs_visibility_iou.restype = ctypes.c_int
@@ -157,13 +157,13 @@ def lib():
     L.gs_sh_colors_bwd.restype = ctypes.c_int
     L.gs_render_bwd_workspace_bytes.argtypes = [_i32]
     L.gs_render_bwd_workspace_bytes.restype = _sz
-    L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 12 +
+    L.gs_render_bwd.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 13 +
                                 [_i32, _vp, _sz] + [_vp] * 9)
     L.gs_render_bwd.restype = ctypes.c_int
-    L.gs_render_fwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 8 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
+    L.gs_render_fwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 9 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
                                    [ctypes.POINTER(GsL1Terms), _vp, _vp, _vp])
     L.gs_render_fwd_l1.restype = ctypes.c_int
-    L.gs_render_bwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 8 +
+    L.gs_render_bwd_l1.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 9 +
                                    [ctypes.POINTER(GsL1Terms), _vp, _vp, _sz] + [_vp] * 9)
     L.gs_render_bwd_l1.restype = ctypes.c_int
     L.gs_l1_signs.argtypes = [_i32, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(GsL1Terms), _vp, _vp]
@@ -243,8 +243,9 @@ def bin_sort_workspace_bytes(P: int, capacity: int, num_tiles: int) -> int:
 
 def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=None, tile_order=True):
     """gs_bin_sort: returns dict(keys [cap] int64, gids [cap] int32, tile_ranges [T,2], n_instances [1]);
-    with tile_order also gs_tile_order's launch order of the tiles (tile_order [T] int32), which the
-    render calls then use."""
+    with tile_order also gs_tile_order's launch order of the tiles (tile_order [T] int32); and
+    inst_masks [cap] uint8, where the forward leaves each instance's pixel-block skip mask for the
+    adjoint of the same frame. The render calls use both."""
     P = proj["depth"].shape[0]
     dev = proj["depth"].device
     T = ((cam.width + TILE - 1) // TILE) * ((cam.height + TILE - 1) // TILE)
@@ -261,6 +262,8 @@ def bin_sort(cam, proj, capacity, workspace=None, out=None, status=None, stream=
                              _ptr(proj["tiles_touched"]), int(capacity), _ptr(ws), ws.numel(), _ptr(o["keys"]),
                              _ptr(o["gids"]), _ptr(o["tile_ranges"]), _ptr(o["n_instances"]), _ptr(st),
                              _stream(stream)), "gs_bin_sort")
+    if o.get("inst_masks") is None:
+        o["inst_masks"] = torch.empty(capacity, dtype=torch.uint8, device=dev)
     if tile_order:
         if o.get("tile_order") is None:
             o["tile_order"] = torch.empty(T, dtype=torch.int32, device=dev)
@@ -298,7 +301,7 @@ def render_fwd(cam, proj, sort, colors, feats=None, flags=None, layout=GS_LAYOUT
     st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
     c = camera_struct(cam)
     args = (ctypes.byref(c), P, _ptr(sort["tile_ranges"]), _ptr(sort.get("tile_order")), _ptr(sort["gids"]),
-            _ptr(proj["uv"]),
+            _ptr(sort.get("inst_masks")), _ptr(proj["uv"]),
             _ptr(proj["conic_opacity"]), _ptr(proj["depth"]), _ptr(colors), _ptr(feats) if feat_on else None,
             N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(o["rgb"]), _ptr(o["depth"]),
             _ptr(o["alpha"]), _ptr(o.get("feat")) if feat_on else None, _ptr(o["T_final"]), _ptr(o["last_idx"]),
@@ -474,7 +477,7 @@ def render_bwd(cam, means, scales, quats, colors, feats, proj, sort, fwd, g_rgb=
         ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(colors), _ptr(feats) if feat_on else None,
         N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(sort["tile_ranges"]),
         _ptr(sort.get("tile_order")),
-        _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
+        _ptr(sort["gids"]), _ptr(sort.get("inst_masks")), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
         _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), _ptr(g_rgb), _ptr(g_depth), _ptr(g_alpha),
         _ptr(g_feat) if feat_on else None, GS_FEAT_GRAD_COUPLED if coupled else GS_FEAT_GRAD_DECOUPLED,
         _ptr(ws), ws.numel(), _ptr(g.get("means")), _ptr(g.get("scales")), _ptr(g.get("quats")),
@@ -511,7 +514,7 @@ def render_bwd_l1(cam, means, scales, quats, colors, feats, proj, sort, fwd, wei
         ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(colors), _ptr(feats) if feat_on else None,
         N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(sort["tile_ranges"]),
         _ptr(sort.get("tile_order")),
-        _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
+        _ptr(sort["gids"]), _ptr(sort.get("inst_masks")), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]), _ptr(proj["depth"]),
         _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), ctypes.byref(terms), _ptr(fwd["l1_signs"]), _ptr(ws), ws.numel(),
         _ptr(g.get("means")), _ptr(g.get("scales")), _ptr(g.get("quats")), _ptr(g.get("opacity")),
         _ptr(g.get("colors")), _ptr(g["feats"]) if feat_on else None, _ptr(g["pose"]), _ptr(st), _stream(stream)),
@@ -600,6 +603,7 @@ class Rasterizer:
                          gids=torch.empty(self.capacity, dtype=torch.int32, device=dev),
                          tile_ranges=torch.empty(self.T, 2, dtype=torch.int32, device=dev),
                          tile_order=torch.empty(self.T, dtype=torch.int32, device=dev),
+                         inst_masks=torch.empty(self.capacity, dtype=torch.uint8, device=dev),
                          n_instances=torch.zeros(1, dtype=torch.int64, device=dev))
 
     def ensure_capacity(self, cam, means, scales, quats, opacity, slack=1.25):

@@ -21,13 +21,13 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
                           int32_t* ranges, int64_t* n_out, int32_t* status, cudaStream_t st);
 gs_status launch_tile_order(int T, const int32_t* ranges, int32_t* order, cudaStream_t st);
 gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                            const float* uv,
+                            uint8_t* masks, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
                             int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1, cudaStream_t st);
 gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                            const float* uv,
+                            const uint8_t* masks, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
                             const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
@@ -264,7 +264,7 @@ gs_status gs_tile_order(int32_t num_tiles, const int32_t* tile_ranges, int32_t* 
 
 namespace {
 gs_status render_fwd_impl(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const int32_t* tile_order,
-                          const uint32_t* gids,
+                          const uint32_t* gids, uint8_t* inst_masks,
                           const float* uv, const float* conic_opacity, const float* depth, const float* colors,
                           const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
                           const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
@@ -290,7 +290,7 @@ gs_status render_fwd_impl(const gs_camera* cam, int32_t P, const int32_t* tile_r
     if (l1) return GS_ERR_UNSUPPORTED;
     if (feat_dtype != GS_BF16 || layout != GS_LAYOUT_HWC || N % 64 != 0 || N > 512) return GS_ERR_UNSUPPORTED;
     // geometry channels and the saved state on the SIMT kernel, features on tcgen05
-    gs_status st = launch_render_fwd(k, tile_ranges, tile_order, gids, uv, conic_opacity, depth, colors, nullptr, 0,
+    gs_status st = launch_render_fwd(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, nullptr, 0,
                                      0, 1, b,
                                      out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, visible,
                                      nullptr, S(stream));
@@ -300,26 +300,26 @@ gs_status render_fwd_impl(const gs_camera* cam, int32_t P, const int32_t* tile_r
                                 S(stream));
   }
   if (l1 && n > 16) return GS_ERR_UNSUPPORTED;
-  return launch_render_fwd(k, tile_ranges, tile_order, gids, uv, conic_opacity, depth, colors, feats, n,
+  return launch_render_fwd(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, n,
                            feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, out_rgb, out_depth, out_alpha, out_feat,
                            T_final, last_idx, n_contrib, visible, l1, S(stream));
 }
 }  // namespace
 
 gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const int32_t* tile_order,
-                        const uint32_t* gids,
+                        const uint32_t* gids, uint8_t* inst_masks,
                         const float* uv, const float* conic_opacity, const float* depth, const float* colors,
                         const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
                         const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
                         float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
                         int32_t* status, void* stream) {
-  return render_fwd_impl(cam, P, tile_ranges, tile_order, gids, uv, conic_opacity, depth, colors, feats, N, feat_dtype, layout,
+  return render_fwd_impl(cam, P, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, N, feat_dtype, layout,
                          flags, bg, out_rgb, out_depth, out_alpha, out_feat, T_final, last_idx, n_contrib, visible,
                          nullptr, status, stream);
 }
 
 gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const int32_t* tile_order,
-                           const uint32_t* gids,
+                           const uint32_t* gids, uint8_t* inst_masks,
                            const float* uv, const float* conic_opacity, const float* depth, const float* colors,
                            const void* feats, int32_t N, int32_t feat_dtype, int32_t layout, int32_t flags,
                            const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
@@ -337,7 +337,7 @@ gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_
   in.w[2] = l1->w_feat;
   in.loss = l1->loss;
   in.signs = reinterpret_cast<uint2*>(l1_signs);
-  return render_fwd_impl(cam, P, tile_ranges, tile_order, gids, uv, conic_opacity, depth, colors, feats, N, feat_dtype, layout,
+  return render_fwd_impl(cam, P, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, N, feat_dtype, layout,
                          flags, bg, out_rgb, out_depth, out_alpha, out_feat, T_final, last_idx, n_contrib, visible,
                          &in, status, stream);
 }
@@ -352,8 +352,8 @@ namespace {
 gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, const float* scales,
                           const float* quats, const float* colors, const void* feats, int32_t N, int32_t feat_dtype,
                           int32_t layout, int32_t flags, const float* bg, const int32_t* tile_ranges,
-                          const int32_t* tile_order, const uint32_t* gids, const float* uv,
-                          const float* conic_opacity, const float* depth, const float* T_final,
+                          const int32_t* tile_order, const uint32_t* gids, const uint8_t* inst_masks,
+                          const float* uv, const float* conic_opacity, const float* depth, const float* T_final,
                           const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
                           const float* dL_dalpha, const float* dL_dfeat, const L1Bwd* l1, int32_t feat_grad_mode,
                           void* workspace, size_t workspace_bytes, float* d_means, float* d_scales, float* d_quats,
@@ -391,7 +391,7 @@ gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, c
   if (cudaMemsetAsync(workspace, 0, gs_render_bwd_workspace_bytes(P), S(stream)) != cudaSuccess) return GS_ERR_CUDA;
   // with the tensor-core form the SIMT adjoint does the geometry only and the
   // feature gradient is a tcgen05 contraction
-  gs_status st = launch_render_bwd(k, tile_ranges, tile_order, gids, uv, conic_opacity, depth, colors, feats, tc ? 0 : n,
+  gs_status st = launch_render_bwd(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, tc ? 0 : n,
                                    feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, T_final, last_idx, dL_drgb,
                                    dL_ddepth, dL_dalpha, (feat_on && !tc) ? dL_dfeat : nullptr, coupled ? 1 : 0, w_uv,
                                    w_conic, w_depth, d_opacity, d_colors, d_feats, l1, S(stream));
@@ -409,14 +409,14 @@ gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, c
 gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales, const float* quats,
                         const float* colors, const void* feats, int32_t N, int32_t feat_dtype, int32_t layout,
                         int32_t flags, const float* bg, const int32_t* tile_ranges, const int32_t* tile_order,
-                        const uint32_t* gids, const float* uv, const float* conic_opacity, const float* depth,
+                        const uint32_t* gids, const uint8_t* inst_masks, const float* uv, const float* conic_opacity, const float* depth,
                         const float* T_final,
                         const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth, const float* dL_dalpha,
                         const float* dL_dfeat, int32_t feat_grad_mode, void* workspace, size_t workspace_bytes,
                         float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_colors,
                         float* d_feats, float* d_pose, int32_t* status, void* stream) {
   return render_bwd_impl(cam, P, means, scales, quats, colors, feats, N, feat_dtype, layout, flags, bg, tile_ranges,
-                         tile_order, gids, uv, conic_opacity, depth, T_final, last_idx, dL_drgb, dL_ddepth, dL_dalpha, dL_dfeat,
+                         tile_order, gids, inst_masks, uv, conic_opacity, depth, T_final, last_idx, dL_drgb, dL_ddepth, dL_dalpha, dL_dfeat,
                          nullptr, feat_grad_mode, workspace, workspace_bytes, d_means, d_scales, d_quats, d_opacity,
                          d_colors, d_feats, d_pose, status, stream);
 }
@@ -424,9 +424,9 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
 gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, const float* scales,
                            const float* quats, const float* colors, const void* feats, int32_t N, int32_t feat_dtype,
                            int32_t layout, int32_t flags, const float* bg, const int32_t* tile_ranges,
-                           const int32_t* tile_order, const uint32_t* gids, const float* uv,
-                           const float* conic_opacity, const float* depth, const float* T_final,
-                           const int32_t* last_idx, const gs_l1_terms* l1,
+                           const int32_t* tile_order, const uint32_t* gids, const uint8_t* inst_masks,
+                           const float* uv, const float* conic_opacity, const float* depth,
+                           const float* T_final, const int32_t* last_idx, const gs_l1_terms* l1,
                            const uint32_t* l1_signs, void* workspace, size_t workspace_bytes, float* d_means,
                            float* d_scales, float* d_quats, float* d_opacity, float* d_colors, float* d_feats,
                            float* d_pose, int32_t* status, void* stream) {
@@ -438,7 +438,7 @@ gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, 
   in.w[1] = l1->w_depth;
   in.w[2] = l1->w_feat;
   return render_bwd_impl(cam, P, means, scales, quats, colors, feats, N, feat_dtype, layout, flags, bg, tile_ranges,
-                         tile_order, gids, uv, conic_opacity, depth, T_final, last_idx, nullptr, nullptr, nullptr, nullptr, &in,
+                         tile_order, gids, inst_masks, uv, conic_opacity, depth, T_final, last_idx, nullptr, nullptr, nullptr, nullptr, &in,
                          GS_FEAT_GRAD_DECOUPLED, workspace, workspace_bytes, d_means, d_scales, d_quats, d_opacity,
                          d_colors, d_feats, d_pose, status, stream);
 }

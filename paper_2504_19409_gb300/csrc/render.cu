@@ -41,6 +41,7 @@ struct FwdParams {
   const int2* ranges;
   const int* order;  // launch order of the tiles, or null
   const uint32_t* gids;
+  uint8_t* masks;    // per loaded instance: its 8x8-block skip mask (see k_render_bwd_mma), or null
   const float2* uv;
   const float4* co;
   const float* depth;
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
       s_co[threadIdx.x] = conic_q(co);  // the walk's alphas take the base-2 form
       // the skip tests of all 8 warp blocks (2 columns x 4 rows of 8x4 pixels)
       s_wmask[threadIdx.x] = (uint8_t)warp_block_mask<8, 4, false>(u, co, tx, ty);
+      if (geom && p.masks) p.masks[idx] = (uint8_t)warp_block_mask<4, 8, true>(u, co, tx, ty);
       if (VIS) s_gid[threadIdx.x] = g;
       if (geom) s_cd[threadIdx.x] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
       if (NC > 0) load_feat_row<NCs>(p.feats, p.bf16, p.N, g, c0, s_f[threadIdx.x]);
@@ -407,6 +409,7 @@ __global__ void __launch_bounds__(kFwd2Threads, 5) k_render_fwd2(const FwdParams
         s_uv[i] = u;
         s_co[i] = conic_q(co);
         s_wmask[i] = (uint8_t)warp_block_mask<4, 8, true>(u, co, tx, ty);
+        if (p.masks) p.masks[idx] = s_wmask[i];
         if (VIS) s_gid[i] = g;
         s_cd[i] = make_float4(p.colors[3 * g], p.colors[3 * g + 1], p.colors[3 * g + 2], p.depth[g]);
         if (NC > 0) load_feat_row<NCs>(p.feats, p.bf16, p.N, g, 0, s_f[i]);
@@ -578,6 +581,7 @@ struct BwdParams {
   const int2* ranges;
   const int* order;  // launch order of the tiles, or null
   const uint32_t* gids;
+  const uint8_t* masks;  // the forward's per-instance 8x8-block skip masks, or null (recomputed)
   const float2* uv;
   const float4* co;
   const float* depth;
@@ -923,9 +927,10 @@ __device__ __forceinline__ void stage_batch(const BwdParams& p, BwdBatch& b, int
   cp_async4(cd + 3, p.depth + g);
 }
 
-// After the slot's copies landed: the warp skip tests of its Gaussian.
-__device__ __forceinline__ void finish_batch(BwdBatch& b, int i, int tx, int ty) {
-  b.wmask[i] = (uint8_t)warp_block_mask<mma_bwd::kNW, 8, true>(b.uv[i], b.co[i], tx, ty);
+// After the slot's copies landed: the base-2 conic and, without the forward's
+// stored masks, the warp skip tests of its Gaussian.
+__device__ __forceinline__ void finish_batch(BwdBatch& b, int i, int tx, int ty, bool stored) {
+  if (!stored) b.wmask[i] = (uint8_t)warp_block_mask<mma_bwd::kNW, 8, true>(b.uv[i], b.co[i], tx, ty);
   b.q[i] = conic_q(b.co[i]);
 }
 
@@ -1105,15 +1110,22 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   auto batch_lo = [&](int b) { return max(rg.x, batch_hi(b) - kBB); };
   // Batches are staged by warp 0 one batch ahead with cp.async (ids read two
   // batches ahead), so each batch costs the block a single barrier.
-  uint32_t g_next = 0;
+  // With the forward's stored skip masks (p.masks, one byte per instance) the
+  // staging warp reads each mask with its id instead of testing the ellipse.
+  const bool stored = p.masks != nullptr;
+  uint32_t g_next = 0, m_next = 0;
   if (wid == 0 && nb > 0) {
     const int lo0 = batch_lo(0);
     if (lane < batch_hi(0) - lo0) {
       stage_batch(p, s_b[0], lane, p.gids[lo0 + lane]);
+      if (stored) s_b[0].wmask[lane] = p.masks[lo0 + lane];
       cp_async_wait_all();
-      finish_batch(s_b[0], lane, tx, ty);
+      finish_batch(s_b[0], lane, tx, ty, stored);
     }
-    if (nb > 1 && lane < batch_hi(1) - batch_lo(1)) g_next = p.gids[batch_lo(1) + lane];
+    if (nb > 1 && lane < batch_hi(1) - batch_lo(1)) {
+      g_next = p.gids[batch_lo(1) + lane];
+      if (stored) m_next = p.masks[batch_lo(1) + lane];
+    }
   }
   __syncthreads();
 
@@ -1130,8 +1142,14 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     float* red = s_red + (b & 1) * kNW * kBB * SR;  // [kNW][kBB][SR] of this batch
     const int lo = batch_lo(b), n = batch_hi(b) - lo;
     const bool stage = wid == 0 && b + 1 < nb && lane < batch_hi(b + 1) - batch_lo(b + 1);
-    if (stage) stage_batch(p, s_b[(b + 1) % kNBuf], lane, g_next);
-    if (wid == 0 && b + 2 < nb && lane < batch_hi(b + 2) - batch_lo(b + 2)) g_next = p.gids[batch_lo(b + 2) + lane];
+    if (stage) {
+      stage_batch(p, s_b[(b + 1) % kNBuf], lane, g_next);
+      if (stored) s_b[(b + 1) % kNBuf].wmask[lane] = (uint8_t)m_next;
+    }
+    if (wid == 0 && b + 2 < nb && lane < batch_hi(b + 2) - batch_lo(b + 2)) {
+      g_next = p.gids[batch_lo(b + 2) + lane];
+      if (stored) m_next = p.masks[batch_lo(b + 2) + lane];
+    }
 
     // Contraction of the warp's tile: rows r < 8 hold w of the r-th Gaussian
     // walked since the last contraction and rows 8 + r its dp. The cotangent
@@ -1238,7 +1256,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     if (rows > 0) flush();
     if (stage) {
       cp_async_wait_all();
-      finish_batch(s_b[(b + 1) % kNBuf], lane, tx, ty);
+      finish_batch(s_b[(b + 1) % kNBuf], lane, tx, ty, stored);
     }
     __syncthreads();
     // the block's sums of the batch: rows of warps that did not walk Gaussian j
@@ -1325,7 +1343,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
 }  // namespace
 
 gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                            const float* uv,
+                            uint8_t* masks, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
@@ -1336,6 +1354,7 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const int32_
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.order = order;
+  p.masks = masks;
   p.gids = gids;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);
@@ -1389,7 +1408,7 @@ gs_status launch_bwd_mma(const BwdParams& p, unsigned tiles, cudaStream_t st) {
 }
 
 gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                            const float* uv,
+                            const uint8_t* masks, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
                             const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
@@ -1401,6 +1420,7 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.order = order;
+  p.masks = masks;
   p.gids = gids;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);

@@ -175,7 +175,9 @@ def test_separate_l1_pass_equals_fused_epilogue(gs, sg, case):
     """gs_l1_signs over a plain forward's images writes the fused forward's
     sign words bit for bit (the same binary32 differences) and the same loss
     to 1e-5 (fp32 sums in another order); the adjoint from its words then
-    equals the fused pair's."""
+    equals the fused pair's to 1e-5 normwise: the same arithmetic, but the
+    per-tile float atomics add in a run-dependent order, and the room frame's
+    quaternion gradients are sums with cancellation."""
     N = {"features_off": 0, "n5_chw": 5, "n8_hwc": 8}.get(case, 16)
     if case == "room":
         sc, _ = sg.room_case()
@@ -200,4 +202,4 @@ def test_separate_l1_pass_equals_fused_epilogue(gs, sg, case):
     for k in CLASSES:
         if k == "feats" and N == 0:
             continue
-        assert _normwise(sep[k], got[k]) <= 1e-6, k
+        assert _normwise(sep[k], got[k]) <= 1e-5, k

@@ -61,3 +61,35 @@ def test_small_and_ragged_tile_counts(gs, T):
     o = order.cpu().numpy()
     assert np.array_equal(np.sort(o), np.arange(T))
     assert np.all(np.diff(_bucket(lengths[o])) <= 0)
+
+
+def test_adjoint_with_and_without_stored_masks(gs, sg):
+    """The forward's per-instance skip masks (inst_masks) change only which
+    pixel blocks skip a Gaussian: the adjoint that reads them equals the one
+    that tests each Gaussian again, to the summation order of its atomics
+    (1e-5 normwise: the room frame's sums cancel)."""
+    sc, cam, proj, srt, t = _frame(gs, sg)
+    means, scales, quats, cols, feats = (t(x) for x in (sc.means, sc.scales, sc.quats, sc.colors, sc.feats))
+    fw = gs.render_fwd(cam, proj, srt, cols, feats, status=srt["status"])
+    rng = np.random.default_rng(8)
+    g_rgb = torch.from_numpy(rng.normal(size=(3, cam.height, cam.width)).astype(np.float32)).cuda()
+    g_feat = torch.from_numpy(rng.normal(size=(sc.N, cam.height, cam.width)).astype(np.float32)).cuda()
+    a = gs.render_bwd(cam, means, scales, quats, cols, feats, proj, srt, fw, g_rgb, None, None, g_feat)
+    plain = {k: v for k, v in srt.items() if k != "inst_masks"}
+    b = gs.render_bwd(cam, means, scales, quats, cols, feats, proj, plain, fw, g_rgb, None, None, g_feat)
+    torch.cuda.synchronize()
+    # every instance the adjoint reads (a tile's positions below its largest
+    # last index, all loaded by the forward) holds a 4-bit mask
+    masks = srt["inst_masks"].cpu().numpy()
+    r = srt["tile_ranges"].cpu().numpy()
+    last = fw["last_idx"].cpu().numpy()
+    H, W = last.shape
+    tx = (W + 15) // 16
+    pad = np.zeros(((H + 15) // 16 * 16, tx * 16), np.int32)
+    pad[:H, :W] = last
+    maxlast = pad.reshape(pad.shape[0] // 16, 16, tx, 16).max(axis=(1, 3)).ravel()
+    read = np.concatenate([np.arange(r[t, 0], r[t, 0] + maxlast[t]) for t in range(r.shape[0]) if maxlast[t] > 0])
+    assert read.size > 100_000 and masks[read].max() <= 15
+    for k in ("means", "scales", "quats", "opacity", "colors", "feats", "pose"):
+        x, y = a[k].double(), b[k].double()
+        assert float((x - y).norm() / y.norm()) <= 1e-5, k
