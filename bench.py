@@ -160,8 +160,8 @@ def algorithmic_flops(stats):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/render_fwd_bwd_room300k_N16_full.md, keyed to
 # the source it was taken on (null once render.cu changes).
-NCU_TRAFFIC = {"k_render_bwd_mma": (40_132_864 + 9_728, "36fc813124e648b8"),
-               "k_render_fwd": (86_089_984 + 47_798_272, "36fc813124e648b8")}
+NCU_TRAFFIC = {"k_render_bwd_mma": (40_786_688 + 156_416, "5842abd2a257ea8e"),
+               "k_render_fwd": (87_773_440 + 49_335_296, "5842abd2a257ea8e")}
 
 
 def ncu_traffic(kernel):
