@@ -545,7 +545,7 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   {
     GS_TRACE("k_tile_ranges", st);
     int nb = (int)((capacity + 255) / 256);
-    if (nb > 4096) nb = 4096;
+    if (nb > 8 * 152) nb = 8 * 152;  // one wave; the kernel strides over the instances
     if (nb < 1) nb = 1;
     launch_pdl(k_tile_ranges, nb, 256, 0, st, tk, gids, depth, ctrl, num_tiles, reinterpret_cast<int2*>(ranges), keys64);
   }
