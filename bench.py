@@ -126,15 +126,16 @@ def algorithmic_bytes(stats):
     12 + depth 4 + features 4N) and writes (5+N)*4 + 12 B per pixel; the
     adjoint reads the same plus the per-pixel state (8 B) and cotangents
     ((5+N)*4 B) and writes 24 + (4+N)*4 B of gradients per visible Gaussian.
-    With the L1 loss fused (this step), the forward also reads the targets
-    ((4+N)*4 B per pixel) and writes the cotangent sign words (8 B per
-    pixel), which the adjoint (k_render_bwd_mma) reads instead of cotangent
-    images."""
+    With the L1 loss (this step), the L1 pass reads the images and the
+    targets ((4+N)*4 B each per pixel) and writes the cotangent sign words
+    (8 B per pixel), which the adjoint (k_render_bwd_mma) reads instead of
+    cotangent images."""
     P, Pv, I, HW, N = stats["P"], stats["P_vis"], stats["I"], WIDTH * HEIGHT, N_FEAT
     rec = 8 + 16 + 12 + 4 + 4 * N
     return {
         "k_project": P * (44 + 48),
-        "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12) + HW * ((4 + N) * 4 + 8),
+        "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12),
+        "k_l1_signs": HW * (2 * (4 + N) * 4 + 8),
         "k_render_bwd": I * 4 + Pv * rec + HW * (8 + (5 + N) * 4) + Pv * (24 + (4 + N) * 4),
         "k_render_bwd_mma": I * 4 + Pv * rec + HW * (8 + 8) + Pv * (24 + (4 + N) * 4),
         "k_project_bwd": P * (40 + 24) + Pv * 40,
@@ -160,8 +161,7 @@ def algorithmic_flops(stats):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/render_fwd_bwd_room300k_N16_full.md, keyed to
 # the source it was taken on (null once render.cu changes).
-NCU_TRAFFIC = {"k_render_bwd_mma": (40_786_688 + 156_416, "5842abd2a257ea8e"),
-               "k_render_fwd": (87_773_440 + 49_335_296, "5842abd2a257ea8e")}
+NCU_TRAFFIC = {"k_render_bwd_mma": (40_786_688 + 156_416, "5842abd2a257ea8e")}
 
 
 def ncu_traffic(kernel):
@@ -209,11 +209,14 @@ def run_ours(args, rank, world, local_rank):
     loss = torch.zeros(1, device=dev)
 
     def step(k):
-        # forward with the L1 loss against the frame's targets (evaluated in the
-        # compositing epilogue), then its adjoint with the pose gradient
+        # forward, the L1 loss against the frame's targets as a streaming pass
+        # over the rendered images (gs_l1_signs: the loss and the cotangent sign
+        # words), then the adjoint with the pose gradient. On GB300 this beats
+        # evaluating the loss in the compositing epilogue (gs_render_fwd_l1),
+        # whose target reads at the end of every tile block stay exposed.
         cam = frame_camera(k)
-        ras.forward(cam, means, scales, quats, opac, cols, feats, l1_targets=targets[k], l1_weights=scales_l1,
-                    l1_loss=loss)
+        ras.forward(cam, means, scales, quats, opac, cols, feats)
+        ras.l1_loss(cam, targets[k], scales_l1, loss)
         return ras.backward_l1(cam, means, scales, quats, cols, feats, scales_l1)
 
     stream = torch.cuda.current_stream()
