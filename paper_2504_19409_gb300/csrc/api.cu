@@ -112,34 +112,75 @@ __global__ void __launch_bounds__(256) k_l1_grad(long long n, const float* __res
   }
 }
 
-// The L1 terms of gs_render_fwd_l1's epilogue as a pass over rendered images,
-// one thread per pixel: the same differences pred - target (the images hold
-// the epilogue's values), hence the same sign words; the loss adds w |d| per
-// term, summed per block and added with one atomic.
-__global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, const float* __restrict__ rgb,
+// The L1 terms of gs_render_fwd_l1's epilogue as a pass over rendered images:
+// the same differences pred - target (the images hold the epilogue's values),
+// hence the same sign words; the loss adds w |d| per term, summed per block
+// and added with one atomic. Four consecutive pixels per thread; with vec
+// (every plane 16-byte aligned and a multiple of 4 pixels, or the HWC feature
+// rows a multiple of 4 channels) each plane is read with 16-byte loads.
+__device__ __forceinline__ void l1_term(float pred, float target, float w, int bit, float& lsum, uint32_t& nz,
+                                        uint32_t& ng) {
+  const float d = pred - target;
+  lsum += w * fabsf(d);
+  nz |= (d != 0.f ? 1u : 0u) << bit;
+  ng |= (d < 0.f ? 1u : 0u) << bit;
+}
+
+__global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, int vec, const float* __restrict__ rgb,
                                                   const float* __restrict__ depth, const float* __restrict__ feat,
                                                   const L1Fwd l1) {
   pdl_wait();
   pdl_trigger();
-  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long pix0 = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
   float lsum = 0.f;
-  if (pix < HW) {
-    uint32_t nz = 0, ng = 0;
-    auto term = [&](float pred, float target, float w, int bit) {
-      const float d = pred - target;
-      lsum += w * fabsf(d);
-      nz |= (d != 0.f ? 1u : 0u) << bit;
-      ng |= (d < 0.f ? 1u : 0u) << bit;
+  if (pix0 < HW) {
+    uint32_t nz[4] = {0u, 0u, 0u, 0u}, ng[4] = {0u, 0u, 0u, 0u};
+    const int np = HW - pix0 < 4 ? (int)(HW - pix0) : 4;
+    // one plane of 4 consecutive pixels (CHW planes, depth): 16-byte loads with vec
+    auto plane4 = [&](const float* a, const float* b, long long off, float w, int bit) {
+      if (vec) {
+        const float4 x = __ldcs(reinterpret_cast<const float4*>(a + off));
+        const float4 y = __ldcs(reinterpret_cast<const float4*>(b + off));
+        l1_term(x.x, y.x, w, bit, lsum, nz[0], ng[0]);
+        l1_term(x.y, y.y, w, bit, lsum, nz[1], ng[1]);
+        l1_term(x.z, y.z, w, bit, lsum, nz[2], ng[2]);
+        l1_term(x.w, y.w, w, bit, lsum, nz[3], ng[3]);
+      } else {
+        for (int k = 0; k < np; ++k) l1_term(a[off + k], b[off + k], w, bit, lsum, nz[k], ng[k]);
+      }
     };
     if (l1.target[0])
-      for (int c = 0; c < 3; ++c) term(rgb[c * HW + pix], l1.target[0][c * HW + pix], l1.w[0], kL1BitRgb + c);
-    if (l1.target[1]) term(depth[pix], l1.target[1][pix], l1.w[1], kL1BitDepth);
-    if (l1.target[2])
-      for (int c = 0; c < N; ++c) {
-        const long long i = hwc ? pix * N + c : c * HW + pix;
-        term(feat[i], l1.target[2][i], l1.w[2], c);
+      for (int c = 0; c < 3; ++c) plane4(rgb, l1.target[0], c * HW + pix0, l1.w[0], kL1BitRgb + c);
+    if (l1.target[1]) plane4(depth, l1.target[1], pix0, l1.w[1], kL1BitDepth);
+    if (l1.target[2]) {
+      if (!hwc) {
+        for (int c = 0; c < N; ++c) plane4(feat, l1.target[2], c * HW + pix0, l1.w[2], c);
+      } else if (vec) {
+        // the 4 pixels' rows are 4 N consecutive floats
+        const float4* a = reinterpret_cast<const float4*>(feat + pix0 * N);
+        const float4* b = reinterpret_cast<const float4*>(l1.target[2] + pix0 * N);
+        for (int v = 0; v < N; ++v) {  // 4 N floats = N float4s
+          const float4 x = __ldcs(a + v), y = __ldcs(b + v);
+          const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int f = 4 * v + e;  // float index within the 4 rows
+            l1_term(xs[e], ys[e], l1.w[2], f % N, lsum, nz[f / N], ng[f / N]);
+          }
+        }
+      } else {
+        for (int k = 0; k < np; ++k)
+          for (int c = 0; c < N; ++c)
+            l1_term(feat[(pix0 + k) * N + c], l1.target[2][(pix0 + k) * N + c], l1.w[2], c, lsum, nz[k], ng[k]);
       }
-    l1.signs[pix] = make_uint2(nz, ng);
+    }
+    if (vec) {
+      uint4* o = reinterpret_cast<uint4*>(l1.signs + pix0);
+      o[0] = make_uint4(nz[0], ng[0], nz[1], ng[1]);
+      o[1] = make_uint4(nz[2], ng[2], nz[3], ng[3]);
+    } else {
+      for (int k = 0; k < np; ++k) l1.signs[pix0 + k] = make_uint2(nz[k], ng[k]);
+    }
   }
   if (l1.loss) {
     __shared__ float s_part[8];
@@ -473,8 +514,15 @@ gs_status gs_l1_signs(int32_t width, int32_t height, int32_t N, int32_t layout, 
   in.loss = l1->loss;
   in.signs = reinterpret_cast<uint2*>(l1_signs);
   const long long HW = (long long)width * height;
+  const bool hwc = layout == GS_LAYOUT_HWC;
+  // 16-byte loads: every plane base aligned and HW % 4 == 0 (CHW planes, and
+  // the rgb and depth planes in either layout), and for HWC N % 4 == 0
+  bool vec = HW % 4 == 0 && aligned(l1_signs, 16) && (!hwc || N % 4 == 0);
+  for (const float* q : {rgb, depth, feat, l1->target_rgb, l1->target_depth, in.target[2]})
+    if (q && !aligned(q, 16)) vec = false;
+  const long long quads = (HW + 3) / 4;
   GS_TRACE("k_l1_signs", S(stream));
-  launch_pdl(k_l1_signs, (unsigned)((HW + 255) / 256), 256, 0, S(stream), HW, N, layout == GS_LAYOUT_HWC ? 1 : 0, rgb,
+  launch_pdl(k_l1_signs, (unsigned)((quads + 255) / 256), 256, 0, S(stream), HW, N, hwc ? 1 : 0, vec ? 1 : 0, rgb,
              depth, feat, in);
   return last_launch_status();
 }

@@ -170,7 +170,8 @@ def test_fused_l1_rejects_unsupported(gs, sg):
         gs.render_bwd_l1(cam, means, scales, quats, cols, feats, proj, srt, fw, {"rgb": 1.0})
 
 
-@pytest.mark.parametrize("case", ["chw_bg", "hwc", "features_off", "rgb_only", "n5_chw", "n8_hwc", "room"])
+@pytest.mark.parametrize("case", ["chw_bg", "hwc", "features_off", "rgb_only", "n5_chw", "n8_hwc", "room",
+                                  "ragged_chw", "ragged_hwc"])
 def test_separate_l1_pass_equals_fused_epilogue(gs, sg, case):
     """gs_l1_signs over a plain forward's images writes the fused forward's
     sign words bit for bit (the same binary32 differences) and the same loss
@@ -182,10 +183,14 @@ def test_separate_l1_pass_equals_fused_epilogue(gs, sg, case):
     if case == "room":
         sc, _ = sg.room_case()
         cam = sg.room_trajectory(11).as_f32()
+    elif case.startswith("ragged"):
+        # 101 x 37 pixels: an odd pixel count, so the pass takes its scalar path
+        cam = sg.identity_camera(101, 37, 45.0).as_f32()
+        sc = sg.frustum_scene(78, 900, cam, N)
     else:
         sc, cam = sg.small_case(seed=4, N=N)
         cam = cam.as_f32()
-    layout = gs.GS_LAYOUT_HWC if case in ("hwc", "n8_hwc") else gs.GS_LAYOUT_CHW
+    layout = gs.GS_LAYOUT_HWC if case in ("hwc", "n8_hwc", "ragged_hwc") else gs.GS_LAYOUT_CHW
     bg = (0.1, 0.3, 0.2) if case == "chw_bg" else None
     args, proj, srt, fw = _setup(gs, cam, sc, layout, bg)
     targets = _targets(fw, np.random.default_rng(70 + len(case)), drop=("depth", "feat") if case == "rgb_only" else ())
