@@ -970,6 +970,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   // J <- alpha c_i . g + (1 - alpha) J (both B_c and S follow that recurrence).
   float T[2], pxc[2], pyc[2], gC0[2], gC1[2], gC2[2], gD[2], J[2];
   int last[2];
+  uint2 sgo[2] = {make_uint2(0u, 0u), make_uint2(0u, 0u)};  // L1: this thread's pixels' sign words
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const bool inside = px[q] < p.cam.W && py[q] < p.cam.H;
@@ -985,6 +986,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       last[q] = p.last_idx[pix];
       if constexpr (L1) {
         const uint2 sg = p.l1.signs[pix];
+        sgo[q] = sg;
         gC0[q] = l1_cot(sg, kL1BitRgb, p.l1.w[0]);
         gC1[q] = l1_cot(sg, kL1BitRgb + 1, p.l1.w[0]);
         gC2[q] = l1_cot(sg, kL1BitRgb + 2, p.l1.w[0]);
@@ -1010,7 +1012,9 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
     const int bx = tx * kTile + (wid & 1) * 8, by = ty * kTile + (wid >> 1) * 8;
     if constexpr (L1) {
       // the signs of w sign(...) from the forward's sign words as exact bf16
-      // (+1 = 0x3f80); each of this lane's 16 pixels is read once
+      // (+1 = 0x3f80); the 16 pixels of this lane's fragments lie in the warp's
+      // own block: pixel (column t + 4 hf, row s + 4 q) is pixel q of lane
+      // t + 4 hf + 8 s, whose word comes by shuffle
       int bit[NT];
       uint32_t on[NT];
 #pragma unroll
@@ -1034,13 +1038,11 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf) {
-          const int qx = bx + t4 + 4 * hf;
+          const int src = t4 + 4 * hf + 8 * s;
           uint2 sg[2];
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int qy = by + s + 4 * q;
-            sg[q] = (qx < p.cam.W && qy < p.cam.H) ? p.l1.signs[(size_t)qy * p.cam.W + qx] : make_uint2(0u, 0u);
-          }
+          for (int q = 0; q < 2; ++q)
+            sg[q] = make_uint2(__shfl_sync(0xffffffffu, sgo[q].x, src), __shfl_sync(0xffffffffu, sgo[q].y, src));
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt)
             bh[nt][s][hf] = half(sg[0], bit[nt], on[nt]) | (half(sg[1], bit[nt], on[nt]) << 16);
