@@ -41,6 +41,7 @@ constexpr int kDkThreads = 1024;    // threads of k_depth_keys (kRsChunk keys pe
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 8;       // keys per thread
 constexpr int kRsChunk = kRsThreads * kRsItems;  // 2048 keys per block
+static_assert(kRsChunk % kDkThreads == 0, "k_depth_keys covers a chunk in whole rounds of its threads");
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRadix = 256;
 
