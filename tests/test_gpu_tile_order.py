@@ -93,3 +93,30 @@ def test_adjoint_with_and_without_stored_masks(gs, sg):
     for k in ("means", "scales", "quats", "opacity", "colors", "feats", "pose"):
         x, y = a[k].double(), b[k].double()
         assert float((x - y).norm() / y.norm()) <= 1e-5, k
+
+
+def test_masks_from_the_chunked_forward_serve_a_pose_only_adjoint(gs, sg):
+    """N = 32 features composite on the one-pixel kernel in 32-channel chunks;
+    its first chunk stores the same 8x8-block masks, which a features-off
+    (pose-only, as in tracking) adjoint of the same frame then reads."""
+    sc, cam = sg.small_case(seed=6, N=32)
+    cam = cam.as_f32()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    means, scales, quats, opac, cols, feats = (t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors,
+                                                              sc.feats))
+    proj = gs.project(cam, means, scales, quats, opac)
+    srt = gs.bin_sort(cam, proj, max(int(proj["n_instances"].item()), 1))
+    fw = gs.render_fwd(cam, proj, srt, cols, feats, status=srt["status"])
+    rng = np.random.default_rng(9)
+    g_rgb = torch.from_numpy(rng.normal(size=(3, cam.height, cam.width)).astype(np.float32)).cuda()
+    g_depth = torch.from_numpy(rng.normal(size=(cam.height, cam.width)).astype(np.float32)).cuda()
+    a = gs.render_bwd(cam, means, scales, quats, cols, None, proj, srt, fw, g_rgb, g_depth, None, None,
+                      flags=gs.GS_FEAT_OFF)
+    plain = {k: v for k, v in srt.items() if k != "inst_masks"}
+    b = gs.render_bwd(cam, means, scales, quats, cols, None, proj, plain, fw, g_rgb, g_depth, None, None,
+                      flags=gs.GS_FEAT_OFF)
+    torch.cuda.synchronize()
+    for k in ("means", "scales", "quats", "opacity", "colors", "pose"):
+        x, y = a[k].double(), b[k].double()
+        assert float(y.norm()) > 0, k
+        assert float((x - y).norm() / y.norm()) <= 1e-5, k
