@@ -359,6 +359,21 @@ gs_status gs_tracking_loss_grad(int32_t width, int32_t height, const float* rgb,
                                 float alpha_min, const uint8_t* m_e, float lambda_t, float* g_rgb,
                                 float* g_depth, float* loss_sum, void* stream);
 
+/* gs_tracking_loss_signs -- the same loss and cotangents as
+ * gs_tracking_loss_grad, kept as the sign words of gs_render_fwd_l1
+ * (l1_signs [H*W][2]: bits 16, 17, 18 colour, 19 depth; a bit of word 0 is
+ * set where the cotangent is nonzero, of word 1 where it is negative) with
+ * their weights written to weights[0] = lambda_t / (3 H W) (colour) and
+ * weights[1] = (1 - lambda_t) / (H W) (depth) (host floats). gs_render_bwd_l1
+ * with those weights (features off) then gives the pose gradient of
+ * gs_render_bwd on gs_tracking_loss_grad's images. *loss_sum as there.
+ */
+gs_status gs_tracking_loss_signs(int32_t width, int32_t height, const float* rgb, const float* depth,
+                                 const float* gt_rgb, const float* gt_depth, const float* alpha_ref, float alpha_min,
+                                 const uint8_t* m_e, float lambda_t, uint32_t* l1_signs, float* weights,
+                                 float* loss_sum, void* stream);
+
+
 /* gs_pose_update -- one optimiser step of the pose (device arrays):
  *   Adam on d_pose [6] (tangent (rho, theta) of the left perturbation, from
  *   gs_render_bwd) with moments adam_m [6], adam_v [6] (zero at the frame's

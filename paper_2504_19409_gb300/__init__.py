@@ -39,7 +39,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
-           "gs_l1_signs")
+           "gs_l1_signs", "gs_tracking_loss_signs")
 
 
 class GsffError(RuntimeError):
@@ -140,6 +140,8 @@ def lib():
     L.gs_edge_mask.argtypes = [_i32, _i32, _vp, _f, _vp, _vp]
     L.gs_edge_mask.restype = ctypes.c_int
     L.gs_tracking_loss_grad.argtypes = [_i32, _i32] + [_vp] * 5 + [_f, _vp, _f, _vp, _vp, _vp, _vp]
+    L.gs_tracking_loss_signs.argtypes = [_i32, _i32] + [_vp] * 5 + [_f, _vp, _f, _vp, _vp, _vp, _vp]
+    L.gs_tracking_loss_signs.restype = ctypes.c_int
     L.gs_tracking_loss_grad.restype = ctypes.c_int
     L.gs_pose_update.argtypes = [_vp] * 4 + [_i32] + [_f] * 7 + [_vp, _vp]
     L.gs_pose_update.restype = ctypes.c_int
@@ -340,6 +342,23 @@ def tracking_loss_grad(rgb, depth, gt_rgb, gt_depth, alpha_ref, m_e, lambda_t=0.
                                        float(alpha_min), _ptr(m_e), float(lambda_t), _ptr(gr), _ptr(gd), _ptr(loss),
                                        _stream(stream)), "gs_tracking_loss_grad")
     return gr, gd
+
+
+def tracking_loss_signs(rgb, depth, gt_rgb, gt_depth, alpha_ref, m_e, lambda_t=0.9, alpha_min=0.5, signs=None,
+                        loss=None, stream=None):
+    """gs_tracking_loss_signs: Eq. 5's cotangents as sign words (int32 [H*W, 2]) and their weights
+    ({"rgb": ..., "depth": ...}) for render_bwd_l1."""
+    H, W = depth.shape
+    for t_, n_, sh in ((rgb, "rgb", (3, H, W)), (gt_rgb, "gt_rgb", (3, H, W)), (gt_depth, "gt_depth", (H, W)),
+                       (alpha_ref, "alpha_ref", (H, W))):
+        _need(t_, torch.float32, n_, sh)
+    _need(m_e, torch.uint8, "m_e", (H, W))
+    sg = signs if signs is not None else torch.empty(H * W, 2, dtype=torch.int32, device=depth.device)
+    w = (ctypes.c_float * 2)()
+    _check(lib().gs_tracking_loss_signs(W, H, _ptr(rgb), _ptr(depth), _ptr(gt_rgb), _ptr(gt_depth), _ptr(alpha_ref),
+                                        float(alpha_min), _ptr(m_e), float(lambda_t), _ptr(sg), ctypes.cast(w, _vp),
+                                        _ptr(loss), _stream(stream)), "gs_tracking_loss_signs")
+    return sg, {"rgb": float(w[0]), "depth": float(w[1]), "feat": 0.0}
 
 
 def pose_update(pose, d_pose, m, v, step, lr_trans=1e-3, lr_rot=3e-3, beta1=0.9, beta2=0.999, eps=1e-8,
@@ -666,6 +685,13 @@ class Rasterizer:
         """The adjoint of the last forward into grads["pose"] only (frozen Gaussians, as in tracking)."""
         render_bwd(cam, means, scales, quats, colors, None, self.proj, self.sort, self.fwd, g_rgb, g_depth,
                    flags=GS_FEAT_OFF, grads=grads, workspace=self.bwd_ws, status=self.status, stream=stream)
+        return grads
+
+    def render_pose_grad_l1(self, cam, means, scales, quats, colors, weights, grads, stream=None):
+        """The pose gradient of the last forward from the L1 sign words in self.fwd["l1_signs"]
+        (e.g. tracking_loss_signs's) and their weights: gs_render_bwd_l1 with the Gaussians frozen."""
+        render_bwd_l1(cam, means, scales, quats, colors, None, self.proj, self.sort, self.fwd, weights,
+                      flags=GS_FEAT_OFF, grads=grads, workspace=self.bwd_ws, status=self.status, stream=stream)
         return grads
 
     def check_status(self):

@@ -90,6 +90,55 @@ __global__ void __launch_bounds__(256) k_tracking_grad(int HW, const float* __re
   }
 }
 
+// The same terms as k_tracking_grad, kept as sign words (bits 16..18 colour,
+// 19 depth; see L1Fwd) for the L1 adjoint: a cotangent is nonzero where its
+// mask holds and the difference is not 0, negative where the difference is.
+__global__ void __launch_bounds__(256) k_tracking_signs(int HW, const float* __restrict__ rgb,
+                                                        const float* __restrict__ depth,
+                                                        const float* __restrict__ gt_rgb,
+                                                        const float* __restrict__ gt_depth,
+                                                        const float* __restrict__ alpha_ref, float alpha_min,
+                                                        const uint8_t* __restrict__ m_e, float sc, float sd,
+                                                        uint2* __restrict__ signs, float* __restrict__ loss) {
+  float acc = 0.f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
+    const bool mv = alpha_ref[p] > alpha_min;
+    const bool col = mv && m_e[p] != 0;
+    uint32_t nz = 0, ng = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t i = (size_t)c * HW + p;
+      const float d = rgb[i] - gt_rgb[i];
+      if (col) {
+        nz |= (d != 0.f ? 1u : 0u) << (kL1BitRgb + c);
+        ng |= (d < 0.f ? 1u : 0u) << (kL1BitRgb + c);
+        acc += sc * fabsf(d);
+      }
+    }
+    const float dg = gt_depth[p];
+    const bool dep = mv && dg > 0.f;
+    const float d = depth[p] - dg;
+    if (dep) {
+      nz |= (d != 0.f ? 1u : 0u) << kL1BitDepth;
+      ng |= (d < 0.f ? 1u : 0u) << kL1BitDepth;
+      acc += sd * fabsf(d);
+    }
+    signs[p] = make_uint2(nz, ng);
+  }
+  if (loss) {
+    __shared__ float s_part[8];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_part[w];
+      if (b != 0.f) atomicAdd(loss, b);
+    }
+  }
+}
+
 struct PoseUpdate {
   float lr_trans, lr_rot, beta1, beta2, eps, tol_trans, tol_rot;
   int step;
@@ -182,6 +231,25 @@ gs_status gs_tracking_loss_grad(int32_t width, int32_t height, const float* rgb,
   GS_TRACE("k_tracking_grad", S(stream));
   k_tracking_grad<<<blocks, 256, 0, S(stream)>>>(HW, rgb, depth, gt_rgb, gt_depth, alpha_ref, alpha_min, m_e, sc, sd,
                                                  g_rgb, g_depth, loss_sum);
+  return last_launch_status();
+}
+
+gs_status gs_tracking_loss_signs(int32_t width, int32_t height, const float* rgb, const float* depth,
+                                 const float* gt_rgb, const float* gt_depth, const float* alpha_ref, float alpha_min,
+                                 const uint8_t* m_e, float lambda_t, uint32_t* l1_signs, float* weights,
+                                 float* loss_sum, void* stream) {
+  if (width <= 0 || height <= 0 || width > (1 << 15) || height > (1 << 15)) return GS_ERR_INVALID_ARG;
+  if (!rgb || !depth || !gt_rgb || !gt_depth || !alpha_ref || !m_e || !l1_signs || !weights) return GS_ERR_INVALID_ARG;
+  if (!(lambda_t >= 0.f && lambda_t <= 1.f) || (reinterpret_cast<uintptr_t>(l1_signs) & 7u)) return GS_ERR_INVALID_ARG;
+  const int HW = width * height;
+  const float sc = (float)((double)lambda_t / (3.0 * HW)), sd = (float)((1.0 - (double)lambda_t) / HW);
+  weights[0] = sc;
+  weights[1] = sd;
+  int blocks = (HW + 1023) / 1024;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  GS_TRACE("k_tracking_signs", S(stream));
+  k_tracking_signs<<<blocks, 256, 0, S(stream)>>>(HW, rgb, depth, gt_rgb, gt_depth, alpha_ref, alpha_min, m_e, sc, sd,
+                                                  reinterpret_cast<uint2*>(l1_signs), loss_sum);
   return last_launch_status();
 }
 

@@ -3,9 +3,10 @@
 With the Gaussians frozen, the frame is rendered at the current pose
 estimate; the first render's opacity gives the visibility mask m_v and the
 observed image's gradient the edge mask m_e (gs_edge_mask); each iteration
-renders (gs_project, gs_bin_sort, gs_render_fwd), forms the cotangents of
-Eq. 5 (gs_tracking_loss_grad), back-propagates to the pose tangent only
-(gs_render_bwd with the Gaussian gradients switched off) and updates the
+renders (gs_project, gs_bin_sort, gs_tile_order, gs_render_fwd), forms the
+cotangents of Eq. 5 as sign words with their two weights
+(gs_tracking_loss_signs), back-propagates to the pose tangent only
+(gs_render_bwd_l1 with the Gaussian gradients switched off) and updates the
 pose on the device (gs_pose_update: Adam, then T <- Exp(delta) T). The pose
 lives in a device array that the camera struct points to, so an iteration has
 no host round trip; the convergence flag is read every `check_every`
@@ -16,7 +17,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import GS_FEAT_OFF, Rasterizer, edge_mask, pose_update, tracking_loss_grad, with_device_pose
+from . import GS_FEAT_OFF, Rasterizer, edge_mask, pose_update, tracking_loss_signs, with_device_pose
 
 
 def pose_array(R, t) -> np.ndarray:
@@ -39,7 +40,7 @@ class Tracker:
         self.m, self.v = z(6), z(6)
         self.converged = z(1, dtype=torch.int32)
         self.grads = dict(pose=z(6))
-        self.g_rgb, self.g_depth = z(3, height, width), z(height, width)
+        self.signs = z(height * width, 2, dtype=torch.int32)
         self.alpha_ref = z(height, width)
         self.m_e = z(height, width, dtype=torch.uint8)
         self.loss = z(1)
@@ -63,13 +64,14 @@ class Tracker:
             if it == 1:
                 self.alpha_ref.copy_(fw["alpha"])
             self.loss.zero_()
-            tracking_loss_grad(fw["rgb"], fw["depth"], gt_rgb, gt_depth, self.alpha_ref, self.m_e,
-                               lambda_t=o["lambda_t"], alpha_min=o["alpha_min"], g_rgb=self.g_rgb,
-                               g_depth=self.g_depth, loss=self.loss)
+            signs, weights = tracking_loss_signs(fw["rgb"], fw["depth"], gt_rgb, gt_depth, self.alpha_ref, self.m_e,
+                                                 lambda_t=o["lambda_t"], alpha_min=o["alpha_min"],
+                                                 signs=self.signs, loss=self.loss)
+            fw["l1_signs"] = signs
             if losses is not None:
                 losses.append(self.loss.clone())
             self.grads["pose"].zero_()
-            self.ras.render_pose_grad(cam, means, scales, quats, cols, self.g_rgb, self.g_depth, self.grads)
+            self.ras.render_pose_grad_l1(cam, means, scales, quats, cols, weights, self.grads)
             pose_update(self.pose, self.grads["pose"], self.m, self.v, it, lr_trans=o["lr_trans"],
                         lr_rot=o["lr_rot"], tol_trans=o["tol_trans"], tol_rot=o["tol_rot"],
                         converged=self.converged)
