@@ -126,11 +126,14 @@ __device__ __forceinline__ void l1_term(float pred, float target, float w, int b
   ng |= (d < 0.f ? 1u : 0u) << bit;
 }
 
+// NF > 0: N == NF known at compile time (CHW, vec), so every plane is unrolled.
+template <int NF>
 __global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, int vec, const float* __restrict__ rgb,
                                                   const float* __restrict__ depth, const float* __restrict__ feat,
                                                   const L1Fwd l1) {
   pdl_wait();
   pdl_trigger();
+  const bool V = NF > 0 || vec != 0;  // compile-time true in the specialised kernel
   const long long pix0 = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
   float lsum = 0.f;
   if (pix0 < HW) {
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, 
     const int np = HW - pix0 < 4 ? (int)(HW - pix0) : 4;
     // one plane of 4 consecutive pixels (CHW planes, depth): 16-byte loads with vec
     auto plane4 = [&](const float* a, const float* b, long long off, float w, int bit) {
-      if (vec) {
+      if (V) {
         const float4 x = __ldcs(reinterpret_cast<const float4*>(a + off));
         const float4 y = __ldcs(reinterpret_cast<const float4*>(b + off));
         l1_term(x.x, y.x, w, bit, lsum, nz[0], ng[0]);
@@ -153,9 +156,12 @@ __global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, 
       for (int c = 0; c < 3; ++c) plane4(rgb, l1.target[0], c * HW + pix0, l1.w[0], kL1BitRgb + c);
     if (l1.target[1]) plane4(depth, l1.target[1], pix0, l1.w[1], kL1BitDepth);
     if (l1.target[2]) {
-      if (!hwc) {
+      if (NF > 0) {
+#pragma unroll
+        for (int c = 0; c < NF; ++c) plane4(feat, l1.target[2], c * HW + pix0, l1.w[2], c);
+      } else if (!hwc) {
         for (int c = 0; c < N; ++c) plane4(feat, l1.target[2], c * HW + pix0, l1.w[2], c);
-      } else if (vec) {
+      } else if (V) {
         // the 4 pixels' rows are 4 N consecutive floats
         const float4* a = reinterpret_cast<const float4*>(feat + pix0 * N);
         const float4* b = reinterpret_cast<const float4*>(l1.target[2] + pix0 * N);
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, 
             l1_term(feat[(pix0 + k) * N + c], l1.target[2][(pix0 + k) * N + c], l1.w[2], c, lsum, nz[k], ng[k]);
       }
     }
-    if (vec) {
+    if (V) {
       uint4* o = reinterpret_cast<uint4*>(l1.signs + pix0);
       o[0] = make_uint4(nz[0], ng[0], nz[1], ng[1]);
       o[1] = make_uint4(nz[2], ng[2], nz[3], ng[3]);
@@ -522,8 +528,11 @@ gs_status gs_l1_signs(int32_t width, int32_t height, int32_t N, int32_t layout, 
     if (q && !aligned(q, 16)) vec = false;
   const long long quads = (HW + 3) / 4;
   GS_TRACE("k_l1_signs", S(stream));
-  launch_pdl(k_l1_signs, (unsigned)((quads + 255) / 256), 256, 0, S(stream), HW, N, hwc ? 1 : 0, vec ? 1 : 0, rgb,
-             depth, feat, in);
+  const unsigned grid = (unsigned)((quads + 255) / 256);
+  if (vec && !hwc && N == 16 && in.target[2])
+    launch_pdl(k_l1_signs<16>, grid, 256, 0, S(stream), HW, N, 0, 1, rgb, depth, feat, in);
+  else
+    launch_pdl(k_l1_signs<0>, grid, 256, 0, S(stream), HW, N, hwc ? 1 : 0, vec ? 1 : 0, rgb, depth, feat, in);
   return last_launch_status();
 }
 
