@@ -131,8 +131,21 @@ def algorithmic_bytes(stats):
     (8 B per pixel), which the adjoint (k_render_bwd_mma) reads instead of
     cotangent images."""
     P, Pv, I, HW, N = stats["P"], stats["P_vis"], stats["I"], WIDTH * HEIGHT, N_FEAT
+    T = ((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)
     rec = 8 + 16 + 12 + 4 + 4 * N
     return {
+        # the sort: depth keys (depth and count read, key and id written), four
+        # depth passes over P and two tile passes over I (key and value read
+        # and written), the depth-ordered count scan, emission (the visible
+        # Gaussians' records read, 8 B per instance written), the tile ranges
+        # (4 B per instance read, 8 B per tile written) and the tile order
+        "k_depth_keys": P * 16,
+        "k_os_scatter": 4 * P * 16 + 2 * I * 16,
+        "k_scan_partials": P * 8,
+        "k_scan_top": (P // 256) * 16,
+        "k_emit": Pv * (4 + 4 + 16) + I * 8,
+        "k_tile_ranges": I * 4 + T * 8,
+        "k_tile_order": T * 12,
         "k_project": P * (44 + 48),
         "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12),
         "k_l1_signs": HW * (2 * (4 + N) * 4 + 8),
@@ -498,6 +511,13 @@ def main():
                     "algorithmic_bytes": alg.get(dom),
                     "hbm_frac": round(alg.get(dom, 0) / (km[dom] * 1e-3) / 1e9 / hbm_peak, 4),
                     "hbm_peak_gbs": hbm_peak}
+            # the whole frame against HBM: every kernel's algorithmic bytes over
+            # the frame time (median of the untimed-trace pass)
+            frame_bytes = sum(alg.get(k, 0) for k in km)
+            frame_ms = float(np.median(r["ms"]))
+            roof["frame_algorithmic_bytes"] = round(frame_bytes)
+            roof["frame_hbm_gbs"] = round(frame_bytes / (frame_ms * 1e-3) / 1e9, 1)
+            roof["frame_hbm_frac"] = round(frame_bytes / (frame_ms * 1e-3) / 1e9 / hbm_peak, 4)
         else:
             achieved = alg.get(dom, 0) / (km[dom] * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
