@@ -444,7 +444,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="slam", choices=["slam", "wide", "decoder", "tracking"],
+    ap.add_argument("--workload", default="slam", choices=["slam", "wide", "decoder", "tracking", "features"],
                     help="slam: the headline SLAM-frame workload (N=16); wide: 500k Gaussians with 512 bf16 feature "
                          "channels, tensor-core vs plain fp32; decoder: latent render + learned decoder vs both; "
                          "tracking: the pose-tracking loop of Sec. 3.2 from 1 cm / 1 deg perturbations")
@@ -470,6 +470,8 @@ def main():
     if args.workload != "slam":
         if rank != 0:
             return 0
+        if args.workload == "features":
+            return run_feature_widths(args)
         return run_tracking(args) if args.workload == "tracking" else run_forms(args)
 
     import torch
@@ -679,6 +681,75 @@ def run_tracking(args):
               "final_error_mm": {"mean": float(np.mean([e[0] for e in err])), "max": float(max(e[0] for e in err))},
               "final_error_deg": {"mean": float(np.mean([e[1] for e in err])), "max": float(max(e[1] for e in err))},
               "kernel_ms_per_iteration": {k: round(v, 4) for k, v in per.items()}}
+    print(json.dumps(result))
+    return 0
+
+
+def run_feature_widths(args):
+    """fwd + bwd (decoupled feature gradient, float cotangents) of the SLAM-frame
+    scene (300k Gaussians, 1200x680) at N = 16, 64, 128 and 512 unit-norm bf16
+    feature channels (the first N of one 512-d set), each on the form the
+    library takes for that width: the two-pixel forward and the tensor-core
+    adjoint at N = 16, the 32-channel chunked SIMT kernels at N = 64, the
+    tcgen05 feature contraction at N = 128 and 512."""
+    import numpy as np
+    import torch
+    import paper_2504_19409_gb300 as g
+    from paper_2504_19409_gb300 import scenegen as sg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sc = sg.room_scene(SCENE_SEED, P_ROOM, 512, feat_kind="unit")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    scene = tuple(t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
+    feats512 = t(sc.feats).to(torch.bfloat16)
+    frames = [k % N_FRAMES for k in range(args.warmup + args.steps)]
+    timed = frames[args.warmup:]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(4)
+    g_rgb = torch.randn(3, HEIGHT, WIDTH, device=dev, generator=gen)
+    g_d = torch.randn(HEIGHT, WIDTH, device=dev, generator=gen)
+    widths = {}
+    blends = None
+    for n, form in ((16, "two-pixel forward + tensor-core adjoint"), (64, "chunked SIMT"),
+                    (128, "tcgen05 feature contraction"), (512, "tcgen05 feature contraction")):
+        tcf = n >= 128
+        flags = g.GS_FEAT_ON | (g.GS_FEAT_TENSOR_CORE if tcf else 0)
+        r = g.Rasterizer(P_ROOM, WIDTH, HEIGHT, N=n, layout=g.GS_LAYOUT_HWC, flags=flags, device=dev)
+        fn = feats512[:, :n].contiguous()
+        gf = torch.randn(HEIGHT, WIDTH, n, device=dev, generator=gen) * (1.0 / n)
+        for k in sorted(set(frames)):
+            r.ensure_capacity(frame_camera(k), *scene[:4])
+        if blends is None:
+            blends = {}
+            for k in sorted(set(timed)):
+                blends[k] = int(r.forward(frame_camera(k), *scene, fn)["n_contrib"].sum().item())
+
+        def step(k, r=r, fn=fn, gf=gf):
+            cam = frame_camera(k)
+            r.forward(cam, *scene, fn)
+            r.backward(cam, scene[0], scene[1], scene[2], scene[4], fn, g_rgb, g_d, None, gf)
+
+        for k in frames[:args.warmup]:
+            step(k)
+        ms, _ = _time_frames(step, timed, flush, stream)
+        _, per = _time_frames(step, timed[:3], flush, stream, trace=True)
+        r.check_status()
+        widths[str(n)] = {"form": form, "ms_per_frame": float(np.median(ms)),
+                          "blends_per_s": sum(blends[k] for k in timed) / (sum(ms) / 1e3),
+                          "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
+        del r
+        torch.cuda.empty_cache()
+    result = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+              "dtype": "bf16 features, fp32 accumulation",
+              "config": {"workload": "feature_widths_room300k_1200x680", "gaussians": P_ROOM,
+                         "image": [WIDTH, HEIGHT], "feature_channels": [16, 64, 128, 512],
+                         "features": "unit (bf16), the first N of one 512-d set", "layout": "HWC",
+                         "l2": "flushed between timed steps (512 MB write)"},
+              "value": widths["16"]["blends_per_s"], "ms_per_step": widths["16"]["ms_per_frame"],
+              "widths": widths}
     print(json.dumps(result))
     return 0
 
