@@ -955,6 +955,11 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   const int tile = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g8 = lane >> 2, t4 = lane & 3;  // MMA fragment row group and column pair
+  // feature channels c0 .. c0 + NC - 1 of this block's chunk (blockIdx.y); the
+  // colour, depth and geometric sums belong to chunk 0 alone
+  // (one chunk with the L1 cotangents, which take N <= 16)
+  const int c0 = L1 ? 0 : (int)blockIdx.y * NC;
+  const bool geom = L1 || blockIdx.y == 0;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
   int px[2], py[2];
   thread_pixels<2>(tx, ty, px, py);
@@ -1054,14 +1059,14 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         const float* plane = nullptr;  // channel c of the cotangent, indexed by pixel * pstride
         size_t pstride = 1;
         if (c < NC) {
-          if (p.g_feat && c < p.N) {
-            plane = p.hwc ? p.g_feat + c : p.g_feat + (size_t)c * HW;
+          if (p.g_feat && c0 + c < p.N) {
+            plane = p.hwc ? p.g_feat + c0 + c : p.g_feat + (size_t)(c0 + c) * HW;
             pstride = p.hwc ? (size_t)p.N : 1;
           }
         } else if (c < NC + 3) {
-          if (p.g_rgb) plane = p.g_rgb + (size_t)(c - NC) * HW;
+          if (geom && p.g_rgb) plane = p.g_rgb + (size_t)(c - NC) * HW;
         } else if (c == NC + 3) {
-          plane = p.g_depth;
+          if (geom) plane = p.g_depth;
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s)
@@ -1284,7 +1289,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
         if (gq < NC / 4) {
           if (!p.d_feats) continue;
           if (L1) sum = make_float4(sum.x * p.l1.w[2], sum.y * p.l1.w[2], sum.z * p.l1.w[2], sum.w * p.l1.w[2]);
-          const int c = 4 * gq;
+          const int c = c0 + 4 * gq;
           if (vec && c + 4 <= p.N) {
             if (sum.x != 0.f || sum.y != 0.f || sum.z != 0.f || sum.w != 0.f)
               atomicAdd(reinterpret_cast<float4*>(p.d_feats + (size_t)g * p.N + c), sum);
@@ -1294,7 +1299,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
             for (int k = 0; k < 4; ++k)
               if (c + k < p.N && sv[k] != 0.f) atomicAdd(p.d_feats + (size_t)g * p.N + c + k, sv[k]);
           }
-        } else {
+        } else if (geom) {
           const float wc = L1 ? p.l1.w[0] : 1.f, wd = L1 ? p.l1.w[1] : 1.f;
           if (p.d_colors) {
             if (sum.x != 0.f) atomicAdd(p.d_colors + 3 * (size_t)g, sum.x * wc);
@@ -1304,7 +1309,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
           if (sum.w != 0.f) atomicAdd(p.d_depth + g, sum.w * wd);
         }
       }
-    } else if (lane < n) {
+    } else if (geom && lane < n) {
       // u, v, conic and opacity of Gaussian `lane`: v_u = -sum (A dx + B dy) dp,
       // v_v = -sum (B dx + C dy) dp, v_A = -sum dx^2 dp / 2, v_B = -sum dx dy dp,
       // v_C = -sum dy^2 dp / 2 (dx = u - pixel centre), v_o = sum dp / o
@@ -1405,7 +1410,8 @@ gs_status launch_bwd_mma(const BwdParams& p, unsigned tiles, cudaStream_t st) {
       return GS_ERR_CUDA;
     attr_done.fetch_or(bit);
   }
-  launch_pdl(k_render_bwd_mma<NC, L1>, tiles, mma_bwd::kThreads, smem, st, p);
+  const int chunks = NC > 0 && p.N > NC ? (p.N + NC - 1) / NC : 1;
+  launch_pdl(k_render_bwd_mma<NC, L1>, dim3(tiles, chunks), dim3(mma_bwd::kThreads), smem, st, p);
   return last_launch_status();
 }
 
@@ -1446,7 +1452,9 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_
   p.d_colors = d_colors;
   p.d_feats = d_feats;
   const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
-  if (N <= 16 && !coupled) {
+  // decoupled features up to 64 channels: the tensor-core adjoint, in chunks of
+  // 16 channels above 16 (chunk 0 also does the geometry)
+  if (N <= 64 && !coupled) {
     GS_TRACE("k_render_bwd_mma", st);
     if (p.l1.on) return N <= 0 ? launch_bwd_mma<0, true>(p, tiles, st) : launch_bwd_mma<16, true>(p, tiles, st);
     return N <= 0 ? launch_bwd_mma<0, false>(p, tiles, st) : launch_bwd_mma<16, false>(p, tiles, st);
