@@ -342,7 +342,7 @@ gs_status render_fwd_impl(const gs_camera* cam, int32_t P, const int32_t* tile_r
                                      out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, visible,
                                      nullptr, S(stream));
     if (st != GS_OK) return st;
-    return launch_render_fwd_tc(k, tile_ranges, gids, uv, conic_opacity,
+    return launch_render_fwd_tc(k, tile_ranges, tile_order, gids, uv, conic_opacity,
                                 static_cast<const __nv_bfloat16*>(feats), last_idx, N, out_feat, status,
                                 S(stream));
   }
@@ -444,7 +444,8 @@ gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, c
                                    w_conic, w_depth, d_opacity, d_colors, d_feats, l1, S(stream));
   if (st != GS_OK) return st;
   if (tc && dL_dfeat) {
-    st = launch_render_bwd_feat_tc(k, tile_ranges, gids, uv, conic_opacity, last_idx, dL_dfeat, N, d_feats, status,
+    st = launch_render_bwd_feat_tc(k, tile_ranges, tile_order, gids, uv, conic_opacity, last_idx, dL_dfeat, N, d_feats,
+                                   status,
                                    S(stream));
     if (st != GS_OK) return st;
   }

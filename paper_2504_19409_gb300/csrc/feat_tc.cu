@@ -154,6 +154,7 @@ __device__ __forceinline__ void tmem_wait_ld(float (&v)[G][8]) {
 struct TcFwdParams {
   CamF cam;
   const int2* ranges;
+  const int* order;  // launch order of the tiles, or null
   const uint32_t* gids;
   const float2* uv;
   const float4* co;
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
   const int tid = threadIdx.x, warp = tid >> 5;
   const int m = tid >> 2, q = tid & 3;  // pixel row of the MMA tile, quarter of the K-step
   const int split = blockIdx.x % p.nsplit;
-  const int tile = (blockIdx.x / p.nsplit) >> 1, half = (blockIdx.x / p.nsplit) & 1;
+  const int lt = (blockIdx.x / p.nsplit) >> 1, half = (blockIdx.x / p.nsplit) & 1;
+  const int tile = p.order ? p.order[lt] : lt;
   const int c0 = split * kTcNC, Nc = min(kTcNC, p.N - c0);
   int tmem_cols = 32;
   while (tmem_cols < Nc) tmem_cols *= 2;
@@ -410,13 +412,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
 
 }  // namespace
 
-gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
+                               const float* uv,
                                const float* co, const __nv_bfloat16* feats, const int32_t* last_idx, int N,
                                float* out_feat, int32_t* status, cudaStream_t st) {
   if (N <= 0 || N % 64 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
   TcFwdParams p;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.order = order;
   p.gids = gids;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);
@@ -480,6 +484,7 @@ struct TbSmem {
 struct TcBwdParams {
   CamF cam;
   const int2* ranges;
+  const int* order;  // launch order of the tiles, or null
   const uint32_t* gids;
   const float2* uv;
   const float4* co;
@@ -516,7 +521,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
   TbSmem& S = *reinterpret_cast<TbSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m = tid >> 2, q = tid & 3;
-  const int tile = blockIdx.x >> 1, half = blockIdx.x & 1;
+  const int tile = p.order ? p.order[blockIdx.x >> 1] : (int)(blockIdx.x >> 1), half = blockIdx.x & 1;
   const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
   const int px = tx * kTile + (m & 15);
   const int py = ty * kTile + half * 8 + (m >> 4);
@@ -727,7 +732,8 @@ gs_status launch_bwd_nmb(const TcBwdParams& p, const CamF& cam, cudaStream_t st)
 
 }  // namespace
 
-gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, const uint32_t* gids, const float* uv,
+gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, const int32_t* order,
+                                    const uint32_t* gids, const float* uv,
                                     const float* co, const int32_t* last_idx, const float* g_feat, int N,
                                     float* d_feats, int32_t* status, cudaStream_t st) {
   if (N <= 0 || N % 128 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
@@ -736,6 +742,7 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, cons
   TcBwdParams p;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.order = order;
   p.gids = gids;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);
