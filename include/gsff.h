@@ -242,6 +242,8 @@ gs_status gs_visibility_iou(int32_t P, const uint8_t* vis_a, const uint8_t* vis_
  * there; dL_dfeat and d_feats must be 16-byte aligned (GS_ERR_INVALID_ARG
  * otherwise), since d_feats rows are accumulated with vector atomics.
  * workspace must hold gs_render_bwd_workspace_bytes(P) bytes.
+ * tile_order and inst_masks as for gs_render_fwd: any permutation or NULL,
+ * and the masks of the forward this call differentiates or NULL.
  */
 size_t gs_render_bwd_workspace_bytes(int32_t P);
 gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales,
