@@ -146,6 +146,9 @@ def algorithmic_bytes(stats):
         "k_emit": Pv * (4 + 4 + 16) + I * 8,
         "k_tile_ranges": I * 4 + T * 8,
         "k_tile_order": T * 12,
+        # the per-frame clears: the instance counter, the tile ranges and the
+        # sort's counters and look-back words, the adjoint's workspace
+        "k_zero": 8 + T * 8 + 7200 + (4 * ((P + 2047) // 2048) + 2 * ((I + 2047) // 2048)) * 256 * 8 + P * 24,
         "k_project": P * (44 + 48),
         "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12),
         "k_l1_signs": HW * (2 * (4 + N) * 4 + 8),

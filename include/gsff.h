@@ -141,7 +141,7 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
  * device current (a CUDA runtime query); make that first call before any
  * stream capture. All calls share the one array and it keeps the previous
  * call's contents (the caller zeroes nothing: the sort clears the counters
- * it needs with a memset node on its stream): calls whose work
+ * it needs with a kernel on its stream): calls whose work
  * overlaps on the GPU (several streams or host threads) race on the array and
  * must be serialised by the caller.
  */

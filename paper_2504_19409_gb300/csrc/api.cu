@@ -202,6 +202,17 @@ __global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, 
   }
 }
 
+__global__ void __launch_bounds__(256) k_zero(uint32_t* __restrict__ a, long long na, uint32_t* __restrict__ b,
+                                              long long nb) {
+  pdl_wait();
+  pdl_trigger();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
+    if (i < na) a[i] = 0u;
+    else b[i - na] = 0u;
+  }
+}
+
 // counts[0] += |{g : a_g != 0 and b_g != 0}|, counts[1] += |{g : a_g != 0 or b_g != 0}|.
 __global__ void __launch_bounds__(256) k_vis_iou(int P, const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
                                                  unsigned long long* __restrict__ counts) {
@@ -244,6 +255,17 @@ inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
 constexpr float kBlack[3] = {0.f, 0.f, 0.f};
 
 }  // namespace
+
+gs_status launch_zero(void* a, size_t a_bytes, void* b, size_t b_bytes, cudaStream_t st) {
+  const long long na = (long long)(a_bytes / 4), nb = b ? (long long)(b_bytes / 4) : 0;
+  if (na + nb == 0) return GS_OK;
+  long long blocks = (na + nb + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  GS_TRACE("k_zero", st);
+  launch_pdl(k_zero, (unsigned)blocks, 256, 0, st, static_cast<uint32_t*>(a), na, static_cast<uint32_t*>(b), nb);
+  return last_launch_status();
+}
+
 }  // namespace gsff
 
 using namespace gsff;
@@ -274,7 +296,7 @@ gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const 
   if (!aligned(quats, 16) || !aligned(conic_opacity, 16) || !aligned(rect, 16) || !aligned(uv, 8) ||
       !aligned(n_instances, 8))
     return GS_ERR_INVALID_ARG;
-  if (n_instances && cudaMemsetAsync(n_instances, 0, sizeof(int64_t), S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+  if (n_instances && launch_zero(n_instances, sizeof(int64_t), nullptr, 0, S(stream)) != GS_OK) return GS_ERR_CUDA;
   launch_project(make_cam(*cam), P, means, scales, quats, opacity, uv, conic_opacity, depth, rect, tiles_touched,
                  n_instances, S(stream));
   return last_launch_status();
@@ -435,7 +457,7 @@ gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, c
   float* w_uv = reinterpret_cast<float*>(ws);
   float* w_conic = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256));
   float* w_depth = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256) + align_up((size_t)P * 3 * 4, 256));
-  if (cudaMemsetAsync(workspace, 0, gs_render_bwd_workspace_bytes(P), S(stream)) != cudaSuccess) return GS_ERR_CUDA;
+  if (launch_zero(workspace, gs_render_bwd_workspace_bytes(P), nullptr, 0, S(stream)) != GS_OK) return GS_ERR_CUDA;
   // with the tensor-core form the SIMT adjoint does the geometry only and the
   // feature gradient is a tcgen05 contraction
   gs_status st = launch_render_bwd(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, tc ? 0 : n,

@@ -505,8 +505,11 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   const long long* n_inst = &ctrl->n_eff;
   const size_t lb_pass_p = (size_t)L.nblk_p * kRadix, lb_pass_i = (size_t)L.nblk_i * kRadix;
 
-  if (cudaMemsetAsync(ranges, 0, (size_t)num_tiles * 2 * sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
-  if (cudaMemsetAsync(os, 0, (L.lb - L.os) + L.lb_bytes, st) != cudaSuccess) return GS_ERR_CUDA;
+  // the tile ranges and the passes' counters and look-back words, in one
+  // kernel of the programmatic-launch chain
+  static_assert(sizeof(OsCtrl) % 4 == 0, "cleared in 4-byte words");
+  if (launch_zero(ranges, (size_t)num_tiles * 2 * sizeof(int32_t), os, (L.lb - L.os) + L.lb_bytes, st) != GS_OK)
+    return GS_ERR_CUDA;
   {
     GS_TRACE("k_depth_keys", st);
     launch_pdl(k_depth_keys, L.nblk_p, kDkThreads, 0, st, P, depth, touched, dk, dv, ctrl, os);

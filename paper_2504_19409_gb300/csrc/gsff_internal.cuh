@@ -20,6 +20,10 @@ namespace gsff {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// Clears two device ranges (4-byte aligned, sizes in multiples of 4 bytes; b
+// may be null) with one kernel of the programmatic-launch chain.
+gs_status launch_zero(void* a, size_t a_bytes, void* b, size_t b_bytes, cudaStream_t st);
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               Args&&... args) {
