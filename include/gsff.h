@@ -151,6 +151,15 @@ gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const float* depth
                              int32_t* tile_ranges, int64_t* n_instances, int32_t* status, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * gs_zero -- clears `bytes` bytes of device memory at `ptr` (4-byte aligned,
+ * bytes a multiple of 4) with one kernel that, like the library's other
+ * kernels, is launched as a programmatic dependent of the previous one on the
+ * stream, so a caller's clear between two library calls does not end their
+ * overlap (e.g. the gradient outputs before gs_render_bwd, which accumulates).
+ */
+gs_status gs_zero(void* ptr, size_t bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * gs_tile_order -- a launch order for the compositing kernels: the tiles by
  * descending length of their lists, so that the longest tiles start first
  * and the shortest fill the end of the grid. The paper has no counterpart

@@ -39,7 +39,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
-           "gs_l1_signs", "gs_tracking_loss_signs")
+           "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero")
 
 
 class GsffError(RuntimeError):
@@ -77,6 +77,12 @@ def l1_terms(targets=None, weights=None, loss=None) -> GsL1Terms:
         for k, w in (weights or {}).items():
             setattr(t, "w_" + k, float(w))
     t.loss = None if loss is None else loss.data_ptr()
+    return t
+
+
+def zero_(t, stream=None):
+    """gs_zero: clears a contiguous device tensor in the library's launch chain (see gs_zero)."""
+    _check(lib().gs_zero(_ptr(t), t.numel() * t.element_size(), _stream(stream)), "gs_zero")
     return t
 
 
@@ -130,6 +136,8 @@ def lib():
     L.gs_bin_sort.restype = ctypes.c_int
     L.gs_bin_sort_static.argtypes = [cam_p, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_bin_sort_static.restype = ctypes.c_int
+    L.gs_zero.argtypes = [_vp, _sz, _vp]
+    L.gs_zero.restype = ctypes.c_int
     L.gs_tile_order.argtypes = [_i32, _vp, _vp, _vp]
     L.gs_tile_order.restype = ctypes.c_int
     L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 9 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)
@@ -655,7 +663,7 @@ class Rasterizer:
     def backward(self, cam, means, scales, quats, colors, feats=None, g_rgb=None, g_depth=None, g_alpha=None,
                  g_feat=None, bg=None, coupled=False, zero=True, stream=None):
         if zero:
-            self.grad_arena.zero_()
+            zero_(self.grad_arena, stream)
         render_bwd(cam, means, scales, quats, colors, feats, self.proj, self.sort, self.fwd, g_rgb, g_depth, g_alpha,
                    g_feat, flags=self.flags, layout=self.layout, bg=bg, coupled=coupled, grads=self.grads,
                    workspace=self.bwd_ws, status=self.status, stream=stream)
@@ -675,7 +683,7 @@ class Rasterizer:
         """The adjoint of the L1 loss that the last forward(..., l1_targets=...) evaluated
         (gs_render_bwd_l1)."""
         if zero:
-            self.grad_arena.zero_()
+            zero_(self.grad_arena, stream)
         render_bwd_l1(cam, means, scales, quats, colors, feats, self.proj, self.sort, self.fwd, weights,
                       flags=self.flags, layout=self.layout, bg=bg, grads=self.grads, workspace=self.bwd_ws,
                       status=self.status, stream=stream)

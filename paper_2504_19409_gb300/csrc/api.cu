@@ -324,6 +324,12 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                          S(stream));
 }
 
+gs_status gs_zero(void* ptr, size_t bytes, void* stream) {
+  if (bytes == 0) return GS_OK;
+  if (!ptr || !aligned(ptr, 4) || bytes % 4 != 0) return GS_ERR_INVALID_ARG;
+  return launch_zero(ptr, bytes, nullptr, 0, S(stream));
+}
+
 gs_status gs_tile_order(int32_t num_tiles, const int32_t* tile_ranges, int32_t* tile_order, void* stream) {
   if (num_tiles < 0 || (num_tiles > 0 && (!tile_ranges || !tile_order)) || !aligned(tile_ranges, 8))
     return GS_ERR_INVALID_ARG;

@@ -58,6 +58,8 @@ def test_invalid_arguments_rejected_synchronously(built):
     assert L.gs_tile_order(-1, None, None, None) == g.GS_ERR_INVALID_ARG
     assert L.gs_tile_order(4, None, None, None) == g.GS_ERR_INVALID_ARG
     assert L.gs_tile_order(0, None, None, None) == g.GS_OK
+    assert L.gs_zero(None, 16, None) == g.GS_ERR_INVALID_ARG
+    assert L.gs_zero(None, 0, None) == g.GS_OK
 
 
 def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
