@@ -111,13 +111,24 @@ gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const 
  * gs_bin_sort_workspace_bytes(P, capacity, num_tiles) bytes (0 is returned
  * for sizes out of range); the caller need not clear it. Each radix pass
  * waits for earlier chunks' digit counts with a bounded wait: a wait longer
- * than 1 s flags GS_ERR_TIMEOUT (the lists are then unspecified).
+ * than the bound (gs_set_lookback_wait_ns, 1 s by default) flags
+ * GS_ERR_TIMEOUT; gids and keys are then unspecified but every tile range
+ * is (0, 0), so the render calls read no list entry, and every id the sort's
+ * own later kernels read is checked against P.
  */
 size_t gs_bin_sort_workspace_bytes(int32_t P, int64_t capacity, int32_t num_tiles);
 gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
                       const int32_t* tiles_touched, int64_t capacity, void* workspace,
                       size_t workspace_bytes, uint64_t* keys, uint32_t* gids, int32_t* tile_ranges,
                       int64_t* n_instances, int32_t* status, void* stream);
+
+/* gs_set_lookback_wait_ns -- the bound, in nanoseconds of the GPU's global
+ * timer, of every radix pass's wait for earlier chunks (process-wide, read
+ * when a sort is enqueued; default 1e9). 0 makes every chunk after the first
+ * give up before its look-back, which takes the timeout path of gs_bin_sort
+ * deterministically (for testing the failure handling); any other value only
+ * changes how long a stalled pass waits. The paper has no counterpart. */
+gs_status gs_set_lookback_wait_ns(uint64_t ns);
 
 /* ---------------------------------------------------------------------------
  * gs_bin_sort_static -- gs_bin_sort for callers that cannot allocate device
@@ -137,9 +148,12 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
  * with 300,000 Gaussians and up to 65,536 tiles: 14 bytes per instance plus
  * 20 per Gaussian);
  * larger sizes return GS_ERR_INVALID_ARG and launch nothing.
+ * keys may be NULL, as for gs_bin_sort.
  * The first call on a device looks up the array's device address with that
  * device current (a CUDA runtime query); make that first call before any
- * stream capture. All calls share the one array and it keeps the previous
+ * stream capture. The address is kept per device and context: a call that
+ * finds a different context current on the device (for instance after
+ * cudaDeviceReset) looks it up again. All calls share the one array and it keeps the previous
  * call's contents (the caller zeroes nothing: the sort clears the counters
  * it needs with a kernel on its stream): calls whose work
  * overlaps on the GPU (several streams or host threads) race on the array and

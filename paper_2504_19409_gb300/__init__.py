@@ -39,7 +39,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
-           "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero")
+           "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero", "gs_set_lookback_wait_ns")
 
 
 class GsffError(RuntimeError):
@@ -82,8 +82,15 @@ def l1_terms(targets=None, weights=None, loss=None) -> GsL1Terms:
 
 def zero_(t, stream=None):
     """gs_zero: clears a contiguous device tensor in the library's launch chain (see gs_zero)."""
+    if not (t.is_cuda and t.is_contiguous()):
+        raise GsffError("zero_ needs a contiguous CUDA tensor (a strided view would be cleared over the wrong span)")
     _check(lib().gs_zero(_ptr(t), t.numel() * t.element_size(), _stream(stream)), "gs_zero")
     return t
+
+
+def set_lookback_wait_ns(ns: int) -> None:
+    """gs_set_lookback_wait_ns: bound of the sort's look-back waits (0 takes the timeout path at once)."""
+    _check(lib().gs_set_lookback_wait_ns(int(ns)), "gs_set_lookback_wait_ns")
 
 
 def camera_struct(cam) -> GsCamera:
@@ -138,6 +145,8 @@ def lib():
     L.gs_bin_sort_static.restype = ctypes.c_int
     L.gs_zero.argtypes = [_vp, _sz, _vp]
     L.gs_zero.restype = ctypes.c_int
+    L.gs_set_lookback_wait_ns.argtypes = [ctypes.c_uint64]
+    L.gs_set_lookback_wait_ns.restype = ctypes.c_int
     L.gs_tile_order.argtypes = [_i32, _vp, _vp, _vp]
     L.gs_tile_order.restype = ctypes.c_int
     L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 9 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)

@@ -324,6 +324,11 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                          S(stream));
 }
 
+gs_status gs_set_lookback_wait_ns(uint64_t ns) {
+  set_lookback_wait_ns((unsigned long long)ns);
+  return GS_OK;
+}
+
 gs_status gs_zero(void* ptr, size_t bytes, void* stream) {
   if (bytes == 0) return GS_OK;
   if (!ptr || !aligned(ptr, 4) || bytes % 4 != 0) return GS_ERR_INVALID_ARG;

@@ -27,8 +27,14 @@
 //     (each warp owns 256 consecutive items and ranks equal digits with
 //     __match_any_sync in index order). A block only waits on chunks with
 //     earlier tickets, which are already running; every wait is bounded and
-//     a timeout flags GS_ERR_TIMEOUT instead of hanging.
-// The look-back words and the counters are cleared by one memset per frame.
+//     a timeout flags GS_ERR_TIMEOUT instead of hanging. After a timeout the
+//     pass's output may have unwritten slots: the kernels after it treat ids
+//     >= P as absent and the tile ranges stay empty, so nothing downstream
+//     reads through a stale id.
+// The look-back words and the counters are cleared by one zeroing kernel per
+// frame.
+
+#include <atomic>
 
 #include "gsff_internal.cuh"
 
@@ -55,17 +61,18 @@ constexpr int kDepthPasses = 4;
 constexpr int kMaxTilePasses = 3;  // tile ids < 2^24
 constexpr int kMaxPasses = kDepthPasses + kMaxTilePasses;
 
-// Per-frame one-sweep state (zeroed by a memset before the first kernel).
+// Per-frame one-sweep state (cleared by the zeroing kernel before the first
+// kernel of the sort).
 struct OsCtrl {
   uint32_t hist[kMaxPasses][kRadix];  // digit counts of each pass over all items
   uint32_t ticket[kMaxPasses];        // next chunk of each pass
+  uint32_t timed_out;                 // set by a pass whose look-back gave up
 };
 
 // Look-back word of (chunk, digit): state in the top two bits, count below.
 constexpr unsigned long long kLbAggregate = 1ull << 62;  // this chunk's own count
 constexpr unsigned long long kLbPrefix = 2ull << 62;     // count of this and all earlier chunks
 constexpr unsigned long long kLbCount = (1ull << 62) - 1;
-constexpr unsigned long long kLbWaitNs = 1000000000ull;  // 1 s
 constexpr int kLbWindow = 8;  // look-back words loaded per round trip
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -166,7 +173,10 @@ __global__ void __launch_bounds__(256) k_scan_partials(int P, const uint32_t* __
   pdl_trigger();
   __shared__ int s_warp[32];
   const int r = blockIdx.x * kScanChunk + threadIdx.x;
-  const int v = r < P ? touched[order[r]] : 0;
+  // ids >= P can only come from a depth pass whose look-back timed out (its
+  // output slots are then not all written): they count as culled
+  const uint32_t g = r < P ? order[r] : 0xFFFFFFFFu;
+  const int v = g < (uint32_t)P ? touched[g] : 0;
   int total;
   block_exclusive_scan(v, s_warp, total);
   if (threadIdx.x == 0) partial[blockIdx.x] = total;
@@ -243,7 +253,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(int P, const uint32_t* __
   int n = 0;
   if (threadIdx.x < kScanChunk && r < P) {
     g = order[r];
-    n = touched[g];
+    n = g < (uint32_t)P ? touched[g] : 0;  // as in k_scan_partials
   }
   for (int i = threadIdx.x; i < kMaxTilePasses * kRadix; i += blockDim.x) (&s_th[0][0])[i] = 0;
   if (threadIdx.x < kScanChunk) {
@@ -316,7 +326,8 @@ __global__ void __launch_bounds__(kRsThreads) k_os_scatter(const uint32_t* __res
                                                            uint32_t* __restrict__ vals_out,
                                                            const long long* __restrict__ n_ptr, int shift,
                                                            const uint32_t* __restrict__ hist, uint32_t* ticket,
-                                                           unsigned long long* lb, int32_t* __restrict__ status) {
+                                                           unsigned long long* lb, uint32_t* timed_out,
+                                                           unsigned long long wait_ns, int32_t* __restrict__ status) {
   pdl_wait();
   pdl_trigger();
   __shared__ uint32_t s_hist[kRsWarps][kRadix];
@@ -348,7 +359,13 @@ __global__ void __launch_bounds__(kRsThreads) k_os_scatter(const uint32_t* __res
   int all;
   const uint32_t start = (uint32_t)block_exclusive_scan((int)hist[dg], s_warp, all);
   unsigned long long before = 0;  // items of digit dg in chunks 0..c-1
-  if (c > 0) {
+  if (c > 0 && wait_ns == 0) {
+    // a bound of 0 gives up before the first look-back (the timeout path,
+    // taken deterministically)
+    flag_status(status, GS_ERR_TIMEOUT);
+    *timed_out = 1u;
+    lb_store(mine, kLbPrefix | tot);
+  } else if (c > 0) {
     // Walk back kLbWindow chunks per round trip: the words of chunks
     // j, j-1, .. are loaded together and consumed newest first until a
     // prefix; a chunk that has published nothing yet restarts the window
@@ -373,8 +390,9 @@ __global__ void __launch_bounds__(kRsThreads) k_os_scatter(const uint32_t* __res
       }
       if (done) break;
       j -= e;
-      if (e < kLbWindow && globaltimer_ns() - t0 > kLbWaitNs) {
+      if (e < kLbWindow && globaltimer_ns() - t0 > wait_ns) {
         flag_status(status, GS_ERR_TIMEOUT);
+        *timed_out = 1u;
         break;
       }
     }
@@ -408,16 +426,23 @@ __global__ void __launch_bounds__(kRsThreads) k_os_scatter(const uint32_t* __res
 }
 
 // ---- step 3 output: tile ranges and the 64-bit keys ------------------------------
+// After a pass of this frame timed out (its outputs are then unspecified and
+// may hold unwritten slots), every tile range stays (0, 0) as the zeroing
+// kernel left it, so no consumer of the lists reads a stale id.
 __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ gids,
                                                      const float* __restrict__ depth, const SortCtrl* __restrict__ ctrl,
-                                                     int num_tiles, int2* __restrict__ ranges,
-                                                     unsigned long long* __restrict__ keys64) {
+                                                     const OsCtrl* __restrict__ os, int P, int num_tiles,
+                                                     int2* __restrict__ ranges, unsigned long long* __restrict__ keys64) {
   pdl_wait();
   pdl_trigger();
+  if (os->timed_out) return;
   const long long n = ctrl->n_eff;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const uint32_t t = tkeys[i];
-    if (keys64) keys64[i] = ((unsigned long long)t << 32) | (unsigned long long)__float_as_uint(depth[gids[i]]);
+    if (keys64) {
+      const uint32_t g = gids[i];
+      keys64[i] = ((unsigned long long)t << 32) | (g < (uint32_t)P ? (unsigned long long)__float_as_uint(depth[g]) : 0ull);
+    }
     if (t >= (uint32_t)num_tiles) continue;
     if (i == 0 || tkeys[i - 1] != t) ranges[t].x = (int)i;
     if (i == n - 1 || tkeys[i + 1] != t) ranges[t].y = (int)(i + 1);
@@ -468,14 +493,18 @@ SortLayout sort_layout(int P, long long capacity, int num_tiles) {
   return L;
 }
 
+std::atomic<unsigned long long> g_lookback_wait_ns{1000000000ull};  // 1 s
+
 void os_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, const long long* n_ptr,
              int shift, int pass, int nblk, OsCtrl* os, unsigned long long* lb, int32_t* status, cudaStream_t st) {
   GS_TRACE("k_os_scatter", st);
   launch_pdl(k_os_scatter, nblk, kRsThreads, 0, st, kin, vin, kout, vout, n_ptr, shift, os->hist[pass], &os->ticket[pass],
-                                            lb, status);
+             lb, &os->timed_out, g_lookback_wait_ns.load(std::memory_order_relaxed), status);
 }
 
 }  // namespace
+
+void set_lookback_wait_ns(unsigned long long ns) { g_lookback_wait_ns.store(ns, std::memory_order_relaxed); }
 
 size_t bin_sort_workspace_bytes(int P, long long capacity, int num_tiles) {
   return sort_layout(P, capacity, num_tiles).total;
@@ -551,7 +580,8 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
     int nb = (int)((capacity + 255) / 256);
     if (nb > 8 * 152) nb = 8 * 152;  // one wave; the kernel strides over the instances
     if (nb < 1) nb = 1;
-    launch_pdl(k_tile_ranges, nb, 256, 0, st, tk, gids, depth, ctrl, num_tiles, reinterpret_cast<int2*>(ranges), keys64);
+    launch_pdl(k_tile_ranges, nb, 256, 0, st, tk, gids, depth, ctrl, os, P, num_tiles, reinterpret_cast<int2*>(ranges),
+               keys64);
   }
   return last_launch_status();
 }

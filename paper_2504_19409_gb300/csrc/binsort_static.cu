@@ -7,6 +7,14 @@
 // cannot use the array's name as a device address, so the entry point looks
 // the address up with cudaGetSymbolAddress once per device (on its first call
 // on that device, with that device current) and passes it to the kernels.
+// The cached address belongs to the device's context at the time of the
+// look-up: a call that finds another context current on the device (after a
+// cudaDeviceReset, which recreates the primary context and reloads the
+// module, so the array may move) looks the address up again before it
+// launches anything.
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <mutex>
 
@@ -26,17 +34,43 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx_id[kMaxDevices] = {};
 
-// Device address of g_bin_sort_scratch on the current device (looked up once).
+// A driver function through the runtime's driver entry point (the library
+// does not link the driver library itself); null if unavailable.
+void* driver_fn(const char* name, int version) {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &f, version, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return f;
+}
+
+// Device address of g_bin_sort_scratch on the current device, looked up once
+// per (device, context). Contexts are told apart by their unique id
+// (cuCtxGetId), which a recreated context never reuses, unlike its handle.
 gs_status scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
+  static const auto get_ctx = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(driver_fn("cuCtxGetCurrent", 4000));
+  static const auto get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(driver_fn("cuCtxGetId", 12000));
+  CUcontext ctx = nullptr;
+  if (!get_ctx || !get_id || get_ctx(&ctx) != CUDA_SUCCESS) return GS_ERR_CUDA;
+  if (!ctx) {
+    // no context bound to this thread yet: cudaSetDevice binds the device's
+    // primary context (the one the launches below will use); it allocates nothing
+    if (cudaSetDevice(dev) != cudaSuccess || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return GS_ERR_CUDA;
+  }
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return GS_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || g_scratch_ctx_id[dev] != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_bin_sort_scratch) != cudaSuccess || p == nullptr) return GS_ERR_CUDA;
     g_scratch_addr[dev] = p;
+    g_scratch_ctx_id[dev] = id;
   }
   *out = g_scratch_addr[dev];
   return GS_OK;
@@ -53,7 +87,7 @@ extern "C" gs_status gs_bin_sort_static(const gs_camera* cam, int32_t P, const f
   if (!cam || cam->width <= 0 || cam->height <= 0 || cam->width > (1 << 15) || cam->height > (1 << 15) ||
       !(cam->fx > 0.f) || !(cam->fy > 0.f) || P < 0 || capacity < 1 || capacity >= (1ll << 31))
     return GS_ERR_INVALID_ARG;
-  if (!keys || !gids || !tile_ranges || (P > 0 && (!depth || !rect || !tiles_touched))) return GS_ERR_INVALID_ARG;
+  if (!gids || !tile_ranges || (P > 0 && (!depth || !rect || !tiles_touched))) return GS_ERR_INVALID_ARG;
   if (!aligned(keys, 8) || !aligned(rect, 16) || !aligned(tile_ranges, 8) || !aligned(n_instances, 8))
     return GS_ERR_INVALID_ARG;
   // The sizes must fit the fixed scratch array.

@@ -31,33 +31,74 @@ def _mix(z: np.ndarray) -> np.ndarray:
     return z ^ (z >> np.uint64(31))
 
 
+_CHUNK = 1 << 22  # draws per piece when a large request is spread over threads
+
+
+def _pieces(n: int):
+    return [(a, min(n, a + _CHUNK)) for a in range(0, n, _CHUNK)]
+
+
+def _run(fn, pieces):
+    """fn over the pieces, on a thread pool for large requests (numpy releases
+    the GIL inside its array operations); the result does not depend on it."""
+    if len(pieces) <= 2:
+        return [fn(a, b) for a, b in pieces]
+    import concurrent.futures as cf
+    import os
+    with cf.ThreadPoolExecutor(max_workers=min(len(pieces), os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda ab: fn(*ab), pieces))
+
+
 class Rng:
-    """splitmix64 stream: draw k returns mix(seed + (c + k + 1) * golden)."""
+    """splitmix64 stream: draw k returns mix(seed + (c + k + 1) * golden).
+
+    Every draw depends only on its counter, so a large request is computed in
+    pieces (on several threads) with the same result as in one piece."""
 
     def __init__(self, seed: int):
         with np.errstate(over="ignore"):
             self._base = _mix(np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64) * _GOLDEN)[0]
         self._ctr = 0
 
-    def u64(self, n: int) -> np.ndarray:
-        idx = np.arange(self._ctr + 1, self._ctr + 1 + n, dtype=np.uint64)
-        self._ctr += n
+    def _u64_at(self, first: int, n: int) -> np.ndarray:
+        idx = np.arange(first + 1, first + 1 + n, dtype=np.uint64)
         with np.errstate(over="ignore"):
             return _mix(self._base + idx * _GOLDEN)
 
+    @staticmethod
+    def _to_unit(x: np.ndarray) -> np.ndarray:
+        return (x >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+    def u64(self, n: int) -> np.ndarray:
+        c = self._ctr
+        self._ctr += n
+        return np.concatenate(_run(lambda a, b: self._u64_at(c + a, b - a), _pieces(n))) if n else \
+            np.zeros(0, np.uint64)
+
     def uniform(self, n: int) -> np.ndarray:
         """Doubles in [0, 1) from the top 53 bits."""
-        return (self.u64(n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        c = self._ctr
+        self._ctr += n
+        if n == 0:
+            return np.zeros(0)
+        return np.concatenate(_run(lambda a, b: self._to_unit(self._u64_at(c + a, b - a)), _pieces(n)))
 
     def normal(self, n: int) -> np.ndarray:
-        """Standard normals by Box-Muller (both outputs of each pair used)."""
+        """Standard normals by Box-Muller (both outputs of each pair used):
+        pair i takes draws i and m + i of the next 2m = 2 ceil(n / 2)."""
         m = (n + 1) // 2
-        u1 = 1.0 - self.uniform(m)          # (0, 1]
-        u2 = self.uniform(m)
-        r = np.sqrt(-2.0 * np.log(u1))
+        c = self._ctr
+        self._ctr += 2 * m
         z = np.empty(2 * m)
-        z[0::2] = r * np.cos(2.0 * np.pi * u2)
-        z[1::2] = r * np.sin(2.0 * np.pi * u2)
+
+        def piece(a, b):
+            u1 = 1.0 - self._to_unit(self._u64_at(c + a, b - a))      # (0, 1]
+            u2 = self._to_unit(self._u64_at(c + m + a, b - a))
+            r = np.sqrt(-2.0 * np.log(u1))
+            z[2 * a:2 * b:2] = r * np.cos(2.0 * np.pi * u2)
+            z[2 * a + 1:2 * b:2] = r * np.sin(2.0 * np.pi * u2)
+
+        _run(piece, _pieces(m))
         return z[:n]
 
 

@@ -170,8 +170,10 @@ def test_trained_decoder_beats_linear_and_untrained(dec_mod):
 def test_decoder_tensor_core_forward_within_bound(dec_mod, ora):
     """gs_decoder_fwd_tc rounds z and the GELU output h to bf16 (weights are
     bf16 already); against the oracle on the bf16-rounded z the remaining
-    difference is the rounding of h: |y_tc - y| <= 2^-8 |h| |W2| + 1e-6 per
-    output (2^-8 = twice bf16's unit roundoff)."""
+    difference is the rounding of h, |fl(h) - h| <= u |h| with u = 2^-8 the
+    unit roundoff of bf16 (8 significant bits), the bf16 x bf16 products being
+    exact in fp32: |y_tc - y| <= u |h| |W2| + 1e-6 per output, the 1e-6
+    covering the fp32 arithmetic of h and of the accumulation."""
     from math import erf, sqrt
     dec = dec_mod.Decoder(seed=13)
     _normal_(dec.params["b1"], 0.2, 104)
@@ -198,12 +200,15 @@ def test_decoder_tensor_core_forward_within_bound(dec_mod, ora):
 
 def test_decoder_labels_from_latents_within_bound(dec_mod, ora):
     """gs_decoder_labels_tc against the oracle's decoded field dotted with the
-    queries: z rounded to bf16 (as in the tensor-core decoder), the hidden
-    layer h and the folded G = W2 q^T rounded to bf16, so each logit lies
-    within 2^-8 sum_k |h_k| |G_kl| + 1e-5 (sum_k |h_k| |G_kl| + |c_l|) + 1e-6 of
-    the exact one. Labels must agree wherever the oracle's two largest logits
-    are more than twice that apart; probabilities within twice the pixel's
-    largest bound."""
+    queries: z rounded to bf16 (as in the tensor-core decoder), and both
+    factors of each product, the hidden layer h and the folded G = W2 q^T,
+    rounded to bf16, |fl(h) fl(G) - h G| <= (2u + u^2) |h| |G| with u = 2^-8
+    the unit roundoff of bf16, so each logit lies within
+    (2u + u^2) sum_k |h_k| |G_kl| + 1e-5 (sum_k |h_k| |G_kl| + |c_l|) + 1e-6 of
+    the exact one (the 1e-5 term: the fp32 fold and accumulation). Labels must
+    agree wherever the oracle's two largest logits are more than twice that
+    apart (80 % of this seeded case's pixels); probabilities within twice the
+    pixel's largest bound."""
     from math import erf, sqrt
     dec = dec_mod.Decoder(seed=17)
     _normal_(dec.params["b1"], 0.2, 106)
@@ -225,10 +230,11 @@ def test_decoder_labels_from_latents_within_bound(dec_mod, ora):
     h = 0.5 * h * (1 + np.vectorize(erf)(h / sqrt(2)))
     G, c = W2 @ qn.T, b2 @ qn.T
     hg = np.abs(h) @ np.abs(G)
-    bound = 2.0 ** -8 * hg + 1e-5 * (hg + np.abs(c)) + 1e-6
+    u = 2.0 ** -8
+    bound = (2 * u + u * u) * hg + 1e-5 * (hg + np.abs(c)) + 1e-6
     srt = np.sort(logits, axis=1)
     sure = (srt[:, -1] - srt[:, -2]) > 2 * bound.max(axis=1)
-    assert sure.mean() > 0.9
+    assert sure.mean() > 0.75
     assert np.array_equal(labels.cpu().numpy()[sure], np.argmax(logits, axis=1)[sure])
     e = np.exp(logits - logits.max(1, keepdims=True))
     p_ref = e / e.sum(1, keepdims=True)
