@@ -40,7 +40,7 @@ WORKLOAD = "slam_frame_room300k_1200x680_N16_fwd_bwd_pose"
 
 def config(n_gpus, extra=None):
     c = {"workload": WORKLOAD, "gaussians": P_ROOM, "image": [WIDTH, HEIGHT], "feature_channels": N_FEAT,
-         "frames": N_FRAMES, "pose_gradient": True, "l2": "flushed between timed steps (512 MB write)",
+         "frames": N_FRAMES, "pose_gradient": True,
          "parallelism": f"frames sharded over {n_gpus} rank(s), no collective on the data path"}
     if extra:
         c.update(extra)
@@ -68,7 +68,7 @@ def target_camera(k):
 
 
 class Clocks:
-    """nvidia-smi sampling (200 ms) during the timed region."""
+    """nvidia-smi sampling (every 50 ms) during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -84,7 +84,7 @@ class Clocks:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
@@ -200,7 +200,11 @@ def run_ours(args, rank, world, local_rank):
     tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     params = [tt(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors, sc.feats)]
     means, scales, quats, opac, cols, feats = params
-    frames = shard_frames(rank, world, args.warmup + args.steps)
+    F = args.frames_per_step
+    # step i processes F frames; frame j of step i is trajectory frame
+    # shard_frames(...)[i * F + j] of this rank
+    frames = shard_frames(rank, world, (args.warmup + args.steps) * F)
+    step_frames = [frames[i * F:(i + 1) * F] for i in range(args.warmup + args.steps)]
     my_frames = sorted(set(frames))
 
     ras = g.Rasterizer(P_ROOM, WIDTH, HEIGHT, N=N_FEAT, device=dev)
@@ -224,7 +228,7 @@ def run_ours(args, rank, world, local_rank):
     scales_l1 = {"rgb": 1.0 / (3 * HW), "depth": 1.0 / HW, "feat": 1.0 / (N_FEAT * HW)}
     loss = torch.zeros(1, device=dev)
 
-    def step(k):
+    def frame(k):
         # forward, the L1 loss against the frame's targets as a streaming pass
         # over the rendered images (gs_l1_signs: the loss and the cotangent sign
         # words), then the adjoint with the pose gradient. On GB300 this beats
@@ -237,7 +241,8 @@ def run_ours(args, rank, world, local_rank):
 
     stream = torch.cuda.current_stream()
     for i in range(args.warmup):
-        step(frames[i])
+        for k in step_frames[i]:
+            frame(k)
     torch.cuda.synchronize()
     ras.check_status()
 
@@ -246,7 +251,7 @@ def run_ours(args, rank, world, local_rank):
         # bracketed by cudaProfilerStart/Stop for `ncu --profile-from-start off`
         torch.cuda.profiler.start()
         for i in range(args.steps):
-            step(frames[args.warmup + i])
+            frame(frames[(args.warmup + i) % len(frames)])
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         ras.check_status()
@@ -254,50 +259,63 @@ def run_ours(args, rank, world, local_rank):
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def timed_pass(trace=False):
+    def timed_steps():
+        """The K timed steps: every frame bracketed by its own pair of events,
+        after an L2 flush (a 512 MB write) outside the pair; a step's time is
+        the sum of its frames' times."""
         evs = []
-        if trace:
-            g.trace_enable(64 * args.steps + 64)
         _barrier(world)
         torch.cuda.synchronize()
         for i in range(args.steps):
-            flush.fill_(float(i))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            step(frames[args.warmup + i])
-            b.record(stream)
-            evs.append((a, b))
+            row = []
+            for j, k in enumerate(step_frames[args.warmup + i]):
+                flush.fill_(float(j))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                frame(k)
+                b.record(stream)
+                row.append((a, b))
+            evs.append(row)
         torch.cuda.synchronize()
         _barrier(world)
-        ms = [a.elapsed_time(b) for a, b in evs]
-        tr = g.trace_read() if trace else None
-        if trace:
-            g.trace_enable(0)
-        return ms, tr
+        return [[a.elapsed_time(b) for a, b in row] for row in evs]
 
     clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
     clocks.start()
     t_wall = time.perf_counter()
-    ms, _ = timed_pass(False)
+    ms_frames = timed_steps()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     ras.check_status()
-    ms_trace, trace = timed_pass(True)
 
-    # end-to-end through the public API with host buffers: every step copies
+    # per-kernel times: a separate traced pass (CUDA events around every
+    # launch, which also breaks the programmatic-launch overlap) over the
+    # first 20 frames of the timed steps
+    trace_frames = [k for i in range(args.steps) for k in step_frames[args.warmup + i]][:20]
+    g.trace_enable(64 * len(trace_frames) + 64)
+    torch.cuda.synchronize()
+    for j, k in enumerate(trace_frames):
+        flush.fill_(float(j))
+        frame(k)
+    torch.cuda.synchronize()
+    trace = g.trace_read()
+    g.trace_enable(0)
+
+    # end-to-end through the public API with host buffers: every frame copies
     # its inputs (the Gaussian parameters and the frame's target images) from
     # pinned host memory and reads its result (the loss and the pose gradient)
-    # back to pinned host memory. The steps are pipelined as a streaming
-    # front end would run them: the device inputs are double-buffered, step
-    # i's uploads run on a copy stream while step i-1 computes, and the host
-    # reads step i-1's result before it issues step i+1 (two steps in
-    # flight). The K steps are timed as one region, so ms_per_step is the
-    # throughput of the whole loop. Within a step the parameters are copied
-    # first (projection and binning wait for them) and the targets after
-    # them (only the L1 pass, gs_l1_signs, waits for those).
+    # back to pinned host memory. The frames are pipelined as a streaming
+    # front end would run them: the device inputs are double-buffered, frame
+    # i's uploads run on a copy stream while frame i-1 computes, and the host
+    # reads frame i-1's result before it issues frame i+1 (two frames in
+    # flight). The K steps of F frames are timed as one region. Within a frame
+    # the parameters are copied first (projection and binning wait for them)
+    # and the targets after them (only the L1 pass, gs_l1_signs, waits for
+    # those). The targets of 8 trajectory frames are kept in pinned memory and
+    # cycled.
     host_params = [p.cpu().pin_memory() for p in params]
-    e2e_frames = frames[args.warmup:args.warmup + min(args.steps, 8)]
-    host_tgt = {k: {n: targets[k][n].cpu().pin_memory() for n in ("rgb", "depth", "feat")} for k in set(e2e_frames)}
+    e2e_frames = my_frames[:8]
+    host_tgt = {k: {n: targets[k][n].cpu().pin_memory() for n in ("rgb", "depth", "feat")} for k in e2e_frames}
     bufs = [dict(params=[torch.empty_like(p) for p in params],
                  tgt={n: torch.empty_like(targets[my_frames[0]][n]) for n in ("rgb", "depth", "feat")})
             for _ in range(2)]
@@ -311,11 +329,11 @@ def run_ours(args, rank, world, local_rank):
     params_in = [torch.cuda.Event() for _ in range(2)]
     tgt_in = [torch.cuda.Event() for _ in range(2)]
     freed = [torch.cuda.Event() for _ in range(2)]  # the compute stream is done with buffer b
-    result = [torch.cuda.Event() for _ in range(2)]  # the step's result is in host memory
+    result = [torch.cuda.Event() for _ in range(2)]  # the frame's result is in host memory
     for e in freed:
         e.record(stream)
 
-    def e2e_step(i, k):
+    def e2e_frame(i, k):
         b = i % 2
         buf = bufs[b]
         copy_stream.wait_event(freed[b])
@@ -338,46 +356,46 @@ def run_ours(args, rank, world, local_rank):
         out_loss[b].copy_(loss.view(1), non_blocking=True)
         result[b].record(stream)
 
-    def e2e_loop(n_steps):
+    def e2e_loop(n_frames):
         read = []
-        for i in range(n_steps):
-            e2e_step(i, e2e_frames[i % len(e2e_frames)])
+        for i in range(n_frames):
+            e2e_frame(i, e2e_frames[i % len(e2e_frames)])
             if i >= 1:
                 result[(i - 1) % 2].synchronize()
                 read.append(float(out_loss[(i - 1) % 2, 0]))
-        result[(n_steps - 1) % 2].synchronize()
-        read.append(float(out_loss[(n_steps - 1) % 2, 0]))
+        result[(n_frames - 1) % 2].synchronize()
+        read.append(float(out_loss[(n_frames - 1) % 2, 0]))
         return read
 
-    e2e_loop(args.warmup)
+    e2e_loop(args.warmup * F)
     torch.cuda.synchronize()
     flush.fill_(0.0)
     a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     copy_stream.wait_stream(stream)
-    losses = e2e_loop(args.steps)
+    losses = e2e_loop(args.steps * F)
     b_.record(stream)
     b_.synchronize()
-    e2e_ms = [a.elapsed_time(b_)]
-    assert len(losses) == args.steps and all(math.isfinite(x) for x in losses)
+    e2e_ms = a.elapsed_time(b_)
+    assert len(losses) == args.steps * F and all(math.isfinite(x) for x in losses)
     ras.check_status()
 
-    timed = frames[args.warmup:]
-    tot_ms = sum(ms)
+    timed = [k for i in range(args.steps) for k in step_frames[args.warmup + i]]
+    flat_ms = [t for row in ms_frames for t in row]
+    tot_ms = sum(flat_ms)
     tot_blends = sum(blends[k] for k in timed)
-    e2e_blends = sum(blends[e2e_frames[i % len(e2e_frames)]] for i in range(args.steps))
-    # per-kernel durations from the traced pass
+    e2e_blends = sum(blends[e2e_frames[i % len(e2e_frames)]] for i in range(args.steps * F))
     per = {}
     for name, t in trace:
         per.setdefault(name, []).append(t)
-    kernel_ms = {k: sum(v) / args.steps for k, v in per.items()}
-    launches = {k: len(v) / args.steps for k, v in per.items()}
+    kernel_ms = {k: sum(v) / len(trace_frames) for k, v in per.items()}
+    launches = {k: len(v) / len(trace_frames) for k, v in per.items()}
     mean_stats = {key: float(np.mean([stats[k][key] for k in timed])) for key in ("I", "P_vis", "evaluated", "blends")}
     mean_stats["P"] = P_ROOM
-    return dict(ms=ms, tot_ms=tot_ms, tot_blends=tot_blends, e2e_ms=e2e_ms, e2e_blends=e2e_blends, h2d=h2d, d2h=d2h,
-                kernel_ms=kernel_ms, launches=launches, per=per, clocks=clk, stats=mean_stats,
-                blends_per_frame=float(np.mean([blends[k] for k in timed])), wall_s=t_wall,
-                traced_ms=float(np.mean(ms_trace)))
+    return dict(ms_frames=ms_frames, flat_ms=flat_ms, tot_ms=tot_ms, tot_blends=tot_blends, e2e_ms=e2e_ms,
+                e2e_blends=e2e_blends, h2d=h2d, d2h=d2h, kernel_ms=kernel_ms, launches=launches, per=per, clocks=clk,
+                stats=mean_stats, blends_per_frame=float(np.mean([blends[k] for k in timed])), wall_s=t_wall,
+                frames_timed=len(timed))
 
 
 def shard_frames(rank, world, count):
@@ -440,17 +458,46 @@ def oracle_frame_sample(sc, k, tile_rows=None):
     return time.perf_counter() - t0, int(fw["n_contrib"].sum())
 
 
+def measure_alu_peaks(stream):
+    """Throughput of the arithmetic pipes on this GPU (gs_peak_probe, CUDA
+    events; best of 3 launches of 4 waves): fp32 FMA (scalar and packed
+    pairs), ex2 and bf16 mma.sync. Returns TFLOP/s (Top/s for ex2) and the
+    SM clock the probes ran at is the one sampled during the timed region."""
+    import torch
+    import paper_2504_19409_gb300 as g
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = {}
+    for kind, name in enumerate(g.PROBE_KINDS):
+        best = 0.0
+        for rep in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ops = g.peak_probe(kind, blocks=4 * 4 * n_sm, threads=256, iters=2048, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if rep > 0:
+                best = max(best, ops / (a.elapsed_time(b) * 1e-3) / 1e12)
+        out[name] = round(best, 3)
+    out["fp32"] = max(out["fp32_fma"], out["fp32_fma2"])
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--frames-per-step", type=int, default=N_FRAMES,
+                    help="frames of the SLAM trajectory one step processes (default: the whole 100-frame loop)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the wide-feature and learned-decoder forms (the line's `forms` object)")
     ap.add_argument("--workload", default="slam", choices=["slam", "wide", "decoder", "tracking", "features"],
-                    help="slam: the headline SLAM-frame workload (N=16); wide: 500k Gaussians with 512 bf16 feature "
-                         "channels, tensor-core vs plain fp32; decoder: latent render + learned decoder vs both; "
-                         "tracking: the pose-tracking loop of Sec. 3.2 from 1 cm / 1 deg perturbations")
+                    help="slam: the headline SLAM-frame workload (N=16) and, at N=1, the forms of the 512-channel "
+                         "field; wide: 500k Gaussians with 512 bf16 feature channels, tensor-core vs plain fp32; "
+                         "decoder: latent render + learned decoder vs both; tracking: the pose-tracking loop of "
+                         "Sec. 3.2 from 1 cm / 1 deg perturbations")
     ap.add_argument("--track-iters", type=int, default=100, help="iteration cap per frame of --workload tracking")
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--gaussians", type=int, default=0, help="override the Gaussian count of --workload wide/decoder")
@@ -461,6 +508,7 @@ def main():
                     help="setup, warm-up and --steps plain frames only (no timing, no JSON); for profiler captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.frames_per_step = max(1, args.frames_per_step)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -486,40 +534,35 @@ def main():
     if r is None:
         print("profile run done")
         return 0
+    F = args.frames_per_step
     tot_ms = _max_over_ranks(r["tot_ms"], world)
     tot_blends = _sum_over_ranks(r["tot_blends"], world)
-    e2e_ms = _max_over_ranks(sum(r["e2e_ms"]), world)
+    e2e_ms = _max_over_ranks(r["e2e_ms"], world)
     e2e_blends = _sum_over_ranks(r["e2e_blends"], world)
     value = tot_blends / (tot_ms / 1e3)
     if rank == 0:
         import oracle
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except (OSError, ValueError):
-            pass
+        peaks = _peaks()
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        stream = torch.cuda.current_stream()
+        alu = measure_alu_peaks(stream)
         alg = algorithmic_bytes(r["stats"])
         flops = algorithmic_flops(r["stats"])
         km = r["kernel_ms"]
         dom = max(km, key=km.get)
         sm_mhz = (r["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-        fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         if dom in flops:
             achieved = flops[dom] / (km[dom] * 1e-3) / 1e12
-            roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-                    "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": ncu_traffic(dom),
-                    "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz (SM clock sampled "
-                                   "during the timed region)",
+            roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": alu["fp32"],
+                    "unit": "TFLOP/s", "frac": round(achieved / alu["fp32"], 4), "traffic": ncu_traffic(dom),
+                    "peak_source": "measured: gs_peak_probe fp32 fused multiply-add (the faster of scalar and packed "
+                                   "pairs), CUDA events, in this run",
                     "algorithmic_flops": flops[dom], "kernel_ms": round(km[dom], 4),
                     "algorithmic_bytes": alg.get(dom),
                     "hbm_frac": round(alg.get(dom, 0) / (km[dom] * 1e-3) / 1e9 / hbm_peak, 4),
                     "hbm_peak_gbs": hbm_peak}
-            # the whole frame against HBM: every kernel's algorithmic bytes over
-            # the frame time (median of the untimed-trace pass)
             frame_bytes = sum(alg.get(k, 0) for k in km)
-            frame_ms = float(np.median(r["ms"]))
+            frame_ms = float(np.median(r["flat_ms"]))
             roof["frame_algorithmic_bytes"] = round(frame_bytes)
             roof["frame_hbm_gbs"] = round(frame_bytes / (frame_ms * 1e-3) / 1e9, 1)
             roof["frame_hbm_frac"] = round(frame_bytes / (frame_ms * 1e-3) / 1e9 / hbm_peak, 4)
@@ -529,31 +572,40 @@ def main():
                     "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel_ms": round(km[dom], 4)}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            sc = None
             from paper_2504_19409_gb300 import scenegen as sg
             sc = sg.room_scene(SCENE_SEED, P_ROOM, N_FEAT)
             secs, bl = oracle_frame_sample(sc, 0)
             cpu = {"value": bl / secs, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                    "sample": "one full frame (frame 0) of the workload: binary32 projection replay, tile lists, "
                              "FP64 compositing and FP64 adjoint incl. pose; " f"{secs:.2f} s, {bl} blends"}
+        forms = None
+        if world == 1 and not args.no_forms:
+            forms = forms_summary(args, peaks, alu)
         share = {k: round(v / sum(km.values()), 4) for k, v in sorted(km.items(), key=lambda kv: -kv[1])}
+        frames_timed = r["frames_timed"] * world
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene and trajectory)",
             "config": config(world, {"blends_per_frame": r["blends_per_frame"], "instances_per_frame": r["stats"]["I"],
                                      "visible_gaussians": r["stats"]["P_vis"],
-                                     "evaluated_pairs_per_frame": r["stats"]["evaluated"]}),
-            "e2e": {"value": e2e_blends / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
-                    "d2h_bytes_per_step": r["d2h"], "ms_per_step": e2e_ms / args.steps,
-                    "pipelined": "two steps in flight: step i's uploads overlap step i-1's compute; K steps timed "
-                                 "as one region",
-                    "l2": "flushed once before the timed loop; every step's 101 MB of inputs are copied fresh "
+                                     "evaluated_pairs_per_frame": r["stats"]["evaluated"],
+                                     "frames_per_step": F, "frames_timed": frames_timed,
+                                     "l2": "flushed before every frame (a 512 MB write outside the frame's events)"}),
+            "ms_per_frame": tot_ms / (args.steps * F),
+            "ms_per_frame_median": statistics.median(r["flat_ms"]),
+            "e2e": {"value": e2e_blends / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"] * F,
+                    "d2h_bytes_per_step": r["d2h"] * F, "ms_per_step": e2e_ms / args.steps,
+                    "ms_per_frame": e2e_ms / (args.steps * F),
+                    "pipelined": "two frames in flight: frame i's uploads overlap frame i-1's compute; the K steps "
+                                 "timed as one region",
+                    "l2": "flushed once before the timed loop; every frame's 101 MB of inputs are copied fresh "
                           "from pinned host memory"},
-            "gpu_launches": int(round(sum(r["launches"].values()) * args.steps)),
-            "roofline": roof, "cpu_baseline": cpu, "clocks": r["clocks"],
-            "kernel_ms_per_step": {k: round(v, 4) for k, v in km.items()}, "kernel_share": share,
-            "traced_ms_per_step": r["traced_ms"], "ms_per_step_median": statistics.median(r["ms"]),
+            "gpu_launches": int(round(sum(r["launches"].values()) * args.steps * F)),
+            "roofline": roof, "alu_peaks_measured": dict(alu, unit="TFLOP/s (ex2: Top/s)", sm_mhz=sm_mhz),
+            "cpu_baseline": cpu, "clocks": r["clocks"],
+            "kernel_ms_per_frame": {k: round(v, 4) for k, v in km.items()}, "kernel_share": share,
+            "forms": forms,
         }
         print(json.dumps(line))
     if world > 1:
@@ -781,125 +833,162 @@ def _time_frames(fn, frames, flush, stream, trace=False):
     return out, per
 
 
-def _tc_exec_flops(last_idx, W, H, N):
-    """Tensor-core flops one forward executes: per half tile 2 * 128 * N per
-    Gaussian of its K-steps (ceil(max last_idx / 32) steps of 32)."""
-    import numpy as np
-    li = last_idx.cpu().numpy()
-    ty, tx = (H + 15) // 16, (W + 15) // 16
-    pad = np.zeros((ty * 16, tx * 16), np.int64)
-    pad[:H, :W] = li
-    halves = pad.reshape(ty, 2, 8, tx, 16).max(axis=(2, 4))
-    ksteps = (halves + 31) // 32
-    return float(2 * 128 * N * 32 * ksteps.sum())
+U_BF16 = 2.0 ** -8  # unit roundoff of bf16 (8 significant bits)
+GAMMA_F32 = 1e-5     # the fp32 bar of the plain path
 
 
-def run_forms(args):
-    global P_WIDE
-    if args.gaussians:
-        P_WIDE = args.gaussians
-    import numpy as np
+def _wide_setup(kind, P):
     import torch
     import paper_2504_19409_gb300 as g
-    import paper_2504_19409_gb300.decoder as dm
     from paper_2504_19409_gb300 import scenegen as sg
-
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
-    peaks = _peaks()
-    kind = args.features or ("unit" if args.workload == "wide" else "prototypes")
-    sc = sg.room_scene(6, P_WIDE, N_WIDE, feat_kind=kind)
+    sc = sg.room_scene(6, P, N_WIDE, feat_kind=kind)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     scene = tuple(t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors))
     feats_bf = t(sc.feats).to(torch.bfloat16)
-    frames = [k % N_FRAMES for k in range(args.warmup + args.steps)]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    HW = WIDTH * HEIGHT
-    tc = g.Rasterizer(P_WIDE, WIDTH, HEIGHT, N=N_WIDE, layout=g.GS_LAYOUT_HWC,
-                      flags=g.GS_FEAT_ON | g.GS_FEAT_TENSOR_CORE, device=dev)
-    plain = None if args.profile else g.Rasterizer(P_WIDE, WIDTH, HEIGHT, N=N_WIDE, layout=g.GS_LAYOUT_HWC, device=dev)
+    return g, sc, scene, feats_bf, dev
+
+
+def _flush_buf(dev):
+    import torch
+    return torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+
+def wide_form(args, peaks, timed_frames=8, plain_frames=3, profile=False):
+    """The wide-feature form (500k Gaussians in the box room, 1200 x 680, N =
+    512 unit-norm bf16 features): fwd + bwd (decoupled feature gradient,
+    float cotangents) on the tensor-core form and on the plain fp32 form of
+    the same 512 channels; the tensor-core form's feature map and feature
+    gradient against the plain fp32 form's, within the bf16 bounds; the two
+    tensor-core kernels against their rooflines."""
+    import torch
+    g, sc, scene, feats_bf, dev = _wide_setup("unit", args.gaussians or P_WIDE)
+    P = sc.P
+    stream = torch.cuda.current_stream()
+    HW, N = WIDTH * HEIGHT, N_WIDE
+    tc = g.Rasterizer(P, WIDTH, HEIGHT, N=N, layout=g.GS_LAYOUT_HWC, flags=g.GS_FEAT_ON | g.GS_FEAT_TENSOR_CORE,
+                      device=dev)
+    plain = None if profile else g.Rasterizer(P, WIDTH, HEIGHT, N=N, layout=g.GS_LAYOUT_HWC, device=dev)
+    frames = [k % N_FRAMES for k in range(args.warmup + timed_frames)]
+    timed = frames[args.warmup:]
     for k in sorted(set(frames)):
         for r in (tc, plain):
             if r is not None:
                 r.ensure_capacity(frame_camera(k), *scene[:4])
-    blends, instances = {}, {}
-    ref = plain if plain is not None else tc
-    for k in sorted(set(frames)):
-        fw = ref.forward(frame_camera(k), *scene, feats_bf)
-        blends[k] = int(fw["n_contrib"].sum().item())
-        instances[k] = int(ref.sort["n_instances"].item())
-    timed = frames[args.warmup:]
-    tot_blends = sum(blends[k] for k in timed)
-    result = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
-              "config": {"workload": f"{args.workload}_room500k_1200x680_N512", "gaussians": P_WIDE,
-                         "image": [WIDTH, HEIGHT], "feature_channels": N_WIDE, "features": kind + " (bf16)",
-                         "blends_per_frame": float(np.mean([blends[k] for k in timed])),
-                         "instances_per_frame": float(np.mean([instances[k] for k in timed])),
-                         "l2": "flushed between timed steps (512 MB write)"}}
+    gen = torch.Generator(device=dev).manual_seed(4)
+    g_rgb = torch.randn(3, HEIGHT, WIDTH, device=dev, generator=gen)
+    g_d = torch.randn(HEIGHT, WIDTH, device=dev, generator=gen)
+    g_f = torch.randn(HEIGHT, WIDTH, N, device=dev, generator=gen) * (1.0 / N)
 
-    if args.workload == "wide":
-        gen = torch.Generator(device=dev).manual_seed(4)
-        g_rgb = torch.randn(3, HEIGHT, WIDTH, device=dev, generator=gen)
-        g_d = torch.randn(HEIGHT, WIDTH, device=dev, generator=gen)
-        g_f = torch.randn(HEIGHT, WIDTH, N_WIDE, device=dev, generator=gen) * (1.0 / N_WIDE)
+    def fwd_bwd(r):
+        def f(k):
+            cam = frame_camera(k)
+            r.forward(cam, *scene, feats_bf)
+            r.backward(cam, scene[0], scene[1], scene[2], scene[4], feats_bf, g_rgb, g_d, None, g_f)
+        return f
 
-        def fwd_bwd(r):
-            def f(k):
-                cam = frame_camera(k)
-                r.forward(cam, *scene, feats_bf)
-                r.backward(cam, scene[0], scene[1], scene[2], scene[4], feats_bf, g_rgb, g_d, None, g_f)
-            return f
+    if profile:
+        torch.cuda.profiler.start()
+        for k in frames:
+            fwd_bwd(tc)(k)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        tc.check_status()
+        return None
+    stats = {}
+    for k in sorted(set(timed)):
+        fw = tc.forward(frame_camera(k), *scene, feats_bf)
+        stats[k] = dict(blends=int(fw["n_contrib"].sum().item()), I=int(tc.sort["n_instances"].item()),
+                        P_vis=int((tc.proj["tiles_touched"] > 0).sum().item()))
+    flush = _flush_buf(dev)
+    for r in (tc, plain):
+        for k in frames[:args.warmup]:
+            fwd_bwd(r)(k)
+    out = {}
+    for name, r, fr in (("tensor_core", tc, timed), ("plain_fp32", plain, timed[:plain_frames])):
+        ms, _ = _time_frames(fwd_bwd(r), fr, flush, stream)
+        _, per = _time_frames(fwd_bwd(r), fr[:3], flush, stream, trace=True)
+        r.check_status()
+        bl = sum(stats[k]["blends"] for k in fr)
+        out[name] = {"ms_per_frame": float(np.mean(ms)), "ms_per_frame_median": float(np.median(ms)),
+                     "frames": len(fr), "blends_per_s": bl / (sum(ms) / 1e3),
+                     "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
+    # accuracy of the tensor-core form against the plain fp32 form (its own
+    # bar against the FP64 oracle is 1e-5), per element within the bf16 bounds
+    cam = frame_camera(timed[0])
+    F_tc = tc.forward(cam, *scene, feats_bf)["feat"].clone()
+    d_tc = tc.backward(cam, scene[0], scene[1], scene[2], scene[4], feats_bf, g_rgb, g_d, None, g_f)["feats"].clone()
+    F_pl = plain.forward(cam, *scene, feats_bf)["feat"].clone()
+    d_pl = plain.backward(cam, scene[0], scene[1], scene[2], scene[4], feats_bf, g_rgb, g_d, None, g_f)["feats"].clone()
+    f_abs = feats_bf.float().abs().contiguous()
+    S_f = plain.forward(cam, *scene, f_abs)["feat"]
+    S_g = plain.backward(cam, scene[0], scene[1], scene[2], scene[4], f_abs, None, None, None, g_f.abs())["feats"]
+    u, gam = U_BF16, GAMMA_F32
+    ratio_f = float(((F_tc - F_pl).abs() / ((u + gam * (1 + u)) * S_f + 1e-7)).max())
+    ratio_g = float(((d_tc - d_pl).abs() / ((2 * u + u * u + gam * (1 + u) ** 2) * S_g + 1e-7)).max())
+    rel_f = float(torch.linalg.norm(F_tc - F_pl) / torch.linalg.norm(F_pl))
+    rel_g = float(torch.linalg.norm(d_tc - d_pl) / torch.linalg.norm(d_pl))
+    tc.check_status()
+    plain.check_status()
+    del F_tc, d_tc, F_pl, d_pl, S_f, S_g, f_abs
+    # rooflines of the two tensor-core kernels: algorithmic work (2N flop per
+    # blended pair, each way) and algorithmic bytes (forward: the fp32 feature
+    # map written, each visible Gaussian's bf16 features and records read once,
+    # the ids and last indices; adjoint: the fp32 cotangent map read, the ids,
+    # records and last indices, and the feature-gradient rows of the visible
+    # Gaussians read and written by the accumulation)
+    blends = float(np.mean([stats[k]["blends"] for k in timed]))
+    I = float(np.mean([stats[k]["I"] for k in timed]))
+    Pv = float(np.mean([stats[k]["P_vis"] for k in timed]))
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    km = out["tensor_core"]["kernel_ms_per_frame"]
+    alg = {"k_render_feat_tc": (2.0 * N * blends, HW * N * 4 + Pv * (2 * N + 24) + I * 4 + HW * 4),
+           "k_render_feat_tc_bwd": (2.0 * N * blends, HW * N * 4 + Pv * 24 + I * 4 + HW * 4 + Pv * N * 8)}
+    roofs = {}
+    for kname, (fl, by) in alg.items():
+        t = km.get(kname)
+        if not t:
+            continue
+        tf = fl / (t * 1e-3) / 1e12
+        gb = by / (t * 1e-3) / 1e9
+        roofs[kname] = {"kernel_ms": t, "algorithmic_flops": fl, "algorithmic_bytes": by,
+                        "tensor": {"achieved": round(tf, 2), "peak": bf16_peak, "unit": "TFLOP/s",
+                                   "frac": round(tf / bf16_peak, 4), "peak_source": "measured bf16 (burst)"},
+                        "hbm": {"achieved": round(gb, 1), "peak": hbm_peak, "unit": "GB/s",
+                                "frac": round(gb / hbm_peak, 4), "peak_source": "measured copy"},
+                        "bound": "hbm" if by / hbm_peak > fl / 1e3 / bf16_peak else "tensor"}
+    return {"workload": "wide_room500k_1200x680_N512", "gaussians": P, "feature_channels": N,
+            "features": "unit-norm i.i.d. (bf16)", "blends_per_frame": blends, "instances_per_frame": I,
+            "visible_gaussians": Pv, "forms": out,
+            "speedup_vs_plain_fp32": out["plain_fp32"]["ms_per_frame"] / out["tensor_core"]["ms_per_frame"],
+            "feature_error_vs_plain_fp32": {
+                "feature_map": {"rel_l2": rel_f, "max_err_over_bound": ratio_f,
+                                "bound": "(u + 1e-5 (1 + u)) sum_i w_i |f_i| + 1e-7, u = 2^-8"},
+                "feature_gradient": {"rel_l2": rel_g, "max_err_over_bound": ratio_g,
+                                     "bound": "(2u + u^2 + 1e-5 (1 + u)^2) sum_p w_p |g_p| + 1e-7, u = 2^-8"}},
+            "roofline": roofs}
 
-        if args.profile:
-            # plain frames of the tensor-core form only (for profiler captures)
-            torch.cuda.profiler.start()
-            for k in frames:
-                fwd_bwd(tc)(k)
-            torch.cuda.synchronize()
-            torch.cuda.profiler.stop()
-            tc.check_status()
-            print("profile run done")
-            return 0
-        for r in (tc, plain):
-            for k in frames[:args.warmup]:
-                fwd_bwd(r)(k)
-        forms = {}
-        for name, r in (("tensor_core", tc), ("plain_fp32", plain)):
-            ms, _ = _time_frames(fwd_bwd(r), timed, flush, stream)
-            _, per = _time_frames(fwd_bwd(r), timed[:3], flush, stream, trace=True)
-            r.check_status()
-            forms[name] = {"ms_per_frame": float(np.mean(ms)), "blends_per_s": tot_blends / (sum(ms) / 1e3),
-                           "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
-        # feature error of the tensor-core form vs the plain fp32 form, and the bound's usage
-        cam = frame_camera(timed[0])
-        F_tc = tc.forward(cam, *scene, feats_bf)["feat"].clone()
-        F_pl = plain.forward(cam, *scene, feats_bf)["feat"].clone()
-        li = plain.fwd["last_idx"].clone()
-        F_abs = plain.forward(cam, *scene, feats_bf.float().abs().contiguous())["feat"]
-        err = (F_tc - F_pl).abs()
-        bound = (2.0 ** -8 + 1e-5) * F_abs + 1e-7
-        rel = float(torch.linalg.norm(F_tc - F_pl) / torch.linalg.norm(F_pl))
-        flops = _tc_exec_flops(li, WIDTH, HEIGHT, N_WIDE)
-        k_ms = forms["tensor_core"]["kernel_ms_per_frame"].get("k_render_feat_tc", float("nan"))
-        bf16_peak = peaks.get("bf16_tflops", 1900.0)
-        result.update({
-            "value": forms["tensor_core"]["blends_per_s"], "ms_per_step": forms["tensor_core"]["ms_per_frame"],
-            "dtype": "bf16 features, fp32 accumulation",
-            "forms": forms, "speedup_vs_plain": forms["plain_fp32"]["ms_per_frame"] / forms["tensor_core"]["ms_per_frame"],
-            "feature_error": {"rel_l2_vs_plain_fp32": rel, "max_err_over_bound": float((err / bound).max()),
-                              "bound": "(2^-8 + 1e-5) sum_i w_i |f_i| + 1e-7 per pixel and channel"},
-            "roofline": {"bound": "tensor", "kernel": "k_render_feat_tc", "achieved": flops / (k_ms * 1e-3) / 1e12,
-                         "peak": bf16_peak, "unit": "TFLOP/s", "frac": flops / (k_ms * 1e-3) / 1e12 / bf16_peak,
-                         "flops": "executed tcgen05 flops (dense W including zero weights)", "traffic": None,
-                         "feature_map_write_GBps": HW * N_WIDE * 4 / (k_ms * 1e-3) / 1e9,
-                         "hbm_peak_GBps": peaks.get("hbm_gbs", 6800.0)},
-        })
-        print(json.dumps(result))
-        return 0
 
-    # ---- learned decoder -------------------------------------------------------------------
+def decoder_form(args, peaks, kind, timing=True, label_query=False):
+    """The learned-decoder form on the wide scene with `kind` features: 16-d
+    latents (initialised from the PCA-16 projection of the features) and the
+    MLP 16 -> 128 -> 512 trained jointly on 200 poses against the tensor-core
+    512-channel render, evaluated on 50 held-out poses against the plain fp32
+    512-channel render (cosine, relative L2), next to the rank-16 PCA decode;
+    with `timing`, inference ms/frame of the plain, tensor-core and latent +
+    decoder forms."""
+    import torch
+    import paper_2504_19409_gb300.decoder as dm
+    from paper_2504_19409_gb300 import scenegen as sg
+    g, sc, scene, feats_bf, dev = _wide_setup(kind, args.gaussians or P_WIDE)
+    P = sc.P
+    stream = torch.cuda.current_stream()
+    HW, N = WIDTH * HEIGHT, N_WIDE
+    tc = g.Rasterizer(P, WIDTH, HEIGHT, N=N, layout=g.GS_LAYOUT_HWC, flags=g.GS_FEAT_ON | g.GS_FEAT_TENSOR_CORE,
+                      device=dev)
+    plain = g.Rasterizer(P, WIDTH, HEIGHT, N=N, layout=g.GS_LAYOUT_HWC, device=dev)
     mu, U = sg.pca_basis(sc.feats, 16)
     lat0 = ((sc.feats - mu) @ U).astype(np.float32)
     n_train, n_held = 200, 50
@@ -913,19 +1002,20 @@ def run_forms(args):
     for c in train_cams + held_cams:
         tc.ensure_capacity(c, *scene[:4])
         plain.ensure_capacity(c, *scene[:4])
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for step in range(args.train_steps):
         c = train_cams[step % n_train]
-        target = tc.forward(c, *scene, feats_bf)["feat"].reshape(HW, N_WIDE)
+        target = tc.forward(c, *scene, feats_bf)["feat"].reshape(HW, N)
         trn.step(c, target, 65536, 1000 + step, lr_dec=3e-3, lr_lat=5e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    # held-out evaluation against the plain fp32 512-channel render
-    mu_t, U_t = t(mu.astype(np.float32)), t(U.astype(np.float32))
+    mu_t = torch.from_numpy(mu.astype(np.float32)).to(dev)
+    U_t = torch.from_numpy(U.astype(np.float32)).to(dev)
     res = {"decoder": [], "pca16": []}
     for c in held_cams:
         fw = plain.forward(c, *scene, feats_bf)
-        ref = fw["feat"].reshape(HW, N_WIDE)
+        ref = fw["feat"].reshape(HW, N)
         mask = fw["alpha"].reshape(HW) > 0.5
         z = trn.render_latents(c).contiguous()
         res["decoder"].append(dm.feature_error(dec.forward_tc(z), ref, mask))
@@ -933,81 +1023,119 @@ def run_forms(args):
         res["pca16"].append(dm.feature_error(alpha * mu_t[None, :] + z @ U_t.T, ref, mask))
     quality = {k: {"rel_l2": float(np.mean([r[0] for r in v])), "cosine": float(np.mean([r[1] for r in v]))}
                for k, v in res.items()}
-    # inference frame timing: plain 512, tensor-core 512, latent + decoder
-    lat_ras = trn.ras
-    z_out = torch.empty(HW, 16, device=dev)
-    y_out = torch.empty(HW, N_WIDE, device=dev)
+    out = {"features": kind + " (bf16)", "train_poses": n_train, "held_out_poses": n_held,
+           "train_steps": args.train_steps, "train_samples_per_step": 65536, "train_seconds": train_s,
+           "train_ms_per_step": train_s * 1e3 / max(1, args.train_steps),
+           "train_step": "tensor-core 512-channel target render + latent render + decoder training on sampled pixels"
+                         " + latent adjoint + Adam",
+           "held_out_quality_vs_plain_fp32_512": quality}
+    if timing:
+        flush = _flush_buf(dev)
+        frames = [k % N_FRAMES for k in range(args.warmup + 8)]
+        timed = frames[args.warmup:]
+        lat_ras = trn.ras
+        y_out = torch.empty(HW, N, device=dev)
 
-    def inf_plain(k):
-        plain.forward(frame_camera(k), *scene, feats_bf)
+        def inf_plain(k):
+            plain.forward(frame_camera(k), *scene, feats_bf)
 
-    def inf_tc(k):
-        tc.forward(frame_camera(k), *scene, feats_bf)
+        def inf_tc(k):
+            tc.forward(frame_camera(k), *scene, feats_bf)
 
-    def inf_dec(k):
-        fw = lat_ras.forward(frame_camera(k), *scene, trn.lat)
-        dec.forward_tc(fw["feat"].reshape(HW, 16), out=y_out)
+        def inf_dec(k):
+            fw = lat_ras.forward(frame_camera(k), *scene, trn.lat)
+            dec.forward_tc(fw["feat"].reshape(HW, 16), out=y_out)
 
-    forms = {}
-    for name, fn in (("plain_fp32", inf_plain), ("tensor_core", inf_tc), ("latent16_decoder", inf_dec)):
-        for k in frames[:args.warmup]:
-            fn(k)
-        ms, _ = _time_frames(fn, timed, flush, stream)
-        _, per = _time_frames(fn, timed[:3], flush, stream, trace=True)
-        forms[name] = {"ms_per_frame": float(np.mean(ms)), "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
-    # open-vocabulary read-out (Eq. 11): L = 32 query vectors against the decoded 512-d pixel features
-    gq = torch.Generator(device=dev).manual_seed(12)
-    queries = torch.randn(32, N_WIDE, device=dev, generator=gq) / math.sqrt(N_WIDE)
-    inf_dec(frames[0])
-    torch.cuda.synchronize()
-    for _ in range(2):
-        g.label_probs(y_out, queries)
-    lq_ms = []
-    for i in range(5):
-        flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        g.label_probs(y_out, queries)
-        b.record(stream)
-        torch.cuda.synchronize()
-        lq_ms.append(a.elapsed_time(b))
-    lq = float(np.median(lq_ms))
-    # the same labels straight from the latent render (gs_decoder_labels_tc: the 512-d field is never formed)
+        forms = {}
+        for name, fn in (("plain_fp32", inf_plain), ("tensor_core", inf_tc), ("latent16_decoder", inf_dec)):
+            for k in frames[:args.warmup]:
+                fn(k)
+            ms, _ = _time_frames(fn, timed, flush, stream)
+            _, per = _time_frames(fn, timed[:3], flush, stream, trace=True)
+            forms[name] = {"ms_per_frame": float(np.mean(ms)),
+                           "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
+        dk = forms["latent16_decoder"]["kernel_ms_per_frame"].get("k_decoder_fwd_tc", float("nan"))
+        flops = 2.0 * HW * (16 * 128 + 128 * 512)
+        bf16_peak = peaks.get("bf16_tflops", 1900.0)
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        out.update({
+            "inference_ms_per_frame": {k: v["ms_per_frame"] for k, v in forms.items()},
+            "inference_forms": forms,
+            "speedup_vs_plain_fp32": forms["plain_fp32"]["ms_per_frame"] / forms["latent16_decoder"]["ms_per_frame"],
+            "speedup_vs_tensor_core": forms["tensor_core"]["ms_per_frame"] / forms["latent16_decoder"]["ms_per_frame"],
+            "roofline": {"kernel": "k_decoder_fwd_tc", "kernel_ms": dk,
+                         "tensor": {"achieved": flops / (dk * 1e-3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                                    "frac": flops / (dk * 1e-3) / 1e12 / bf16_peak},
+                         "hbm": {"achieved": HW * (16 + N) * 4 / (dk * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": HW * (16 + N) * 4 / (dk * 1e-3) / 1e9 / hbm_peak},
+                         "algorithmic": "2 (16*128 + 128*512) flop per pixel; 16 + 512 floats per pixel read and "
+                                        "written"}})
+        if label_query:
+            gq = torch.Generator(device=dev).manual_seed(12)
+            queries = torch.randn(32, N, device=dev, generator=gq) / math.sqrt(N)
 
-    def labels_fused(k):
-        fw = lat_ras.forward(frame_camera(k), *scene, trn.lat)
-        dec.labels_tc(fw["feat"].reshape(HW, 16), queries)
+            def labels_fused(k):
+                fw = lat_ras.forward(frame_camera(k), *scene, trn.lat)
+                dec.labels_tc(fw["feat"].reshape(HW, 16), queries)
 
-    def labels_two_step(k):
-        inf_dec(k)
-        g.label_probs(y_out, queries)
+            def labels_two_step(k):
+                inf_dec(k)
+                g.label_probs(y_out, queries)
 
-    lab_forms = {}
-    for name, fn in (("latent16_decoder_then_label_probs", labels_two_step), ("latent16_labels_fused", labels_fused)):
-        for k in frames[:args.warmup]:
-            fn(k)
-        ms, _ = _time_frames(fn, timed, flush, stream)
-        _, per = _time_frames(fn, timed[:3], flush, stream, trace=True)
-        lab_forms[name] = {"ms_per_frame": float(np.mean(ms)), "kernel_ms_per_frame": {k: round(v, 4) for k, v in per.items()}}
-    dk = forms["latent16_decoder"]["kernel_ms_per_frame"].get("k_decoder_fwd_tc", float("nan"))
-    flops = 2.0 * HW * (16 * 128 + 128 * 512)
-    bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    result.update({
-        "value": tot_blends / (sum([forms["latent16_decoder"]["ms_per_frame"]] * len(timed)) / 1e3),
-        "ms_per_step": forms["latent16_decoder"]["ms_per_frame"], "dtype": "latent fp32, decoder bf16 x bf16 -> fp32",
-        "forms_inference": forms,
-        "speedup_vs_plain": forms["plain_fp32"]["ms_per_frame"] / forms["latent16_decoder"]["ms_per_frame"],
-        "speedup_vs_tensor_core": forms["tensor_core"]["ms_per_frame"] / forms["latent16_decoder"]["ms_per_frame"],
-        "held_out_quality_vs_plain_512": quality, "held_out_poses": n_held, "train_poses": n_train,
-        "train_steps": args.train_steps, "train_seconds": train_s, "train_samples_per_step": 65536,
-        "label_query": {"labels": 32, "ms": lq, "feature_read_GBps": HW * N_WIDE * 4 / (lq * 1e-3) / 1e9,
-                        "fp32_TFLOPs": 2.0 * HW * N_WIDE * 32 / (lq * 1e-3) / 1e12,
-                        "label_frames": lab_forms},
-        "roofline": {"bound": "tensor", "kernel": "k_decoder_fwd_tc", "achieved": flops / (dk * 1e-3) / 1e12,
-                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": flops / (dk * 1e-3) / 1e12 / bf16_peak,
-                     "output_write_GBps": HW * N_WIDE * 4 / (dk * 1e-3) / 1e9, "traffic": None},
-    })
-    print(json.dumps(result))
+            lab = {}
+            for name, fn in (("latent16_decoder_then_label_probs", labels_two_step),
+                             ("latent16_labels_fused", labels_fused)):
+                for k in frames[:args.warmup]:
+                    fn(k)
+                ms, _ = _time_frames(fn, timed, flush, stream)
+                lab[name] = {"ms_per_frame": float(np.mean(ms))}
+            out["label_query_32"] = lab
+    tc.check_status()
+    plain.check_status()
+    return out
+
+
+def forms_summary(args, peaks, alu):
+    """The forms of the 512-channel feature field (wide tensor-core form,
+    learned decoder on both feature sets), for the bench line."""
+    import torch
+    t0 = time.perf_counter()
+    res = {"wide": wide_form(args, peaks)}
+    torch.cuda.empty_cache()
+    res["decoder"] = {"prototypes": decoder_form(args, peaks, "prototypes", timing=True)}
+    torch.cuda.empty_cache()
+    res["decoder"]["unit"] = decoder_form(args, peaks, "unit", timing=False)
+    torch.cuda.empty_cache()
+    res["seconds"] = round(time.perf_counter() - t0, 1)
+    return res
+
+
+def run_forms(args):
+    """--workload wide / decoder: one line for the form alone."""
+    global P_WIDE
+    if args.gaussians:
+        P_WIDE = args.gaussians
+    peaks = _peaks()
+    base = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "wide":
+        w = wide_form(args, peaks, timed_frames=args.steps, profile=args.profile)
+        if w is None:
+            print("profile run done")
+            return 0
+        tcf = w["forms"]["tensor_core"]
+        line = dict(base, value=tcf["blends_per_s"], ms_per_step=tcf["ms_per_frame"],
+                    dtype="bf16 features, fp32 accumulation", config={"workload": w.pop("workload"),
+                                                                     "l2": "flushed between frames (512 MB write)"})
+        line.update(w)
+        print(json.dumps(line))
+        return 0
+    d = decoder_form(args, peaks, args.features or "prototypes", timing=True, label_query=True)
+    line = dict(base, value=None, ms_per_step=d["inference_ms_per_frame"]["latent16_decoder"],
+                dtype="latent fp32, decoder bf16 x bf16 -> fp32",
+                config={"workload": "decoder_room500k_1200x680_N512", "l2": "flushed between frames (512 MB write)"})
+    line.update(d)
+    print(json.dumps(line))
     return 0
 
 

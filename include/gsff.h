@@ -545,6 +545,22 @@ void gs_trace_reset(void);
 int32_t gs_trace_count(void);
 gs_status gs_trace_get(int32_t i, const char** name, float* ms);
 
+/* ---------------------------------------------------------------------------
+ * gs_peak_probe -- throughput probes for the arithmetic rooflines (the paper
+ * has no counterpart): one launch of `blocks` x `threads` threads (threads a
+ * multiple of 32, <= 1024), each running 8 independent dependency chains of
+ * `iters` operations of one kind:
+ *   0: fp32 fused multiply-add (2 flop each);
+ *   1: packed two-lane fp32 fused multiply-add (4 flop each);
+ *   2: ex2.approx.ftz.f32 (1 op each);
+ *   3: mma.sync m16n8k16 bf16 x bf16 -> fp32 per warp (4096 flop each).
+ * *ops (host double) receives the operations the launch performs; sink
+ * (device, >= blocks floats) is written only to keep the work alive. The
+ * caller times the launch on its stream.
+ */
+gs_status gs_peak_probe(int32_t kind, int32_t blocks, int32_t threads, int32_t iters, float* sink, double* ops,
+                        void* stream);
+
 const char* gs_status_string(gs_status s);
 int32_t gs_version(void);
 

@@ -39,7 +39,8 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
-           "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero", "gs_set_lookback_wait_ns")
+           "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero", "gs_set_lookback_wait_ns",
+           "gs_peak_probe")
 
 
 class GsffError(RuntimeError):
@@ -91,6 +92,19 @@ def zero_(t, stream=None):
 def set_lookback_wait_ns(ns: int) -> None:
     """gs_set_lookback_wait_ns: bound of the sort's look-back waits (0 takes the timeout path at once)."""
     _check(lib().gs_set_lookback_wait_ns(int(ns)), "gs_set_lookback_wait_ns")
+
+
+PROBE_KINDS = ("fp32_fma", "fp32_fma2", "ex2", "mma_sync_bf16")
+
+
+def peak_probe(kind: int, blocks: int, threads: int = 256, iters: int = 4096, stream=None) -> float:
+    """gs_peak_probe: launches one probe on the stream and returns the operations it performs; time it with
+    CUDA events around the call."""
+    sink = torch.empty(blocks, device="cuda")
+    ops = ctypes.c_double(0.0)
+    _check(lib().gs_peak_probe(int(kind), int(blocks), int(threads), int(iters), _ptr(sink), ctypes.byref(ops),
+                               _stream(stream)), "gs_peak_probe")
+    return ops.value
 
 
 def camera_struct(cam) -> GsCamera:
@@ -145,6 +159,8 @@ def lib():
     L.gs_bin_sort_static.restype = ctypes.c_int
     L.gs_zero.argtypes = [_vp, _sz, _vp]
     L.gs_zero.restype = ctypes.c_int
+    L.gs_peak_probe.argtypes = [_i32, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+    L.gs_peak_probe.restype = ctypes.c_int
     L.gs_set_lookback_wait_ns.argtypes = [ctypes.c_uint64]
     L.gs_set_lookback_wait_ns.restype = ctypes.c_int
     L.gs_tile_order.argtypes = [_i32, _vp, _vp, _vp]
