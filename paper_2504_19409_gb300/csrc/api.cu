@@ -375,7 +375,7 @@ gs_status render_fwd_impl(const gs_camera* cam, int32_t P, const int32_t* tile_r
                                      out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, visible,
                                      nullptr, S(stream));
     if (st != GS_OK) return st;
-    return launch_render_fwd_tc(k, tile_ranges, tile_order, gids, uv, conic_opacity,
+    return launch_render_fwd_tc(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity,
                                 static_cast<const __nv_bfloat16*>(feats), last_idx, N, out_feat, status,
                                 S(stream));
   }

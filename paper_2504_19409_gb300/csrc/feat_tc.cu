@@ -1,35 +1,24 @@
 // Tensor-core (tcgen05) form of the feature channels of Eq. 3.
 //
-// Per tile the N feature channels are a dense contraction: with the tile's
-// depth-sorted list as the contraction index k,
+// Per half tile (16 x 8 = 128 pixels, the M = 128 rows of a tcgen05 tile)
+// the N feature channels are a dense contraction over the tile's
+// depth-sorted list:
 //     F[p, :] = sum_k w[p, k] f[g_k, :],   w[p, k] = alpha_k(p) T_k(p)
-// (w = 0 where pixel p skips or has stopped). One CTA owns half a tile
-// (16 x 8 = 128 pixels = the 128 rows of a tcgen05 M=128 tile) and up to 256
-// of the channels (a 256-column accumulator, so two CTAs share an SM's tensor
-// memory and overlap one's epilogue with the other's main loop), and walks
-// the list in K-steps of 32 Gaussians:
-//   - 4 threads per pixel (512 threads) each evaluate alpha for 8 of the 32
-//     Gaussians with the SIMT kernel's exact skip test; below last_idx no
-//     pixel has stopped, so T_k is the product of (1 - alpha_j) over the
-//     blended j < k, combined across the 4 threads by a width-4 shuffle
-//     scan; each thread stores its 8 weights (bf16) as one 16-byte row of a
-//     core matrix of the A operand [128 x 32] (K-major);
-//   - the 32 feature rows (bf16) are copied with cp.async into the B operand
-//     [32 x N] (MN-major: channels contiguous);
-//   - one thread issues tcgen05.mma kind::f16 (M=128, N<=256 per
-//     instruction, K=16) accumulating F in fp32 in tensor memory (N columns);
-//   - a 3-stage shared-memory ring lets the next step's loads and weights
-//     proceed while the tensor core consumes the current step
-//     (tcgen05.commit -> mbarrier per stage).
-// The epilogue reads F from tensor memory (tcgen05.ld 32x32b), stages it in
-// shared memory and writes it in HWC layout with bulk asynchronous copies. RGB, depth, alpha, T_final and last_idx come from the SIMT
-// forward kernel launched before this one (its last_idx bounds each pixel).
+// (w = 0 where pixel p skips or has stopped). Below a pixel's last index
+// (from the SIMT forward) no pixel has stopped, so T_k is the product of
+// (1 - alpha_j) over the blended j < k. A Gaussian whose footprint does not
+// reach the half tile (the SIMT forward's per-instance skip mask) has w = 0
+// at all its pixels and is left out of the contraction. The weights are
+// rounded to bf16 (A operand, K-major), the features are bf16 (B operand,
+// channels contiguous), and the products accumulate in fp32 in tensor
+// memory. The forward kernel is persistent and warp-specialised (its
+// comment below has the roles); RGB, depth, alpha, T_final and last_idx come
+// from the SIMT forward launched before it.
 //
 // Shared-memory operand layouts (no swizzle; 16-byte core-matrix rows):
 //   A: element (m, k) at (m/8)*512 + (k/8)*128 + (m%8)*16 + (k%8)*2
 //      descriptor LBO = 128 (K direction), SBO = 512 (M direction)
-//   B: element (k, n) at (n/8)*128 + (k/8)*SK + (k%8)*16 + (n%8)*2, SK = Nc*16
-//      (Nc <= 256 channels of this CTA)
+//   B: element (k, n) at (n/8)*128 + (k/8)*SK + (k%8)*16 + (n%8)*2, SK = N*16
 //      descriptor LBO = SK (K direction), SBO = 128 (N direction)
 // Every wait is bounded (1 s of %globaltimer); a timeout flags
 // GS_ERR_TIMEOUT, waits (bounded) for the tensor core, frees tensor memory
@@ -45,29 +34,10 @@
 namespace gsff {
 namespace {
 
-constexpr int kTcPix = 128;    // pixels per CTA = MMA M
-constexpr int kTcThreads = 512;  // 4 threads per pixel
-constexpr int kTcK = 32;       // Gaussians per K-step
-constexpr int kTcStages = 3;
+constexpr int kTcPix = 128;      // pixels per half tile = MMA M
+constexpr int kTcThreads = 512;  // threads of the adjoint's CTA (4 per pixel)
 constexpr int kTcMaxN = 512;
-constexpr int kTcNC = 256;     // channels per CTA (tensor-memory columns of one accumulator)
 constexpr unsigned long long kWaitNs = 1000000000ull;
-
-struct TcStage {
-  uint8_t A[kTcPix * kTcK * 2];       // 8 KB
-  uint8_t B[kTcK * kTcNC * 2];        // 16 KB (256 channels)
-  float2 uv[kTcK];
-  float4 co[kTcK];
-};
-
-struct TcSmem {
-  TcStage st[kTcStages];  // also the epilogue's staging area (128 rows x 528 B)
-  unsigned long long mbar[kTcStages];
-  uint32_t tmem;
-  int maxlast;
-};
-
-static_assert(sizeof(TcStage) * kTcStages >= (kTcPix - 1) * 528 + 512, "epilogue staging does not fit the ring");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -151,183 +121,404 @@ __device__ __forceinline__ void tmem_wait_ld(float (&v)[G][8]) {
                  "+f"(v[g][6]), "+f"(v[g][7]));
 }
 
-struct TcFwdParams {
-  CamF cam;
-  const int2* ranges;
-  const int* order;  // launch order of the tiles, or null
-  const uint32_t* gids;
-  const float2* uv;
-  const float4* co;
-  const __nv_bfloat16* feats;
-  const int* last_idx;
-  int N;          // feature channels in total
-  int nsplit;     // CTAs per half tile, each owning kTcNC channels (the last may own fewer)
-  float* out_feat;
-  int32_t* status;
-};
-
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
   const int n = valid ? 8 : 0;
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
 }
 
-// Gaussian ids a thread needs to issue the copies of one K-step: the record
-// id (threads 0..31) and the ids of its feature rows (16-byte chunks tid and
-// tid + 512). They are fetched one step before use, so no id load stalls the
-// step that issues the copies.
-struct TcIds {
-  uint32_t rec;
-  uint32_t row[2];
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+
+// ---------------------------------------------------------------------------
+// Forward of the feature channels (persistent, warp-specialised).
+//
+// One CTA per SM walks a fixed list of half tiles (128 pixels each; the
+// tiles in the launch order, half tiles dealt to the CTAs round by round,
+// alternating direction). The whole N-channel accumulator of a half tile
+// lives in tensor memory (128 lanes x N fp32 columns). Roles:
+//   warp 0 (producer): per half tile, the largest last index of its pixels
+//     bounds the list; the list is compacted to the Gaussians whose skip
+//     mask (from the SIMT forward) reaches the half tile, which are the only
+//     ones with a nonzero weight there (ids and masks read 128 positions at
+//     a time, one batch ahead; the next half tile's range and last indices
+//     one half tile ahead); every 32 entries fill one stage of a 4-deep
+//     ring: the records (uv, conic and opacity) by cp.async and the id list;
+//   warps 22-29 (loaders): the stage's bf16 feature rows (B operand,
+//     channels contiguous) by 16-byte cp.async, 4 rows per warp; the stage's
+//     "full" barrier completes when every copy has landed;
+//   warps 6-21 (weight builders, 4 threads per pixel, 8 entries each):
+//     alpha of each entry (exact skip test; 0 at or past the pixel's last
+//     index), w = alpha T with T the product of (1 - alpha) over the entries
+//     in front (a width-4 shuffle scan joins the quarters), rounded to bf16
+//     into the A operand (K-major), then the stage's "weights ready" barrier;
+//   warp 1 (one thread): per stage, tcgen05.mma M=128, N<=256 per
+//     instruction, K=16 x 2, accumulating in tensor memory; commits free the
+//     stage, and after the last stage of a half tile signal the epilogue. The
+//     first stage of a half tile waits for the epilogue to have read the
+//     previous accumulator, channel half by channel half;
+//   warps 2-5 (epilogue; warp w reads tensor-memory lanes 32 (w % 4)..):
+//     32 columns at a time into registers, into a 4 KB box of shared memory
+//     in the 128-byte swizzled order, then one TMA tensor store of the box
+//     (32 channels x 16 pixels x 2 rows of the HWC map; the tensor map clips
+//     the image edge); two boxes per warp alternate. Each channel half of
+//     tensor memory is released as soon as every warp has read it.
+// Every wait is bounded (1 s of %globaltimer): a role that gives up flags
+// GS_ERR_TIMEOUT and raises the CTA's abort word, on which every other wait
+// returns, and the CTA drains its copies and tensor-core work before it frees
+// tensor memory.
+constexpr int kFwThreads = 960;
+constexpr int kFwStages = 4;
+constexpr int kFwK = 32;
+constexpr int kFwWarpMma = 1, kFwWarpEpi = 2, kFwWarpBuild = 6, kFwWarpLoad = 22, kFwLoaders = 8;
+constexpr int kFwBuilders = kFwWarpLoad - kFwWarpBuild;  // 16 warps: 4 threads per pixel
+
+struct alignas(1024) FwStage {
+  uint8_t A[kTcPix * kFwK * 2];   // 8 KB: element (m, k) at (m/8)*512 + (k/8)*128 + (m%8)*16 + (k%8)*2
+  uint8_t B[kFwK * kTcMaxN * 2];  // 32 KB: element (k, n) at (n/8)*128 + (k/8)*(16 N) + (k%8)*16 + (n%8)*2
+  float2 uv[kFwK];                // entry k at slot (k % 8) * 4 + k / 8
+  float4 co[kFwK];                // conic and opacity
+  int pos[kFwK];                  // list position (from the tile's start); INT_MAX past the stage's entries
+  uint32_t gid[kFwK];             // Gaussian of entry k (0 past the stage's entries)
+  int nvalid, flags;              // flags: 1 first stage of its half tile, 2 last
 };
-static_assert(kTcK * kTcNC / 8 <= 2 * kTcThreads, "two feature chunks per thread per K-step");
+static_assert(sizeof(FwStage) % 1024 == 0, "stages keep 1024-byte alignment");
 
-__device__ __forceinline__ TcIds tc_fetch_ids(const TcFwdParams& p, int t, int2 rg, int maxlast, int cpr) {
-  const int tid = threadIdx.x;
-  const int base = rg.x + t * kTcK, lim = rg.x + maxlast;
-  TcIds ids{0u, {0u, 0u}};
-  if (tid < kTcK && base + tid < lim) ids.rec = p.gids[base + tid];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int e = tid + i * kTcThreads;
-    if (e < kTcK * cpr) {
-      const int k = e / cpr;
-      if (base + k < lim) ids.row[i] = p.gids[base + k];
-    }
-  }
-  return ids;
+struct FwSmem {
+  FwStage st[kFwStages];
+  uint8_t box[4][2][4096];  // epilogue boxes (1024-aligned: 128-byte swizzle)
+  uint32_t cgid[64];        // the producer's compaction queue
+  int cpos[64];
+  unsigned long long ids[kFwStages], full[kFwStages], ready[kFwStages], empty[kFwStages];
+  unsigned long long acc_full, acc_empty[2], drain;
+  uint32_t tmem;
+  int abort;
+};
+
+static_assert(sizeof(FwSmem) + 1024 <= 227 * 1024, "shared memory of the forward");
+static_assert(kFwWarpBuild * 32 + 4 * kTcPix == kFwWarpLoad * 32, "four builder threads per pixel");
+static_assert((kFwWarpLoad + kFwLoaders) * 32 == kFwThreads && kFwK % kFwLoaders == 0, "loader warps");
+
+struct FwParams {
+  CamF cam;
+  const int2* ranges;
+  const int* order;  // launch order of the tiles, or null
+  const uint32_t* gids;
+  const uint8_t* masks;  // per instance: 8x8-block skip mask of the SIMT forward (bits 0,1: rows 0-7), or null
+  const float2* uv;
+  const float4* co;
+  const __nv_bfloat16* feats;
+  const int* last_idx;
+  int N, tmem_cols, nhalf;
+  int32_t* status;
+};
+
+__device__ __forceinline__ int fw_slot(int k) { return ((k & 7) << 2) | (k >> 3); }
+
+// Half tile number r of this CTA's list (-1 past the end): round r deals
+// half tiles [r G, r G + G) to the G CTAs, in alternating direction.
+__device__ __forceinline__ int fw_half_tile(int r, int nhalf) {
+  const int G = gridDim.x;
+  const int b = (r & 1) ? (G - 1 - (int)blockIdx.x) : (int)blockIdx.x;
+  const int h = r * G + b;
+  return h < nhalf ? h : -1;
 }
 
-// Asynchronous copies of K-step t into stage `st`: the Gaussian records
-// (threads 0..31) and the feature rows (16-byte chunks), zero-filled past the
-// list; one commit group per step.
-__device__ __forceinline__ void tc_issue_loads(const TcFwdParams& p, TcStage& st, int t, int2 rg, int maxlast, int c0,
-                                               int Nc, const TcIds& ids) {
-  const int tid = threadIdx.x;
-  const int base = rg.x + t * kTcK;
-  const int lim = rg.x + maxlast;
-  if (tid < kTcK) {
-    const bool valid = base + tid < lim;
-    cp_async8(smem_u32(&st.uv[rec_slot(tid)]), p.uv + ids.rec, valid);
-    cp_async16(smem_u32(&st.co[rec_slot(tid)]), p.co + ids.rec, valid);
-  }
-  const int cpr = Nc / 8;  // 16-byte chunks of this CTA's channels per feature row
-  const uint32_t SK = (uint32_t)Nc * 16;
-  const uint32_t b0 = smem_u32(st.B);
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int e = tid + i * kTcThreads;
-    if (e < kTcK * cpr) {
-      const int k = e / cpr, c = e - k * cpr;
-      const bool valid = base + k < lim;
-      const __nv_bfloat16* src = p.feats + (size_t)ids.row[i] * p.N + c0 + 8 * c;
-      const uint32_t dst = b0 + (uint32_t)c * 128u + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
-      cp_async16(dst, src, valid);
+// Bounded wait for the phase of the given parity; false (and the abort word
+// raised, GS_ERR_TIMEOUT flagged) after 1 s, false at once if another role
+// has raised the abort word.
+__device__ __forceinline__ bool fw_wait(uint32_t bar, uint32_t parity, volatile int* abort, int32_t* status) {
+  const unsigned long long t0 = gtime();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort) return false;
+    if (gtime() - t0 > kWaitNs) {
+      *abort = 1;
+      flag_status(status, GS_ERR_TIMEOUT);
+      return false;
     }
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdParams p) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int m = tid >> 2, q = tid & 3;  // pixel row of the MMA tile, quarter of the K-step
-  const int split = blockIdx.x % p.nsplit;
-  const int lt = (blockIdx.x / p.nsplit) >> 1, half = (blockIdx.x / p.nsplit) & 1;
-  const int tile = p.order ? p.order[lt] : lt;
-  const int c0 = split * kTcNC, Nc = min(kTcNC, p.N - c0);
-  int tmem_cols = 32;
-  while (tmem_cols < Nc) tmem_cols *= 2;
-  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
-  const int px = tx * kTile + (m & 15);
-  const int py = ty * kTile + half * 8 + (m >> 4);
-  const bool inside = px < p.cam.W && py < p.cam.H;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-  const int2 rg = p.ranges[tile];
-  const int last = inside ? p.last_idx[(size_t)py * p.cam.W + px] : 0;
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
-  if (tid == 0) S.maxlast = 0;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
-                 "r"(tmem_cols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[s])));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (q == 0 && last > 0) atomicMax(&S.maxlast, last);
-  __syncthreads();
-  const int maxlast = S.maxlast;
-  const uint32_t tmem = S.tmem;
-  const int nsteps = (maxlast + kTcK - 1) / kTcK;
-  const uint32_t SK = (uint32_t)Nc * 16;
-  bool ok = true;
+__device__ __forceinline__ void tile_of(const FwParams& p, int h, int& tx, int& ty, int& half) {
+  const int t = p.order ? p.order[h >> 1] : (h >> 1);
+  tx = t % p.cam.tiles_x;
+  ty = t / p.cam.tiles_x;
+  half = h & 1;
+}
 
-  const int cpr = Nc / 8;
-  if (nsteps > 0) tc_issue_loads(p, S.st[0], 0, rg, maxlast, c0, Nc, tc_fetch_ids(p, 0, rg, maxlast, cpr));
-  if (nsteps > 1) tc_issue_loads(p, S.st[1], 1, rg, maxlast, c0, Nc, tc_fetch_ids(p, 1, rg, maxlast, cpr));
-  TcIds next_ids = tc_fetch_ids(p, 2, rg, maxlast, cpr);  // ids of the next K-step to issue
-  float T = 1.f;  // transmittance in front of this K-step (same in the 4 threads of a pixel)
-  int last_issued = -1;  // last K-step whose MMAs were issued (block-uniform)
-  for (int t = 0; t < nsteps && ok; ++t) {
-    const int s = t % kTcStages;
-    TcStage& st = S.st[s];
-    if (t + 1 < nsteps) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    // alphas of my 8 Gaussians (0 where skipped or past last_idx)
-    float a[8];
-    float prod = 1.f;
+// warp 0: compaction, records and the stages' id lists
+__device__ void fw_producer(const FwParams& p, FwSmem& S) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  volatile int* abort = &S.abort;
+  int s = 0;
+  uint32_t ph = 0;  // parity of the ring's current round
+  // the next half tile's range and its pixels' last indices are loaded one
+  // half tile ahead, the ids and masks of the list one batch of 128 ahead
+  auto fetch_meta = [&](int r, int2& rg, int (&li)[4], int& half) {
+    const int h = fw_half_tile(r, p.nhalf);
+    rg = make_int2(0, 0);
+    half = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      a[j] = 0.f;
-      const int k = 8 * q + j, ks = rec_slot(k);
-      PairAlpha pa;
-      if (t * kTcK + k < last && pair_alpha(st.co[ks], st.uv[ks].x - pxc, st.uv[ks].y - pyc, pa)) {
-        a[j] = pa.alpha;
-        prod = __fmul_rn(prod, __fsub_rn(1.f, pa.alpha));
+    for (int i = 0; i < 4; ++i) li[i] = 0;
+    if (h < 0) return;
+    int tx, ty;
+    tile_of(p, h, tx, ty, half);
+    rg = p.ranges[ty * p.cam.tiles_x + tx];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = lane + 32 * i;
+      const int px = tx * kTile + (m & 15), py = ty * kTile + half * 8 + (m >> 4);
+      if (px < p.cam.W && py < p.cam.H) li[i] = p.last_idx[(size_t)py * p.cam.W + px];
+    }
+  };
+  auto fetch_batch = [&](int2 rg, int maxlast, int base, uint32_t (&gb)[4], uint32_t (&mb)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int pos = base + 32 * i + lane;
+      gb[i] = pos < maxlast ? p.gids[rg.x + pos] : 0u;
+      mb[i] = pos < maxlast ? (p.masks ? (uint32_t)p.masks[rg.x + pos] : 0xFu) : 0u;
+    }
+  };
+  int2 nrg;
+  int nli[4], nhalf_;
+  fetch_meta(0, nrg, nli, nhalf_);
+  for (int r = 0;; ++r) {
+    if (fw_half_tile(r, p.nhalf) < 0) break;
+    const int2 rg = nrg;
+    const int half = nhalf_;
+    int maxlast = max(max(nli[0], nli[1]), max(nli[2], nli[3]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
+    fetch_meta(r + 1, nrg, nli, nhalf_);
+    int fill = 0;
+    bool first = true;
+    // emits queue entries [0, n) as one stage: records by cp.async, then the
+    // id list for the loader warps
+    auto emit = [&](int n, bool last) -> bool {
+      FwStage& st = S.st[s];
+      if (!fw_wait(smem_u32(&S.empty[s]), ph ^ 1u, abort, p.status)) return false;
+      const uint32_t g = lane < n ? S.cgid[lane] : 0u;
+      const int slot = fw_slot(lane);
+      cp_async8(smem_u32(&st.uv[slot]), p.uv + g, lane < n);
+      cp_async16(smem_u32(&st.co[slot]), p.co + g, lane < n);
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[s])) : "memory");
+      st.pos[slot] = lane < n ? S.cpos[lane] : 0x7fffffff;
+      st.gid[lane] = g;
+      if (lane == 0) {
+        st.nvalid = n;
+        st.flags = (first ? 1 : 0) | (last ? 2 : 0);
+      }
+      mbar_arrive(smem_u32(&S.full[s]));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&S.ids[s]));
+      first = false;
+      if (++s == kFwStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+      return true;
+    };
+    uint32_t gb[4], mb[4];
+    if (maxlast > 0) fetch_batch(rg, maxlast, 0, gb, mb);
+    for (int base = 0; base < maxlast; base += 128) {
+      uint32_t gc[4], mc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        gc[i] = gb[i];
+        mc[i] = mb[i];
+      }
+      if (base + 128 < maxlast) fetch_batch(rg, maxlast, base + 128, gb, mb);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int pos = base + 32 * i + lane;
+        const bool hit = ((mc[i] >> (2 * half)) & 3u) != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int idx = fill + __popc(bal & lt);
+          S.cgid[idx] = gc[i];
+          S.cpos[idx] = pos;
+        }
+        fill += __popc(bal);
+        __syncwarp();
+        if (fill > 32) {
+          // a full stage, and more entries follow
+          if (!emit(32, false)) return;
+          const bool mv = lane < fill - 32;
+          const uint32_t mg = mv ? S.cgid[32 + lane] : 0u;
+          const int mp = mv ? S.cpos[32 + lane] : 0;
+          __syncwarp();
+          if (mv) {
+            S.cgid[lane] = mg;
+            S.cpos[lane] = mp;
+          }
+          fill -= 32;
+          __syncwarp();
+        }
       }
     }
-    // exclusive product over the quarters before mine (lanes 4m..4m+3)
-    float incl = prod;
-    float y = __shfl_up_sync(0xffffffffu, incl, 1, 4);
-    if (q >= 1) incl = __fmul_rn(incl, y);
-    y = __shfl_up_sync(0xffffffffu, incl, 2, 4);
-    if (q >= 2) incl = __fmul_rn(incl, y);
-    float excl = __shfl_up_sync(0xffffffffu, incl, 1, 4);
-    if (q == 0) excl = 1.f;
-    const float total = __shfl_sync(0xffffffffu, incl, 3, 4);
-    float Tj = __fmul_rn(T, excl);
-    uint32_t packed[4];
+    // the last stage of the half tile (also the one stage of an empty half
+    // tile, whose weights and rows are all zero)
+    if (!emit(fill, true)) return;
+  }
+}
+
+// warps 22-29: the bf16 feature rows of each stage (B operand), 4 rows per
+// warp, by 16-byte cp.async; each lane's copies complete an arrival on the
+// stage's "full" barrier
+__device__ void fw_loader(const FwParams& p, FwSmem& S) {
+  const int lane = threadIdx.x & 31, L = (threadIdx.x >> 5) - kFwWarpLoad;
+  volatile int* abort = &S.abort;
+  const int cpr = p.N / 8;  // 16-byte chunks per feature row
+  const uint32_t SK = (uint32_t)p.N * 16;
+  constexpr int kRows = kFwK / kFwLoaders;
+  int s = 0;
+  uint32_t ph = 0;
+  for (int r = 0;; ++r) {
+    if (fw_half_tile(r, p.nhalf) < 0) break;
+    while (true) {
+      if (!fw_wait(smem_u32(&S.ids[s]), ph, abort, p.status)) return;
+      FwStage& st = S.st[s];
+      const int n = st.nvalid, flags = st.flags;
+      const uint32_t b0 = smem_u32(st.B);
 #pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-      const float w0 = __fmul_rn(a[j], Tj);
-      if (a[j] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j]));
-      const float w1 = __fmul_rn(a[j + 1], Tj);
-      if (a[j + 1] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j + 1]));
-      const __nv_bfloat162 b2 = __floats2bfloat162_rn(w0, w1);
-      packed[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+      for (int i = 0; i < kRows; ++i) {
+        const int k = kRows * L + i;
+        const bool valid = k < n;
+        const __nv_bfloat16* row = p.feats + (size_t)st.gid[k] * p.N;
+        const uint32_t dk = b0 + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
+        for (int c = lane; c < cpr; c += 32) cp_async16(dk + (uint32_t)c * 128u, row + 8 * c, valid);
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[s])) : "memory");
+      if (++s == kFwStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+      if (flags & 2) break;
     }
-    T = __fmul_rn(T, total);
-    *reinterpret_cast<uint4*>(st.A + (m >> 3) * 512 + q * 128 + (m & 7) * 16) =
-        make_uint4(packed[0], packed[1], packed[2], packed[3]);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+}
+
+// warps 6-21: weights, four threads per pixel (entries 8 q .. 8 q + 7 of each
+// stage); T in front of a thread's entries is the product over the quarters
+// before it (width-4 shuffle scan), so the four threads of a pixel carry the
+// same T from stage to stage
+__device__ void fw_builder(const FwParams& p, FwSmem& S) {
+  const int b = threadIdx.x - kFwWarpBuild * 32;
+  const int m = b >> 2, q = b & 3, lane = threadIdx.x & 31;
+  volatile int* abort = &S.abort;
+  int s = 0;
+  uint32_t ph = 0;
+  for (int r = 0;; ++r) {
+    const int h = fw_half_tile(r, p.nhalf);
+    if (h < 0) break;
+    int tx, ty, half;
+    tile_of(p, h, tx, ty, half);
+    const int px = tx * kTile + (m & 15), py = ty * kTile + half * 8 + (m >> 4);
+    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const int last = (px < p.cam.W && py < p.cam.H) ? p.last_idx[(size_t)py * p.cam.W + px] : 0;
+    float T = 1.f;
+    while (true) {
+      if (!fw_wait(smem_u32(&S.full[s]), ph, abort, p.status)) return;
+      FwStage& st = S.st[s];
+      float a[8];
+      float prod = 1.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int sl = 4 * j + q;  // slot of entry 8 q + j
+        a[j] = 0.f;
+        PairAlpha pa;
+        if (st.pos[sl] < last && pair_alpha(st.co[sl], st.uv[sl].x - pxc, st.uv[sl].y - pyc, pa)) {
+          a[j] = pa.alpha;
+          prod = __fmul_rn(prod, __fsub_rn(1.f, pa.alpha));
+        }
+      }
+      // exclusive product over the quarters before mine (lanes 4m .. 4m+3)
+      float incl = prod;
+      float y = __shfl_up_sync(0xffffffffu, incl, 1, 4);
+      if (q >= 1) incl = __fmul_rn(incl, y);
+      y = __shfl_up_sync(0xffffffffu, incl, 2, 4);
+      if (q >= 2) incl = __fmul_rn(incl, y);
+      float excl = __shfl_up_sync(0xffffffffu, incl, 1, 4);
+      if (q == 0) excl = 1.f;
+      const float total = __shfl_sync(0xffffffffu, incl, 3, 4);
+      float Tj = __fmul_rn(T, excl);
+      uint32_t packed[4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        const float w0 = __fmul_rn(a[j], Tj);
+        if (a[j] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j]));
+        const float w1 = __fmul_rn(a[j + 1], Tj);
+        if (a[j + 1] > 0.f) Tj = __fmul_rn(Tj, __fsub_rn(1.f, a[j + 1]));
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(w0, w1);
+        packed[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      T = __fmul_rn(T, total);
+      *reinterpret_cast<uint4*>(st.A + (m >> 3) * 512 + q * 128 + (m & 7) * 16) =
+          make_uint4(packed[0], packed[1], packed[2], packed[3]);
+      const int flags = st.flags;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&S.ready[s]));
+      if (++s == kFwStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+      if (flags & 2) break;
+    }
+  }
+}
+
+// warp 1, one thread: the tensor-core products
+__device__ void fw_mma(const FwParams& p, FwSmem& S, uint32_t tmem) {
+  volatile int* abort = &S.abort;
+  const uint32_t SK = (uint32_t)p.N * 16;
+  int s = 0;
+  uint32_t ph = 0;
+  for (int r = 0;; ++r) {
+    if (fw_half_tile(r, p.nhalf) < 0) break;
+    const uint32_t acc_par = ((uint32_t)r & 1u) ^ 1u;  // the epilogue's release of the previous accumulator
+    while (true) {
+      if (!fw_wait(smem_u32(&S.full[s]), ph, abort, p.status)) return;
+      if (!fw_wait(smem_u32(&S.ready[s]), ph, abort, p.status)) return;
+      FwStage& st = S.st[s];
+      const int flags = st.flags;
+      const bool first = flags & 1;
       const uint32_t a0 = smem_u32(st.A), b0 = smem_u32(st.B);
-      for (int n0 = 0; n0 < Nc; n0 += 256) {
-        const int nn = min(256, Nc - n0);
+      for (int n0 = 0, hb = 0; n0 < p.N; n0 += 256, ++hb) {
+        if (first && !fw_wait(smem_u32(&S.acc_empty[hb]), acc_par, abort, p.status)) return;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int nn = min(256, p.N - n0);
         const uint32_t idesc = idesc_bf16(kTcPix, nn, 1);
 #pragma unroll
-        for (int k16 = 0; k16 < kTcK / 16; ++k16) {
-          const uint64_t ad = smem_desc(a0 + k16 * 256, 128, 512);
+        for (int k16 = 0; k16 < kFwK / 16; ++k16) {
+          const uint64_t ad = smem_desc(a0 + (uint32_t)k16 * 256u, 128, 512);
           const uint64_t bd = smem_desc(b0 + (uint32_t)(n0 / 8) * 128u + (uint32_t)k16 * 2u * SK, SK, 128);
-          const uint32_t acc = (t > 0 || k16 > 0) ? 1u : 0u;
+          const uint32_t acc = (!first || k16 > 0) ? 1u : 0u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)n0),
@@ -335,112 +526,173 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_render_feat_tc(const TcFwdPar
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&S.mbar[s])));
-    }
-    last_issued = t;
-    if (t + 2 < nsteps) {
-      // stage (t+2)%3 was last read by the MMAs of step t-1
-      bool w_ok = true;
-      if (t >= 1) w_ok = mbar_wait(smem_u32(&S.mbar[(t - 1) % kTcStages]), (uint32_t)(((t - 1) / kTcStages) & 1));
-      ok = __syncthreads_and(w_ok) != 0;
-      if (ok) {
-        tc_issue_loads(p, S.st[(t + 2) % kTcStages], t + 2, rg, maxlast, c0, Nc, next_ids);
-        next_ids = tc_fetch_ids(p, t + 3, rg, maxlast, cpr);
+          smem_u32(&S.empty[s])));
+      if (flags & 2)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&S.acc_full)));
+      if (++s == kFwStages) {
+        s = 0;
+        ph ^= 1u;
       }
+      if (flags & 2) break;
     }
   }
-  if (nsteps > 0 && ok) {
-    const int tl = nsteps - 1;
-    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar[tl % kTcStages]), (uint32_t)((tl / kTcStages) & 1))) != 0;
-  }
-  if (!ok) {
-    if (tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
-    // bounded drain of the last issued commit before freeing tensor memory
-    if (last_issued >= 0)
-      mbar_wait(smem_u32(&S.mbar[last_issued % kTcStages]), (uint32_t)((last_issued / kTcStages) & 1));
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok) {
-    // Epilogue through shared memory and the bulk-copy engine: for each slab
-    // of pw <= 128 columns (the last slab of a 192-channel share is 64 wide),
-    // warp w (tensor-memory lanes 32*(w%4).., column quarter w/4) stages its
-    // 32 x 32 block into the idle operand ring with rows padded to 528 B
-    // (conflict-free 16-byte stores), then one thread per pixel row issues a
-    // bulk copy of its pw * 4 contiguous bytes into the HWC output.
-    uint8_t* stage = S.st[0].A;  // >= 128 * 528 bytes of the idle ring
-    const uint32_t stage_u32 = smem_u32(stage);
-    const int row = 32 * (warp & 3) + (tid & 31);
-    const int PW = Nc < 128 ? Nc : 128;
-    for (int p0 = 0; p0 < Nc; p0 += PW) {
-      const int pw = min(PW, Nc - p0);  // columns in this slab: a multiple of 32 (Nc % 64 == 0)
-      const int cbase = 32 * (warp >> 2);
-      if (cbase < pw) {
-        float v[32];
-        if (nsteps > 0) {
-          tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(p0 + cbase), v);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = 0.f;
-        }
-        uint8_t* dst = stage + row * 528 + cbase * 4;
-#pragma unroll
-        for (int i = 0; i < 32; i += 4)
-          *reinterpret_cast<float4*>(dst + i * 4) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
+
+// warps 2-5: tensor memory -> swizzled boxes -> TMA tensor stores
+__device__ void fw_epilogue(const FwParams& p, FwSmem& S, uint32_t tmem, const CUtensorMap* omap) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int qd = warp & 3;  // tensor-memory lanes 32 qd .. 32 qd + 31 = pixel rows 2 qd, 2 qd + 1 of the half tile
+  volatile int* abort = &S.abort;
+  const int nbox = p.N / 32;
+  const int half0 = min(p.N, 256) / 32;  // boxes of the first channel half
+  int used = 0;  // boxes this warp has stored so far
+  for (int r = 0;; ++r) {
+    const int h = fw_half_tile(r, p.nhalf);
+    if (h < 0) break;
+    int tx, ty, half;
+    tile_of(p, h, tx, ty, half);
+    if (!fw_wait(smem_u32(&S.acc_full), (uint32_t)r & 1u, abort, p.status)) return;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int x0 = tx * kTile, y0 = ty * kTile + half * 8 + 2 * qd;
+    for (int c = 0; c < nbox; ++c, ++used) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * c), v);
+      if (c + 1 == half0 || c + 1 == nbox) {
+        // this warp has read every column of the channel half: release it
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&S.acc_empty[c + 1 == half0 ? 0 : 1]));
       }
+      uint8_t* box = S.box[qd][used & 1];
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // the box's last store has read it
+      __syncwarp();
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch)
+        *reinterpret_cast<float4*>(box + lane * 128 + ((ch ^ (lane & 7)) << 4)) =
+            make_float4(v[4 * ch], v[4 * ch + 1], v[4 * ch + 2], v[4 * ch + 3]);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid < kTcPix) {
-        const int ex = tx * kTile + (tid & 15), ey = ty * kTile + half * 8 + (tid >> 4);
-        if (ex < p.cam.W && ey < p.cam.H) {
-          float* g = p.out_feat + ((size_t)ey * p.cam.W + ex) * p.N + c0 + p0;
-          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g),
-                       "r"(stage_u32 + (uint32_t)tid * 528u), "r"(pw * 4)
-                       : "memory");
-        }
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile(
+            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(omap),
+            "r"(smem_u32(box)), "r"(32 * c), "r"(x0), "r"(y0)
+            : "memory");
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       }
-      __syncthreads();
     }
-    if (tid < kTcPix) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+}
+
+__global__ void __launch_bounds__(kFwThreads, 1) k_render_feat_tc(const FwParams p,
+                                                                  const __grid_constant__ CUtensorMap omap) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  FwSmem& S = *reinterpret_cast<FwSmem*>(smem_raw + pad);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pdl_wait();
+  pdl_trigger();
+  if (tid == 0) {
+    for (int s = 0; s < kFwStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.ids[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.full[s])), "r"(64 + 32 * kFwLoaders));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.ready[s])), "r"(kFwBuilders));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.acc_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&S.acc_empty[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&S.acc_empty[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.drain)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    S.abort = 0;
+  }
+  if (warp == kFwWarpMma) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(p.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = S.tmem;
+
+  if (warp == 0) {
+    fw_producer(p, S);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == kFwWarpMma) {
+    if (lane == 0) {
+      fw_mma(p, S, tmem);
+      // every product issued has completed before tensor memory is freed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.drain)));
+      volatile int never = 0;
+      fw_wait(smem_u32(&S.drain), 0u, &never, p.status);
+    }
+  } else if (warp >= kFwWarpEpi && warp < kFwWarpBuild) {
+    fw_epilogue(p, S, tmem, &omap);
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  } else if (warp < kFwWarpLoad) {
+    fw_builder(p, S);
+  } else {
+    fw_loader(p, S);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == kFwWarpMma) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+  }
 }
 
 }  // namespace
 
 gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                               const float* uv,
-                               const float* co, const __nv_bfloat16* feats, const int32_t* last_idx, int N,
-                               float* out_feat, int32_t* status, cudaStream_t st) {
+                               const uint8_t* masks, const float* uv, const float* co, const __nv_bfloat16* feats,
+                               const int32_t* last_idx, int N, float* out_feat, int32_t* status, cudaStream_t st) {
   if (N <= 0 || N % 64 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
-  TcFwdParams p;
+  FwParams p;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.order = order;
   p.gids = gids;
+  p.masks = masks;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);
   p.feats = feats;
   p.last_idx = last_idx;
   p.N = N;
-  p.nsplit = (N + kTcNC - 1) / kTcNC;
-  p.out_feat = out_feat;
+  int cols = 32;
+  while (cols < N) cols *= 2;
+  p.tmem_cols = cols;
+  p.nhalf = 2 * cam.tiles_x * cam.tiles_y;
   p.status = status;
-  const size_t smem = sizeof(TcSmem) + 1024;
+  // the HWC feature map as a 3D tensor (channels, x, y) for the epilogue's
+  // TMA stores of 32 x 16 x 2 boxes with 128-byte swizzle
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return GS_ERR_CUDA;
+  CUtensorMap omap;
+  const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)cam.W, (cuuint64_t)cam.H};
+  const cuuint64_t strides[2] = {(cuuint64_t)N * sizeof(float), (cuuint64_t)cam.W * N * sizeof(float)};
+  const cuuint32_t boxdim[3] = {32, 16, 2};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (encode(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, out_feat, dims, strides, boxdim, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return GS_ERR_CUDA;
+  const size_t smem = sizeof(FwSmem) + 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_render_feat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_render_feat_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_render_feat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return GS_ERR_CUDA;
     attr_set = true;
   }
-  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2 * p.nsplit);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned blocks = (unsigned)(p.nhalf < sms ? p.nhalf : sms);
   GS_TRACE("k_render_feat_tc", st);
-  k_render_feat_tc<<<blocks, kTcThreads, smem, st>>>(p);
+  launch_pdl(k_render_feat_tc, blocks, kFwThreads, smem, st, p, omap);
   return last_launch_status();
 }
 
@@ -969,22 +1221,6 @@ __global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p,
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library); looked up once.
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  });
-  return fn;
 }
 
 }  // namespace
