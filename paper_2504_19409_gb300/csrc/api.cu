@@ -477,7 +477,8 @@ gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, c
                                    w_conic, w_depth, d_opacity, d_colors, d_feats, l1, S(stream));
   if (st != GS_OK) return st;
   if (tc && dL_dfeat) {
-    st = launch_render_bwd_feat_tc(k, tile_ranges, tile_order, gids, uv, conic_opacity, last_idx, dL_dfeat, N, d_feats,
+    st = launch_render_bwd_feat_tc(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, last_idx, dL_dfeat,
+                                   N, d_feats,
                                    status,
                                    S(stream));
     if (st != GS_OK) return st;

@@ -35,7 +35,6 @@ namespace gsff {
 namespace {
 
 constexpr int kTcPix = 128;      // pixels per half tile = MMA M
-constexpr int kTcThreads = 512;  // threads of the adjoint's CTA (4 per pixel)
 constexpr int kTcMaxN = 512;
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
@@ -95,11 +94,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-// Record slot of the k-th Gaussian of a 32-Gaussian step: thread quarter q
-// reads Gaussians 8q..8q+7, so slot 4 (k % 8) + k / 8 puts the four quarters'
-// j-th records side by side (one bank group, no conflicts).
-__device__ __forceinline__ int rec_slot(int k) { return ((k & 7) << 2) | (k >> 3); }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
@@ -700,202 +694,229 @@ gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const int
 // ===========================================================================
 // Adjoint of the feature channels in the paper's decoupled mode (Sec. 3.1:
 // the feature cotangent reaches only f): dL/df_g = sum_p w_g(p) dL/dF(p, :).
-// Per half tile, transposed so that every operand keeps a validated layout:
+// Per half tile and block of 32 Gaussians, transposed so that every operand
+// keeps a validated layout:
 //     D [N channels x 32 Gaussians] = dF^T [N x 128 px] * W [128 px x 32]
-//   A = dF^T, K-major, converted to bf16 once per CTA, NMB = N/128 M-blocks.
-//       Channel c sits in M-block c % NMB, row r = c / NMB, so that a
-//       tensor-memory lane r holds the NMB contiguous channels NMB r .. and
-//       the epilogue adds them with one vector atomic:
+//   A = dF^T, K-major, bf16, NMB = N/128 M-blocks; channel c sits in M-block
+//       c % NMB, row r = c / NMB, so that a tensor-memory lane r holds the
+//       NMB contiguous channels NMB r .. and the epilogue adds them with one
+//       vector atomic:
 //       element (mb, r, p) at mb*32768 + (r/8)*2048 + (p/8)*128 + (r%8)*16 + (p%8)*2
 //       descriptor LBO = 128 (K = pixels), SBO = 2048 (M = channel rows)
-//   B = W, MN-major (Gaussians contiguous for a pixel), one 16-byte row per
-//       thread exactly as in the forward:
+//   B = W, MN-major (Gaussians contiguous for a pixel):
 //       element (p, g) at (g/8)*128 + (p/8)*512 + (p%8)*16 + (g%8)*2
 //       descriptor LBO = 512 (K = pixels), SBO = 128 (N = Gaussians)
-// D is double-buffered in tensor memory (2 x NMB x 32 columns), so the MMAs
-// of a Gaussian block overlap the epilogue of the previous one. In the
-// epilogue warp w takes lanes 32 (w % 4).. and Gaussians 8 (w / 4)..+7 of the
-// block and skips Gaussians that weigh nothing in this half tile (a bit mask
-// built with one warp reduction per warp).
+// The kernel is persistent (one CTA per SM, the forward's list of half
+// tiles). For each half tile every warp first stages dF^T (the fp32
+// cotangents of its 128 pixels, eight 16-byte loads in flight per thread,
+// rounded to bf16); then the roles run over the blocks of its compacted
+// list (the Gaussians whose skip mask reaches the half tile):
+//   warp 0 (producer): the compaction and the records of each block by
+//     cp.async into a 4-deep ring;
+//   warps 10-25 (builders, 4 threads per pixel): W as in the forward, and
+//     the bits of the block's Gaussians that weigh something here;
+//   warp 1 (one thread): NMB x 8 tcgen05.mma (M=128, N=32, K=16) per block
+//     into one of two tensor-memory accumulators;
+//   warps 2-9 (epilogue; lanes 32 (w % 4).., Gaussians 16 (w >= 6)..+15):
+//     the accumulator into registers, then one vector atomic per (Gaussian,
+//     lane) into d_feats for the Gaussians that weigh something.
+// Every wait is bounded (1 s); a timeout flags GS_ERR_TIMEOUT and raises the
+// abort word, on which every role stops.
 namespace {
 
 constexpr int kTbG = 32;  // Gaussians per block (MMA N)
+constexpr int kBwThreads = 832;
+constexpr int kBwStages = 4;
+constexpr int kBwWarpMma = 1, kBwWarpEpi = 2, kBwEpi = 8, kBwWarpBuild = 10, kBwBuilders = 16;
+static_assert(kBwWarpBuild * 32 + 4 * kTcPix == kBwThreads, "four builder threads per pixel");
 
-struct TbSmem {
-  uint8_t A[kTcMaxN * kTcPix * 2];  // dF^T, 128 KB for N = 512
-  uint8_t B[2][kTcPix * kTbG * 2];  // W, 8 KB per buffer
-  float2 uv[3][kTbG];  // record ring: block b uses slot b % 3, Gaussian k at rec_slot(k)
-  float4 co[3][kTbG];
-  uint32_t gid[3][kTbG];  // by position k in the block
-  uint32_t nz[3];         // bit k: Gaussian k has a nonzero weight in this half tile
-  unsigned long long mbar[2];
-  uint32_t tmem;
-  int maxlast;
+struct alignas(1024) BwStage {
+  uint8_t W[kTcPix * kTbG * 2];  // 8 KB, B operand
+  float2 uv[kTbG];               // entry k at slot (k % 8) * 4 + k / 8
+  float4 co[kTbG];
+  int pos[kTbG];
+  uint32_t gid[kTbG];            // by entry
+  uint32_t nz;                   // bit k: entry k weighs something in this half tile
+  int nvalid, flags;             // flags: 1 first block of its half tile, 2 last
 };
 
-struct TcBwdParams {
+struct BwSmem {
+  uint8_t A[kTcMaxN * kTcPix * 2];  // dF^T, 128 KB for N = 512
+  BwStage st[kBwStages];
+  uint32_t cgid[64];
+  int cpos[64];
+  unsigned long long full[kBwStages], ready[kBwStages], empty[kBwStages];
+  unsigned long long done[2], dfree[2], drain;
+  uint32_t tmem;
+  int abort;
+};
+static_assert(sizeof(BwSmem) + 1024 <= 227 * 1024, "shared memory of the adjoint");
+
+struct BwParams {
   CamF cam;
   const int2* ranges;
-  const int* order;  // launch order of the tiles, or null
+  const int* order;
   const uint32_t* gids;
+  const uint8_t* masks;
   const float2* uv;
   const float4* co;
   const int* last_idx;
   const float* g_feat;  // [H, W, N]
-  int N;
-  int tmem_cols;
+  int N, tmem_cols, nhalf;
   float* d_feats;  // [P, N]
   int32_t* status;
 };
 
-__device__ __forceinline__ uint32_t tb_fetch_id(const TcBwdParams& p, int b, int2 rg, int maxlast) {
-  const int pos = rg.x + b * kTbG + (int)threadIdx.x;
-  return pos < rg.x + maxlast ? p.gids[pos] : 0u;
+__device__ __forceinline__ void bw_tile(const BwParams& p, int h, int& tx, int& ty, int& half) {
+  const int t = p.order ? p.order[h >> 1] : (h >> 1);
+  tx = t % p.cam.tiles_x;
+  ty = t / p.cam.tiles_x;
+  half = h & 1;
 }
 
-// Records of Gaussian block b into ring slot `slot` (threads 0..31): id from
-// registers, uv and conic/opacity by asynchronous copy (zero past the list).
-__device__ __forceinline__ void tb_issue(const TcBwdParams& p, TbSmem& S, int slot, int b, int2 rg, int maxlast,
-                                         uint32_t g) {
-  const int tid = threadIdx.x;
-  const bool valid = rg.x + b * kTbG + tid < rg.x + maxlast;
-  const int k = rec_slot(tid);
-  cp_async8(smem_u32(&S.uv[slot][k]), p.uv + g, valid);
-  cp_async16(smem_u32(&S.co[slot][k]), p.co + g, valid);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  S.gid[slot][tid] = g;
-  if (tid == 0) S.nz[slot] = 0u;
-}
-
+// All threads: dF^T of half tile (tx, ty, half) into A. Item (i, pg): channel
+// quad i (4 i .. 4 i + 3) of the 8 pixels m = 8 pg .. 8 pg + 7 (one row
+// segment of the image); a warp reads 32 consecutive quads of a pixel and
+// writes 16-byte rows of 8 pixels.
 template <int NMB>
-__global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBwdParams p) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  TbSmem& S = *reinterpret_cast<TbSmem*>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m = tid >> 2, q = tid & 3;
-  const int tile = p.order ? p.order[blockIdx.x >> 1] : (int)(blockIdx.x >> 1), half = blockIdx.x & 1;
-  const int tx = tile % p.cam.tiles_x, ty = tile / p.cam.tiles_x;
-  const int px = tx * kTile + (m & 15);
-  const int py = ty * kTile + half * 8 + (m >> 4);
-  const bool inside = px < p.cam.W && py < p.cam.H;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-  const int2 rg = p.ranges[tile];
-  const int last = inside ? p.last_idx[(size_t)py * p.cam.W + px] : 0;
-  constexpr uint32_t dcols = (uint32_t)(NMB * kTbG);  // tensor-memory columns per D buffer
-  const int N = NMB * 128;
-
-  if (tid == 0) S.maxlast = 0;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
-                 "r"(p.tmem_cols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[s])));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  // dF^T for this half tile. Item (i, pg): channel quad i (4 i .. 4 i + 3) of
-  // the 8 pixels m = 8 pg .. 8 pg + 7 (one row segment of the image); the 32
-  // lanes of a warp read 32 consecutive quads of a pixel (coalesced) and write
-  // 16-byte rows of 8 pixels (distinct bank groups for NMB = 4).
-  {
-    const int nq = N / 4;
-    const int ry0 = ty * kTile + half * 8;
-    const int rx0 = tx * kTile;
-    for (int it = tid; it < nq * 16; it += kTcThreads) {
-      const int i = it % nq, pg = it / nq;
-      const int ry = ry0 + (pg >> 1), rx = rx0 + (pg & 1) * 8;
-      float4 v[8];
+__device__ __forceinline__ void bw_stage_cotangents(const BwParams& p, BwSmem& S, int tx, int ty, int half) {
+  constexpr int N = NMB * 128, nq = N / 4;
+  const int ry0 = ty * kTile + half * 8, rx0 = tx * kTile;
+  for (int it = threadIdx.x; it < nq * 16; it += kBwThreads) {
+    const int i = it % nq, pg = it / nq;
+    const int ry = ry0 + (pg >> 1), rx = rx0 + (pg & 1) * 8;
+    float4 v[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        v[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ry < p.cam.H && rx + e < p.cam.W)
-          v[e] = __ldg(reinterpret_cast<const float4*>(p.g_feat + ((size_t)ry * p.cam.W + rx + e) * N) + i);
+    for (int e = 0; e < 8; ++e) {
+      v[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ry < p.cam.H && rx + e < p.cam.W)
+        v[e] = __ldg(reinterpret_cast<const float4*>(p.g_feat + ((size_t)ry * p.cam.W + rx + e) * N) + i);
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int c = 4 * i + s, mb = c % NMB, r = c / NMB;
+      uint32_t w4[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float f0 = s == 0 ? v[2 * e].x : s == 1 ? v[2 * e].y : s == 2 ? v[2 * e].z : v[2 * e].w;
+        const float f1 = s == 0 ? v[2 * e + 1].x : s == 1 ? v[2 * e + 1].y : s == 2 ? v[2 * e + 1].z : v[2 * e + 1].w;
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f0, f1);
+        w4[e] = *reinterpret_cast<const uint32_t*>(&b2);
       }
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int c = 4 * i + s, mb = c % NMB, r = c / NMB;
-        float f[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] = s == 0 ? v[e].x : s == 1 ? v[e].y : s == 2 ? v[e].z : v[e].w;
-        uint32_t w4[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
-          w4[e] = *reinterpret_cast<const uint32_t*>(&b2);
-        }
-        *reinterpret_cast<uint4*>(S.A + mb * 32768 + (r >> 3) * 2048 + pg * 128 + (r & 7) * 16) =
-            make_uint4(w4[0], w4[1], w4[2], w4[3]);
-      }
+      *reinterpret_cast<uint4*>(S.A + mb * 32768 + (r >> 3) * 2048 + pg * 128 + (r & 7) * 16) =
+          make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (q == 0 && last > 0) atomicMax(&S.maxlast, last);
-  __syncthreads();
-  const int maxlast = S.maxlast;
-  const uint32_t tmem = S.tmem;
-  const int nb = (maxlast + kTbG - 1) / kTbG;
-  bool ok = true;
-  uint32_t next_id = 0;  // id of this thread's Gaussian in the next block to stage (threads 0..31)
-  if (nb > 0 && tid < kTbG) {
-    tb_issue(p, S, 0, 0, rg, maxlast, tb_fetch_id(p, 0, rg, maxlast));
-    if (nb > 1) next_id = tb_fetch_id(p, 1, rg, maxlast);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-  }
-  __syncthreads();
+}
 
-  float T = 1.f;
-  int last_issued = -1;
-  auto epilogue = [&](int b) -> bool {
-    const int buf = b & 1, slot = b % 3;
-    const bool w_ok =
-        __syncthreads_and(mbar_wait(smem_u32(&S.mbar[buf]), (uint32_t)((b >> 1) & 1))) != 0;
-    if (!w_ok) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int r = 32 * (warp & 3) + lane;  // channel row: channels NMB r .. NMB r + NMB - 1
-    const int g0 = 8 * (warp >> 2);
-    float v[NMB][8];
-    const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)buf * dcols + (uint32_t)g0;
+// warp 0: compaction and records of one half tile's blocks; returns false on abort
+__device__ bool bw_producer(const BwParams& p, BwSmem& S, int tx, int ty, int half, int& s, uint32_t& ph) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  volatile int* abort = &S.abort;
+  const int2 rg = p.ranges[ty * p.cam.tiles_x + tx];
+  int maxlast = 0;
 #pragma unroll
-    for (int mb = 0; mb < NMB; ++mb) tmem_ld8(ta + (uint32_t)(mb * kTbG), v[mb]);
-    tmem_wait_ld<NMB>(v);
-    const uint32_t msk = S.nz[slot] >> g0;
+  for (int i = 0; i < 4; ++i) {
+    const int m = lane + 32 * i;
+    const int px = tx * kTile + (m & 15), py = ty * kTile + half * 8 + (m >> 4);
+    if (px < p.cam.W && py < p.cam.H) maxlast = max(maxlast, p.last_idx[(size_t)py * p.cam.W + px]);
+  }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (!((msk >> j) & 1u)) continue;
-      float* dst = p.d_feats + (size_t)S.gid[slot][g0 + j] * N + NMB * r;
-      if constexpr (NMB == 4) {
-        atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[0][j], v[1][j], v[2][j], v[3][j]));
-      } else if constexpr (NMB == 2) {
-        atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0][j], v[1][j]));
-      } else {
-#pragma unroll
-        for (int mb = 0; mb < NMB; ++mb) atomicAdd(dst + mb, v[mb][j]);
-      }
+  for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
+  int fill = 0;
+  bool first = true;
+  auto emit = [&](int n, bool last) -> bool {
+    BwStage& st = S.st[s];
+    if (!fw_wait(smem_u32(&S.empty[s]), ph ^ 1u, abort, p.status)) return false;
+    const uint32_t g = lane < n ? S.cgid[lane] : 0u;
+    const int slot = fw_slot(lane);
+    cp_async8(smem_u32(&st.uv[slot]), p.uv + g, lane < n);
+    cp_async16(smem_u32(&st.co[slot]), p.co + g, lane < n);
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[s])) : "memory");
+    st.pos[slot] = lane < n ? S.cpos[lane] : 0x7fffffff;
+    st.gid[lane] = g;
+    if (lane == 0) {
+      st.nvalid = n;
+      st.flags = (first ? 1 : 0) | (last ? 2 : 0);
+      st.nz = 0u;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    mbar_arrive(smem_u32(&S.full[s]));
+    first = false;
+    if (++s == kBwStages) {
+      s = 0;
+      ph ^= 1u;
+    }
     return true;
   };
-
-  for (int b = 0; b < nb && ok; ++b) {
-    const int buf = b & 1, slot = b % 3;
-    // stage block b+1's records (slot (b+1)%3 was last read by the epilogue of
-    // block b-2, which finished in the previous iteration); fetch the ids of b+2
-    if (b + 1 < nb && tid < kTbG) {
-      tb_issue(p, S, (b + 1) % 3, b + 1, rg, maxlast, next_id);
-      if (b + 2 < nb) next_id = tb_fetch_id(p, b + 2, rg, maxlast);
+  uint32_t gb[4], mb[4];
+  auto fetch_batch = [&](int base) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int pos = base + 32 * i + lane;
+      gb[i] = pos < maxlast ? p.gids[rg.x + pos] : 0u;
+      mb[i] = pos < maxlast ? (p.masks ? (uint32_t)p.masks[rg.x + pos] : 0xFu) : 0u;
     }
-    // weights of my 8 Gaussians (one 16-byte row of B)
+  };
+  if (maxlast > 0) fetch_batch(0);
+  for (int base = 0; base < maxlast; base += 128) {
+    uint32_t gc[4], mc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      gc[i] = gb[i];
+      mc[i] = mb[i];
+    }
+    if (base + 128 < maxlast) fetch_batch(base + 128);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int pos = base + 32 * i + lane;
+      const bool hit = ((mc[i] >> (2 * half)) & 3u) != 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int idx = fill + __popc(bal & lt);
+        S.cgid[idx] = gc[i];
+        S.cpos[idx] = pos;
+      }
+      fill += __popc(bal);
+      __syncwarp();
+      if (fill > 32) {
+        if (!emit(32, false)) return false;
+        const bool mv = lane < fill - 32;
+        const uint32_t mg = mv ? S.cgid[32 + lane] : 0u;
+        const int mp = mv ? S.cpos[32 + lane] : 0;
+        __syncwarp();
+        if (mv) {
+          S.cgid[lane] = mg;
+          S.cpos[lane] = mp;
+        }
+        fill -= 32;
+        __syncwarp();
+      }
+    }
+  }
+  return emit(fill, true);
+}
+
+// warps 10-25: W of each block of one half tile (as the forward's weights)
+__device__ bool bw_builder(const BwParams& p, BwSmem& S, int tx, int ty, int half, int& s, uint32_t& ph) {
+  const int b = threadIdx.x - kBwWarpBuild * 32;
+  const int m = b >> 2, q = b & 3, lane = threadIdx.x & 31;
+  volatile int* abort = &S.abort;
+  const int px = tx * kTile + (m & 15), py = ty * kTile + half * 8 + (m >> 4);
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const int last = (px < p.cam.W && py < p.cam.H) ? p.last_idx[(size_t)py * p.cam.W + px] : 0;
+  float T = 1.f;
+  while (true) {
+    if (!fw_wait(smem_u32(&S.full[s]), ph, abort, p.status)) return false;
+    BwStage& st = S.st[s];
     float a[8];
     float prod = 1.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
+      const int sl = 4 * j + q;
       a[j] = 0.f;
-      const int k = 8 * q + j, ks = rec_slot(k);
       PairAlpha pa;
-      if (b * kTbG + k < last && pair_alpha(S.co[slot][ks], S.uv[slot][ks].x - pxc, S.uv[slot][ks].y - pyc, pa)) {
+      if (st.pos[sl] < last && pair_alpha(st.co[sl], st.uv[sl].x - pxc, st.uv[sl].y - pyc, pa)) {
         a[j] = pa.alpha;
         prod = __fmul_rn(prod, __fsub_rn(1.f, pa.alpha));
       }
@@ -923,52 +944,193 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_render_feat_tc_bwd(const TcBw
       packed[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
     }
     T = __fmul_rn(T, total);
-    const uint32_t wmask = __reduce_or_sync(0xffffffffu, mine);
-    if (lane == 0 && wmask) atomicOr(&S.nz[slot], wmask);
-    *reinterpret_cast<uint4*>(S.B[buf] + q * 128 + (m >> 3) * 512 + (m & 7) * 16) =
+    *reinterpret_cast<uint4*>(st.W + q * 128 + (m >> 3) * 512 + (m & 7) * 16) =
         make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    const uint32_t wmask = __reduce_or_sync(0xffffffffu, mine);
+    if (lane == 0 && wmask) atomicOr(&st.nz, wmask);
+    const int flags = st.flags;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(S.A), b0 = smem_u32(S.B[buf]);
-      const uint32_t idesc = idesc_bf16(kTcPix, kTbG, 1);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&S.ready[s]));
+    if (++s == kBwStages) {
+      s = 0;
+      ph ^= 1u;
+    }
+    if (flags & 2) return true;
+  }
+}
+
+// warp 1, one thread: the products of one half tile's blocks
+template <int NMB>
+__device__ bool bw_mma(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint32_t& ph, uint32_t& nblk) {
+  volatile int* abort = &S.abort;
+  constexpr uint32_t dcols = (uint32_t)(NMB * kTbG);
+  const uint32_t a0 = smem_u32(S.A);
+  while (true) {
+    if (!fw_wait(smem_u32(&S.ready[s]), ph, abort, p.status)) return false;
+    BwStage& st = S.st[s];
+    const int flags = st.flags;
+    const uint32_t buf = nblk & 1u, use = nblk >> 1;
+    if (!fw_wait(smem_u32(&S.dfree[buf]), (use & 1u) ^ 1u, abort, p.status)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t b0 = smem_u32(st.W);
+    const uint32_t idesc = idesc_bf16(kTcPix, kTbG, 1);
 #pragma unroll
-      for (int mb = 0; mb < NMB; ++mb) {
+    for (int mb = 0; mb < NMB; ++mb) {
 #pragma unroll
-        for (int k16 = 0; k16 < kTcPix / 16; ++k16) {
-          const uint64_t ad = smem_desc(a0 + (uint32_t)mb * 16u * 2048u + (uint32_t)k16 * 256u, 128, 2048);
-          const uint64_t bd = smem_desc(b0 + (uint32_t)k16 * 1024u, 512, 128);
-          const uint32_t acc = k16 > 0 ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-                  tmem + (uint32_t)buf * dcols + (uint32_t)(mb * kTbG)),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      for (int k16 = 0; k16 < kTcPix / 16; ++k16) {
+        const uint64_t ad = smem_desc(a0 + (uint32_t)mb * 32768u + (uint32_t)k16 * 256u, 128, 2048);
+        const uint64_t bd = smem_desc(b0 + (uint32_t)k16 * 1024u, 512, 128);
+        const uint32_t acc = k16 > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                tmem + buf * dcols + (uint32_t)(mb * kTbG)),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&S.done[buf])));
+    ++nblk;
+    if (++s == kBwStages) {
+      s = 0;
+      ph ^= 1u;
+    }
+    if (flags & 2) return true;
+  }
+}
+
+// warps 2-9: accumulators into the feature gradient
+template <int NMB>
+__device__ bool bw_epilogue(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint32_t& ph, uint32_t& nblk) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int qd = warp & 3, gh = (warp - kBwWarpEpi) >> 2;  // lane quarter, Gaussians 16 gh .. 16 gh + 15
+  volatile int* abort = &S.abort;
+  constexpr uint32_t dcols = (uint32_t)(NMB * kTbG);
+  constexpr int N = NMB * 128;
+  const int r = 32 * qd + lane;  // channel row: channels NMB r .. NMB r + NMB - 1
+  while (true) {
+    const uint32_t buf = nblk & 1u, use = nblk >> 1;
+    if (!fw_wait(smem_u32(&S.done[buf]), use & 1u, abort, p.status)) return false;
+    // the builders' release of this block (its gids, bits and flags)
+    if (!fw_wait(smem_u32(&S.ready[s]), ph, abort, p.status)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    BwStage& st = S.st[s];
+    const int flags = st.flags;
+    const uint32_t nzm = st.nz >> (16 * gh);
+    const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + buf * dcols + (uint32_t)(16 * gh);
+    // two groups of 8 Gaussians: the accumulator is released after the
+    // second group's load, the stage after the last atomic is issued
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      float v[NMB][8];
+#pragma unroll
+      for (int mb = 0; mb < NMB; ++mb) tmem_ld8(ta + (uint32_t)(mb * kTbG + 8 * i), v[mb]);
+      tmem_wait_ld<NMB>(v);
+      if (i == 1) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&S.dfree[buf]));
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (!((nzm >> (8 * i + j)) & 1u)) continue;
+        float* dst = p.d_feats + (size_t)st.gid[16 * gh + 8 * i + j] * N + NMB * r;
+        if constexpr (NMB == 4) {
+          atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[0][j], v[1][j], v[2][j], v[3][j]));
+        } else if constexpr (NMB == 2) {
+          atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0][j], v[1][j]));
+        } else {
+#pragma unroll
+          for (int mb = 0; mb < NMB; ++mb) atomicAdd(dst + mb, v[mb][j]);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&S.mbar[buf])));
     }
-    last_issued = b;
-    if (b >= 1) ok = epilogue(b - 1);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&S.empty[s]));
+    ++nblk;
+    if (++s == kBwStages) {
+      s = 0;
+      ph ^= 1u;
+    }
+    if (flags & 2) return true;
   }
-  if (ok && nb > 0) ok = epilogue(nb - 1);
-  if (!ok) {
-    if (tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
-    if (last_issued >= 0) mbar_wait(smem_u32(&S.mbar[last_issued & 1]), (uint32_t)((last_issued >> 1) & 1));
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
 }
 
 template <int NMB>
-gs_status launch_bwd_nmb(const TcBwdParams& p, const CamF& cam, cudaStream_t st) {
-  const size_t smem = sizeof(TbSmem) + 1024;
+__global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  BwSmem& S = *reinterpret_cast<BwSmem*>(smem_raw + pad);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pdl_wait();
+  pdl_trigger();
+  if (tid == 0) {
+    for (int s = 0; s < kBwStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 64;" ::"r"(smem_u32(&S.full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.ready[s])), "r"(kBwBuilders));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.empty[s])), "r"(kBwEpi));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.done[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.dfree[b])), "r"(kBwEpi));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.drain)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    S.abort = 0;
+  }
+  if (warp == kBwWarpMma) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(p.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = S.tmem;
+  int s = 0;
+  uint32_t ph = 0, nblk = 0;
+  for (int rr = 0;; ++rr) {
+    const int h = fw_half_tile(rr, p.nhalf);
+    if (h < 0) break;
+    int tx, ty, half;
+    bw_tile(p, h, tx, ty, half);
+    // every role is done with the previous half tile (its products have
+    // completed: the epilogue waited for them), so A is free
+    __syncthreads();
+    if (S.abort) break;
+    bw_stage_cotangents<NMB>(p, S, tx, ty, half);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+      bw_producer(p, S, tx, ty, half, s, ph);
+    } else if (warp == kBwWarpMma) {
+      if (lane == 0) bw_mma<NMB>(p, S, tmem, s, ph, nblk);
+    } else if (warp < kBwWarpBuild) {
+      bw_epilogue<NMB>(p, S, tmem, s, ph, nblk);
+    } else {
+      bw_builder(p, S, tx, ty, half, s, ph);
+    }
+  }
+  if (warp == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+  if (warp == kBwWarpMma && lane == 0) {
+    // every product issued has completed before tensor memory is freed
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(&S.drain)));
+    volatile int never = 0;
+    fw_wait(smem_u32(&S.drain), 0u, &never, p.status);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == kBwWarpMma) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+  }
+}
+
+template <int NMB>
+gs_status launch_bwd_nmb(const BwParams& p, cudaStream_t st) {
+  const size_t smem = sizeof(BwSmem) + 1024;
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_render_feat_tc_bwd<NMB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -976,26 +1138,30 @@ gs_status launch_bwd_nmb(const TcBwdParams& p, const CamF& cam, cudaStream_t st)
       return GS_ERR_CUDA;
     attr_set = true;
   }
-  const unsigned blocks = (unsigned)(cam.tiles_x * cam.tiles_y * 2);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned blocks = (unsigned)(p.nhalf < sms ? p.nhalf : sms);
   GS_TRACE("k_render_feat_tc_bwd", st);
-  k_render_feat_tc_bwd<NMB><<<blocks, kTcThreads, smem, st>>>(p);
+  launch_pdl(k_render_feat_tc_bwd<NMB>, blocks, kBwThreads, smem, st, p);
   return last_launch_status();
 }
 
 }  // namespace
 
 gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, const int32_t* order,
-                                    const uint32_t* gids, const float* uv,
-                                    const float* co, const int32_t* last_idx, const float* g_feat, int N,
-                                    float* d_feats, int32_t* status, cudaStream_t st) {
+                                    const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
+                                    const int32_t* last_idx, const float* g_feat, int N, float* d_feats,
+                                    int32_t* status, cudaStream_t st) {
   if (N <= 0 || N % 128 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
   // the vector atomics of the epilogue need NMB * 4-byte alignment of every row
   if ((reinterpret_cast<uintptr_t>(d_feats) & 15u) != 0) return GS_ERR_INVALID_ARG;
-  TcBwdParams p;
+  BwParams p;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.order = order;
   p.gids = gids;
+  p.masks = masks;
   p.uv = reinterpret_cast<const float2*>(uv);
   p.co = reinterpret_cast<const float4*>(co);
   p.last_idx = last_idx;
@@ -1004,13 +1170,14 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, cons
   int cols = 32;
   while (cols < 2 * (N / 128) * kTbG) cols *= 2;
   p.tmem_cols = cols;
+  p.nhalf = 2 * cam.tiles_x * cam.tiles_y;
   p.d_feats = d_feats;
   p.status = status;
   switch (N / 128) {
-    case 1: return launch_bwd_nmb<1>(p, cam, st);
-    case 2: return launch_bwd_nmb<2>(p, cam, st);
-    case 3: return launch_bwd_nmb<3>(p, cam, st);
-    default: return launch_bwd_nmb<4>(p, cam, st);
+    case 1: return launch_bwd_nmb<1>(p, st);
+    case 2: return launch_bwd_nmb<2>(p, st);
+    case 3: return launch_bwd_nmb<3>(p, st);
+    default: return launch_bwd_nmb<4>(p, st);
   }
 }
 

@@ -185,8 +185,7 @@ gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const int
                                const uint8_t* masks, const float* uv, const float* co, const __nv_bfloat16* feats,
                                const int32_t* last_idx, int N, float* out_feat, int32_t* status, cudaStream_t st);
 gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                                    const float* uv, const float* co, const int32_t* last_idx,
-                                    const float* g_feat, int N, float* d_feats, int32_t* status,
-                                    cudaStream_t st);
+                                    const uint8_t* masks, const float* uv, const float* co, const int32_t* last_idx,
+                                    const float* g_feat, int N, float* d_feats, int32_t* status, cudaStream_t st);
 
 }  // namespace gsff
