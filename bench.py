@@ -660,7 +660,7 @@ def _peaks():
 def run_tracking(args):
     """Pose tracking (Sec. 3.2) on the SLAM scene: each timed frame starts at
     the true pose perturbed by Exp(1 cm, 1 deg) (a seeded direction) and runs
-    the library's loop (render, Eq. 5 cotangents, pose-only adjoint, Adam +
+    the library's loop (render, Eq. 6 cotangents, pose-only adjoint, Adam +
     Exp update on the device) until the update converges or --track-iters;
     the convergence flag is read every 10 iterations. Observations are the
     renders (RGB + depth) at the true poses."""
@@ -724,7 +724,7 @@ def run_tracking(args):
         per[name] = per.get(name, 0.0) + tt / tr.iterations
     g.trace_enable(0)
     total_it = sum(iters)
-    result = {"metric": "tracking iterations/s (render + Eq. 5 cotangents + pose adjoint + pose update)",
+    result = {"metric": "tracking iterations/s (render + Eq. 6 cotangents + pose adjoint + pose update)",
               "value": total_it / (sum(ms) / 1e3), "unit": "iterations/s", "n_gpus": 1, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene and trajectory)",

@@ -39,7 +39,9 @@ typedef enum {
   GS_ERR_CAPACITY = 2,     /* device: more tile instances than the caller's capacity */
   GS_ERR_TIMEOUT = 3,      /* device: a bounded wait gave up */
   GS_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
-  GS_ERR_UNSUPPORTED = 5   /* a valid but unimplemented combination of options */
+  GS_ERR_UNSUPPORTED = 5,  /* a valid but unimplemented combination of options */
+  GS_ERR_BOUNDS = 6        /* device, bounds-checked build only: an index read from the inputs (a Gaussian id
+                              of the sorted lists, a saved last index) was out of range; it was not followed */
 } gs_status;
 
 /* Pinhole camera and world->camera transform T_CW: mu_c = R mu + t.
@@ -122,6 +124,12 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                       size_t workspace_bytes, uint64_t* keys, uint32_t* gids, int32_t* tile_ranges,
                       int64_t* n_instances, int32_t* status, void* stream);
 
+/* gs_count_nonfinite -- adds to *count (device uint64, the caller zeroes it)
+ * the number of NaN or infinite values among the n floats at x (device,
+ * 4-byte aligned): the scan of an output or gradient buffer for non-finite
+ * values. The paper has no counterpart. */
+gs_status gs_count_nonfinite(int64_t n, const float* x, uint64_t* count, void* stream);
+
 /* gs_set_lookback_wait_ns -- the bound, in nanoseconds of the GPU's global
  * timer, of every radix pass's wait for earlier chunks (process-wide, read
  * when a sort is enqueued; default 1e9). 0 makes every chunk after the first
@@ -201,7 +209,7 @@ gs_status gs_tile_order(int32_t num_tiles, const int32_t* tile_ranges, int32_t* 
  *      of the last blended Gaussian + 1; n_contrib [H,W] = blended count.
  * visible [P] (u8, may be NULL): set to 1 for every Gaussian blended at some
  *      pixel with T > 0.5 in front of it (the visibility V_id of the keyframe
- *      selection, Sec. 3.2, Eq. 6); other entries are left unchanged, so the
+ *      selection, Sec. 3.2, Eq. 5); other entries are left unchanged, so the
  *      caller zeroes the array (or keeps OR-ing frames into it).
  * feats [P,N] is float32 (GS_F32) or bfloat16 (GS_BF16); may be NULL with
  * GS_FEAT_OFF. bg: 3 host floats, NULL = black.
@@ -282,7 +290,7 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
 
 /* ---------------------------------------------------------------------------
  * L1 image loss fused into compositing: the colour and depth L1 terms of the
- * mapping loss (Sec. 3.2) and the feature L1 term (Eq. 10 on the rendered
+ * mapping loss (Sec. 3.2) and the feature L1 term (Eq. 11 on the rendered
  * field),
  *   L = w_rgb sum |rgb - rgb*| + w_depth sum |D - D*| + w_feat sum |F - F*|
  * (sums over pixels and channels), with dL/dpred = w sign(pred - target),
@@ -348,14 +356,14 @@ gs_status gs_l1_signs(int32_t width, int32_t height, int32_t N, int32_t layout, 
 
 /* ---------------------------------------------------------------------------
  * gs_l1_loss_grad -- the L1 photometric term of the tracking and mapping
- * losses (Eq. 5, Eq. 7): grad[i] = scale * sign(pred[i] - target[i]) (sign(0)
+ * losses (Eq. 6, Eq. 8): grad[i] = scale * sign(pred[i] - target[i]) (sign(0)
  * = 0) and *loss_sum += scale * sum |pred - target| (device float, atomic).
  */
 gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, float scale,
                           float* grad, float* loss_sum, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Camera tracking (Sec. 3.2, Eq. 5): with the Gaussians frozen, the pose is
+ * Camera tracking (Sec. 3.2, Eq. 6): with the Gaussians frozen, the pose is
  * refined on its tangent until the update converges.
  *
  * gs_edge_mask -- m_e, the pixels of the observed image with a significant
@@ -369,7 +377,7 @@ gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, flo
 gs_status gs_edge_mask(int32_t width, int32_t height, const float* rgb, float tau, uint8_t* m_e,
                        void* stream);
 
-/* gs_tracking_loss_grad -- cotangents of Eq. 5 for one render:
+/* gs_tracking_loss_grad -- cotangents of Eq. 6 for one render:
  *   m_v = alpha_ref > alpha_min (alpha_ref: the opacity of the frame's first
  *   render, the 2D visibility map); colour term on m_v m_e, depth term on
  *   m_v and gt_depth > 0;
@@ -444,7 +452,7 @@ gs_status gs_sh_colors_bwd(const gs_camera* cam, int32_t P, int32_t degree, cons
 /* ---------------------------------------------------------------------------
  * Semantic supervision and read-out of the feature field (Sec. 3.3).
  *
- * gs_semantic_ce_grad -- the ground-truth loss of Eq. 8 on the rendered map
+ * gs_semantic_ce_grad -- the ground-truth loss of Eq. 9 on the rendered map
  * feat (N channels, layout CHW [N,H,W] or HWC [H,W,N]) read as per-pixel
  * logits normalised by a softmax over the channels:
  *   loss_sum += (1/HW) sum_p [logsumexp_c F_p(c) - F_p(l_p)],
@@ -455,13 +463,13 @@ gs_status gs_sh_colors_bwd(const gs_camera* cam, int32_t P, int32_t degree, cons
 gs_status gs_semantic_ce_grad(int32_t width, int32_t height, int32_t N, int32_t layout, const float* feat,
                               const int32_t* labels, float* grad, float* loss_sum, void* stream);
 
-/* gs_argmax_labels -- predicted labels argmax_c F_p(c) (Eq. 9; ties take the
+/* gs_argmax_labels -- predicted labels argmax_c F_p(c) (Eq. 10; ties take the
  * lowest channel) of feat (layout as above) into labels [H,W] int32.
  */
 gs_status gs_argmax_labels(int32_t width, int32_t height, int32_t N, int32_t layout, const float* feat,
                            int32_t* labels, void* stream);
 
-/* gs_label_probs -- label probabilities of Eq. 11 for npix pixel features
+/* gs_label_probs -- label probabilities of Eq. 12 for npix pixel features
  * feat [npix, M] (fp32 rows, 16-byte aligned; M % 4 == 0) against L query
  * vectors queries [L, M] (1 <= L <= 64, L M <= 51200):
  *   probs [npix, L] (may be NULL) = softmax_l(f . q(l)),
@@ -472,7 +480,7 @@ gs_status gs_label_probs(int64_t npix, int32_t M, int32_t L, const float* feat, 
                          float* probs, int32_t* labels, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Per-pixel feature decoder o(.) of Eq. 9, read as a 1x1 lift of a rendered
+ * Per-pixel feature decoder o(.) of Eq. 11, read as a 1x1 lift of a rendered
  * latent map (a din-channel render of per-Gaussian latents):
  *     y = W2^T gelu(W1^T z + b1) + b2,   gelu(x) = x (1 + erf(x / sqrt 2)) / 2.
  * W1 [din, dh] and W2 [dh, dout] are row-major fp32 arrays whose values are
@@ -515,8 +523,8 @@ gs_status gs_decoder_train(const gs_decoder* dec, int64_t nsample, int64_t npix,
 gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, const float* z, float* y, int32_t* status,
                             void* stream);
 
-/* Label read-out of the decoded field without forming it (Eq. 9 composed
- * with Eq. 11): since y = W2^T h + b2, the logit of query l is
+/* Label read-out of the decoded field without forming it (Eq. 11 composed
+ * with Eq. 12): since y = W2^T h + b2, the logit of query l is
  * y . q(l) = h . G(:, l) + c(l) with G = W2 q^T and c = b2 . q^T, so per
  * pixel the 16-d latent z [npix, 16] goes through W1, the GELU (rounded to
  * bf16) and one tcgen05 product with G (folded in fp32, rounded to bf16);

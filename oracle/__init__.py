@@ -135,7 +135,7 @@ def edge_mask(rgb, tau):
 
 
 def tracking_grad(rgb, depth, gt_rgb, gt_depth, alpha_ref, alpha_min, m_e, lam):
-    """(loss, g_rgb, g_depth) of Eq. 5 in double."""
+    """(loss, g_rgb, g_depth) of Eq. 6 in double."""
     H, W = depth.shape
     g_rgb, g_depth = np.zeros((3, H, W)), np.zeros((H, W))
     me = np.ascontiguousarray(m_e, np.uint8)
@@ -157,7 +157,7 @@ def pose_update(pose, g, m, v, step, lr_t, lr_r, b1=0.9, b2=0.999, eps=1e-8, tol
 
 
 def semantic_ce(feat, labels, hwc=False):
-    """(loss, grad) of Eq. 8 on logits feat ([N,H,W], or [H,W,N] with hwc) in double."""
+    """(loss, grad) of Eq. 9 on logits feat ([N,H,W], or [H,W,N] with hwc) in double."""
     feat = _f64(feat)
     if hwc:
         H, W, N = feat.shape
@@ -172,12 +172,12 @@ def semantic_ce(feat, labels, hwc=False):
 
 
 def argmax_labels(feat, hwc=False):
-    """Eq. 9: argmax over the channels (first maximum) of the given binary32 values."""
+    """Eq. 10: argmax over the channels (first maximum) of the given binary32 values."""
     return np.argmax(np.asarray(feat), axis=-1 if hwc else 0).astype(np.int32)
 
 
 def label_logits_b32(f, q):
-    """Eq. 11 logits replayed in binary32 (the GPU's fused multiply-add order); f [npix, M], q [L, M]."""
+    """Eq. 12 logits replayed in binary32 (the GPU's fused multiply-add order); f [npix, M], q [L, M]."""
     f = np.ascontiguousarray(f, np.float32)
     q = np.ascontiguousarray(q, np.float32)
     z = np.zeros((f.shape[0], q.shape[0]), np.float32)
@@ -188,7 +188,7 @@ def label_logits_b32(f, q):
 
 
 def label_probs(f, q):
-    """Eq. 11 probabilities in double; f [npix, M], q [L, M]."""
+    """Eq. 12 probabilities in double; f [npix, M], q [L, M]."""
     f, q = _f64(f), _f64(q)
     out = np.zeros((f.shape[0], q.shape[0]))
     lib().ora_label_probs(ctypes.c_longlong(f.shape[0]), ctypes.c_int(f.shape[1]), ctypes.c_int(q.shape[0]), _p(f),
@@ -312,7 +312,7 @@ def linear_loss(fw, g_rgb, g_depth, g_alpha, g_feat):
     return L
 
 
-# ---- per-pixel decoder o(.) (Eq. 9) ------------------------------------------
+# ---- per-pixel decoder o(.) (Eq. 11) ------------------------------------------
 
 def decoder_fwd(z, W1, b1, W2, b2):
     z = _f64(z)

@@ -21,12 +21,12 @@
 //                        visible when that transmittance exceeds 0.5).
 //   ora_edge_mask        tracking edge mask m_e (Sec. 3.2): binary32 replay
 //                        of the Sobel test, so the decision matches bit for bit.
-//   ora_tracking_grad    cotangents and value of the tracking loss (Eq. 5).
+//   ora_tracking_grad    cotangents and value of the tracking loss (Eq. 6).
 //   ora_pose_update      Adam on the pose tangent and T <- Exp(delta) T.
-//   ora_semantic_ce      Eq. 8 cross-entropy of per-pixel logits and its gradient.
-//   ora_label_logits_b32 Eq. 11 logits f . q(l) replayed in binary32 with the
+//   ora_semantic_ce      Eq. 9 cross-entropy of per-pixel logits and its gradient.
+//   ora_label_logits_b32 Eq. 12 logits f . q(l) replayed in binary32 with the
 //                        GPU's order of fused multiply-adds (for the argmax).
-//   ora_label_probs      Eq. 11 probabilities in double.
+//   ora_label_probs      Eq. 12 probabilities in double.
 //   ora_sh_colors        view-dependent colour from SH coefficients (Sec. 3.1),
 //                        the basis from Legendre recurrences, its gradient by
 //                        forward-mode dual numbers; ora_sh_colors_bwd its adjoint.
@@ -790,7 +790,7 @@ void ora_project_bwd_f64(const double* cam, int P, const double* means, const do
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Per-pixel feature decoder o(.) of Eq. 9, read as a 1x1 lift of the latent
+// Per-pixel feature decoder o(.) of Eq. 11, read as a 1x1 lift of the latent
 // feature map: y = W2^T gelu(W1^T z + b1) + b2 with the exact (erf) GELU,
 // gelu(x) = x (1 + erf(x / sqrt 2)) / 2. Shapes: z [n, din], W1 [din, dh],
 // b1 [dh], W2 [dh, dout], b2 [dout], y [n, dout]; all double.
@@ -850,7 +850,7 @@ void ora_decoder_bwd(int n, int din, int dh, int dout, const double* z, const do
 }
 
 
-// ---- tracking (Sec. 3.2, Eq. 5) ------------------------------------------------
+// ---- tracking (Sec. 3.2, Eq. 6) ------------------------------------------------
 
 // Edge mask: luminance L = ((r + g) + b) * (1/3), Sobel differences with the
 // image border replicated, each divided by 8; edge where gx^2 + gy^2 > tau^2.
@@ -880,7 +880,7 @@ void ora_edge_mask(int W, int H, const float* rgb, float tau, uint8_t* m_e) {
     }
 }
 
-// Eq. 5: L = lambda/(3HW) sum_{m_v m_e} |C - C_obs| + (1 - lambda)/(HW) sum_{m_v, D_obs > 0} |D - D_obs|,
+// Eq. 6: L = lambda/(3HW) sum_{m_v m_e} |C - C_obs| + (1 - lambda)/(HW) sum_{m_v, D_obs > 0} |D - D_obs|,
 // m_v = alpha_ref > alpha_min. Returns L; writes dL/dC and dL/dD (sign(0) = 0).
 double ora_tracking_grad(int W, int H, const double* rgb, const double* depth, const double* gt_rgb,
                          const double* gt_depth, const double* alpha_ref, double alpha_min, const uint8_t* m_e,
@@ -962,7 +962,7 @@ int ora_pose_update(double* pose, const double* g, double* m, double* v, int ste
 
 // ---- semantics (Sec. 3.3) -------------------------------------------------------
 
-// Eq. 8 with F_p read as logits: loss = (1/HW) sum_p [log sum_c exp F_p(c) - F_p(l_p)],
+// Eq. 9 with F_p read as logits: loss = (1/HW) sum_p [log sum_c exp F_p(c) - F_p(l_p)],
 // grad = (softmax(F_p) - onehot(l_p)) / HW; labels outside [0, N) are ignored.
 // Layout: hwc = 0 -> F[c * HW + p], 1 -> F[p * N + c].
 double ora_semantic_ce(int W, int H, int N, int hwc, const double* F, const int32_t* labels, double* grad) {
@@ -986,7 +986,7 @@ double ora_semantic_ce(int W, int H, int N, int hwc, const double* F, const int3
   return loss;
 }
 
-// Eq. 11 logits in binary32: z_l = fma(f[M-1], q_l[M-1], ... fma(f[0], q_l[0], 0)),
+// Eq. 12 logits in binary32: z_l = fma(f[M-1], q_l[M-1], ... fma(f[0], q_l[0], 0)),
 // one rounding per fused multiply-add in channel order.
 void ora_label_logits_b32(long long npix, int M, int L, const float* f, const float* q, float* z) {
   for (long long p = 0; p < npix; ++p)
@@ -997,7 +997,7 @@ void ora_label_logits_b32(long long npix, int M, int L, const float* f, const fl
     }
 }
 
-// Eq. 11 probabilities in double.
+// Eq. 12 probabilities in double.
 void ora_label_probs(long long npix, int M, int L, const double* f, const double* q, double* probs) {
   std::vector<double> z((size_t)L);
   for (long long p = 0; p < npix; ++p) {

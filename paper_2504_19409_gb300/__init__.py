@@ -22,9 +22,11 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgsff.so")
+# GSFF_CHECKED=1 loads the bounds-checked build (the same kernels with the ids
+# they follow checked; see build.py)
+LIB_PATH = os.path.join(_HERE, "libgsff_checked.so" if os.environ.get("GSFF_CHECKED") == "1" else "libgsff.so")
 
-GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_UNSUPPORTED = range(6)
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_UNSUPPORTED, GS_ERR_BOUNDS = range(7)
 GS_FEAT_OFF, GS_FEAT_ON, GS_FEAT_TENSOR_CORE = 0, 1, 2
 GS_FEAT_GRAD_DECOUPLED, GS_FEAT_GRAD_COUPLED = 0, 1
 GS_F32, GS_BF16 = 0, 1
@@ -40,7 +42,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
            "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero", "gs_set_lookback_wait_ns",
-           "gs_peak_probe")
+           "gs_peak_probe", "gs_count_nonfinite")
 
 
 class GsffError(RuntimeError):
@@ -87,6 +89,18 @@ def zero_(t, stream=None):
         raise GsffError("zero_ needs a contiguous CUDA tensor (a strided view would be cleared over the wrong span)")
     _check(lib().gs_zero(_ptr(t), t.numel() * t.element_size(), _stream(stream)), "gs_zero")
     return t
+
+
+def count_nonfinite(tensors, stream=None):
+    """gs_count_nonfinite over each float32 CUDA tensor given: returns a device int64 [len(tensors)] with the
+    number of NaN / infinite values in each (one kernel per tensor, no host round trip)."""
+    tensors = list(tensors)
+    out = torch.zeros(max(1, len(tensors)), dtype=torch.int64, device=tensors[0].device if tensors else "cuda")
+    for i, t in enumerate(tensors):
+        _need(t, torch.float32, "scanned tensor")
+        _check(lib().gs_count_nonfinite(t.numel(), _ptr(t), _vp(out.data_ptr() + 8 * i), _stream(stream)),
+               "gs_count_nonfinite")
+    return out[:len(tensors)]
 
 
 def set_lookback_wait_ns(ns: int) -> None:
@@ -161,6 +175,8 @@ def lib():
     L.gs_zero.restype = ctypes.c_int
     L.gs_peak_probe.argtypes = [_i32, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_double), _vp]
     L.gs_peak_probe.restype = ctypes.c_int
+    L.gs_count_nonfinite.argtypes = [_i64, _vp, _vp, _vp]
+    L.gs_count_nonfinite.restype = ctypes.c_int
     L.gs_set_lookback_wait_ns.argtypes = [ctypes.c_uint64]
     L.gs_set_lookback_wait_ns.restype = ctypes.c_int
     L.gs_tile_order.argtypes = [_i32, _vp, _vp, _vp]
@@ -226,6 +242,11 @@ def lib():
     L.gs_version.restype = _i32
     _lib = L
     return L
+
+
+def status_names(word: int):
+    """The error kinds OR-ed as bits (1 << gs_status) into a device status word, by name."""
+    return [lib().gs_status_string(i).decode() for i in range(1, GS_ERR_BOUNDS + 1) if word & (1 << i)]
 
 
 def _check(code: int, what: str):
@@ -363,7 +384,7 @@ def edge_mask(rgb, tau, out=None, stream=None):
 
 def tracking_loss_grad(rgb, depth, gt_rgb, gt_depth, alpha_ref, m_e, lambda_t=0.9, alpha_min=0.5, g_rgb=None,
                        g_depth=None, loss=None, stream=None):
-    """gs_tracking_loss_grad: the cotangents (g_rgb [3,H,W], g_depth [H,W]) of Eq. 5."""
+    """gs_tracking_loss_grad: the cotangents (g_rgb [3,H,W], g_depth [H,W]) of Eq. 6."""
     H, W = depth.shape
     for t_, n_, sh in ((rgb, "rgb", (3, H, W)), (gt_rgb, "gt_rgb", (3, H, W)), (gt_depth, "gt_depth", (H, W)),
                        (alpha_ref, "alpha_ref", (H, W))):
@@ -379,7 +400,7 @@ def tracking_loss_grad(rgb, depth, gt_rgb, gt_depth, alpha_ref, m_e, lambda_t=0.
 
 def tracking_loss_signs(rgb, depth, gt_rgb, gt_depth, alpha_ref, m_e, lambda_t=0.9, alpha_min=0.5, signs=None,
                         loss=None, stream=None):
-    """gs_tracking_loss_signs: Eq. 5's cotangents as sign words (int32 [H*W, 2]) and their weights
+    """gs_tracking_loss_signs: Eq. 6's cotangents as sign words (int32 [H*W, 2]) and their weights
     ({"rgb": ..., "depth": ...}) for render_bwd_l1."""
     H, W = depth.shape
     for t_, n_, sh in ((rgb, "rgb", (3, H, W)), (gt_rgb, "gt_rgb", (3, H, W)), (gt_depth, "gt_depth", (H, W)),
@@ -439,7 +460,7 @@ def _feat_shape(feat, layout):
 
 
 def semantic_ce_grad(feat, labels, layout=GS_LAYOUT_CHW, grad=None, loss=None, stream=None):
-    """gs_semantic_ce_grad (Eq. 8): the softmax cross-entropy cotangent of a rendered map; labels < 0 ignored."""
+    """gs_semantic_ce_grad (Eq. 9): the softmax cross-entropy cotangent of a rendered map; labels < 0 ignored."""
     N, H, W = _feat_shape(feat, layout)
     _need(labels, torch.int32, "labels", (H, W))
     g = grad if grad is not None else torch.empty_like(feat)
@@ -449,7 +470,7 @@ def semantic_ce_grad(feat, labels, layout=GS_LAYOUT_CHW, grad=None, loss=None, s
 
 
 def argmax_labels(feat, layout=GS_LAYOUT_CHW, out=None, stream=None):
-    """gs_argmax_labels (Eq. 9): int32 [H,W] labels, ties to the lowest channel."""
+    """gs_argmax_labels (Eq. 10): int32 [H,W] labels, ties to the lowest channel."""
     N, H, W = _feat_shape(feat, layout)
     o = out if out is not None else torch.empty(H, W, dtype=torch.int32, device=feat.device)
     _check(lib().gs_argmax_labels(W, H, N, layout, _ptr(feat), _ptr(o), _stream(stream)), "gs_argmax_labels")
@@ -457,7 +478,7 @@ def argmax_labels(feat, layout=GS_LAYOUT_CHW, out=None, stream=None):
 
 
 def label_probs(feat, queries, probs=True, labels=True, stream=None):
-    """gs_label_probs (Eq. 11): (probs [npix, L], labels [npix]) of pixel features [npix, M] against
+    """gs_label_probs (Eq. 12): (probs [npix, L], labels [npix]) of pixel features [npix, M] against
     queries [L, M]; either output can be skipped."""
     _need(feat, torch.float32, "feat")
     _need(queries, torch.float32, "queries")
@@ -727,11 +748,21 @@ class Rasterizer:
                       flags=GS_FEAT_OFF, grads=grads, workspace=self.bwd_ws, status=self.status, stream=stream)
         return grads
 
+    def check_finite(self, grads=True, stream=None):
+        """Scans the last forward's images (and, with grads, the gradient arena) for NaN / infinite values;
+        raises GsffError naming the buffers that hold any."""
+        bufs = {k: v for k, v in self.fwd.items() if v.dtype == torch.float32}
+        if grads:
+            bufs["gradients"] = self.grad_arena
+        counts = count_nonfinite(bufs.values(), stream=stream).cpu().tolist()
+        bad = {k: c for k, c in zip(bufs, counts) if c}
+        if bad:
+            raise GsffError(f"non-finite values: {bad}")
+
     def check_status(self):
         s = int(self.status.item())
         if s:
-            names = [lib().gs_status_string(i).decode() for i in range(1, 6) if s & (1 << i)]
-            raise GsffError("device status: " + ", ".join(names))
+            raise GsffError("device status: " + ", ".join(status_names(s)))
 
 
 # ---- autograd -----------------------------------------------------------------

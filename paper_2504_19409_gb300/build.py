@@ -3,6 +3,11 @@
 Each translation unit under csrc/ is compiled in parallel, then linked into
 one shared library with the CUDA runtime linked statically. No torch headers
 are involved: the library's boundary is plain C (include/gsff.h).
+
+build(checked=True) makes libgsff_checked.so, the same sources compiled with
+GS_CHECKED: the ids the kernels read from their inputs and follow are
+bounds-checked, and a failure sets GS_ERR_BOUNDS in the status word instead of
+reading past the caller's arrays (the package loads it when GSFF_CHECKED=1).
 """
 from __future__ import annotations
 
@@ -18,6 +23,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgsff.so")
+LIB_CHECKED = os.path.join(HERE, "libgsff_checked.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -45,23 +51,25 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "gsff.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
+    bdir = BUILD_DIR + ("_checked" if checked else "")
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
 
     def one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        cmd = [cc, "-c", src, "-o", obj] + _flags(verbose_ptxas)
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
+        cmd = [cc, "-c", src, "-o", obj] + _flags(verbose_ptxas) + (["-DGS_CHECKED"] if checked else [])
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -72,14 +80,14 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if verbose_ptxas:
         for _, err in results:
             sys.stderr.write(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-Xcompiler", "-fPIC", "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -25,14 +25,16 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const int32_
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
-                            int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1, cudaStream_t st);
+                            int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1, int P, int32_t* status,
+                            cudaStream_t st);
 gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
                             const uint8_t* masks, const float* uv,
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
                             const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
                             int coupled, float* d_uv, float* d_conic, float* d_depth, float* d_opacity,
-                            float* d_colors, float* d_feats, const L1Bwd* l1, cudaStream_t st);
+                            float* d_colors, float* d_feats, const L1Bwd* l1, int P, int32_t* status,
+                            cudaStream_t st);
 
 // ---- tracing -----------------------------------------------------------------
 namespace {
@@ -202,15 +204,48 @@ __global__ void __launch_bounds__(256) k_l1_signs(long long HW, int N, int hwc, 
   }
 }
 
+// Clears one range of 4-byte words: the words before the first 16-byte
+// boundary and after the last one singly, the rest with 16-byte stores.
+__device__ __forceinline__ void zero_range(uint32_t* __restrict__ a, long long n, long long t, long long stride) {
+  const long long head = min(n, (long long)(((16u - ((uintptr_t)a & 15u)) & 15u) >> 2));
+  const long long nv = (n - head) >> 2;
+  uint4* v = reinterpret_cast<uint4*>(a + head);
+  for (long long i = t; i < nv; i += stride) v[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (t < head) a[t] = 0u;
+  const long long tail = head + 4 * nv;
+  if (t < n - tail) a[tail + t] = 0u;
+}
+
 __global__ void __launch_bounds__(256) k_zero(uint32_t* __restrict__ a, long long na, uint32_t* __restrict__ b,
                                               long long nb) {
   pdl_wait();
   pdl_trigger();
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < na + nb; i += stride) {
-    if (i < na) a[i] = 0u;
-    else b[i - na] = 0u;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  zero_range(a, na, t, stride);
+  if (b) zero_range(b, nb, t, stride);
+}
+
+// *count += the number of non-finite values among x[0 .. n), 16-byte loads
+// where x is 16-byte aligned, one atomic per warp that found any.
+__global__ void __launch_bounds__(256) k_count_nonfinite(const float* __restrict__ x, long long n,
+                                                         unsigned long long* __restrict__ count) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned c = 0;
+  const long long head = min(n, (long long)(((16u - ((uintptr_t)x & 15u)) & 15u) >> 2));
+  const long long nv = (n - head) >> 2;
+  const float4* v = reinterpret_cast<const float4*>(x + head);
+  for (long long i = t; i < nv; i += stride) {
+    const float4 a = v[i];
+    c += !isfinite(a.x) + !isfinite(a.y) + !isfinite(a.z) + !isfinite(a.w);
   }
+  if (t < head) c += !isfinite(x[t]);
+  const long long tail = head + 4 * nv;
+  if (t < n - tail) c += !isfinite(x[tail + t]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
 }
 
 // counts[0] += |{g : a_g != 0 and b_g != 0}|, counts[1] += |{g : a_g != 0 or b_g != 0}|.
@@ -259,7 +294,7 @@ constexpr float kBlack[3] = {0.f, 0.f, 0.f};
 gs_status launch_zero(void* a, size_t a_bytes, void* b, size_t b_bytes, cudaStream_t st) {
   const long long na = (long long)(a_bytes / 4), nb = b ? (long long)(b_bytes / 4) : 0;
   if (na + nb == 0) return GS_OK;
-  long long blocks = (na + nb + 255) / 256;
+  long long blocks = (na / 4 + nb / 4 + 255) / 256 + 1;  // one 16-byte store per thread per round
   if (blocks > 152 * 8) blocks = 152 * 8;
   GS_TRACE("k_zero", st);
   launch_pdl(k_zero, (unsigned)blocks, 256, 0, st, static_cast<uint32_t*>(a), na, static_cast<uint32_t*>(b), nb);
@@ -282,6 +317,7 @@ const char* gs_status_string(gs_status s) {
     case GS_ERR_TIMEOUT: return "bounded wait timed out";
     case GS_ERR_CUDA: return "CUDA error";
     case GS_ERR_UNSUPPORTED: return "unsupported option combination";
+    case GS_ERR_BOUNDS: return "index out of range (bounds-checked build)";
   }
   return "unknown status";
 }
@@ -289,6 +325,7 @@ const char* gs_status_string(gs_status s) {
 gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const float* scales, const float* quats,
                      const float* opacity, float* uv, float* conic_opacity, float* depth, int32_t* rect,
                      int32_t* tiles_touched, int64_t* n_instances, void* stream) {
+  GS_NVTX("gs_project");
   if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
   if (P > 0 && (!means || !scales || !quats || !opacity || !uv || !conic_opacity || !depth || !rect ||
                 !tiles_touched))
@@ -311,6 +348,7 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                       const int32_t* tiles_touched, int64_t capacity, void* workspace, size_t workspace_bytes,
                       uint64_t* keys, uint32_t* gids, int32_t* tile_ranges, int64_t* n_instances, int32_t* status,
                       void* stream) {
+  GS_NVTX("gs_bin_sort");
   if (!cam_ok(cam) || P < 0 || capacity < 1 || capacity >= (1ll << 31)) return GS_ERR_INVALID_ARG;
   if (num_tiles(cam) > (1 << 24)) return GS_ERR_INVALID_ARG;
   if (!gids || !tile_ranges || !workspace || (P > 0 && (!depth || !rect || !tiles_touched)))
@@ -324,18 +362,30 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
                          S(stream));
 }
 
+gs_status gs_count_nonfinite(int64_t n, const float* x, uint64_t* count, void* stream) {
+  if (n < 0 || (n > 0 && !x) || !count || !aligned(x, 4) || !aligned(count, 8)) return GS_ERR_INVALID_ARG;
+  if (n == 0) return GS_OK;
+  long long blocks = (n / 4 + 255) / 256 + 1;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  GS_TRACE("k_count_nonfinite", S(stream));
+  k_count_nonfinite<<<(unsigned)blocks, 256, 0, S(stream)>>>(x, (long long)n, reinterpret_cast<unsigned long long*>(count));
+  return last_launch_status();
+}
+
 gs_status gs_set_lookback_wait_ns(uint64_t ns) {
   set_lookback_wait_ns((unsigned long long)ns);
   return GS_OK;
 }
 
 gs_status gs_zero(void* ptr, size_t bytes, void* stream) {
+  GS_NVTX("gs_zero");
   if (bytes == 0) return GS_OK;
   if (!ptr || !aligned(ptr, 4) || bytes % 4 != 0) return GS_ERR_INVALID_ARG;
   return launch_zero(ptr, bytes, nullptr, 0, S(stream));
 }
 
 gs_status gs_tile_order(int32_t num_tiles, const int32_t* tile_ranges, int32_t* tile_order, void* stream) {
+  GS_NVTX("gs_tile_order");
   if (num_tiles < 0 || (num_tiles > 0 && (!tile_ranges || !tile_order)) || !aligned(tile_ranges, 8))
     return GS_ERR_INVALID_ARG;
   if (num_tiles == 0) return GS_OK;
@@ -373,16 +423,16 @@ gs_status render_fwd_impl(const gs_camera* cam, int32_t P, const int32_t* tile_r
     gs_status st = launch_render_fwd(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, nullptr, 0,
                                      0, 1, b,
                                      out_rgb, out_depth, out_alpha, nullptr, T_final, last_idx, n_contrib, visible,
-                                     nullptr, S(stream));
+                                     nullptr, P, status, S(stream));
     if (st != GS_OK) return st;
-    return launch_render_fwd_tc(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity,
+    return launch_render_fwd_tc(k, P, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity,
                                 static_cast<const __nv_bfloat16*>(feats), last_idx, N, out_feat, status,
                                 S(stream));
   }
   if (l1 && n > 16) return GS_ERR_UNSUPPORTED;
   return launch_render_fwd(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, n,
                            feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, out_rgb, out_depth, out_alpha, out_feat,
-                           T_final, last_idx, n_contrib, visible, l1, S(stream));
+                           T_final, last_idx, n_contrib, visible, l1, P, status, S(stream));
 }
 }  // namespace
 
@@ -393,6 +443,7 @@ gs_status gs_render_fwd(const gs_camera* cam, int32_t P, const int32_t* tile_ran
                         const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
                         float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
                         int32_t* status, void* stream) {
+  GS_NVTX("gs_render_fwd");
   return render_fwd_impl(cam, P, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, N, feat_dtype, layout,
                          flags, bg, out_rgb, out_depth, out_alpha, out_feat, T_final, last_idx, n_contrib, visible,
                          nullptr, status, stream);
@@ -405,6 +456,7 @@ gs_status gs_render_fwd_l1(const gs_camera* cam, int32_t P, const int32_t* tile_
                            const float* bg, float* out_rgb, float* out_depth, float* out_alpha, float* out_feat,
                            float* T_final, int32_t* last_idx, int32_t* n_contrib, uint8_t* visible,
                            const gs_l1_terms* l1, uint32_t* l1_signs, int32_t* status, void* stream) {
+  GS_NVTX("gs_render_fwd_l1");
   if (!l1 || !l1_signs || !aligned(l1_signs, 8)) return GS_ERR_INVALID_ARG;
   const bool feat_on = (flags & GS_FEAT_ON) != 0;
   L1Fwd in{};
@@ -474,10 +526,10 @@ gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, c
   gs_status st = launch_render_bwd(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, depth, colors, feats, tc ? 0 : n,
                                    feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, T_final, last_idx, dL_drgb,
                                    dL_ddepth, dL_dalpha, (feat_on && !tc) ? dL_dfeat : nullptr, coupled ? 1 : 0, w_uv,
-                                   w_conic, w_depth, d_opacity, d_colors, d_feats, l1, S(stream));
+                                   w_conic, w_depth, d_opacity, d_colors, d_feats, l1, P, status, S(stream));
   if (st != GS_OK) return st;
   if (tc && dL_dfeat) {
-    st = launch_render_bwd_feat_tc(k, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, last_idx, dL_dfeat,
+    st = launch_render_bwd_feat_tc(k, P, tile_ranges, tile_order, gids, inst_masks, uv, conic_opacity, last_idx, dL_dfeat,
                                    N, d_feats,
                                    status,
                                    S(stream));
@@ -497,6 +549,7 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
                         const float* dL_dfeat, int32_t feat_grad_mode, void* workspace, size_t workspace_bytes,
                         float* d_means, float* d_scales, float* d_quats, float* d_opacity, float* d_colors,
                         float* d_feats, float* d_pose, int32_t* status, void* stream) {
+  GS_NVTX("gs_render_bwd");
   return render_bwd_impl(cam, P, means, scales, quats, colors, feats, N, feat_dtype, layout, flags, bg, tile_ranges,
                          tile_order, gids, inst_masks, uv, conic_opacity, depth, T_final, last_idx, dL_drgb, dL_ddepth, dL_dalpha, dL_dfeat,
                          nullptr, feat_grad_mode, workspace, workspace_bytes, d_means, d_scales, d_quats, d_opacity,
@@ -512,6 +565,7 @@ gs_status gs_render_bwd_l1(const gs_camera* cam, int32_t P, const float* means, 
                            const uint32_t* l1_signs, void* workspace, size_t workspace_bytes, float* d_means,
                            float* d_scales, float* d_quats, float* d_opacity, float* d_colors, float* d_feats,
                            float* d_pose, int32_t* status, void* stream) {
+  GS_NVTX("gs_render_bwd_l1");
   if (!l1 || !l1_signs || !aligned(l1_signs, 8)) return GS_ERR_INVALID_ARG;
   L1Bwd in{};
   in.on = 1;
@@ -539,6 +593,7 @@ gs_status gs_l1_loss_grad(int64_t n, const float* pred, const float* target, flo
 
 gs_status gs_l1_signs(int32_t width, int32_t height, int32_t N, int32_t layout, const float* rgb, const float* depth,
                       const float* feat, const gs_l1_terms* l1, uint32_t* l1_signs, void* stream) {
+  GS_NVTX("gs_l1_signs");
   if (width <= 0 || height <= 0 || N < 0 || !l1 || !l1_signs || !aligned(l1_signs, 8)) return GS_ERR_INVALID_ARG;
   if (layout != GS_LAYOUT_CHW && layout != GS_LAYOUT_HWC) return GS_ERR_INVALID_ARG;
   if (N > 16) return GS_ERR_UNSUPPORTED;

@@ -1,4 +1,4 @@
-// Per-pixel feature decoder o(.) (Eq. 9, read as a 1x1 lift of the latent
+// Per-pixel feature decoder o(.) (Eq. 11, read as a 1x1 lift of the latent
 // feature map): y = W2^T gelu(W1^T z + b1) + b2, exact-erf GELU, trained on
 // sampled pixels with an MSE loss against the full-width render, and Adam.
 //

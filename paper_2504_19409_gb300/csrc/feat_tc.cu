@@ -152,8 +152,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 //     one half tile ahead); every 32 entries fill one stage of a 4-deep
 //     ring: the records (uv, conic and opacity) by cp.async and the id list;
 //   warps 22-29 (loaders): the stage's bf16 feature rows (B operand,
-//     channels contiguous) by 16-byte cp.async, 4 rows per warp; the stage's
-//     "full" barrier completes when every copy has landed;
+//     channels contiguous) by 16-byte cp.async, each instruction whole core
+//     matrices (4 chunks of 8 rows); the stage's "full" barrier completes
+//     when every copy has landed;
 //   warps 6-21 (weight builders, 4 threads per pixel, 8 entries each):
 //     alpha of each entry (exact skip test; 0 at or past the pixel's last
 //     index), w = alpha T with T the product of (1 - alpha) over the entries
@@ -217,6 +218,7 @@ struct FwParams {
   const __nv_bfloat16* feats;
   const int* last_idx;
   int N, tmem_cols, nhalf;
+  int P;  // Gaussians (bound of the checked build's id checks)
   int32_t* status;
 };
 
@@ -294,7 +296,7 @@ __device__ void fw_producer(const FwParams& p, FwSmem& S) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int pos = base + 32 * i + lane;
-      gb[i] = pos < maxlast ? p.gids[rg.x + pos] : 0u;
+      gb[i] = pos < maxlast ? checked_id(p.gids[rg.x + pos], p.P, p.status) : 0u;
       mb[i] = pos < maxlast ? (p.masks ? (uint32_t)p.masks[rg.x + pos] : 0xFu) : 0u;
     }
   };
@@ -308,6 +310,7 @@ __device__ void fw_producer(const FwParams& p, FwSmem& S) {
     int maxlast = max(max(nli[0], nli[1]), max(nli[2], nli[3]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
+    maxlast = checked_len(maxlast, rg.y - rg.x, p.status);
     fetch_meta(r + 1, nrg, nli, nhalf_);
     int fill = 0;
     bool first = true;
@@ -381,15 +384,19 @@ __device__ void fw_producer(const FwParams& p, FwSmem& S) {
   }
 }
 
-// warps 22-29: the bf16 feature rows of each stage (B operand), 4 rows per
-// warp, by 16-byte cp.async; each lane's copies complete an arrival on the
-// stage's "full" barrier
+// warps 22-29: the bf16 feature rows of each stage (B operand) by 16-byte
+// cp.async; warp L copies rows 8 (L / 2) .. 8 (L / 2) + 7 and half of their
+// chunks, each instruction 4 chunks of 8 rows, which are whole 128-byte core
+// matrices in shared memory (no bank conflicts); each lane's copies complete
+// an arrival on the stage's "full" barrier
 __device__ void fw_loader(const FwParams& p, FwSmem& S) {
   const int lane = threadIdx.x & 31, L = (threadIdx.x >> 5) - kFwWarpLoad;
   volatile int* abort = &S.abort;
   const int cpr = p.N / 8;  // 16-byte chunks per feature row
   const uint32_t SK = (uint32_t)p.N * 16;
-  constexpr int kRows = kFwK / kFwLoaders;
+  static_assert(kFwLoaders == 2 * (kFwK / 8), "two loader warps per group of 8 rows");
+  const int k = 8 * (L >> 1) + (lane & 7);    // this lane's row
+  const int c_begin = (L & 1) * (cpr / 2) + (lane >> 3), c_end = (L & 1) ? cpr : cpr / 2;
   int s = 0;
   uint32_t ph = 0;
   for (int r = 0;; ++r) {
@@ -398,15 +405,10 @@ __device__ void fw_loader(const FwParams& p, FwSmem& S) {
       if (!fw_wait(smem_u32(&S.ids[s]), ph, abort, p.status)) return;
       FwStage& st = S.st[s];
       const int n = st.nvalid, flags = st.flags;
-      const uint32_t b0 = smem_u32(st.B);
-#pragma unroll
-      for (int i = 0; i < kRows; ++i) {
-        const int k = kRows * L + i;
-        const bool valid = k < n;
-        const __nv_bfloat16* row = p.feats + (size_t)st.gid[k] * p.N;
-        const uint32_t dk = b0 + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
-        for (int c = lane; c < cpr; c += 32) cp_async16(dk + (uint32_t)c * 128u, row + 8 * c, valid);
-      }
+      const bool valid = k < n;
+      const __nv_bfloat16* row = p.feats + (size_t)st.gid[k] * p.N;
+      const uint32_t dk = smem_u32(st.B) + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 16u;
+      for (int c = c_begin; c < c_end; c += 4) cp_async16(dk + (uint32_t)c * 128u, row + 8 * c, valid);
       asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[s])) : "memory");
       if (++s == kFwStages) {
         s = 0;
@@ -641,11 +643,13 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_render_feat_tc(const FwParams
 
 }  // namespace
 
-gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                               const uint8_t* masks, const float* uv, const float* co, const __nv_bfloat16* feats,
-                               const int32_t* last_idx, int N, float* out_feat, int32_t* status, cudaStream_t st) {
+gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,
+                               const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
+                               const __nv_bfloat16* feats, const int32_t* last_idx, int N, float* out_feat,
+                               int32_t* status, cudaStream_t st) {
   if (N <= 0 || N % 64 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
   FwParams p;
+  p.P = P;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.order = order;
@@ -763,6 +767,7 @@ struct BwParams {
   const int* last_idx;
   const float* g_feat;  // [H, W, N]
   int N, tmem_cols, nhalf;
+  int P;  // Gaussians (bound of the checked build's id checks)
   float* d_feats;  // [P, N]
   int32_t* status;
 };
@@ -824,6 +829,7 @@ __device__ bool bw_producer(const BwParams& p, BwSmem& S, int tx, int ty, int ha
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(0xffffffffu, maxlast, o));
+  maxlast = checked_len(maxlast, rg.y - rg.x, p.status);
   int fill = 0;
   bool first = true;
   auto emit = [&](int n, bool last) -> bool {
@@ -854,7 +860,7 @@ __device__ bool bw_producer(const BwParams& p, BwSmem& S, int tx, int ty, int ha
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int pos = base + 32 * i + lane;
-      gb[i] = pos < maxlast ? p.gids[rg.x + pos] : 0u;
+      gb[i] = pos < maxlast ? checked_id(p.gids[rg.x + pos], p.P, p.status) : 0u;
       mb[i] = pos < maxlast ? (p.masks ? (uint32_t)p.masks[rg.x + pos] : 0xFu) : 0u;
     }
   };
@@ -1149,7 +1155,7 @@ gs_status launch_bwd_nmb(const BwParams& p, cudaStream_t st) {
 
 }  // namespace
 
-gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, const int32_t* order,
+gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,
                                     const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
                                     const int32_t* last_idx, const float* g_feat, int N, float* d_feats,
                                     int32_t* status, cudaStream_t st) {
@@ -1157,6 +1163,7 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, cons
   // the vector atomics of the epilogue need NMB * 4-byte alignment of every row
   if ((reinterpret_cast<uintptr_t>(d_feats) & 15u) != 0) return GS_ERR_INVALID_ARG;
   BwParams p;
+  p.P = P;
   p.cam = cam;
   p.ranges = reinterpret_cast<const int2*>(ranges);
   p.order = order;
@@ -1392,8 +1399,8 @@ __global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p,
 
 }  // namespace
 
-// Label read-out straight from the latent render (Eq. 9 composed with
-// Eq. 11): with y = W2^T h + b2, the logit of label l is
+// Label read-out straight from the latent render (Eq. 11 composed with
+// Eq. 12): with y = W2^T h + b2, the logit of label l is
 //   y . q(l) = h . G(:, l) + c(l),   G = W2 q^T [128 x L],   c = b2 . q^T,
 // so the 512-d features never have to be formed. Per 128-pixel tile:
 //   D1 [128 x 128] = z W1 (one K=16 MMA), h = gelu(D1 + b1) -> bf16 -> H,

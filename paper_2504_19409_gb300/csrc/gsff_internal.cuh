@@ -7,6 +7,8 @@
 
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gsff.h"
 
 namespace gsff {
@@ -99,6 +101,32 @@ __device__ __forceinline__ void flag_status(int32_t* status, gs_status s) {
   if (status) atomicOr(status, 1 << (int)s);
 }
 
+// Indices the kernels read from their inputs and then follow: the Gaussian
+// ids of the sorted lists and the saved last indices. In the bounds-checked
+// build (GS_CHECKED) an id past P flags GS_ERR_BOUNDS and is replaced by 0,
+// and a list length past the tile's list is cut to it (flagged the same way),
+// so that no gather leaves the caller's arrays; in the normal build both are
+// used as given.
+__device__ __forceinline__ uint32_t checked_id(uint32_t g, int P, int32_t* status) {
+#ifdef GS_CHECKED
+  if (g >= (uint32_t)P) {
+    flag_status(status, GS_ERR_BOUNDS);
+    return 0u;
+  }
+#endif
+  return g;
+}
+
+__device__ __forceinline__ int checked_len(int n, int list_len, int32_t* status) {
+#ifdef GS_CHECKED
+  if (n > list_len || n < 0) {
+    flag_status(status, GS_ERR_BOUNDS);
+    return n < 0 ? 0 : list_len;
+  }
+#endif
+  return n;
+}
+
 // alpha of one (pixel, Gaussian) pair, o exp(-(A dx^2 + 2 B dx dy + C dy^2) / 2)
 // clamped to 0.99. It is evaluated in base 2 from the conic scaled by log2(e)
 // (conic_q, which a kernel may compute once per Gaussian): the exponent
@@ -169,6 +197,14 @@ struct TraceScope {
 
 #define GS_TRACE(name, stream) ::gsff::TraceScope _gs_trace_scope_(name, stream)
 
+// An NVTX range around an ABI call (seen by profilers that record NVTX; a
+// no-op otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+#define GS_NVTX(name) ::gsff::NvtxRange _gs_nvtx_range_(name)
+
 inline gs_status last_launch_status() {
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
@@ -181,11 +217,13 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 void set_lookback_wait_ns(unsigned long long ns);
 
 // ---- launchers implemented in the .cu files ---------------------------------
-gs_status launch_render_fwd_tc(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                               const uint8_t* masks, const float* uv, const float* co, const __nv_bfloat16* feats,
-                               const int32_t* last_idx, int N, float* out_feat, int32_t* status, cudaStream_t st);
-gs_status launch_render_bwd_feat_tc(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
-                                    const uint8_t* masks, const float* uv, const float* co, const int32_t* last_idx,
-                                    const float* g_feat, int N, float* d_feats, int32_t* status, cudaStream_t st);
+gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,
+                               const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
+                               const __nv_bfloat16* feats, const int32_t* last_idx, int N, float* out_feat,
+                               int32_t* status, cudaStream_t st);
+gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,
+                                    const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
+                                    const int32_t* last_idx, const float* g_feat, int N, float* d_feats,
+                                    int32_t* status, cudaStream_t st);
 
 }  // namespace gsff

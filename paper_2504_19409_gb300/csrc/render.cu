@@ -58,6 +58,8 @@ struct FwdParams {
   int* n_contrib;
   uint8_t* visible;  // [P] or null: set to 1 when blended with T > 0.5 in front (Sec. 3.2)
   L1Fwd l1;          // L1 loss against targets, evaluated in the epilogue (N <= 16)
+  int P;             // Gaussians (bound of the checked build's id checks)
+  int32_t* status;
 };
 
 
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const FwdParams p) {
     if (__syncthreads_count(done) == kTilePix) break;
     const int idx = start + threadIdx.x;
     if (idx < rg.y) {
-      const uint32_t g = p.gids[idx];
+      const uint32_t g = checked_id(p.gids[idx], p.P, p.status);
       const float4 co = p.co[g];
       const float2 u = p.uv[g];
       s_uv[threadIdx.x] = u;
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kFwd2Threads, 5) k_render_fwd2(const FwdParams
     for (int i = threadIdx.x; i < kB; i += kFwd2Threads) {
       const int idx = start + i;
       if (idx < rg.y) {
-        const uint32_t g = p.gids[idx];
+        const uint32_t g = checked_id(p.gids[idx], p.P, p.status);
         const float4 co = p.co[g];
         const float2 u = p.uv[g];
         s_uv[i] = u;
@@ -602,6 +604,8 @@ struct BwdParams {
   float* d_colors;
   float* d_feats;
   L1Bwd l1;  // cotangents rebuilt from the forward's L1 sign bits (tensor-core adjoint only)
+  int P;     // Gaussians (bound of the checked build's id checks)
+  int32_t* status;
 };
 
 // Lane l ends up with the warp-wide sum of v[l] (see the file comment).
@@ -700,13 +704,13 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
     bgdot[q] = p.bg[0] * gC0[q] + p.bg[1] * gC1[q] + p.bg[2] * gC2[q];
   }
   __syncthreads();
-  const int maxlast = s_maxlast;
+  const int maxlast = checked_len(s_maxlast, rg.y - rg.x, p.status);
 
   for (int hi = rg.x + maxlast; hi > rg.x; hi -= BB) {
     const int lo = max(rg.x, hi - BB);
     const int n = hi - lo;
     if ((int)threadIdx.x < n) {
-      const uint32_t g = p.gids[lo + threadIdx.x];
+      const uint32_t g = checked_id(p.gids[lo + threadIdx.x], p.P, p.status);
       const float4 co = p.co[g];
       const float2 u = p.uv[g];
       s_gid[threadIdx.x] = g;
@@ -1106,7 +1110,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       bm[s][hf] = *reinterpret_cast<const uint32_t*>(&v);
     }
   __syncthreads();
-  const int maxlast = s_maxlast;
+  const int maxlast = checked_len(s_maxlast, rg.y - rg.x, p.status);
   // the walk's per-pixel state, pixel q in lane q of packed operands
   float2 T2 = make_float2(T[0], T[1]), J2 = make_float2(J[0], J[1]);
   const float2 gC02 = make_float2(gC0[0], gC0[1]), gC12 = make_float2(gC1[0], gC1[1]);
@@ -1126,13 +1130,13 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
   if (wid == 0 && nb > 0) {
     const int lo0 = batch_lo(0);
     if (lane < batch_hi(0) - lo0) {
-      stage_batch(p, s_b[0], lane, p.gids[lo0 + lane]);
+      stage_batch(p, s_b[0], lane, checked_id(p.gids[lo0 + lane], p.P, p.status));
       if (stored) s_b[0].wmask[lane] = p.masks[lo0 + lane];
       cp_async_wait_all();
       finish_batch(s_b[0], lane, tx, ty, stored);
     }
     if (nb > 1 && lane < batch_hi(1) - batch_lo(1)) {
-      g_next = p.gids[batch_lo(1) + lane];
+      g_next = checked_id(p.gids[batch_lo(1) + lane], p.P, p.status);
       if (stored) m_next = p.masks[batch_lo(1) + lane];
     }
   }
@@ -1156,7 +1160,7 @@ __global__ void __launch_bounds__(mma_bwd::kThreads, 4) k_render_bwd_mma(const B
       if (stored) s_b[(b + 1) % kNBuf].wmask[lane] = (uint8_t)m_next;
     }
     if (wid == 0 && b + 2 < nb && lane < batch_hi(b + 2) - batch_lo(b + 2)) {
-      g_next = p.gids[batch_lo(b + 2) + lane];
+      g_next = checked_id(p.gids[batch_lo(b + 2) + lane], p.P, p.status);
       if (stored) m_next = p.masks[batch_lo(b + 2) + lane];
     }
 
@@ -1356,8 +1360,11 @@ gs_status launch_render_fwd(const CamF& cam, const int32_t* ranges, const int32_
                             const float* co, const float* depth, const float* colors, const void* feats, int N,
                             int bf16, int hwc, const float bg[3], float* out_rgb, float* out_depth,
                             float* out_alpha, float* out_feat, float* T_final, int32_t* last_idx,
-                            int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1, cudaStream_t st) {
+                            int32_t* n_contrib, uint8_t* visible, const L1Fwd* l1, int P, int32_t* status,
+                            cudaStream_t st) {
   FwdParams p;
+  p.P = P;
+  p.status = status;
   p.l1 = l1 ? *l1 : L1Fwd{};
   if (p.l1.on && N > 16) return GS_ERR_UNSUPPORTED;
   p.cam = cam;
@@ -1423,8 +1430,11 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_
                             int bf16, int hwc, const float bg[3], const float* T_final, const int32_t* last_idx,
                             const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
                             int coupled, float* d_uv, float* d_conic, float* d_depth, float* d_opacity,
-                            float* d_colors, float* d_feats, const L1Bwd* l1, cudaStream_t st) {
+                            float* d_colors, float* d_feats, const L1Bwd* l1, int P, int32_t* status,
+                            cudaStream_t st) {
   BwdParams p;
+  p.P = P;
+  p.status = status;
   p.l1 = l1 ? *l1 : L1Bwd{};
   if (p.l1.on && (N > 16 || coupled)) return GS_ERR_UNSUPPORTED;
   p.cam = cam;

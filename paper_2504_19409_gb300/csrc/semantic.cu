@@ -1,13 +1,13 @@
 // Semantic supervision and read-out of the rendered feature field (Sec. 3.3).
 //
-//   Eq. 8:  L_s = -(1/HW) sum_p sum_c L_p(c) log F_p(c), with L_p one-hot
+//   Eq. 9:  L_s = -(1/HW) sum_p sum_c L_p(c) log F_p(c), with L_p one-hot
 //           labels; F is read as per-pixel logits over the N channels
 //           normalised by a softmax (the rendered features are unbounded),
 //           so L_s = (1/HW) sum_p [logsumexp(F_p) - F_p(l_p)] and
 //           dL/dF_p = (softmax(F_p) - onehot(l_p)) / HW. Pixels with a
 //           negative label are ignored (no loss, zero gradient).
-//   Eq. 9:  predicted labels argmax_c F_p(c) (ties: the lowest channel).
-//   Eq. 11: p(l | x) = exp(f(x) . q(l)) / sum_l' exp(f(x) . q(l')), per
+//   Eq. 10:  predicted labels argmax_c F_p(c) (ties: the lowest channel).
+//   Eq. 12: p(l | x) = exp(f(x) . q(l)) / sum_l' exp(f(x) . q(l')), per
 //           pixel feature f(x) (M channels) and L query vectors q(l).
 
 #include "gsff_internal.cuh"

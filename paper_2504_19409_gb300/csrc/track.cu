@@ -1,4 +1,4 @@
-// Camera tracking (Sec. 3.2): the tracking loss of Eq. 5 and the pose update.
+// Camera tracking (Sec. 3.2): the tracking loss of Eq. 6 and the pose update.
 //
 //   L = lambda_t m_v m_e L_c + (1 - lambda_t) m_v L_d,
 //

@@ -1,8 +1,8 @@
-"""Learned per-pixel decoder o(.) of Eq. 9 and its trainer.
+"""Learned per-pixel decoder o(.) of Eq. 11 and its trainer.
 
 A din-channel latent per Gaussian is rendered with the rasterizer (Eq. 3 with
 f := latent) and lifted per pixel to the full feature width by
-y = W2^T gelu(W1^T z + b1) + b2 (Eq. 9, read as a 1x1 lift). Every step runs
+y = W2^T gelu(W1^T z + b1) + b2 (Eq. 11, read as a 1x1 lift). Every step runs
 in the library's kernels (gs_render_fwd / gs_render_bwd for the latent
 render, gs_decoder_train for the MLP, gs_adam_step for the updates); this
 module only owns device buffers and orders the calls.
@@ -78,7 +78,7 @@ class Decoder:
         return y
 
     def labels_tc(self, z: torch.Tensor, queries: torch.Tensor, probs=True, labels=True, status=None, stream=None):
-        """Eq. 11 label probabilities / labels of the decoded field straight from the latents z [n, 16]
+        """Eq. 12 label probabilities / labels of the decoded field straight from the latents z [n, 16]
         (the 512-d features are never formed): returns (probs [n, L] or None, labels [n] or None)."""
         n, L = z.shape[0], queries.shape[0]
         pr = torch.empty(n, L, device=self.device) if probs else None

@@ -4,7 +4,7 @@ With the Gaussians frozen, the frame is rendered at the current pose
 estimate; the first render's opacity gives the visibility mask m_v and the
 observed image's gradient the edge mask m_e (gs_edge_mask); each iteration
 renders (gs_project, gs_bin_sort, gs_tile_order, gs_render_fwd), forms the
-cotangents of Eq. 5 as sign words with their two weights
+cotangents of Eq. 6 as sign words with their two weights
 (gs_tracking_loss_signs), back-propagates to the pose tangent only
 (gs_render_bwd_l1 with the Gaussian gradients switched off) and updates the
 pose on the device (gs_pose_update: Adam, then T <- Exp(delta) T). The pose

@@ -70,3 +70,26 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(g, "_lib", None)
     with pytest.raises(g.GsffError):
         g.lib()
+
+
+def test_checked_build_exports_the_same_symbols():
+    """The bounds-checked variant (GS_CHECKED) is the same C ABI."""
+    from paper_2504_19409_gb300 import build
+    lib = ctypes.CDLL(build.build(checked=True))
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_status_word_plumbing(built):
+    """Device status words decode bit by bit into the error kinds, including
+    the bounds-checked build's GS_ERR_BOUNDS (no GPU needed)."""
+    import paper_2504_19409_gb300 as g
+    assert g.GS_ERR_BOUNDS == 6
+    assert g.status_names(1 << g.GS_ERR_BOUNDS) == ["index out of range (bounds-checked build)"]
+    both = (1 << g.GS_ERR_TIMEOUT) | (1 << g.GS_ERR_BOUNDS)
+    assert g.status_names(both) == ["bounded wait timed out", "index out of range (bounds-checked build)"]
+    assert g.status_names(0) == []
+    L = g.lib()
+    # the scan rejects a missing output synchronously (nothing is launched)
+    assert L.gs_count_nonfinite(16, ctypes.c_void_p(256), None, None) == g.GS_ERR_INVALID_ARG
+    assert L.gs_count_nonfinite(-1, None, ctypes.c_void_p(256), None) == g.GS_ERR_INVALID_ARG

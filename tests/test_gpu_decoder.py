@@ -1,4 +1,4 @@
-"""Learned decoder o(.) (Eq. 9 as a per-pixel 1x1 lift, 16 -> 128 -> 512,
+"""Learned decoder o(.) (Eq. 11 as a per-pixel 1x1 lift, 16 -> 128 -> 512,
 exact-erf GELU, bf16 weights, fp32 accumulation) on the GPU vs the FP64
 oracle, and what training it gains.
 

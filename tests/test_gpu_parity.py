@@ -351,7 +351,7 @@ def test_room_scale_gradients(room_frame):
     check_grads(g["grads"], o["grads"], ("means", "scales", "quats", "opacity", "colors", "feats", "pose"))
 
 
-# ---- keyframe visibility (Sec. 3.2, Eq. 6) and co-visibility IoU ----------------
+# ---- keyframe visibility (Sec. 3.2, Eq. 5) and co-visibility IoU ----------------
 
 VIS_BAND = 1e-5  # relative distance of the oracle's max T from 0.5 below which a decision is not compared
 

@@ -1,9 +1,9 @@
 """Semantic supervision and read-out (Sec. 3.3) on the GPU against the oracle.
 
-Bars: the Eq. 8 gradient within 2e-6 / HW per entry and the loss within 1e-5
-(fp32 softmax against FP64); the argmax of Eq. 9 and the Eq. 11 labels are
+Bars: the Eq. 9 gradient within 2e-6 / HW per entry and the loss within 1e-5
+(fp32 softmax against FP64); the argmax of Eq. 10 and the Eq. 12 labels are
 decisions taken on the same binary32 values (the logits replayed with the
-kernel's fused multiply-add order), so they are compared exactly; the Eq. 11
+kernel's fused multiply-add order), so they are compared exactly; the Eq. 12
 probabilities within 1e-5.
 """
 import numpy as np

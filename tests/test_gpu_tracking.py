@@ -1,4 +1,4 @@
-"""Camera tracking (Sec. 3.2, Eq. 5) on the GPU against the oracle, and
+"""Camera tracking (Sec. 3.2, Eq. 6) on the GPU against the oracle, and
 what the loop achieves.
 
 Bars: the edge mask and the loss cotangents are decisions and signs taken on

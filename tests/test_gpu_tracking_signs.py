@@ -1,4 +1,4 @@
-"""gs_tracking_loss_signs: Eq. 5's cotangents as sign words. The words are
+"""gs_tracking_loss_signs: Eq. 6's cotangents as sign words. The words are
 exactly the signs of gs_tracking_loss_grad's float cotangents (the same
 binary32 differences and masks), the loss is the same to 1e-5, and the pose
 gradient through gs_render_bwd_l1 equals the one of gs_render_bwd on the

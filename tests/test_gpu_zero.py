@@ -1,15 +1,15 @@
 """gs_zero, the clearing kernel of the launch chain (it clears the gradient
 arena before every adjoint): the requested words become zero and nothing
 around them changes, for spans past the kernel's grid stride (1216 blocks of
-256 threads, one word per thread per round), odd word counts and slices that
-start off a 16-byte boundary."""
+256 threads, one 16-byte store per thread per round), odd word counts and
+slices that start off a 16-byte boundary (single-word head and tail)."""
 import numpy as np
 import pytest
 import torch
 
 pytestmark = pytest.mark.gpu
 
-GRID_WORDS = 1216 * 256
+GRID_WORDS = 1216 * 256 * 4
 PATTERN = 0x5A5A5A5A
 
 

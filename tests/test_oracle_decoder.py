@@ -1,4 +1,4 @@
-"""Pins of the oracle's per-pixel decoder (Eq. 9 read as a 1x1 lift,
+"""Pins of the oracle's per-pixel decoder (Eq. 11 read as a 1x1 lift,
 y = W2^T gelu(W1^T z + b1) + b2 with the exact erf GELU)."""
 import math
 

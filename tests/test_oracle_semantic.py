@@ -1,5 +1,5 @@
-"""Pins of the oracle's semantic pieces (Sec. 3.3): the Eq. 8 cross-entropy
-on per-pixel logits, the Eq. 9 argmax and the Eq. 11 label probabilities.
+"""Pins of the oracle's semantic pieces (Sec. 3.3): the Eq. 9 cross-entropy
+on per-pixel logits, the Eq. 10 argmax and the Eq. 12 label probabilities.
 
 * closed forms: two classes give loss = softplus(b - a) for label 0 and the
   gradient (sigmoid(a - b) - 1, sigmoid(b - a)) / HW; identity queries make

@@ -1,4 +1,4 @@
-"""Pins of the oracle's tracking pieces (Sec. 3.2, Eq. 5): the SE(3) update,
+"""Pins of the oracle's tracking pieces (Sec. 3.2, Eq. 6): the SE(3) update,
 the Adam step on the pose tangent, the edge mask and the tracking loss.
 
 * Exp(delta) against scipy.linalg.expm of the 4x4 twist matrix (an
@@ -154,7 +154,7 @@ def test_edge_mask_against_scipy_sobel(ora):
 
 
 def test_tracking_loss_two_by_two(ora):
-    """Hand-worked Eq. 5 on a 2x2 image, lambda = 0.75, HW = 4:
+    """Hand-worked Eq. 6 on a 2x2 image, lambda = 0.75, HW = 4:
     colour weight 0.75/12 = 1/16 on pixels with m_v m_e, depth weight
     0.25/4 = 1/16 on pixels with m_v and observed depth > 0."""
     rgb = np.zeros((3, 2, 2))
