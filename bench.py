@@ -1095,6 +1095,83 @@ def decoder_form(args, peaks, kind, timing=True, label_query=False):
     return out
 
 
+def pair_state_form(args):
+    """Config 3's comparison on the SLAM-frame scene (300k Gaussians, 1200 x
+    680) with N = 64 fp32 features: fwd + bwd (decoupled feature gradient,
+    float cotangents) with the transmittance recovered by division from the
+    saved T_final / last index (8 B per pixel), against storing the
+    transmittance in front of every blended pair (4 B per pair, plus the
+    per-pixel offsets) and reading it in the adjoint; both on the SIMT adjoint
+    in 32-channel chunks (gs_render_bwd_pairs), the library's default adjoint
+    at N = 64 (tensor-core pixel sums in 16-channel chunks) beside them. The
+    accuracy of both forms against the FP64 oracle is measured by the tests
+    (500-Gaussian case and a near-opaque case)."""
+    import torch
+    import paper_2504_19409_gb300 as g
+    from paper_2504_19409_gb300 import scenegen as sg
+    dev = torch.device("cuda", 0)
+    N = 64
+    sc = sg.room_scene(SCENE_SEED, P_ROOM, N)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    means, scales, quats, opac, cols, feats = (t(x) for x in (sc.means, sc.scales, sc.quats, sc.opacity, sc.colors,
+                                                              sc.feats))
+    ras = g.Rasterizer(P_ROOM, WIDTH, HEIGHT, N=N, device=dev)
+    frames = [k % N_FRAMES for k in range(args.warmup + 8)]
+    timed = frames[args.warmup:]
+    for k in sorted(set(frames)):
+        ras.ensure_capacity(frame_camera(k), means, scales, quats, opac)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    g_rgb = torch.randn(3, HEIGHT, WIDTH, device=dev, generator=gen)
+    g_d = torch.randn(HEIGHT, WIDTH, device=dev, generator=gen)
+    g_f = torch.randn(N, HEIGHT, WIDTH, device=dev, generator=gen) / N
+    blends = {}
+    for k in sorted(set(frames)):
+        blends[k] = int(ras.forward(frame_camera(k), means, scales, quats, opac, cols, feats)["n_contrib"].sum().item())
+    pairs = {}
+    cap = int(max(blends.values()) * 1.05) + 1024
+    pairs = g.render_fwd_pairs(frame_camera(frames[0]), ras.proj, ras.sort, ras.fwd, capacity=cap)
+
+    def division(k):
+        cam = frame_camera(k)
+        ras.forward(cam, means, scales, quats, opac, cols, feats)
+        g.zero_(ras.grad_arena)
+        g.render_bwd_pairs(cam, means, scales, quats, cols, feats, ras.proj, ras.sort, ras.fwd, None, g_rgb, g_d, None,
+                           g_f, grads=ras.grads, workspace=ras.bwd_ws, status=ras.status)
+
+    def stored(k):
+        cam = frame_camera(k)
+        ras.forward(cam, means, scales, quats, opac, cols, feats)
+        g.render_fwd_pairs(cam, ras.proj, ras.sort, ras.fwd, capacity=cap, out=pairs, status=ras.status)
+        g.zero_(ras.grad_arena)
+        g.render_bwd_pairs(cam, means, scales, quats, cols, feats, ras.proj, ras.sort, ras.fwd, pairs, g_rgb, g_d,
+                           None, g_f, grads=ras.grads, workspace=ras.bwd_ws, status=ras.status)
+
+    def default(k):
+        cam = frame_camera(k)
+        ras.forward(cam, means, scales, quats, opac, cols, feats)
+        ras.backward(cam, means, scales, quats, cols, feats, g_rgb, g_d, None, g_f)
+
+    flush = _flush_buf(dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fn in (("saved_T_final_division", division), ("stored_pair_transmittance", stored),
+                     ("default_tensor_core_adjoint", default)):
+        for k in frames[:args.warmup]:
+            fn(k)
+        ms, _ = _time_frames(fn, timed, flush, stream)
+        _, per = _time_frames(fn, timed[:3], flush, stream, trace=True)
+        out[name] = {"ms_per_frame": float(np.mean(ms)),
+                     "kernel_ms_per_frame": {kk: round(v, 4) for kk, v in per.items()}}
+    ras.check_status()
+    HW = WIDTH * HEIGHT
+    bl = float(np.mean([blends[k] for k in timed]))
+    return {"workload": "slam_frame_room300k_1200x680_N64", "feature_channels": N, "blends_per_frame": bl,
+            "forms": out,
+            "saved_state_bytes": {"T_final_last_idx": HW * 8,
+                                  "stored_pair_transmittance": int(4 * bl + 8 * (HW + 1)),
+                                  "per_pixel": "8 B", "per_blended_pair": "4 B (+ 8 B per pixel of offsets)"}}
+
+
 def forms_summary(args, peaks, alu):
     """The forms of the 512-channel feature field (wide tensor-core form,
     learned decoder on both feature sets), for the bench line."""
@@ -1105,6 +1182,8 @@ def forms_summary(args, peaks, alu):
     res["decoder"] = {"prototypes": decoder_form(args, peaks, "prototypes", timing=True)}
     torch.cuda.empty_cache()
     res["decoder"]["unit"] = decoder_form(args, peaks, "unit", timing=False)
+    torch.cuda.empty_cache()
+    res["saved_state_N64"] = pair_state_form(args)
     torch.cuda.empty_cache()
     res["seconds"] = round(time.perf_counter() - t0, 1)
     return res

@@ -289,6 +289,46 @@ gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, con
                         float* d_pose, int32_t* status, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Per-pair saved state (the alternative to the saved T_final and last index
+ * that gs_render_bwd recovers the transmittance from, Sec. 3.1): the
+ * transmittance in front of every blended (pixel, Gaussian) pair, so that an
+ * adjoint reads T_i instead of dividing, T_i = T_{i+1} / (1 - alpha_i), which
+ * loses accuracy where alpha nears the 0.99 clamp. The paper has no
+ * counterpart; the calls exist to measure the two against each other
+ * (memory: 8 bytes per pixel against 4 bytes per blended pair).
+ *
+ * gs_render_fwd_pairs -- after gs_render_fwd (its last_idx and n_contrib):
+ * pair_off [H*W + 1] (int64) = the exclusive scan of n_contrib (pixels row
+ * major; pair_off[H*W] = the number of blended pairs), and pair_T[k] for k in
+ * [pair_off[q], pair_off[q + 1]) = T in front of pixel q's blended Gaussians
+ * in list order, bit for bit the forward's values. More pairs than capacity
+ * flags GS_ERR_CAPACITY (pair_T holds the first capacity). workspace: at least
+ * gs_pair_state_workspace_bytes(width, height) bytes, 256-byte aligned.
+ * gs_render_bwd_pairs -- gs_render_bwd (same arguments without inst_masks,
+ * no GS_FEAT_TENSOR_CORE) on the SIMT adjoint in 32-channel chunks, the
+ * transmittance read from pair_T (pair_off/pair_T of gs_render_fwd_pairs for
+ * the same frame) or, with pair_T NULL, recovered by division as in
+ * gs_render_bwd.
+ */
+size_t gs_pair_state_workspace_bytes(int32_t width, int32_t height);
+gs_status gs_render_fwd_pairs(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const int32_t* tile_order,
+                              const uint32_t* gids, const float* uv, const float* conic_opacity,
+                              const int32_t* last_idx, const int32_t* n_contrib, void* workspace,
+                              size_t workspace_bytes, int64_t capacity, int64_t* pair_off, float* pair_T,
+                              int32_t* status, void* stream);
+gs_status gs_render_bwd_pairs(const gs_camera* cam, int32_t P, const float* means, const float* scales,
+                              const float* quats, const float* colors, const void* feats, int32_t N,
+                              int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
+                              const int32_t* tile_ranges, const int32_t* tile_order, const uint32_t* gids,
+                              const float* uv, const float* conic_opacity, const float* depth, const float* T_final,
+                              const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
+                              const float* dL_dalpha, const float* dL_dfeat, int32_t feat_grad_mode,
+                              const int64_t* pair_off, const float* pair_T, void* workspace,
+                              size_t workspace_bytes, float* d_means, float* d_scales, float* d_quats,
+                              float* d_opacity, float* d_colors, float* d_feats, float* d_pose, int32_t* status,
+                              void* stream);
+
+/* ---------------------------------------------------------------------------
  * L1 image loss fused into compositing: the colour and depth L1 terms of the
  * mapping loss (Sec. 3.2) and the feature L1 term (Eq. 11 on the rendered
  * field),

@@ -42,7 +42,8 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
            "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero", "gs_set_lookback_wait_ns",
-           "gs_peak_probe", "gs_count_nonfinite")
+           "gs_peak_probe", "gs_count_nonfinite", "gs_pair_state_workspace_bytes", "gs_render_fwd_pairs",
+           "gs_render_bwd_pairs")
 
 
 class GsffError(RuntimeError):
@@ -175,6 +176,13 @@ def lib():
     L.gs_zero.restype = ctypes.c_int
     L.gs_peak_probe.argtypes = [_i32, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_double), _vp]
     L.gs_peak_probe.restype = ctypes.c_int
+    L.gs_pair_state_workspace_bytes.argtypes = [_i32, _i32]
+    L.gs_pair_state_workspace_bytes.restype = _sz
+    L.gs_render_fwd_pairs.argtypes = [cam_p, _i32] + [_vp] * 8 + [_sz, _i64, _vp, _vp, _vp, _vp]
+    L.gs_render_fwd_pairs.restype = ctypes.c_int
+    L.gs_render_bwd_pairs.argtypes = ([cam_p, _i32] + [_vp] * 5 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 12 +
+                                      [_i32, _vp, _vp, _vp, _sz] + [_vp] * 9)
+    L.gs_render_bwd_pairs.restype = ctypes.c_int
     L.gs_count_nonfinite.argtypes = [_i64, _vp, _vp, _vp]
     L.gs_count_nonfinite.restype = ctypes.c_int
     L.gs_set_lookback_wait_ns.argtypes = [ctypes.c_uint64]
@@ -592,6 +600,70 @@ def render_bwd_l1(cam, means, scales, quats, colors, feats, proj, sort, fwd, wei
         _ptr(g.get("means")), _ptr(g.get("scales")), _ptr(g.get("quats")), _ptr(g.get("opacity")),
         _ptr(g.get("colors")), _ptr(g["feats"]) if feat_on else None, _ptr(g["pose"]), _ptr(st), _stream(stream)),
         "gs_render_bwd_l1")
+    return g
+
+
+def render_fwd_pairs(cam, proj, sort, fwd, capacity=None, out=None, status=None, stream=None):
+    """gs_render_fwd_pairs: the per-pair saved state of the last forward: dict(pair_off [H*W+1] int64,
+    pair_T [capacity] float32 (the transmittance in front of each blended pair), n_pairs [1] int64 view)."""
+    H, W = cam.height, cam.width
+    dev = fwd["T_final"].device
+    P = proj["depth"].shape[0]
+    if capacity is None:
+        capacity = int(fwd["n_contrib"].sum().item())
+    o = out if out is not None else {}
+    if o.get("pair_off") is None or o["pair_off"].numel() != H * W + 1:
+        o["pair_off"] = torch.empty(H * W + 1, dtype=torch.int64, device=dev)
+    if o.get("pair_T") is None or o["pair_T"].numel() < capacity:
+        o["pair_T"] = torch.empty(max(1, capacity), device=dev)
+    wsb = int(lib().gs_pair_state_workspace_bytes(W, H))
+    if o.get("ws") is None or o["ws"].numel() < wsb:
+        o["ws"] = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    _check(lib().gs_render_fwd_pairs(ctypes.byref(c), P, _ptr(sort["tile_ranges"]), _ptr(sort.get("tile_order")),
+                                     _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]),
+                                     _ptr(fwd["last_idx"]), _ptr(fwd["n_contrib"]), _ptr(o["ws"]), o["ws"].numel(),
+                                     int(o["pair_T"].numel()), _ptr(o["pair_off"]), _ptr(o["pair_T"]), _ptr(st),
+                                     _stream(stream)), "gs_render_fwd_pairs")
+    o["n_pairs"] = o["pair_off"][H * W:]
+    return o
+
+
+def render_bwd_pairs(cam, means, scales, quats, colors, feats, proj, sort, fwd, pairs=None, g_rgb=None, g_depth=None,
+                     g_alpha=None, g_feat=None, flags=None, layout=GS_LAYOUT_CHW, bg=None, coupled=False, grads=None,
+                     workspace=None, status=None, stream=None):
+    """gs_render_bwd_pairs: the SIMT adjoint with the transmittance read from pairs (render_fwd_pairs of the same
+    frame) or, with pairs=None, recovered by division; gradients as render_bwd."""
+    P = means.shape[0]
+    dev = means.device
+    N = 0 if feats is None else feats.shape[1]
+    if flags is None:
+        flags = GS_FEAT_ON if N > 0 else GS_FEAT_OFF
+    feat_on = bool(flags & GS_FEAT_ON)
+    dtype = GS_BF16 if (feats is not None and feats.dtype == torch.bfloat16) else GS_F32
+    g = grads if grads is not None else dict(
+        means=torch.zeros(P, 3, device=dev), scales=torch.zeros(P, 3, device=dev),
+        quats=torch.zeros(P, 4, device=dev), opacity=torch.zeros(P, device=dev),
+        colors=torch.zeros(P, 3, device=dev), feats=torch.zeros(P, max(N, 1), device=dev)[:, :N],
+        pose=torch.zeros(6, device=dev))
+    ws = workspace if workspace is not None else torch.empty(max(render_bwd_workspace_bytes(P), 256),
+                                                             dtype=torch.uint8, device=dev)
+    bgc = (ctypes.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0)))
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    cont = lambda t: None if t is None else t.contiguous()
+    g_rgb, g_depth, g_alpha, g_feat = cont(g_rgb), cont(g_depth), cont(g_alpha), cont(g_feat)
+    _check(lib().gs_render_bwd_pairs(
+        ctypes.byref(c), P, _ptr(means), _ptr(scales), _ptr(quats), _ptr(colors), _ptr(feats) if feat_on else None,
+        N if feat_on else 0, dtype, layout, flags, ctypes.cast(bgc, _vp), _ptr(sort["tile_ranges"]),
+        _ptr(sort.get("tile_order")), _ptr(sort["gids"]), _ptr(proj["uv"]), _ptr(proj["conic_opacity"]),
+        _ptr(proj["depth"]), _ptr(fwd["T_final"]), _ptr(fwd["last_idx"]), _ptr(g_rgb), _ptr(g_depth), _ptr(g_alpha),
+        _ptr(g_feat) if feat_on else None, GS_FEAT_GRAD_COUPLED if coupled else GS_FEAT_GRAD_DECOUPLED,
+        _ptr(pairs["pair_off"]) if pairs else None, _ptr(pairs["pair_T"]) if pairs else None, _ptr(ws), ws.numel(),
+        _ptr(g.get("means")), _ptr(g.get("scales")), _ptr(g.get("quats")), _ptr(g.get("opacity")),
+        _ptr(g.get("colors")), _ptr(g["feats"]) if feat_on else None, _ptr(g["pose"]), _ptr(st), _stream(stream)),
+        "gs_render_bwd_pairs")
     return g
 
 

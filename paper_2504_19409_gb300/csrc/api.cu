@@ -36,6 +36,20 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_
                             float* d_colors, float* d_feats, const L1Bwd* l1, int P, int32_t* status,
                             cudaStream_t st);
 
+size_t pair_state_workspace_bytes(long long HW);
+gs_status launch_store_pairs(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,
+                             const uint32_t* gids, const float* uv, const float* co, const int32_t* last_idx,
+                             const int32_t* n_contrib, void* workspace, long long capacity, int64_t* pair_off,
+                             float* pair_T, int32_t* status, cudaStream_t st);
+gs_status launch_render_bwd_pairs(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
+                                  const float* uv, const float* co, const float* depth, const float* colors,
+                                  const void* feats, int N, int bf16, int hwc, const float bg[3],
+                                  const float* T_final, const int32_t* last_idx, const float* g_rgb,
+                                  const float* g_depth, const float* g_alpha, const float* g_feat, int coupled,
+                                  const long long* pair_off, const float* pair_T, float* d_uv, float* d_conic,
+                                  float* d_depth, float* d_opacity, float* d_colors, float* d_feats, int P,
+                                  int32_t* status, cudaStream_t st);
+
 // ---- tracing -----------------------------------------------------------------
 namespace {
 struct TraceState {
@@ -539,6 +553,78 @@ gs_status render_bwd_impl(const gs_camera* cam, int32_t P, const float* means, c
   return last_launch_status();
 }
 }  // namespace
+
+size_t gs_pair_state_workspace_bytes(int32_t width, int32_t height) {
+  if (width <= 0 || height <= 0) return 0;
+  return pair_state_workspace_bytes((long long)width * height);
+}
+
+gs_status gs_render_fwd_pairs(const gs_camera* cam, int32_t P, const int32_t* tile_ranges, const int32_t* tile_order,
+                              const uint32_t* gids, const float* uv, const float* conic_opacity,
+                              const int32_t* last_idx, const int32_t* n_contrib, void* workspace,
+                              size_t workspace_bytes, int64_t capacity, int64_t* pair_off, float* pair_T,
+                              int32_t* status, void* stream) {
+  GS_NVTX("gs_render_fwd_pairs");
+  if (!cam_ok(cam) || P < 0 || capacity < 0) return GS_ERR_INVALID_ARG;
+  if (!tile_ranges || !gids || !last_idx || !n_contrib || !workspace || !pair_off || (capacity > 0 && !pair_T))
+    return GS_ERR_INVALID_ARG;
+  if (P > 0 && (!uv || !conic_opacity)) return GS_ERR_INVALID_ARG;
+  if (!aligned(conic_opacity, 16) || !aligned(uv, 8) || !aligned(tile_ranges, 8) || !aligned(pair_off, 8) ||
+      !aligned(workspace, 256))
+    return GS_ERR_INVALID_ARG;
+  if (workspace_bytes < gs_pair_state_workspace_bytes(cam->width, cam->height)) return GS_ERR_INVALID_ARG;
+  return launch_store_pairs(make_cam(*cam), P, tile_ranges, tile_order, gids, uv, conic_opacity, last_idx, n_contrib,
+                            workspace, capacity, pair_off, pair_T, status, S(stream));
+}
+
+gs_status gs_render_bwd_pairs(const gs_camera* cam, int32_t P, const float* means, const float* scales,
+                              const float* quats, const float* colors, const void* feats, int32_t N,
+                              int32_t feat_dtype, int32_t layout, int32_t flags, const float* bg,
+                              const int32_t* tile_ranges, const int32_t* tile_order, const uint32_t* gids,
+                              const float* uv, const float* conic_opacity, const float* depth, const float* T_final,
+                              const int32_t* last_idx, const float* dL_drgb, const float* dL_ddepth,
+                              const float* dL_dalpha, const float* dL_dfeat, int32_t feat_grad_mode,
+                              const int64_t* pair_off, const float* pair_T, void* workspace,
+                              size_t workspace_bytes, float* d_means, float* d_scales, float* d_quats,
+                              float* d_opacity, float* d_colors, float* d_feats, float* d_pose, int32_t* status,
+                              void* stream) {
+  GS_NVTX("gs_render_bwd_pairs");
+  if (!cam_ok(cam) || P < 0) return GS_ERR_INVALID_ARG;
+  if (!tile_ranges || !gids || !T_final || !last_idx || !workspace || !d_pose) return GS_ERR_INVALID_ARG;
+  if (P > 0 && (!means || !scales || !quats || !colors || !uv || !conic_opacity || !depth)) return GS_ERR_INVALID_ARG;
+  if (pair_T && !pair_off) return GS_ERR_INVALID_ARG;
+  if (!aligned(workspace, 256) || !aligned(quats, 16) || !aligned(conic_opacity, 16) || !aligned(uv, 8) ||
+      !aligned(pair_off, 8))
+    return GS_ERR_INVALID_ARG;
+  if (workspace_bytes < gs_render_bwd_workspace_bytes(P)) return GS_ERR_INVALID_ARG;
+  if (feat_dtype != GS_F32 && feat_dtype != GS_BF16) return GS_ERR_INVALID_ARG;
+  if (layout != GS_LAYOUT_CHW && layout != GS_LAYOUT_HWC) return GS_ERR_INVALID_ARG;
+  if (feat_grad_mode != GS_FEAT_GRAD_DECOUPLED && feat_grad_mode != GS_FEAT_GRAD_COUPLED) return GS_ERR_INVALID_ARG;
+  if (flags & GS_FEAT_TENSOR_CORE) return GS_ERR_UNSUPPORTED;
+  const bool feat_on = (flags & GS_FEAT_ON) != 0;
+  int n = 0;
+  if (feat_on) {
+    if (N <= 0 || N > 4096 || (P > 0 && (!d_feats || !feats))) return GS_ERR_INVALID_ARG;
+    if (!aligned(feats, 16)) return GS_ERR_INVALID_ARG;
+    n = N;
+  }
+  const bool coupled = feat_on && feat_grad_mode == GS_FEAT_GRAD_COUPLED && dL_dfeat;
+  const float* b = bg ? bg : kBlack;
+  const CamF k = make_cam(*cam);
+  char* ws = static_cast<char*>(workspace);
+  float* w_uv = reinterpret_cast<float*>(ws);
+  float* w_conic = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256));
+  float* w_depth = reinterpret_cast<float*>(ws + align_up((size_t)P * 2 * 4, 256) + align_up((size_t)P * 3 * 4, 256));
+  if (launch_zero(workspace, gs_render_bwd_workspace_bytes(P), nullptr, 0, S(stream)) != GS_OK) return GS_ERR_CUDA;
+  gs_status st = launch_render_bwd_pairs(k, tile_ranges, tile_order, gids, uv, conic_opacity, depth, colors, feats, n,
+                                         feat_dtype == GS_BF16, layout == GS_LAYOUT_HWC, b, T_final, last_idx, dL_drgb,
+                                         dL_ddepth, dL_dalpha, feat_on ? dL_dfeat : nullptr, coupled ? 1 : 0,
+                                         reinterpret_cast<const long long*>(pair_off), pair_T, w_uv, w_conic, w_depth,
+                                         d_opacity, d_colors, d_feats, P, status, S(stream));
+  if (st != GS_OK) return st;
+  launch_project_bwd(k, P, means, scales, quats, w_uv, w_conic, w_depth, d_means, d_scales, d_quats, d_pose, S(stream));
+  return last_launch_status();
+}
 
 gs_status gs_render_bwd(const gs_camera* cam, int32_t P, const float* means, const float* scales, const float* quats,
                         const float* colors, const void* feats, int32_t N, int32_t feat_dtype, int32_t layout,

@@ -606,6 +606,11 @@ struct BwdParams {
   L1Bwd l1;  // cotangents rebuilt from the forward's L1 sign bits (tensor-core adjoint only)
   int P;     // Gaussians (bound of the checked build's id checks)
   int32_t* status;
+  // per-pair saved state (k_render_bwd<..., STORED>): pixel q's pairs are
+  // [pair_off[q], pair_off[q + 1]) of pair_T, the transmittance in front of
+  // each blended Gaussian in list order
+  const long long* pair_off;
+  const float* pair_T;
 };
 
 // Lane l ends up with the warp-wide sum of v[l] (see the file comment).
@@ -633,7 +638,9 @@ struct BwdShape {
 };
 
 // PPT pixels per thread (1 or 2); kTilePix / PPT threads per tile block.
-template <int NC, bool COUPLED, int PPT>
+// STORED: the transmittance in front of each blended Gaussian is read from the
+// per-pair saved state instead of being recovered as T_{i+1} / (1 - alpha_i).
+template <int NC, bool COUPLED, int PPT, bool STORED = false>
 __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || COUPLED) ? 2 : 3))
     k_render_bwd(const BwdParams p) {
   using S = BwdShape<NC>;
@@ -668,6 +675,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
   float Bc0[PPT], Bc1[PPT], Bc2[PPT], Bd[PPT], Sx[PPT];
   float gF[PPT][NCs], Bf[PPT][NFs];
   int last[PPT];
+  long long pt[PPT];  // STORED: the pixel's next saved pair, walking backwards
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
     const bool inside = px[q] < p.cam.W && py[q] < p.cam.H;
@@ -683,9 +691,11 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
     for (int c = 0; c < NCs; ++c) gF[q][c] = 0.f;
 #pragma unroll
     for (int c = 0; c < NFs; ++c) Bf[q][c] = 0.f;
+    pt[q] = 0;
     if (inside) {
       T[q] = p.T_final[pix];
       last[q] = p.last_idx[pix];
+      if (STORED) pt[q] = p.pair_off[pix + 1] - 1;
       if (p.g_rgb) {
         gC0[q] = p.g_rgb[pix];
         gC1[q] = p.g_rgb[HW + pix];
@@ -744,7 +754,8 @@ __global__ void __launch_bounds__(kTilePix / PPT, (PPT == 2) ? 4 : ((NC > 16 || 
         if (!(pos < last[q] && pair_alpha(cj, dx, dy, pa))) continue;
         any = true;
         const float om = 1.f - pa.alpha;
-        T[q] = __fdividef(T[q], om);
+        if (STORED) T[q] = p.pair_T[pt[q]--];
+        else T[q] = __fdividef(T[q], om);
         const float w = pa.alpha * T[q];
         float da = 0.f;
         if (geom) {
@@ -1435,6 +1446,8 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_
   BwdParams p;
   p.P = P;
   p.status = status;
+  p.pair_off = nullptr;
+  p.pair_T = nullptr;
   p.l1 = l1 ? *l1 : L1Bwd{};
   if (p.l1.on && (N > 16 || coupled)) return GS_ERR_UNSUPPORTED;
   p.cam = cam;
@@ -1476,6 +1489,62 @@ gs_status launch_render_bwd(const CamF& cam, const int32_t* ranges, const int32_
     k_render_bwd<16, true, 1><<<dim3(tiles, 1), kTilePix, 0, st>>>(p);
   } else {
     const dim3 grid(tiles, (N + 31) / 32);
+    if (coupled) k_render_bwd<32, true, 1><<<grid, kTilePix, 0, st>>>(p);
+    else k_render_bwd<32, false, 1><<<grid, kTilePix, 0, st>>>(p);
+  }
+  return last_launch_status();
+}
+
+// The SIMT adjoint in 32-channel chunks with the transmittance either
+// recovered by division (pair_T null) or read from the per-pair saved state.
+gs_status launch_render_bwd_pairs(const CamF& cam, const int32_t* ranges, const int32_t* order, const uint32_t* gids,
+                                  const float* uv, const float* co, const float* depth, const float* colors,
+                                  const void* feats, int N, int bf16, int hwc, const float bg[3],
+                                  const float* T_final, const int32_t* last_idx, const float* g_rgb,
+                                  const float* g_depth, const float* g_alpha, const float* g_feat, int coupled,
+                                  const long long* pair_off, const float* pair_T, float* d_uv, float* d_conic,
+                                  float* d_depth, float* d_opacity, float* d_colors, float* d_feats, int P,
+                                  int32_t* status, cudaStream_t st) {
+  BwdParams p;
+  p.l1 = L1Bwd{};
+  p.P = P;
+  p.status = status;
+  p.cam = cam;
+  p.ranges = reinterpret_cast<const int2*>(ranges);
+  p.order = order;
+  p.masks = nullptr;
+  p.gids = gids;
+  p.uv = reinterpret_cast<const float2*>(uv);
+  p.co = reinterpret_cast<const float4*>(co);
+  p.depth = depth;
+  p.colors = colors;
+  p.feats = feats;
+  p.N = N;
+  p.bf16 = bf16;
+  p.hwc = hwc;
+  for (int i = 0; i < 3; ++i) p.bg[i] = bg[i];
+  p.T_final = T_final;
+  p.last_idx = last_idx;
+  p.g_rgb = g_rgb;
+  p.g_depth = g_depth;
+  p.g_alpha = g_alpha;
+  p.g_feat = g_feat;
+  p.d_uv = d_uv;
+  p.d_conic = d_conic;
+  p.d_depth = d_depth;
+  p.d_opacity = d_opacity;
+  p.d_colors = d_colors;
+  p.d_feats = d_feats;
+  p.pair_off = pair_off;
+  p.pair_T = pair_T;
+  const unsigned tiles = (unsigned)(cam.tiles_x * cam.tiles_y);
+  const dim3 grid(tiles, N > 0 ? (N + 31) / 32 : 1);
+  if (pair_T) {
+    GS_TRACE("k_render_bwd_stored", st);
+    if (coupled) k_render_bwd<32, true, 1, true><<<grid, kTilePix, 0, st>>>(p);
+    else k_render_bwd<32, false, 1, true><<<grid, kTilePix, 0, st>>>(p);
+  } else {
+    GS_TRACE("k_render_bwd", st);
     if (coupled) k_render_bwd<32, true, 1><<<grid, kTilePix, 0, st>>>(p);
     else k_render_bwd<32, false, 1><<<grid, kTilePix, 0, st>>>(p);
   }
