@@ -96,27 +96,25 @@ gs_status gs_project(const gs_camera* cam, int32_t P, const float* means, const 
                      void* stream);
 
 /* ---------------------------------------------------------------------------
- * gs_bin_sort -- tile x depth keys and a stable device radix sort (Sec. 3.1:
- * "sorted by depth in a front-to-back order", per 16x16 tile).
+ * gs_bin_sort -- the per-tile depth-sorted instance lists (Sec. 3.1: the
+ * projected Gaussians are sorted front to back per 16x16 tile).
  *
  * For every Gaussian g and every tile k of its rectangle there is one
  * instance; the instances are ordered by the key (k << 32) | bits(depth_g)
  * with equal keys in ascending g (bits(depth) orders like depth, as depth > 0).
- * Computed as a stable depth sort of the Gaussians, emission of the
- * instances in that order, and a stable sort on the tile id alone.
+ * Computed per tile: the instances are counted and placed into their tiles'
+ * ranges, then each tile's (depth bits, g) pairs are sorted on their own.
  * In:  depth [P], rect [P,4], tiles_touched [P] from gs_project.
  * Out: gids [capacity] (u32), first I entries valid; keys [capacity] (u64,
  *      may be NULL) = the sorted keys; tile_ranges [num_tiles,2] = [start,
  *      end) into gids, (0,0) if empty; n_instances (device int64) = I.
  * If I > capacity, GS_ERR_CAPACITY is flagged in *status and the lists are
- * truncated (contents unspecified). workspace must hold
+ * truncated: tiles that start past the capacity get (0, 0) and the tile
+ * across it a shortened range over some of its instances (which ones is
+ * unspecified); every range covers written ids < P only. workspace must hold
  * gs_bin_sort_workspace_bytes(P, capacity, num_tiles) bytes (0 is returned
- * for sizes out of range); the caller need not clear it. Each radix pass
- * waits for earlier chunks' digit counts with a bounded wait: a wait longer
- * than the bound (gs_set_lookback_wait_ns, 1 s by default) flags
- * GS_ERR_TIMEOUT; gids and keys are then unspecified but every tile range
- * is (0, 0), so the render calls read no list entry, and every id the sort's
- * own later kernels read is checked against P.
+ * for sizes out of range); the caller need not clear it. The sort has no
+ * wait on other blocks.
  */
 size_t gs_bin_sort_workspace_bytes(int32_t P, int64_t capacity, int32_t num_tiles);
 gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const int32_t* rect,
@@ -129,14 +127,6 @@ gs_status gs_bin_sort(const gs_camera* cam, int32_t P, const float* depth, const
  * 4-byte aligned): the scan of an output or gradient buffer for non-finite
  * values. The paper has no counterpart. */
 gs_status gs_count_nonfinite(int64_t n, const float* x, uint64_t* count, void* stream);
-
-/* gs_set_lookback_wait_ns -- the bound, in nanoseconds of the GPU's global
- * timer, of every radix pass's wait for earlier chunks (process-wide, read
- * when a sort is enqueued; default 1e9). 0 makes every chunk after the first
- * give up before its look-back, which takes the timeout path of gs_bin_sort
- * deterministically (for testing the failure handling); any other value only
- * changes how long a stalled pass waits. The paper has no counterpart. */
-gs_status gs_set_lookback_wait_ns(uint64_t ns);
 
 /* ---------------------------------------------------------------------------
  * gs_bin_sort_static -- gs_bin_sort for callers that cannot allocate device
@@ -152,9 +142,8 @@ gs_status gs_set_lookback_wait_ns(uint64_t ns);
  * caller workspace. It calls no allocator. Every device that loads the
  * library holds that array until the process exits.
  * Limit: gs_bin_sort_workspace_bytes(P, capacity, num_tiles) must not exceed
- * GS_BIN_SORT_STATIC_SCRATCH_BYTES (about 1.96 million instances of capacity
- * with 300,000 Gaussians and up to 65,536 tiles: 14 bytes per instance plus
- * 20 per Gaussian);
+ * GS_BIN_SORT_STATIC_SCRATCH_BYTES (about 2.08 million instances of capacity
+ * with up to 65,536 tiles: 16 bytes per instance plus 4 per tile, whatever P);
  * larger sizes return GS_ERR_INVALID_ARG and launch nothing.
  * keys may be NULL, as for gs_bin_sort.
  * The first call on a device looks up the array's device address with that

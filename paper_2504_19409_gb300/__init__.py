@@ -41,7 +41,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_adam_step", "gs_decoder_fwd_tc", "gs_visibility_iou", "gs_edge_mask", "gs_tracking_loss_grad",
            "gs_pose_update", "gs_semantic_ce_grad", "gs_argmax_labels", "gs_label_probs", "gs_decoder_labels_tc",
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
-           "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero", "gs_set_lookback_wait_ns",
+           "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero",
            "gs_peak_probe", "gs_count_nonfinite", "gs_pair_state_workspace_bytes", "gs_render_fwd_pairs",
            "gs_render_bwd_pairs")
 
@@ -102,11 +102,6 @@ def count_nonfinite(tensors, stream=None):
         _check(lib().gs_count_nonfinite(t.numel(), _ptr(t), _vp(out.data_ptr() + 8 * i), _stream(stream)),
                "gs_count_nonfinite")
     return out[:len(tensors)]
-
-
-def set_lookback_wait_ns(ns: int) -> None:
-    """gs_set_lookback_wait_ns: bound of the sort's look-back waits (0 takes the timeout path at once)."""
-    _check(lib().gs_set_lookback_wait_ns(int(ns)), "gs_set_lookback_wait_ns")
 
 
 PROBE_KINDS = ("fp32_fma", "fp32_fma2", "ex2", "mma_sync_bf16")
@@ -185,8 +180,6 @@ def lib():
     L.gs_render_bwd_pairs.restype = ctypes.c_int
     L.gs_count_nonfinite.argtypes = [_i64, _vp, _vp, _vp]
     L.gs_count_nonfinite.restype = ctypes.c_int
-    L.gs_set_lookback_wait_ns.argtypes = [ctypes.c_uint64]
-    L.gs_set_lookback_wait_ns.restype = ctypes.c_int
     L.gs_tile_order.argtypes = [_i32, _vp, _vp, _vp]
     L.gs_tile_order.restype = ctypes.c_int
     L.gs_render_fwd.argtypes = ([cam_p, _i32] + [_vp] * 9 + [_i32, _i32, _i32, _i32, _vp] + [_vp] * 10)

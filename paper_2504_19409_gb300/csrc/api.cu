@@ -386,11 +386,6 @@ gs_status gs_count_nonfinite(int64_t n, const float* x, uint64_t* count, void* s
   return last_launch_status();
 }
 
-gs_status gs_set_lookback_wait_ns(uint64_t ns) {
-  set_lookback_wait_ns((unsigned long long)ns);
-  return GS_OK;
-}
-
 gs_status gs_zero(void* ptr, size_t bytes, void* stream) {
   GS_NVTX("gs_zero");
   if (bytes == 0) return GS_OK;

@@ -1,513 +1,380 @@
 // Tile x depth binning and sorting (Sec. 3.1: projected Gaussians are sorted
 // front-to-back per 16x16 tile).
 //
-// The result equals a stable sort of all (tile, Gaussian) instances by the
-// 64-bit key (tile << 32 | depth bits) with ties in ascending Gaussian id,
-// but it is computed in two much smaller stable sorts:
-//   1. the P Gaussians by depth (32-bit keys, 4 passes over P pairs);
-//      culled Gaussians get the largest key;
-//   2. instances are emitted in that depth order (an exclusive scan of the
-//      touched counts taken in sorted order, then a load-balanced expansion
-//      of each 256-Gaussian chunk), each carrying its tile id;
-//   3. the instances are sorted stably by tile id alone (ceil(bits/8) passes,
-//      2 for up to 65,536 tiles), which keeps the depth order inside a tile.
-// Every kernel reads its item count from device memory, so one frame is
-// enqueued without a host round trip (grids are sized from P and the
-// caller's capacity; idle blocks exit).
-//
-// One LSD pass over (u32 key, u32 value) pairs is a single kernel in the
-// one-sweep style (a decoupled look-back across chunks):
-//   - the digit counts of every pass are accumulated up front by the kernel
-//     that writes the keys (k_depth_keys for the depth passes, k_emit for the
-//     tile passes), so a pass knows where each digit starts globally;
-//   - k_os_scatter: a block takes the next chunk of 2048 items by an atomic
-//     ticket (chunks start in order), counts its digits, publishes the counts,
-//     and sums its predecessors' counts per digit by walking back until a
-//     chunk that has published its inclusive prefix; then scatters stably
-//     (each warp owns 256 consecutive items and ranks equal digits with
-//     __match_any_sync in index order). A block only waits on chunks with
-//     earlier tickets, which are already running; every wait is bounded and
-//     a timeout flags GS_ERR_TIMEOUT instead of hanging. After a timeout the
-//     pass's output may have unwritten slots: the kernels after it treat ids
-//     >= P as absent and the tile ranges stay empty, so nothing downstream
-//     reads through a stale id.
-// The look-back words and the counters are cleared by one zeroing kernel per
-// frame.
-
-#include <atomic>
+// The result equals a sort of all (tile, Gaussian) instances by the 64-bit key
+// (tile << 32 | depth bits) with ties in ascending Gaussian id. It is computed
+// per tile, with no global sort:
+//   1. k_bin_count: every instance adds one to its tile's count; the last
+//      block to finish turns the counts into the tile ranges (an exclusive
+//      scan), the instance total I and the capacity check;
+//   2. k_bin_scatter: every instance takes a free slot of its tile (an atomic
+//      count-down of the tile's count) and writes (depth bits << 32 | g) there;
+//      the order of the slots inside a tile is arbitrary;
+//   3. k_bin_tile_sort: one block per tile sorts the tile's keys ascending.
+//      (depth bits, g) is unique inside a tile, so the sorted order, and with
+//      it the result, does not depend on the slot order of step 2. Lists of up
+//      to 2048 keys are sorted by a bitonic network held in registers
+//      (partners less than 32 apart through warp shuffles, 32..255 apart
+//      through shared memory, further apart inside a thread); longer lists
+//      are cut into 2048-key runs sorted that way and then merged pairwise in
+//      global memory (merge path) until one run remains.
+// Steps 1 and 2 share each block's 512 Gaussians' instances evenly over its
+// threads (a block scan of the tile counts, then each thread finds its
+// instance's Gaussian by a binary search over the scan in shared memory). The
+// sort has no wait on other blocks. Every kernel reads its item counts from device memory, so one frame
+// is enqueued without a host round trip.
 
 #include "gsff_internal.cuh"
 
 namespace gsff {
 namespace {
 
-constexpr int kScanChunk = 256;   // Gaussians per chunk of the touched-count scan / emission
-constexpr int kEmitThreads = 1024;  // threads sharing a chunk's instances in k_emit
-constexpr int kDkThreads = 1024;    // threads of k_depth_keys (kRsChunk keys per block)
-constexpr int kRsThreads = 256;
-constexpr int kRsItems = 8;       // keys per thread
-constexpr int kRsChunk = kRsThreads * kRsItems;  // 2048 keys per block
-static_assert(kRsChunk % kDkThreads == 0, "k_depth_keys covers a chunk in whole rounds of its threads");
-constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRadix = 256;
+constexpr int kBinThreads = 512;    // threads of steps 1 and 2 (one Gaussian each)
+constexpr int kTsThreads = 256;     // threads of a tile-sort block
+constexpr int kTsMaxE = 8;          // keys per thread of the register sort
+constexpr int kTsRun = kTsThreads * kTsMaxE;  // 2048: the longest list sorted in one piece
+constexpr unsigned long long kPadKey = ~0ull;  // sorts after every real key (depth bits < 0x7f800000)
+// Each tile's counter sits alone in a 128-byte line: a frame's ~700k counter
+// atomics on counters packed 32 to a line serialise in the L2 line by line.
+constexpr int kCntStride = 32;
 
-struct SortCtrl {
-  long long n_total;    // I (may exceed capacity)
-  long long n_eff;      // min(I, capacity)
-  long long n_gauss;    // P
+struct BinCtrl {
+  unsigned int done;      // blocks of step 1 that have finished counting
+  unsigned int pad;
+  long long n_total;      // I
 };
 
-constexpr int kDepthPasses = 4;
-constexpr int kMaxTilePasses = 3;  // tile ids < 2^24
-constexpr int kMaxPasses = kDepthPasses + kMaxTilePasses;
-
-// Per-frame one-sweep state (cleared by the zeroing kernel before the first
-// kernel of the sort).
-struct OsCtrl {
-  uint32_t hist[kMaxPasses][kRadix];  // digit counts of each pass over all items
-  uint32_t ticket[kMaxPasses];        // next chunk of each pass
-  uint32_t timed_out;                 // set by a pass whose look-back gave up
+// The block's Gaussians [g0, g0 + 512) in shared memory: their exclusive
+// instance offsets, rectangles and 64-bit keys (depth bits << 32 | g).
+struct BinStage {
+  int off[kBinThreads + 1];
+  int4 rc[kBinThreads];
+  unsigned long long key[kBinThreads];
+  long long warp[kBinThreads / 32];
 };
 
-// Look-back word of (chunk, digit): state in the top two bits, count below.
-constexpr unsigned long long kLbAggregate = 1ull << 62;  // this chunk's own count
-constexpr unsigned long long kLbPrefix = 2ull << 62;     // count of this and all earlier chunks
-constexpr unsigned long long kLbCount = (1ull << 62) - 1;
-constexpr int kLbWindow = 8;  // look-back words loaded per round trip
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& total) {
-  // blockDim.x threads (a multiple of 32, <= 1024); returns the exclusive prefix of v.
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int x = v;
+// Stages the block's Gaussians and returns its instance count. With KEYS the
+// Gaussians' depths are read for the keys.
+template <bool KEYS>
+__device__ __forceinline__ int stage_gaussians(long long g0, int P, const int* __restrict__ touched,
+                                               const int4* __restrict__ rect, const float* __restrict__ depth,
+                                               BinStage& S) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long g = g0 + threadIdx.x;
+  const int n = g < P ? max(touched[g], 0) : 0;
+  if (n > 0) {
+    S.rc[threadIdx.x] = rect[g];
+    if (KEYS) S.key[threadIdx.x] = ((unsigned long long)__float_as_uint(depth[g]) << 32) | (unsigned long long)g;
+  }
+  int x = n;
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane >= off) x += y;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) S.warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = lane < kBinThreads / 32 ? S.warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kBinThreads / 32) S.warp[lane] = w;
+  }
+  __syncthreads();
+  const int ex = (wid > 0 ? (int)S.warp[wid - 1] : 0) + x - n;
+  S.off[threadIdx.x] = ex;
+  if (threadIdx.x == kBinThreads - 1) S.off[kBinThreads] = ex + n;
+  __syncthreads();
+  return S.off[kBinThreads];
+}
+
+// Calls f(tile, Gaussian slot k) for every instance of the staged Gaussians,
+// instance i by thread i mod 512; k is the last slot with off[k] <= i (slots
+// without instances share the next slot's offset and lose to it).
+template <class F>
+__device__ __forceinline__ void for_each_instance(const BinStage& S, int total, int tiles_x, int num_tiles, F&& f) {
+  for (int i = threadIdx.x; i < total; i += kBinThreads) {
+    int k = 0;
+#pragma unroll
+    for (int step = kBinThreads / 2; step > 0; step >>= 1)
+      if (S.off[k + step] <= i) k += step;
+    const int4 rc = S.rc[k];
+    const int li = i - S.off[k];
+    const int rw = max(rc.z - rc.x, 1);
+    const int t = (rc.y + li / rw) * tiles_x + rc.x + li % rw;
+    if ((unsigned)t < (unsigned)num_tiles) f(t, k);
+  }
+}
+
+// ---- step 1: counts, then the ranges (last block) ---------------------------------
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(int P, const int* __restrict__ touched,
+                                                           const int4* __restrict__ rect, int tiles_x, int num_tiles,
+                                                           long long capacity, unsigned int* __restrict__ cnt,
+                                                           BinCtrl* __restrict__ ctrl, int2* __restrict__ ranges,
+                                                           long long* __restrict__ n_out, int32_t* __restrict__ status) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ BinStage S;
+  __shared__ long long s_warp[32];
+  __shared__ bool s_last;
+  const int total = stage_gaussians<false>((long long)blockIdx.x * kBinThreads, P, touched, rect, nullptr, S);
+  for_each_instance(S, total, tiles_x, num_tiles, [&](int t, int) { atomicAdd(&cnt[(size_t)t * kCntStride], 1u); });
+  // the last block to get here sees every block's counts
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // each thread a contiguous run of tiles: its sum, a block scan, then the ranges
+  const int per = (num_tiles + kBinThreads - 1) / kBinThreads;
+  const int t0 = min((int)threadIdx.x * per, num_tiles), t1 = min(t0 + per, num_tiles);
+  long long sum = 0;
+  for (int t = t0; t < t1; t += 8) {
+    unsigned int c[8];  // eight loads in flight at a time
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = t + u < t1 ? __ldcg(cnt + (size_t)(t + u) * kCntStride) : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sum += c[u];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
   if (lane == 31) s_warp[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    int w = lane < nw ? s_warp[lane] : 0;
+    long long w = lane < kBinThreads / 32 ? s_warp[lane] : 0;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, off);
-      if (lane >= off) w += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    if (lane < nw) s_warp[lane] = w;
+    s_warp[lane] = w;
   }
   __syncthreads();
-  total = s_warp[nw - 1];
-  const int before = wid > 0 ? s_warp[wid - 1] : 0;
-  __syncthreads();
-  return before + x - v;
-}
-
-// ---- step 1: depth keys ------------------------------------------------------
-// One block per kRsChunk Gaussians. Culled Gaussians get the largest key. The
-// block also adds its digit counts for the four depth passes to the frame's
-// histograms (culled keys are 0xFFFFFFFF: digit 255 in every pass).
-__global__ void __launch_bounds__(kDkThreads) k_depth_keys(int P, const float* __restrict__ depth,
-                                                           const int* __restrict__ touched, uint32_t* __restrict__ dk,
-                                                           uint32_t* __restrict__ dv, SortCtrl* __restrict__ ctrl,
-                                                           OsCtrl* __restrict__ os) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ uint32_t s_h[kDepthPasses][kRadix];
-  __shared__ uint32_t s_cull;
-  for (int i = threadIdx.x; i < kDepthPasses * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
-  if (threadIdx.x == 0) s_cull = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->n_gauss = P;
-  __syncthreads();
-  const int base = blockIdx.x * kRsChunk;
-  uint32_t ncull = 0;
+  long long run = (wid > 0 ? s_warp[wid - 1] : 0) + x - sum;
+  for (int t = t0; t < t1; t += 8) {
+    unsigned int c[8];
 #pragma unroll
-  for (int r = 0; r < kRsChunk / kDkThreads; ++r) {
-    const int g = base + r * kDkThreads + threadIdx.x;
-    bool culled = false;
-    if (g < P) {
-      const bool vis = touched[g] > 0;
-      const uint32_t key = vis ? __float_as_uint(depth[g]) : 0xFFFFFFFFu;
-      dk[g] = key;
-      dv[g] = (uint32_t)g;
-      if (vis) {
+    for (int u = 0; u < 8; ++u) c[u] = t + u < t1 ? __ldcg(cnt + (size_t)(t + u) * kCntStride) : 0u;
 #pragma unroll
-        for (int p = 0; p < kDepthPasses; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & (kRadix - 1)], 1u);
-      }
-      culled = !vis;
-    }
-    ncull += __popc(__ballot_sync(0xffffffffu, culled));
-  }
-  if ((threadIdx.x & 31) == 0 && ncull) atomicAdd(&s_cull, ncull);
-  __syncthreads();
-  const int d = threadIdx.x;
-  if (d < kRadix) {
-#pragma unroll
-    for (int p = 0; p < kDepthPasses; ++p) {
-      const uint32_t v = s_h[p][d] + (d == kRadix - 1 ? s_cull : 0u);
-      if (v) atomicAdd(&os->hist[p][d], v);
+    for (int u = 0; u < 8; ++u) {
+      // empty tiles and tiles past the capacity keep (0, 0); a tile across it is cut
+      if (c[u] > 0 && run < capacity) ranges[t + u] = make_int2((int)run, (int)min(run + (long long)c[u], capacity));
+      run += c[u];
     }
   }
-}
-
-// ---- step 2: scan of touched counts in depth order, emission -------------------
-__global__ void __launch_bounds__(256) k_scan_partials(int P, const uint32_t* __restrict__ order,
-                                                       const int* __restrict__ touched,
-                                                       long long* __restrict__ partial) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ int s_warp[32];
-  const int r = blockIdx.x * kScanChunk + threadIdx.x;
-  // ids >= P can only come from a depth pass whose look-back timed out (its
-  // output slots are then not all written): they count as culled
-  const uint32_t g = r < P ? order[r] : 0xFFFFFFFFu;
-  const int v = g < (uint32_t)P ? touched[g] : 0;
-  int total;
-  block_exclusive_scan(v, s_warp, total);
-  if (threadIdx.x == 0) partial[blockIdx.x] = total;
-}
-
-// Single block: exclusive scan of the chunk sums (in place), I, capacity check.
-__global__ void __launch_bounds__(1024) k_scan_top(int nchunks, long long* __restrict__ partial, long long capacity,
-                                                   SortCtrl* __restrict__ ctrl, long long* __restrict__ n_out,
-                                                   int32_t* __restrict__ status) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ long long s_carry;
-  __shared__ long long s_warp[32];
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = 0; base < nchunks; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const long long v = i < nchunks ? partial[i] : 0;
-    long long x = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, x, off);
-      if (lane >= off) x += y;
-    }
-    if (lane == 31) s_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      long long w = s_warp[lane];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, w, off);
-        if (lane >= off) w += y;
-      }
-      s_warp[lane] = w;
-    }
-    __syncthreads();
-    const long long before = (wid > 0 ? s_warp[wid - 1] : 0) + s_carry;
-    if (i < nchunks) partial[i] = before + x - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_carry = before + x;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const long long I = s_carry;
+  if (threadIdx.x == kBinThreads - 1) {
+    const long long I = run;
     ctrl->n_total = I;
-    ctrl->n_eff = I < capacity ? I : capacity;
     if (n_out) *n_out = I;
     if (I > capacity) flag_status(status, GS_ERR_CAPACITY);
   }
 }
 
-// Each block: 256 consecutive depth-ordered Gaussians (one per thread of the
-// first eight warps). The block's instances [0, total) are spread evenly over
-// all 1024 of its threads (culled Gaussians sort last, so only a few chunks
-// hold instances and each needs many threads); instance
-// i belongs to the Gaussian k with off[k] <= i < off[k+1] (binary search in
-// shared memory) and is tile (i - off[k]) of its rectangle, row-major.
-// Writes are contiguous.
-__global__ void __launch_bounds__(kEmitThreads) k_emit(int P, const uint32_t* __restrict__ order,
-                                              const int* __restrict__ touched, const int4* __restrict__ rect,
-                                              const long long* __restrict__ partial, int tiles_x, long long capacity,
-                                              int npass, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals,
-                                              OsCtrl* __restrict__ os) {
+// ---- step 2: the keys into their tiles' slots -------------------------------------
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(int P, const int* __restrict__ touched,
+                                                             const int4* __restrict__ rect,
+                                                             const float* __restrict__ depth, int tiles_x,
+                                                             int num_tiles, const int2* __restrict__ ranges,
+                                                             unsigned int* __restrict__ cnt,
+                                                             unsigned long long* __restrict__ keys) {
   pdl_wait();
   pdl_trigger();
-  __shared__ uint32_t s_th[kMaxTilePasses][kRadix];  // digit counts of the written tile keys
-  __shared__ int s_off[kScanChunk + 1];
-  __shared__ uint32_t s_g[kScanChunk];
-  __shared__ int4 s_rc[kScanChunk];
-  __shared__ int s_warp[32];
-  const int r = blockIdx.x * kScanChunk + threadIdx.x;
-  uint32_t g = 0;
-  int n = 0;
-  if (threadIdx.x < kScanChunk && r < P) {
-    g = order[r];
-    n = g < (uint32_t)P ? touched[g] : 0;  // as in k_scan_partials
-  }
-  for (int i = threadIdx.x; i < kMaxTilePasses * kRadix; i += blockDim.x) (&s_th[0][0])[i] = 0;
-  if (threadIdx.x < kScanChunk) {
-    s_g[threadIdx.x] = g;
-    if (n > 0) s_rc[threadIdx.x] = rect[g];
-  }
-  int total;
-  const int ex = block_exclusive_scan(n, s_warp, total);  // threads past the chunk add 0
-  if (threadIdx.x < kScanChunk) s_off[threadIdx.x] = ex;
-  if (threadIdx.x == 0) s_off[kScanChunk] = total;
-  __syncthreads();
-  const long long base = partial[blockIdx.x];
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    int lo = 0, hi = kScanChunk - 1;  // largest k with s_off[k] <= i
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    const int4 rc = s_rc[lo];
-    const int li = i - s_off[lo];
-    const int rw = rc.z - rc.x;
-    const int ty = rc.y + li / rw, tx = rc.x + li % rw;
-    const long long o = base + i;
-    if (o < capacity) {
-      const uint32_t t = (uint32_t)(ty * tiles_x + tx);
-      tkeys[o] = t;
-      vals[o] = s_g[lo];
-      for (int p = 0; p < npass; ++p) atomicAdd(&s_th[p][(t >> (8 * p)) & (kRadix - 1)], 1u);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < kRadix)
-    for (int p = 0; p < npass; ++p) {
-      const uint32_t v = s_th[p][threadIdx.x];
-      if (v) atomicAdd(&os->hist[kDepthPasses + p][threadIdx.x], v);
-    }
+  __shared__ BinStage S;
+  const int total = stage_gaussians<true>((long long)blockIdx.x * kBinThreads, P, touched, rect, depth, S);
+  for_each_instance(S, total, tiles_x, num_tiles, [&](int t, int k) {
+    const int2 r = ranges[t];
+    const int slot = (int)atomicSub(&cnt[(size_t)t * kCntStride], 1u) - 1;
+    if (slot < r.y - r.x) keys[r.x + slot] = S.key[k];
+  });
 }
 
-// ---- one LSD radix pass over (u32 key, u32 value) ------------------------------
-// The count of items is *n (device); each block owns kRsChunk consecutive
-// items; warp w of a block owns items [w*256, (w+1)*256) of the chunk, in 8
-// rounds of 32 consecutive items.
-__device__ __forceinline__ void rs_load_and_count(const uint32_t* __restrict__ keys_in, long long n, int shift,
-                                                  long long base, uint32_t (&k)[kRsItems], int (&d)[kRsItems],
-                                                  uint32_t (*s_hist)[kRadix]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kRsWarps * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
-  __syncthreads();
+// ---- step 3: per-tile sort --------------------------------------------------------
+__device__ __forceinline__ unsigned long long kmin(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+__device__ __forceinline__ unsigned long long kmax(unsigned long long a, unsigned long long b) { return a < b ? b : a; }
+
+// One compare-exchange stage between the thread's own elements e and e + JE
+// (partners 256 JE apart).
+template <int E, int JE>
+__device__ __forceinline__ void stage_in_thread(unsigned long long (&r)[E], int k) {
 #pragma unroll
-  for (int r = 0; r < kRsItems; ++r) {
-    const long long idx = base + wid * (kRsItems * 32) + r * 32 + lane;
-    const bool valid = idx < n;
-    k[r] = valid ? keys_in[idx] : 0u;
-    d[r] = valid ? (int)((k[r] >> shift) & (kRadix - 1)) : kRadix;
+  for (int e = 0; e < E; ++e) {
+    if (e & JE) continue;
+    const bool asc = (((e * kTsThreads + (int)threadIdx.x) & k) == 0);
+    const unsigned long long a = r[e], b = r[e + JE];
+    r[e] = asc ? kmin(a, b) : kmax(a, b);
+    r[e + JE] = asc ? kmax(a, b) : kmin(a, b);
   }
-#pragma unroll
-  for (int r = 0; r < kRsItems; ++r) {
-    const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
-    if (lane == __ffs(peers) - 1 && d[r] < kRadix) s_hist[wid][d[r]] += __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
 }
 
-// One pass: see the file comment. `hist` = this pass's digit counts over all
-// items, `ticket` its chunk counter, `lb` its look-back words [chunks][256].
-__global__ void __launch_bounds__(kRsThreads) k_os_scatter(const uint32_t* __restrict__ keys_in,
-                                                           const uint32_t* __restrict__ vals_in,
-                                                           uint32_t* __restrict__ keys_out,
-                                                           uint32_t* __restrict__ vals_out,
-                                                           const long long* __restrict__ n_ptr, int shift,
-                                                           const uint32_t* __restrict__ hist, uint32_t* ticket,
-                                                           unsigned long long* lb, uint32_t* timed_out,
-                                                           unsigned long long wait_ns, int32_t* __restrict__ status) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ uint32_t s_hist[kRsWarps][kRadix];
-  __shared__ int s_warp[32];
-  __shared__ uint32_t s_chunk;
-  if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const long long c = s_chunk;
-  const long long n = *n_ptr;
-  const long long base = c * kRsChunk;
-  if (base >= n) return;
-  uint32_t k[kRsItems];
-  int d[kRsItems];
-  rs_load_and_count(keys_in, n, shift, base, k, d, s_hist);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t v[kRsItems];  // values loaded before the look-back, so their latency overlaps it
+// Bitonic sort, ascending, of the block's 256 E keys: thread t holds element
+// e * 256 + t in r[e]. For a stage (k, j), element i meets partner i ^ j and
+// keeps the smaller key if (i & j) == 0 equals (i & k) == 0, else the larger.
+// s: shared scratch of 256 E keys. UNROLL unrolls the stage loops (for
+// E <= 2; a fully unrolled network of E = 8 needs over 200 registers).
+template <int E, bool UNROLL>
+__device__ __forceinline__ void bitonic_regs(unsigned long long (&r)[E], unsigned long long* s) {
+  constexpr int LOG_M = 8 + (E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : 3);
+  const int t = threadIdx.x;
+#pragma unroll(UNROLL ? LOG_M : 1)
+  for (int lk = 1; lk <= LOG_M; ++lk) {
+    const int k = 1 << lk;
+#pragma unroll(UNROLL ? LOG_M : 1)
+    for (int lj = lk - 1; lj >= 0; --lj) {
+      const int j = 1 << lj;
+      if (j >= kTsThreads) {
+        if (E >= 2 && j == kTsThreads) stage_in_thread<E, 1>(r, k);
+        else if (E >= 4 && j == 2 * kTsThreads) stage_in_thread<E, (E >= 4 ? 2 : 1)>(r, k);
+        else if (E >= 8) stage_in_thread<E, (E >= 8 ? 4 : 1)>(r, k);
+      } else if (j >= 32) {
+        __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kRsItems; ++r) {
-    const long long idx = base + wid * (kRsItems * 32) + r * 32 + lane;
-    v[r] = idx < n ? vals_in[idx] : 0u;
-  }
-  const int dg = threadIdx.x;
-  uint32_t tot = 0;
+        for (int e = 0; e < E; ++e) s[e * kTsThreads + t] = r[e];
+        __syncthreads();
 #pragma unroll
-  for (int w = 0; w < kRsWarps; ++w) tot += s_hist[w][dg];
-  unsigned long long* mine = lb + c * kRadix + dg;
-  lb_store(mine, (c == 0 ? kLbPrefix : kLbAggregate) | tot);
-  // where digit dg starts in the output: exclusive scan of the digit counts
-  int all;
-  const uint32_t start = (uint32_t)block_exclusive_scan((int)hist[dg], s_warp, all);
-  unsigned long long before = 0;  // items of digit dg in chunks 0..c-1
-  if (c > 0 && wait_ns == 0) {
-    // a bound of 0 gives up before the first look-back (the timeout path,
-    // taken deterministically)
-    flag_status(status, GS_ERR_TIMEOUT);
-    *timed_out = 1u;
-    lb_store(mine, kLbPrefix | tot);
-  } else if (c > 0) {
-    // Walk back kLbWindow chunks per round trip: the words of chunks
-    // j, j-1, .. are loaded together and consumed newest first until a
-    // prefix; a chunk that has published nothing yet restarts the window
-    // at that chunk.
-    const unsigned long long t0 = globaltimer_ns();
-    long long j = c - 1;
-    while (true) {
-      unsigned long long w[kLbWindow];
+        for (int e = 0; e < E; ++e) {
+          const unsigned long long o = s[e * kTsThreads + (t ^ j)];
+          const int i = e * kTsThreads + t;
+          r[e] = (((i & j) == 0) == ((i & k) == 0)) ? kmin(r[e], o) : kmax(r[e], o);
+        }
+      } else {
 #pragma unroll
-      for (int e = 0; e < kLbWindow; ++e) w[e] = j - e >= 0 ? lb_load(lb + (j - e) * kRadix + dg) : kLbPrefix;
-      int e = 0;
-      bool done = false;
-#pragma unroll
-      for (; e < kLbWindow; ++e) {
-        const unsigned long long state = w[e] & ~kLbCount;
-        if (state == 0) break;
-        before += w[e] & kLbCount;
-        if (state == kLbPrefix) {
-          done = true;
-          break;
+        for (int e = 0; e < E; ++e) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, r[e], j);
+          const int i = e * kTsThreads + t;
+          r[e] = (((i & j) == 0) == ((i & k) == 0)) ? kmin(r[e], o) : kmax(r[e], o);
         }
       }
-      if (done) break;
-      j -= e;
-      if (e < kLbWindow && globaltimer_ns() - t0 > wait_ns) {
-        flag_status(status, GS_ERR_TIMEOUT);
-        *timed_out = 1u;
-        break;
-      }
     }
-    lb_store(mine, kLbPrefix | (before + tot));
-  }
-  {
-    uint32_t run = start + (uint32_t)before;
-#pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) {
-      const uint32_t cnt = s_hist[w][dg];
-      s_hist[w][dg] = run;
-      run += cnt;
-    }
-  }
-  __syncthreads();
-  const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-  for (int r = 0; r < kRsItems; ++r) {
-    const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
-    if (d[r] < kRadix) {
-      const uint32_t pos = s_hist[wid][d[r]] + __popc(peers & lt);
-      if ((long long)pos < n) {
-        keys_out[pos] = k[r];
-        vals_out[pos] = v[r];
-      }
-    }
-    __syncwarp();
-    if (d[r] < kRadix && lane == __ffs(peers) - 1) s_hist[wid][d[r]] += __popc(peers);
-    __syncwarp();
   }
 }
 
-// ---- step 3 output: tile ranges and the 64-bit keys ------------------------------
-// After a pass of this frame timed out (its outputs are then unspecified and
-// may hold unwritten slots), every tile range stays (0, 0) as the zeroing
-// kernel left it, so no consumer of the lists reads a stale id.
-__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ gids,
-                                                     const float* __restrict__ depth, const SortCtrl* __restrict__ ctrl,
-                                                     const OsCtrl* __restrict__ os, int P, int num_tiles,
-                                                     int2* __restrict__ ranges, unsigned long long* __restrict__ keys64) {
+// Where a tile's sorted keys go: its ids (and 64-bit keys) from list
+// position `at` on, or, for a run of a long list, back into the key buffer.
+struct TileOut {
+  uint32_t* gids;
+  unsigned long long* keys64;
+  unsigned long long tile_hi;  // tile << 32
+  long long at;
+  __device__ __forceinline__ void put(int i, unsigned long long k) const {
+    gids[at + i] = (uint32_t)k;
+    if (keys64) keys64[at + i] = tile_hi | (k >> 32);
+  }
+};
+
+// Sorts src[0, n), n <= 256 E: to o (FINAL) or back into src.
+template <int E, bool FINAL>
+__device__ __forceinline__ void sort_piece(unsigned long long* src, int n, const TileOut& o, unsigned long long* s) {
+  unsigned long long r[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * kTsThreads + threadIdx.x;
+    r[e] = i < n ? src[i] : kPadKey;
+  }
+  bitonic_regs<E, (E <= 2)>(r, s);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = e * kTsThreads + threadIdx.x;
+    if (i < n) {
+      if (FINAL) o.put(i, r[e]);
+      else src[i] = r[e];
+    }
+  }
+}
+
+// Merges the sorted runs a[0, la) and b[0, lb) into out[0, la + lb); each
+// thread writes one contiguous share, located by a binary search on its
+// first output's diagonal (keys are distinct).
+__device__ void merge_pair(const unsigned long long* a, int la, const unsigned long long* b, int lb,
+                           unsigned long long* out) {
+  const int total = la + lb;
+  const int per = (total + kTsThreads - 1) / kTsThreads;
+  const int d0 = min((int)threadIdx.x * per, total), d1 = min(d0 + per, total);
+  int lo = max(0, d0 - lb), hi = min(d0, la);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < b[d0 - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  int i = lo, j = d0 - lo;
+  for (int d = d0; d < d1; ++d) {
+    const bool take_a = j >= lb || (i < la && a[i] < b[j]);
+    out[d] = take_a ? a[i++] : b[j++];
+  }
+}
+
+__global__ void __launch_bounds__(kTsThreads, 5) k_bin_tile_sort(const int2* __restrict__ ranges,
+                                                              unsigned long long* __restrict__ keys,
+                                                              unsigned long long* __restrict__ alt,
+                                                              uint32_t* __restrict__ gids,
+                                                              unsigned long long* __restrict__ keys64) {
   pdl_wait();
   pdl_trigger();
-  if (os->timed_out) return;
-  const long long n = ctrl->n_eff;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const uint32_t t = tkeys[i];
-    if (keys64) {
-      const uint32_t g = gids[i];
-      keys64[i] = ((unsigned long long)t << 32) | (g < (uint32_t)P ? (unsigned long long)__float_as_uint(depth[g]) : 0ull);
-    }
-    if (t >= (uint32_t)num_tiles) continue;
-    if (i == 0 || tkeys[i - 1] != t) ranges[t].x = (int)i;
-    if (i == n - 1 || tkeys[i + 1] != t) ranges[t].y = (int)(i + 1);
+  __shared__ unsigned long long s[kTsRun];
+  const int t = blockIdx.x;
+  const int2 r = ranges[t];
+  const int n = r.y - r.x;
+  if (n <= 0) return;
+  const TileOut o{gids, keys64, (unsigned long long)t << 32, r.x};
+  unsigned long long* src = keys + r.x;
+  if (n <= kTsThreads) return sort_piece<1, true>(src, n, o, s);
+  if (n <= 2 * kTsThreads) return sort_piece<2, true>(src, n, o, s);
+  if (n <= 4 * kTsThreads) return sort_piece<4, true>(src, n, o, s);
+  if (n <= kTsRun) return sort_piece<kTsMaxE, true>(src, n, o, s);
+  // a long list: sorted runs, then pairwise merges (ping-pong with alt)
+  for (int c = 0; c < n; c += kTsRun) {
+    sort_piece<kTsMaxE, false>(src + c, min(kTsRun, n - c), o, s);
+    __syncthreads();  // s is reused by the next run
   }
+  unsigned long long* dst = alt + r.x;
+  for (int len = kTsRun; len < n; len *= 2) {
+    __syncthreads();  // the previous round's writes are visible to the block
+    for (int c = 0; c < n; c += 2 * len) {
+      const int la = min(len, n - c), lb = min(len, n - c - la);
+      merge_pair(src + c, la, src + c + la, lb, dst + c);
+    }
+    unsigned long long* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += kTsThreads) o.put(i, src[i]);
 }
 
 struct SortLayout {
-  size_t dk, dv, dk2, dv2, partial, os, lb, ctrl, tk_alt, tv_alt, tk, total;
-  size_t lb_bytes;   // look-back words of all passes (zeroed each frame with os)
-  int nscan, nblk_p, nblk_i, npass_t;
+  size_t keys, alt, cnt, ctrl, total;
 };
 
-int tile_bits(int num_tiles) {
-  int b = 1;
-  while ((1 << b) < num_tiles) ++b;
-  return b;
-}
-
-SortLayout sort_layout(int P, long long capacity, int num_tiles) {
+SortLayout sort_layout(long long capacity, int num_tiles) {
   SortLayout L;
-  L.nscan = (P + kScanChunk - 1) / kScanChunk;
-  if (L.nscan < 1) L.nscan = 1;
-  L.nblk_p = (P + kRsChunk - 1) / kRsChunk;
-  if (L.nblk_p < 1) L.nblk_p = 1;
-  L.nblk_i = (int)((capacity + kRsChunk - 1) / kRsChunk);
-  if (L.nblk_i < 1) L.nblk_i = 1;
-  L.npass_t = (tile_bits(num_tiles) + 7) / 8;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
     o = align_up(o + bytes, 256);
     return at;
   };
-  L.dk = take((size_t)P * 4);
-  L.dv = take((size_t)P * 4);
-  L.dk2 = take((size_t)P * 4);
-  L.dv2 = take((size_t)P * 4);
-  L.partial = take((size_t)L.nscan * 8);
-  L.ctrl = take(sizeof(SortCtrl));
-  // os and lb are adjacent: one memset clears both
-  L.lb_bytes = ((size_t)kDepthPasses * L.nblk_p + (size_t)L.npass_t * L.nblk_i) * kRadix * 8;
-  L.os = take(sizeof(OsCtrl));
-  L.lb = take(L.lb_bytes);
-  L.tk = take((size_t)capacity * 4);
-  L.tk_alt = take((size_t)capacity * 4);
-  L.tv_alt = take((size_t)capacity * 4);
+  L.keys = take((size_t)capacity * 8);
+  L.alt = take((size_t)capacity * 8);
+  // cnt and ctrl are adjacent: one span clears both
+  L.cnt = take((size_t)num_tiles * kCntStride * 4);
+  L.ctrl = take(sizeof(BinCtrl));
   L.total = o;
   return L;
 }
 
-std::atomic<unsigned long long> g_lookback_wait_ns{1000000000ull};  // 1 s
-
-void os_pass(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, const long long* n_ptr,
-             int shift, int pass, int nblk, OsCtrl* os, unsigned long long* lb, int32_t* status, cudaStream_t st) {
-  GS_TRACE("k_os_scatter", st);
-  launch_pdl(k_os_scatter, nblk, kRsThreads, 0, st, kin, vin, kout, vout, n_ptr, shift, os->hist[pass], &os->ticket[pass],
-             lb, &os->timed_out, g_lookback_wait_ns.load(std::memory_order_relaxed), status);
-}
-
 }  // namespace
 
-void set_lookback_wait_ns(unsigned long long ns) { g_lookback_wait_ns.store(ns, std::memory_order_relaxed); }
-
 size_t bin_sort_workspace_bytes(int P, long long capacity, int num_tiles) {
-  return sort_layout(P, capacity, num_tiles).total;
+  (void)P;
+  return sort_layout(capacity, num_tiles).total;
 }
 
 // Enqueues the whole binning on `st`. The workspace base must be 256-aligned.
@@ -516,72 +383,35 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
                           long long capacity, void* workspace, unsigned long long* keys64, uint32_t* gids,
                           int32_t* ranges, int64_t* n_out, int32_t* status, cudaStream_t st) {
   const int num_tiles = cam.tiles_x * cam.tiles_y;
-  const SortLayout L = sort_layout(P, capacity, num_tiles);
-  if (L.npass_t > kMaxTilePasses) return GS_ERR_INVALID_ARG;
+  const SortLayout L = sort_layout(capacity, num_tiles);
   char* ws = static_cast<char*>(workspace);
-  auto* dk = reinterpret_cast<uint32_t*>(ws + L.dk);
-  auto* dv = reinterpret_cast<uint32_t*>(ws + L.dv);
-  auto* dk2 = reinterpret_cast<uint32_t*>(ws + L.dk2);
-  auto* dv2 = reinterpret_cast<uint32_t*>(ws + L.dv2);
-  auto* partial = reinterpret_cast<long long*>(ws + L.partial);
-  auto* ctrl = reinterpret_cast<SortCtrl*>(ws + L.ctrl);
-  auto* os = reinterpret_cast<OsCtrl*>(ws + L.os);
-  auto* lb = reinterpret_cast<unsigned long long*>(ws + L.lb);
-  auto* tk = reinterpret_cast<uint32_t*>(ws + L.tk);
-  auto* tk_alt = reinterpret_cast<uint32_t*>(ws + L.tk_alt);
-  auto* tv_alt = reinterpret_cast<uint32_t*>(ws + L.tv_alt);
-  const long long* n_gauss = &ctrl->n_gauss;
-  const long long* n_inst = &ctrl->n_eff;
-  const size_t lb_pass_p = (size_t)L.nblk_p * kRadix, lb_pass_i = (size_t)L.nblk_i * kRadix;
-
-  // the tile ranges and the passes' counters and look-back words, in one
-  // kernel of the programmatic-launch chain
-  static_assert(sizeof(OsCtrl) % 4 == 0, "cleared in 4-byte words");
-  if (launch_zero(ranges, (size_t)num_tiles * 2 * sizeof(int32_t), os, (L.lb - L.os) + L.lb_bytes, st) != GS_OK)
+  auto* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
+  auto* alt = reinterpret_cast<unsigned long long*>(ws + L.alt);
+  auto* cnt = reinterpret_cast<unsigned int*>(ws + L.cnt);
+  auto* ctrl = reinterpret_cast<BinCtrl*>(ws + L.ctrl);
+  auto* rg = reinterpret_cast<int2*>(ranges);
+  const auto* rc = reinterpret_cast<const int4*>(rect);
+  static_assert(sizeof(BinCtrl) % 4 == 0, "cleared in 4-byte words");
+  // the tile ranges, the counts and the block counter, in one kernel of the
+  // programmatic-launch chain
+  if (launch_zero(ranges, (size_t)num_tiles * 2 * sizeof(int32_t), cnt, (L.ctrl - L.cnt) + sizeof(BinCtrl), st) !=
+      GS_OK)
     return GS_ERR_CUDA;
+  const long long nbl = ((long long)P + kBinThreads - 1) / kBinThreads;
+  const unsigned nb = (unsigned)(nbl > 0 ? nbl : 1);
   {
-    GS_TRACE("k_depth_keys", st);
-    launch_pdl(k_depth_keys, L.nblk_p, kDkThreads, 0, st, P, depth, touched, dk, dv, ctrl, os);
-  }
-  // 1. depth sort: 4 passes, ending in (dk, dv)
-  os_pass(dk, dv, dk2, dv2, n_gauss, 0, 0, L.nblk_p, os, lb, status, st);
-  os_pass(dk2, dv2, dk, dv, n_gauss, 8, 1, L.nblk_p, os, lb + lb_pass_p, status, st);
-  os_pass(dk, dv, dk2, dv2, n_gauss, 16, 2, L.nblk_p, os, lb + 2 * lb_pass_p, status, st);
-  os_pass(dk2, dv2, dk, dv, n_gauss, 24, 3, L.nblk_p, os, lb + 3 * lb_pass_p, status, st);
-  // 2. scan + emission in depth order
-  {
-    GS_TRACE("k_scan_partials", st);
-    launch_pdl(k_scan_partials, L.nscan, 256, 0, st, P, dv, touched, partial);
+    GS_TRACE("k_bin_count", st);
+    launch_pdl(k_bin_count, nb, kBinThreads, 0, st, P, touched, rc, cam.tiles_x, num_tiles, capacity, cnt, ctrl, rg,
+               reinterpret_cast<long long*>(n_out), status);
   }
   {
-    GS_TRACE("k_scan_top", st);
-    launch_pdl(k_scan_top, 1, 1024, 0, st, L.nscan, partial, capacity, ctrl, reinterpret_cast<long long*>(n_out), status);
-  }
-  // 3. tile sort: passes ping-pong so that the last one lands in (tk, gids)
-  const int npass = L.npass_t;
-  uint32_t* kb[2];
-  uint32_t* vb[2];
-  if (npass % 2 == 0) {
-    kb[0] = tk; vb[0] = gids; kb[1] = tk_alt; vb[1] = tv_alt;
-  } else {
-    kb[0] = tk_alt; vb[0] = tv_alt; kb[1] = tk; vb[1] = gids;
+    GS_TRACE("k_bin_scatter", st);
+    launch_pdl(k_bin_scatter, nb, kBinThreads, 0, st, P, touched, rc, depth, cam.tiles_x, num_tiles,
+               (const int2*)rg, cnt, keys);
   }
   {
-    GS_TRACE("k_emit", st);
-    launch_pdl(k_emit, L.nscan, kEmitThreads, 0, st, P, dv, touched, reinterpret_cast<const int4*>(rect), partial, cam.tiles_x,
-                                    capacity, npass, kb[0], vb[0], os);
-  }
-  unsigned long long* lb_t = lb + kDepthPasses * lb_pass_p;
-  for (int p = 0; p < npass; ++p)
-    os_pass(kb[p & 1], vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], n_inst, 8 * p, kDepthPasses + p, L.nblk_i, os,
-            lb_t + p * lb_pass_i, status, st);
-  {
-    GS_TRACE("k_tile_ranges", st);
-    int nb = (int)((capacity + 255) / 256);
-    if (nb > 8 * 152) nb = 8 * 152;  // one wave; the kernel strides over the instances
-    if (nb < 1) nb = 1;
-    launch_pdl(k_tile_ranges, nb, 256, 0, st, tk, gids, depth, ctrl, os, P, num_tiles, reinterpret_cast<int2*>(ranges),
-               keys64);
+    GS_TRACE("k_bin_tile_sort", st);
+    launch_pdl(k_bin_tile_sort, (unsigned)num_tiles, kTsThreads, 0, st, (const int2*)rg, keys, alt, gids, keys64);
   }
   return last_launch_status();
 }

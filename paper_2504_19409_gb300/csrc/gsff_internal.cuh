@@ -214,7 +214,6 @@ inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Bound of the radix passes' look-back waits in ns (binsort.cu; 0 = give up at once).
-void set_lookback_wait_ns(unsigned long long ns);
 
 // ---- launchers implemented in the .cu files ---------------------------------
 gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,

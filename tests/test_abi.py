@@ -38,10 +38,8 @@ def test_host_only_entry_points(built):
     # workspace sizing is pure host arithmetic
     a = g.bin_sort_workspace_bytes(1000, 5000, 48)
     b = g.bin_sort_workspace_bytes(1000, 50000, 48)
-    assert a > 5000 * 12 and b > a and a % 256 == 0
+    assert a >= 5000 * 16 and b > a and a % 256 == 0
     assert g.render_bwd_workspace_bytes(1000) >= 1000 * 24
-    # the look-back bound is a host-side setting read when a sort is enqueued
-    assert L.gs_set_lookback_wait_ns(10 ** 9) == g.GS_OK
 
 
 def test_invalid_arguments_rejected_synchronously(built):
