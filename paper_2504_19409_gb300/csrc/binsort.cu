@@ -4,9 +4,9 @@
 // The result equals a sort of all (tile, Gaussian) instances by the 64-bit key
 // (tile << 32 | depth bits) with ties in ascending Gaussian id. It is computed
 // per tile, with no global sort:
-//   1. k_bin_count: every instance adds one to its tile's count; the last
-//      block to finish turns the counts into the tile ranges (an exclusive
-//      scan), the instance total I and the capacity check;
+//   1. k_bin_count: every instance adds one to its tile's count; then
+//      k_bin_ranges (one block) turns the counts into the tile ranges (an
+//      exclusive scan), the instance total I and the capacity check;
 //   2. k_bin_scatter: every instance takes a free slot of its tile (an atomic
 //      count-down of the tile's count) and writes (depth bits << 32 | g) there;
 //      the order of the slots inside a tile is arbitrary;
@@ -34,15 +34,7 @@ constexpr int kTsThreads = 256;     // threads of a tile-sort block
 constexpr int kTsMaxE = 8;          // keys per thread of the register sort
 constexpr int kTsRun = kTsThreads * kTsMaxE;  // 2048: the longest list sorted in one piece
 constexpr unsigned long long kPadKey = ~0ull;  // sorts after every real key (depth bits < 0x7f800000)
-// Each tile's counter sits alone in a 128-byte line: a frame's ~700k counter
-// atomics on counters packed 32 to a line serialise in the L2 line by line.
-constexpr int kCntStride = 32;
-
-struct BinCtrl {
-  unsigned int done;      // blocks of step 1 that have finished counting
-  unsigned int pad;
-  long long n_total;      // I
-};
+constexpr int kRgThreads = 1024;    // threads of the one-block range scan
 
 // The block's Gaussians [g0, g0 + 512) in shared memory: their exclusive
 // instance offsets, rectangles and 64-bit keys (depth bits << 32 | g).
@@ -91,52 +83,64 @@ __device__ __forceinline__ int stage_gaussians(long long g0, int P, const int* _
   return S.off[kBinThreads];
 }
 
-// Calls f(tile, Gaussian slot k) for every instance of the staged Gaussians,
-// instance i by thread i mod 512; k is the last slot with off[k] <= i (slots
-// without instances share the next slot's offset and lose to it).
-template <class F>
-__device__ __forceinline__ void for_each_instance(const BinStage& S, int total, int tiles_x, int num_tiles, F&& f) {
-  for (int i = threadIdx.x; i < total; i += kBinThreads) {
-    int k = 0;
+// The tile and Gaussian slot k of the block's instance i: k is the last slot
+// with off[k] <= i (slots without instances share the next slot's offset and
+// lose to it). False for a tile outside the grid.
+__device__ __forceinline__ bool locate(const BinStage& S, int i, int tiles_x, int num_tiles, int& t, int& k) {
+  k = 0;
 #pragma unroll
-    for (int step = kBinThreads / 2; step > 0; step >>= 1)
-      if (S.off[k + step] <= i) k += step;
-    const int4 rc = S.rc[k];
-    const int li = i - S.off[k];
-    const int rw = max(rc.z - rc.x, 1);
-    const int t = (rc.y + li / rw) * tiles_x + rc.x + li % rw;
-    if ((unsigned)t < (unsigned)num_tiles) f(t, k);
-  }
+  for (int step = kBinThreads / 2; step > 0; step >>= 1)
+    if (S.off[k + step] <= i) k += step;
+  const int4 rc = S.rc[k];
+  const int li = i - S.off[k];
+  const int rw = max(rc.z - rc.x, 1);
+  t = (rc.y + li / rw) * tiles_x + rc.x + li % rw;
+  return (unsigned)t < (unsigned)num_tiles;
 }
 
-// ---- step 1: counts, then the ranges (last block) ---------------------------------
+// Instances per thread and round in steps 1 and 2: their searches and memory
+// operations are independent, so four are in flight at a time.
+constexpr int kBinIlp = 4;
+
+// ---- step 1: counts, then the ranges ---------------------------------------------
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(int P, const int* __restrict__ touched,
                                                            const int4* __restrict__ rect, int tiles_x, int num_tiles,
-                                                           long long capacity, unsigned int* __restrict__ cnt,
-                                                           BinCtrl* __restrict__ ctrl, int2* __restrict__ ranges,
-                                                           long long* __restrict__ n_out, int32_t* __restrict__ status) {
+                                                           unsigned int* __restrict__ cnt) {
   pdl_wait();
   pdl_trigger();
   __shared__ BinStage S;
-  __shared__ long long s_warp[32];
-  __shared__ bool s_last;
   const int total = stage_gaussians<false>((long long)blockIdx.x * kBinThreads, P, touched, rect, nullptr, S);
-  for_each_instance(S, total, tiles_x, num_tiles, [&](int t, int) { atomicAdd(&cnt[(size_t)t * kCntStride], 1u); });
-  // the last block to get here sees every block's counts
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->done, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // each thread a contiguous run of tiles: its sum, a block scan, then the ranges
-  const int per = (num_tiles + kBinThreads - 1) / kBinThreads;
+  for (int i0 = threadIdx.x; i0 < total; i0 += kBinIlp * kBinThreads) {
+    int t[kBinIlp], k[kBinIlp];
+    bool v[kBinIlp];
+#pragma unroll
+    for (int u = 0; u < kBinIlp; ++u) {
+      const int i = i0 + u * kBinThreads;
+      v[u] = i < total && locate(S, i, tiles_x, num_tiles, t[u], k[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kBinIlp; ++u)
+      if (v[u]) atomicAdd(&cnt[t[u]], 1u);
+  }
+}
+
+// One block: each thread a contiguous run of tiles (its sum, a block scan,
+// then the ranges); empty tiles and tiles past the capacity keep (0, 0) and a
+// tile across the capacity is cut to it.
+__global__ void __launch_bounds__(kRgThreads) k_bin_ranges(int num_tiles, long long capacity,
+                                                           const unsigned int* __restrict__ cnt,
+                                                           int2* __restrict__ ranges, long long* __restrict__ n_out,
+                                                           int32_t* __restrict__ status) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ long long s_warp[32];
+  const int per = (num_tiles + kRgThreads - 1) / kRgThreads;
   const int t0 = min((int)threadIdx.x * per, num_tiles), t1 = min(t0 + per, num_tiles);
   long long sum = 0;
   for (int t = t0; t < t1; t += 8) {
     unsigned int c[8];  // eight loads in flight at a time
 #pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] = t + u < t1 ? __ldcg(cnt + (size_t)(t + u) * kCntStride) : 0u;
+    for (int u = 0; u < 8; ++u) c[u] = t + u < t1 ? cnt[t + u] : 0u;
 #pragma unroll
     for (int u = 0; u < 8; ++u) sum += c[u];
   }
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(int P, const int* __r
   if (lane == 31) s_warp[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    long long w = lane < kBinThreads / 32 ? s_warp[lane] : 0;
+    long long w = s_warp[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const long long y = __shfl_up_sync(0xffffffffu, w, o);
@@ -163,19 +167,16 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(int P, const int* __r
   for (int t = t0; t < t1; t += 8) {
     unsigned int c[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) c[u] = t + u < t1 ? __ldcg(cnt + (size_t)(t + u) * kCntStride) : 0u;
+    for (int u = 0; u < 8; ++u) c[u] = t + u < t1 ? cnt[t + u] : 0u;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      // empty tiles and tiles past the capacity keep (0, 0); a tile across it is cut
       if (c[u] > 0 && run < capacity) ranges[t + u] = make_int2((int)run, (int)min(run + (long long)c[u], capacity));
       run += c[u];
     }
   }
-  if (threadIdx.x == kBinThreads - 1) {
-    const long long I = run;
-    ctrl->n_total = I;
-    if (n_out) *n_out = I;
-    if (I > capacity) flag_status(status, GS_ERR_CAPACITY);
+  if (threadIdx.x == kRgThreads - 1) {
+    if (n_out) *n_out = run;
+    if (run > capacity) flag_status(status, GS_ERR_CAPACITY);
   }
 }
 
@@ -190,17 +191,29 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(int P, const int* _
   pdl_trigger();
   __shared__ BinStage S;
   const int total = stage_gaussians<true>((long long)blockIdx.x * kBinThreads, P, touched, rect, depth, S);
-  for_each_instance(S, total, tiles_x, num_tiles, [&](int t, int k) {
-    const int2 r = ranges[t];
-    const int slot = (int)atomicSub(&cnt[(size_t)t * kCntStride], 1u) - 1;
-    if (slot < r.y - r.x) keys[r.x + slot] = S.key[k];
-  });
+  for (int i0 = threadIdx.x; i0 < total; i0 += kBinIlp * kBinThreads) {
+    int t[kBinIlp], k[kBinIlp];
+    bool v[kBinIlp];
+#pragma unroll
+    for (int u = 0; u < kBinIlp; ++u) {
+      const int i = i0 + u * kBinThreads;
+      v[u] = i < total && locate(S, i, tiles_x, num_tiles, t[u], k[u]);
+    }
+    int2 r[kBinIlp];
+    int slot[kBinIlp];
+#pragma unroll
+    for (int u = 0; u < kBinIlp; ++u)
+      if (v[u]) {
+        r[u] = ranges[t[u]];
+        slot[u] = (int)atomicSub(&cnt[t[u]], 1u) - 1;
+      }
+#pragma unroll
+    for (int u = 0; u < kBinIlp; ++u)
+      if (v[u] && slot[u] < r[u].y - r[u].x) keys[r[u].x + slot[u]] = S.key[k[u]];
+  }
 }
 
 // ---- step 3: per-tile sort --------------------------------------------------------
-__device__ __forceinline__ unsigned long long kmin(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
-__device__ __forceinline__ unsigned long long kmax(unsigned long long a, unsigned long long b) { return a < b ? b : a; }
-
 // One compare-exchange stage between the thread's own elements e and e + JE
 // (partners 256 JE apart).
 template <int E, int JE>
@@ -210,8 +223,9 @@ __device__ __forceinline__ void stage_in_thread(unsigned long long (&r)[E], int 
     if (e & JE) continue;
     const bool asc = (((e * kTsThreads + (int)threadIdx.x) & k) == 0);
     const unsigned long long a = r[e], b = r[e + JE];
-    r[e] = asc ? kmin(a, b) : kmax(a, b);
-    r[e + JE] = asc ? kmax(a, b) : kmin(a, b);
+    const bool swap = (b < a) == asc;
+    r[e] = swap ? b : a;
+    r[e + JE] = swap ? a : b;
   }
 }
 
@@ -243,14 +257,17 @@ __device__ __forceinline__ void bitonic_regs(unsigned long long (&r)[E], unsigne
         for (int e = 0; e < E; ++e) {
           const unsigned long long o = s[e * kTsThreads + (t ^ j)];
           const int i = e * kTsThreads + t;
-          r[e] = (((i & j) == 0) == ((i & k) == 0)) ? kmin(r[e], o) : kmax(r[e], o);
+          // keep the smaller key iff (i & j) == 0 equals (i & k) == 0
+          const bool take = (o < r[e]) == (((i & j) == 0) == ((i & k) == 0));
+          r[e] = take ? o : r[e];
         }
       } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const unsigned long long o = __shfl_xor_sync(0xffffffffu, r[e], j);
           const int i = e * kTsThreads + t;
-          r[e] = (((i & j) == 0) == ((i & k) == 0)) ? kmin(r[e], o) : kmax(r[e], o);
+          const bool take = (o < r[e]) == (((i & j) == 0) == ((i & k) == 0));
+          r[e] = take ? o : r[e];
         }
       }
     }
@@ -350,7 +367,7 @@ __global__ void __launch_bounds__(kTsThreads, 5) k_bin_tile_sort(const int2* __r
 }
 
 struct SortLayout {
-  size_t keys, alt, cnt, ctrl, total;
+  size_t keys, alt, cnt, total;
 };
 
 SortLayout sort_layout(long long capacity, int num_tiles) {
@@ -363,9 +380,7 @@ SortLayout sort_layout(long long capacity, int num_tiles) {
   };
   L.keys = take((size_t)capacity * 8);
   L.alt = take((size_t)capacity * 8);
-  // cnt and ctrl are adjacent: one span clears both
-  L.cnt = take((size_t)num_tiles * kCntStride * 4);
-  L.ctrl = take(sizeof(BinCtrl));
+  L.cnt = take((size_t)num_tiles * 4);
   L.total = o;
   return L;
 }
@@ -388,20 +403,20 @@ gs_status launch_bin_sort(const CamF& cam, int P, const float* depth, const int3
   auto* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
   auto* alt = reinterpret_cast<unsigned long long*>(ws + L.alt);
   auto* cnt = reinterpret_cast<unsigned int*>(ws + L.cnt);
-  auto* ctrl = reinterpret_cast<BinCtrl*>(ws + L.ctrl);
   auto* rg = reinterpret_cast<int2*>(ranges);
   const auto* rc = reinterpret_cast<const int4*>(rect);
-  static_assert(sizeof(BinCtrl) % 4 == 0, "cleared in 4-byte words");
-  // the tile ranges, the counts and the block counter, in one kernel of the
-  // programmatic-launch chain
-  if (launch_zero(ranges, (size_t)num_tiles * 2 * sizeof(int32_t), cnt, (L.ctrl - L.cnt) + sizeof(BinCtrl), st) !=
-      GS_OK)
+  // the tile ranges and the counts, in one kernel of the programmatic-launch chain
+  if (launch_zero(ranges, (size_t)num_tiles * 2 * sizeof(int32_t), cnt, (size_t)num_tiles * 4, st) != GS_OK)
     return GS_ERR_CUDA;
   const long long nbl = ((long long)P + kBinThreads - 1) / kBinThreads;
   const unsigned nb = (unsigned)(nbl > 0 ? nbl : 1);
   {
     GS_TRACE("k_bin_count", st);
-    launch_pdl(k_bin_count, nb, kBinThreads, 0, st, P, touched, rc, cam.tiles_x, num_tiles, capacity, cnt, ctrl, rg,
+    launch_pdl(k_bin_count, nb, kBinThreads, 0, st, P, touched, rc, cam.tiles_x, num_tiles, cnt);
+  }
+  {
+    GS_TRACE("k_bin_ranges", st);
+    launch_pdl(k_bin_ranges, 1u, kRgThreads, 0, st, num_tiles, capacity, (const unsigned int*)cnt, rg,
                reinterpret_cast<long long*>(n_out), status);
   }
   {
