@@ -134,21 +134,20 @@ def algorithmic_bytes(stats):
     T = ((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)
     rec = 8 + 16 + 12 + 4 + 4 * N
     return {
-        # the sort: depth keys (depth and count read, key and id written), four
-        # depth passes over P and two tile passes over I (key and value read
-        # and written), the depth-ordered count scan, emission (the visible
-        # Gaussians' records read, 8 B per instance written), the tile ranges
-        # (4 B per instance read, 8 B per tile written) and the tile order
-        "k_depth_keys": P * 16,
-        "k_os_scatter": 4 * P * 16 + 2 * I * 16,
-        "k_scan_partials": P * 8,
-        "k_scan_top": (P // 256) * 16,
-        "k_emit": Pv * (4 + 4 + 16) + I * 8,
-        "k_tile_ranges": I * 4 + T * 8,
+        # the sort: the count reads every Gaussian's touched count and the
+        # visible ones' rectangles and adds 4 B per instance; the range scan
+        # reads the counts and writes the ranges; the scatter reads the same
+        # plus the visible depths and writes an 8-byte key per instance; the
+        # tile sort reads the keys and writes a 4-byte id per instance; then
+        # the tile order
+        "k_bin_count": P * 4 + Pv * 16 + I * 4,
+        "k_bin_ranges": T * (4 + 8),
+        "k_bin_scatter": P * 4 + Pv * (16 + 4) + I * 8,
+        "k_bin_tile_sort": T * 8 + I * (8 + 4),
         "k_tile_order": T * 12,
-        # the per-frame clears: the instance counter, the tile ranges and the
-        # sort's counters and look-back words, the adjoint's workspace
-        "k_zero": 8 + T * 8 + 7200 + (4 * ((P + 2047) // 2048) + 2 * ((I + 2047) // 2048)) * 256 * 8 + P * 24,
+        # the per-frame clears: the instance counter, the tile ranges and
+        # counts, the adjoint's workspace
+        "k_zero": 8 + T * (8 + 4) + P * 24,
         "k_project": P * (44 + 48),
         "k_render_fwd": I * 4 + Pv * rec + HW * ((5 + N) * 4 + 12),
         "k_l1_signs": HW * (2 * (4 + N) * 4 + 8),
@@ -174,9 +173,9 @@ def algorithmic_flops(stats):
     return {"k_render_fwd": 14 * E + (11 + 2 * N) * B, "k_render_bwd": bwd, "k_render_bwd_mma": bwd}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
-# capture summarised in profiles/render_fwd_bwd_room300k_N16_full.md, keyed to
-# the source it was taken on (null once render.cu changes).
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel,
+# from one ncu capture on the bench workload, keyed to the source it was taken
+# on (null once render.cu changes).
 NCU_TRAFFIC = {"k_render_bwd_mma": (40_770_000 + 6_140, "271ad14c3006b068")}
 
 
