@@ -1069,6 +1069,41 @@ def decoder_form(args, peaks, kind, timing=True, label_query=False):
                                  "frac": HW * (16 + N) * 4 / (dk * 1e-3) / 1e9 / hbm_peak},
                          "algorithmic": "2 (16*128 + 128*512) flop per pixel; 16 + 512 floats per pixel read and "
                                         "written"}})
+        # the decoder's training evaluation alone (65536 samples of a trained
+        # pose's latent map against its 512-channel target): the two tcgen05
+        # kernels against the fp32 SIMT chain, each timed with CUDA events
+        # after warm-up and an L2 flush
+        c = train_cams[0]
+        z_map = trn.render_latents(c).contiguous()
+        tgt_map = tc.forward(c, *scene, feats_bf)["feat"].reshape(HW, N).contiguous()
+        dz_map = torch.zeros(HW, 16, device=dev)
+        S = 65536
+        tr_ms = {}
+        for name, fn in (("tensor_core", dec.train_eval_tc), ("fp32_simt", dec.train_eval)):
+            ts = []
+            for it in range(args.warmup + 5):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn(z_map, tgt_map, S, 5000 + it, 1.0 / (S * 512), dz_map=dz_map)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    ts.append(e0.elapsed_time(e1))
+            tr_ms[name] = float(np.median(ts))
+        tflop = S * 2.0 * 3 * (16 * 128 + 128 * 512) / 1e12  # forward, and the two products per layer backward
+        gbytes = S * (512 * 4 + 16 * 4 + 2 * (128 + 512) * 2 + 16 * 4) / 1e9
+        t_tc = tr_ms["tensor_core"] * 1e-3
+        out["decoder_training"] = {
+            "samples": S, "ms": tr_ms, "speedup_tensor_core": tr_ms["fp32_simt"] / tr_ms["tensor_core"],
+            "kernels": "k_decoder_train_tc (forward, loss, dH, dPRE, dz, dW1, db1, db2) + k_decoder_dw2_tc (dW2)",
+            "roofline": {"tensor": {"achieved": tflop / t_tc, "peak": peaks.get("bf16_tflops", 1900.0),
+                                    "unit": "TFLOP/s", "frac": tflop / t_tc / peaks.get("bf16_tflops", 1900.0)},
+                         "hbm": {"achieved": gbytes / t_tc, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                                 "frac": gbytes / t_tc / peaks.get("hbm_gbs", 6800.0)},
+                         "algorithmic": "6 (16*128 + 128*512) flop per sample; per sample the 512 fp32 target "
+                                        "values and 16 latents read, H and dY (bf16) written and read back, 16 "
+                                        "floats of dz added"}}
         if label_query:
             gq = torch.Generator(device=dev).manual_seed(12)
             queries = torch.randn(32, N, device=dev, generator=gq) / math.sqrt(N)

@@ -544,6 +544,27 @@ gs_status gs_decoder_train(const gs_decoder* dec, int64_t nsample, int64_t npix,
                            size_t workspace_bytes, float* dW1, float* db1, float* dW2, float* db2,
                            float* dz_map, float* loss_sum, void* stream);
 
+/* The same training evaluation on tcgen05 tensor cores, for din = 16,
+ * dh = 128, dout = 512 (GS_ERR_UNSUPPORTED otherwise), in two fused kernels:
+ * the first takes each 128-sample tile through W1, the GELU, W2, the loss
+ * and its cotangent dY, then back through W2 and the GELU to dPRE, dz and
+ * dW1 / db1 (db1 and db2 from the fp32 values); the second forms dW2 from the
+ * tiles' H and dY, which the first leaves in the workspace. z, H, dY and
+ * dPRE enter the products rounded to bf16 (unit roundoff u = 2^-8), every
+ * sum is fp32: to first order each gradient's error is bounded by u times
+ * the sum of |terms| of every rounded operand it passes through (the
+ * tensor-core training test states the bound per gradient). Same sampling
+ * rule, loss and accumulation as gs_decoder_train; z_map, dz_map, dW1, db1
+ * and dW2 16-byte aligned (vector atomics), workspace 256-byte aligned with
+ * gs_decoder_train_tc_workspace_bytes(nsample) bytes (1.25 KB per sample).
+ * Device errors (a bounded wait that gave up) are OR-ed into *status (may be
+ * NULL). */
+size_t gs_decoder_train_tc_workspace_bytes(int64_t nsample);
+gs_status gs_decoder_train_tc(const gs_decoder* dec, int64_t nsample, int64_t npix, uint64_t seed,
+                              const float* z_map, const float* target, float loss_scale, void* workspace,
+                              size_t workspace_bytes, float* dW1, float* db1, float* dW2, float* db2,
+                              float* dz_map, float* loss_sum, int32_t* status, void* stream);
+
 /* The decoder forward on tcgen05 tensor cores for din = 16, dh = 128,
  * dout = 512: z and W rounded to bf16, fp32 accumulation, the hidden layer
  * rounded to bf16 after the exact GELU; y = D + b2 in fp32. No workspace.

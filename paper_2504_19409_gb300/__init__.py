@@ -43,7 +43,7 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
            "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero",
            "gs_peak_probe", "gs_count_nonfinite", "gs_pair_state_workspace_bytes", "gs_render_fwd_pairs",
-           "gs_render_bwd_pairs")
+           "gs_render_bwd_pairs", "gs_decoder_train_tc_workspace_bytes", "gs_decoder_train_tc")
 
 
 class GsffError(RuntimeError):
@@ -234,6 +234,10 @@ def lib():
     L.gs_decoder_fwd.restype = ctypes.c_int
     L.gs_decoder_train.argtypes = [dec_p, _i64, _i64, ctypes.c_uint64, _vp, _vp, _f32, _vp, _sz] + [_vp] * 7
     L.gs_decoder_train.restype = ctypes.c_int
+    L.gs_decoder_train_tc_workspace_bytes.argtypes = [_i64]
+    L.gs_decoder_train_tc_workspace_bytes.restype = _sz
+    L.gs_decoder_train_tc.argtypes = [dec_p, _i64, _i64, ctypes.c_uint64, _vp, _vp, _f32, _vp, _sz] + [_vp] * 8
+    L.gs_decoder_train_tc.restype = ctypes.c_int
     L.gs_decoder_fwd_tc.argtypes = [dec_p, _i64, _vp, _vp, _vp, _vp]
     L.gs_decoder_fwd_tc.restype = ctypes.c_int
     L.gs_adam_step.argtypes = [_i64, _vp, _vp, _vp, _vp, _f32, _f32, _f32, _f32, _i32, _vp, _vp]

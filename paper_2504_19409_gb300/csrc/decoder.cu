@@ -92,16 +92,10 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
   }
 }
 
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// Pixel sample s of a step: splitmix64(seed + (s + 1) * golden) mod npix.
+// Pixel sample s of a step (decoder_sample_pixel: the ABI's sampling rule).
 __global__ void k_sample(long long S, long long npix, unsigned long long seed, int* __restrict__ idx) {
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x)
-    idx[s] = (int)(splitmix64(seed + (unsigned long long)(s + 1) * 0x9E3779B97F4A7C15ull) % (unsigned long long)npix);
+    idx[s] = (int)decoder_sample_pixel(seed, s, npix);
 }
 
 __global__ void k_gather(long long S, int d, const int* __restrict__ idx, const float* __restrict__ src,

@@ -205,6 +205,17 @@ struct NvtxRange {
 };
 #define GS_NVTX(name) ::gsff::NvtxRange _gs_nvtx_range_(name)
 
+// The decoder trainers' pixel sample s of a step (the ABI's sampling rule):
+// splitmix64(seed + (s + 1) * 0x9E3779B97F4A7C15) mod npix, splitmix64 being
+// Steele, Lea and Flood's 64-bit finaliser.
+__device__ __forceinline__ long long decoder_sample_pixel(unsigned long long seed, long long s, long long npix) {
+  unsigned long long z = seed + (unsigned long long)(s + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (long long)(z % (unsigned long long)npix);
+}
+
 inline gs_status last_launch_status() {
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

@@ -42,6 +42,7 @@ class Decoder:
         self.v = {k: torch.zeros_like(v) for k, v in self.params.items()}
         self.step = 0
         self._ws = None
+        self._ws_tc = None
 
     def struct(self) -> GsDecoder:
         d = GsDecoder()
@@ -102,6 +103,20 @@ class Decoder:
                                       _ptr(g["W1"]), _ptr(g["b1"]), _ptr(g["W2"]), _ptr(g["b2"]), _ptr(dz_map),
                                       _ptr(loss), _stream(stream)), "gs_decoder_train")
 
+    def train_eval_tc(self, z_map, target, nsample, seed, loss_scale, dz_map=None, loss=None, status=None,
+                      stream=None):
+        """The same accumulation on tcgen05 (gs_decoder_train_tc; bf16 operands, fp32 sums)."""
+        need = int(lib().gs_decoder_train_tc_workspace_bytes(int(nsample)))
+        if self._ws_tc is None or self._ws_tc.numel() < need:
+            self._ws_tc = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        d = self.struct()
+        g = self.grads
+        _check(lib().gs_decoder_train_tc(ctypes.byref(d), int(nsample), int(z_map.shape[0]), ctypes.c_uint64(seed),
+                                         _ptr(z_map), _ptr(target), float(loss_scale), _ptr(self._ws_tc),
+                                         self._ws_tc.numel(), _ptr(g["W1"]), _ptr(g["b1"]), _ptr(g["W2"]),
+                                         _ptr(g["b2"]), _ptr(dz_map), _ptr(loss), _ptr(status), _stream(stream)),
+               "gs_decoder_train_tc")
+
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         self.step += 1
         for k, p in self.params.items():
@@ -109,6 +124,48 @@ class Decoder:
             _check(lib().gs_adam_step(p.numel(), _ptr(p), _ptr(self.grads[k]), _ptr(self.m[k]), _ptr(self.v[k]),
                                       float(lr), float(beta1), float(beta2), float(eps), self.step, _ptr(q),
                                       _stream(stream)), "gs_adam_step")
+
+
+    # ---- checkpoint / resume (raw little-endian binary) ------------------
+    # magic "GSFFDEC1", int32 din, dh, dout, step, then for W1, b1, W2, b2 in
+    # turn the fp32 parameter, its first and its second Adam moment. The bf16
+    # working copies are the parameters' bf16 rounding, rebuilt on load.
+    _MAGIC = b"GSFFDEC1"
+    _NAMES = ("W1", "b1", "W2", "b2")
+
+    def state_bytes(self) -> bytes:
+        head = self._MAGIC + np.array([self.din, self.dh, self.dout, self.step], "<i4").tobytes()
+        body = b"".join(t.detach().cpu().numpy().astype("<f4").tobytes()
+                        for k in self._NAMES for t in (self.params[k], self.m[k], self.v[k]))
+        return head + body
+
+    def load_state_bytes(self, blob: bytes) -> int:
+        """Restores the state from state_bytes(); returns the bytes consumed."""
+        if blob[:8] != self._MAGIC:
+            raise ValueError("not a decoder checkpoint")
+        din, dh, dout, step = (int(x) for x in np.frombuffer(blob, "<i4", 4, 8))
+        if (din, dh, dout) != (self.din, self.dh, self.dout):
+            raise ValueError(f"checkpoint is {din}x{dh}x{dout}, decoder is {self.din}x{self.dh}x{self.dout}")
+        off = 24
+        for k in self._NAMES:
+            for t in (self.params[k], self.m[k], self.v[k]):
+                n = t.numel()
+                if len(blob) < off + 4 * n:
+                    raise ValueError("truncated decoder checkpoint")
+                t.copy_(torch.from_numpy(np.frombuffer(blob, "<f4", n, off).reshape(t.shape).copy()))
+                off += 4 * n
+        for k in self.work:
+            self.work[k].copy_(_bf16_round(self.params[k]))
+        self.step = step
+        return off
+
+    def save(self, path) -> None:
+        with open(path, "wb") as f:
+            f.write(self.state_bytes())
+
+    def load(self, path) -> None:
+        with open(path, "rb") as f:
+            self.load_state_bytes(f.read())
 
 
 def adam_tensor(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
@@ -127,7 +184,7 @@ class LatentFieldTrainer:
     """
 
     def __init__(self, scene_tensors, latents0: np.ndarray, cam_like, decoder: Decoder, capacity=None,
-                 device="cuda"):
+                 device="cuda", tensor_core=True):
         self.means, self.scales, self.quats, self.opac, self.cols = scene_tensors
         self.device = torch.device(device)
         self.lat = torch.tensor(np.asarray(latents0, np.float32), device=self.device)
@@ -136,6 +193,9 @@ class LatentFieldTrainer:
         self.lat_v = torch.zeros_like(self.lat)
         self.lat_step = 0
         self.dec = decoder
+        # the decoder's training on tcgen05 (gs_decoder_train_tc) where its
+        # shape allows, else the fp32 SIMT chain (gs_decoder_train)
+        self.tensor_core = tensor_core and (decoder.din, decoder.dh, decoder.dout) == (16, 128, 512)
         P, din = self.lat.shape
         self.ras = Rasterizer(P, cam_like.width, cam_like.height, N=din, capacity=capacity, layout=GS_LAYOUT_HWC,
                               device=device)
@@ -156,12 +216,40 @@ class LatentFieldTrainer:
         self.dec.zero_grad()
         self.dz.zero_()
         scale = 1.0 / (nsample * self.dec.dout)
-        self.dec.train_eval(z, target, nsample, seed, scale, dz_map=self.dz, loss=self.loss)
+        train = self.dec.train_eval_tc if self.tensor_core else self.dec.train_eval
+        train(z, target, nsample, seed, scale, dz_map=self.dz, loss=self.loss)
         g_feat = self.dz.reshape(cam.height, cam.width, -1)
         gr = self.ras.backward(cam, self.means, self.scales, self.quats, self.cols, self.lat, g_feat=g_feat)
         self.dec.adam(lr_dec)
         self.lat_step += 1
         adam_tensor(self.lat, gr["feats"], self.lat_m, self.lat_v, self.lat_step, lr_lat)
+
+    # checkpoint: magic "GSFFLAT1", int64 P, int32 din, int32 latent step, the
+    # latents and their two Adam moments (fp32), then the decoder's state
+    _MAGIC = b"GSFFLAT1"
+
+    def save(self, path) -> None:
+        P, din = self.lat.shape
+        head = self._MAGIC + np.array([P], "<i8").tobytes() + np.array([din, self.lat_step], "<i4").tobytes()
+        body = b"".join(t.detach().cpu().numpy().astype("<f4").tobytes() for t in (self.lat, self.lat_m, self.lat_v))
+        with open(path, "wb") as f:
+            f.write(head + body + self.dec.state_bytes())
+
+    def load(self, path) -> None:
+        with open(path, "rb") as f:
+            blob = f.read()
+        if blob[:8] != self._MAGIC:
+            raise ValueError("not a latent-field checkpoint")
+        P = int(np.frombuffer(blob, "<i8", 1, 8)[0])
+        din, step = (int(x) for x in np.frombuffer(blob, "<i4", 2, 16))
+        if (P, din) != tuple(self.lat.shape):
+            raise ValueError(f"checkpoint holds {P}x{din} latents, trainer has {tuple(self.lat.shape)}")
+        off, n = 24, P * din
+        for t in (self.lat, self.lat_m, self.lat_v):
+            t.copy_(torch.from_numpy(np.frombuffer(blob, "<f4", n, off).reshape(P, din).copy()))
+            off += 4 * n
+        self.lat_step = step
+        self.dec.load_state_bytes(blob[off:])
 
     def decode(self, cam):
         return self.dec.forward(self.render_latents(cam).contiguous())

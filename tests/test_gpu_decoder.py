@@ -95,6 +95,142 @@ def test_decoder_training_gradients_match_oracle(dec_mod, ora):
         assert rel < 1e-4, (k, rel)
 
 
+U_BF16 = 2.0 ** -8
+GAMMA_F32 = 2.0 ** -24  # per term of an fp32 sum (with the term count as factor)
+
+
+def _gelu(x):
+    return 0.5 * x * (1.0 + np.vectorize(math.erf)(x / math.sqrt(2.0)))
+
+
+def _gelu_d(x):
+    phi = np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    return 0.5 * (1.0 + np.vectorize(math.erf)(x / math.sqrt(2.0))) + x * phi
+
+
+def _gelu_dd(x):
+    return np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi) * (2.0 - x * x)
+
+
+def _tc_training_bound(zs, W1, b1, W2, t_minus_b2, scale, idx, npix):
+    """First-order bound of the tensor-core training's error: z, H, dY and dPRE
+    enter the products rounded to bf16 (relative error <= u each), every sum
+    is fp32 (gamma = k 2^-24 of the sum of |terms| over its k terms). The
+    magnitudes propagate through the step in its order, with |gelu'| and
+    |gelu''| at the exact pre-activation."""
+    u, S = U_BF16, zs.shape[0]
+    pre = zs @ W1 + b1
+    H = _gelu(pre)
+    r = H @ W2 - t_minus_b2  # = y - target
+    g = 2 * scale * r
+    aW1, aW2, az = np.abs(W1), np.abs(W2), np.abs(zs)
+    d_pre = u * az @ aW1 + 16 * GAMMA_F32 * (az @ aW1)
+    d_H = u * np.abs(H) + np.abs(_gelu_d(pre)) * d_pre
+    d_Y = d_H @ aW2 + 128 * GAMMA_F32 * (np.abs(H) @ aW2)
+    d_g = 2 * scale * d_Y                  # the fp32 cotangent (loss, db2)
+    d_gb = u * np.abs(g) + d_g              # the bf16 dY of the products
+    dH = g @ W2.T
+    d_dH = d_gb @ aW2.T + 512 * GAMMA_F32 * (np.abs(g) @ aW2.T)
+    dpre = dH * _gelu_d(pre)
+    d_dpre = u * np.abs(dpre) + np.abs(_gelu_d(pre)) * d_dH + np.abs(dH) * np.abs(_gelu_dd(pre)) * d_pre
+    gS = S * GAMMA_F32
+    b = dict(
+        W2=d_H.T @ np.abs(g) + np.abs(H).T @ d_gb + gS * (np.abs(H).T @ np.abs(g)),
+        b2=d_g.sum(0) + gS * np.abs(g).sum(0),
+        W1=(u * az).T @ np.abs(dpre) + az.T @ d_dpre + gS * (az.T @ np.abs(dpre)),
+        b1=d_dpre.sum(0) + gS * np.abs(dpre).sum(0),
+    )
+    dz_rows = d_dpre @ aW1.T + 128 * GAMMA_F32 * (np.abs(dpre) @ aW1.T)
+    b["z"] = np.zeros((npix, zs.shape[1]))
+    np.add.at(b["z"], idx, dz_rows)
+    b["loss"] = scale * (2 * np.abs(r) * d_Y).sum() + S * 512 * GAMMA_F32 * scale * (r * r).sum()
+    return b
+
+
+@pytest.mark.parametrize("S", [100, 2000])
+def test_decoder_training_tc_within_bf16_bound(dec_mod, ora, S):
+    """gs_decoder_train_tc against the FP64 oracle's loss and gradients (exact
+    fp32 z, the same bf16-exact weights):
+    * element by element within twice the first-order worst-case bound of
+      _tc_training_bound (the factor covers second-order terms). That bound
+      adds |terms|, so for these sums of random-sign terms it is loose (of the
+      order of the gradients themselves);
+    * normwise within u = 2^-8, one bf16 rounding: every gradient passes
+      through at most four rounded operands with independent errors of
+      relative size <= u, which mostly cancel (a numpy emulation of the same
+      roundings and fp32 sums lands at 0.03-0.6 u on the S = 2000 case).
+    S = 100 is one partial tile; 2000 is 16 tiles with a ragged last one,
+    spread over several CTAs."""
+    dec = dec_mod.Decoder(seed=5)
+    _normal_(dec.params["b1"], 0.1, 103)
+    _normal_(dec.params["b2"], 0.1, 104)
+    rng = np.random.default_rng(6)
+    npix, seed = 2500, 77
+    z = torch.tensor(rng.normal(size=(npix, 16)).astype(np.float32), device="cuda")
+    tgt = torch.tensor(rng.normal(size=(npix, 512)).astype(np.float32), device="cuda")
+    dz = torch.zeros(npix, 16, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    scale = 1.0 / (S * 512)
+    dec.zero_grad()
+    dec.train_eval_tc(z, tgt, S, seed, scale, dz_map=dz, loss=loss, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    idx = _samples(seed, S, npix)
+    W1, b1, W2, b2 = _np(dec.work["W1"]), _np(dec.params["b1"]), _np(dec.work["W2"]), _np(dec.params["b2"])
+    zs, ts = _np(z)[idx], _np(tgt)[idx]
+    y = ora.decoder_fwd(zs, W1, b1, W2, b2)
+    g = 2 * scale * (y - ts)
+    gr = ora.decoder_bwd(zs, W1, b1, W2, g)
+    dz_ref = np.zeros((npix, 16))
+    np.add.at(dz_ref, idx, gr["z"])
+    bound = _tc_training_bound(zs, W1, b1, W2, ts - b2, scale, idx, npix)
+    want_loss = scale * ((y - ts) ** 2).sum()
+    assert abs(loss.item() - want_loss) <= 2 * bound["loss"] + 1e-6 * want_loss
+    got = dict(W1=dec.grads["W1"], b1=dec.grads["b1"], W2=dec.grads["W2"], b2=dec.grads["b2"], z=dz)
+    want = dict(W1=gr["W1"], b1=gr["b1"], W2=gr["W2"], b2=gr["b2"], z=dz_ref)
+    for k in want:
+        a, b = _np(got[k]), want[k]
+        err = np.abs(a - b)
+        assert np.all(err <= 2 * bound[k] + 1e-12), (k, float((err / (bound[k] + 1e-30)).max()))
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= U_BF16, (k, rel)
+
+
+def test_checkpoint_resume_reproduces_the_next_step(dec_mod, tmp_path):
+    """Three tensor-core training steps with Adam, a checkpoint, then the next
+    step twice: from the live decoder and from a decoder of another seed
+    loaded from the file. Given the same gradients (the gradient sums use
+    float atomics, whose order may differ between runs), the resumed Adam
+    step gives bit-identical weights, moments and bf16 copies."""
+    rng = np.random.default_rng(12)
+    npix, S = 3000, 1000
+    z = torch.tensor(rng.normal(size=(npix, 16)).astype(np.float32), device="cuda")
+    tgt = torch.tensor(rng.normal(size=(npix, 512)).astype(np.float32), device="cuda")
+    a = dec_mod.Decoder(seed=9)
+    for step in range(3):
+        a.zero_grad()
+        a.train_eval_tc(z, tgt, S, 100 + step, 1.0 / (S * 512))
+        a.adam(1e-3)
+    path = tmp_path / "dec.bin"
+    a.save(path)
+    b = dec_mod.Decoder(seed=10)
+    b.load(path)
+    a.zero_grad()
+    a.train_eval_tc(z, tgt, S, 103, 1.0 / (S * 512))
+    for k in a.grads:
+        b.grads[k].copy_(a.grads[k])
+    a.adam(1e-3)
+    b.adam(1e-3)
+    torch.cuda.synchronize()
+    assert a.step == b.step == 4
+    for k in a.params:
+        for x, y in ((a.params[k], b.params[k]), (a.m[k], b.m[k]), (a.v[k], b.v[k])):
+            assert torch.equal(x.view(torch.int32), y.view(torch.int32)), k
+    for k in a.work:
+        assert torch.equal(a.work[k], b.work[k]), k
+
+
 def test_adam_step_formula(dec_mod):
     rng = np.random.default_rng(8)
     p0 = rng.normal(size=1000).astype(np.float32)
