@@ -170,7 +170,20 @@ def algorithmic_bytes(stats):
 def algorithmic_flops(stats):
     E, B, N = stats["evaluated"], stats["blends"], N_FEAT
     bwd = 14 * E + (65 + 2 * N) * B
-    return {"k_render_fwd": 14 * E + (11 + 2 * N) * B, "k_render_bwd": bwd, "k_render_bwd_mma": bwd}
+    return {"k_render_fwd": 14 * E + (11 + 2 * N) * B, "k_render_bwd": bwd,
+            "k_render_bwd_mma": bwd_mma_pipe_flops(stats)["fp32"]}
+
+
+# The tensor-core adjoint (k_render_bwd_mma) splits the same work over two
+# pipes. On the fp32 pipe (SIMT): every evaluated pair's alpha (14) and, per
+# blended pair, the transmittance recovery 2, the weight 1, dL/dalpha 17, the
+# suffix sums 13 and opacity / power 2 -> 35. On the tensor pipe (mma.sync,
+# bf16 operands): per blended pair the products of w with the N + 4 channel
+# cotangents and of dp with the six pixel monomials, each summed over the
+# pixels -> 2 (N + 4) + 2 * 6 flops.
+def bwd_mma_pipe_flops(stats):
+    E, B, N = stats["evaluated"], stats["blends"], N_FEAT
+    return {"fp32": 14 * E + 35 * B, "mma_sync": (2 * (N + 4) + 12) * B}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel,
@@ -560,6 +573,20 @@ def main():
                     "algorithmic_bytes": alg.get(dom),
                     "hbm_frac": round(alg.get(dom, 0) / (km[dom] * 1e-3) / 1e9 / hbm_peak, 4),
                     "hbm_peak_gbs": hbm_peak}
+            if dom == "k_render_bwd_mma":
+                # the fp32 pipe above; the tensor pipe's share against its own measured peak
+                pf = bwd_mma_pipe_flops(r["stats"])
+                t_s = km[dom] * 1e-3
+                roof["pipes"] = {
+                    "fp32": {"flops": pf["fp32"], "achieved": round(pf["fp32"] / t_s / 1e12, 3), "peak": alu["fp32"],
+                             "frac": round(pf["fp32"] / t_s / 1e12 / alu["fp32"], 4)},
+                    "mma_sync_bf16": {"flops": pf["mma_sync"], "achieved": round(pf["mma_sync"] / t_s / 1e12, 3),
+                                      "peak": alu["mma_sync_bf16"],
+                                      "frac": round(pf["mma_sync"] / t_s / 1e12 / alu["mma_sync_bf16"], 4)},
+                    "unit": "TFLOP/s",
+                    "model": "fp32: 14 per evaluated pair + 35 per blended pair (alpha, T recovery, weight, "
+                             "dL/dalpha, suffix sums); mma.sync: 2 (N + 4) + 12 per blended pair (channel and "
+                             "moment products summed over pixels)"}
             frame_bytes = sum(alg.get(k, 0) for k in km)
             frame_ms = float(np.median(r["flat_ms"]))
             roof["frame_algorithmic_bytes"] = round(frame_bytes)
