@@ -189,7 +189,7 @@ def bwd_mma_pipe_flops(stats):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the kernel,
 # from one ncu capture on the bench workload, keyed to the source it was taken
 # on (null once render.cu changes).
-NCU_TRAFFIC = {"k_render_bwd_mma": (40_770_000 + 6_140, "271ad14c3006b068")}
+NCU_TRAFFIC = {"k_render_bwd_mma": (40_754_176 + 67_328, "1a153c64361d83ef")}
 
 
 def ncu_traffic(kernel):
@@ -1029,6 +1029,22 @@ def decoder_form(args, peaks, kind, timing=True, label_query=False):
         tc.ensure_capacity(c, *scene[:4])
         plain.ensure_capacity(c, *scene[:4])
     torch.cuda.synchronize()
+    if args.profile:
+        # the tensor-core training evaluation alone (65,536 samples of the first
+        # training pose), --steps times between cudaProfilerStart/Stop, after
+        # --warmup untimed ones
+        c = train_cams[0]
+        z_map = trn.render_latents(c).contiguous()
+        tgt_map = tc.forward(c, *scene, feats_bf)["feat"].reshape(HW, N).contiguous()
+        for it in range(args.warmup):
+            dec.train_eval_tc(z_map, tgt_map, 65536, 7000 + it, 1.0 / (65536 * 512))
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for it in range(args.steps):
+            dec.train_eval_tc(z_map, tgt_map, 65536, 8000 + it, 1.0 / (65536 * 512))
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return None
     t0 = time.perf_counter()
     for step in range(args.train_steps):
         c = train_cams[step % n_train]
@@ -1271,6 +1287,9 @@ def run_forms(args):
         print(json.dumps(line))
         return 0
     d = decoder_form(args, peaks, args.features or "prototypes", timing=True, label_query=True)
+    if d is None:
+        print("profile run done")
+        return 0
     line = dict(base, value=None, ms_per_step=d["inference_ms_per_frame"]["latent16_decoder"],
                 dtype="latent fp32, decoder bf16 x bf16 -> fp32",
                 config={"workload": "decoder_room500k_1200x680_N512", "l2": "flushed between frames (512 MB write)"})
