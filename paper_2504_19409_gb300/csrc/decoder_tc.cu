@@ -163,6 +163,12 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_decoder_train_tc(const DtPara
       const long long gs = s0 + s;
       const long long pix = gs < p.nsample ? decoder_sample_pixel(p.seed, gs, p.npix) : -1;
       S.pix[s] = pix;
+      // the sample's 2 KB target row into L2 now: the loss epilogues read it
+      // after the first two products, 32 outputs per thread at a time
+      if (pix >= 0) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.target + pix * 512 + 32 * c));
+      }
       float v[16];
 #pragma unroll
       for (int d = 0; d < 16; ++d) v[d] = 0.f;

@@ -112,3 +112,30 @@ def test_sort_is_repeatable_on_a_dirty_workspace(gs, ora, sg):
         assert int(srt["status"].item()) == 0
         assert np.array_equal(srt["tile_ranges"].cpu().numpy(), ranges)
         assert np.array_equal(srt["gids"].cpu().numpy()[:I].view(np.uint32), gids.astype(np.uint32))
+
+
+def test_many_tiles_and_an_empty_frame(gs, ora):
+    """2,000 Gaussians on a 2560 x 1440 image (14,400 tiles: the one-block range
+    scan takes 15 tiles per thread, in two rounds of loads), then the same
+    Gaussians all behind the camera (no instance: every range (0, 0), I = 0)."""
+    sc, _ = sg_mod.small_case(seed=13, P=2000, N=0)
+    cam = sg_mod.identity_camera(2560, 1440, 1000.0).as_f32()
+    assert cam.tiles_x * cam.tiles_y == 14400
+    proj = _project(gs, cam, sc)
+    I = int(proj["n_instances"].item())
+    assert I > 10_000
+    srt = gs.bin_sort(cam, proj, I, tile_order=False)
+    torch.cuda.synchronize()
+    assert int(srt["status"].item()) == 0
+    _, ranges, gids = _oracle_lists(ora, cam, sc)
+    assert np.array_equal(srt["tile_ranges"].cpu().numpy(), ranges)
+    assert np.array_equal(srt["gids"].cpu().numpy()[:I].view(np.uint32), gids.astype(np.uint32))
+    behind = sg_mod.Scene(sc.means * np.array([1, 1, -1], np.float32), sc.scales, sc.quats, sc.opacity, sc.colors,
+                          sc.feats)
+    proj = _project(gs, cam, behind)
+    assert int(proj["n_instances"].item()) == 0
+    srt = gs.bin_sort(cam, proj, 16, tile_order=False)
+    torch.cuda.synchronize()
+    assert int(srt["status"].item()) == 0
+    assert int(srt["n_instances"].item()) == 0
+    assert not srt["tile_ranges"].any()
