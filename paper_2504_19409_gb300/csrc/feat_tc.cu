@@ -605,30 +605,46 @@ gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, co
 //       element (p, g) at (g/8)*128 + (p/8)*512 + (p%8)*16 + (g%8)*2
 //       descriptor LBO = 512 (K = pixels), SBO = 128 (N = Gaussians)
 // The kernel is persistent (one CTA per SM, the forward's list of half
-// tiles). For each half tile every warp first stages dF^T (the fp32
-// cotangents of its 128 pixels, eight 16-byte loads in flight per thread,
-// rounded to bf16); then the roles run over the blocks of its compacted
-// list (the Gaussians whose skip mask reaches the half tile):
+// tiles). Each half tile starts with dF^T in A: the first one staged by every
+// warp from global memory (the fp32 cotangents of its 128 pixels, eight
+// 16-byte loads in flight per thread, rounded to bf16), every later one
+// copied in from tensor memory, where the epilogue warps left it while the
+// previous half tile ran (see below); the roles run over the blocks of the
+// compacted lists (the Gaussians whose skip mask reaches the half tile) of
+// all the CTA's half tiles without a CTA-wide barrier between half tiles, so
+// the producer and builders run up to the ring's depth ahead across them:
 //   warp 0 (producer): the compaction and the records of each block by
-//     cp.async into a 4-deep ring;
+//     cp.async into a 3-deep ring;
 //   warps 10-25 (builders, 4 threads per pixel): W as in the forward, and
 //     the bits of the block's Gaussians that weigh something here;
 //   warp 1 (one thread): NMB x 8 tcgen05.mma (M=128, N=32, K=16) per block
 //     into one of two tensor-memory accumulators;
 //   warps 2-9 (epilogue; lanes 32 (w % 4).., Gaussians 16 (w >= 6)..+15):
 //     the accumulator into registers, then one vector atomic per (Gaussian,
-//     lane) into d_feats for the Gaussians that weigh something.
+//     lane) into d_feats for the Gaussians that weigh something. While they
+//     wait for the products they stage the NEXT half tile's cotangents: 16
+//     chunks of 8 pixels (one row segment, all N channels, fp32) through a
+//     4-slot shared-memory ring by cp.async (every epilogue thread copies a
+//     share of each chunk; the slot's barrier completes when all copies have
+//     landed), and per chunk one set of four warps (one per tensor-memory
+//     lane quarter) rounds it to bf16 and stores it with tcgen05.st into the
+//     tensor-memory columns the accumulators leave free (lane = row r of the
+//     M-blocks, column = staging base + mb * 64 + pixel / 2, two pixels per
+//     32-bit column). After a half tile's last block (whose completion
+//     implies every product of the half tile has read A) the epilogue warps
+//     move it into A and signal the MMA thread, which waits for that before
+//     the next half tile's first product.
 // Every wait is bounded (1 s); a timeout flags GS_ERR_TIMEOUT and raises the
 // abort word, on which every role stops.
 namespace {
 
 constexpr int kTbG = 32;  // Gaussians per block (MMA N)
 constexpr int kBwThreads = 832;
-constexpr int kBwStages = 4;
+constexpr int kBwStages = 3;
 constexpr int kBwWarpMma = 1, kBwWarpEpi = 2, kBwEpi = 8, kBwWarpBuild = 10, kBwBuilders = 16;
 static_assert(kBwWarpBuild * 32 + 4 * kTcPix == kBwThreads, "four builder threads per pixel");
 
-struct alignas(1024) BwStage {
+struct alignas(16) BwStage {
   uint8_t W[kTcPix * kTbG * 2];  // 8 KB, B operand
   float2 uv[kTbG];               // entry k at slot (k % 8) * 4 + k / 8
   float4 co[kTbG];
@@ -638,17 +654,25 @@ struct alignas(1024) BwStage {
   int nvalid, flags;             // flags: 1 first block of its half tile, 2 last
 };
 
+constexpr int kStgSlots = 4;   // cotangent staging ring (chunks of 8 pixels)
+constexpr int kStgChunks = 16;  // chunks per half tile
+
 struct BwSmem {
   uint8_t A[kTcMaxN * kTcPix * 2];  // dF^T, 128 KB for N = 512
   BwStage st[kBwStages];
+  float stg[kStgSlots][8 * kTcMaxN];  // 16 KB per slot: pixel e's N channels at e * N
+  unsigned long long stg_full[kStgSlots], stg_empty[kStgSlots];
   uint32_t cgid[64];
   int cpos[64];
   unsigned long long full[kBwStages], ready[kBwStages], empty[kBwStages];
   unsigned long long done[2], dfree[2], drain;
+  unsigned long long a_full;  // the epilogue warps have moved the next half tile's dF^T into A
   uint32_t tmem;
   int abort;
 };
-static_assert(sizeof(BwSmem) + 1024 <= 227 * 1024, "shared memory of the adjoint");
+// the structure is placed at the first 128-byte boundary of the dynamic shared
+// memory (no operand here is swizzled: 16-byte alignment is what they need)
+static_assert(sizeof(BwSmem) + 128 <= 227 * 1024, "shared memory of the adjoint");
 
 struct BwParams {
   CamF cam;
@@ -705,6 +729,168 @@ __device__ __forceinline__ void bw_stage_cotangents(const BwParams& p, BwSmem& S
       *reinterpret_cast<uint4*>(S.A + mb * 32768 + (r >> 3) * 2048 + pg * 128 + (r & 7) * 16) =
           make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
+  }
+}
+
+// Non-blocking test of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// The epilogue warps' staging of the next half tile (see the kernel comment).
+// Chunk c of the half tile is the CTA's chunk number g = g0 + c: ring slot
+// g % kStgSlots, its use number u = g / kStgSlots picks the barrier phases.
+struct BwStg {
+  bool on;
+  int tx, ty, half;  // the next half tile
+  int ci;            // next chunk this warp copies (every epilogue warp copies a share of each)
+  int cc;            // next chunk this warp converts (its set's chunks: cc = set, set + 2, ..)
+  uint32_t g0;
+};
+
+template <int NMB>
+__device__ __forceinline__ void bw_stg_copy(const BwParams& p, BwSmem& S, const BwStg& c, int chunk, uint32_t slot) {
+  constexpr int N = NMB * 128, nq = N / 4;
+  const int et = threadIdx.x - kBwWarpEpi * 32;  // 0 .. 255
+  const int ry = c.ty * kTile + c.half * 8 + (chunk >> 1), rx0 = c.tx * kTile + (chunk & 1) * 8;
+  const uint32_t dst0 = smem_u32(S.stg[slot]);
+#pragma unroll
+  for (int j = 0; j < NMB; ++j) {
+    const int i = et + 256 * j, e = i / nq, q = i - e * nq;
+    const bool ok = ry < p.cam.H && rx0 + e < p.cam.W;
+    const float* src = p.g_feat + ((size_t)(ok ? ry : 0) * p.cam.W + (ok ? rx0 + e : 0)) * N + 4 * q;
+    cp_async16(dst0 + (uint32_t)(e * N + 4 * q) * 4u, src, ok);
+  }
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.stg_full[slot])) : "memory");
+}
+
+// chunk -> bf16 -> tensor memory, by the warp of lane quarter (warp % 4)
+template <int NMB>
+__device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chunk, uint32_t slot) {
+  constexpr int N = NMB * 128;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = 32 * (warp & 3) + lane;  // row: channels NMB r .. NMB r + NMB - 1
+  const float* src = S.stg[slot];
+  float v[8][NMB];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const float* q = src + e * N + NMB * r;  // lanes read consecutive NMB-float groups
+    if constexpr (NMB == 4) {
+      const float4 x = *reinterpret_cast<const float4*>(q);
+      v[e][0] = x.x, v[e][1] = x.y, v[e][2] = x.z, v[e][3] = x.w;
+    } else if constexpr (NMB == 2) {
+      const float2 x = *reinterpret_cast<const float2*>(q);
+      v[e][0] = x.x, v[e][1] = x.y;
+    } else {
+#pragma unroll
+      for (int mb = 0; mb < NMB; ++mb) v[e][mb] = q[mb];
+    }
+  }
+  const uint32_t col0 = (uint32_t)(NMB * 64) + (uint32_t)((chunk >> 1) * 8 + (chunk & 1) * 4);
+  const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + col0;
+#pragma unroll
+  for (int mb = 0; mb < NMB; ++mb) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * k][mb], v[2 * k + 1][mb]);
+      w[k] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + (uint32_t)(mb * 64)),
+                 "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// One round of staging work that needs no waiting: copy the next chunk if
+// its slot is free, convert this warp's next chunk if it has landed.
+template <int NMB>
+__device__ bool bw_stg_step(const BwParams& p, BwSmem& S, uint32_t tmem, BwStg& c) {
+  if (!c.on) return false;
+  bool progress = false;
+  if (c.ci < kStgChunks) {
+    const uint32_t g = c.g0 + (uint32_t)c.ci, slot = g % kStgSlots, u = g / kStgSlots;
+    if (u == 0 || mbar_test(smem_u32(&S.stg_empty[slot]), (u - 1) & 1u)) {
+      bw_stg_copy<NMB>(p, S, c, c.ci, slot);
+      ++c.ci;
+      progress = true;
+    }
+  }
+  if (c.cc < kStgChunks) {
+    const uint32_t g = c.g0 + (uint32_t)c.cc, slot = g % kStgSlots, u = g / kStgSlots;
+    if (mbar_test(smem_u32(&S.stg_full[slot]), u & 1u)) {
+      bw_stg_convert<NMB>(S, tmem, c.cc, slot);
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&S.stg_empty[slot]));
+      c.cc += 2;
+      progress = true;
+    }
+  }
+  return progress;
+}
+
+// Bounded wait for a barrier phase that stages while it waits; false on
+// timeout (the abort word raised, GS_ERR_TIMEOUT flagged) or another role's abort.
+template <int NMB>
+__device__ bool bw_wait_staging(const BwParams& p, BwSmem& S, uint32_t tmem, BwStg& c, uint32_t bar,
+                                uint32_t parity) {
+  volatile int* abort = &S.abort;
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_test(bar, parity)) return true;
+    if (bw_stg_step<NMB>(p, S, tmem, c)) continue;
+    if (*abort) return false;
+    if (gtime() - t0 > kWaitNs) {
+      *abort = 1;
+      flag_status(p.status, GS_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// The rest of the next half tile's staging after the current one's last block.
+template <int NMB>
+__device__ bool bw_stg_finish(const BwParams& p, BwSmem& S, uint32_t tmem, BwStg& c) {
+  volatile int* abort = &S.abort;
+  const unsigned long long t0 = gtime();
+  while (c.on && (c.ci < kStgChunks || c.cc < kStgChunks)) {
+    if (bw_stg_step<NMB>(p, S, tmem, c)) continue;
+    if (*abort) return false;
+    if (gtime() - t0 > kWaitNs) {
+      *abort = 1;
+      flag_status(p.status, GS_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// The epilogue warps: the staged dF^T from tensor memory into A (warp w
+// moves lanes 32 (w % 4) .., items (M-block, 16-pixel group) dealt over the
+// two epilogue warps of its lane quarter).
+template <int NMB>
+__device__ __forceinline__ void bw_copy_staged(BwSmem& S, uint32_t tmem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, qd = warp & 3;
+  const int j = (warp - kBwWarpEpi) >> 2, nw = kBwEpi / 4;
+  const int r = 32 * qd + lane;
+  const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(NMB * 64);
+  for (int it = j; it < NMB * 8; it += nw) {
+    const int mb = it >> 3, pg2 = it & 7;
+    float f[8];
+    tmem_ld8(ta + (uint32_t)(mb * 64 + pg2 * 8), f);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    uint8_t* dst = S.A + mb * 32768 + (r >> 3) * 2048 + (2 * pg2) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(dst) =
+        make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]), __float_as_uint(f[3]));
+    *reinterpret_cast<uint4*>(dst + 128) =
+        make_uint4(__float_as_uint(f[4]), __float_as_uint(f[5]), __float_as_uint(f[6]), __float_as_uint(f[7]));
   }
 }
 
@@ -902,7 +1088,8 @@ __device__ bool bw_mma(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint
 
 // warps 2-9: accumulators into the feature gradient
 template <int NMB>
-__device__ bool bw_epilogue(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint32_t& ph, uint32_t& nblk) {
+__device__ bool bw_epilogue(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint32_t& ph, uint32_t& nblk,
+                            BwStg& stg) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int qd = warp & 3, gh = (warp - kBwWarpEpi) >> 2;  // lane quarter, Gaussians 16 gh .. 16 gh + 15
   volatile int* abort = &S.abort;
@@ -911,7 +1098,7 @@ __device__ bool bw_epilogue(const BwParams& p, BwSmem& S, uint32_t tmem, int& s,
   const int r = 32 * qd + lane;  // channel row: channels NMB r .. NMB r + NMB - 1
   while (true) {
     const uint32_t buf = nblk & 1u, use = nblk >> 1;
-    if (!fw_wait(smem_u32(&S.done[buf]), use & 1u, abort, p.status)) return false;
+    if (!bw_wait_staging<NMB>(p, S, tmem, stg, smem_u32(&S.done[buf]), use & 1u)) return false;
     // the builders' release of this block (its gids, bits and flags)
     if (!fw_wait(smem_u32(&S.ready[s]), ph, abort, p.status)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -960,7 +1147,7 @@ __device__ bool bw_epilogue(const BwParams& p, BwSmem& S, uint32_t tmem, int& s,
 template <int NMB>
 __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwParams p) {
   extern __shared__ uint8_t smem_raw[];
-  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  const uint32_t pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
   BwSmem& S = *reinterpret_cast<BwSmem*>(smem_raw + pad);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pdl_wait();
@@ -976,6 +1163,11 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.dfree[b])), "r"(kBwEpi));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.drain)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.a_full)));
+    for (int k = 0; k < kStgSlots; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.stg_full[k])), "r"(kBwEpi * 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.stg_empty[k])), "r"(kBwEpi / 2));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     S.abort = 0;
   }
@@ -990,29 +1182,81 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
   const uint32_t tmem = S.tmem;
   int s = 0;
   uint32_t ph = 0, nblk = 0;
-  for (int rr = 0;; ++rr) {
-    const int h = fw_half_tile(rr, p.nhalf);
-    if (h < 0) break;
-    int tx, ty, half;
-    bw_tile(p, h, tx, ty, half);
-    // every role is done with the previous half tile (its products have
-    // completed: the epilogue waited for them), so A is free
-    __syncthreads();
-    if (S.abort) break;
-    bw_stage_cotangents<NMB>(p, S, tx, ty, half);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-      bw_producer(p, S, tx, ty, half, s, ph);
-    } else if (warp == kBwWarpMma) {
-      if (lane == 0) bw_mma<NMB>(p, S, tmem, s, ph, nblk);
-    } else if (warp < kBwWarpBuild) {
-      bw_epilogue<NMB>(p, S, tmem, s, ph, nblk);
-    } else {
-      bw_builder(p, S, tx, ty, half, s, ph);
+  // the first half tile's dF^T, by every warp from global memory
+  {
+    const int h0 = fw_half_tile(0, p.nhalf);
+    if (h0 >= 0) {
+      int tx, ty, half;
+      bw_tile(p, h0, tx, ty, half);
+      bw_stage_cotangents<NMB>(p, S, tx, ty, half);
     }
   }
-  if (warp == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    for (int rr = 0;; ++rr) {
+      const int h = fw_half_tile(rr, p.nhalf);
+      if (h < 0) break;
+      int tx, ty, half;
+      bw_tile(p, h, tx, ty, half);
+      if (!bw_producer(p, S, tx, ty, half, s, ph)) break;
+    }
+  } else if (warp == kBwWarpMma) {
+    if (lane == 0) {
+      volatile int* abort = &S.abort;
+      for (int rr = 0;; ++rr) {
+        if (fw_half_tile(rr, p.nhalf) < 0) break;
+        // this half tile's dF^T is in A
+        if (rr > 0 && !fw_wait(smem_u32(&S.a_full), (uint32_t)(rr - 1) & 1u, abort, p.status)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!bw_mma<NMB>(p, S, tmem, s, ph, nblk)) break;
+      }
+    }
+  } else if (warp < kBwWarpBuild) {
+    uint32_t gchunks = 0;  // staging chunks this CTA has used (ring slot phases)
+    for (int rr = 0;; ++rr) {
+      if (fw_half_tile(rr, p.nhalf) < 0) break;
+      const int hn = fw_half_tile(rr + 1, p.nhalf);
+      BwStg stg;
+      stg.on = hn >= 0;
+      if (stg.on) bw_tile(p, hn, stg.tx, stg.ty, stg.half);
+      stg.ci = 0;
+      stg.cc = (warp - kBwWarpEpi) >> 2;
+      stg.g0 = gchunks;
+      bool ok = bw_epilogue<NMB>(p, S, tmem, s, ph, nblk, stg);
+      if (ok) ok = bw_stg_finish<NMB>(p, S, tmem, stg);
+      // every epilogue warp has staged its chunks and read its accumulators;
+      // the last block's completion means every product of this half tile has
+      // read A. The decision to stop is taken together (a barrier reduction).
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      int stop;
+      asm volatile(
+          "{\n\t.reg .pred q, r;\n\tsetp.ne.b32 q, %1, 0;\n\tbar.red.or.pred r, 1, %2, q;\n\tselp.u32 %0, 1, 0, r;\n\t}\n"
+          : "=r"(stop)
+          : "r"((int)(!ok || S.abort || hn < 0)), "n"(kBwEpi * 32)
+          : "memory");
+      if (stop) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      bw_copy_staged<NMB>(S, tmem);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kBwEpi * 32) : "memory");
+      // the next staging's tensor-memory stores come after every warp's loads
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (warp == kBwWarpEpi && lane == 0) mbar_arrive(smem_u32(&S.a_full));
+      gchunks += kStgChunks;
+    }
+  } else {
+    for (int rr = 0;; ++rr) {
+      const int h = fw_half_tile(rr, p.nhalf);
+      if (h < 0) break;
+      int tx, ty, half;
+      bw_tile(p, h, tx, ty, half);
+      if (!bw_builder(p, S, tx, ty, half, s, ph)) break;
+    }
+  }
+  // every thread's copies have landed (the epilogue warps' staging, warp 0's records)
+  asm volatile("cp.async.wait_all;" ::: "memory");
   if (warp == kBwWarpMma && lane == 0) {
     // every product issued has completed before tensor memory is freed
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -1030,7 +1274,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
 
 template <int NMB>
 gs_status launch_bwd_nmb(const BwParams& p, cudaStream_t st) {
-  const size_t smem = sizeof(BwSmem) + 1024;
+  const size_t smem = sizeof(BwSmem) + 128;
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_render_feat_tc_bwd<NMB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -1068,8 +1312,9 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* range
   p.last_idx = last_idx;
   p.g_feat = g_feat;
   p.N = N;
+  // two accumulators (NMB x 32 columns each) and the staged next dF^T (NMB x 64)
   int cols = 32;
-  while (cols < 2 * (N / 128) * kTbG) cols *= 2;
+  while (cols < 4 * (N / 128) * kTbG) cols *= 2;
   p.tmem_cols = cols;
   p.nhalf = 2 * cam.tiles_x * cam.tiles_y;
   p.d_feats = d_feats;
