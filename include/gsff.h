@@ -619,6 +619,20 @@ gs_status gs_trace_get(int32_t i, const char** name, float* ms);
 gs_status gs_peak_probe(int32_t kind, int32_t blocks, int32_t threads, int32_t iters, float* sink, double* ops,
                         void* stream);
 
+/* ---------------------------------------------------------------------------
+ * gs_test_hold_tc_producer -- test hook of the bounded waits (failure
+ * detection; the paper has no counterpart). While `on` is nonzero, the
+ * tensor-core feature forward (gs_render_fwd with GS_FEAT_TENSOR_CORE) runs
+ * with its producer warps idle: no stage is ever filled, so every other
+ * role's mbarrier wait runs out after its bound (1 s of %globaltimer). The
+ * launch then ORs 1 << GS_ERR_TIMEOUT into the status word, frees its tensor
+ * memory and returns; the feature map is unspecified, everything else the
+ * call writes is as usual. Nothing is copied or issued to the tensor core
+ * before the waits give up, so the context stays usable. Process-wide, read
+ * at each launch; not for use while other threads render. Returns GS_OK.
+ */
+gs_status gs_test_hold_tc_producer(int32_t on);
+
 const char* gs_status_string(gs_status s);
 int32_t gs_version(void);
 

@@ -43,7 +43,8 @@ EXPORTS = ("gs_project", "gs_bin_sort_workspace_bytes", "gs_bin_sort", "gs_rende
            "gs_sh_colors", "gs_sh_colors_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_tile_order",
            "gs_l1_signs", "gs_tracking_loss_signs", "gs_zero",
            "gs_peak_probe", "gs_count_nonfinite", "gs_pair_state_workspace_bytes", "gs_render_fwd_pairs",
-           "gs_render_bwd_pairs", "gs_decoder_train_tc_workspace_bytes", "gs_decoder_train_tc")
+           "gs_render_bwd_pairs", "gs_decoder_train_tc_workspace_bytes", "gs_decoder_train_tc",
+           "gs_test_hold_tc_producer")
 
 
 class GsffError(RuntimeError):
@@ -90,6 +91,12 @@ def zero_(t, stream=None):
         raise GsffError("zero_ needs a contiguous CUDA tensor (a strided view would be cleared over the wrong span)")
     _check(lib().gs_zero(_ptr(t), t.numel() * t.element_size(), _stream(stream)), "gs_zero")
     return t
+
+
+def hold_tc_producer(on):
+    """gs_test_hold_tc_producer: while on, the tensor-core forward's producer warps stay idle, so its
+    bounded waits run out (the launch flags GS_ERR_TIMEOUT and returns); a failure-detection test hook."""
+    _check(lib().gs_test_hold_tc_producer(1 if on else 0), "gs_test_hold_tc_producer")
 
 
 def count_nonfinite(tensors, stream=None):
@@ -169,6 +176,8 @@ def lib():
     L.gs_bin_sort_static.restype = ctypes.c_int
     L.gs_zero.argtypes = [_vp, _sz, _vp]
     L.gs_zero.restype = ctypes.c_int
+    L.gs_test_hold_tc_producer.argtypes = [_i32]
+    L.gs_test_hold_tc_producer.restype = ctypes.c_int
     L.gs_peak_probe.argtypes = [_i32, _i32, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_double), _vp]
     L.gs_peak_probe.restype = ctypes.c_int
     L.gs_pair_state_workspace_bytes.argtypes = [_i32, _i32]

@@ -323,6 +323,11 @@ extern "C" {
 
 int32_t gs_version(void) { return 1; }
 
+gs_status gs_test_hold_tc_producer(int32_t on) {
+  set_tc_test_hold(on);
+  return GS_OK;
+}
+
 const char* gs_status_string(gs_status s) {
   switch (s) {
     case GS_OK: return "ok";

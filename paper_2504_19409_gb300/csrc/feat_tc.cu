@@ -24,6 +24,8 @@
 // GS_ERR_TIMEOUT, waits (bounded) for the tensor core, frees tensor memory
 // and returns.
 
+#include <atomic>
+
 #include "tc_util.cuh"
 
 namespace gsff {
@@ -63,7 +65,9 @@ constexpr int kTcMaxN = 512;
 //     32 columns at a time into registers, into a 4 KB box of shared memory
 //     in the 128-byte swizzled order, then one TMA tensor store of the box
 //     (32 channels x 16 pixels x 2 rows of the HWC map; the tensor map clips
-//     the image edge); two boxes per warp alternate. Each channel half of
+//     the image edge) with an L2 evict-first hint (the map is not read again
+//     here; the feature rows that later half tiles reuse stay in L2); two
+//     boxes per warp alternate. Each channel half of
 //     tensor memory is released as soon as every warp has read it.
 // Every wait is bounded (1 s of %globaltimer): a role that gives up flags
 // GS_ERR_TIMEOUT and raises the CTA's abort word, on which every other wait
@@ -113,6 +117,7 @@ struct FwParams {
   const int* last_idx;
   int N, tmem_cols, nhalf;
   int P;  // Gaussians (bound of the checked build's id checks)
+  int hold;  // test hook: the producer issues nothing, so the other roles' waits run out
   int32_t* status;
 };
 
@@ -465,7 +470,9 @@ __device__ void fw_epilogue(const FwParams& p, FwSmem& S, uint32_t tmem, const C
       __syncwarp();
       if (lane == 0) {
         asm volatile(
-            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(omap),
+            "{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%2, %3, %4}], [%1], pol;"
+            "\n\t}\n" ::"l"(omap),
             "r"(smem_u32(box)), "r"(32 * c), "r"(x0), "r"(y0)
             : "memory");
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -507,7 +514,7 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_render_feat_tc(const FwParams
   const uint32_t tmem = S.tmem;
 
   if (warp == 0) {
-    fw_producer(p, S);
+    if (!p.hold) fw_producer(p, S);
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == kFwWarpMma) {
     if (lane == 0) {
@@ -535,7 +542,11 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_render_feat_tc(const FwParams
   }
 }
 
+std::atomic<int> g_tc_hold{0};
+
 }  // namespace
+
+void set_tc_test_hold(int on) { g_tc_hold.store(on ? 1 : 0); }
 
 gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,
                                const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
@@ -558,6 +569,7 @@ gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, co
   while (cols < N) cols *= 2;
   p.tmem_cols = cols;
   p.nhalf = 2 * cam.tiles_x * cam.tiles_y;
+  p.hold = g_tc_hold.load();
   p.status = status;
   // the HWC feature map as a 3D tensor (channels, x, y) for the epilogue's
   // TMA stores of 32 x 16 x 2 boxes with 128-byte swizzle

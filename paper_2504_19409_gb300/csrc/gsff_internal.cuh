@@ -224,8 +224,6 @@ inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Bound of the radix passes' look-back waits in ns (binsort.cu; 0 = give up at once).
-
 // ---- launchers implemented in the .cu files ---------------------------------
 gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, const int32_t* order,
                                const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
@@ -235,5 +233,8 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* range
                                     const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
                                     const int32_t* last_idx, const float* g_feat, int N, float* d_feats,
                                     int32_t* status, cudaStream_t st);
+// Test hook of the tensor-core forward's bounded waits (feat_tc.cu): while
+// set, its producer warps issue nothing.
+void set_tc_test_hold(int on);
 
 }  // namespace gsff
