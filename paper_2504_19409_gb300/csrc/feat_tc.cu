@@ -635,14 +635,16 @@ gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, co
 //     the accumulator into registers, then one vector atomic per (Gaussian,
 //     lane) into d_feats for the Gaussians that weigh something. While they
 //     wait for the products they stage the NEXT half tile's cotangents: 16
-//     chunks of 8 pixels (one row segment, all N channels, fp32) through a
-//     4-slot shared-memory ring by cp.async (every epilogue thread copies a
-//     share of each chunk; the slot's barrier completes when all copies have
-//     landed), and per chunk one set of four warps (one per tensor-memory
-//     lane quarter) rounds it to bf16 and stores it with tcgen05.st into the
-//     tensor-memory columns the accumulators leave free (lane = row r of the
-//     M-blocks, column = staging base + mb * 64 + pixel / 2, two pixels per
-//     32-bit column). After a half tile's last block (whose completion
+//     chunks of 8 pixels (one row segment, all N channels, fp32) arrive in a
+//     4-slot shared-memory ring, and per chunk one set of four warps (one per
+//     tensor-memory lane quarter) rounds it to bf16 and stores it with
+//     tcgen05.st into the tensor-memory columns the accumulators leave free
+//     (lane = row r of the M-blocks, column = staging base + mb * 64 +
+//     pixel / 2, two pixels per 32-bit column);
+//   warp 26 (one thread, the copier): each chunk (8 consecutive pixels of a
+//     row, contiguous in the HWC map) by one bulk copy into its slot as soon
+//     as the slot's previous chunk has been converted; the copy's bytes
+//     complete the slot's barrier. After a half tile's last block (whose completion
 //     implies every product of the half tile has read A) the epilogue warps
 //     move it into A and signal the MMA thread, which waits for that before
 //     the next half tile's first product.
@@ -651,10 +653,11 @@ gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, co
 namespace {
 
 constexpr int kTbG = 32;  // Gaussians per block (MMA N)
-constexpr int kBwThreads = 832;
+constexpr int kBwThreads = 864;
 constexpr int kBwStages = 3;
-constexpr int kBwWarpMma = 1, kBwWarpEpi = 2, kBwEpi = 8, kBwWarpBuild = 10, kBwBuilders = 16;
-static_assert(kBwWarpBuild * 32 + 4 * kTcPix == kBwThreads, "four builder threads per pixel");
+constexpr int kBwWarpMma = 1, kBwWarpEpi = 2, kBwEpi = 8, kBwWarpBuild = 10, kBwBuilders = 16, kBwWarpCopy = 26;
+static_assert(kBwWarpBuild * 32 + 4 * kTcPix == kBwWarpCopy * 32, "four builder threads per pixel");
+static_assert((kBwWarpCopy + 1) * 32 == kBwThreads, "one copier warp after the builders");
 
 struct alignas(16) BwStage {
   uint8_t W[kTcPix * kTbG * 2];  // 8 KB, B operand
@@ -761,30 +764,21 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 struct BwStg {
   bool on;
   int tx, ty, half;  // the next half tile
-  int ci;            // next chunk this warp copies (every epilogue warp copies a share of each)
   int cc;            // next chunk this warp converts (its set's chunks: cc = set, set + 2, ..)
   uint32_t g0;
 };
 
-template <int NMB>
-__device__ __forceinline__ void bw_stg_copy(const BwParams& p, BwSmem& S, const BwStg& c, int chunk, uint32_t slot) {
-  constexpr int N = NMB * 128, nq = N / 4;
-  const int et = threadIdx.x - kBwWarpEpi * 32;  // 0 .. 255
-  const int ry = c.ty * kTile + c.half * 8 + (chunk >> 1), rx0 = c.tx * kTile + (chunk & 1) * 8;
-  const uint32_t dst0 = smem_u32(S.stg[slot]);
-#pragma unroll
-  for (int j = 0; j < NMB; ++j) {
-    const int i = et + 256 * j, e = i / nq, q = i - e * nq;
-    const bool ok = ry < p.cam.H && rx0 + e < p.cam.W;
-    const float* src = p.g_feat + ((size_t)(ok ? ry : 0) * p.cam.W + (ok ? rx0 + e : 0)) * N + 4 * q;
-    cp_async16(dst0 + (uint32_t)(e * N + 4 * q) * 4u, src, ok);
-  }
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.stg_full[slot])) : "memory");
+// Pixels of chunk c of a half tile that lie in the image (the chunk's first
+// nv pixels; 0 for a row below the image).
+__device__ __forceinline__ int bw_chunk_pixels(const BwParams& p, int tx, int ty, int half, int c) {
+  const int ry = ty * kTile + half * 8 + (c >> 1), rx0 = tx * kTile + (c & 1) * 8;
+  return ry < p.cam.H ? max(0, min(8, p.cam.W - rx0)) : 0;
 }
 
-// chunk -> bf16 -> tensor memory, by the warp of lane quarter (warp % 4)
+// chunk -> bf16 -> tensor memory, by the warp of lane quarter (warp % 4);
+// pixels past the chunk's nv valid ones (not copied) are zero
 template <int NMB>
-__device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chunk, uint32_t slot) {
+__device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chunk, uint32_t slot, int nv) {
   constexpr int N = NMB * 128;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = 32 * (warp & 3) + lane;  // row: channels NMB r .. NMB r + NMB - 1
@@ -793,7 +787,10 @@ __device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chu
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const float* q = src + e * N + NMB * r;  // lanes read consecutive NMB-float groups
-    if constexpr (NMB == 4) {
+    if (e >= nv) {
+#pragma unroll
+      for (int mb = 0; mb < NMB; ++mb) v[e][mb] = 0.f;
+    } else if constexpr (NMB == 4) {
       const float4 x = *reinterpret_cast<const float4*>(q);
       v[e][0] = x.x, v[e][1] = x.y, v[e][2] = x.z, v[e][3] = x.w;
     } else if constexpr (NMB == 2) {
@@ -821,31 +818,18 @@ __device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chu
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// One round of staging work that needs no waiting: copy the next chunk if
-// its slot is free, convert this warp's next chunk if it has landed.
+// One round of staging work that needs no waiting: convert this warp's next
+// chunk if it has landed.
 template <int NMB>
 __device__ bool bw_stg_step(const BwParams& p, BwSmem& S, uint32_t tmem, BwStg& c) {
-  if (!c.on) return false;
-  bool progress = false;
-  if (c.ci < kStgChunks) {
-    const uint32_t g = c.g0 + (uint32_t)c.ci, slot = g % kStgSlots, u = g / kStgSlots;
-    if (u == 0 || mbar_test(smem_u32(&S.stg_empty[slot]), (u - 1) & 1u)) {
-      bw_stg_copy<NMB>(p, S, c, c.ci, slot);
-      ++c.ci;
-      progress = true;
-    }
-  }
-  if (c.cc < kStgChunks) {
-    const uint32_t g = c.g0 + (uint32_t)c.cc, slot = g % kStgSlots, u = g / kStgSlots;
-    if (mbar_test(smem_u32(&S.stg_full[slot]), u & 1u)) {
-      bw_stg_convert<NMB>(S, tmem, c.cc, slot);
-      __syncwarp();
-      if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&S.stg_empty[slot]));
-      c.cc += 2;
-      progress = true;
-    }
-  }
-  return progress;
+  if (!c.on || c.cc >= kStgChunks) return false;
+  const uint32_t g = c.g0 + (uint32_t)c.cc, slot = g % kStgSlots, u = g / kStgSlots;
+  if (!mbar_test(smem_u32(&S.stg_full[slot]), u & 1u)) return false;
+  bw_stg_convert<NMB>(S, tmem, c.cc, slot, bw_chunk_pixels(p, c.tx, c.ty, c.half, c.cc));
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&S.stg_empty[slot]));
+  c.cc += 2;
+  return true;
 }
 
 // Bounded wait for a barrier phase that stages while it waits; false on
@@ -872,7 +856,7 @@ template <int NMB>
 __device__ bool bw_stg_finish(const BwParams& p, BwSmem& S, uint32_t tmem, BwStg& c) {
   volatile int* abort = &S.abort;
   const unsigned long long t0 = gtime();
-  while (c.on && (c.ci < kStgChunks || c.cc < kStgChunks)) {
+  while (c.on && c.cc < kStgChunks) {
     if (bw_stg_step<NMB>(p, S, tmem, c)) continue;
     if (*abort) return false;
     if (gtime() - t0 > kWaitNs) {
@@ -1098,6 +1082,55 @@ __device__ bool bw_mma(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint
   }
 }
 
+// warp 26, one thread: the staging ring's copies. Chunk g of the CTA (the
+// chunks of its half tiles after the first, in order) goes to slot
+// g % kStgSlots once the chunk kStgSlots before it there has been converted:
+// one bulk copy of the chunk's valid pixels (8 consecutive pixels of a row,
+// contiguous in the HWC map), completing the slot's barrier with its bytes.
+// Before returning it waits (bounded, whatever the abort word says) until
+// every copy it issued has landed.
+__device__ void bw_copier(const BwParams& p, BwSmem& S) {
+  volatile int* abort = &S.abort;
+  const int N = p.N;
+  uint32_t g = 0;
+  for (int rr = 1;; ++rr) {
+    const int h = fw_half_tile(rr, p.nhalf);
+    if (h < 0) break;
+    int tx, ty, half;
+    bw_tile(p, h, tx, ty, half);
+    bool ok = true;
+    for (int c = 0; c < kStgChunks && ok; ++c, ++g) {
+      const uint32_t slot = g % kStgSlots, u = g / kStgSlots;
+      if (u > 0 && !fw_wait(smem_u32(&S.stg_empty[slot]), (u - 1) & 1u, abort, p.status)) {
+        ok = false;
+        break;
+      }
+      const uint32_t bar = smem_u32(&S.stg_full[slot]);
+      const uint32_t bytes = (uint32_t)bw_chunk_pixels(p, tx, ty, half, c) * (uint32_t)N * 4u;
+      if (bytes) {
+        const int ry = ty * kTile + half * 8 + (c >> 1), rx0 = tx * kTile + (c & 1) * 8;
+        const float* src = p.g_feat + ((size_t)ry * p.cam.W + rx0) * N;
+        asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(S.stg[slot])),
+            "l"(src), "r"(bytes), "r"(bar)
+            : "memory");
+      } else {
+        mbar_arrive(bar);
+      }
+    }
+    if (!ok) break;
+  }
+  // the last use of each slot this thread filled has landed
+  volatile int never = 0;
+  for (uint32_t k = 0; k < kStgSlots && k < g; ++k) {
+    const uint32_t last = g - 1 - k, slot = last % kStgSlots, u = last / kStgSlots;
+    fw_wait(smem_u32(&S.stg_full[slot]), u & 1u, &never, p.status);
+  }
+}
+
 // warps 2-9: accumulators into the feature gradient
 template <int NMB>
 __device__ bool bw_epilogue(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint32_t& ph, uint32_t& nblk,
@@ -1177,7 +1210,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.drain)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.a_full)));
     for (int k = 0; k < kStgSlots; ++k) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.stg_full[k])), "r"(kBwEpi * 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.stg_full[k])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.stg_empty[k])), "r"(kBwEpi / 2));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -1232,7 +1265,6 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
       BwStg stg;
       stg.on = hn >= 0;
       if (stg.on) bw_tile(p, hn, stg.tx, stg.ty, stg.half);
-      stg.ci = 0;
       stg.cc = (warp - kBwWarpEpi) >> 2;
       stg.g0 = gchunks;
       bool ok = bw_epilogue<NMB>(p, S, tmem, s, ph, nblk, stg);
@@ -1258,7 +1290,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
       if (warp == kBwWarpEpi && lane == 0) mbar_arrive(smem_u32(&S.a_full));
       gchunks += kStgChunks;
     }
-  } else {
+  } else if (warp < kBwWarpCopy) {
     for (int rr = 0;; ++rr) {
       const int h = fw_half_tile(rr, p.nhalf);
       if (h < 0) break;
@@ -1266,8 +1298,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
       bw_tile(p, h, tx, ty, half);
       if (!bw_builder(p, S, tx, ty, half, s, ph)) break;
     }
+  } else if (lane == 0) {
+    bw_copier(p, S);
   }
-  // every thread's copies have landed (the epilogue warps' staging, warp 0's records)
+  // every thread's copies have landed (warp 0's records; the copier waited for its own)
   asm volatile("cp.async.wait_all;" ::: "memory");
   if (warp == kBwWarpMma && lane == 0) {
     // every product issued has completed before tensor memory is freed
@@ -1312,6 +1346,8 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* range
   if (N <= 0 || N % 128 != 0 || N > kTcMaxN) return GS_ERR_UNSUPPORTED;
   // the vector atomics of the epilogue need NMB * 4-byte alignment of every row
   if ((reinterpret_cast<uintptr_t>(d_feats) & 15u) != 0) return GS_ERR_INVALID_ARG;
+  // the staging's bulk copies start on 16-byte boundaries
+  if ((reinterpret_cast<uintptr_t>(g_feat) & 15u) != 0) return GS_ERR_INVALID_ARG;
   BwParams p;
   p.P = P;
   p.cam = cam;
