@@ -671,6 +671,11 @@ struct alignas(16) BwStage {
 
 constexpr int kStgSlots = 4;   // cotangent staging ring (chunks of 8 pixels)
 constexpr int kStgChunks = 16;  // chunks per half tile
+// The two converting warp sets take alternate chunks (and kStgChunks is
+// even), so with an even slot count every slot is converted by one set, in
+// order: a converter never tests a slot's barrier one use ahead of a copy
+// still in flight, which would alias its phase parity.
+static_assert(kStgSlots % 2 == 0 && kStgChunks % 2 == 0, "each staging slot belongs to one converting set");
 
 struct BwSmem {
   uint8_t A[kTcMaxN * kTcPix * 2];  // dF^T, 128 KB for N = 512
