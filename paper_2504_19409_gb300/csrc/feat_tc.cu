@@ -607,21 +607,26 @@ gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, co
 // Per half tile and block of 32 Gaussians, transposed so that every operand
 // keeps a validated layout:
 //     D [N channels x 32 Gaussians] = dF^T [N x 128 px] * W [128 px x 32]
-//   A = dF^T, K-major, bf16, NMB = N/128 M-blocks; channel c sits in M-block
-//       c % NMB, row r = c / NMB, so that a tensor-memory lane r holds the
-//       NMB contiguous channels NMB r .. and the epilogue adds them with one
-//       vector atomic:
+//   A = dF^T, bf16, NMB = N/128 M-blocks; channel c sits in M-block c % NMB,
+//       row r = c / NMB, so that a tensor-memory lane r holds the NMB
+//       contiguous channels NMB r .. and the epilogue adds them with one
+//       vector atomic. Staged in shared memory, K-major:
 //       element (mb, r, p) at mb*32768 + (r/8)*2048 + (p/8)*128 + (r%8)*16 + (p%8)*2
-//       descriptor LBO = 128 (K = pixels), SBO = 2048 (M = channel rows)
+//       and copied from there into tensor memory (tcgen05.cp, 128 rows x 32
+//       bytes per M-block and 16 pixels; descriptor LBO = 128, SBO = 2048):
+//       row r in lane r, pixels p, p + 1 in column A0 + 64 mb + p / 2, where
+//       the products read it (A0 = 64 NMB, after the accumulators);
 //   B = W, MN-major (Gaussians contiguous for a pixel):
 //       element (p, g) at (g/8)*128 + (p/8)*512 + (p%8)*16 + (g%8)*2
 //       descriptor LBO = 512 (K = pixels), SBO = 128 (N = Gaussians)
 // The kernel is persistent (one CTA per SM, the forward's list of half
-// tiles). Each half tile starts with dF^T in A: the first one staged by every
-// warp from global memory (the fp32 cotangents of its 128 pixels, eight
-// 16-byte loads in flight per thread, rounded to bf16), every later one
-// copied in from tensor memory, where the epilogue warps left it while the
-// previous half tile ran (see below); the roles run over the blocks of the
+// tiles). Each half tile's dF^T is staged in shared memory: the first one by
+// every warp from global memory (the fp32 cotangents of its 128 pixels,
+// eight 16-byte loads in flight per thread, rounded to bf16), every later
+// one by the epilogue warps while the previous half tile ran (see below).
+// At the start of a half tile the MMA thread copies it into tensor memory
+// (its products are ordered after the copies) and the copies' commit frees
+// shared memory for the next staging. The roles run over the blocks of the
 // compacted lists (the Gaussians whose skip mask reaches the half tile) of
 // all the CTA's half tiles without a CTA-wide barrier between half tiles, so
 // the producer and builders run up to the ring's depth ahead across them:
@@ -629,25 +634,24 @@ gs_status launch_render_fwd_tc(const CamF& cam, int P, const int32_t* ranges, co
 //     cp.async into a 3-deep ring;
 //   warps 10-25 (builders, 4 threads per pixel): W as in the forward, and
 //     the bits of the block's Gaussians that weigh something here;
-//   warp 1 (one thread): NMB x 8 tcgen05.mma (M=128, N=32, K=16) per block
-//     into one of two tensor-memory accumulators;
+//   warp 1 (one thread): per half tile the copies of A, then per block
+//     NMB x 8 tcgen05.mma (M=128, N=32, K=16, A from tensor memory) into one
+//     of two tensor-memory accumulators;
 //   warps 2-9 (epilogue; lanes 32 (w % 4).., Gaussians 16 (w >= 6)..+15):
 //     the accumulator into registers, then one vector atomic per (Gaussian,
 //     lane) into d_feats for the Gaussians that weigh something. While they
 //     wait for the products they stage the NEXT half tile's cotangents: 16
 //     chunks of 8 pixels (one row segment, all N channels, fp32) arrive in a
-//     4-slot shared-memory ring, and per chunk one set of four warps (one per
-//     tensor-memory lane quarter) rounds it to bf16 and stores it with
-//     tcgen05.st into the tensor-memory columns the accumulators leave free
-//     (lane = row r of the M-blocks, column = staging base + mb * 64 +
-//     pixel / 2, two pixels per 32-bit column);
+//     4-slot shared-memory ring, and per chunk one set of four warps (rows
+//     32 (w % 4) ..) rounds it to bf16 into A once the copy of the current
+//     half tile's A has completed. After a half tile's last block (whose
+//     completion implies every product of the half tile has read A) they
+//     signal the MMA thread, which copies the staged A in before the next
+//     half tile's first product;
 //   warp 26 (one thread, the copier): each chunk (8 consecutive pixels of a
 //     row, contiguous in the HWC map) by one bulk copy into its slot as soon
 //     as the slot's previous chunk has been converted; the copy's bytes
-//     complete the slot's barrier. After a half tile's last block (whose completion
-//     implies every product of the half tile has read A) the epilogue warps
-//     move it into A and signal the MMA thread, which waits for that before
-//     the next half tile's first product.
+//     complete the slot's barrier.
 // Every wait is bounded (1 s); a timeout flags GS_ERR_TIMEOUT and raises the
 // abort word, on which every role stops.
 namespace {
@@ -686,7 +690,8 @@ struct BwSmem {
   int cpos[64];
   unsigned long long full[kBwStages], ready[kBwStages], empty[kBwStages];
   unsigned long long done[2], dfree[2], drain;
-  unsigned long long a_full;  // the epilogue warps have moved the next half tile's dF^T into A
+  unsigned long long a_full;  // the epilogue warps have staged the next half tile's dF^T in A (shared)
+  unsigned long long a_free;  // the tensor core has copied A into tensor memory (A may be overwritten)
   uint32_t tmem;
   int abort;
 };
@@ -771,6 +776,8 @@ struct BwStg {
   int tx, ty, half;  // the next half tile
   int cc;            // next chunk this warp converts (its set's chunks: cc = set, set + 2, ..)
   uint32_t g0;
+  bool afree;        // the current half tile's A has been copied out of shared memory
+  uint32_t apar;     // parity of that copy's a_free phase
 };
 
 // Pixels of chunk c of a half tile that lie in the image (the chunk's first
@@ -780,10 +787,12 @@ __device__ __forceinline__ int bw_chunk_pixels(const BwParams& p, int tx, int ty
   return ry < p.cam.H ? max(0, min(8, p.cam.W - rx0)) : 0;
 }
 
-// chunk -> bf16 -> tensor memory, by the warp of lane quarter (warp % 4);
-// pixels past the chunk's nv valid ones (not copied) are zero
+// chunk -> bf16 -> A in shared memory (the next half tile's dF^T), by the
+// warp of lane quarter (warp % 4), rows r = 32 (warp % 4) + lane; chunk c
+// holds the half tile's pixels 8 c .. 8 c + 7, one 16-byte core-matrix row per
+// (M-block, r); pixels past the chunk's nv valid ones are zero
 template <int NMB>
-__device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chunk, uint32_t slot, int nv) {
+__device__ __forceinline__ void bw_stg_convert(BwSmem& S, int chunk, uint32_t slot, int nv) {
   constexpr int N = NMB * 128;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = 32 * (warp & 3) + lane;  // row: channels NMB r .. NMB r + NMB - 1
@@ -806,8 +815,7 @@ __device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chu
       for (int mb = 0; mb < NMB; ++mb) v[e][mb] = q[mb];
     }
   }
-  const uint32_t col0 = (uint32_t)(NMB * 64) + (uint32_t)((chunk >> 1) * 8 + (chunk & 1) * 4);
-  const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + col0;
+  uint8_t* dst = S.A + (r >> 3) * 2048 + chunk * 128 + (r & 7) * 16;
 #pragma unroll
   for (int mb = 0; mb < NMB; ++mb) {
     uint32_t w[4];
@@ -816,11 +824,8 @@ __device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chu
       const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * k][mb], v[2 * k + 1][mb]);
       w[k] = *reinterpret_cast<const uint32_t*>(&b2);
     }
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta + (uint32_t)(mb * 64)),
-                 "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
-                 : "memory");
+    *reinterpret_cast<uint4*>(dst + mb * 32768) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // One round of staging work that needs no waiting: convert this warp's next
@@ -828,9 +833,14 @@ __device__ __forceinline__ void bw_stg_convert(BwSmem& S, uint32_t tmem, int chu
 template <int NMB>
 __device__ bool bw_stg_step(const BwParams& p, BwSmem& S, uint32_t tmem, BwStg& c) {
   if (!c.on || c.cc >= kStgChunks) return false;
+  // A is overwritten only after the tensor core has copied the current half tile's out
+  if (!c.afree) {
+    if (!mbar_test(smem_u32(&S.a_free), c.apar)) return false;
+    c.afree = true;
+  }
   const uint32_t g = c.g0 + (uint32_t)c.cc, slot = g % kStgSlots, u = g / kStgSlots;
   if (!mbar_test(smem_u32(&S.stg_full[slot]), u & 1u)) return false;
-  bw_stg_convert<NMB>(S, tmem, c.cc, slot, bw_chunk_pixels(p, c.tx, c.ty, c.half, c.cc));
+  bw_stg_convert<NMB>(S, c.cc, slot, bw_chunk_pixels(p, c.tx, c.ty, c.half, c.cc));
   __syncwarp();
   if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&S.stg_empty[slot]));
   c.cc += 2;
@@ -871,28 +881,6 @@ __device__ bool bw_stg_finish(const BwParams& p, BwSmem& S, uint32_t tmem, BwStg
     }
   }
   return true;
-}
-
-// The epilogue warps: the staged dF^T from tensor memory into A (warp w
-// moves lanes 32 (w % 4) .., items (M-block, 16-pixel group) dealt over the
-// two epilogue warps of its lane quarter).
-template <int NMB>
-__device__ __forceinline__ void bw_copy_staged(BwSmem& S, uint32_t tmem) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, qd = warp & 3;
-  const int j = (warp - kBwWarpEpi) >> 2, nw = kBwEpi / 4;
-  const int r = 32 * qd + lane;
-  const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(NMB * 64);
-  for (int it = j; it < NMB * 8; it += nw) {
-    const int mb = it >> 3, pg2 = it & 7;
-    float f[8];
-    tmem_ld8(ta + (uint32_t)(mb * 64 + pg2 * 8), f);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    uint8_t* dst = S.A + mb * 32768 + (r >> 3) * 2048 + (2 * pg2) * 128 + (r & 7) * 16;
-    *reinterpret_cast<uint4*>(dst) =
-        make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]), __float_as_uint(f[3]));
-    *reinterpret_cast<uint4*>(dst + 128) =
-        make_uint4(__float_as_uint(f[4]), __float_as_uint(f[5]), __float_as_uint(f[6]), __float_as_uint(f[7]));
-  }
 }
 
 // warp 0: compaction and records of one half tile's blocks; returns false on abort
@@ -1052,7 +1040,7 @@ template <int NMB>
 __device__ bool bw_mma(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint32_t& ph, uint32_t& nblk) {
   volatile int* abort = &S.abort;
   constexpr uint32_t dcols = (uint32_t)(NMB * kTbG);
-  const uint32_t a0 = smem_u32(S.A);
+  const uint32_t a0 = tmem + (uint32_t)(NMB * 64);  // A in tensor memory
   while (true) {
     if (!fw_wait(smem_u32(&S.ready[s]), ph, abort, p.status)) return false;
     BwStage& st = S.st[s];
@@ -1066,14 +1054,14 @@ __device__ bool bw_mma(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint
     for (int mb = 0; mb < NMB; ++mb) {
 #pragma unroll
       for (int k16 = 0; k16 < kTcPix / 16; ++k16) {
-        const uint64_t ad = smem_desc(a0 + (uint32_t)mb * 32768u + (uint32_t)k16 * 256u, 128, 2048);
+        const uint32_t at = a0 + (uint32_t)(mb * 64 + k16 * 8);
         const uint64_t bd = smem_desc(b0 + (uint32_t)k16 * 1024u, 512, 128);
         const uint32_t acc = k16 > 0 ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(
                 tmem + buf * dcols + (uint32_t)(mb * kTbG)),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            "r"(at), "l"(bd), "r"(idesc), "r"(acc));
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -1214,6 +1202,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.drain)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.a_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.a_free)));
     for (int k = 0; k < kStgSlots; ++k) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.stg_full[k])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.stg_empty[k])), "r"(kBwEpi / 2));
@@ -1256,9 +1245,23 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
       volatile int* abort = &S.abort;
       for (int rr = 0;; ++rr) {
         if (fw_half_tile(rr, p.nhalf) < 0) break;
-        // this half tile's dF^T is in A
+        // this half tile's dF^T is in A (shared memory); the previous half
+        // tile's products, which read A in tensor memory, have completed (the
+        // epilogue signals a_full after its last block's completion)
         if (rr > 0 && !fw_wait(smem_u32(&S.a_full), (uint32_t)(rr - 1) & 1u, abort, p.status)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // A -> tensor memory: per M-block and 16 pixels, 128 rows x 32 bytes;
+        // the products that follow are ordered after these copies
+        const uint32_t as = smem_u32(S.A);
+#pragma unroll 1
+        for (int mb = 0; mb < NMB; ++mb)
+#pragma unroll
+          for (int k16 = 0; k16 < kTcPix / 16; ++k16)
+            asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(tmem + (uint32_t)(NMB * 64 + mb * 64 +
+                                                                                            k16 * 8)),
+                         "l"(smem_desc(as + (uint32_t)mb * 32768u + (uint32_t)k16 * 256u, 128, 2048)));
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&S.a_free)));
         if (!bw_mma<NMB>(p, S, tmem, s, ph, nblk)) break;
       }
     }
@@ -1272,11 +1275,16 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
       if (stg.on) bw_tile(p, hn, stg.tx, stg.ty, stg.half);
       stg.cc = (warp - kBwWarpEpi) >> 2;
       stg.g0 = gchunks;
+      stg.afree = false;
+      stg.apar = (uint32_t)rr & 1u;
       bool ok = bw_epilogue<NMB>(p, S, tmem, s, ph, nblk, stg);
       if (ok) ok = bw_stg_finish<NMB>(p, S, tmem, stg);
-      // every epilogue warp has staged its chunks and read its accumulators;
-      // the last block's completion means every product of this half tile has
-      // read A. The decision to stop is taken together (a barrier reduction).
+      // every epilogue warp has staged its chunks into A and read its
+      // accumulators; the last block's completion means every product of this
+      // half tile has completed. This thread's writes to A are made visible to
+      // the tensor core's copy; the decision to stop is taken together (a
+      // barrier reduction, which also joins the warps before a_full).
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       int stop;
       asm volatile(
@@ -1285,13 +1293,6 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
           : "r"((int)(!ok || S.abort || hn < 0)), "n"(kBwEpi * 32)
           : "memory");
       if (stop) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      bw_copy_staged<NMB>(S, tmem);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      asm volatile("bar.sync 1, %0;" ::"n"(kBwEpi * 32) : "memory");
-      // the next staging's tensor-memory stores come after every warp's loads
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (warp == kBwWarpEpi && lane == 0) mbar_arrive(smem_u32(&S.a_full));
       gchunks += kStgChunks;
     }

@@ -97,15 +97,18 @@ def test_tc_rejects_unsupported_shapes(gs, sg):
 
 @pytest.mark.parametrize("N,shape,P,seed", [(256, (96, 64), 1200, 31), (512, (100, 37), 900, 33),
                                              (128, (64, 48), 700, 34), (384, (72, 40), 800, 35),
-                                             (512, (400, 300), 6000, 36), (384, (400, 300), 6000, 37)])
+                                             (512, (400, 300), 6000, 36), (384, (410, 300), 6000, 37)])
 def test_tc_feature_gradient_within_bound(gs, ora, sg, N, shape, P, seed):
     """Decoupled feature gradient on tcgen05 within the adjoint bound of the
     module docstring; the geometry gradients equal the fp32 path's
     (tolerance 1e-5). Every channel-block count (N / 128 = 1..4) and a
-    ragged image are covered. The 400 x 300 cases have 950 half tiles, more
-    than one per CTA, so every half tile after a CTA's first takes its
-    cotangents from the tensor-memory staging (the last tile row is 12
-    pixels tall: its lower half tiles stage 4 rows and 4 zero rows)."""
+    ragged image are covered. The 400 x 300 and 410 x 300 cases have 950 and
+    988 half tiles, more than one per CTA, so every half tile after a CTA's
+    first takes its cotangents through the staging ring (one bulk copy per
+    8-pixel row chunk): the last tile row is 12 pixels tall, so its lower
+    half tiles have 4 rows of chunks with no pixel in the image (nothing
+    copied, zeros converted), and at 410 pixels the last tile column is 10
+    wide, so its second chunk of each row copies 2 pixels and zeros 6."""
     cam = sg.identity_camera(shape[0], shape[1], 0.73 * shape[0]).as_f32()
     sc = sg.frustum_scene(seed, P, cam, N)
     sc.feats = (sc.feats / np.linalg.norm(sc.feats, axis=1, keepdims=True)).astype(np.float32)
