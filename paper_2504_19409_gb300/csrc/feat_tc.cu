@@ -1080,8 +1080,10 @@ __device__ bool bw_mma(const BwParams& p, BwSmem& S, uint32_t tmem, int& s, uint
 // g % kStgSlots once the chunk kStgSlots before it there has been converted:
 // one bulk copy of the chunk's valid pixels (8 consecutive pixels of a row,
 // contiguous in the HWC map), completing the slot's barrier with its bytes.
-// Before returning it waits (bounded, whatever the abort word says) until
-// every copy it issued has landed.
+// The copies carry an L2 evict-first policy: the cotangents are read once, and
+// the feature-gradient rows that the epilogue's atomics keep updating should
+// stay in L2. Before returning it waits (bounded, whatever the abort word
+// says) until every copy it issued has landed.
 __device__ void bw_copier(const BwParams& p, BwSmem& S) {
   volatile int* abort = &S.abort;
   const int N = p.N;
@@ -1106,8 +1108,9 @@ __device__ void bw_copier(const BwParams& p, BwSmem& S) {
         asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                      : "memory");
         asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(S.stg[slot])),
+            "{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], pol;"
+            "\n\t}\n" ::"r"(smem_u32(S.stg[slot])),
             "l"(src), "r"(bytes), "r"(bar)
             : "memory");
       } else {
