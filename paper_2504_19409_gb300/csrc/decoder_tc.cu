@@ -29,7 +29,9 @@
 // columns for the whole sample set, so it cannot share the first kernel's.
 //
 // Rounding: z, H, dY and dPRE enter the products as bf16 (unit roundoff
-// 2^-8), the weights are bf16-exact by contract, every sum is fp32.
+// 2^-8), the weights are bf16-exact by contract, every sum is fp32. GELU and
+// its derivative take erf from Abramowitz & Stegun 7.1.26 (absolute error at
+// most 1.5e-7) with one exponential shared with the normal density.
 
 #include <atomic>
 #include <cstddef>
@@ -43,6 +45,7 @@ constexpr int kDtThreads = 512;
 constexpr int kDtS = 128;             // samples per tile
 constexpr uint32_t kCs = 144;         // bytes between 8-column groups of the transposed operands
 constexpr uint32_t kRs = 16 * kCs;    // bytes between 8-row groups of a 128-column transposed operand
+static_assert(kDtThreads == 4 * kDtS, "the gather takes four threads per sample");
 
 struct DtSmem {
   uint8_t W2T[512 * 128 * 2];  // (o, h) at (o/8)*2048 + (h/8)*128 + (o%8)*16 + (h%8)*2
@@ -157,41 +160,31 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_decoder_train_tc(const DtPara
   };
   for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const long long s0 = t * kDtS;
-    // gather: sample row s -> Z (s, d) and ZT1 (d, s)
-    if (tid < kDtS) {
-      const int s = tid;
+    // gather: sample row s -> Z (s, d) and ZT1 (d, s), four threads per
+    // sample (latents 4 c .. 4 c + 3 each)
+    {
+      const int s = tid >> 2, c = tid & 3;
       const long long gs = s0 + s;
       const long long pix = gs < p.nsample ? decoder_sample_pixel(p.seed, gs, p.npix) : -1;
-      S.pix[s] = pix;
-      // the sample's 2 KB target row into L2 now: the loss epilogues read it
-      // after the first two products, 32 outputs per thread at a time
+      if (c == 0) S.pix[s] = pix;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
       if (pix >= 0) {
+        // the sample's 2 KB target row into L2 now: the loss epilogues read it
+        // after the first two products, 32 outputs per thread at a time
 #pragma unroll
-        for (int c = 0; c < 16; ++c) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.target + pix * 512 + 32 * c));
+        for (int k = 0; k < 4; ++k)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.target + pix * 512 + 32 * (4 * c + k)));
+        a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 4 * c);
       }
-      float v[16];
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(a.x, a.y), hi = __floats2bfloat162_rn(a.z, a.w);
+      *reinterpret_cast<uint2*>(S.Z + (s >> 3) * 256 + (c >> 1) * 128 + (s & 7) * 16 + (c & 1) * 8) =
+          make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+      const float v[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-      for (int d = 0; d < 16; ++d) v[d] = 0.f;
-      if (pix >= 0) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float4 a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 4 * c);
-          v[4 * c] = a.x, v[4 * c + 1] = a.y, v[4 * c + 2] = a.z, v[4 * c + 3] = a.w;
-        }
+      for (int k = 0; k < 4; ++k) {
+        const int d = 4 * c + k;
+        st_bf16(S.ZT1, (uint32_t)((d >> 3) * kRs + (s >> 3) * kCs + (d & 7) * 16 + (s & 7) * 2), v[k]);
       }
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        uint32_t pk[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * c + 2 * i], v[8 * c + 2 * i + 1]);
-          pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
-        }
-        *reinterpret_cast<uint4*>(S.Z + (s >> 3) * 256 + c * 128 + (s & 7) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      }
-#pragma unroll
-      for (int d = 0; d < 16; ++d)
-        st_bf16(S.ZT1, (uint32_t)((d >> 3) * kRs + (s >> 3) * kCs + (d & 7) * 16 + (s & 7) * 2), v[d]);
     }
     before_sync();
     __syncthreads();
@@ -209,7 +202,7 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_decoder_train_tc(const DtPara
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const int h = 32 * cq + i;
-        const __nv_bfloat16 hb = __float2bfloat16_rn(gelu_exact(v[i] + S.b1[h]));
+        const __nv_bfloat16 hb = __float2bfloat16_rn(gelu_as(v[i] + S.b1[h]));
         *reinterpret_cast<__nv_bfloat16*>(S.HT + (h >> 3) * kRs + (s >> 3) * kCs + (h & 7) * 16 + (s & 7) * 2) = hb;
         p.HTg[(size_t)h * p.s_pad + s0 + s] = hb;
       }
@@ -284,8 +277,8 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_decoder_train_tc(const DtPara
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int j = 8 * c + 2 * i, h = 32 * cq + j;
-          const float x0 = dh[j] * gelu_grad_exact(pre[j] + S.b1[h]);
-          const float x1 = dh[j + 1] * gelu_grad_exact(pre[j + 1] + S.b1[h + 1]);
+          const float x0 = dh[j] * gelu_grad_as(pre[j] + S.b1[h]);
+          const float x1 = dh[j + 1] * gelu_grad_as(pre[j + 1] + S.b1[h + 1]);
           const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
           pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
         }
