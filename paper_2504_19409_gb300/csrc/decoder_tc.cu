@@ -218,18 +218,19 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_decoder_train_tc(const DtPara
       mma_commit(mbar);
     }
     for (int q = 0; q < 4; ++q) {
+      // E2: row = output o' of quarter q, columns s = 32 cq ..; the targets
+      // are loaded before the wait for the products, under it
+      const int o = 128 * q + row;
+      float tg[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const long long pix = S.pix[32 * cq + i];
+        tg[i] = pix >= 0 ? __ldg(p.target + pix * 512 + o) : 0.f;
+      }
       if (!wait_mma()) break;
-      // E2: row = output o' of quarter q, columns s = 32 cq ..
       {
-        const int o = 128 * q + row;
         float v[32];
         tmem_ld32(tmem + lane_off + cD2 + 128 * (q & 1) + 32 * cq, v);
-        float tg[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const long long pix = S.pix[32 * cq + i];
-          tg[i] = pix >= 0 ? __ldg(p.target + pix * 512 + o) : 0.f;
-        }
         const float b = S.b2[o];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
