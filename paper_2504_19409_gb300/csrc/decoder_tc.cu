@@ -158,24 +158,32 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_decoder_train_tc(const DtPara
     if (ok) after_sync();
     return ok;
   };
+  // gather: sample row s of tile tt -> its pixel and latents 4 c .. 4 c + 3,
+  // four threads per sample; issued one tile ahead (under the previous tile's
+  // last products), with the sample's 2 KB target row prefetched into L2 for
+  // the loss epilogues
+  const int gs_s = tid >> 2, gs_c = tid & 3;
+  auto fetch = [&](long long tt, long long& pix, float4& a) {
+    const long long gs = tt * kDtS + gs_s;
+    pix = (tt < ntiles && gs < p.nsample) ? decoder_sample_pixel(p.seed, gs, p.npix) : -1;
+    a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pix >= 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p.target + pix * 512 + 32 * (4 * gs_c + k)));
+      a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 4 * gs_c);
+    }
+  };
+  long long pix_n;
+  float4 a_n;
+  fetch(blockIdx.x, pix_n, a_n);
   for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const long long s0 = t * kDtS;
-    // gather: sample row s -> Z (s, d) and ZT1 (d, s), four threads per
-    // sample (latents 4 c .. 4 c + 3 each)
+    // the fetched sample rows -> Z (s, d) and ZT1 (d, s)
     {
-      const int s = tid >> 2, c = tid & 3;
-      const long long gs = s0 + s;
-      const long long pix = gs < p.nsample ? decoder_sample_pixel(p.seed, gs, p.npix) : -1;
-      if (c == 0) S.pix[s] = pix;
-      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (pix >= 0) {
-        // the sample's 2 KB target row into L2 now: the loss epilogues read it
-        // after the first two products, 32 outputs per thread at a time
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(p.target + pix * 512 + 32 * (4 * c + k)));
-        a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 4 * c);
-      }
+      const int s = gs_s, c = gs_c;
+      if (c == 0) S.pix[s] = pix_n;
+      const float4 a = a_n;
       const __nv_bfloat162 lo = __floats2bfloat162_rn(a.x, a.y), hi = __floats2bfloat162_rn(a.z, a.w);
       *reinterpret_cast<uint2*>(S.Z + (s >> 3) * 256 + (c >> 1) * 128 + (s & 7) * 16 + (c & 1) * 8) =
           make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
@@ -302,6 +310,9 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_decoder_train_tc(const DtPara
       }
       mma_commit(mbar);
     }
+    // the next tile's sample rows, under these products (Z and ZT1 are
+    // rewritten only after them)
+    fetch(t + gridDim.x, pix_n, a_n);
     if (!wait_mma()) break;
     // E4: dZ to the sampled pixels (column quarter 0 holds its 16 columns);
     // dW1x rows 0-16 (lane group 0) to dW1 and db1
