@@ -622,14 +622,16 @@ gs_status gs_peak_probe(int32_t kind, int32_t blocks, int32_t threads, int32_t i
 /* ---------------------------------------------------------------------------
  * gs_test_hold_tc_producer -- test hook of the bounded waits (failure
  * detection; the paper has no counterpart). While `on` is nonzero, the
- * tensor-core feature forward (gs_render_fwd with GS_FEAT_TENSOR_CORE) runs
- * with its producer warps idle: no stage is ever filled, so every other
- * role's mbarrier wait runs out after its bound (1 s of %globaltimer). The
- * launch then ORs 1 << GS_ERR_TIMEOUT into the status word, frees its tensor
- * memory and returns; the feature map is unspecified, everything else the
- * call writes is as usual. Nothing is copied or issued to the tensor core
- * before the waits give up, so the context stays usable. Process-wide, read
- * at each launch; not for use while other threads render. Returns GS_OK.
+ * tensor-core feature kernels (gs_render_fwd and gs_render_bwd with
+ * GS_FEAT_TENSOR_CORE) run with their producer warps idle: no stage of
+ * records is ever filled, so the other roles' mbarrier waits run out after
+ * their bound (1 s of %globaltimer). The launch then ORs 1 << GS_ERR_TIMEOUT
+ * into the status word, waits for the copies it issued, frees its tensor
+ * memory and returns; the feature map (forward) or the feature gradient
+ * (adjoint) is unspecified, everything else the call writes is as usual. No
+ * product is issued before the waits give up, so the context stays usable.
+ * Process-wide, read at each launch; not for use while other threads render.
+ * Returns GS_OK.
  */
 gs_status gs_test_hold_tc_producer(int32_t on);
 

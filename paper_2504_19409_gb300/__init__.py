@@ -94,8 +94,8 @@ def zero_(t, stream=None):
 
 
 def hold_tc_producer(on):
-    """gs_test_hold_tc_producer: while on, the tensor-core forward's producer warps stay idle, so its
-    bounded waits run out (the launch flags GS_ERR_TIMEOUT and returns); a failure-detection test hook."""
+    """gs_test_hold_tc_producer: while on, the tensor-core feature kernels' producer warps stay idle, so
+    their bounded waits run out (the launch flags GS_ERR_TIMEOUT and returns); a failure-detection test hook."""
     _check(lib().gs_test_hold_tc_producer(1 if on else 0), "gs_test_hold_tc_producer")
 
 

@@ -712,6 +712,7 @@ struct BwParams {
   int N, tmem_cols, nhalf;
   int P;  // Gaussians (bound of the checked build's id checks)
   float* d_feats;  // [P, N]
+  int hold;  // test hook: the producer issues nothing, so the other roles' waits run out
   int32_t* status;
 };
 
@@ -1236,7 +1237,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_render_feat_tc_bwd(const BwPa
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    for (int rr = 0;; ++rr) {
+    for (int rr = 0; !p.hold; ++rr) {
       const int h = fw_half_tile(rr, p.nhalf);
       if (h < 0) break;
       int tx, ty, half;
@@ -1375,6 +1376,7 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* range
   p.tmem_cols = cols;
   p.nhalf = 2 * cam.tiles_x * cam.tiles_y;
   p.d_feats = d_feats;
+  p.hold = g_tc_hold.load();
   p.status = status;
   switch (N / 128) {
     case 1: return launch_bwd_nmb<1>(p, st);

@@ -233,8 +233,8 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* range
                                     const uint32_t* gids, const uint8_t* masks, const float* uv, const float* co,
                                     const int32_t* last_idx, const float* g_feat, int N, float* d_feats,
                                     int32_t* status, cudaStream_t st);
-// Test hook of the tensor-core forward's bounded waits (feat_tc.cu): while
-// set, its producer warps issue nothing.
+// Test hook of the tensor-core feature kernels' bounded waits (feat_tc.cu):
+// while set, their producer warps issue nothing.
 void set_tc_test_hold(int on);
 
 }  // namespace gsff
