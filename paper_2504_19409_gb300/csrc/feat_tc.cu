@@ -1393,34 +1393,41 @@ gs_status launch_render_bwd_feat_tc(const CamF& cam, int P, const int32_t* range
 //   h = gelu(D1 + b1) -> bf16 -> shared memory (A operand of the next product)
 //   D2 [128 x 512] = h [128 x 128] * W2 [128 x 512]      (2 x 8 MMAs, N = 256)
 //   y = D2 + b2 -> fp32 rows [128 x 512]
-// Persistent CTAs (one per SM, 512 threads) keep W1 and W2 in shared memory
-// as bf16. Layouts (validated rule: LBO along K, SBO along M/N):
+// Persistent CTAs (one per SM) keep W1 and W2 in shared memory as bf16.
+// Layouts (validated rule: LBO along K, SBO along M/N):
 //   A1 z  : (m/8)*256  + (k/8)*128 + (m%8)*16 + (k%8)*2   LBO 128, SBO 256
 //   B1 W1 : (n/8)*128  + (k/8)*2048 + (k%8)*16 + (n%8)*2  LBO 2048, SBO 128
 //   A2 h  : (m/8)*2048 + (k/8)*128 + (m%8)*16 + (k%8)*2   LBO 128, SBO 2048
 //   B2 W2 : (n/8)*128  + (k/8)*8192 + (k%8)*16 + (n%8)*2  LBO 8192, SBO 128
-// D1 occupies tensor-memory columns [0, 128) and is overwritten by D2
-// (columns [0, 512)) once read.
-// Epilogue: warp w (tensor-memory lanes 32 (w % 4).., columns 128 (w / 4)..)
-// adds b2 to 32 x 32 blocks of D2 and writes each into its own 4 KB box in
-// shared memory in the 128-byte swizzled order (16-byte chunk q of box row r
-// at chunk q ^ (r % 8): conflict-free stores), then stores the box with one
-// TMA tensor store. The tensor map clips rows past npix. The 16 boxes reuse
-// H (free once D2 is complete) and the 32 KB after it, from a 1024-byte
-// boundary.
+// Tensor memory: D1 in columns [0, 128), then D2 in [0, 512): half a
+// (outputs 0-255) in [0, 256), half b in [256, 512). Roles, so that a tile's
+// drain overlaps the next tile's work:
+//   warps 0-7 (group A): the gather of z, the GELU into H, then the drain of
+//     half a; then, with half a free, the next tile's gather and GELU while
+//     group B still drains half b;
+//   warps 8-15 (group B): the drain of half b;
+//   warp 16 (one thread): the products: G1 when z is in, G2a when H is, G2b
+//     once group B has released half b of the previous tile.
+// A drain warp (lanes 32 (w % 4).., 128 columns of its group's half) adds b2
+// to 16 columns at a time and writes them into its own 2 KB box in the 64-byte
+// swizzled order (16-byte chunk q of box row r at chunk q ^ ((r / 2) % 4):
+// conflict-free stores), then stores the box with one TMA tensor store (the
+// tensor map clips rows past npix). Every wait is bounded (1 s); a group takes
+// each decision to stop together (a barrier reduction).
 namespace {
 
 struct DecSmem {
-  uint8_t W2[128 * 512 * 2];   // 128 KB
-  uint8_t H[128 * 128 * 2];    // 32 KB; also the first half of the output boxes
-  uint8_t Ybox[128 * 128 * 2 + 1024];  // second half of the boxes (+ room to align them)
-  uint8_t W1[16 * 128 * 2];    // 4 KB
-  uint8_t Z[128 * 16 * 2];     // 4 KB
+  uint8_t W2[128 * 512 * 2];            // 128 KB
+  uint8_t H[128 * 128 * 2];             // 32 KB
+  uint8_t Ybox[16 * 2048 + 1024];       // one 2 KB output box per drain warp (+ room to align them)
+  uint8_t W1[16 * 128 * 2];             // 4 KB
+  uint8_t Z[128 * 16 * 2];              // 4 KB
   float b1[128];
   float b2[512];
-  unsigned long long mbar;
+  unsigned long long z_ready, d1_full, h_ready, d2a_full, d2b_full, b_free, drain;
   uint32_t tmem;
 };
+constexpr int kDecThreads = 32 * 17;  // two drain groups of 8 warps and the MMA warp
 
 struct DecTcParams {
   long long npix;
@@ -1433,34 +1440,44 @@ struct DecTcParams {
   int32_t* status;
 };
 
-__global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p,
-                                                           const __grid_constant__ CUtensorMap ymap) {
+// All 256 threads of drain group g (named barrier 1 + g) agree on v.
+__device__ __forceinline__ bool dec_group_and(bool v, int g) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, r;\n\tsetp.ne.b32 q, %1, 0;\n\tbar.red.and.pred r, %2, 256, q;\n\tselp.u32 %0, 1, 0, r;\n\t}\n"
+      : "=r"(r)
+      : "r"((int)v), "r"(1 + g)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(kDecThreads, 1) k_decoder_fwd_tc(const DecTcParams p,
+                                                                   const __grid_constant__ CUtensorMap ymap) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   DecSmem& S = *reinterpret_cast<DecSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lg = warp & 3, cq = warp >> 2;  // tensor-memory lane group, column quarter
-  const int row = 32 * lg + lane;           // pixel row of the tile this thread reads back
 
   // weights -> bf16 operands (once per CTA)
-  for (int e = tid; e < 128 * 512; e += 512) {
+  for (int e = tid; e < 128 * 512; e += kDecThreads) {
     const int k = e / 512, n = e % 512;
     *reinterpret_cast<__nv_bfloat16*>(S.W2 + (n >> 3) * 128 + (k >> 3) * 8192 + (k & 7) * 16 + (n & 7) * 2) =
         __float2bfloat16_rn(p.W2[e]);
   }
-  for (int e = tid; e < 16 * 128; e += 512) {
+  for (int e = tid; e < 16 * 128; e += kDecThreads) {
     const int k = e / 128, n = e % 128;
     *reinterpret_cast<__nv_bfloat16*>(S.W1 + (n >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 + (n & 7) * 2) =
         __float2bfloat16_rn(p.W1[e]);
   }
-  for (int e = tid; e < 128; e += 512) S.b1[e] = p.b1[e];
-  for (int e = tid; e < 512; e += 512) S.b2[e] = p.b2[e];
+  for (int e = tid; e < 128; e += kDecThreads) S.b1[e] = p.b1[e];
+  for (int e = tid; e < 512; e += kDecThreads) S.b2[e] = p.b2[e];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)));
+    unsigned long long* bars[7] = {&S.z_ready, &S.d1_full, &S.h_ready, &S.d2a_full, &S.d2b_full, &S.b_free, &S.drain};
+    for (int b = 0; b < 7; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars[b])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1468,99 +1485,140 @@ __global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = S.tmem;
-  const uint32_t idesc1 = idesc_bf16(128, 128, 1), idesc2 = idesc_bf16(128, 256, 1);
   const long long ntiles = (p.npix + 127) / 128;
-  uint32_t phase = 0;
-  bool ok = true;
-  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const long long base = t * 128;
-    // z rows -> A1 (threads with cq < 2 write chunk cq of row `row`)
-    if (cq < 2) {
-      const long long pix = base + row;
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = 0.f;
-      if (pix < p.npix) {
-        const float4 a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * cq);
-        const float4 b = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * cq + 4);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-      }
-      uint32_t pk[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
-      }
-      *reinterpret_cast<uint4*>(S.Z + (row >> 3) * 256 + cq * 128 + (row & 7) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      mma_bf16(tmem, smem_desc(smem_u32(S.Z), 128, 256), smem_desc(smem_u32(S.W1), 2048, 128), idesc1, 0u);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&S.mbar)));
-    }
-    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar), phase)) != 0;
-    phase ^= 1u;
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    {
-      // hidden layer: columns [32 cq, 32 cq + 32) of D1 for pixel row `row`
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(32 * cq), v);
-      uint32_t pk[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float h0 = gelu_exact(v[2 * i] + S.b1[32 * cq + 2 * i]);
-        const float h1 = gelu_exact(v[2 * i + 1] + S.b1[32 * cq + 2 * i + 1]);
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(h0, h1);
-        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        *reinterpret_cast<uint4*>(S.H + (row >> 3) * 2048 + (4 * cq + c) * 128 + (row & 7) * 16) =
-            make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
+
+  if (warp == 16) {
+    // the products
+    if (lane == 0) {
+      const uint32_t idesc1 = idesc_bf16(128, 128, 1), idesc2 = idesc_bf16(128, 256, 1);
       const uint32_t a0 = smem_u32(S.H), b0 = smem_u32(S.W2);
-      for (int nh = 0; nh < 2; ++nh)
+      bool ok = true;
+      int n = 0;
+      for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++n) {
+        const uint32_t par = (uint32_t)n & 1u;
+        if (!mbar_wait(smem_u32(&S.z_ready), par)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        mma_bf16(tmem, smem_desc(smem_u32(S.Z), 128, 256), smem_desc(smem_u32(S.W1), 2048, 128), idesc1, 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&S.d1_full)));
+        if (!mbar_wait(smem_u32(&S.h_ready), par)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int k16 = 0; k16 < 8; ++k16)
-          mma_bf16(tmem + (uint32_t)(256 * nh), smem_desc(a0 + k16 * 256, 128, 2048),
-                   smem_desc(b0 + (uint32_t)nh * 4096u + (uint32_t)k16 * 16384u, 8192, 128), idesc2,
-                   k16 > 0 ? 1u : 0u);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&S.mbar)));
-    }
-    ok = __syncthreads_and(mbar_wait(smem_u32(&S.mbar), phase)) != 0;
-    phase ^= 1u;
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    {
-      const uint32_t box = ((smem_u32(S.H) + 1023u) & ~1023u) + (uint32_t)warp * 4096u;
-      const uint32_t rowa = box + (uint32_t)lane * 128u;
-      const int row0 = (int)(base + 32 * lg);
-      for (int s4 = 0; s4 < 4; ++s4) {
-        const int c = 128 * cq + 32 * s4;
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c, v);
-        if (s4 > 0) {
-          // the previous box must have been read out before it is overwritten
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-          __syncwarp();
-        }
+          mma_bf16(tmem, smem_desc(a0 + k16 * 256, 128, 2048), smem_desc(b0 + (uint32_t)k16 * 16384u, 8192, 128),
+                   idesc2, k16 > 0 ? 1u : 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&S.d2a_full)));
+        // half b of the previous tile has been read out
+        if (n > 0 && !mbar_wait(smem_u32(&S.b_free), par ^ 1u)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int k16 = 0; k16 < 8; ++k16)
+          mma_bf16(tmem + 256u, smem_desc(a0 + k16 * 256, 128, 2048),
+                   smem_desc(b0 + 4096u + (uint32_t)k16 * 16384u, 8192, 128), idesc2, k16 > 0 ? 1u : 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&S.d2b_full)));
+      }
+      if (!ok) flag_status(p.status, GS_ERR_TIMEOUT);
+      // every product issued has completed before tensor memory is freed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&S.drain)));
+      mbar_wait(smem_u32(&S.drain), 0u);
+    }
+  } else {
+    const int g = warp >> 3, gw = warp & 7;  // group (0: A, 1: B), warp in the group
+    const int lq = warp & 3, cb = gw >> 2;   // tensor-memory lane quarter, column block of the group's half
+    const int row = 32 * lq + lane;          // pixel row of the tile this thread reads back
+    const uint32_t lane_off = (uint32_t)(32 * lq) << 16;
+    const uint32_t box = ((smem_u32(S.Ybox) + 1023u) & ~1023u) + (uint32_t)warp * 2048u;
+    const uint32_t rowa = box + (uint32_t)lane * 64u;
+    bool ok = true;
+    int n = 0;
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++n) {
+      const uint32_t par = (uint32_t)n & 1u;
+      const long long base = t * 128;
+      if (g == 0) {
+        // z rows -> A1: two threads per row, 8 latents each (Z was last read by
+        // the previous tile's G1, complete before its D1 was read)
+        {
+          const int r = tid >> 1, h8 = tid & 1;
+          const long long pix = base + r;
+          float v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = 0.f;
+          if (pix < p.npix) {
+            const float4 a = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * h8);
+            const float4 b = *reinterpret_cast<const float4*>(p.z + pix * 16 + 8 * h8 + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+          }
+          uint32_t pk[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
+          *reinterpret_cast<uint4*>(S.Z + (r >> 3) * 256 + h8 * 128 + (r & 7) * 16) =
+              make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        // the previous tile's half a has been read out (its loads waited for)
+        // and z is in: the products may overwrite half a
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (tid == 0) mbar_arrive(smem_u32(&S.z_ready));
+        ok = dec_group_and(mbar_wait(smem_u32(&S.d1_full), par), 0);
+        // H is overwritten only after the previous tile's G2b has read it
+        if (ok && n > 0) ok = dec_group_and(mbar_wait(smem_u32(&S.d2b_full), par ^ 1u), 0);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // hidden layer: columns [64 cb, 64 cb + 64) of D1 for pixel row `row`
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+          const int c0 = 64 * cb + 32 * k;
+          float v[32];
+          tmem_ld32(tmem + lane_off + (uint32_t)c0, v);
+          uint32_t pk[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float h0 = gelu_exact(v[2 * i] + S.b1[c0 + 2 * i]);
+            const float h1 = gelu_exact(v[2 * i + 1] + S.b1[c0 + 2 * i + 1]);
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(h0, h1);
+            pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4*>(S.H + (row >> 3) * 2048 + (c0 / 8 + c) * 128 + (row & 7) * 16) =
+                make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (tid == 0) mbar_arrive(smem_u32(&S.h_ready));
+        ok = dec_group_and(mbar_wait(smem_u32(&S.d2a_full), par), 0);
+      } else {
+        ok = dec_group_and(mbar_wait(smem_u32(&S.d2b_full), par), 1);
+      }
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // drain: this warp's 128 columns of its group's half, 16 at a time
+      const int colbase = 256 * g + 128 * cb;
+      const int row0 = (int)(base + 32 * lq);
+#pragma unroll 1
+      for (int s8 = 0; s8 < 8; ++s8) {
+        const int c = colbase + 16 * s8;
+        float v[2][8];
+        tmem_ld8(tmem + lane_off + (uint32_t)c, v[0]);
+        tmem_ld8(tmem + lane_off + (uint32_t)(c + 8), v[1]);
+        tmem_wait_ld<2>(v);
+        // the box's previous store has read it
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
           const float4 b = *reinterpret_cast<const float4*>(&S.b2[c + 4 * q]);
-          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + (uint32_t)((q ^ (lane & 7)) << 4)),
-                       "f"(v[4 * q] + b.x), "f"(v[4 * q + 1] + b.y), "f"(v[4 * q + 2] + b.z),
-                       "f"(v[4 * q + 3] + b.w)
+          const float* x = &v[q >> 1][4 * (q & 1)];
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + (uint32_t)((q ^ ((lane >> 1) & 3)) << 4)),
+                       "f"(x[0] + b.x), "f"(x[1] + b.y), "f"(x[2] + b.z), "f"(x[3] + b.w)
                        : "memory");
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1572,18 +1630,22 @@ __global__ void __launch_bounds__(512, 1) k_decoder_fwd_tc(const DecTcParams p,
           asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
       }
-      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      __syncwarp();
+      // this half of the tile's tensor memory has been read out
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (g == 1) {
+        asm volatile("bar.sync 2, 256;" ::: "memory");
+        if (tid == 256) mbar_arrive(smem_u32(&S.b_free));
+      }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    if (!ok && lane == 0) flag_status(p.status, GS_ERR_TIMEOUT);
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this warp's stores complete
   }
-  if (!ok && tid == 0) flag_status(p.status, GS_ERR_TIMEOUT);
-  if (!ok) mbar_wait(smem_u32(&S.mbar), phase ^ 1u);  // bounded drain of the outstanding commit
-  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this warp's stores complete
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
 }
 
 }  // namespace
@@ -1828,16 +1890,16 @@ extern "C" gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, cons
   if (npix < 0 || (npix > 0 && (!z || !y)) || !aligned(z, 16) || !aligned(y, 16)) return GS_ERR_INVALID_ARG;
   if (npix == 0) return GS_OK;
   if (npix >= (1ll << 31)) return GS_ERR_UNSUPPORTED;  // row coordinates of the output tensor map are int32
-  // output y [npix, 512] fp32 as a 2D tensor for TMA stores of 32 x 32 boxes, 128-byte swizzle
+  // output y [npix, 512] fp32 as a 2D tensor for TMA stores of 16-column x 32-row boxes, 64-byte swizzle
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return GS_ERR_CUDA;
   CUtensorMap ymap;
   const cuuint64_t dims[2] = {512, (cuuint64_t)npix};
   const cuuint64_t strides[1] = {512 * sizeof(float)};
-  const cuuint32_t boxdim[2] = {32, 32};
+  const cuuint32_t boxdim[2] = {16, 32};
   const cuuint32_t estr[2] = {1, 1};
   if (encode(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, y, dims, strides, boxdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return GS_ERR_CUDA;
   DecTcParams p;
@@ -1863,7 +1925,7 @@ extern "C" gs_status gs_decoder_fwd_tc(const gs_decoder* dec, int64_t npix, cons
   const unsigned blocks = (unsigned)(ntiles < sms ? ntiles : sms);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GS_TRACE("k_decoder_fwd_tc", st);
-  k_decoder_fwd_tc<<<blocks, 512, smem, st>>>(p, ymap);
+  k_decoder_fwd_tc<<<blocks, kDecThreads, smem, st>>>(p, ymap);
   return last_launch_status();
 }
 
