@@ -1097,18 +1097,21 @@ def decoder_form(args, peaks, kind, timing=True, label_query=False):
         plain.ensure_capacity(c, *scene[:4])
     torch.cuda.synchronize()
     if args.profile:
-        # the tensor-core training evaluation alone (65,536 samples of the first
-        # training pose), --steps times between cudaProfilerStart/Stop, after
-        # --warmup untimed ones
+        # the tensor-core training evaluation (65,536 samples of the first
+        # training pose) and the tensor-core inference of the whole latent map,
+        # --steps times between cudaProfilerStart/Stop, after --warmup untimed ones
         c = train_cams[0]
         z_map = trn.render_latents(c).contiguous()
         tgt_map = tc.forward(c, *scene, feats_bf)["feat"].reshape(HW, N).contiguous()
+        y_map = torch.empty(HW, N, device=dev)
         for it in range(args.warmup):
             dec.train_eval_tc(z_map, tgt_map, 65536, 7000 + it, 1.0 / (65536 * 512))
+            dec.forward_tc(z_map, out=y_map)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         for it in range(args.steps):
             dec.train_eval_tc(z_map, tgt_map, 65536, 8000 + it, 1.0 / (65536 * 512))
+            dec.forward_tc(z_map, out=y_map)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         return None
